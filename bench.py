@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark: simulate the 30-qubit, 20-cycle Sycamore-pattern circuit (5x6 grid, ABCDCDAB,
+fSim(pi/2, pi/6), random sqrt(X/Y/W)) on one GB300 and report amplitude updates per second.
+
+One step = one pass of the whole hot path over one circuit: aggregation planning and FP64
+composition (host), reset to |0...0>, every fused block applied on the device, and the
+norm / Porter-Thomas / XEB reduction.  The state (8 GiB complex64) is larger than L2, so no
+flush is needed between steps.
+
+metric value = 2^n * (original gates) * steps / device time   ("gate" amplitude updates/s)
+pass updates = 2^n * (fused blocks) * steps / device time      (roofline basis, 16 B/amp/pass)
+
+--impl reference times the CPU oracle (complex128, gate by gate) on the host cores on a bounded
+sample of the same workload (the first gates of the circuit on the full 30-qubit state).
+Multi-GPU (torchrun): independent replicas, one circuit per rank (seed = rank), no collective
+on the data path; time = max over ranks, value = all ranks' updates / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "syc30_5x6_d20"
+METRIC = "amplitude-updates/s"
+UNIT = "amp-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--kmax", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-gates", type=int, default=42)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(circ, sample_gates: int, steps: int = 1):
+    """Time the oracle (complex128, gate by gate, all host cores) on the first `sample_gates`
+    gates of the circuit applied to the full state."""
+    import oracle
+    import syc_inputs as si
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    sample = si.Circuit(circ.n_qubits, circ.gates[:sample_gates], name=circ.name)
+    psi = oracle.basis_state(circ.n_qubits, 0)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.apply_gates(psi, sample)
+        times.append(time.perf_counter() - t0)
+    del psi
+    amps = float(1 << circ.n_qubits)
+    return {"value": amps * sample_gates * steps / sum(times), "unit": UNIT,
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {sample_gates} of {circ.n_gates} gates of {circ.name} on the full "
+                      f"2^{circ.n_qubits} complex128 state, {steps} run(s)",
+            "seconds": sum(times)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import syc_inputs as si
+    circ = si.workload_circuit(args.workload, seed=0)
+    g = max(1, min(args.cpu_sample_gates, 8))
+    total_steps = args.warmup + args.steps
+    import oracle
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    psi = oracle.basis_state(circ.n_qubits, 0)
+    sample = si.Circuit(circ.n_qubits, circ.gates[:g], name=circ.name)
+    times = []
+    for i in range(total_steps):
+        t0 = time.perf_counter()
+        oracle.apply_gates(psi, sample)
+        times.append(time.perf_counter() - t0)
+    t = sum(times[args.warmup:])
+    amps = float(1 << circ.n_qubits)
+    value = amps * g * args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random circuit)",
+            "config": {"workload": args.workload, "n_qubits": circ.n_qubits,
+                       "sample": f"each step applies the first {g} gates of the circuit"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"first {g} of {circ.n_gates} gates per step, full state"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+    from paper_1910_09534_gb300 import build as pkg_build
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    pkg_build.build()
+
+    circ = si.workload_circuit(args.workload, seed=rank)
+    n = circ.n_qubits
+    amps = 1 << n
+    gates = pkg.gates_array(circ)
+    h = pkg.sim_create(n, 0, device=local)
+    _, stream_ptr = pkg.sim_state_ptr(h)
+    stream = torch.cuda.ExternalStream(stream_ptr)
+
+    def step():
+        plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
+        pkg.sim_reset(h)
+        pkg.sim_apply_plan(h, plan)
+        out = pkg.sim_reduce(h)
+        nb = pkg.sim_plan_info(plan)[0]
+        pkg.sim_plan_destroy(plan)
+        return out, nb
+
+    for _ in range(args.warmup):
+        (norm, s2, xeb), nblocks = step()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pkg.sim_profile_enable(h, True)
+    launches0 = pkg.sim_launch_count(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            (norm, s2, xeb), nblocks = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = pkg.sim_launch_count(h) - launches0
+    a_n, a_ms, a_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
+    r_n, r_ms, r_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_REDUCE)
+    pkg.sim_profile_enable(h, False)
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_updates = float(amps) * circ.n_gates * args.steps * ws
+    value = total_updates / (ms_max / 1e3)
+    pass_updates = float(amps) * nblocks * args.steps * ws / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: gate records from pinned host
+    # memory in, all 2^n amplitudes out to pinned host memory, every step
+    gates_pinned = pkg.pinned_array(gates.size, dtype=pkg._native.GATE_DTYPE)
+    gates_pinned[:] = gates
+    out = pkg.pinned_array(amps, dtype=np.complex64)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax)
+        pkg.sim_reset(h)
+        pkg.sim_apply_plan(h, plan)
+        pkg.sim_amplitudes(h, out=out)
+        pkg.sim_plan_destroy(plan)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    et = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = float(amps) * circ.n_gates * args.e2e_steps * ws / float(et.item())
+    matrix_bytes = 0
+    plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
+    for i in range(pkg.sim_plan_info(plan)[0]):
+        tg, _ = pkg.sim_plan_block(plan, i)
+        matrix_bytes += 8 * (1 << (2 * len(tg)))
+    pkg.sim_plan_destroy(plan)
+    sanity = out[:4].copy()
+    pkg.sim_host_free(out.ctypes.data)
+    pkg.sim_host_free(gates_pinned.ctypes.data)
+    pkg.sim_destroy(h)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = a_bytes / (a_ms / 1e3) / 1e9 if a_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random Sycamore-pattern circuit; state from |0...0>)",
+        "config": {"workload": args.workload, "n_qubits": n, "cycles": si.WORKLOADS[args.workload]["cycles"],
+                   "gates": circ.n_gates, "kmax": args.kmax, "fused_blocks": nblocks,
+                   "state_bytes": amps * 8, "l2": "state 8 GiB > 129 MB L2: no flush needed",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
+        "pass_updates_per_s": pass_updates,
+        "gpu_launches": launches,
+        "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "fused apply (k_apply_direct/k_apply_tiled)",
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "launches": a_n, "avg_launch_ms": a_ms / max(a_n, 1)},
+        "breakdown_ms_per_step": {"apply": a_ms / args.steps, "reduce": r_ms / args.steps,
+                                  "other": ms_max / args.steps - (a_ms + r_ms) / args.steps},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes + matrix_bytes),
+                "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps},
+        "clocks": clk.summary(),
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(circ, args.cpu_sample_gates)
+    _ = sanity
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

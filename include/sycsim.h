@@ -1,0 +1,212 @@
+/*
+ * sycsim.h -- C ABI of the GB300 (sm_103a) slice-and-store state-vector
+ * simulator for random Sycamore-pattern circuits, after Pednault et al.,
+ * "Leveraging Secondary Storage to Simulate Deep 54-qubit Sycamore Circuits"
+ * (arXiv:1910.09534).
+ *
+ * Problem statement (Abstract; Sect. 5): simulate a circuit and output all of
+ * its amplitudes.  The method (Sect. 2, 4, 5): evolve the full state
+ * ("Schroedinger approach"), with gates aggregated into k-qubit blocks whose
+ * 2^k x 2^k matrices are applied to the state (Sect. 5); qubits split into
+ * local and sliced ("global") ones, reorganised between phases (Sect. 4); and
+ * slices kept in secondary storage -- here pinned host memory -- and streamed
+ * through device memory phase by phase (Sect. 4, logical files).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: SIM_OK (0) or a negative SIM_E_* code.
+ *    Nothing aborts, traps or exits.  sim_last_error(h) gives a message for the
+ *    last failure on handle h (on the calling thread when h is NULL).
+ *  - Qubit q is bit q of the LOGICAL amplitude index (little-endian).  The
+ *    library may store the state under another bit order (its layout); calls
+ *    that read or write amplitudes say which order they use.
+ *  - Matrices are row-major, interleaved complex128 (re, im); bit j of a
+ *    row/column index is the value of targets[j].
+ *  - The library copies every input array before returning; the caller may
+ *    free or reuse it at once.  Output buffers belong to the caller.
+ *  - Asynchronous calls are ordered on the handle's CUDA stream; sim_sync()
+ *    waits for them.  A handle must not be used by two host threads at once.
+ */
+#ifndef SYCSIM_H
+#define SYCSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SIM_OK 0
+#define SIM_E_INVAL (-1)      /* bad argument (range, duplicate target, non-bijection, ...) */
+#define SIM_E_NOMEM_DEV (-2)  /* device allocation failed */
+#define SIM_E_NOMEM_HOST (-3) /* pinned host allocation failed */
+#define SIM_E_NONLOCAL (-4)   /* a target qubit is currently sliced (Sect. 4: gates act on local qubits) */
+#define SIM_E_CUDA (-5)       /* a CUDA call failed; see sim_last_error */
+#define SIM_E_TIMEOUT (-6)    /* a bounded wait ran out */
+#define SIM_E_BUSY (-7)       /* resource exhausted right now (e.g. serving budget) */
+#define SIM_E_UNSUPPORTED (-8)/* valid request this build does not implement */
+
+/* ---- arithmetic of the gate apply ------------------------------------ */
+#define SIM_FP32 0   /* CUDA-core FP32 FMA (the default) */
+
+/* ---- amplitude dtypes for readout/load ------------------------------- */
+#define SIM_C64 0    /* complex64: 2 x float32, interleaved */
+#define SIM_C128 1   /* complex128: 2 x float64, interleaved */
+
+/* ---- state storage ---------------------------------------------------- */
+#define SIM_STORE_DEVICE 0 /* whole state resident in device memory (HBM) */
+
+typedef struct sim_s sim_t;
+
+typedef struct sim_opts {
+    int store;          /* SIM_STORE_DEVICE */
+    int device;         /* CUDA device ordinal */
+    void *stream;       /* cudaStream_t to order work on; NULL = library-owned stream */
+    void *ext_state;    /* optional caller-owned device buffer for the state (>= 8 * 2^n bytes),
+                           e.g. a torch tensor's storage; NULL = library allocates */
+    uint64_t ext_bytes; /* size of ext_state in bytes */
+    int reserved[8];
+} sim_opts;
+
+/* Message for the last failure on h (h == NULL: the calling thread's last failure
+ * not tied to a handle).  The string is owned by the library and valid until the
+ * next call on h. */
+const char *sim_last_error(const sim_t *h);
+
+/* Library version string, and the CUDA device architecture it was built for. */
+const char *sim_version(void);
+
+/* Create a simulator for n_qubits (1..40) with `slice_bits` sliced qubits
+ * (Sect. 4: the top slice_bits physical bits address 2^slice_bits slices of
+ * 2^(n - slice_bits) amplitudes; gates may only target local qubits).
+ * The state starts as |0...0>.  opts may be NULL (device 0, own stream, own
+ * buffer).  On success *out is a handle to pass to sim_destroy(). */
+int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out);
+int sim_destroy(sim_t *h);
+
+/* n_qubits, slice_bits and the current layout: bit_of[q] = physical bit that
+ * holds logical qubit q (array of n_qubits ints, may be NULL). */
+int sim_info(const sim_t *h, int *n_qubits, int *slice_bits, int *bit_of);
+
+/* Device pointer of the state buffer (physical order, complex64) and the
+ * cudaStream_t the handle orders its work on. */
+int sim_state_ptr(const sim_t *h, void **dptr, void **stream);
+
+/* Set the state to the computational basis state |basis> (logical index),
+ * asynchronously on the handle's stream. */
+int sim_reset(sim_t *h, uint64_t basis);
+
+/* Aggregated-gate apply (Sect. 5: gates aggregated into k-qubit kernels given by
+ * 2^k x 2^k unitary matrices, applied to the state as matrix-vector products).
+ * For every group of 2^k amplitudes that differ only in the target bits,
+ * psi_g <- M psi_g, in place.  k in 1..6; targets: k distinct logical qubits, all
+ * local (SIM_E_NONLOCAL otherwise); matrix: 2^k x 2^k complex128, row-major,
+ * bit j of its index <-> targets[j]; precision: SIM_FP32.  Asynchronous. */
+int sim_apply_fused(sim_t *h, int k, const int *targets, const double *matrix, int precision);
+
+/* Qubit reorganisation (Sect. 4: between phases the memory layout is changed so
+ * that other qubits become local/global).  perm[q] = new physical bit of logical
+ * qubit q; must be a bijection on 0..n-1.  The logical state is unchanged; the
+ * amplitudes move so that physical index pi(i) holds what i held, pi moving bit
+ * bit_of[q] to bit perm[q].  Bit-exact (pure data movement), in place.
+ * Asynchronous. */
+int sim_permute(sim_t *h, const int *perm);
+
+/* Copy `count` amplitudes starting at index `first` to host memory `out`
+ * (dtype SIM_C64 or SIM_C128), in logical order (physical_order = 0) or in
+ * the stored physical order (physical_order = 1).  Synchronous: returns when
+ * out is filled.  out may be pageable or pinned (pinned is faster). */
+int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtype,
+                   int physical_order);
+
+/* Overwrite `count` amplitudes starting at `first` with complex64 values from
+ * host memory `src` (logical or physical order as above).  Synchronous. */
+int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *src,
+                        int physical_order);
+
+/* Reductions over p_i = |psi_i|^2 (used to check simulations; not in the paper):
+ * norm = sum p, sum_p2_scaled = 2^n sum p^2 (Porter-Thomas: about 2), and
+ * xeb = 2^n sum p^2 - 1 (linear cross-entropy of the ideal distribution).
+ * Per-thread partial sums in FP32 over 16 amplitudes, combined in FP64 in a
+ * fixed order (deterministic).  Synchronous.  Any output pointer may be NULL. */
+int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb);
+
+/* Wait for all work queued on the handle's stream, at most timeout_ms
+ * milliseconds (< 0: no limit).  SIM_E_TIMEOUT if it did not finish. */
+int sim_sync(sim_t *h, int timeout_ms);
+
+/* ---- per-launch profiling (kernel durations on the handle's stream) ------
+ * sim_profile_enable(h, 1) clears the counters and brackets every kernel
+ * launch that follows with a pair of CUDA events; sim_profile_read() waits for
+ * the stream and returns, for one kernel class, the number of launches, their
+ * summed device time in ms and their algorithmic bytes (apply: 16 B per
+ * amplitude; permute: 16 B per amplitude moved; reduce: 8 B per amplitude).
+ * sim_launch_count() is the number of kernels the handle has launched. */
+#define SIM_PROF_APPLY 0
+#define SIM_PROF_PERMUTE 1
+#define SIM_PROF_REDUCE 2
+#define SIM_PROF_OTHER 3
+int sim_profile_enable(sim_t *h, int on);
+int sim_profile_read(sim_t *h, int cls, uint64_t *launches, double *total_ms, double *alg_bytes);
+int sim_launch_count(const sim_t *h, uint64_t *n);
+
+/* Pinned host memory helpers for callers that want fast copies. */
+int sim_host_alloc(size_t bytes, void **out);
+int sim_host_free(void *p);
+
+/* ---- circuits and the aggregation planner ----------------------------- */
+
+/* Gate kinds (Sect. 3): single-qubit sqrt(X), sqrt(Y), sqrt(W) -- read as
+ * (I - iP)/sqrt(2) -- and the two-qubit fSim of Eq. 1 with theta, phi and
+ * the detunings D+, D-, D-,off; plus caller-given 1- and 2-qubit matrices. */
+#define SIM_GATE_SQRT_X 0
+#define SIM_GATE_SQRT_Y 1
+#define SIM_GATE_SQRT_W 2
+#define SIM_GATE_FSIM 3
+#define SIM_GATE_U1 4 /* u[0..7]: 2x2 complex128 row-major interleaved */
+#define SIM_GATE_U2 5 /* u[0..31]: 4x4 complex128, index b(q0) + 2 b(q1) */
+
+typedef struct sim_gate {
+    int32_t kind;
+    int32_t q0, q1; /* q1 ignored for single-qubit kinds */
+    int32_t reserved;
+    double theta, phi, dplus, dminus, dminus_off; /* fSim parameters (Eq. 1) */
+    double u[32];                                 /* SIM_GATE_U1 / SIM_GATE_U2 matrix */
+} sim_gate;
+
+/* Matrix of one gate record (2x2 or 4x4 complex128, row-major interleaved, 32
+ * doubles of room).  Returns the dimension (2 or 4) or SIM_E_INVAL.  Host-only. */
+int sim_gate_matrix(const sim_gate *g, double *out);
+
+typedef struct sim_plan_s sim_plan_t;
+
+typedef struct sim_plan_opts {
+    int kmax;      /* largest block width, 1..6 (Sect. 5 uses k_max = 5) */
+    int precision; /* arithmetic for the blocks' apply: SIM_FP32 */
+    int reserved[6];
+} sim_plan_opts;
+
+/* Aggregation planner (Sect. 5: gates grouped into blocks of at most k_max
+ * qubits; Appendix A "new cache" lines list such groups).  Partitions the gate
+ * list into blocks that respect gate order on every qubit and composes each
+ * block's 2^k x 2^k matrix in FP64 (later gates multiply from the left).
+ * Host-side; the plan is immutable and may be applied to many handles. */
+int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
+                    sim_plan_t **out);
+int sim_plan_destroy(sim_plan_t *p);
+
+/* Number of blocks, number of gates planned and the widest block. */
+int sim_plan_info(const sim_plan_t *p, int *n_blocks, int *n_gates, int *max_k);
+
+/* Block i: its width k, its targets (k ints, ascending logical qubits) and its
+ * matrix (2^k x 2^k complex128, bit j <-> targets[j]); any output may be NULL. */
+int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *matrix);
+
+/* Apply every block of the plan in order (each as sim_apply_fused).  Async. */
+int sim_apply_plan(sim_t *h, const sim_plan_t *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SYCSIM_H */

@@ -1,0 +1,306 @@
+"""ctypes binding of libsycsim.so (the C ABI in include/sycsim.h).
+
+Argument marshalling only: every function forwards to the native library with the
+same name.  Failures raise ``SimError`` carrying the status code and the library's
+message.  Importing this module does not need a GPU; calling anything that touches
+the device does.  If the library has not been built, ``lib()`` raises -- there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsycsim.so")
+
+SIM_OK = 0
+SIM_E_INVAL = -1
+SIM_E_NOMEM_DEV = -2
+SIM_E_NOMEM_HOST = -3
+SIM_E_NONLOCAL = -4
+SIM_E_CUDA = -5
+SIM_E_TIMEOUT = -6
+SIM_E_BUSY = -7
+SIM_E_UNSUPPORTED = -8
+
+SIM_FP32 = 0
+SIM_C64 = 0
+SIM_C128 = 1
+SIM_STORE_DEVICE = 0
+
+SIM_GATE_SQRT_X = 0
+SIM_GATE_SQRT_Y = 1
+SIM_GATE_SQRT_W = 2
+SIM_GATE_FSIM = 3
+SIM_GATE_U1 = 4
+SIM_GATE_U2 = 5
+
+# numpy mirror of struct sim_gate
+GATE_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("reserved", "<i4"),
+                       ("theta", "<f8"), ("phi", "<f8"), ("dplus", "<f8"), ("dminus", "<f8"),
+                       ("dminus_off", "<f8"), ("u", "<f8", (32,))], align=True)
+
+
+class SimOpts(ctypes.Structure):
+    _fields_ = [("store", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("ext_state", ctypes.c_void_p), ("ext_bytes", ctypes.c_uint64),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("kmax", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    # name: (restype, argtypes)
+    "sim_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "sim_version": (ctypes.c_char_p, []),
+    "sim_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_state_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_reset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sim_apply_fused": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int]),
+    "sim_permute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sim_load_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_void_p, ctypes.c_int]),
+    "sim_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sim_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sim_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "sim_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_void_p]),
+    "sim_host_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_gate_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "sim_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_plan_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "sim_apply_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """The loaded native library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1910_09534_gb300.build.build() "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return a
+
+
+def _check(rc: int, handle=None):
+    if rc < 0:
+        msg = lib().sim_last_error(handle)
+        raise SimError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---------------------------------------------------------------- C ABI, same names
+
+def sim_version() -> str:
+    return lib().sim_version().decode()
+
+
+def sim_create(n_qubits: int, slice_bits: int = 0, device: int = 0, stream: int | None = None,
+               ext_state: int | None = None, ext_bytes: int = 0):
+    o = SimOpts()
+    o.store = SIM_STORE_DEVICE
+    o.device = device
+    o.stream = stream
+    o.ext_state = ext_state
+    o.ext_bytes = ext_bytes
+    h = ctypes.c_void_p()
+    _check(lib().sim_create(n_qubits, slice_bits, ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def sim_destroy(h) -> None:
+    _check(lib().sim_destroy(h))
+
+
+def sim_info(h):
+    n, s = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_info(h, ctypes.byref(n), ctypes.byref(s), None), h)
+    bit_of = np.zeros(n.value, dtype=np.int32)
+    _check(lib().sim_info(h, None, None, _ptr(bit_of)), h)
+    return n.value, s.value, bit_of
+
+
+def sim_state_ptr(h):
+    p, st = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().sim_state_ptr(h, ctypes.byref(p), ctypes.byref(st)), h)
+    return p.value, st.value
+
+
+def sim_reset(h, basis: int = 0) -> None:
+    _check(lib().sim_reset(h, basis), h)
+
+
+def sim_apply_fused(h, targets, matrix, precision: int = SIM_FP32) -> None:
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    m = np.ascontiguousarray(matrix, dtype=np.complex128)
+    if m.shape != (1 << t.size, 1 << t.size):
+        raise ValueError("matrix must be 2^k x 2^k")
+    _check(lib().sim_apply_fused(h, int(t.size), _ptr(t), _ptr(m), precision), h)
+
+
+def sim_permute(h, perm) -> None:
+    p = np.ascontiguousarray(perm, dtype=np.int32)
+    _check(lib().sim_permute(h, _ptr(p)), h)
+
+
+def sim_amplitudes(h, first: int = 0, count: int | None = None, dtype: int = SIM_C64,
+                   physical_order: bool = False, out: np.ndarray | None = None) -> np.ndarray:
+    n, _, _ = sim_info(h)
+    if count is None:
+        count = (1 << n) - first
+    npdt = np.complex64 if dtype == SIM_C64 else np.complex128
+    if out is None:
+        out = np.empty(count, dtype=npdt)
+    assert out.dtype == npdt and out.size >= count and out.flags.c_contiguous
+    _check(lib().sim_amplitudes(h, first, count, _ptr(out), dtype, int(physical_order)), h)
+    return out
+
+
+def sim_load_amplitudes(h, src: np.ndarray, first: int = 0, physical_order: bool = False) -> None:
+    a = np.ascontiguousarray(src, dtype=np.complex64)
+    _check(lib().sim_load_amplitudes(h, first, a.size, _ptr(a), int(physical_order)), h)
+
+
+def sim_reduce(h):
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sim_reduce(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
+
+
+def sim_sync(h, timeout_ms: int = -1) -> None:
+    _check(lib().sim_sync(h, timeout_ms), h)
+
+
+SIM_PROF_APPLY = 0
+SIM_PROF_PERMUTE = 1
+SIM_PROF_REDUCE = 2
+SIM_PROF_OTHER = 3
+
+
+def sim_profile_enable(h, on: bool = True) -> None:
+    _check(lib().sim_profile_enable(h, int(on)), h)
+
+
+def sim_profile_read(h, cls: int):
+    """(launches, total_ms, algorithmic_bytes) of one kernel class since profiling was enabled."""
+    n, ms, b = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sim_profile_read(h, cls, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)), h)
+    return n.value, ms.value, b.value
+
+
+def sim_launch_count(h) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().sim_launch_count(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def sim_host_alloc(nbytes: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().sim_host_alloc(nbytes, ctypes.byref(p)))
+    return p.value
+
+
+def sim_host_free(p: int) -> None:
+    _check(lib().sim_host_free(ctypes.c_void_p(p)))
+
+
+def pinned_array(count: int, dtype=np.complex64):
+    """numpy array over pinned host memory; free with sim_host_free(arr.ctypes.data)."""
+    nbytes = int(count) * np.dtype(dtype).itemsize
+    p = sim_host_alloc(max(nbytes, 1))
+    buf = (ctypes.c_char * max(nbytes, 1)).from_address(p)
+    return np.frombuffer(buf, dtype=dtype, count=count)
+
+
+def gates_array(circuit) -> np.ndarray:
+    """struct sim_gate records of a syc_inputs.Circuit (or of (kind,q0,q1,theta,phi) tuples)."""
+    gates = circuit.gates if hasattr(circuit, "gates") else circuit
+    a = np.zeros(len(gates), dtype=GATE_DTYPE)
+    for i, (kind, q0, q1, th, ph) in enumerate(gates):
+        a[i]["kind"], a[i]["q0"], a[i]["q1"] = kind, q0, q1
+        a[i]["theta"], a[i]["phi"] = th, ph
+    return a
+
+
+def sim_gate_matrix(gate) -> np.ndarray:
+    g = np.zeros(1, dtype=GATE_DTYPE)
+    g[0] = gate
+    out = np.zeros(32, dtype=np.float64)
+    d = _check(lib().sim_gate_matrix(_ptr(g), _ptr(out)))
+    return out[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
+
+
+def sim_plan_create(n_qubits: int, gates: np.ndarray, kmax: int = 4, precision: int = SIM_FP32):
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    o = PlanOpts()
+    o.kmax = kmax
+    o.precision = precision
+    p = ctypes.c_void_p()
+    _check(lib().sim_plan_create(n_qubits, int(g.size), _ptr(g), ctypes.byref(o), ctypes.byref(p)))
+    return p
+
+
+def sim_plan_destroy(p) -> None:
+    _check(lib().sim_plan_destroy(p))
+
+
+def sim_plan_info(p):
+    nb, ng, mk = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_plan_info(p, ctypes.byref(nb), ctypes.byref(ng), ctypes.byref(mk)))
+    return nb.value, ng.value, mk.value
+
+
+def sim_plan_block(p, i: int):
+    k = ctypes.c_int()
+    _check(lib().sim_plan_block(p, i, ctypes.byref(k), None, None))
+    t = np.zeros(k.value, dtype=np.int32)
+    m = np.zeros((1 << k.value, 1 << k.value), dtype=np.complex128)
+    _check(lib().sim_plan_block(p, i, None, _ptr(t), _ptr(m)))
+    return t, m
+
+
+def sim_apply_plan(h, p) -> None:
+    _check(lib().sim_apply_plan(h, p), h)
+
+
+def exported_symbols() -> list:
+    return list(_SIGS)

@@ -1,0 +1,419 @@
+// apply.cu -- aggregated k-qubit gate apply on CUDA cores, FP32 (Sect. 5: gates are
+// aggregated into k-qubit kernels, each a 2^k x 2^k unitary applied to the state).
+//
+// For targets t_0 < ... < t_{k-1} (physical bits), a "group" is the 2^k amplitudes that
+// share every non-target bit; member j of a group sits at base + sum_b bit_b(j) 2^{t_b}.
+// Each group is replaced by M times itself.  One pass reads and writes every amplitude
+// once: 16 bytes per amplitude of HBM traffic, 8 * 2^k - 2 real flops per amplitude.
+//
+// Two kernels:
+//  * direct -- every target >= 5: thread = group; the 32 threads of a warp take 32
+//    consecutive groups, so each member load/store is one contiguous 256-byte run.
+//    Amplitudes go straight to registers; no shared memory.
+//  * tiled -- some target < 5: a CTA stages a tile of 2^(F+k) amplitudes (2^h rows of
+//    2^m contiguous amplitudes, the rows indexed by the h targets >= m) through shared
+//    memory with coalesced loads, each of its 2^F threads applies M to one group, and
+//    the tile is written back.  An XOR swizzle maps the low target bits onto free bits
+//    so that shared-memory accesses stay conflict-free for any target set.
+//
+// The matrix (FP32, complex64) is a kernel parameter for k <= 5: the FMAs read it
+// straight from the constant bank.  k = 6 (32 KiB) exceeds the parameter space and is
+// read from device memory into shared memory once per CTA.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace sycsim {
+namespace {
+
+template <int K>
+struct MatP {
+    float2 m[(1 << K) * (1 << K)];
+};
+
+struct MatPtr {
+    const float2 *p;
+};
+
+struct DirectGeom {
+    float2 *psi;
+    uint64_t n_groups;
+    int tpos[kMaxK];     // ascending physical target bits
+    uint64_t moff[64];   // offset of member j
+};
+
+struct TiledGeom {
+    float2 *psi;
+    int F;               // log2(threads per CTA) = log2(groups per tile)
+    int m;               // log2(row length) = F + nlow
+    int nlow, nhigh;     // targets below / at-or-above m
+    int ltpos[kMaxK];    // low target bits (ascending, < m)
+    int hpos[kMaxK];     // high target bits (ascending, >= m)
+    int nsw;             // swizzle pairs: bit sw_src[i] of a tile position is XORed into bit sw_dst[i]
+    int sw_src[4], sw_dst[4];
+    uint32_t soff[64];   // tile-local offset of member j
+    uint64_t rowoff[64]; // global offset of tile row r
+};
+
+__device__ __forceinline__ uint64_t insert_zero_bits(uint64_t x, const int *pos, int cnt)
+{
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i) {
+        if (i >= cnt) break;
+        const int p = pos[i];
+        const uint64_t lo = x & ((1ull << p) - 1);
+        x = ((x >> p) << (p + 1)) | lo;
+    }
+    return x;
+}
+
+// 8-byte asynchronous global -> shared copy (no register staging) and its completion wait.
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Opaque copies: stop the compiler from keeping load-phase addresses alive through the
+// compute phase (it would otherwise reuse them for the stores and spill).
+__device__ __forceinline__ float2 *opaque(float2 *p)
+{
+    float2 *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
+__device__ __forceinline__ uint32_t opaque_tid()
+{
+    uint32_t t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t swizzle(uint32_t p, const TiledGeom &g)
+{
+    uint32_t x = p;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (i < g.nsw) x ^= ((p >> g.sw_src[i]) & 1u) << g.sw_dst[i];
+    return x;
+}
+
+// y = M x for one group; rows are produced RB at a time (RB independent FMA chains per
+// real/imag part) and handed to `st(row, value)`.
+template <int K, bool kUnrollRows, typename MatAt, typename Store>
+__device__ __forceinline__ void apply_group(const float2 (&x)[1 << K], MatAt M, Store st)
+{
+    constexpr int D = 1 << K;
+    constexpr int RB = D >= 4 ? 4 : D;
+#pragma unroll(kUnrollRows ? D / RB : 1)
+    for (int r0 = 0; r0 < D; r0 += RB) {
+        float yr[RB], yi[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) yr[b] = yi[b] = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const float2 mm = M(r0 + b, c);
+                yr[b] = fmaf(mm.x, x[c].x, yr[b]);
+                yr[b] = fmaf(mm.y, -x[c].y, yr[b]);
+                yi[b] = fmaf(mm.x, x[c].y, yi[b]);
+                yi[b] = fmaf(mm.y, x[c].x, yi[b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) st(r0 + b, make_float2(yr[b], yi[b]));
+    }
+}
+
+// Copy a 2^K x 2^K matrix from global memory to shared memory (all threads).
+template <int K>
+__device__ __forceinline__ void stage_matrix(float2 *sm, const float2 *gm)
+{
+    constexpr int N = (1 << K) * (1 << K);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = gm[i];
+    __syncthreads();
+}
+
+// Occupancy targets (CTAs per SM) that bound the register count of each width.
+constexpr int direct_min_blocks(int k) { return k <= 3 ? 4 : (k <= 5 ? 2 : 1); }
+constexpr int tiled_threads(int k) { return k <= 4 ? 256 : (k == 5 ? 128 : 64); }
+constexpr int tiled_min_blocks(int k) { return k <= 3 ? 4 : (k <= 5 ? 2 : 4); }
+
+template <int K, typename MatSrc>
+__global__ void __launch_bounds__(256, direct_min_blocks(K)) k_apply_direct(DirectGeom g, MatSrc M)
+{
+    constexpr int D = 1 << K;
+    constexpr bool kSmemMat = std::is_same<MatSrc, MatPtr>::value;
+    extern __shared__ float2 smem[];
+    if constexpr (kSmemMat) stage_matrix<K>(smem, M.p);
+    const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.n_groups) return;
+    float2 *p = g.psi + insert_zero_bits(gi, g.tpos, K);
+    float2 x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = __ldcs(p + g.moff[j]);
+    float2 *const q = opaque(p);
+    auto st = [&](int r, float2 y) { __stcs(q + g.moff[r], y); };
+    if constexpr (kSmemMat)
+        apply_group<K, false>(x, [&](int r, int c) { return smem[r * D + c]; }, st);
+    else
+        apply_group<K, true>(x, [&](int r, int c) { return M.m[r * D + c]; }, st);
+}
+
+template <int K, typename MatSrc>
+__global__ void __launch_bounds__(tiled_threads(K), tiled_min_blocks(K)) k_apply_tiled(TiledGeom g, MatSrc M)
+{
+    constexpr int D = 1 << K;
+    constexpr bool kSmemMat = std::is_same<MatSrc, MatPtr>::value;
+    extern __shared__ float2 smem[];
+    float2 *tile = smem;
+    float2 *msm = smem + ((size_t)D << g.F);
+    if constexpr (kSmemMat) stage_matrix<K>(msm, M.p);
+
+    const uint32_t tid = threadIdx.x;
+    const int F = g.F;
+    const uint32_t lowmask = (1u << g.nlow) - 1;
+    const uint64_t base = insert_zero_bits((uint64_t)blockIdx.x << g.m, g.hpos, g.nhigh);
+    float2 *gp = g.psi + base;
+
+    // load: linear tile position p = tid + c 2^F; row r = c >> nlow, column ((c & lowmask) << F) | tid
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const uint32_t p = tid + ((uint32_t)c << F);
+        const uint32_t col = ((c & lowmask) << F) | tid;
+        cp_async8(&tile[swizzle(p, g)], gp + g.rowoff[c >> g.nlow] + col);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    // compute: thread tid owns group tid
+    const uint32_t bg = (uint32_t)insert_zero_bits(tid, g.ltpos, g.nlow);
+    const uint32_t sb = swizzle(bg, g);
+    float2 x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = tile[sb ^ g.soff[j]];
+    auto st = [&](int r, float2 y) { tile[sb ^ g.soff[r]] = y; };
+    if constexpr (kSmemMat)
+        apply_group<K, false>(x, [&](int r, int c) { return msm[r * D + c]; }, st);
+    else
+        apply_group<K, true>(x, [&](int r, int c) { return M.m[r * D + c]; }, st);
+    __syncthreads();
+
+    // store
+    const uint32_t tid2 = opaque_tid();
+    float2 *const gq = opaque(gp);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const uint32_t p = tid2 + ((uint32_t)c << F);
+        const uint32_t col = ((c & lowmask) << F) | tid2;
+        __stcs(gq + g.rowoff[c >> g.nlow] + col, tile[swizzle(p, g)]);
+    }
+}
+
+// Threads per CTA (log2) of the tiled kernel for width k.
+int tiled_F(int k) { return k <= 4 ? 8 : (k == 5 ? 7 : 6); }
+static_assert(tiled_threads(4) == 256 && tiled_threads(5) == 128 && tiled_threads(6) == 64, "F");
+
+template <typename Kern>
+cudaError_t ensure_smem(Kern kern, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int K, typename MatSrc>
+int launch_k(float2 *psi, int nbits, const int *tpos, const MatSrc &M, cudaStream_t st)
+{
+    constexpr int D = 1 << K;
+    constexpr bool kSmemMat = std::is_same<MatSrc, MatPtr>::value;
+    const size_t mat_bytes = kSmemMat ? sizeof(float2) * D * D : 0;
+    const bool direct = tpos[0] >= 5 && nbits - K >= 8;
+    if (direct) {
+        DirectGeom g{};
+        g.psi = psi;
+        g.n_groups = 1ull << (nbits - K);
+        for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];
+        for (int j = 0; j < D; j++) {
+            uint64_t o = 0;
+            for (int b = 0; b < K; b++)
+                if ((j >> b) & 1) o += 1ull << tpos[b];
+            g.moff[j] = o;
+        }
+        const uint64_t blocks = (g.n_groups + 255) / 256;
+        auto kern = k_apply_direct<K, MatSrc>;
+        if (ensure_smem(kern, mat_bytes) != cudaSuccess) return -1;
+        kern<<<(unsigned)blocks, 256, mat_bytes, st>>>(g, M);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+
+    TiledGeom g{};
+    g.psi = psi;
+    g.F = std::min(tiled_F(K), nbits - K);
+    int m = g.F;
+    for (;;) {  // m = F + #(targets below m)
+        int below = 0;
+        for (int i = 0; i < K; i++) below += tpos[i] < m;
+        if (g.F + below == m) break;
+        m = g.F + below;
+    }
+    g.m = m;
+    g.nlow = g.nhigh = 0;
+    for (int i = 0; i < K; i++) {
+        if (tpos[i] < m)
+            g.ltpos[g.nlow++] = tpos[i];
+        else
+            g.hpos[g.nhigh++] = tpos[i];
+    }
+    // swizzle: the free (non-target) tile bits f0 < f1 < ... ; the first four of them at or
+    // above bit 4 are XORed into the target bits below 4, in order.
+    {
+        int dsts[4], nd = 0, srcs[4], ns = 0;
+        for (int i = 0; i < g.nlow; i++)
+            if (g.ltpos[i] < 4) dsts[nd++] = g.ltpos[i];
+        int free_seen = 0;
+        for (int b = 0; b < m && free_seen < 4; b++) {
+            bool is_t = false;
+            for (int i = 0; i < g.nlow; i++) is_t |= g.ltpos[i] == b;
+            if (is_t) continue;
+            if (b >= 4 && ns < nd) srcs[ns++] = b;
+            free_seen++;
+        }
+        g.nsw = std::min(nd, ns);
+        for (int i = 0; i < g.nsw; i++) {
+            g.sw_src[i] = srcs[i];
+            g.sw_dst[i] = dsts[i];
+        }
+    }
+    for (int j = 0; j < D; j++) {
+        uint32_t o = 0;
+        for (int b = 0; b < g.nlow; b++)
+            if ((j >> b) & 1) o |= 1u << g.ltpos[b];
+        o |= (uint32_t)(j >> g.nlow) << m;
+        g.soff[j] = o;
+    }
+    for (int r = 0; r < (1 << g.nhigh); r++) {
+        uint64_t o = 0;
+        for (int b = 0; b < g.nhigh; b++)
+            if ((r >> b) & 1) o += 1ull << g.hpos[b];
+        g.rowoff[r] = o;
+    }
+    const uint64_t tiles = 1ull << (nbits - g.F - K);
+    const size_t smem = (sizeof(float2) << (g.F + K)) + mat_bytes;
+    auto kern = k_apply_tiled<K, MatSrc>;
+    if (ensure_smem(kern, smem) != cudaSuccess) return -1;
+    kern<<<(unsigned)tiles, 1u << g.F, smem, st>>>(g, M);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int K>
+int launch_param(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st)
+{
+    MatP<K> M;
+    std::memcpy(M.m, mat, sizeof(M.m));
+    return launch_k<K, MatP<K>>(psi, nbits, tpos, M, st);
+}
+
+}  // namespace
+
+int launch_apply_fp32(sim_t *, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                      const float2 *mat6_dev, cudaStream_t st)
+{
+    switch (k) {
+    case 1: return launch_param<1>(psi, nbits, tpos, mat, st);
+    case 2: return launch_param<2>(psi, nbits, tpos, mat, st);
+    case 3: return launch_param<3>(psi, nbits, tpos, mat, st);
+    case 4: return launch_param<4>(psi, nbits, tpos, mat, st);
+    case 5: return launch_param<5>(psi, nbits, tpos, mat, st);
+    case 6: return launch_k<6, MatPtr>(psi, nbits, tpos, MatPtr{mat6_dev}, st);
+    default: return -1;
+    }
+}
+
+// Validate targets, map them to physical bits, sort, and reorder + round the FP64 matrix
+// to FP32 in sorted-bit order.  Returns SIM_OK or an error code (message set on h).
+int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos,
+                  float2 *mat)
+{
+    if (k < 1 || k > kMaxK) return fail(h, SIM_E_INVAL, "apply: k=%d outside 1..%d", k, kMaxK);
+    if (!targets || !matrix) return fail(h, SIM_E_INVAL, "apply: NULL targets or matrix");
+    if (k > h->n - h->s)
+        return fail(h, SIM_E_NONLOCAL, "apply: k=%d exceeds the %d local qubits", k, h->n - h->s);
+    int phys[kMaxK], order[kMaxK];
+    for (int j = 0; j < k; j++) {
+        const int q = targets[j];
+        if (q < 0 || q >= h->n) return fail(h, SIM_E_INVAL, "apply: target %d outside 0..%d", q, h->n - 1);
+        for (int i = 0; i < j; i++)
+            if (targets[i] == q) return fail(h, SIM_E_INVAL, "apply: duplicate target %d", q);
+        phys[j] = h->bit_of[q];
+        if (phys[j] >= h->n - h->s)
+            return fail(h, SIM_E_NONLOCAL, "apply: qubit %d is sliced (physical bit %d >= %d)", q,
+                        phys[j], h->n - h->s);
+        order[j] = j;
+    }
+    std::sort(order, order + k, [&](int a, int b) { return phys[a] < phys[b]; });
+    for (int i = 0; i < k; i++) tpos[i] = phys[order[i]];
+    const int D = 1 << k;
+    int map[64];
+    for (int x = 0; x < D; x++) {
+        int y = 0;
+        for (int i = 0; i < k; i++)
+            if ((x >> i) & 1) y |= 1 << order[i];
+        map[x] = y;
+    }
+    for (int r = 0; r < D; r++)
+        for (int c = 0; c < D; c++) {
+            const double *e = matrix + 2 * ((size_t)map[r] * D + map[c]);
+            mat[r * D + c] = make_float2((float)e[0], (float)e[1]);
+        }
+    return SIM_OK;
+}
+
+// Enqueue one prepared block on the handle's state.
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat)
+{
+    const float2 *mat6 = nullptr;
+    if (k == 6) {
+        const int slot = h->mat6_next;
+        h->mat6_next = (slot + 1) % sim_s::kMat6Slots;
+        SIM_CUDA_TRY(h, cudaEventSynchronize(h->mat6_ev[slot]));  // host staging slot free
+        std::memcpy(h->h_mat6 + 4096 * slot, mat, sizeof(float2) * 4096);
+        float2 *dst = h->d_mat6 + 4096 * slot;
+        SIM_CUDA_TRY(h, cudaMemcpyAsync(dst, h->h_mat6 + 4096 * slot, sizeof(float2) * 4096,
+                                        cudaMemcpyHostToDevice, h->stream));
+        SIM_CUDA_TRY(h, cudaEventRecord(h->mat6_ev[slot], h->stream));
+        mat6 = dst;
+    }
+    const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * (double)h->amps);
+    const int rc = launch_apply_fp32(h, h->d_state, h->n, k, tpos, mat, mat6, h->stream);
+    prof_end(h, ps);
+    if (rc != 0)
+        return fail(h, SIM_E_CUDA, "apply: kernel launch failed: %s",
+                    cudaGetErrorString(cudaGetLastError()));
+    return SIM_OK;
+}
+
+}  // namespace sycsim
+
+using namespace sycsim;
+
+extern "C" int sim_apply_fused(sim_t *h, int k, const int *targets, const double *matrix,
+                               int precision)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_fused: NULL handle");
+    if (precision != SIM_FP32)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: precision %d not supported", precision);
+    int tpos[kMaxK];
+    static thread_local float2 mat[4096];
+    int rc = prepare_block(h, k, targets, matrix, tpos, mat);
+    if (rc != SIM_OK) return rc;
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    return enqueue_block(h, k, tpos, mat);
+}

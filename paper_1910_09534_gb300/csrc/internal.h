@@ -1,0 +1,118 @@
+// internal.h -- shared internals of the sycsim library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/sycsim.h"
+
+namespace sycsim {
+
+constexpr int kMaxQubits = 40;
+constexpr int kMaxK = 6;
+constexpr int kReduceBlocks = 152 * 4;   // persistent reduction grid: 4 CTAs per SM
+constexpr uint64_t kStageAmps = 1ull << 23;  // 64 MiB readout/load staging buffer
+
+// Thread-local error text for failures not tied to a handle.
+void set_thread_error(const char *fmt, ...);
+const char *thread_error();
+
+}  // namespace sycsim
+
+struct sim_s {
+    int n = 0;            // qubits
+    int s = 0;            // sliced (top) physical bits
+    int store = SIM_STORE_DEVICE;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    float2 *d_state = nullptr;  // 2^n amplitudes, physical order
+    bool own_state = false;
+    uint64_t amps = 0;
+
+    int bit_of[sycsim::kMaxQubits];    // logical qubit -> physical bit
+    int qubit_at[sycsim::kMaxQubits];  // physical bit -> logical qubit
+
+    // reduction scratch: per-CTA partials and the final (sum p, sum p^2)
+    double *d_partials = nullptr;
+    double *d_result = nullptr;
+    double *h_result = nullptr;  // pinned
+
+    // staging for logical-order readout / load
+    float2 *d_stage = nullptr;
+
+    // k = 6 matrices go through device memory (the kernel-parameter space holds k <= 5)
+    static constexpr int kMat6Slots = 16;
+    float2 *d_mat6 = nullptr;
+    float2 *h_mat6 = nullptr;  // pinned staging
+    cudaEvent_t mat6_ev[kMat6Slots] = {};
+    int mat6_next = 0;
+
+    // profiling: CUDA-event pairs around kernel launches, per kernel class
+    struct ProfSlot {
+        cudaEvent_t a = nullptr, b = nullptr;
+        int cls = 0;
+        double bytes = 0.0;
+    };
+    std::vector<ProfSlot> prof;
+    int prof_used = 0;
+    bool prof_on = false;
+    uint64_t launches = 0;  // kernels this handle launched
+
+    std::string err;
+};
+
+namespace sycsim {
+
+// Record an error on h (or the thread when h is null) and return `code`.
+int fail(sim_t *h, int code, const char *fmt, ...);
+
+#define SIM_CUDA_TRY(h, call)                                                           \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::sycsim::fail((h), SIM_E_CUDA, "%s failed: %s (%s:%d)", #call,      \
+                                  cudaGetErrorString(e_), __FILE__, __LINE__);           \
+    } while (0)
+
+// True if the layout is the identity map.
+bool layout_is_identity(const sim_t *h);
+
+// Physical index of a logical index under h's layout.
+uint64_t logical_to_physical(const sim_t *h, uint64_t i);
+
+// Profiling brackets: prof_begin records a start event for kernel class `cls` (SIM_PROF_*)
+// when profiling is on and returns the slot (or -1); prof_end records the stop event.
+int prof_begin(sim_t *h, int cls, double alg_bytes);
+void prof_end(sim_t *h, int slot);
+
+// ---- kernel launchers (apply.cu) ----
+// Apply a 2^k x 2^k FP32 matrix (row-major complex64, bit j <-> tpos[j], tpos ascending
+// physical bits) to a buffer of 2^nbits amplitudes.  mat6_dev: device copy of the
+// matrix, used only for k == 6.
+int launch_apply_fp32(sim_t *h, float2 *psi, int nbits, int k, const int *tpos,
+                      const float2 *mat, const float2 *mat6_dev, cudaStream_t st);
+
+// ---- permute.cu ----
+// In-place bit permutation of 2^nbits amplitudes: element i moves to pi(i) where pi
+// moves bit b to bit perm[b].
+int launch_permute(sim_t *h, float2 *psi, int nbits, const int *perm, cudaStream_t st);
+
+// ---- reduce.cu ----
+int launch_reduce(sim_t *h, const float2 *psi, uint64_t amps, double *d_partials,
+                  double *d_result, cudaStream_t st);
+int launch_gather_logical(const float2 *psi, float2 *dst, uint64_t first, uint64_t count,
+                          int n, const int *bit_of, int scatter, cudaStream_t st);
+int launch_set_basis(float2 *psi, uint64_t amps, uint64_t phys, cudaStream_t st);
+
+// ---- gates.cpp ----
+// Matrix of a gate record (2x2 or 4x4 complex128, row-major); returns the dimension or 0.
+int gate_matrix(const sim_gate &g, double *out /* 32 doubles */);
+
+}  // namespace sycsim

@@ -1,0 +1,229 @@
+// permute.cu -- in-place qubit-bit permutation of the state (Sect. 4: between phases the
+// layout is reorganised so that a different set of qubits is local; on one GPU this is a
+// permutation of the amplitude-index bits).  Pure data movement: bit-exact.
+//
+// A bit permutation pi is written as sigma2 o sigma1 with both sigmas involutions (products
+// of disjoint bit transpositions): a cycle c_0 -> c_1 -> ... -> c_{L-1} is the reflection
+// x -> 1 - x (mod L) after the reflection x -> -x (mod L).  Each involution is one pass:
+//  * transpositions between two bits >= LB swap whole tiles (tile tau <-> tile sigma(tau));
+//  * transpositions with one bit < LB make the other bit a "row" bit of the tile;
+//  * transpositions inside [0, LB) act within the tile.
+// A CTA loads a tile pair (2^(LB+q) amplitudes each, rows of 2^LB contiguous amplitudes),
+// permutes it in shared memory and writes it back with coalesced stores.  Tiles that
+// nothing moves are skipped, so a single high-bit swap touches half of the state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace sycsim {
+namespace {
+
+constexpr int kMaxRow = 6;
+
+struct PermGeom {
+    float2 *psi;
+    int LB, q;                    // low-block bits, row bits
+    int rowpos[kMaxRow];          // global bit of row bit i (ascending)
+    int sig[16];                  // in-tile involution on local bits 0..LB+q-1
+    int nhh, hh_a[20], hh_b[20];  // high-high transpositions
+    int trivial_in;               // sig is the identity
+    uint32_t fsw[1 << kMaxRow];   // row r -> XOR applied to its low index (bank spreading)
+    uint64_t rowoff[1 << kMaxRow];
+};
+
+__device__ __forceinline__ uint64_t insert_zero_bits_p(uint64_t x, const int *pos, int cnt)
+{
+    for (int i = 0; i < cnt; ++i) {
+        const int p = pos[i];
+        const uint64_t lo = x & ((1ull << p) - 1);
+        x = ((x >> p) << (p + 1)) | lo;
+    }
+    return x;
+}
+
+__global__ void __launch_bounds__(256) k_permute_pass(PermGeom g)
+{
+    extern __shared__ float2 sm[];
+    const uint64_t baseA = insert_zero_bits_p((uint64_t)blockIdx.x << g.LB, g.rowpos, g.q);
+    uint64_t baseB = baseA;
+    for (int i = 0; i < g.nhh; ++i) {
+        const uint64_t ba = (baseA >> g.hh_a[i]) & 1, bb = (baseA >> g.hh_b[i]) & 1;
+        if (ba != bb) baseB ^= (1ull << g.hh_a[i]) | (1ull << g.hh_b[i]);
+    }
+    if (baseB < baseA) return;  // the partner CTA moves this pair
+    const bool same = baseA == baseB;
+    if (same && g.trivial_in) return;  // nothing in this tile moves
+
+    const int T = 1 << (g.LB + g.q);
+    const uint32_t lbmask = (1u << g.LB) - 1;
+    auto sidx = [&](uint32_t p) {
+        const uint32_t r = p >> g.LB;
+        return (r << g.LB) | ((p & lbmask) ^ g.fsw[r]);
+    };
+    for (int p = threadIdx.x; p < T; p += blockDim.x) {
+        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
+        sm[sidx(p)] = __ldcs(g.psi + baseA + off);
+        if (!same) sm[T + sidx(p)] = __ldcs(g.psi + baseB + off);
+    }
+    __syncthreads();
+    const int nloc = g.LB + g.q;
+    for (int p = threadIdx.x; p < T; p += blockDim.x) {
+        uint32_t s = 0;
+        for (int x = 0; x < nloc; ++x) s |= ((p >> x) & 1u) << g.sig[x];
+        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
+        if (same) {
+            __stcs(g.psi + baseA + off, sm[sidx(s)]);
+        } else {
+            __stcs(g.psi + baseB + off, sm[sidx(s)]);
+            __stcs(g.psi + baseA + off, sm[T + sidx(s)]);
+        }
+    }
+}
+
+// One involution pass; inv[b] = partner of bit b (inv[b] == b: fixed).
+int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
+{
+    bool any = false;
+    for (int b = 0; b < nbits; b++) any |= inv[b] != b;
+    if (!any) return 0;
+
+    // low block: smallest LB >= min(5, nbits) with LB + q >= min(10, nbits)
+    int LB = std::min(5, nbits), q = 0;
+    for (;; LB++) {
+        q = 0;
+        for (int b = 0; b < LB; b++)
+            if (inv[b] >= LB) q++;
+        if (LB + q >= std::min(10, nbits) || LB == nbits) break;
+    }
+    if (q > kMaxRow) return -2;
+
+    PermGeom g{};
+    g.psi = psi;
+    g.LB = LB;
+    g.q = q;
+    std::vector<std::pair<int, int>> rows;  // (global high bit, low partner)
+    for (int b = 0; b < LB; b++)
+        if (inv[b] >= LB) rows.push_back({inv[b], b});
+    std::sort(rows.begin(), rows.end());
+    for (int i = 0; i < q; i++) g.rowpos[i] = rows[i].first;
+    for (int x = 0; x < 16; x++) g.sig[x] = x;
+    g.trivial_in = 1;
+    for (int b = 0; b < LB; b++) {
+        if (inv[b] == b) continue;
+        g.trivial_in = 0;
+        if (inv[b] < LB) {
+            g.sig[b] = inv[b];
+        } else {
+            int i = 0;
+            while (rows[i].first != inv[b]) i++;
+            g.sig[b] = LB + i;
+            g.sig[LB + i] = b;
+        }
+    }
+    g.nhh = 0;
+    for (int b = LB; b < nbits; b++)
+        if (inv[b] > b) {
+            bool row = false;
+            for (int i = 0; i < q; i++) row |= g.rowpos[i] == b || g.rowpos[i] == inv[b];
+            if (!row) {
+                g.hh_a[g.nhh] = b;
+                g.hh_b[g.nhh] = inv[b];
+                g.nhh++;
+            }
+        }
+    for (int r = 0; r < (1 << q); r++) {
+        uint64_t o = 0;
+        uint32_t f = 0;
+        for (int i = 0; i < q; i++)
+            if ((r >> i) & 1) {
+                o += 1ull << g.rowpos[i];
+                f ^= 1u << rows[i].second;  // row bit i lands on bank bit of its low partner
+            }
+        g.rowoff[r] = o;
+        g.fsw[r] = f & ((1u << LB) - 1);
+    }
+    const uint64_t tiles = 1ull << (nbits - LB - q);
+    const size_t smem = 2 * sizeof(float2) << (LB + q);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_permute_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -1;
+    const int threads = std::min(256, 1 << (LB + q));
+    k_permute_pass<<<(unsigned)tiles, threads, smem, st>>>(g);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+// Amplitudes an involution moves: those whose bits differ across at least one transposition.
+static double moved_fraction(int nbits, const int *inv)
+{
+    int pairs = 0;
+    for (int b = 0; b < nbits; b++) pairs += inv[b] > b;
+    return 1.0 - std::ldexp(1.0, -pairs);
+}
+
+int launch_permute(sim_t *h, float2 *psi, int nbits, const int *perm, cudaStream_t st)
+{
+    // split pi into cycles; sigma1 = reflection x -> -x, sigma2 = reflection x -> 1 - x
+    int s1[kMaxQubits], s2[kMaxQubits];
+    bool seen[kMaxQubits] = {};
+    for (int b = 0; b < nbits; b++) s1[b] = s2[b] = b;
+    for (int b = 0; b < nbits; b++) {
+        if (seen[b]) continue;
+        std::vector<int> cyc;
+        for (int x = b; !seen[x]; x = perm[x]) {
+            seen[x] = true;
+            cyc.push_back(x);
+        }
+        const int L = (int)cyc.size();
+        for (int x = 0; x < L; x++) {
+            s1[cyc[x]] = cyc[(L - x) % L];
+            s2[cyc[x]] = cyc[(L + 1 - x) % L];
+        }
+    }
+    const double amps = std::ldexp(1.0, nbits);
+    int rc = 0;
+    for (const int *inv : {s1, s2}) {
+        const double frac = moved_fraction(nbits, inv);
+        if (frac == 0.0) continue;
+        const int ps = h ? prof_begin(h, SIM_PROF_PERMUTE, 16.0 * amps * frac) : -1;
+        rc = launch_involution(psi, nbits, inv, st);
+        if (h) prof_end(h, ps);
+        if (rc != 0) return rc;
+    }
+    return 0;
+}
+
+}  // namespace sycsim
+
+using namespace sycsim;
+
+extern "C" int sim_permute(sim_t *h, const int *perm)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_permute: NULL handle");
+    if (!perm) return fail(h, SIM_E_INVAL, "sim_permute: NULL perm");
+    bool used[kMaxQubits] = {};
+    for (int q = 0; q < h->n; q++) {
+        if (perm[q] < 0 || perm[q] >= h->n || used[perm[q]])
+            return fail(h, SIM_E_INVAL, "sim_permute: perm is not a bijection on 0..%d", h->n - 1);
+        used[perm[q]] = true;
+    }
+    // physical permutation: old bit bit_of[q] -> new bit perm[q]
+    int phys[kMaxQubits];
+    for (int q = 0; q < h->n; q++) phys[h->bit_of[q]] = perm[q];
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    int rc = launch_permute(h, h->d_state, h->n, phys, h->stream);
+    if (rc != 0)
+        return fail(h, SIM_E_CUDA, "sim_permute: launch failed (%d): %s", rc,
+                    cudaGetErrorString(cudaGetLastError()));
+    for (int q = 0; q < h->n; q++) {
+        h->bit_of[q] = perm[q];
+        h->qubit_at[perm[q]] = q;
+    }
+    return SIM_OK;
+}

@@ -1,0 +1,258 @@
+// plan.cpp -- gate aggregation planner and FP64 block composition (Sect. 5: gates are
+// aggregated into k-qubit kernels, k <= k_max, each a 2^k x 2^k unitary; Appendix A's
+// "new cache" lines list such qubit groups and the gates that follow belong to them).
+//
+// First every single-qubit gate is folded into a neighbouring two-qubit gate (Sect. 3), giving
+// "units" of at most two qubits.  Then, greedily in unit order, a unit on qubit set Q may join
+// block b only if b is not earlier than the block holding the last unit on any qubit of Q (so
+// every qubit sees its gates in circuit order) and |qubits(b) u Q| <= k_max.  It joins the
+// block of its most recent predecessor when that fits, else the earliest later block with
+// room, else opens a new block.  Block matrices are composed in FP64 on the block's own
+// qubits (ascending), later gates multiplying from the left.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace sycsim {
+int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos,
+                  float2 *mat);
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat);
+}  // namespace sycsim
+
+using namespace sycsim;
+
+struct PlanBlock {
+    std::vector<int> qubits;  // ascending logical qubits
+    std::vector<int> gates;   // gate indices, circuit order
+    std::vector<double> mat;  // 2 * D * D, row-major interleaved
+};
+
+struct sim_plan_s {
+    int n = 0, n_gates = 0, kmax = 0, precision = 0;
+    std::vector<PlanBlock> blocks;
+};
+
+namespace {
+
+// U <- G U, G acting on local bits (l0) or (l0, l1) of a k-qubit block matrix U.
+void left_multiply(std::vector<double> &U, int k, const double *G, int dg, int l0, int l1)
+{
+    const int D = 1 << k;
+    const int gd = dg;  // 2 or 4
+    std::vector<int> rows(gd);
+    std::vector<double> tmp(2 * gd);
+    for (int base = 0; base < D; base++) {
+        if ((base >> l0) & 1) continue;
+        if (gd == 4 && ((base >> l1) & 1)) continue;
+        rows[0] = base;
+        rows[1] = base | (1 << l0);
+        if (gd == 4) {
+            rows[2] = base | (1 << l1);
+            rows[3] = base | (1 << l0) | (1 << l1);
+        }
+        for (int c = 0; c < D; c++) {
+            for (int r = 0; r < gd; r++) {
+                double re = 0, im = 0;
+                for (int x = 0; x < gd; x++) {
+                    const double gr = G[2 * (r * gd + x)], gi = G[2 * (r * gd + x) + 1];
+                    const double ur = U[2 * (rows[x] * D + c)], ui = U[2 * (rows[x] * D + c) + 1];
+                    re += gr * ur - gi * ui;
+                    im += gr * ui + gi * ur;
+                }
+                tmp[2 * r] = re;
+                tmp[2 * r + 1] = im;
+            }
+            for (int r = 0; r < gd; r++) {
+                U[2 * (rows[r] * D + c)] = tmp[2 * r];
+                U[2 * (rows[r] * D + c) + 1] = tmp[2 * r + 1];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_gate_matrix(const sim_gate *g, double *out)
+{
+    if (!g || !out) return fail(nullptr, SIM_E_INVAL, "sim_gate_matrix: NULL argument");
+    const int d = gate_matrix(*g, out);
+    if (!d) return fail(nullptr, SIM_E_INVAL, "sim_gate_matrix: unknown kind %d", g->kind);
+    return d;
+}
+
+int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
+                    sim_plan_t **out)
+{
+    if (!out) return fail(nullptr, SIM_E_INVAL, "sim_plan_create: out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > kMaxQubits)
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_create: n_qubits=%d", n_qubits);
+    if (n_gates < 0 || (n_gates > 0 && !gates))
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_create: bad gate list");
+    sim_plan_opts opts{};
+    opts.kmax = 4;
+    if (o) opts = *o;
+    if (opts.kmax < 2 || opts.kmax > kMaxK)
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_create: kmax=%d outside 2..%d", opts.kmax, kMaxK);
+    if (opts.precision != SIM_FP32)
+        return fail(nullptr, SIM_E_UNSUPPORTED, "sim_plan_create: precision %d", opts.precision);
+
+    auto *p = new sim_plan_s();
+    p->n = n_qubits;
+    p->n_gates = n_gates;
+    p->kmax = opts.kmax;
+    p->precision = opts.precision;
+    // Pass 1 (Sect. 3: single-qubit gates can be aggregated with neighbouring two-qubit gates):
+    // each single-qubit gate joins the next two-qubit gate on its qubit, or the previous one
+    // when none follows; a qubit without two-qubit gates keeps its own unit.
+    struct Unit {
+        int q[2];
+        int nq;
+        std::vector<int> gates;
+    };
+    std::vector<Unit> units;
+    std::vector<std::vector<int>> pending(n_qubits);
+    std::vector<int> last2q(n_qubits, -1);
+    double G[32];
+    for (int gi = 0; gi < n_gates; gi++) {
+        const sim_gate &g = gates[gi];
+        const int d = gate_matrix(g, G);
+        if (!d) {
+            delete p;
+            return fail(nullptr, SIM_E_INVAL, "sim_plan_create: gate %d has unknown kind %d", gi, g.kind);
+        }
+        const int nq = d == 2 ? 1 : 2;
+        const int Q[2] = {g.q0, g.q1};
+        for (int i = 0; i < nq; i++)
+            if (Q[i] < 0 || Q[i] >= n_qubits || (i == 1 && Q[1] == Q[0])) {
+                delete p;
+                return fail(nullptr, SIM_E_INVAL, "sim_plan_create: gate %d has bad qubits", gi);
+            }
+        if (nq == 1) {
+            pending[g.q0].push_back(gi);
+            continue;
+        }
+        Unit u{{g.q0, g.q1}, 2, {}};
+        for (int i = 0; i < 2; i++) {
+            u.gates.insert(u.gates.end(), pending[Q[i]].begin(), pending[Q[i]].end());
+            pending[Q[i]].clear();
+            last2q[Q[i]] = (int)units.size();
+        }
+        u.gates.push_back(gi);
+        units.push_back(std::move(u));
+    }
+    for (int q = 0; q < n_qubits; q++) {
+        if (pending[q].empty()) continue;
+        if (last2q[q] >= 0) {
+            auto &gl = units[last2q[q]].gates;
+            gl.insert(gl.end(), pending[q].begin(), pending[q].end());
+        } else {
+            units.push_back(Unit{{q, -1}, 1, pending[q]});
+        }
+    }
+
+    // Pass 2: greedy grouping of the units into blocks of at most kmax qubits.
+    std::vector<int> last(n_qubits, -1);
+    for (const Unit &u : units) {
+        const int nq = u.nq;
+        const int *Q = u.q;
+        int lo = -1;
+        for (int i = 0; i < nq; i++) lo = std::max(lo, last[Q[i]]);
+        auto grown = [&](const PlanBlock &b) {
+            int add = 0;
+            for (int i = 0; i < nq; i++)
+                add += std::find(b.qubits.begin(), b.qubits.end(), Q[i]) == b.qubits.end();
+            return (int)b.qubits.size() + add;
+        };
+        int chosen = -1;
+        if (lo >= 0 && grown(p->blocks[lo]) <= opts.kmax) chosen = lo;
+        for (int b = std::max(lo + 1, 0); chosen < 0 && b < (int)p->blocks.size(); b++)
+            if (grown(p->blocks[b]) <= opts.kmax) chosen = b;
+        if (chosen < 0) {
+            p->blocks.emplace_back();
+            chosen = (int)p->blocks.size() - 1;
+        }
+        PlanBlock &b = p->blocks[chosen];
+        for (int i = 0; i < nq; i++)
+            if (std::find(b.qubits.begin(), b.qubits.end(), Q[i]) == b.qubits.end())
+                b.qubits.push_back(Q[i]);
+        b.gates.insert(b.gates.end(), u.gates.begin(), u.gates.end());
+        for (int i = 0; i < nq; i++) last[Q[i]] = chosen;
+    }
+    // compose each block in FP64
+    for (auto &b : p->blocks) {
+        std::sort(b.qubits.begin(), b.qubits.end());
+        const int k = (int)b.qubits.size(), D = 1 << k;
+        b.mat.assign(2 * D * D, 0.0);
+        for (int i = 0; i < D; i++) b.mat[2 * (i * D + i)] = 1.0;
+        for (int gi : b.gates) {
+            const sim_gate &g = gates[gi];
+            const int d = gate_matrix(g, G);
+            const int l0 = (int)(std::find(b.qubits.begin(), b.qubits.end(), g.q0) - b.qubits.begin());
+            const int l1 = d == 4 ? (int)(std::find(b.qubits.begin(), b.qubits.end(), g.q1) -
+                                          b.qubits.begin())
+                                  : -1;
+            left_multiply(b.mat, k, G, d, l0, l1);
+        }
+    }
+    *out = p;
+    return SIM_OK;
+}
+
+int sim_plan_destroy(sim_plan_t *p)
+{
+    if (!p) return fail(nullptr, SIM_E_INVAL, "sim_plan_destroy: NULL plan");
+    delete p;
+    return SIM_OK;
+}
+
+int sim_plan_info(const sim_plan_t *p, int *n_blocks, int *n_gates, int *max_k)
+{
+    if (!p) return fail(nullptr, SIM_E_INVAL, "sim_plan_info: NULL plan");
+    if (n_blocks) *n_blocks = (int)p->blocks.size();
+    if (n_gates) *n_gates = p->n_gates;
+    if (max_k) {
+        int m = 0;
+        for (auto &b : p->blocks) m = std::max(m, (int)b.qubits.size());
+        *max_k = m;
+    }
+    return SIM_OK;
+}
+
+int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *matrix)
+{
+    if (!p) return fail(nullptr, SIM_E_INVAL, "sim_plan_block: NULL plan");
+    if (i < 0 || i >= (int)p->blocks.size())
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_block: index %d outside 0..%zu", i,
+                    p->blocks.size());
+    const PlanBlock &b = p->blocks[i];
+    if (k) *k = (int)b.qubits.size();
+    if (targets) std::copy(b.qubits.begin(), b.qubits.end(), targets);
+    if (matrix) std::copy(b.mat.begin(), b.mat.end(), matrix);
+    return SIM_OK;
+}
+
+int sim_apply_plan(sim_t *h, const sim_plan_t *p)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_plan: NULL handle");
+    if (!p) return fail(h, SIM_E_INVAL, "sim_apply_plan: NULL plan");
+    if (p->n != h->n)
+        return fail(h, SIM_E_INVAL, "sim_apply_plan: plan has %d qubits, handle %d", p->n, h->n);
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    static thread_local float2 mat[4096];
+    int tpos[kMaxK];
+    for (auto &b : p->blocks) {
+        const int k = (int)b.qubits.size();
+        int rc = prepare_block(h, k, b.qubits.data(), b.mat.data(), tpos, mat);
+        if (rc != SIM_OK) return rc;
+        rc = enqueue_block(h, k, tpos, mat);
+        if (rc != SIM_OK) return rc;
+    }
+    return SIM_OK;
+}
+
+}  // extern "C"

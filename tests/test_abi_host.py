@@ -1,0 +1,149 @@
+"""Host-side checks of the native library (no GPU): it loads, exports every symbol declared in
+include/*.h, validates arguments without touching the device, and its host logic -- gate
+matrices and the aggregation planner -- agrees with the CPU oracle."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import syc_inputs as si
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1910_09534_gb300 import build
+    build.build()
+    import paper_1910_09534_gb300 as p
+    p.lib()
+    return p
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\([^;]*\)\s*;", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(pkg):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = pkg.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding wraps each of them
+    assert sorted(set(names) - set(pkg._native.exported_symbols())) == []
+
+
+def test_version(pkg):
+    assert "sm_103a" in pkg.sim_version()
+
+
+def test_errors_without_touching_device(pkg):
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    assert L.sim_create(0, 0, None, ctypes.byref(h)) == pkg.SIM_E_INVAL
+    assert b"n_qubits" in L.sim_last_error(None)
+    assert L.sim_create(10, 10, None, ctypes.byref(h)) == pkg.SIM_E_INVAL
+    assert L.sim_destroy(None) == pkg.SIM_E_INVAL
+    assert L.sim_apply_fused(None, 1, None, None, 0) == pkg.SIM_E_INVAL
+    assert L.sim_plan_create(4, 1, None, None, ctypes.byref(h)) == pkg.SIM_E_INVAL
+
+
+def test_gate_matrices_match_oracle(pkg, oracle_mod):
+    rng = np.random.default_rng(0)
+    for kind in (si.SQRT_X, si.SQRT_Y, si.SQRT_W):
+        g = np.zeros(1, dtype=pkg._native.GATE_DTYPE)[0]
+        g["kind"] = kind
+        assert np.allclose(pkg.sim_gate_matrix(g), oracle_mod.gate_matrix(kind), atol=1e-15)
+    for _ in range(5):
+        th, ph, dp, dm, do = rng.uniform(-3, 3, 5)
+        g = np.zeros(1, dtype=pkg._native.GATE_DTYPE)[0]
+        g["kind"], g["theta"], g["phi"] = si.FSIM, th, ph
+        g["dplus"], g["dminus"], g["dminus_off"] = dp, dm, do
+        assert np.allclose(pkg.sim_gate_matrix(g), oracle_mod.gate_matrix(si.FSIM, th, ph, dp, dm, do),
+                           atol=1e-15)
+
+
+def plan_blocks(pkg, plan):
+    nb, _, _ = pkg.sim_plan_info(plan)
+    return [pkg.sim_plan_block(plan, i) for i in range(nb)]
+
+
+@pytest.mark.parametrize("kmax", [2, 3, 4, 5, 6])
+def test_planner_blocks_reproduce_circuit(pkg, oracle_mod, kmax):
+    # Sect. 5 aggregation: applying the composed blocks in plan order equals applying the
+    # gates one by one (oracle), up to FP64 rounding.
+    circ = si.sycamore_circuit(si.Grid(3, 4), cycles=8, seed=4)
+    plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax)
+    try:
+        nb, ng, mk = pkg.sim_plan_info(plan)
+        assert ng == circ.n_gates and mk <= kmax and nb >= 1
+        psi = oracle_mod.basis_state(circ.n_qubits, 0)
+        for t, m in plan_blocks(pkg, plan):
+            assert list(t) == sorted(t) and len(set(t)) == len(t) <= kmax
+            assert np.allclose(m.conj().T @ m, np.eye(m.shape[0]), atol=1e-12)
+            oracle_mod.apply_kq(psi, t, m)
+        want = oracle_mod.run_circuit(circ)
+        assert np.linalg.norm(psi - want) < 1e-12
+    finally:
+        pkg.sim_plan_destroy(plan)
+
+
+def test_planner_counts_on_30q_circuit(pkg):
+    # Wider blocks -> fewer passes over the state (Sect. 5, Tables 1-2 count "5Q kernels").
+    circ = si.workload_circuit("syc30_5x6_d20", seed=0)
+    counts = {}
+    for kmax in (2, 3, 4, 5, 6):
+        plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax)
+        counts[kmax] = pkg.sim_plan_info(plan)[0]
+        pkg.sim_plan_destroy(plan)
+    assert counts[2] <= 245  # at most one block per fSim once single-qubit gates merge in
+    assert counts[2] > counts[3] > counts[4] > counts[5] >= counts[6]
+
+
+def test_planner_custom_matrices(pkg, oracle_mod):
+    n = 5
+    rng = np.random.default_rng(2)
+    recs = np.zeros(6, dtype=pkg._native.GATE_DTYPE)
+    psi = oracle_mod.basis_state(n, 3)
+    for i in range(6):
+        if i % 2 == 0:
+            q = int(rng.integers(n))
+            u = si.random_unitary(1, seed=i)
+            recs[i]["kind"], recs[i]["q0"] = pkg.SIM_GATE_U1, q
+            recs[i]["u"][:8] = u.view(np.float64).ravel()
+            oracle_mod.apply_1q(psi, q, u)
+        else:
+            q0, q1 = (int(x) for x in rng.choice(n, 2, replace=False))
+            u = si.random_unitary(2, seed=i)
+            recs[i]["kind"], recs[i]["q0"], recs[i]["q1"] = pkg.SIM_GATE_U2, q0, q1
+            recs[i]["u"][:] = u.view(np.float64).ravel()
+            oracle_mod.apply_2q(psi, q0, q1, u)
+    plan = pkg.sim_plan_create(n, recs, kmax=3)
+    got = oracle_mod.basis_state(n, 3)
+    for t, m in plan_blocks(pkg, plan):
+        oracle_mod.apply_kq(got, t, m)
+    pkg.sim_plan_destroy(plan)
+    assert np.linalg.norm(got - psi) < 1e-12
+
+
+def test_planner_rejects_bad_gates(pkg):
+    recs = np.zeros(1, dtype=pkg._native.GATE_DTYPE)
+    recs[0]["kind"], recs[0]["q0"], recs[0]["q1"] = si.FSIM, 2, 2
+    with pytest.raises(pkg.SimError):
+        pkg.sim_plan_create(4, recs)
+    recs[0]["kind"] = 77
+    with pytest.raises(pkg.SimError):
+        pkg.sim_plan_create(4, recs)
+    with pytest.raises(pkg.SimError):
+        pkg.sim_plan_create(4, np.zeros(0, dtype=pkg._native.GATE_DTYPE), kmax=7)
