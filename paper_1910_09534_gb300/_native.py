@@ -80,6 +80,8 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_int]),
     "sim_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sim_reduce_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "sim_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sim_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -204,6 +206,12 @@ def sim_reduce(h):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().sim_reduce(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
     return a.value, b.value, c.value
+
+
+def sim_reduce_noalloc(d_state: int, n_amps: int, d_out: int, stream: int | None = None) -> None:
+    """Reduction over a caller-owned device buffer; writes 3 doubles to device memory d_out."""
+    _check(lib().sim_reduce_noalloc(ctypes.c_void_p(d_state), n_amps, ctypes.c_void_p(d_out),
+                                    ctypes.c_void_p(stream) if stream else None))
 
 
 def sim_sync(h, timeout_ms: int = -1) -> None:

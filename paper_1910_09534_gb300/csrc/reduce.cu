@@ -7,6 +7,8 @@
 // are combined by one warp in a fixed order, so the result is deterministic.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace sycsim {
@@ -101,7 +103,39 @@ __global__ void k_gather_logical(float2 *psi, float2 *dst, uint64_t first, uint6
 
 __global__ void k_set_basis(float2 *psi, uint64_t phys) { psi[phys] = make_float2(1.f, 0.f); }
 
+// Final step of the allocation-free reduction: sum p, scale * sum p^2, and that minus 1.
+__global__ void k_reduce_final3(const double *partials, int nblocks, double scale, double *out)
+{
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 32) {
+        s1 += partials[2 * i];
+        s2 += partials[2 * i + 1];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (threadIdx.x == 0) {
+        out[0] = s1;
+        out[1] = s2 * scale;
+        out[2] = s2 * scale - 1.0;
+    }
+}
+
+constexpr int kNoAllocPartials = 2 * kReduceBlocks;
+constexpr uint64_t kNoAllocMaxAmps = 1ull << kMaxQubits;
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
 }  // namespace
+}  // namespace sycsim
+
+// Scratch of sim_reduce_noalloc: one (sum p, sum p^2) pair per CTA of the reduction grid,
+// 2 * 608 doubles = 9.5 KiB.  A file-scope device array: every GPU that loads this library
+// holds it until the process exits, and no call allocates it.
+static __device__ __align__(256) double g_noalloc_partials[sycsim::kNoAllocPartials];
+
+namespace sycsim {
 
 int launch_reduce(sim_t *, const float2 *psi, uint64_t amps, double *d_partials, double *d_result,
                   cudaStream_t st)
@@ -122,6 +156,58 @@ int launch_gather_logical(const float2 *psi, float2 *dst, uint64_t first, uint64
     k_gather_logical<<<(unsigned)blocks, 256, 0, st>>>((float2 *)psi, dst, first, count, n, m, scatter);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+}  // namespace sycsim
+
+using namespace sycsim;
+
+// Same reduction as sim_reduce, for callers that hand in their own device buffers and cannot
+// allocate.  The scratch is g_noalloc_partials; host code only ever sees a host-side stand-in
+// for that name, so its device address is looked up once per device (with that device
+// current) and passed to the kernels.
+extern "C" int sim_reduce_noalloc(const void *d_state, uint64_t n_amps, double *d_out, void *stream)
+{
+    if (!d_state || !d_out) return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: NULL buffer");
+    if (((uintptr_t)d_state & 15) != 0)
+        return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: state must be 16-byte aligned");
+    if (n_amps < 2 || (n_amps & 1))
+        return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: n_amps=%llu must be even and >= 2",
+                    (unsigned long long)n_amps);
+    if (n_amps > kNoAllocMaxAmps)
+        return fail(nullptr, SIM_E_INVAL,
+                    "sim_reduce_noalloc: n_amps=%llu exceeds the maximum 2^%d amplitudes",
+                    (unsigned long long)n_amps, kMaxQubits);
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return fail(nullptr, SIM_E_CUDA, "sim_reduce_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: device %d outside 0..%d", dev,
+                    kNoAllocMaxDevices - 1);
+    double *partials = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess || !p)
+                return fail(nullptr, SIM_E_CUDA, "sim_reduce_noalloc: cudaGetSymbolAddress: %s",
+                            cudaGetErrorString(e));
+            g_noalloc_addr[dev] = (double *)p;
+        }
+        partials = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    k_reduce_partials<<<kReduceBlocks, kReduceThreads, 0, st>>>((const float4 *)d_state, n_amps / 2,
+                                                                partials);
+    k_reduce_final3<<<1, 32, 0, st>>>(partials, kReduceBlocks, (double)n_amps, d_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(nullptr, SIM_E_CUDA, "sim_reduce_noalloc: launch: %s", cudaGetErrorString(e));
+    return SIM_OK;
+}
+
+namespace sycsim {
 
 int launch_set_basis(float2 *psi, uint64_t amps, uint64_t phys, cudaStream_t st)
 {
