@@ -6,11 +6,13 @@
 // Each group is replaced by M times itself.  One pass reads and writes every amplitude
 // once: 16 bytes per amplitude of HBM traffic, 8 * 2^k - 2 real flops per amplitude.
 //
-// Two kernels:
+// Three kernels:
+//  * reg (default for k <= 5, n >= k + 5) -- see the comment above k_apply_reg: persistent
+//    warps, register-resident groups, warp-shuffle exchange for targets below bit 5.
 //  * direct -- every target >= 5: thread = group; the 32 threads of a warp take 32
 //    consecutive groups, so each member load/store is one contiguous 256-byte run.
-//    Amplitudes go straight to registers; no shared memory.
-//  * tiled -- some target < 5: a CTA stages a tile of 2^(F+k) amplitudes (2^h rows of
+//    Amplitudes go straight to registers; no shared memory.  Used for k <= 3.
+//  * tiled -- small states and k = 6: a CTA stages a tile of 2^(F+k) amplitudes (2^h rows of
 //    2^m contiguous amplitudes, the rows indexed by the h targets >= m) through shared
 //    memory with coalesced loads, each of its 2^F threads applies M to one group, and
 //    the tile is written back.  An XOR swizzle maps the low target bits onto free bits
@@ -313,11 +315,190 @@ int launch_k(float2 *psi, int nbits, const int *tpos, const MatSrc &M, cudaStrea
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// ---------------------------------------------------------------------------------------
+// Register-resident apply for k <= 5 (the default path when n >= k + 5).
+//
+// A warp owns a "warp tile": 32 lanes (index bits 0..4) x 2^k registers.  Register bit
+// j < J (J = number of targets below bit 5) first stands for a free index bit E_j >= 5,
+// register bits j >= J for the high targets.  Loads and stores are therefore 256-byte runs
+// per register.  Each low target t_j (a lane bit) is then exchanged with register bit j by
+// warp shuffles, after which every lane holds one complete group in registers and applies M
+// with the matrix read from the constant bank; the same exchanges undo the transpose before
+// the stores.  Warps are persistent.  (Double-buffering the next tile in registers was
+// measured slower than simply running more CTAs per SM, so it is off by default.)
+// ---------------------------------------------------------------------------------------
+struct RegGeom {
+    float2 *psi;
+    uint64_t n_wtiles;  // 2^(n - 5 - k)
+    int J;              // targets below bit 5
+    int lt[5];          // their bit positions (lane bits), ascending
+    int nfix;           // index bits >= 5 owned by registers (high targets + E), ascending
+    int fix[kMaxK];
+    uint64_t xoff[32];  // offset of register x (pre-exchange meaning)
+};
+
+template <int K>
+__device__ __forceinline__ void lane_reg_exchange(float2 (&v)[1 << K], const RegGeom &g, int lane)
+{
+#pragma unroll
+    for (int b = 0; b < (K < 5 ? K : 5); ++b) {
+        if (b < g.J) {
+            const int t = g.lt[b];
+            const bool s = (lane >> t) & 1;
+#pragma unroll
+            for (int x = 0; x < (1 << K); ++x) {
+                if (x & (1 << b)) continue;
+                const int x1 = x | (1 << b);
+                const float2 send = s ? v[x] : v[x1];
+                float2 r;
+                r.x = __shfl_xor_sync(0xffffffffu, send.x, 1 << t);
+                r.y = __shfl_xor_sync(0xffffffffu, send.y, 1 << t);
+                v[x] = s ? r : v[x];
+                v[x1] = s ? v[x1] : r;
+            }
+        }
+    }
+}
+
+// Tuning constants (overridable at build time): widest k that double-buffers the next tile
+// in registers, and the CTAs per SM each width is compiled for.
+#ifndef SYCSIM_REG_PREFETCH_KMAX
+#define SYCSIM_REG_PREFETCH_KMAX 0
+#endif
+#ifndef SYCSIM_REG_MINB_K3
+#define SYCSIM_REG_MINB_K3 4
+#endif
+#ifndef SYCSIM_REG_MINB_K4
+#define SYCSIM_REG_MINB_K4 3
+#endif
+#ifndef SYCSIM_REG_MINB_K5
+#define SYCSIM_REG_MINB_K5 1
+#endif
+constexpr bool reg_prefetch(int k) { return k <= SYCSIM_REG_PREFETCH_KMAX; }
+constexpr int reg_min_blocks(int k, bool low)
+{
+    return k <= 2 ? 4
+                  : (k == 3 ? SYCSIM_REG_MINB_K3
+                            : (k == 4 ? SYCSIM_REG_MINB_K4 : (low ? SYCSIM_REG_MINB_K5 : 2)));
+}
+
+template <int K, bool kLow>
+__global__ void __launch_bounds__(256, reg_min_blocks(K, kLow)) k_apply_reg(RegGeom g, MatP<K> M)
+{
+    constexpr int D = 1 << K;
+    constexpr bool kPrefetch = reg_prefetch(K);
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= g.n_wtiles) return;
+    auto tile_ptr = [&](uint64_t wt) {
+        return g.psi + insert_zero_bits(wt << 5, g.fix, g.nfix) + lane;
+    };
+    auto MatAt = [&](int r, int c) { return M.m[r * D + c]; };
+    float2 x[D];
+    {
+        const float2 *p = tile_ptr(w);
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = __ldcs(p + g.xoff[j]);
+    }
+    for (; w < g.n_wtiles; w += nw) {
+        const uint64_t wn = w + nw;
+        float2 xn[D];
+        if constexpr (kPrefetch) {
+            if (wn < g.n_wtiles) {
+                const float2 *pn = tile_ptr(wn);
+#pragma unroll
+                for (int j = 0; j < D; ++j) xn[j] = __ldcs(pn + g.xoff[j]);
+            }
+        }
+        float2 *const q = opaque(tile_ptr(w));
+        if constexpr (kLow) {
+            lane_reg_exchange<K>(x, g, lane);
+            float2 y[D];
+            apply_group<K, true>(x, MatAt, [&](int r, float2 v) { y[r] = v; });
+            lane_reg_exchange<K>(y, g, lane);
+#pragma unroll
+            for (int j = 0; j < D; ++j) __stcs(q + g.xoff[j], y[j]);
+        } else {
+            apply_group<K, true>(x, MatAt, [&](int r, float2 v) { __stcs(q + g.xoff[r], v); });
+        }
+        if constexpr (kPrefetch) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) x[j] = xn[j];
+        } else if (wn < g.n_wtiles) {
+            const float2 *pn = tile_ptr(wn);
+#pragma unroll
+            for (int j = 0; j < D; ++j) x[j] = __ldcs(pn + g.xoff[j]);
+        }
+    }
+}
+
+template <int K, bool kLow>
+int launch_reg_kernel(const RegGeom &g, const MatP<K> &M, cudaStream_t st)
+{
+    static int occ = 0;  // resident CTAs per SM for this instantiation
+    static int sms = 0;
+    auto kern = k_apply_reg<K, kLow>;
+    if (!occ) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1)
+            occ = 1;
+    }
+    const uint64_t need = (g.n_wtiles + 7) / 8;  // 8 warps per CTA
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    kern<<<(unsigned)grid, 256, 0, st>>>(g, M);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int K>
+int launch_reg(float2 *psi, int nbits, const int *tpos, const MatP<K> &M, cudaStream_t st)
+{
+    RegGeom g{};
+    g.psi = psi;
+    g.n_wtiles = 1ull << (nbits - 5 - K);
+    g.J = 0;
+    int high[kMaxK], nh = 0;
+    for (int i = 0; i < K; i++) {
+        if (tpos[i] < 5)
+            g.lt[g.J++] = tpos[i];
+        else
+            high[nh++] = tpos[i];
+    }
+    int extra[5], ne = 0;  // the J lowest free bits >= 5
+    for (int b = 5; ne < g.J && b < nbits; b++) {
+        bool used = false;
+        for (int i = 0; i < nh; i++) used |= high[i] == b;
+        if (!used) extra[ne++] = b;
+    }
+    if (ne < g.J) return -1;
+    g.nfix = 0;
+    for (int i = 0; i < ne; i++) g.fix[g.nfix++] = extra[i];
+    for (int i = 0; i < nh; i++) g.fix[g.nfix++] = high[i];
+    std::sort(g.fix, g.fix + g.nfix);
+    for (int x = 0; x < (1 << K); x++) {
+        uint64_t o = 0;
+        for (int b = 0; b < g.J; b++)
+            if ((x >> b) & 1) o += 1ull << extra[b];
+        for (int i = 0; i < nh; i++)
+            if ((x >> (g.J + i)) & 1) o += 1ull << high[i];
+        g.xoff[x] = o;
+    }
+    return g.J ? launch_reg_kernel<K, true>(g, M, st) : launch_reg_kernel<K, false>(g, M, st);
+}
+
 template <int K>
 int launch_param(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st)
 {
     MatP<K> M;
     std::memcpy(M.m, mat, sizeof(M.m));
+    // Measured on GB300 at n = 30: for k <= 3 with every target >= 5 the one-group-per-thread
+    // kernel streams at ~7.0 TB/s, ~10% above the persistent register kernel; everywhere
+    // else (k = 4, or any target below bit 5) the register kernel is faster.
+    const bool all_high = tpos[0] >= 5;
+    if (K <= 3 && all_high && nbits - K >= 8) return launch_k<K, MatP<K>>(psi, nbits, tpos, M, st);
+    if (nbits >= K + 5) return launch_reg<K>(psi, nbits, tpos, M, st);
     return launch_k<K, MatP<K>>(psi, nbits, tpos, M, st);
 }
 
