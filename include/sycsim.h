@@ -56,6 +56,12 @@ extern "C" {
 
 /* ---- state storage ---------------------------------------------------- */
 #define SIM_STORE_DEVICE 0 /* whole state resident in device memory (HBM) */
+#define SIM_STORE_HOST 1   /* whole state in pinned host memory -- the secondary storage of
+                              Sect. 4 -- streamed through device slots one slice at a time */
+
+/* ---- slice transfer directions ---------------------------------------- */
+#define SIM_H2D 0
+#define SIM_D2H 1
 
 typedef struct sim_s sim_t;
 
@@ -66,6 +72,9 @@ typedef struct sim_opts {
     void *ext_state;    /* optional caller-owned device buffer for the state (>= 8 * 2^n bytes),
                            e.g. a torch tensor's storage; NULL = library allocates */
     uint64_t ext_bytes; /* size of ext_state in bytes */
+    int slots;          /* SIM_STORE_HOST: device slice buffers, 2..4 (0 = 3) */
+    int set_a[8];       /* SIM_STORE_HOST: the two sliced qubit sets A and B (Sect. 4: the */
+    int set_b[8];       /* sliced qubits alternate between two sets); slice_bits qubits each, disjoint */
     int reserved[8];
 } sim_opts;
 
@@ -81,7 +90,15 @@ const char *sim_version(void);
  * (Sect. 4: the top slice_bits physical bits address 2^slice_bits slices of
  * 2^(n - slice_bits) amplitudes; gates may only target local qubits).
  * The state starts as |0...0>.  opts may be NULL (device 0, own stream, own
- * buffer).  On success *out is a handle to pass to sim_destroy(). */
+ * buffer).  On success *out is a handle to pass to sim_destroy().
+ *
+ * SIM_STORE_HOST (Sect. 4, secondary storage organised as logical files indexed
+ * by the sliced qubits): 1 <= slice_bits <= 8 and 2*slice_bits < n_qubits; the
+ * state lives in pinned host memory in the layout [other qubits, ascending |
+ * set_b in order | set_a in order] (bit 0 first), so that the 2^(2 slice_bits)
+ * "files" (fixed values of A and B) are contiguous runs; the device holds
+ * `slots` buffers of 2^(n - slice_bits) amplitudes.  Gates run through
+ * sim_run_phase / sim_run_phases only. */
 int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out);
 int sim_destroy(sim_t *h);
 
@@ -223,6 +240,48 @@ int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *mat
 
 /* Apply every block of the plan in order (each as sim_apply_fused).  Async. */
 int sim_apply_plan(sim_t *h, const sim_plan_t *p);
+
+/* ---- secondary storage: slices and phases (Sect. 4) ------------------------ */
+
+/* Move slice `value` of sliced set `set` (0 = A, 1 = B; value's bit i is the value
+ * of set[i]) between the host store and device slot `slot` (0..slots-1), dir
+ * SIM_H2D or SIM_D2H.  Asynchronous; copies run on the handle's copy streams and
+ * are ordered by events against the compute work on that slot.  Bit-exact.
+ * SIM_E_UNSUPPORTED if the handle has no host store. */
+int sim_stream_slice(sim_t *h, int set, uint64_t value, int dir, int slot);
+
+/* Device pointer of slot `slot` (2^(n - slice_bits) complex64 amplitudes; with set
+ * A sliced its layout is [rest | B], with set B sliced [rest | A]). */
+int sim_slot_ptr(const sim_t *h, int slot, void **dptr);
+
+/* Copy `count` complex64 amplitudes of slot `slot` starting at `first` to host
+ * memory `out`, after the slot's pending copy-in.  Synchronous. */
+int sim_slot_read(sim_t *h, int slot, uint64_t first, uint64_t count, void *out);
+
+/* One phase (Sect. 4: for each value of the sliced qubits, read the slice, apply
+ * the phase's gates, write it back): for every value of set `set`, stream the
+ * slice in, apply every block of plan p (whose qubits must avoid that set --
+ * SIM_E_NONLOCAL otherwise), stream it out; slices rotate through the slots so
+ * copies overlap compute.  On a device-resident handle the plan is applied to
+ * the whole state instead.  Asynchronous. */
+int sim_run_phase(sim_t *h, int set, const sim_plan_t *p);
+
+/* Phase planner (Sect. 4: sliced qubits alternate between two sets; gates are
+ * applied while their qubits are local).  Splits the gate list into phases that
+ * alternate between slicing set A and set B: a phase takes, in order, every
+ * remaining gate that avoids its sliced set and does not follow a deferred gate
+ * on one of its qubits.  Each phase's gates are aggregated as by
+ * sim_plan_create.  SIM_E_NONLOCAL if a gate couples a qubit of A with one of B. */
+typedef struct sim_phases_s sim_phases_t;
+int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
+                      int slice_bits, const int *set_a, const int *set_b, sim_phases_t **out);
+int sim_phases_destroy(sim_phases_t *ph);
+int sim_phases_info(const sim_phases_t *ph, int *n_phases, int *total_blocks);
+int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **plan);
+
+/* Run every phase in order (sim_run_phase); the handle's sets must be the
+ * phases' sets.  Asynchronous. */
+int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
 #ifdef __cplusplus
 }

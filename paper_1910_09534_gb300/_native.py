@@ -30,6 +30,9 @@ SIM_FP32 = 0
 SIM_C64 = 0
 SIM_C128 = 1
 SIM_STORE_DEVICE = 0
+SIM_STORE_HOST = 1
+SIM_H2D = 0
+SIM_D2H = 1
 
 SIM_GATE_SQRT_X = 0
 SIM_GATE_SQRT_Y = 1
@@ -47,6 +50,7 @@ GATE_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("reserved
 class SimOpts(ctypes.Structure):
     _fields_ = [("store", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("ext_state", ctypes.c_void_p), ("ext_bytes", ctypes.c_uint64),
+                ("slots", ctypes.c_int), ("set_a", ctypes.c_int * 8), ("set_b", ctypes.c_int * 8),
                 ("reserved", ctypes.c_int * 8)]
 
 
@@ -96,6 +100,18 @@ _SIGS = {
     "sim_plan_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "sim_apply_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_stream_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                        ctypes.c_int]),
+    "sim_slot_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sim_slot_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_void_p]),
+    "sim_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sim_phases_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_phases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_phases_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_phases_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_run_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -137,13 +153,19 @@ def sim_version() -> str:
 
 
 def sim_create(n_qubits: int, slice_bits: int = 0, device: int = 0, stream: int | None = None,
-               ext_state: int | None = None, ext_bytes: int = 0):
+               ext_state: int | None = None, ext_bytes: int = 0, store: int = SIM_STORE_DEVICE,
+               set_a=(), set_b=(), slots: int = 0):
     o = SimOpts()
-    o.store = SIM_STORE_DEVICE
+    o.store = store
     o.device = device
     o.stream = stream
     o.ext_state = ext_state
     o.ext_bytes = ext_bytes
+    o.slots = slots
+    for i, q in enumerate(set_a):
+        o.set_a[i] = q
+    for i, q in enumerate(set_b):
+        o.set_b[i] = q
     h = ctypes.c_void_p()
     _check(lib().sim_create(n_qubits, slice_bits, ctypes.byref(o), ctypes.byref(h)))
     return h
@@ -308,6 +330,63 @@ def sim_plan_block(p, i: int):
 
 def sim_apply_plan(h, p) -> None:
     _check(lib().sim_apply_plan(h, p), h)
+
+
+def sim_stream_slice(h, set_: int, value: int, direction: int, slot: int) -> None:
+    _check(lib().sim_stream_slice(h, set_, value, direction, slot), h)
+
+
+def sim_slot_ptr(h, slot: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().sim_slot_ptr(h, slot, ctypes.byref(p)))
+    return p.value
+
+
+def sim_slot_read(h, slot: int, first: int = 0, count: int | None = None) -> np.ndarray:
+    n, s, _ = sim_info(h)
+    if count is None:
+        count = (1 << (n - s)) - first
+    out = np.empty(count, dtype=np.complex64)
+    _check(lib().sim_slot_read(h, slot, first, count, _ptr(out)), h)
+    return out
+
+
+def sim_run_phase(h, set_: int, plan) -> None:
+    _check(lib().sim_run_phase(h, set_, plan), h)
+
+
+def sim_phases_create(n_qubits: int, gates: np.ndarray, slice_bits: int, set_a, set_b, kmax: int = 4,
+                      precision: int = SIM_FP32):
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    a = np.ascontiguousarray(set_a, dtype=np.int32)
+    b = np.ascontiguousarray(set_b, dtype=np.int32)
+    o = PlanOpts()
+    o.kmax = kmax
+    o.precision = precision
+    p = ctypes.c_void_p()
+    _check(lib().sim_phases_create(n_qubits, int(g.size), _ptr(g), ctypes.byref(o), slice_bits, _ptr(a),
+                                   _ptr(b), ctypes.byref(p)))
+    return p
+
+
+def sim_phases_destroy(ph) -> None:
+    _check(lib().sim_phases_destroy(ph))
+
+
+def sim_phases_info(ph):
+    n, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_phases_info(ph, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def sim_phases_get(ph, i: int):
+    s, p = ctypes.c_int(), ctypes.c_void_p()
+    _check(lib().sim_phases_get(ph, i, ctypes.byref(s), ctypes.byref(p)))
+    return s.value, p
+
+
+def sim_run_phases(h, ph) -> None:
+    _check(lib().sim_run_phases(h, ph), h)
 
 
 def exported_symbols() -> list:

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -518,25 +519,26 @@ int launch_apply_fp32(sim_t *, float2 *psi, int nbits, int k, const int *tpos, c
     }
 }
 
-// Validate targets, map them to physical bits, sort, and reorder + round the FP64 matrix
-// to FP32 in sorted-bit order.  Returns SIM_OK or an error code (message set on h).
-int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos,
-                  float2 *mat)
+// Validate targets, map them to physical bits through phys_of (a qubit whose entry is < 0 or
+// >= nlocal is not local), sort, and reorder + round the FP64 matrix to FP32 in sorted-bit
+// order.  Returns SIM_OK or an error code (message set on h).
+int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
+                      int nlocal, int *tpos, float2 *mat)
 {
     if (k < 1 || k > kMaxK) return fail(h, SIM_E_INVAL, "apply: k=%d outside 1..%d", k, kMaxK);
     if (!targets || !matrix) return fail(h, SIM_E_INVAL, "apply: NULL targets or matrix");
-    if (k > h->n - h->s)
-        return fail(h, SIM_E_NONLOCAL, "apply: k=%d exceeds the %d local qubits", k, h->n - h->s);
+    if (k > nlocal)
+        return fail(h, SIM_E_NONLOCAL, "apply: k=%d exceeds the %d local qubits", k, nlocal);
     int phys[kMaxK], order[kMaxK];
     for (int j = 0; j < k; j++) {
         const int q = targets[j];
         if (q < 0 || q >= h->n) return fail(h, SIM_E_INVAL, "apply: target %d outside 0..%d", q, h->n - 1);
         for (int i = 0; i < j; i++)
             if (targets[i] == q) return fail(h, SIM_E_INVAL, "apply: duplicate target %d", q);
-        phys[j] = h->bit_of[q];
-        if (phys[j] >= h->n - h->s)
-            return fail(h, SIM_E_NONLOCAL, "apply: qubit %d is sliced (physical bit %d >= %d)", q,
-                        phys[j], h->n - h->s);
+        phys[j] = phys_of[q];
+        if (phys[j] < 0 || phys[j] >= nlocal)
+            return fail(h, SIM_E_NONLOCAL, "apply: qubit %d is sliced (not among the %d local bits)", q,
+                        nlocal);
         order[j] = j;
     }
     std::sort(order, order + k, [&](int a, int b) { return phys[a] < phys[b]; });
@@ -557,8 +559,14 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
     return SIM_OK;
 }
 
-// Enqueue one prepared block on the handle's state.
-int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat)
+int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat)
+{
+    return prepare_block_map(h, k, targets, matrix, h->bit_of, h->n - h->s, tpos, mat);
+}
+
+// Enqueue one prepared block on a buffer of 2^nbits amplitudes, on stream st.
+int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                     cudaStream_t st)
 {
     const float2 *mat6 = nullptr;
     if (k == 6) {
@@ -568,17 +576,22 @@ int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat)
         std::memcpy(h->h_mat6 + 4096 * slot, mat, sizeof(float2) * 4096);
         float2 *dst = h->d_mat6 + 4096 * slot;
         SIM_CUDA_TRY(h, cudaMemcpyAsync(dst, h->h_mat6 + 4096 * slot, sizeof(float2) * 4096,
-                                        cudaMemcpyHostToDevice, h->stream));
-        SIM_CUDA_TRY(h, cudaEventRecord(h->mat6_ev[slot], h->stream));
+                                        cudaMemcpyHostToDevice, st));
+        SIM_CUDA_TRY(h, cudaEventRecord(h->mat6_ev[slot], st));
         mat6 = dst;
     }
-    const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * (double)h->amps);
-    const int rc = launch_apply_fp32(h, h->d_state, h->n, k, tpos, mat, mat6, h->stream);
-    prof_end(h, ps);
+    const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
+    const int rc = launch_apply_fp32(h, psi, nbits, k, tpos, mat, mat6, st);
+    prof_end(h, ps, st);
     if (rc != 0)
         return fail(h, SIM_E_CUDA, "apply: kernel launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));
     return SIM_OK;
+}
+
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat)
+{
+    return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, h->stream);
 }
 
 }  // namespace sycsim
@@ -589,6 +602,8 @@ extern "C" int sim_apply_fused(sim_t *h, int k, const int *targets, const double
                                int precision)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_fused: NULL handle");
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: host-store state: use sim_run_phase");
     if (precision != SIM_FP32)
         return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: precision %d not supported", precision);
     int tpos[kMaxK];

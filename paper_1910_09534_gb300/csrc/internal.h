@@ -65,7 +65,37 @@ struct sim_s {
     bool prof_on = false;
     uint64_t launches = 0;  // kernels this handle launched
 
+    // host store (SIM_STORE_HOST, Sect. 4 secondary storage): pinned 2^n amplitudes in the
+    // host layout [rest qubits | set B | set A] and device slots of 2^(n - s) amplitudes
+    static constexpr int kMaxSlots = 4;
+    float2 *h_store = nullptr;
+    int nslots = 0;
+    float2 *d_slot[kMaxSlots] = {};
+    cudaStream_t st_in = nullptr, st_out = nullptr;
+    cudaEvent_t ev_in[kMaxSlots] = {}, ev_done[kMaxSlots] = {}, ev_out[kMaxSlots] = {};
+    int set[2][8] = {};                       // sliced sets A (0) and B (1), logical qubits
+    int slice_phys[2][sycsim::kMaxQubits];    // phase with set X sliced: qubit -> slot bit (-1: sliced)
+    double *h_partials = nullptr;             // pinned, 2 per slice (host-mode reduction)
+
     std::string err;
+};
+
+struct PlanBlock {
+    std::vector<int> qubits;  // ascending logical qubits
+    std::vector<int> gates;   // gate indices, circuit order
+    std::vector<double> mat;  // 2 * D * D, row-major interleaved
+};
+
+struct sim_plan_s {
+    int n = 0, n_gates = 0, kmax = 0, precision = 0;
+    std::vector<PlanBlock> blocks;
+};
+
+struct sim_phases_s {
+    int n = 0, s = 0;
+    int set_a[8] = {}, set_b[8] = {};
+    std::vector<int> set_of;          // sliced set of each phase (0 = A, 1 = B)
+    std::vector<sim_plan_t *> plans;  // blocks of each phase
 };
 
 namespace sycsim {
@@ -89,8 +119,17 @@ uint64_t logical_to_physical(const sim_t *h, uint64_t i);
 
 // Profiling brackets: prof_begin records a start event for kernel class `cls` (SIM_PROF_*)
 // when profiling is on and returns the slot (or -1); prof_end records the stop event.
-int prof_begin(sim_t *h, int cls, double alg_bytes);
-void prof_end(sim_t *h, int slot);
+int prof_begin(sim_t *h, int cls, double alg_bytes, cudaStream_t st);
+void prof_end(sim_t *h, int slot, cudaStream_t st);
+
+// apply.cu: block preparation (targets -> sorted physical bits, FP32 matrix in that order)
+// and enqueueing on an arbitrary buffer/stream.
+int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
+                      int nlocal, int *tpos, float2 *mat);
+int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat);
+int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                     cudaStream_t st);
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat);
 
 // ---- kernel launchers (apply.cu) ----
 // Apply a 2^k x 2^k FP32 matrix (row-major complex64, bit j <-> tpos[j], tpos ascending
@@ -110,6 +149,14 @@ int launch_reduce(sim_t *h, const float2 *psi, uint64_t amps, double *d_partials
 int launch_gather_logical(const float2 *psi, float2 *dst, uint64_t first, uint64_t count,
                           int n, const int *bit_of, int scatter, cudaStream_t st);
 int launch_set_basis(float2 *psi, uint64_t amps, uint64_t phys, cudaStream_t st);
+
+// ---- store.cu (host store) ----
+int host_store_create(sim_t *h, const sim_opts &o);
+void host_store_release(sim_t *h);
+int host_reset(sim_t *h, uint64_t basis);
+int host_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtype, int physical);
+int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int physical);
+int host_reduce(sim_t *h, double *s1, double *s2);
 
 // ---- gates.cpp ----
 // Matrix of a gate record (2x2 or 4x4 complex128, row-major); returns the dimension or 0.

@@ -191,9 +191,9 @@ int launch_permute(sim_t *h, float2 *psi, int nbits, const int *perm, cudaStream
     for (const int *inv : {s1, s2}) {
         const double frac = moved_fraction(nbits, inv);
         if (frac == 0.0) continue;
-        const int ps = h ? prof_begin(h, SIM_PROF_PERMUTE, 16.0 * amps * frac) : -1;
+        const int ps = h ? prof_begin(h, SIM_PROF_PERMUTE, 16.0 * amps * frac, st) : -1;
         rc = launch_involution(psi, nbits, inv, st);
-        if (h) prof_end(h, ps);
+        if (h) prof_end(h, ps, st);
         if (rc != 0) return rc;
     }
     return 0;
@@ -207,6 +207,8 @@ extern "C" int sim_permute(sim_t *h, const int *perm)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_permute: NULL handle");
     if (!perm) return fail(h, SIM_E_INVAL, "sim_permute: NULL perm");
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_permute: the host store's layout is fixed by its sliced sets");
     bool used[kMaxQubits] = {};
     for (int q = 0; q < h->n; q++) {
         if (perm[q] < 0 || perm[q] >= h->n || used[perm[q]])

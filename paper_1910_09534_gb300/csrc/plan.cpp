@@ -15,24 +15,7 @@
 
 #include "internal.h"
 
-namespace sycsim {
-int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos,
-                  float2 *mat);
-int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat);
-}  // namespace sycsim
-
 using namespace sycsim;
-
-struct PlanBlock {
-    std::vector<int> qubits;  // ascending logical qubits
-    std::vector<int> gates;   // gate indices, circuit order
-    std::vector<double> mat;  // 2 * D * D, row-major interleaved
-};
-
-struct sim_plan_s {
-    int n = 0, n_gates = 0, kmax = 0, precision = 0;
-    std::vector<PlanBlock> blocks;
-};
 
 namespace {
 
@@ -242,6 +225,8 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
     if (!p) return fail(h, SIM_E_INVAL, "sim_apply_plan: NULL plan");
     if (p->n != h->n)
         return fail(h, SIM_E_INVAL, "sim_apply_plan: plan has %d qubits, handle %d", p->n, h->n);
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_apply_plan: host-store state: use sim_run_phase");
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
     static thread_local float2 mat[4096];
     int tpos[kMaxK];
@@ -250,6 +235,141 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
         int rc = prepare_block(h, k, b.qubits.data(), b.mat.data(), tpos, mat);
         if (rc != SIM_OK) return rc;
         rc = enqueue_block(h, k, tpos, mat);
+        if (rc != SIM_OK) return rc;
+    }
+    return SIM_OK;
+}
+
+// ---- phases over two alternating sliced sets (Sect. 4) ----
+
+int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
+                      int slice_bits, const int *set_a, const int *set_b, sim_phases_t **out)
+{
+    if (!out) return fail(nullptr, SIM_E_INVAL, "sim_phases_create: out is NULL");
+    *out = nullptr;
+    if (n_qubits < 2 || n_qubits > kMaxQubits || slice_bits < 1 || slice_bits > 8 ||
+        2 * slice_bits >= n_qubits || !set_a || !set_b || (n_gates > 0 && !gates) || n_gates < 0)
+        return fail(nullptr, SIM_E_INVAL, "sim_phases_create: bad arguments");
+    std::vector<int> which(n_qubits, -1);  // 0: set A, 1: set B
+    for (int w = 0; w < 2; w++)
+        for (int i = 0; i < slice_bits; i++) {
+            const int q = w ? set_b[i] : set_a[i];
+            if (q < 0 || q >= n_qubits || which[q] >= 0)
+                return fail(nullptr, SIM_E_INVAL, "sim_phases_create: sets must be disjoint qubits");
+            which[q] = w;
+        }
+    double G[32];
+    for (int g = 0; g < n_gates; g++) {
+        const int d = gate_matrix(gates[g], G);
+        if (d == 4 && which[gates[g].q0] >= 0 && which[gates[g].q1] >= 0 &&
+            which[gates[g].q0] != which[gates[g].q1])
+            return fail(nullptr, SIM_E_NONLOCAL,
+                        "sim_phases_create: gate %d couples set A and set B; no phase can apply it", g);
+    }
+    // Greedy: in a phase with set X sliced, apply (in order) every remaining gate that avoids X
+    // and every qubit already holding a deferred gate; the deferred gates form the next
+    // phase's input, with the other set sliced.  Both starting sets are tried.
+    auto run = [&](int first, std::vector<std::pair<int, std::vector<int>>> &phases) {
+        std::vector<int> rem(n_gates);
+        for (int g = 0; g < n_gates; g++) rem[g] = g;
+        int cur = first, idle = 0;
+        while (!rem.empty() && idle < 2) {
+            std::vector<char> blocked(n_qubits, 0);
+            for (int q = 0; q < n_qubits; q++) blocked[q] = which[q] == cur;
+            std::vector<int> take, defer;
+            for (int g : rem) {
+                const int d = gate_matrix(gates[g], G);
+                const int Q[2] = {gates[g].q0, gates[g].q1};
+                const int nq = d == 2 ? 1 : 2;
+                bool ok = true;
+                for (int i = 0; i < nq; i++) ok &= !blocked[Q[i]];
+                if (ok) {
+                    take.push_back(g);
+                } else {
+                    defer.push_back(g);
+                    for (int i = 0; i < nq; i++) blocked[Q[i]] = 1;
+                }
+            }
+            if (take.empty()) {
+                idle++;
+            } else {
+                idle = 0;
+                phases.push_back({cur, take});
+            }
+            rem.swap(defer);
+            cur = 1 - cur;
+        }
+        return rem.empty();
+    };
+    std::vector<std::pair<int, std::vector<int>>> best, alt;
+    const bool ok0 = run(0, best), ok1 = run(1, alt);
+    if (!ok0 && !ok1) return fail(nullptr, SIM_E_INVAL, "sim_phases_create: circuit cannot be phased");
+    if (!ok0 || (ok1 && alt.size() < best.size())) best.swap(alt);
+
+    auto *ph = new sim_phases_s();
+    ph->n = n_qubits;
+    ph->s = slice_bits;
+    for (int i = 0; i < slice_bits; i++) {
+        ph->set_a[i] = set_a[i];
+        ph->set_b[i] = set_b[i];
+    }
+    for (auto &pr : best) {
+        std::vector<sim_gate> sub(pr.second.size());
+        for (size_t i = 0; i < pr.second.size(); i++) sub[i] = gates[pr.second[i]];
+        sim_plan_t *plan = nullptr;
+        const int rc = sim_plan_create(n_qubits, (int)sub.size(), sub.data(), o, &plan);
+        if (rc != SIM_OK) {
+            sim_phases_destroy(ph);
+            return rc;
+        }
+        ph->set_of.push_back(pr.first);
+        ph->plans.push_back(plan);
+    }
+    *out = ph;
+    return SIM_OK;
+}
+
+int sim_phases_destroy(sim_phases_t *ph)
+{
+    if (!ph) return fail(nullptr, SIM_E_INVAL, "sim_phases_destroy: NULL");
+    for (auto *p : ph->plans) delete p;
+    delete ph;
+    return SIM_OK;
+}
+
+int sim_phases_info(const sim_phases_t *ph, int *n_phases, int *total_blocks)
+{
+    if (!ph) return fail(nullptr, SIM_E_INVAL, "sim_phases_info: NULL");
+    if (n_phases) *n_phases = (int)ph->plans.size();
+    if (total_blocks) {
+        int t = 0;
+        for (auto *p : ph->plans) t += (int)p->blocks.size();
+        *total_blocks = t;
+    }
+    return SIM_OK;
+}
+
+int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **plan)
+{
+    if (!ph || i < 0 || i >= (int)ph->plans.size())
+        return fail(nullptr, SIM_E_INVAL, "sim_phases_get: no phase %d", i);
+    if (set) *set = ph->set_of[i];
+    if (plan) *plan = ph->plans[i];
+    return SIM_OK;
+}
+
+int sim_run_phases(sim_t *h, const sim_phases_t *ph)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_run_phases: NULL handle");
+    if (!ph || ph->n != h->n) return fail(h, SIM_E_INVAL, "sim_run_phases: phases missing or for another n");
+    if (h->store == SIM_STORE_HOST) {
+        if (ph->s != h->s) return fail(h, SIM_E_INVAL, "sim_run_phases: slice_bits differ");
+        for (int i = 0; i < ph->s; i++)
+            if (ph->set_a[i] != h->set[0][i] || ph->set_b[i] != h->set[1][i])
+                return fail(h, SIM_E_INVAL, "sim_run_phases: sliced sets differ from the handle's");
+    }
+    for (size_t i = 0; i < ph->plans.size(); i++) {
+        const int rc = sim_run_phase(h, ph->set_of[i], ph->plans[i]);
         if (rc != SIM_OK) return rc;
     }
     return SIM_OK;

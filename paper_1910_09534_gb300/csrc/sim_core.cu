@@ -52,7 +52,7 @@ uint64_t logical_to_physical(const sim_t *h, uint64_t i)
     return j;
 }
 
-int prof_begin(sim_t *h, int cls, double alg_bytes)
+int prof_begin(sim_t *h, int cls, double alg_bytes, cudaStream_t st)
 {
     h->launches++;
     if (!h->prof_on) return -1;
@@ -65,13 +65,13 @@ int prof_begin(sim_t *h, int cls, double alg_bytes)
     const int i = h->prof_used++;
     h->prof[i].cls = cls;
     h->prof[i].bytes = alg_bytes;
-    cudaEventRecord(h->prof[i].a, h->stream);
+    cudaEventRecord(h->prof[i].a, st);
     return i;
 }
 
-void prof_end(sim_t *h, int slot)
+void prof_end(sim_t *h, int slot, cudaStream_t st)
 {
-    if (slot >= 0) cudaEventRecord(h->prof[slot].b, h->stream);
+    if (slot >= 0) cudaEventRecord(h->prof[slot].b, st);
 }
 
 static void release(sim_t *h)
@@ -83,6 +83,7 @@ static void release(sim_t *h)
         cudaEventDestroy(s.a);
         cudaEventDestroy(s.b);
     }
+    host_store_release(h);
     if (h->own_state && h->d_state) cudaFree(h->d_state);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->d_result) cudaFree(h->d_result);
@@ -117,8 +118,8 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
         return fail(nullptr, SIM_E_INVAL, "sim_create: slice_bits=%d outside 0..n-1", slice_bits);
     sim_opts o{};
     if (opts) o = *opts;
-    if (o.store != SIM_STORE_DEVICE)
-        return fail(nullptr, SIM_E_UNSUPPORTED, "sim_create: store mode %d not supported", o.store);
+    if (o.store != SIM_STORE_DEVICE && o.store != SIM_STORE_HOST)
+        return fail(nullptr, SIM_E_INVAL, "sim_create: store mode %d", o.store);
 
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
@@ -154,7 +155,13 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
         h->own_stream = true;
     }
     const uint64_t bytes = h->amps * sizeof(float2);
-    if (o.ext_state) {
+    if (h->store == SIM_STORE_HOST) {
+        const int rc = host_store_create(h, o);
+        if (rc != SIM_OK) {
+            release(h);
+            return rc;
+        }
+    } else if (o.ext_state) {
         if (o.ext_bytes < bytes || ((uintptr_t)o.ext_state & 15)) {
             release(h);
             return fail(nullptr, SIM_E_INVAL,
@@ -171,7 +178,8 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
     CREATE_TRY(cudaHostAlloc(&h->h_result, sizeof(double) * 4, cudaHostAllocDefault),
                SIM_E_NOMEM_HOST);
     const uint64_t stage = h->amps < kStageAmps ? h->amps : kStageAmps;
-    CREATE_TRY(cudaMalloc(&h->d_stage, stage * sizeof(float2)), SIM_E_NOMEM_DEV);
+    if (h->store == SIM_STORE_DEVICE)
+        CREATE_TRY(cudaMalloc(&h->d_stage, stage * sizeof(float2)), SIM_E_NOMEM_DEV);
     CREATE_TRY(cudaMalloc(&h->d_mat6, sizeof(float2) * 4096 * sim_s::kMat6Slots), SIM_E_NOMEM_DEV);
     CREATE_TRY(cudaHostAlloc(&h->h_mat6, sizeof(float2) * 4096 * sim_s::kMat6Slots,
                              cudaHostAllocDefault),
@@ -209,6 +217,8 @@ int sim_info(const sim_t *h, int *n_qubits, int *slice_bits, int *bit_of)
 int sim_state_ptr(const sim_t *h, void **dptr, void **stream)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_state_ptr: NULL handle");
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(nullptr, SIM_E_UNSUPPORTED, "sim_state_ptr: state is in the host store (sim_slot_ptr)");
     if (dptr) *dptr = h->d_state;
     if (stream) *stream = (void *)h->stream;
     return SIM_OK;
@@ -220,10 +230,11 @@ int sim_reset(sim_t *h, uint64_t basis)
     if (h->n < 64 && (basis >> h->n) != 0)
         return fail(h, SIM_E_INVAL, "sim_reset: basis index has bits above n=%d", h->n);
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->store == SIM_STORE_HOST) return host_reset(h, basis);
     SIM_CUDA_TRY(h, cudaMemsetAsync(h->d_state, 0, h->amps * sizeof(float2), h->stream));
-    const int ps = prof_begin(h, SIM_PROF_OTHER, 0.0);
+    const int ps = prof_begin(h, SIM_PROF_OTHER, 0.0, h->stream);
     const int rc = launch_set_basis(h->d_state, h->amps, logical_to_physical(h, basis), h->stream);
-    prof_end(h, ps);
+    prof_end(h, ps, h->stream);
     return rc == 0 ? SIM_OK
                    : fail(h, SIM_E_CUDA, "sim_reset: launch failed: %s",
                           cudaGetErrorString(cudaGetLastError()));
@@ -234,12 +245,16 @@ int sim_sync(sim_t *h, int timeout_ms)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_sync: NULL handle");
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
     if (timeout_ms < 0) {
+        if (h->st_in) SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
         SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        if (h->st_out) SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_out));
         return SIM_OK;
     }
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(h->stream);
+        if (e == cudaSuccess && h->st_in) e = cudaStreamQuery(h->st_in);
+        if (e == cudaSuccess && h->st_out) e = cudaStreamQuery(h->st_out);
         if (e == cudaSuccess) return SIM_OK;
         if (e != cudaErrorNotReady)
             return fail(h, SIM_E_CUDA, "sim_sync: %s", cudaGetErrorString(e));
@@ -276,6 +291,7 @@ int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtyp
     if (count == 0) return SIM_OK;
     if (!out) return fail(h, SIM_E_INVAL, "sim_amplitudes: out is NULL");
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->store == SIM_STORE_HOST) return host_amplitudes(h, first, count, out, dtype, physical_order);
     char *dst = (char *)out;
     if (physical_order || layout_is_identity(h)) {
         SIM_CUDA_TRY(h, cudaMemcpyAsync(dst, h->d_state + first, count * sizeof(float2),
@@ -284,10 +300,10 @@ int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtyp
         const uint64_t stage = h->amps < kStageAmps ? h->amps : kStageAmps;
         for (uint64_t done = 0; done < count; done += stage) {
             uint64_t c = count - done < stage ? count - done : stage;
-            const int ps = prof_begin(h, SIM_PROF_OTHER, 16.0 * c);
+            const int ps = prof_begin(h, SIM_PROF_OTHER, 16.0 * c, h->stream);
             const int rc = launch_gather_logical(h->d_state, h->d_stage, first + done, c, h->n,
                                                  h->bit_of, 0, h->stream);
-            prof_end(h, ps);
+            prof_end(h, ps, h->stream);
             if (rc != 0)
                 return fail(h, SIM_E_CUDA, "sim_amplitudes: gather launch failed: %s",
                             cudaGetErrorString(cudaGetLastError()));
@@ -310,6 +326,7 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
     if (count == 0) return SIM_OK;
     if (!src) return fail(h, SIM_E_INVAL, "sim_load_amplitudes: src is NULL");
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->store == SIM_STORE_HOST) return host_load(h, first, count, src, physical_order);
     const char *s = (const char *)src;
     if (physical_order || layout_is_identity(h)) {
         SIM_CUDA_TRY(h, cudaMemcpyAsync(h->d_state + first, s, count * sizeof(float2),
@@ -320,10 +337,10 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
             uint64_t c = count - done < stage ? count - done : stage;
             SIM_CUDA_TRY(h, cudaMemcpyAsync(h->d_stage, s + done * sizeof(float2),
                                             c * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
-            const int ps = prof_begin(h, SIM_PROF_OTHER, 16.0 * c);
+            const int ps = prof_begin(h, SIM_PROF_OTHER, 16.0 * c, h->stream);
             const int rc = launch_gather_logical(h->d_state, h->d_stage, first + done, c, h->n,
                                                  h->bit_of, 1, h->stream);
-            prof_end(h, ps);
+            prof_end(h, ps, h->stream);
             if (rc != 0)
                 return fail(h, SIM_E_CUDA, "sim_load_amplitudes: scatter launch failed: %s",
                             cudaGetErrorString(cudaGetLastError()));
@@ -338,10 +355,19 @@ int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reduce: NULL handle");
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
-    const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps);
+    if (h->store == SIM_STORE_HOST) {
+        double a = 0.0, b = 0.0;
+        const int rc = host_reduce(h, &a, &b);
+        if (rc != SIM_OK) return rc;
+        if (norm) *norm = a;
+        if (sum_p2_scaled) *sum_p2_scaled = ldexp(b, h->n);
+        if (xeb) *xeb = ldexp(b, h->n) - 1.0;
+        return SIM_OK;
+    }
+    const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps, h->stream);
     h->launches++;  // the reduction is two kernels (partials + final)
     const int rc = launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, h->stream);
-    prof_end(h, ps);
+    prof_end(h, ps, h->stream);
     if (rc != 0)
         return fail(h, SIM_E_CUDA, "sim_reduce: launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));

@@ -1,0 +1,335 @@
+// store.cu -- secondary storage (Sect. 4): the state in pinned host memory, organised so that
+// the "logical files" indexed by the sliced qubits are contiguous, streamed through device
+// slots one slice at a time.
+//
+// Layout of the host store (bit 0 first): the qubits in neither sliced set, ascending; then
+// set B in the given order; then set A in the given order.  A file is one run of
+// 2^(n - 2s) amplitudes with fixed values of A and B.  With set A sliced, slice v is the
+// 2^s files with A = v -- one contiguous run -- and its device layout is [rest | B].  With set
+// B sliced, slice w gathers the 2^s files with B = w (one copy per file) into [rest | A].
+// Every file is read and written whole, once per phase (Sect. 4).
+//
+// Pipelining: slices rotate through `slots` device buffers.  Host->device copies run on
+// st_in, device->host copies on st_out, the fused blocks on the handle's stream; events order
+// each slot's copy-in -> compute -> copy-out and stop a copy-in from overwriting a slot before
+// the previous slice has left it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace sycsim {
+
+namespace {
+
+// Split [0, n) over the host's cores.
+template <typename F>
+void parallel_for(uint64_t n, F f)
+{
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < (1u << 20) || nt == 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const uint64_t chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; t++) {
+        const uint64_t a = t * chunk, b = std::min(n, a + chunk);
+        if (a < b) th.emplace_back([=] { f(a, b); });
+    }
+    for (auto &x : th) x.join();
+}
+
+int s_of(const sim_t *h) { return h->s; }
+
+}  // namespace
+
+int host_store_create(sim_t *h, const sim_opts &o)
+{
+    const int n = h->n, s = h->s;
+    if (s < 1 || s > 8 || 2 * s >= n)
+        return fail(nullptr, SIM_E_INVAL, "sim_create(host store): need 1 <= slice_bits <= 8 and "
+                                          "2*slice_bits < n (got n=%d, slice_bits=%d)", n, s);
+    bool used[kMaxQubits] = {};
+    for (int w = 0; w < 2; w++)
+        for (int i = 0; i < s; i++) {
+            const int q = w ? o.set_b[i] : o.set_a[i];
+            if (q < 0 || q >= n || used[q])
+                return fail(nullptr, SIM_E_INVAL,
+                            "sim_create(host store): sets A and B must be %d distinct qubits each, "
+                            "disjoint, within 0..%d", s, n - 1);
+            used[q] = true;
+            h->set[w][i] = q;
+        }
+    // host layout: rest ascending, then B, then A
+    int b = 0;
+    for (int q = 0; q < n; q++)
+        if (!used[q]) h->bit_of[q] = b++;
+    for (int i = 0; i < s; i++) h->bit_of[h->set[1][i]] = n - 2 * s + i;
+    for (int i = 0; i < s; i++) h->bit_of[h->set[0][i]] = n - s + i;
+    for (int q = 0; q < n; q++) h->qubit_at[h->bit_of[q]] = q;
+    // slot layouts: phase with set A sliced -> [rest | B]; with set B sliced -> [rest | A]
+    for (int w = 0; w < 2; w++) {
+        for (int q = 0; q < n; q++) h->slice_phys[w][q] = used[q] ? -1 : h->bit_of[q];
+        for (int i = 0; i < s; i++) h->slice_phys[w][h->set[1 - w][i]] = n - 2 * s + i;
+    }
+    h->nslots = o.slots ? o.slots : 3;
+    if (h->nslots < 2 || h->nslots > sim_s::kMaxSlots)
+        return fail(nullptr, SIM_E_INVAL, "sim_create(host store): slots=%d outside 2..%d", h->nslots,
+                    sim_s::kMaxSlots);
+    cudaError_t e = cudaHostAlloc(&h->h_store, sizeof(float2) * h->amps, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        h->h_store = nullptr;
+        return fail(nullptr, SIM_E_NOMEM_HOST, "sim_create(host store): pinning %llu bytes: %s",
+                    (unsigned long long)(sizeof(float2) * h->amps), cudaGetErrorString(e));
+    }
+    const uint64_t slice = 1ull << (n - s);
+    for (int i = 0; i < h->nslots; i++) {
+        e = cudaMalloc(&h->d_slot[i], sizeof(float2) * slice);
+        if (e != cudaSuccess)
+            return fail(nullptr, SIM_E_NOMEM_DEV, "sim_create(host store): slot %d: %s", i,
+                        cudaGetErrorString(e));
+    }
+    if ((e = cudaStreamCreateWithFlags(&h->st_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->st_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(nullptr, SIM_E_CUDA, "sim_create(host store): streams: %s", cudaGetErrorString(e));
+    for (int i = 0; i < h->nslots; i++)
+        for (cudaEvent_t *ev : {&h->ev_in[i], &h->ev_done[i], &h->ev_out[i]}) {
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess)
+                return fail(nullptr, SIM_E_CUDA, "sim_create(host store): events: %s",
+                            cudaGetErrorString(e));
+            cudaEventRecord(*ev, h->stream);
+        }
+    e = cudaHostAlloc(&h->h_partials, sizeof(double) * 2 * ((size_t)1 << s), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        h->h_partials = nullptr;
+        return fail(nullptr, SIM_E_NOMEM_HOST, "sim_create(host store): %s", cudaGetErrorString(e));
+    }
+    return SIM_OK;
+}
+
+void host_store_release(sim_t *h)
+{
+    if (h->st_in) cudaStreamSynchronize(h->st_in);
+    if (h->st_out) cudaStreamSynchronize(h->st_out);
+    for (int i = 0; i < sim_s::kMaxSlots; i++) {
+        if (h->d_slot[i]) cudaFree(h->d_slot[i]);
+        for (cudaEvent_t ev : {h->ev_in[i], h->ev_done[i], h->ev_out[i]})
+            if (ev) cudaEventDestroy(ev);
+    }
+    if (h->st_in) cudaStreamDestroy(h->st_in);
+    if (h->st_out) cudaStreamDestroy(h->st_out);
+    if (h->h_store) cudaFreeHost(h->h_store);
+    if (h->h_partials) cudaFreeHost(h->h_partials);
+}
+
+// Enqueue the copy of slice `value` of sliced set `set` between the host store and device slot.
+static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int slot)
+{
+    const int n = h->n, s = s_of(h);
+    const uint64_t slice = 1ull << (n - s), file = 1ull << (n - 2 * s);
+    float2 *dev = h->d_slot[slot];
+    if (dir == SIM_H2D) {
+        // the slot must be free: its previous compute and copy-out are done
+        SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_done[slot], 0));
+        SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_out[slot], 0));
+        if (set == 0) {
+            SIM_CUDA_TRY(h, cudaMemcpyAsync(dev, h->h_store + value * slice, sizeof(float2) * slice,
+                                            cudaMemcpyHostToDevice, h->st_in));
+        } else {
+            for (uint64_t v = 0; v < (1ull << s); v++)
+                SIM_CUDA_TRY(h, cudaMemcpyAsync(dev + v * file, h->h_store + v * slice + value * file,
+                                                sizeof(float2) * file, cudaMemcpyHostToDevice, h->st_in));
+        }
+        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_in[slot], h->st_in));
+        SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0));
+    } else {
+        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_done[slot], h->stream));
+        SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_out, h->ev_done[slot], 0));
+        if (set == 0) {
+            SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_store + value * slice, dev, sizeof(float2) * slice,
+                                            cudaMemcpyDeviceToHost, h->st_out));
+        } else {
+            for (uint64_t v = 0; v < (1ull << s); v++)
+                SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_store + v * slice + value * file, dev + v * file,
+                                                sizeof(float2) * file, cudaMemcpyDeviceToHost, h->st_out));
+        }
+        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_out[slot], h->st_out));
+    }
+    return SIM_OK;
+}
+
+static int host_sync_all(sim_t *h)
+{
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_out));
+    return SIM_OK;
+}
+
+int host_reset(sim_t *h, uint64_t basis)
+{
+    int rc = host_sync_all(h);
+    if (rc != SIM_OK) return rc;
+    float2 *st = h->h_store;
+    parallel_for(h->amps, [st](uint64_t a, uint64_t b) { std::memset(st + a, 0, sizeof(float2) * (b - a)); });
+    st[logical_to_physical(h, basis)] = make_float2(1.f, 0.f);
+    return SIM_OK;
+}
+
+int host_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtype, int physical)
+{
+    int rc = host_sync_all(h);
+    if (rc != SIM_OK) return rc;
+    const float2 *st = h->h_store;
+    if (dtype == SIM_C64) {
+        float2 *o = (float2 *)out;
+        parallel_for(count, [&](uint64_t a, uint64_t b) {
+            for (uint64_t j = a; j < b; j++) o[j] = st[physical ? first + j : logical_to_physical(h, first + j)];
+        });
+    } else {
+        double *o = (double *)out;
+        parallel_for(count, [&](uint64_t a, uint64_t b) {
+            for (uint64_t j = a; j < b; j++) {
+                const float2 v = st[physical ? first + j : logical_to_physical(h, first + j)];
+                o[2 * j] = v.x;
+                o[2 * j + 1] = v.y;
+            }
+        });
+    }
+    return SIM_OK;
+}
+
+int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int physical)
+{
+    int rc = host_sync_all(h);
+    if (rc != SIM_OK) return rc;
+    float2 *st = h->h_store;
+    const float2 *in = (const float2 *)src;
+    parallel_for(count, [&](uint64_t a, uint64_t b) {
+        for (uint64_t j = a; j < b; j++) st[physical ? first + j : logical_to_physical(h, first + j)] = in[j];
+    });
+    return SIM_OK;
+}
+
+int host_reduce(sim_t *h, double *s1, double *s2)
+{
+    const int s = s_of(h);
+    const uint64_t nsl = 1ull << s, slice = 1ull << (h->n - s);
+    for (uint64_t v = 0; v < nsl; v++) {
+        const int slot = (int)(v % h->nslots);
+        int rc = enqueue_slice_copy(h, 0, v, SIM_H2D, slot);
+        if (rc != SIM_OK) return rc;
+        const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)slice, h->stream);
+        h->launches++;
+        rc = launch_reduce(h, h->d_slot[slot], slice, h->d_partials, h->d_result, h->stream);
+        prof_end(h, ps, h->stream);
+        if (rc != 0) return fail(h, SIM_E_CUDA, "sim_reduce: launch failed");
+        SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_partials + 2 * v, h->d_result, sizeof(double) * 2,
+                                        cudaMemcpyDeviceToHost, h->stream));
+        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_done[slot], h->stream));
+    }
+    int rc = host_sync_all(h);
+    if (rc != SIM_OK) return rc;
+    double a = 0.0, b = 0.0;
+    for (uint64_t v = 0; v < nsl; v++) {
+        a += h->h_partials[2 * v];
+        b += h->h_partials[2 * v + 1];
+    }
+    *s1 = a;
+    *s2 = b;
+    return SIM_OK;
+}
+
+}  // namespace sycsim
+
+using namespace sycsim;
+
+extern "C" {
+
+int sim_stream_slice(sim_t *h, int set, uint64_t value, int dir, int slot)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_stream_slice: NULL handle");
+    if (h->store != SIM_STORE_HOST)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_stream_slice: handle has no host store");
+    if (set < 0 || set > 1 || (dir != SIM_H2D && dir != SIM_D2H) || slot < 0 || slot >= h->nslots ||
+        value >= (1ull << h->s))
+        return fail(h, SIM_E_INVAL, "sim_stream_slice: set=%d value=%llu dir=%d slot=%d out of range",
+                    set, (unsigned long long)value, dir, slot);
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    return enqueue_slice_copy(h, set, value, dir, slot);
+}
+
+int sim_slot_ptr(const sim_t *h, int slot, void **dptr)
+{
+    if (!h || !dptr) return fail(nullptr, SIM_E_INVAL, "sim_slot_ptr: NULL argument");
+    if (h->store != SIM_STORE_HOST || slot < 0 || slot >= h->nslots)
+        return fail(nullptr, SIM_E_INVAL, "sim_slot_ptr: no slot %d", slot);
+    *dptr = h->d_slot[slot];
+    return SIM_OK;
+}
+
+int sim_slot_read(sim_t *h, int slot, uint64_t first, uint64_t count, void *out)
+{
+    if (!h || !out) return fail(nullptr, SIM_E_INVAL, "sim_slot_read: NULL argument");
+    if (h->store != SIM_STORE_HOST || slot < 0 || slot >= h->nslots)
+        return fail(h, SIM_E_INVAL, "sim_slot_read: no slot %d", slot);
+    const uint64_t slice = 1ull << (h->n - h->s);
+    if (first > slice || count > slice - first)
+        return fail(h, SIM_E_INVAL, "sim_slot_read: range outside the slot");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
+    SIM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_slot[slot] + first, sizeof(float2) * count,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SIM_OK;
+}
+
+int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_run_phase: NULL handle");
+    if (!p || p->n != h->n) return fail(h, SIM_E_INVAL, "sim_run_phase: plan missing or for another n");
+    if (set < 0 || set > 1) return fail(h, SIM_E_INVAL, "sim_run_phase: set must be 0 (A) or 1 (B)");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    if (h->store != SIM_STORE_HOST) {
+        // resident state: the phase's blocks apply to the whole state
+        return sim_apply_plan(h, p);
+    }
+    const int nl = h->n - h->s;
+    struct Prepared {
+        int k;
+        int tpos[kMaxK];
+        std::vector<float2> mat;
+    };
+    std::vector<Prepared> blocks(p->blocks.size());
+    for (size_t i = 0; i < p->blocks.size(); i++) {
+        const PlanBlock &b = p->blocks[i];
+        Prepared &pb = blocks[i];
+        pb.k = (int)b.qubits.size();
+        pb.mat.resize((size_t)1 << (2 * pb.k));
+        int rc = prepare_block_map(h, pb.k, b.qubits.data(), b.mat.data(), h->slice_phys[set], nl,
+                                   pb.tpos, pb.mat.data());
+        if (rc != SIM_OK) return rc;
+    }
+    const uint64_t nsl = 1ull << h->s;
+    for (uint64_t v = 0; v < nsl; v++) {
+        const int slot = (int)(v % h->nslots);
+        int rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
+        if (rc != SIM_OK) return rc;
+        for (const Prepared &pb : blocks) {
+            rc = enqueue_block_on(h, h->d_slot[slot], nl, pb.k, pb.tpos, pb.mat.data(), h->stream);
+            if (rc != SIM_OK) return rc;
+        }
+        rc = enqueue_slice_copy(h, set, v, SIM_D2H, slot);
+        if (rc != SIM_OK) return rc;
+    }
+    // later work on the handle's stream (and sim_sync) follows the last copy-out
+    for (int i = 0; i < h->nslots; i++) SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_out[i], 0));
+    return SIM_OK;
+}
+
+}  // extern "C"

@@ -147,3 +147,47 @@ def test_planner_rejects_bad_gates(pkg):
         pkg.sim_plan_create(4, recs)
     with pytest.raises(pkg.SimError):
         pkg.sim_plan_create(4, np.zeros(0, dtype=pkg._native.GATE_DTYPE), kmax=7)
+
+
+def phase_list(pkg, ph):
+    n_ph, _ = pkg.sim_phases_info(ph)
+    out = []
+    for i in range(n_ph):
+        s, plan = pkg.sim_phases_get(ph, i)
+        nb = pkg.sim_plan_info(plan)[0]
+        out.append((s, [pkg.sim_plan_block(plan, j) for j in range(nb)]))
+    return out
+
+
+@pytest.mark.parametrize("grid,cycles,s", [((3, 4), 8, 2), ((4, 5), 12, 3), ((5, 7), 16, 4)])
+def test_phases_reproduce_circuit_and_avoid_sliced_sets(pkg, oracle_mod, grid, cycles, s):
+    # Sect. 4: phases alternate the sliced set; within a phase no gate touches it.
+    circ = si.sycamore_circuit(si.Grid(*grid), cycles=cycles, seed=5)
+    n = circ.n_qubits
+    set_a = list(range(s))                 # one end of the lattice
+    set_b = list(range(n - s, n))          # the other end
+    ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=4)
+    try:
+        phases = phase_list(pkg, ph)
+        assert all(phases[i][0] != phases[i + 1][0] for i in range(len(phases) - 1))
+        if n <= 20:
+            psi = oracle_mod.basis_state(n, 0)
+        for which, blocks in phases:
+            sliced = set(set_a if which == 0 else set_b)
+            for t, m in blocks:
+                assert not sliced & set(int(q) for q in t)
+                if n <= 20:
+                    oracle_mod.apply_kq(psi, t, m)
+        if n <= 20:
+            assert np.linalg.norm(psi - oracle_mod.run_circuit(circ)) < 1e-12
+        assert sum(len(b) for _, b in phases) == pkg.sim_phases_info(ph)[1]
+    finally:
+        pkg.sim_phases_destroy(ph)
+
+
+def test_phases_reject_gate_across_sets(pkg):
+    recs = np.zeros(1, dtype=pkg._native.GATE_DTYPE)
+    recs[0]["kind"], recs[0]["q0"], recs[0]["q1"] = si.FSIM, 0, 5
+    with pytest.raises(pkg.SimError) as e:
+        pkg.sim_phases_create(8, recs, 1, [0], [5])
+    assert e.value.code == pkg.SIM_E_NONLOCAL
