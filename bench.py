@@ -256,7 +256,7 @@ def run_ours(args):
     et = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = float(amps) * circ.n_gates * args.e2e_steps * ws / float(et.item())
+    e2e_value = float(amps) * circ.n_gates * args.e2e_steps * ws / max(float(et.item()), 1e-9)
     matrix_bytes = 0
     plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
     for i in range(pkg.sim_plan_info(plan)[0]):

@@ -73,6 +73,8 @@ struct sim_s {
     float2 *d_slot[kMaxSlots] = {};
     cudaStream_t st_in = nullptr, st_out = nullptr;
     cudaEvent_t ev_in[kMaxSlots] = {}, ev_done[kMaxSlots] = {}, ev_out[kMaxSlots] = {};
+    int out_set[kMaxSlots] = {-1, -1, -1, -1};  // (set, value) of each slot's last copy-out
+    uint64_t out_val[kMaxSlots] = {};
     int set[2][8] = {};                       // sliced sets A (0) and B (1), logical qubits
     int slice_phys[2][sycsim::kMaxQubits];    // phase with set X sliced: qubit -> slot bit (-1: sliced)
     double *h_partials = nullptr;             // pinned, 2 per slice (host-mode reduction)

@@ -137,6 +137,13 @@ static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int sl
         // the slot must be free: its previous compute and copy-out are done
         SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_done[slot], 0));
         SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_out[slot], 0));
+        // and the files it reads must be written: a copy-out of the other set touched some of
+        // them (every slice of one set meets every slice of the other), a copy-out of the same
+        // slice all of them.  Copy-ins are ordered on one stream, so waiting on each slot's
+        // latest copy-out also covers that slot's earlier ones.
+        for (int i = 0; i < h->nslots; i++)
+            if (h->out_set[i] >= 0 && (h->out_set[i] != set || h->out_val[i] == value))
+                SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_out[i], 0));
         if (set == 0) {
             SIM_CUDA_TRY(h, cudaMemcpyAsync(dev, h->h_store + value * slice, sizeof(float2) * slice,
                                             cudaMemcpyHostToDevice, h->st_in));
@@ -159,6 +166,8 @@ static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int sl
                                                 sizeof(float2) * file, cudaMemcpyDeviceToHost, h->st_out));
         }
         SIM_CUDA_TRY(h, cudaEventRecord(h->ev_out[slot], h->st_out));
+        h->out_set[slot] = set;
+        h->out_val[slot] = value;
     }
     return SIM_OK;
 }

@@ -165,6 +165,9 @@ WORKLOADS = {
     "syc33_6x6m3_d20": dict(grid=Grid(6, 6, removed=((0, 0), (0, 5), (5, 0))), cycles=20),
     "syc28_4x7_d20": dict(grid=Grid(4, 7), cycles=20),
     "syc35_5x7_d16": dict(grid=Grid(5, 7), cycles=16),
+    # 35 qubits need a 256 GiB host store; hosts with less memory run the same pattern on the
+    # 5x7 grid minus one corner site (34 qubits, 128 GiB)
+    "syc34_5x7m1_d16": dict(grid=Grid(5, 7, removed=((4, 6),)), cycles=16),
 }
 
 

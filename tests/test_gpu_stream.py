@@ -122,3 +122,24 @@ def test_host_store_rejects_sliced_targets_and_device_calls(pkg):
         pkg.sim_destroy(h)
     with pytest.raises(pkg.SimError):
         pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=[0, 1], set_b=[1, 9])
+
+
+@pytest.mark.parametrize("slots", [2, 3, 4])
+def test_phase_boundaries_order_copies(pkg, oracle_mod, slots):
+    # Every slice of one set meets every slice of the other, so a phase must not read a file
+    # before the previous phase has written it back.  Many slices per slot stress the ordering.
+    circ = si.sycamore_circuit(si.Grid(4, 6), cycles=14, seed=4)
+    n, s = circ.n_qubits, 4
+    set_a, set_b = [0, 1, 2, 3], [20, 21, 22, 23]
+    ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=4)
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=slots)
+    try:
+        assert pkg.sim_phases_info(ph)[0] >= 3
+        pkg.sim_run_phases(h, ph)
+        norm, _, _ = pkg.sim_reduce(h)
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_destroy(h)
+        pkg.sim_phases_destroy(ph)
+    assert abs(norm - 1.0) < 1e-5
+    assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= TOL_FP32
