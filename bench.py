@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
+                         "apply k=4 (targets >= bit 5, then mixed), k=2, a high-bit permutation and a "
+                         "reduction, each twice, then exit; meant to run under ncu")
     return ap.parse_args()
 
 
@@ -305,9 +309,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def kernel_case():
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+    from paper_1910_09534_gb300 import build as pkg_build
+
+    pkg_build.build()
+    n = 28
+    h = pkg.sim_create(n)
+    for t in ([12, 13, 14, 15], [1, 3, 14, 20], [12, 13]):
+        u = si.random_unitary(len(t), 1)
+        for _ in range(2):
+            pkg.sim_apply_fused(h, t, u)
+    perm = list(range(n))
+    for a, b in ((25, 10), (26, 11), (27, 12)):
+        perm[a], perm[b] = b, a
+    pkg.sim_permute(h, perm)
+    pkg.sim_permute(h, list(range(n)))
+    pkg.sim_reduce(h)
+    pkg.sim_reduce(h)
+    pkg.sim_destroy(h)
+    print("kernel case done", flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernel_case:
+        kernel_case()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -27,6 +27,8 @@ SIM_E_BUSY = -7
 SIM_E_UNSUPPORTED = -8
 
 SIM_FP32 = 0
+SIM_TF32 = 1
+SIM_TF32X3 = 2
 SIM_C64 = 0
 SIM_C128 = 1
 SIM_STORE_DEVICE = 0

@@ -566,8 +566,17 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
 
 // Enqueue one prepared block on a buffer of 2^nbits amplitudes, on stream st.
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
-                     cudaStream_t st)
+                     int precision, cudaStream_t st)
 {
+    if (precision != SIM_FP32 && tc_eligible(nbits, k, tpos)) {
+        const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
+        const int rc = launch_apply_tc(h, psi, nbits, k, tpos, mat, precision, st);
+        prof_end(h, ps, st);
+        if (rc != 0)
+            return fail(h, SIM_E_CUDA, "apply (tensor cores): launch failed: %s",
+                        cudaGetErrorString(cudaGetLastError()));
+        return SIM_OK;
+    }
     const float2 *mat6 = nullptr;
     if (k == 6) {
         const int slot = h->mat6_next;
@@ -589,10 +598,12 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
     return SIM_OK;
 }
 
-int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat)
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision)
 {
-    return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, h->stream);
+    return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, precision, h->stream);
 }
+
+bool precision_ok(int precision) { return precision == SIM_FP32 || precision == SIM_TF32 || precision == SIM_TF32X3; }
 
 }  // namespace sycsim
 
@@ -604,12 +615,12 @@ extern "C" int sim_apply_fused(sim_t *h, int k, const int *targets, const double
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_fused: NULL handle");
     if (h->store != SIM_STORE_DEVICE)
         return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: host-store state: use sim_run_phase");
-    if (precision != SIM_FP32)
-        return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: precision %d not supported", precision);
+    if (!precision_ok(precision))
+        return fail(h, SIM_E_INVAL, "sim_apply_fused: precision %d", precision);
     int tpos[kMaxK];
     static thread_local float2 mat[4096];
     int rc = prepare_block(h, k, targets, matrix, tpos, mat);
     if (rc != SIM_OK) return rc;
     SIM_CUDA_TRY(h, cudaSetDevice(h->device));
-    return enqueue_block(h, k, tpos, mat);
+    return enqueue_block(h, k, tpos, mat, precision);
 }

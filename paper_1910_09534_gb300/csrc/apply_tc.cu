@@ -1,0 +1,230 @@
+// apply_tc.cu -- aggregated k-qubit gate apply on tensor cores (k = 4..6).
+//
+// The block y = M x (M complex 2^k x 2^k) is written over the reals: with x as 2^(k+1) reals,
+// R = [[Re M, -Im M], [Im M, Re M]] (interleaved), and for a tile of 16 groups
+//     W^T (16 x 2^(k+1)) = V^T (16 x 2^(k+1)) . R^T,
+// one warp-level mma.sync m16n8k8 (TF32 in, FP32 accumulate) per 8x8 piece of R^T.
+//
+// Orderings are chosen so that every thread moves whole complex amplitudes:
+//  * K (input reals) in steps of 8 = 4 members: column c < 4 is Re of member 4s + c, column
+//    c >= 4 is Im of member 4s + c - 4.  A thread's A fragment (rows g, g+8; columns t, t+4)
+//    is then the two complex values member 4s + t of groups g and g + 8: one 8-byte load each.
+//  * N (output reals) in tiles of 8 = 4 members: columns 2t, 2t+1 are Re, Im of member 4n + t,
+//    so a thread's accumulator pairs are whole output amplitudes: one 8-byte store each.
+// The B fragments (R^T, permuted as above, split hi/lo for the 3xTF32 mode) are arranged
+// fragment-major on the host and staged once per CTA in shared memory.
+//
+// Modes: TF32 (one MMA per piece; TF32 keeps 10 mantissa bits, so ~1e-3 relative error per
+// pass) and 3xTF32 (a = a_hi + a_lo with both parts TF32; hi*hi + hi*lo + lo*hi recovers
+// ~FP32 accuracy).  Used when every target is >= bit 4, so the 16 groups of a tile are 16
+// consecutive amplitude indices and each member load is a 64-byte run per 8 groups.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace sycsim {
+namespace {
+
+struct MmaGeom {
+    float2 *psi;
+    uint64_t n_mtiles;      // tiles of 16 groups: 2^(nbits - k - 4)
+    int tpos[kMaxK];        // ascending target bits (all >= 4)
+    uint64_t moff[64];      // offset of member j
+    const uint32_t *bfrag;  // [split][kstep][ntile][lane][2] TF32 bit patterns
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint64_t insert_zero_bits_t(uint64_t x, const int *pos, int cnt)
+{
+#pragma unroll
+    for (int i = 0; i < kMaxK; ++i) {
+        if (i >= cnt) break;
+        const int p = pos[i];
+        const uint64_t lo = x & ((1ull << p) - 1);
+        x = ((x >> p) << (p + 1)) | lo;
+    }
+    return x;
+}
+
+constexpr int mma_min_blocks(int k) { return k <= 5 ? 2 : 1; }
+
+template <int K, bool kSplit>
+__global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma(MmaGeom g)
+{
+    constexpr int D = 1 << K;
+    constexpr int KS = D / 4;  // k-steps (4 input members each)
+    constexpr int NT = D / 4;  // n-tiles (4 output members each)
+    constexpr int NSPLIT = kSplit ? 2 : 1;
+    constexpr int FRAG_WORDS = KS * NT * 64;
+    extern __shared__ uint32_t sb[];
+    for (int i = threadIdx.x; i < NSPLIT * FRAG_WORDS; i += blockDim.x) sb[i] = g.bfrag[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, gid = lane >> 2, t = lane & 3;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t mt = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; mt < g.n_mtiles;
+         mt += nw) {
+        const uint64_t grp = mt * 16 + gid;
+        float2 *p0 = g.psi + insert_zero_bits_t(grp, g.tpos, K);
+        float2 *p1 = g.psi + insert_zero_bits_t(grp + 8, g.tpos, K);
+        float2 x0[KS], x1[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            x0[s] = __ldcs(p0 + g.moff[4 * s + t]);
+            x1[s] = __ldcs(p1 + g.moff[4 * s + t]);
+        }
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            const float av[4] = {x0[s].x, x1[s].x, x0[s].y, x1[s].y};
+            uint32_t ahi[4], alo[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ahi[i] = to_tf32(av[i]);
+                if constexpr (kSplit) alo[i] = to_tf32(av[i] - __uint_as_float(ahi[i]));
+            }
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const uint2 bh = *reinterpret_cast<const uint2 *>(sb + ((s * NT + n) * 32 + lane) * 2);
+                mma_tf32(acc[n], ahi, bh.x, bh.y);
+                if constexpr (kSplit) {
+                    const uint2 bl =
+                        *reinterpret_cast<const uint2 *>(sb + FRAG_WORDS + ((s * NT + n) * 32 + lane) * 2);
+                    mma_tf32(acc[n], ahi, bl.x, bl.y);
+                    mma_tf32(acc[n], alo, bh.x, bh.y);
+                }
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            __stcs(p0 + g.moff[4 * n + t], make_float2(acc[n][0], acc[n][1]));
+            __stcs(p1 + g.moff[4 * n + t], make_float2(acc[n][2], acc[n][3]));
+        }
+    }
+}
+
+// Round an FP32 value to TF32 (nearest, ties away from zero, as cvt.rna), host side.
+uint32_t host_tf32(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u & 0xffffe000u;  // inf/nan: truncate
+    u += 0x1000u;                                                   // half of the dropped 13 bits
+    return u & 0xffffe000u;
+}
+
+float tf32_value(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+template <int K, bool kSplit>
+int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
+                 uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+{
+    constexpr int D = 1 << K, KS = D / 4, NT = D / 4, NSPLIT = kSplit ? 2 : 1;
+    constexpr int FRAG_WORDS = KS * NT * 64;
+    // B[k][n] = R^T, permuted: k = (step s, column c): member 4s + (c & 3), Re for c < 4, Im for
+    // c >= 4; n = (tile m, column c'): member 4m + c'/2, Re for even c', Im for odd c'.
+    for (int s = 0; s < KS; s++)
+        for (int n = 0; n < NT; n++)
+            for (int lane = 0; lane < 32; lane++) {
+                const int gid = lane >> 2, t = lane & 3;
+                const int i = 4 * s + t;            // input member (b0: Re part, b1: Im part)
+                const int o = 4 * n + (gid >> 1);   // output member
+                const bool out_im = gid & 1;
+                const float2 m = mat[o * D + i];
+                const float b0 = out_im ? m.y : m.x;   // Re x -> (Re y: Mr, Im y: Mi)
+                const float b1 = out_im ? m.x : -m.y;  // Im x -> (Re y: -Mi, Im y: Mr)
+                const size_t idx = ((size_t)(s * NT + n) * 32 + lane) * 2;
+                const uint32_t h0 = host_tf32(b0), h1 = host_tf32(b1);
+                h_frag[idx] = h0;
+                h_frag[idx + 1] = h1;
+                if (kSplit) {
+                    h_frag[FRAG_WORDS + idx] = host_tf32(b0 - tf32_value(h0));
+                    h_frag[FRAG_WORDS + idx + 1] = host_tf32(b1 - tf32_value(h1));
+                }
+            }
+    const size_t bytes = sizeof(uint32_t) * NSPLIT * FRAG_WORDS;
+    if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
+
+    MmaGeom g{};
+    g.psi = psi;
+    g.n_mtiles = 1ull << (nbits - K - 4);
+    for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];
+    for (int j = 0; j < D; j++) {
+        uint64_t o = 0;
+        for (int b = 0; b < K; b++)
+            if ((j >> b) & 1) o += 1ull << tpos[b];
+        g.moff[j] = o;
+    }
+    g.bfrag = d_frag;
+    auto kern = k_apply_mma<K, kSplit>;
+    static int occ = 0, sms = 0;
+    if (!occ) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (bytes > 48 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+            return -1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, bytes) != cudaSuccess || occ < 1)
+            occ = 1;
+    }
+    const uint64_t need = (g.n_mtiles + 7) / 8;
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    kern<<<(unsigned)grid, 256, bytes, st>>>(g);
+    (void)h;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+bool tc_eligible(int nbits, int k, const int *tpos) { return k >= 4 && k <= 6 && tpos[0] >= 4 && nbits >= k + 4; }
+
+int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                    int precision, cudaStream_t st)
+{
+    const int slot = h->frag_next;
+    h->frag_next = (slot + 1) % sim_s::kFragSlots;
+    if (cudaEventSynchronize(h->frag_ev[slot]) != cudaSuccess) return -1;  // host staging free
+    uint32_t *hf = h->h_frag + sim_s::kFragWords * slot;
+    uint32_t *df = h->d_frag + sim_s::kFragWords * slot;
+    cudaEvent_t ev = h->frag_ev[slot];
+    const bool split = precision == SIM_TF32X3;
+    switch (k) {
+    case 4: return split ? launch_mma_k<4, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<4, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 5: return split ? launch_mma_k<5, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<5, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 6: return split ? launch_mma_k<6, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<6, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    default: return -1;
+    }
+}
+
+}  // namespace sycsim

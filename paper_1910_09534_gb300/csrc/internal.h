@@ -54,6 +54,14 @@ struct sim_s {
     cudaEvent_t mat6_ev[kMat6Slots] = {};
     int mat6_next = 0;
 
+    // tensor-core B fragments (fragment-major R^T, hi/lo) go through a device ring
+    static constexpr int kFragSlots = 8;
+    static constexpr int kFragWords = 2 * 16 * 16 * 64;  // k = 6, split: 128 KiB
+    uint32_t *d_frag = nullptr;
+    uint32_t *h_frag = nullptr;  // pinned staging
+    cudaEvent_t frag_ev[kFragSlots] = {};
+    int frag_next = 0;
+
     // profiling: CUDA-event pairs around kernel launches, per kernel class
     struct ProfSlot {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -130,8 +138,15 @@ int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix,
                       int nlocal, int *tpos, float2 *mat);
 int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat);
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
-                     cudaStream_t st);
-int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat);
+                     int precision, cudaStream_t st);
+int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);
+
+bool precision_ok(int precision);
+
+// ---- apply_tc.cu (tensor cores) ----
+bool tc_eligible(int nbits, int k, const int *tpos);
+int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                    int precision, cudaStream_t st);
 
 // ---- kernel launchers (apply.cu) ----
 // Apply a 2^k x 2^k FP32 matrix (row-major complex64, bit j <-> tpos[j], tpos ascending

@@ -81,8 +81,8 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
     if (o) opts = *o;
     if (opts.kmax < 2 || opts.kmax > kMaxK)
         return fail(nullptr, SIM_E_INVAL, "sim_plan_create: kmax=%d outside 2..%d", opts.kmax, kMaxK);
-    if (opts.precision != SIM_FP32)
-        return fail(nullptr, SIM_E_UNSUPPORTED, "sim_plan_create: precision %d", opts.precision);
+    if (!precision_ok(opts.precision))
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_create: precision %d", opts.precision);
 
     auto *p = new sim_plan_s();
     p->n = n_qubits;
@@ -234,7 +234,7 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
         const int k = (int)b.qubits.size();
         int rc = prepare_block(h, k, b.qubits.data(), b.mat.data(), tpos, mat);
         if (rc != SIM_OK) return rc;
-        rc = enqueue_block(h, k, tpos, mat);
+        rc = enqueue_block(h, k, tpos, mat, p->precision);
         if (rc != SIM_OK) return rc;
     }
     return SIM_OK;

@@ -93,6 +93,10 @@ static void release(sim_t *h)
     if (h->h_mat6) cudaFreeHost(h->h_mat6);
     for (auto &e : h->mat6_ev)
         if (e) cudaEventDestroy(e);
+    if (h->d_frag) cudaFree(h->d_frag);
+    if (h->h_frag) cudaFreeHost(h->h_frag);
+    for (auto &e : h->frag_ev)
+        if (e) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -185,6 +189,12 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
                              cudaHostAllocDefault),
                SIM_E_NOMEM_HOST);
     for (auto &e : h->mat6_ev) CREATE_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), SIM_E_CUDA);
+    CREATE_TRY(cudaMalloc(&h->d_frag, sizeof(uint32_t) * sim_s::kFragWords * sim_s::kFragSlots),
+               SIM_E_NOMEM_DEV);
+    CREATE_TRY(cudaHostAlloc(&h->h_frag, sizeof(uint32_t) * sim_s::kFragWords * sim_s::kFragSlots,
+                             cudaHostAllocDefault),
+               SIM_E_NOMEM_HOST);
+    for (auto &e : h->frag_ev) CREATE_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), SIM_E_CUDA);
 #undef CREATE_TRY
 
     int rc = sim_reset(h, 0);

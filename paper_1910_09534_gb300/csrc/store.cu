@@ -330,7 +330,8 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         int rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
         if (rc != SIM_OK) return rc;
         for (const Prepared &pb : blocks) {
-            rc = enqueue_block_on(h, h->d_slot[slot], nl, pb.k, pb.tpos, pb.mat.data(), h->stream);
+            rc = enqueue_block_on(h, h->d_slot[slot], nl, pb.k, pb.tpos, pb.mat.data(), p->precision,
+                                  h->stream);
             if (rc != SIM_OK) return rc;
         }
         rc = enqueue_slice_copy(h, set, v, SIM_D2H, slot);
