@@ -290,6 +290,57 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * phases' sets.  Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
+/* ---- serving: many circuits on one GPU (no counterpart in the paper) --------
+ * A continuous-batching server.  srv_submit plans the circuit (aggregation as
+ * sim_plan_create) on the caller's thread and queues it; a scheduler thread
+ * admits queued circuits in arrival order while their device footprint
+ * (8 * 2^n bytes + 64 KiB) fits the HBM budget -- a circuit that does not fit
+ * can be overtaken by at most 64 later ones -- and runs them concurrently:
+ * circuits with n <= small_n are packed into one kernel launch (one thread block
+ * per circuit: reset, every block, reduction); larger ones run on `slots`
+ * streams with stream-ordered memory.  A circuit always takes the same path and
+ * plan, so its result does not depend on what else is in flight. */
+typedef struct srv_s srv_t;
+
+typedef struct srv_opts {
+    int device;
+    int slots;           /* concurrent circuits above small_n (0 = 6, max 32) */
+    int small_n;         /* circuits with n <= small_n are packed (0 = 20, max 24) */
+    int max_pack;        /* most circuits per packed launch (0 = 1024) */
+    int kmax;            /* aggregation width (0 = 5 for n <= 24, else 4) */
+    int precision;       /* circuits above small_n: SIM_FP32, SIM_TF32 or SIM_TF32X3 */
+    uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
+    int reserved[8];
+} srv_opts;
+
+typedef struct srv_stats_t {
+    uint64_t submitted, completed, rejected, in_flight;
+    double p50_ms, p99_ms, mean_ms; /* latency: submit -> completion */
+    double circuits_per_s;          /* completed / (last completion - first submit) */
+    uint64_t hbm_budget, hbm_used;
+} srv_stats_t;
+
+int srv_create(const srv_opts *o, srv_t **out);
+/* Finishes every queued circuit, then frees the server. */
+int srv_destroy(srv_t *s);
+const char *srv_last_error(const srv_t *s);
+
+/* Queue one circuit (gate records as for sim_plan_create); out_amps, if not NULL,
+ * receives all 2^n complex64 amplitudes (logical order) and must stay valid until
+ * srv_wait returns for this ticket (pinned memory is faster).  SIM_E_BUSY if the
+ * circuit can never fit the budget; SIM_E_INVAL for a bad gate list. */
+int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void *out_amps,
+               uint64_t *ticket);
+
+/* Wait at most timeout_ms (< 0: no limit) for a ticket; SIM_E_TIMEOUT if not done.
+ * On success returns the circuit's norm, 2^n sum p^2 and its latency; the ticket
+ * is then forgotten. */
+int srv_wait(srv_t *s, uint64_t ticket, int timeout_ms, double *norm, double *sum_p2_scaled,
+             double *latency_ms);
+
+/* Counters and the latency distribution of completed circuits. */
+int srv_stats(srv_t *s, srv_stats_t *out);
+
 #ifdef __cplusplus
 }
 #endif

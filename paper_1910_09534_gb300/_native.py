@@ -60,6 +60,20 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
+class SrvOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int), ("small_n", ctypes.c_int),
+                ("max_pack", ctypes.c_int), ("kmax", ctypes.c_int), ("precision", ctypes.c_int),
+                ("hbm_budget", ctypes.c_uint64), ("reserved", ctypes.c_int * 8)]
+
+
+class SrvStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("in_flight", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("circuits_per_s", ctypes.c_double), ("hbm_budget", ctypes.c_uint64),
+                ("hbm_used", ctypes.c_uint64)]
+
+
 class SimError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"[{code}] {msg}")
@@ -114,6 +128,14 @@ _SIGS = {
     "sim_phases_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_phases_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_run_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "srv_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "srv_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "srv_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "srv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "srv_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p]),
+    "srv_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -389,6 +411,50 @@ def sim_phases_get(ph, i: int):
 
 def sim_run_phases(h, ph) -> None:
     _check(lib().sim_run_phases(h, ph), h)
+
+
+def _srv_check(rc: int, srv=None):
+    if rc < 0:
+        msg = lib().srv_last_error(srv)
+        raise SimError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def srv_create(device: int = 0, slots: int = 0, small_n: int = 0, max_pack: int = 0, kmax: int = 0,
+               precision: int = SIM_FP32, hbm_budget: int = 0):
+    o = SrvOpts()
+    o.device, o.slots, o.small_n, o.max_pack, o.kmax, o.precision = device, slots, small_n, max_pack, kmax, precision
+    o.hbm_budget = hbm_budget
+    srv = ctypes.c_void_p()
+    _srv_check(lib().srv_create(ctypes.byref(o), ctypes.byref(srv)))
+    return srv
+
+
+def srv_destroy(srv) -> None:
+    _srv_check(lib().srv_destroy(srv))
+
+
+def srv_submit(srv, n_qubits: int, gates: np.ndarray, out_amps: np.ndarray | None = None) -> int:
+    """Queue a circuit; out_amps (complex64, 2^n, kept alive by the caller) receives the amplitudes."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    if out_amps is not None:
+        assert out_amps.dtype == np.complex64 and out_amps.size >= (1 << n_qubits) and out_amps.flags.c_contiguous
+    t = ctypes.c_uint64()
+    _srv_check(lib().srv_submit(srv, n_qubits, int(g.size), _ptr(g), _ptr(out_amps), ctypes.byref(t)), srv)
+    return t.value
+
+
+def srv_wait(srv, ticket: int, timeout_ms: int = -1):
+    """(norm, 2^n sum p^2, latency_ms) of a finished circuit."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _srv_check(lib().srv_wait(srv, ticket, timeout_ms, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), srv)
+    return a.value, b.value, c.value
+
+
+def srv_stats(srv) -> dict:
+    st = SrvStats()
+    _srv_check(lib().srv_stats(srv, ctypes.byref(st)), srv)
+    return {f: getattr(st, f) for f, _ in SrvStats._fields_}
 
 
 def exported_symbols() -> list:

@@ -523,8 +523,9 @@ int launch_apply_fp32(sim_t *, float2 *psi, int nbits, int k, const int *tpos, c
 // >= nlocal is not local), sort, and reorder + round the FP64 matrix to FP32 in sorted-bit
 // order.  Returns SIM_OK or an error code (message set on h).
 int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
-                      int nlocal, int *tpos, float2 *mat)
+                      int nlocal, int *tpos, float2 *mat, int nq)
 {
+    if (nq < 0) nq = h->n;
     if (k < 1 || k > kMaxK) return fail(h, SIM_E_INVAL, "apply: k=%d outside 1..%d", k, kMaxK);
     if (!targets || !matrix) return fail(h, SIM_E_INVAL, "apply: NULL targets or matrix");
     if (k > nlocal)
@@ -532,7 +533,7 @@ int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix,
     int phys[kMaxK], order[kMaxK];
     for (int j = 0; j < k; j++) {
         const int q = targets[j];
-        if (q < 0 || q >= h->n) return fail(h, SIM_E_INVAL, "apply: target %d outside 0..%d", q, h->n - 1);
+        if (q < 0 || q >= nq) return fail(h, SIM_E_INVAL, "apply: target %d outside 0..%d", q, nq - 1);
         for (int i = 0; i < j; i++)
             if (targets[i] == q) return fail(h, SIM_E_INVAL, "apply: duplicate target %d", q);
         phys[j] = phys_of[q];

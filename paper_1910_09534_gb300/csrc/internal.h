@@ -135,7 +135,7 @@ void prof_end(sim_t *h, int slot, cudaStream_t st);
 // apply.cu: block preparation (targets -> sorted physical bits, FP32 matrix in that order)
 // and enqueueing on an arbitrary buffer/stream.
 int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
-                      int nlocal, int *tpos, float2 *mat);
+                      int nlocal, int *tpos, float2 *mat, int nq = -1);
 int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat);
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st);

@@ -1,0 +1,653 @@
+// serve.cu -- continuous-batching server for many circuits on one GPU (no counterpart in the
+// paper, which simulates one circuit; it reuses the paper's per-circuit path: aggregation,
+// Sect. 5, and the fused-block apply).
+//
+// Requests arrive through srv_submit from any thread.  The caller's thread validates the gate
+// list, plans it (aggregation) and rounds the block matrices, so planning runs in parallel
+// with the GPU.  One scheduler thread then:
+//  * admits requests in arrival order while their device footprint (8 * 2^n bytes plus
+//    scratch) fits the HBM budget; a request that does not fit may be overtaken by smaller
+//    ones at most kMaxBypass times, after which admission waits for it (no starvation);
+//  * packs small circuits (n <= small_n) into one launch of k_circuit_cta: one CTA runs one
+//    whole circuit -- reset, every block, the reduction -- with the block matrix in shared
+//    memory, so a batch of small circuits costs one kernel launch instead of one per block;
+//  * runs larger circuits on one of several slot streams with stream-ordered allocation, so
+//    circuits of different sizes overlap on the device;
+//  * detects completion by polling events, frees memory and budget, and wakes waiters.
+// Results (norm, 2^n sum p^2, XEB; optionally all amplitudes into the caller's buffer) and
+// latencies (submit -> completion seen) are recorded; srv_stats reports p50/p99 and circuits/s.
+// The same circuit always takes the same path and the same plan, so its result does not depend
+// on what else is being served.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace sycsim {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct PackedBlock {
+    int k;
+    int tpos[kMaxK];
+    uint32_t mat_off;  // float2 offset of the block's matrix in the batch's matrix table
+};
+
+struct PackedJob {
+    float2 *psi;
+    const PackedBlock *blocks;
+    const float2 *mats;
+    double *out;  // [sum p, sum p^2]
+    int n, nblocks;
+};
+
+constexpr int kPackThreads = 256;
+constexpr int kPackMaxK = 5;
+
+__device__ __forceinline__ uint64_t insert_zero_bits_s(uint64_t x, const int *pos, int cnt)
+{
+    for (int i = 0; i < cnt; ++i) {
+        const int p = pos[i];
+        const uint64_t lo = x & ((1ull << p) - 1);
+        x = ((x >> p) << (p + 1)) | lo;
+    }
+    return x;
+}
+
+template <int K>
+__device__ __forceinline__ void cta_block(float2 *psi, int n, const int *tpos, const float2 *M,
+                                          const uint32_t *moff)
+{
+    constexpr int D = 1 << K;
+    const uint64_t ngroups = 1ull << (n - K);
+    for (uint64_t gi = threadIdx.x; gi < ngroups; gi += blockDim.x) {
+        float2 *p = psi + insert_zero_bits_s(gi, tpos, K);
+        float2 x[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) x[j] = p[moff[j]];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            float yr = 0.f, yi = 0.f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float2 m = M[r * D + c];
+                yr = fmaf(m.x, x[c].x, yr);
+                yr = fmaf(m.y, -x[c].y, yr);
+                yi = fmaf(m.x, x[c].y, yi);
+                yi = fmaf(m.y, x[c].x, yi);
+            }
+            p[moff[r]] = make_float2(yr, yi);
+        }
+    }
+}
+
+// One CTA = one whole small circuit.
+__global__ void __launch_bounds__(kPackThreads) k_circuit_cta(const PackedJob *jobs)
+{
+    __shared__ float2 M[32 * 32];
+    __shared__ uint32_t moff[32];
+    __shared__ int tpos[kMaxK];
+    __shared__ double red[2][kPackThreads / 32];
+    const PackedJob J = jobs[blockIdx.x];
+    const uint64_t amps = 1ull << J.n;
+    for (uint64_t i = threadIdx.x; i < amps; i += blockDim.x) J.psi[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (threadIdx.x == 0) J.psi[0] = make_float2(1.f, 0.f);
+    for (int b = 0; b < J.nblocks; ++b) {
+        const PackedBlock B = J.blocks[b];
+        const int D = 1 << B.k;
+        __syncthreads();  // previous block done with M, psi and tpos
+        for (int i = threadIdx.x; i < D * D; i += blockDim.x) M[i] = J.mats[B.mat_off + i];
+        if (threadIdx.x < D) {
+            uint32_t o = 0;
+            for (int q = 0; q < B.k; ++q)
+                if ((threadIdx.x >> q) & 1) o += 1u << B.tpos[q];
+            moff[threadIdx.x] = o;
+        }
+        if (threadIdx.x < kMaxK) tpos[threadIdx.x] = B.tpos[threadIdx.x];
+        __syncthreads();
+        switch (B.k) {
+        case 1: cta_block<1>(J.psi, J.n, tpos, M, moff); break;
+        case 2: cta_block<2>(J.psi, J.n, tpos, M, moff); break;
+        case 3: cta_block<3>(J.psi, J.n, tpos, M, moff); break;
+        case 4: cta_block<4>(J.psi, J.n, tpos, M, moff); break;
+        default: cta_block<5>(J.psi, J.n, tpos, M, moff); break;
+        }
+    }
+    __syncthreads();
+    double s1 = 0.0, s2 = 0.0;
+    for (uint64_t i = threadIdx.x; i < amps; i += blockDim.x) {
+        const float2 v = J.psi[i];
+        const double p = (double)v.x * v.x + (double)v.y * v.y;
+        s1 += p;
+        s2 += p * p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = s1;
+        red[1][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < kPackThreads / 32; ++w) {
+            a += red[0][w];
+            c += red[1][w];
+        }
+        J.out[0] = a;
+        J.out[1] = c;
+    }
+}
+
+struct Prepared {
+    int k;
+    int tpos[kMaxK];
+    std::vector<float2> mat;
+};
+
+struct Req {
+    uint64_t ticket = 0;
+    int n = 0;
+    int precision = SIM_FP32;
+    bool packed = false;
+    void *out_amps = nullptr;
+    std::vector<Prepared> blocks;
+    uint64_t bytes = 0;  // admission footprint
+    Clock::time_point t_submit, t_done;
+    int status = 1;  // 1 pending, 0 ok, < 0 error
+    double norm = 0.0, s2 = 0.0;
+    int bypassed = 0;
+    // in flight (unpacked)
+    int slot = -1;
+    float2 *d_state = nullptr;
+    cudaEvent_t ev = nullptr;
+    double *h_res = nullptr;  // pinned pair
+};
+
+struct Batch {
+    std::vector<std::shared_ptr<Req>> jobs;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    void *d_mem = nullptr;          // states + tables + results, one stream-ordered allocation
+    std::vector<char> h_table;      // pinned copy source lives in h_stage
+    char *h_stage = nullptr;        // pinned
+    size_t stage_bytes = 0;
+    double *h_res = nullptr;        // pinned, 2 per job
+    bool busy = false;
+};
+
+constexpr int kMaxBypass = 64;
+constexpr int kResultRing = 1 << 16;
+
+}  // namespace
+}  // namespace sycsim
+
+using namespace sycsim;
+
+struct srv_s {
+    srv_opts o{};
+    uint64_t budget = 0, used = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Req>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Req>> reqs;
+    uint64_t next_ticket = 1;
+    std::vector<sim_t *> slots;
+    std::vector<std::shared_ptr<Req>> slot_req;
+    std::vector<Batch> batches;
+    double *h_results = nullptr;  // pinned ring of result pairs for unpacked requests
+    std::thread worker;
+    bool stop = false;
+    std::string err;
+    // stats
+    uint64_t submitted = 0, completed = 0, rejected = 0;
+    std::vector<double> lat_ms;
+    Clock::time_point t_first, t_last;
+    bool any_done = false;
+};
+
+namespace {
+
+int srv_fail(srv_t *s, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s)
+        s->err = buf;
+    else
+        set_thread_error("%s", buf);
+    return code;
+}
+
+// kmax by size: launch-bound small and mid-size states gain from fewer, wider blocks;
+// HBM-bound large states from the width whose pass stays HBM-bound on CUDA cores.
+int auto_kmax(int n, bool packed) { return packed ? 5 : (n <= 24 ? 5 : 4); }
+
+void finish(srv_t *s, const std::shared_ptr<Req> &r, int status, double a, double b)
+{
+    r->status = status;
+    r->norm = a;
+    r->s2 = b;
+    r->t_done = Clock::now();
+    s->used -= r->bytes;
+    s->completed++;
+    const double ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    s->lat_ms.push_back(ms);
+    if (!s->any_done || r->t_done > s->t_last) s->t_last = r->t_done;
+    s->any_done = true;
+}
+
+// Launch one unpacked request on slot i (scheduler thread, lock held).
+int launch_unpacked(srv_t *s, int i, const std::shared_ptr<Req> &r)
+{
+    sim_t *h = s->slots[i];
+    cudaStream_t st = h->stream;
+    const uint64_t amps = 1ull << r->n;
+    if (cudaMallocAsync(&r->d_state, sizeof(float2) * amps, st) != cudaSuccess) return SIM_E_NOMEM_DEV;
+    if (cudaMemsetAsync(r->d_state, 0, sizeof(float2) * amps, st) != cudaSuccess) return SIM_E_CUDA;
+    if (launch_set_basis(r->d_state, amps, 0, st) != 0) return SIM_E_CUDA;
+    for (const Prepared &b : r->blocks) {
+        const int rc = enqueue_block_on(h, r->d_state, r->n, b.k, b.tpos, b.mat.data(), r->precision, st);
+        if (rc != SIM_OK) return rc;
+    }
+    if (launch_reduce(h, r->d_state, amps, h->d_partials, h->d_result, st) != 0) return SIM_E_CUDA;
+    if (cudaMemcpyAsync(r->h_res, h->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SIM_E_CUDA;
+    if (r->out_amps &&
+        cudaMemcpyAsync(r->out_amps, r->d_state, sizeof(float2) * amps, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SIM_E_CUDA;
+    if (cudaFreeAsync(r->d_state, st) != cudaSuccess) return SIM_E_CUDA;
+    if (cudaEventRecord(r->ev, st) != cudaSuccess) return SIM_E_CUDA;
+    r->slot = i;
+    s->slot_req[i] = r;
+    return SIM_OK;
+}
+
+// Launch one packed batch of small requests (scheduler thread, lock held).
+int launch_packed(srv_t *s, Batch &B)
+{
+    size_t nblk = 0, nmat = 0, state_amps = 0;
+    for (auto &r : B.jobs) {
+        nblk += r->blocks.size();
+        for (auto &b : r->blocks) nmat += b.mat.size();
+        state_amps += 1ull << r->n;
+    }
+    const size_t nj = B.jobs.size();
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t off_jobs = 0, off_blk = align(off_jobs + nj * sizeof(PackedJob));
+    const size_t off_mat = align(off_blk + nblk * sizeof(PackedBlock));
+    const size_t off_res = align(off_mat + nmat * sizeof(float2));
+    const size_t off_state = align(off_res + nj * 2 * sizeof(double));
+    const size_t table_bytes = off_res;
+    const size_t total = off_state + state_amps * sizeof(float2);
+    if (B.stage_bytes < table_bytes) {
+        if (B.h_stage) cudaFreeHost(B.h_stage);
+        B.h_stage = nullptr;
+        if (cudaHostAlloc(&B.h_stage, table_bytes * 2, cudaHostAllocDefault) != cudaSuccess) return SIM_E_NOMEM_HOST;
+        B.stage_bytes = table_bytes * 2;
+    }
+    if (cudaMallocAsync(&B.d_mem, total, B.st) != cudaSuccess) return SIM_E_NOMEM_DEV;
+    char *d = (char *)B.d_mem;
+    PackedJob *hj = (PackedJob *)(B.h_stage + off_jobs);
+    PackedBlock *hb = (PackedBlock *)(B.h_stage + off_blk);
+    float2 *hm = (float2 *)(B.h_stage + off_mat);
+    size_t bi = 0, mi = 0, si = 0;
+    for (size_t j = 0; j < nj; j++) {
+        auto &r = B.jobs[j];
+        hj[j].psi = (float2 *)(d + off_state) + si;
+        hj[j].blocks = (const PackedBlock *)(d + off_blk) + bi;
+        hj[j].mats = (const float2 *)(d + off_mat);
+        hj[j].out = (double *)(d + off_res) + 2 * j;
+        hj[j].n = r->n;
+        hj[j].nblocks = (int)r->blocks.size();
+        for (auto &b : r->blocks) {
+            PackedBlock &pb = hb[bi++];
+            pb.k = b.k;
+            for (int q = 0; q < kMaxK; q++) pb.tpos[q] = q < b.k ? b.tpos[q] : 0;
+            pb.mat_off = (uint32_t)mi;
+            std::memcpy(hm + mi, b.mat.data(), b.mat.size() * sizeof(float2));
+            mi += b.mat.size();
+        }
+        si += 1ull << r->n;
+    }
+    if (cudaMemcpyAsync(d, B.h_stage, table_bytes, cudaMemcpyHostToDevice, B.st) != cudaSuccess) return SIM_E_CUDA;
+    k_circuit_cta<<<(unsigned)nj, kPackThreads, 0, B.st>>>((const PackedJob *)d);
+    if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+    if (cudaMemcpyAsync(B.h_res, d + off_res, nj * 2 * sizeof(double), cudaMemcpyDeviceToHost, B.st) != cudaSuccess)
+        return SIM_E_CUDA;
+    si = 0;
+    for (size_t j = 0; j < nj; j++) {
+        auto &r = B.jobs[j];
+        if (r->out_amps &&
+            cudaMemcpyAsync(r->out_amps, (float2 *)(d + off_state) + si, sizeof(float2) << r->n,
+                            cudaMemcpyDeviceToHost, B.st) != cudaSuccess)
+            return SIM_E_CUDA;
+        si += 1ull << r->n;
+    }
+    if (cudaFreeAsync(B.d_mem, B.st) != cudaSuccess) return SIM_E_CUDA;
+    if (cudaEventRecord(B.ev, B.st) != cudaSuccess) return SIM_E_CUDA;
+    B.busy = true;
+    return SIM_OK;
+}
+
+void scheduler(srv_t *s)
+{
+    cudaSetDevice(s->o.device);
+    std::vector<std::shared_ptr<Req>> pack_pending;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        bool progressed = false;
+        // completions: unpacked slots
+        for (size_t i = 0; i < s->slots.size(); i++) {
+            auto &r = s->slot_req[i];
+            if (!r) continue;
+            const cudaError_t e = cudaEventQuery(r->ev);
+            if (e == cudaErrorNotReady) continue;
+            finish(s, r, e == cudaSuccess ? SIM_OK : SIM_E_CUDA, r->h_res[0], r->h_res[1]);
+            r.reset();
+            progressed = true;
+        }
+        // completions: packed batches
+        for (auto &B : s->batches) {
+            if (!B.busy) continue;
+            const cudaError_t e = cudaEventQuery(B.ev);
+            if (e == cudaErrorNotReady) continue;
+            for (size_t j = 0; j < B.jobs.size(); j++)
+                finish(s, B.jobs[j], e == cudaSuccess ? SIM_OK : SIM_E_CUDA, B.h_res[2 * j], B.h_res[2 * j + 1]);
+            B.jobs.clear();
+            B.busy = false;
+            progressed = true;
+        }
+        if (progressed) s->cv_done.notify_all();
+        if (s->stop && s->queue.empty()) {
+            bool idle = pack_pending.empty();
+            for (auto &r : s->slot_req) idle &= !r;
+            for (auto &B : s->batches) idle &= !B.busy;
+            if (idle) break;
+        }
+        // admission, in arrival order; a request that does not fit may be overtaken by later ones
+        // at most kMaxBypass times, then admission waits for it
+        std::shared_ptr<Req> first_blocked;
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+            if (first_blocked && first_blocked->bypassed >= kMaxBypass) break;
+            auto r = *it;
+            bool admitted = false;
+            if (s->used + r->bytes <= s->budget) {
+                if (r->packed) {
+                    s->used += r->bytes;
+                    pack_pending.push_back(r);
+                    admitted = true;
+                } else {
+                    for (size_t i = 0; i < s->slots.size(); i++)
+                        if (!s->slot_req[i]) {
+                            s->used += r->bytes;
+                            const int rc = launch_unpacked(s, (int)i, r);
+                            if (rc != SIM_OK) {
+                                finish(s, r, rc, 0.0, 0.0);
+                                s->cv_done.notify_all();
+                            }
+                            admitted = true;
+                            break;
+                        }
+                }
+            }
+            if (admitted) {
+                if (first_blocked) first_blocked->bypassed++;
+                it = s->queue.erase(it);
+                progressed = true;
+                continue;
+            }
+            if (!first_blocked) first_blocked = r;
+            ++it;
+        }
+        // packed launch: whenever a batch stream is free
+        if (!pack_pending.empty())
+            for (auto &B : s->batches)
+                if (!B.busy) {
+                    const size_t take = std::min(pack_pending.size(), (size_t)s->o.max_pack);
+                    B.jobs.assign(pack_pending.begin(), pack_pending.begin() + take);
+                    pack_pending.erase(pack_pending.begin(), pack_pending.begin() + take);
+                    const int rc = launch_packed(s, B);
+                    if (rc != SIM_OK) {
+                        for (auto &r : B.jobs) finish(s, r, rc, 0.0, 0.0);
+                        B.jobs.clear();
+                        B.busy = false;
+                        s->cv_done.notify_all();
+                    }
+                    progressed = true;
+                    break;
+                }
+        if (!progressed) s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    }
+}
+
+void srv_release(srv_t *s)
+{
+    if (!s) return;
+    if (s->worker.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stop = true;
+        }
+        s->cv_work.notify_all();
+        s->worker.join();
+    }
+    cudaSetDevice(s->o.device);
+    for (auto &B : s->batches) {
+        if (B.st) cudaStreamSynchronize(B.st);
+        if (B.ev) cudaEventDestroy(B.ev);
+        if (B.st) cudaStreamDestroy(B.st);
+        if (B.h_stage) cudaFreeHost(B.h_stage);
+        if (B.h_res) cudaFreeHost(B.h_res);
+    }
+    for (auto &kv : s->reqs)
+        if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    for (auto *h : s->slots) sim_destroy(h);
+    if (s->h_results) cudaFreeHost(s->h_results);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srv_create(const srv_opts *opts, srv_t **out)
+{
+    if (!out) return srv_fail(nullptr, SIM_E_INVAL, "srv_create: out is NULL");
+    *out = nullptr;
+    auto *s = new srv_s();
+    if (opts) s->o = *opts;
+    if (s->o.slots <= 0) s->o.slots = 6;
+    if (s->o.small_n <= 0) s->o.small_n = 20;
+    if (s->o.max_pack <= 0) s->o.max_pack = 1024;
+    if (s->o.slots > 32 || s->o.small_n > 24 || s->o.max_pack > 65536 ||
+        (s->o.precision != SIM_FP32 && s->o.precision != SIM_TF32 && s->o.precision != SIM_TF32X3)) {
+        delete s;
+        return srv_fail(nullptr, SIM_E_INVAL, "srv_create: slots <= 32, small_n <= 24, max_pack <= 65536");
+    }
+    if (cudaSetDevice(s->o.device) != cudaSuccess) {
+        delete s;
+        return srv_fail(nullptr, SIM_E_CUDA, "srv_create: device %d unavailable", s->o.device);
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    s->budget = s->o.hbm_budget ? s->o.hbm_budget : (uint64_t)(0.8 * (double)free_b);
+    // keep freed stream-ordered memory in the pool instead of returning it to the driver
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->o.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    for (int i = 0; i < s->o.slots; i++) {
+        sim_opts so{};
+        so.device = s->o.device;
+        sim_t *h = nullptr;
+        const int rc = sim_create(1, 0, &so, &h);
+        if (rc != SIM_OK) {
+            srv_release(s);
+            return srv_fail(nullptr, rc, "srv_create: slot %d: %s", i, sim_last_error(nullptr));
+        }
+        s->slots.push_back(h);
+    }
+    s->slot_req.resize(s->slots.size());
+    s->batches.resize(2);
+    for (auto &B : s->batches) {
+        if (cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaHostAlloc(&B.h_res, sizeof(double) * 2 * s->o.max_pack, cudaHostAllocDefault) != cudaSuccess) {
+            srv_release(s);
+            return srv_fail(nullptr, SIM_E_CUDA, "srv_create: stream/pinned setup failed");
+        }
+    }
+    if (cudaHostAlloc(&s->h_results, sizeof(double) * 2 * kResultRing, cudaHostAllocDefault) != cudaSuccess) {
+        s->h_results = nullptr;
+        srv_release(s);
+        return srv_fail(nullptr, SIM_E_NOMEM_HOST, "srv_create: pinned results");
+    }
+    s->worker = std::thread(scheduler, s);
+    *out = s;
+    return SIM_OK;
+}
+
+int srv_destroy(srv_t *s)
+{
+    if (!s) return srv_fail(nullptr, SIM_E_INVAL, "srv_destroy: NULL");
+    srv_release(s);
+    return SIM_OK;
+}
+
+const char *srv_last_error(const srv_t *s) { return s ? s->err.c_str() : thread_error(); }
+
+int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void *out_amps, uint64_t *ticket)
+{
+    if (!s || !ticket) return srv_fail(s, SIM_E_INVAL, "srv_submit: NULL argument");
+    *ticket = 0;
+    auto r = std::make_shared<Req>();
+    r->n = n_qubits;
+    r->packed = n_qubits <= s->o.small_n;
+    r->precision = r->packed ? SIM_FP32 : s->o.precision;
+    r->out_amps = out_amps;
+    r->bytes = (sizeof(float2) << n_qubits) + (1u << 16);
+    if (r->bytes > s->budget) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->rejected++;
+        return srv_fail(s, SIM_E_BUSY, "srv_submit: %d qubits need %llu bytes, budget %llu", n_qubits,
+                        (unsigned long long)r->bytes, (unsigned long long)s->budget);
+    }
+    // plan on the caller's thread
+    sim_plan_opts po{};
+    po.kmax = s->o.kmax ? s->o.kmax : auto_kmax(n_qubits, r->packed);
+    if (r->packed) po.kmax = std::min(po.kmax, kPackMaxK);
+    po.precision = r->precision;
+    sim_plan_t *plan = nullptr;
+    int rc = sim_plan_create(n_qubits, n_gates, gates, &po, &plan);
+    if (rc != SIM_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->rejected++;
+        return srv_fail(s, rc, "srv_submit: %s", sim_last_error(nullptr));
+    }
+    int ident[kMaxQubits];
+    for (int q = 0; q < kMaxQubits; q++) ident[q] = q;
+    r->blocks.resize(plan->blocks.size());
+    for (size_t i = 0; i < plan->blocks.size(); i++) {
+        const PlanBlock &b = plan->blocks[i];
+        Prepared &pb = r->blocks[i];
+        pb.k = (int)b.qubits.size();
+        pb.mat.resize((size_t)1 << (2 * pb.k));
+        rc = prepare_block_map(s->slots[0], pb.k, b.qubits.data(), b.mat.data(), ident, n_qubits, pb.tpos,
+                               pb.mat.data(), n_qubits);
+        if (rc != SIM_OK) break;
+    }
+    sim_plan_destroy(plan);
+    if (rc != SIM_OK) return srv_fail(s, rc, "srv_submit: block preparation failed");
+    int prev_dev = 0;
+    cudaGetDevice(&prev_dev);
+    cudaSetDevice(s->o.device);
+    const cudaError_t ee = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+    cudaSetDevice(prev_dev);
+    if (ee != cudaSuccess) return srv_fail(s, SIM_E_CUDA, "srv_submit: event");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return srv_fail(s, SIM_E_BUSY, "srv_submit: server is stopping");
+        r->ticket = s->next_ticket++;
+        r->h_res = s->h_results + 2 * (r->ticket % kResultRing);
+        r->t_submit = Clock::now();
+        if (s->submitted == 0) s->t_first = r->t_submit;
+        s->submitted++;
+        s->reqs[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return SIM_OK;
+}
+
+int srv_wait(srv_t *s, uint64_t ticket, int timeout_ms, double *norm, double *sum_p2_scaled, double *latency_ms)
+{
+    if (!s) return srv_fail(nullptr, SIM_E_INVAL, "srv_wait: NULL server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return srv_fail(s, SIM_E_INVAL, "srv_wait: unknown ticket %llu", (unsigned long long)ticket);
+    auto r = it->second;
+    auto done = [&] { return r->status != 1; };
+    if (timeout_ms < 0)
+        s->cv_done.wait(lk, done);
+    else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done))
+        return srv_fail(s, SIM_E_TIMEOUT, "srv_wait: ticket %llu not done after %d ms", (unsigned long long)ticket,
+                        timeout_ms);
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+    s->reqs.erase(it);
+    if (r->status != SIM_OK) return srv_fail(s, r->status, "srv_wait: request failed");
+    if (norm) *norm = r->norm;
+    if (sum_p2_scaled) *sum_p2_scaled = std::ldexp(r->s2, r->n);
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    return SIM_OK;
+}
+
+int srv_stats(srv_t *s, srv_stats_t *out)
+{
+    if (!s || !out) return srv_fail(s, SIM_E_INVAL, "srv_stats: NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof *out);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->in_flight = s->submitted - s->completed;
+    std::vector<double> v = s->lat_ms;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5))]; };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        double sum = 0.0;
+        for (double x : v) sum += x;
+        out->mean_ms = sum / (double)v.size();
+        const double span = std::chrono::duration<double>(s->t_last - s->t_first).count();
+        out->circuits_per_s = span > 0 ? (double)s->completed / span : 0.0;
+    }
+    out->hbm_budget = s->budget;
+    out->hbm_used = s->used;
+    return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""GPU: the continuous-batching server (srv_*).
+
+Each served result is checked against the oracle; a circuit served alone and served in a mix
+of others must give bit-identical amplitudes (same path, plan and kernels); admission must keep
+the device footprint under the HBM budget; waits are bounded.
+"""
+import numpy as np
+import pytest
+
+import syc_inputs as si
+
+pytestmark = pytest.mark.gpu
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1910_09534_gb300 import build
+    build.build()
+    import paper_1910_09534_gb300 as p
+    return p
+
+
+def mixed_circuits():
+    # packed (n <= 14 with small_n = 14) and stream-path circuits of several depths
+    out = []
+    for i, (n, d) in enumerate([(10, 8), (12, 12), (14, 10), (15, 9), (17, 14), (11, 20), (16, 8), (13, 16),
+                                (18, 10), (14, 8)]):
+        out.append(si.sycamore_circuit(si.near_square_grid(n), d, seed=100 + i))
+    return out
+
+
+def serve(pkg, circuits, together, **opts):
+    srv = pkg.srv_create(**opts)
+    outs = [np.zeros(1 << c.n_qubits, dtype=np.complex64) for c in circuits]
+    res = [None] * len(circuits)
+    try:
+        if together:
+            tickets = [pkg.srv_submit(srv, c.n_qubits, pkg.gates_array(c), o) for c, o in zip(circuits, outs)]
+            for i, t in enumerate(tickets):
+                res[i] = pkg.srv_wait(srv, t, timeout_ms=60000)
+        else:
+            for i, (c, o) in enumerate(zip(circuits, outs)):
+                res[i] = pkg.srv_wait(srv, pkg.srv_submit(srv, c.n_qubits, pkg.gates_array(c), o), 60000)
+        stats = pkg.srv_stats(srv)
+    finally:
+        pkg.srv_destroy(srv)
+    return outs, res, stats
+
+
+def test_served_results_match_oracle_and_alone_equals_mix(pkg, oracle_mod):
+    circuits = mixed_circuits()
+    mix, res_mix, stats = serve(pkg, circuits, True, small_n=14, slots=3)
+    alone, res_alone, _ = serve(pkg, circuits, False, small_n=14, slots=3)
+    assert stats["completed"] == len(circuits) and stats["p99_ms"] >= stats["p50_ms"] > 0
+    for c, a, b, (norm, s2, lat) in zip(circuits, mix, alone, res_mix):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
+        want = oracle_mod.run_circuit(c)
+        assert np.linalg.norm(a.astype(np.complex128) - want) <= TOL_FP32
+        onorm, os2, _ = oracle_mod.reduce(want)
+        assert abs(norm - 1.0) < 1e-5 and abs(s2 - os2) < 1e-3 * os2 and lat > 0
+
+
+def test_admission_respects_hbm_budget(pkg, oracle_mod):
+    # 20-qubit states are 8 MiB; a 20 MiB budget admits two at a time
+    circuits = [si.sycamore_circuit(si.near_square_grid(20), 6, seed=s) for s in range(5)]
+    outs, res, stats = serve(pkg, circuits, True, small_n=16, slots=4, hbm_budget=20 << 20)
+    assert stats["completed"] == 5 and stats["hbm_used"] == 0
+    for c, o in zip(circuits, outs):
+        assert np.linalg.norm(o.astype(np.complex128) - oracle_mod.run_circuit(c)) <= TOL_FP32
+    srv = pkg.srv_create(hbm_budget=20 << 20)
+    try:
+        big = si.sycamore_circuit(si.near_square_grid(22), 2, seed=1)  # 32 MiB > budget
+        with pytest.raises(pkg.SimError) as e:
+            pkg.srv_submit(srv, big.n_qubits, pkg.gates_array(big))
+        assert e.value.code == pkg.SIM_E_BUSY
+        assert pkg.srv_stats(srv)["rejected"] == 1
+    finally:
+        pkg.srv_destroy(srv)
+
+
+def test_wait_is_bounded_and_errors_are_reported(pkg):
+    srv = pkg.srv_create(small_n=12)
+    try:
+        c = si.sycamore_circuit(si.near_square_grid(24), 20, seed=3)
+        t = pkg.srv_submit(srv, c.n_qubits, pkg.gates_array(c))
+        try:
+            pkg.srv_wait(srv, t, timeout_ms=0)  # a 24-qubit, 20-cycle circuit is not done at once
+            timed_out = False
+        except pkg.SimError as e:
+            assert e.code == pkg.SIM_E_TIMEOUT
+            timed_out = True
+        assert timed_out
+        norm, _, _ = pkg.srv_wait(srv, t, timeout_ms=60000)
+        assert abs(norm - 1) < 1e-5
+        with pytest.raises(pkg.SimError):
+            pkg.srv_wait(srv, t, timeout_ms=10)  # forgotten after a successful wait
+        bad = pkg.gates_array([(si.FSIM, 0, 0, 1.0, 0.5)])
+        with pytest.raises(pkg.SimError) as e:
+            pkg.srv_submit(srv, 4, bad)
+        assert e.value.code == pkg.SIM_E_INVAL
+    finally:
+        pkg.srv_destroy(srv)
+
+
+def test_packed_path_many_small_circuits(pkg, oracle_mod):
+    circuits = [si.sycamore_circuit(si.near_square_grid(12 + (i % 5)), 6 + (i % 7), seed=i) for i in range(300)]
+    outs, res, stats = serve(pkg, circuits, True, small_n=20)
+    assert stats["completed"] == 300
+    for i in range(0, 300, 37):
+        assert np.linalg.norm(outs[i].astype(np.complex128) - oracle_mod.run_circuit(circuits[i])) <= TOL_FP32
