@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--kmax", type=int, default=4)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "tf32x3", "tf32"],
+                    help="arithmetic of blocks with k >= 5 (narrower blocks always run FP32 on CUDA cores)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
@@ -200,8 +202,11 @@ def run_ours(args):
     _, stream_ptr = pkg.sim_state_ptr(h)
     stream = torch.cuda.ExternalStream(stream_ptr)
 
+    prec = {"fp32": pkg.SIM_FP32, "fp16x3": pkg.SIM_FP16X3, "tf32x3": pkg.SIM_TF32X3,
+            "tf32": pkg.SIM_TF32}[args.precision]
+
     def step():
-        plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
+        plan = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec)
         pkg.sim_reset(h)
         pkg.sim_apply_plan(h, plan)
         out = pkg.sim_reduce(h)
@@ -250,7 +255,7 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax)
+        plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
         pkg.sim_reset(h)
         pkg.sim_apply_plan(h, plan)
         pkg.sim_amplitudes(h, out=out)
@@ -281,10 +286,12 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"{args.precision} (k>=5 blocks; f32 accumulate)",
         "data": "synthetic (seeded random Sycamore-pattern circuit; state from |0...0>)",
         "config": {"workload": args.workload, "n_qubits": n, "cycles": si.WORKLOADS[args.workload]["cycles"],
-                   "gates": circ.n_gates, "kmax": args.kmax, "fused_blocks": nblocks,
+                   "gates": circ.n_gates, "kmax": args.kmax, "precision": args.precision,
+                   "fused_blocks": nblocks,
                    "state_bytes": amps * 8, "l2": "state 8 GiB > 129 MB L2: no flush needed",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
         "pass_updates_per_s": pass_updates,

@@ -51,8 +51,9 @@ extern "C" {
 #define SIM_FP32 0   /* CUDA-core FP32 FMA (the default) */
 #define SIM_TF32 1   /* tensor cores, TF32 inputs, FP32 accumulate (~1e-3 relative per pass) */
 #define SIM_TF32X3 2 /* tensor cores, 3xTF32 split (hi*hi + hi*lo + lo*hi), ~FP32 accuracy */
-/* The tensor-core modes apply to blocks with k >= 4 whose targets are all >= physical bit 4;
- * other blocks run on CUDA cores in FP32. */
+#define SIM_FP16X3 3 /* tensor cores, 3xFP16 split with a per-tile power-of-two scale, ~FP32 accuracy */
+/* The tensor-core modes apply to blocks with k >= 5 (measured: for k <= 4 the CUDA-core FP32
+ * kernel is faster); narrower blocks run on CUDA cores in FP32. */
 
 /* ---- amplitude dtypes for readout/load ------------------------------- */
 #define SIM_C64 0    /* complex64: 2 x float32, interleaved */
@@ -123,7 +124,7 @@ int sim_reset(sim_t *h, uint64_t basis);
  * For every group of 2^k amplitudes that differ only in the target bits,
  * psi_g <- M psi_g, in place.  k in 1..6; targets: k distinct logical qubits, all
  * local (SIM_E_NONLOCAL otherwise); matrix: 2^k x 2^k complex128, row-major,
- * bit j of its index <-> targets[j]; precision: SIM_FP32, SIM_TF32 or SIM_TF32X3
+ * bit j of its index <-> targets[j]; precision: SIM_FP32, SIM_TF32, SIM_TF32X3 or SIM_FP16X3
  * (Sect. 5 suggests GPUs for the matrix-vector products; the tensor-core modes
  * treat a tile of 16 groups as a real GEMM with [[Re M, -Im M], [Im M, Re M]]).
  * Asynchronous. */
@@ -225,7 +226,7 @@ typedef struct sim_plan_s sim_plan_t;
 
 typedef struct sim_plan_opts {
     int kmax;      /* largest block width, 1..6 (Sect. 5 uses k_max = 5) */
-    int precision; /* arithmetic for the blocks' apply: SIM_FP32, SIM_TF32, SIM_TF32X3 */
+    int precision; /* arithmetic for the blocks' apply: SIM_FP32, SIM_TF32, SIM_TF32X3, SIM_FP16X3 */
     int reserved[6];
 } sim_plan_opts;
 
@@ -308,7 +309,7 @@ typedef struct srv_opts {
     int small_n;         /* circuits with n <= small_n are packed (0 = 20, max 24) */
     int max_pack;        /* most circuits per packed launch (0 = 1024) */
     int kmax;            /* aggregation width (0 = 5 for n <= 24, else 4) */
-    int precision;       /* circuits above small_n: SIM_FP32, SIM_TF32 or SIM_TF32X3 */
+    int precision;       /* circuits above small_n: SIM_FP32, SIM_TF32, SIM_TF32X3, SIM_FP16X3 */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
     int reserved[8];
 } srv_opts;

@@ -604,7 +604,7 @@ int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int preci
     return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, precision, h->stream);
 }
 
-bool precision_ok(int precision) { return precision == SIM_FP32 || precision == SIM_TF32 || precision == SIM_TF32X3; }
+bool precision_ok(int precision) { return precision >= SIM_FP32 && precision <= SIM_FP16X3; }
 
 }  // namespace sycsim
 

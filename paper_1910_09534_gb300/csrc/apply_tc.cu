@@ -14,10 +14,19 @@
 // The B fragments (R^T, permuted as above, split hi/lo for the 3xTF32 mode) are arranged
 // fragment-major on the host and staged once per CTA in shared memory.
 //
+// Accumulation: chaining many MMAs through one FP32 accumulator was measured to shrink the
+// state's norm systematically (the tensor cores' internal accumulation is not round-to-nearest):
+// -4e-7 per k = 5 pass.  So each k-step's main product starts from a zero accumulator and is
+// added with round-to-nearest FP32 adds, and the small hi*lo + lo*hi corrections (2^-11 of
+// the main term) are chained in a second accumulator.  Outputs are produced in chunks of at
+// most 4 n-tiles to bound the accumulator registers.
+//
 // Modes: TF32 (one MMA per piece; TF32 keeps 10 mantissa bits, so ~1e-3 relative error per
 // pass) and 3xTF32 (a = a_hi + a_lo with both parts TF32; hi*hi + hi*lo + lo*hi recovers
-// ~FP32 accuracy).  Used when every target is >= bit 4, so the 16 groups of a tile are 16
-// consecutive amplitude indices and each member load is a 64-byte run per 8 groups.
+// ~FP32 accuracy); see also 3xFP16 below.  Used for k >= 5.  A tile's 16 groups are 16
+// consecutive group indices; with every target >= bit 4 each member load is a 64-byte run
+// per 8 groups, with low targets the runs interleave members instead.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +41,7 @@ namespace {
 struct MmaGeom {
     float2 *psi;
     uint64_t n_mtiles;      // tiles of 16 groups: 2^(nbits - k - 4)
-    int tpos[kMaxK];        // ascending target bits (all >= 4)
+    int tpos[kMaxK];        // ascending target bits
     uint64_t moff[64];      // offset of member j
     const uint32_t *bfrag;  // [split][kstep][ntile][lane][2] TF32 bit patterns
 };
@@ -73,6 +82,7 @@ __global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma(MmaGeom g)
     constexpr int D = 1 << K;
     constexpr int KS = D / 4;  // k-steps (4 input members each)
     constexpr int NT = D / 4;  // n-tiles (4 output members each)
+    constexpr int NC = NT < 4 ? NT : 4;  // n-tiles per output chunk (bounds the accumulators)
     constexpr int NSPLIT = kSplit ? 2 : 1;
     constexpr int FRAG_WORDS = KS * NT * 64;
     extern __shared__ uint32_t sb[];
@@ -92,36 +102,217 @@ __global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma(MmaGeom g)
             x0[s] = __ldcs(p0 + g.moff[4 * s + t]);
             x1[s] = __ldcs(p1 + g.moff[4 * s + t]);
         }
-        float acc[NT][4];
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += NC) {
+            float acc[NC][4], cor[NC][4];
 #pragma unroll
-        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+            for (int n = 0; n < NC; ++n)
 #pragma unroll
-        for (int s = 0; s < KS; ++s) {
-            const float av[4] = {x0[s].x, x1[s].x, x0[s].y, x1[s].y};
-            uint32_t ahi[4], alo[4];
+                for (int i = 0; i < 4; ++i) acc[n][i] = cor[n][i] = 0.f;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                ahi[i] = to_tf32(av[i]);
-                if constexpr (kSplit) alo[i] = to_tf32(av[i] - __uint_as_float(ahi[i]));
-            }
+            for (int s = 0; s < KS; ++s) {
+                const float av[4] = {x0[s].x, x1[s].x, x0[s].y, x1[s].y};
+                uint32_t ahi[4], alo[4];
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const uint2 bh = *reinterpret_cast<const uint2 *>(sb + ((s * NT + n) * 32 + lane) * 2);
-                mma_tf32(acc[n], ahi, bh.x, bh.y);
-                if constexpr (kSplit) {
-                    const uint2 bl =
-                        *reinterpret_cast<const uint2 *>(sb + FRAG_WORDS + ((s * NT + n) * 32 + lane) * 2);
-                    mma_tf32(acc[n], ahi, bl.x, bl.y);
-                    mma_tf32(acc[n], alo, bh.x, bh.y);
+                for (int i = 0; i < 4; ++i) {
+                    ahi[i] = to_tf32(av[i]);
+                    if constexpr (kSplit) alo[i] = to_tf32(av[i] - __uint_as_float(ahi[i]));
+                }
+#pragma unroll
+                for (int n = 0; n < NC; ++n) {
+                    const int nt = c0 + n;
+                    const uint2 bh = *reinterpret_cast<const uint2 *>(sb + ((s * NT + nt) * 32 + lane) * 2);
+                    float part[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_tf32(part, ahi, bh.x, bh.y);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[n][i] += part[i];
+                    if constexpr (kSplit) {
+                        const uint2 bl = *reinterpret_cast<const uint2 *>(
+                            sb + FRAG_WORDS + ((s * NT + nt) * 32 + lane) * 2);
+                        mma_tf32(cor[n], ahi, bl.x, bl.y);
+                        mma_tf32(cor[n], alo, bh.x, bh.y);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            __stcs(p0 + g.moff[4 * n + t], make_float2(acc[n][0], acc[n][1]));
-            __stcs(p1 + g.moff[4 * n + t], make_float2(acc[n][2], acc[n][3]));
+            for (int n = 0; n < NC; ++n) {
+                const int nt = c0 + n;
+                __stcs(p0 + g.moff[4 * nt + t], make_float2(acc[n][0] + cor[n][0], acc[n][1] + cor[n][1]));
+                __stcs(p1 + g.moff[4 * nt + t], make_float2(acc[n][2] + cor[n][2], acc[n][3] + cor[n][3]));
+            }
         }
     }
+}
+
+// ---- 3xFP16: the same GEMM with m16n8k16 FP16 MMAs (twice the TF32 rate on this GPU) ----
+// K steps of 16 reals = 8 members: columns 2t, 2t+1 are (Re, Im) of member 8s + t, columns
+// 2t+8, 2t+9 of member 8s + 4 + t, so each A register is one packed half2 amplitude.  The
+// state is scaled per warp tile by a power of two so that its largest component sits near
+// 2^14 (FP16 keeps it normal), split as hi = fp16(a), lo = fp16(a - hi); the products
+// hi*hi + hi*lo + lo*hi are accumulated in FP32 and the scale is removed exactly.
+__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void split_half2(float re, float im, uint32_t &hi, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(re, im);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma_f16x3(MmaGeom g)
+{
+    constexpr int D = 1 << K;
+    constexpr int KS = D / 8;  // k-steps (8 input members each)
+    constexpr int NT = D / 4;  // n-tiles (4 output members each)
+    constexpr int NC = NT < 4 ? NT : 4;
+    constexpr int FRAG_WORDS = KS * NT * 64;
+    extern __shared__ uint32_t sb[];
+    for (int i = threadIdx.x; i < 2 * FRAG_WORDS; i += blockDim.x) sb[i] = g.bfrag[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, gid = lane >> 2, t = lane & 3;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t mt = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; mt < g.n_mtiles;
+         mt += nw) {
+        const uint64_t grp = mt * 16 + gid;
+        float2 *p0 = g.psi + insert_zero_bits_t(grp, g.tpos, K);
+        float2 *p1 = g.psi + insert_zero_bits_t(grp + 8, g.tpos, K);
+        float2 x0[2 * KS], x1[2 * KS];  // members 8s + t (even index) and 8s + 4 + t (odd index)
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            x0[2 * s] = __ldcs(p0 + g.moff[8 * s + t]);
+            x0[2 * s + 1] = __ldcs(p0 + g.moff[8 * s + 4 + t]);
+            x1[2 * s] = __ldcs(p1 + g.moff[8 * s + t]);
+            x1[2 * s + 1] = __ldcs(p1 + g.moff[8 * s + 4 + t]);
+        }
+        float amax = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2 * KS; ++i)
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(x0[i].x), fabsf(x0[i].y)), fmaxf(fabsf(x1[i].x), fabsf(x1[i].y))));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        int e = 0;
+        frexpf(amax, &e);                       // amax < 2^e
+        const int sh = amax > 0.f ? max(-100, min(100, 14 - e)) : 0;  // largest component < 2^14
+        const float sc = ldexpf(1.f, sh), inv = ldexpf(1.f, -sh);
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += NC) {
+            float acc[NC][4], cor[NC][4];
+#pragma unroll
+            for (int n = 0; n < NC; ++n)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[n][i] = cor[n][i] = 0.f;
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                uint32_t ahi[4], alo[4];
+                split_half2(x0[2 * s].x * sc, x0[2 * s].y * sc, ahi[0], alo[0]);
+                split_half2(x1[2 * s].x * sc, x1[2 * s].y * sc, ahi[1], alo[1]);
+                split_half2(x0[2 * s + 1].x * sc, x0[2 * s + 1].y * sc, ahi[2], alo[2]);
+                split_half2(x1[2 * s + 1].x * sc, x1[2 * s + 1].y * sc, ahi[3], alo[3]);
+#pragma unroll
+                for (int n = 0; n < NC; ++n) {
+                    const int nt = c0 + n;
+                    const uint2 bh = *reinterpret_cast<const uint2 *>(sb + ((s * NT + nt) * 32 + lane) * 2);
+                    const uint2 bl =
+                        *reinterpret_cast<const uint2 *>(sb + FRAG_WORDS + ((s * NT + nt) * 32 + lane) * 2);
+                    float part[4] = {0.f, 0.f, 0.f, 0.f};
+                    mma_f16(part, ahi, bh.x, bh.y);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[n][i] += part[i];
+                    mma_f16(cor[n], ahi, bl.x, bl.y);
+                    mma_f16(cor[n], alo, bh.x, bh.y);
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < NC; ++n) {
+                const int nt = c0 + n;
+                __stcs(p0 + g.moff[4 * nt + t],
+                       make_float2((acc[n][0] + cor[n][0]) * inv, (acc[n][1] + cor[n][1]) * inv));
+                __stcs(p1 + g.moff[4 * nt + t],
+                       make_float2((acc[n][2] + cor[n][2]) * inv, (acc[n][3] + cor[n][3]) * inv));
+            }
+        }
+    }
+}
+
+uint32_t pack_half2(float lo, float hi)
+{
+    const __half a = __float2half_rn(lo), b = __float2half_rn(hi);
+    uint16_t ua, ub;
+    std::memcpy(&ua, &a, 2);
+    std::memcpy(&ub, &b, 2);
+    return (uint32_t)ua | ((uint32_t)ub << 16);
+}
+
+template <int K>
+int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
+                   uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+{
+    constexpr int D = 1 << K, KS = D / 8, NT = D / 4;
+    constexpr int FRAG_WORDS = KS * NT * 64;
+    // B fragment (k rows 2t, 2t+1 | 2t+8, 2t+9; n column gid) as half2 (Re-input, Im-input)
+    // of input member 8s + t (b0) and 8s + 4 + t (b1) for output member 4n + gid/2.
+    for (int s = 0; s < KS; s++)
+        for (int n = 0; n < NT; n++)
+            for (int lane = 0; lane < 32; lane++) {
+                const int gid = lane >> 2, t = lane & 3;
+                const int o = 4 * n + (gid >> 1);
+                const bool out_im = gid & 1;
+                const size_t idx = ((size_t)(s * NT + n) * 32 + lane) * 2;
+                for (int j = 0; j < 2; j++) {
+                    const float2 m = mat[o * D + 8 * s + 4 * j + t];
+                    const float re_in = out_im ? m.y : m.x;   // coefficient of Re x
+                    const float im_in = out_im ? m.x : -m.y;  // coefficient of Im x
+                    const uint32_t hi = pack_half2(re_in, im_in);
+                    __half hr, hm;
+                    const uint16_t lo16 = (uint16_t)(hi & 0xffffu), hi16 = (uint16_t)(hi >> 16);
+                    std::memcpy(&hr, &lo16, 2);
+                    std::memcpy(&hm, &hi16, 2);
+                    h_frag[idx + j] = hi;
+                    h_frag[FRAG_WORDS + idx + j] =
+                        pack_half2(re_in - __half2float(hr), im_in - __half2float(hm));
+                }
+            }
+    const size_t bytes = sizeof(uint32_t) * 2 * FRAG_WORDS;
+    if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
+    MmaGeom g{};
+    g.psi = psi;
+    g.n_mtiles = 1ull << (nbits - K - 4);
+    for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];
+    for (int j = 0; j < D; j++) {
+        uint64_t o = 0;
+        for (int b = 0; b < K; b++)
+            if ((j >> b) & 1) o += 1ull << tpos[b];
+        g.moff[j] = o;
+    }
+    g.bfrag = d_frag;
+    auto kern = k_apply_mma_f16x3<K>;
+    static int occ = 0, sms = 0;
+    if (!occ) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (bytes > 48 * 1024 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+            return -1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, bytes) != cudaSuccess || occ < 1)
+            occ = 1;
+    }
+    const uint64_t need = (g.n_mtiles + 7) / 8;
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    kern<<<(unsigned)grid, 256, bytes, st>>>(g);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Round an FP32 value to TF32 (nearest, ties away from zero, as cvt.rna), host side.
@@ -204,7 +395,10 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
 
 }  // namespace
 
-bool tc_eligible(int nbits, int k, const int *tpos) { return k >= 4 && k <= 6 && tpos[0] >= 4 && nbits >= k + 4; }
+// Measured on GB300 (n = 30): for k = 4 the CUDA-core FP32 kernel is faster than every
+// tensor-core mode (2.8 ms vs >= 3.6 ms per pass), for k >= 5 the tensor cores win (3xFP16 k = 5:
+// 3.3 ms vs 7.0 ms).  Any target set works: groups map to amplitude offsets by bit insertion.
+bool tc_eligible(int nbits, int k, const int *) { return k >= 5 && k <= 6 && nbits >= k + 4; }
 
 int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                     int precision, cudaStream_t st)
@@ -215,6 +409,14 @@ int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, co
     uint32_t *hf = h->h_frag + sim_s::kFragWords * slot;
     uint32_t *df = h->d_frag + sim_s::kFragWords * slot;
     cudaEvent_t ev = h->frag_ev[slot];
+    if (precision == SIM_FP16X3) {
+        switch (k) {
+        case 4: return launch_f16x3_k<4>(psi, nbits, tpos, mat, st, hf, df, ev);
+        case 5: return launch_f16x3_k<5>(psi, nbits, tpos, mat, st, hf, df, ev);
+        case 6: return launch_f16x3_k<6>(psi, nbits, tpos, mat, st, hf, df, ev);
+        default: return -1;
+        }
+    }
     const bool split = precision == SIM_TF32X3;
     switch (k) {
     case 4: return split ? launch_mma_k<4, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)

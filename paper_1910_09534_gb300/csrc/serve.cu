@@ -480,7 +480,7 @@ int srv_create(const srv_opts *opts, srv_t **out)
     if (s->o.small_n <= 0) s->o.small_n = 20;
     if (s->o.max_pack <= 0) s->o.max_pack = 1024;
     if (s->o.slots > 32 || s->o.small_n > 24 || s->o.max_pack > 65536 ||
-        (s->o.precision != SIM_FP32 && s->o.precision != SIM_TF32 && s->o.precision != SIM_TF32X3)) {
+        !precision_ok(s->o.precision)) {
         delete s;
         return srv_fail(nullptr, SIM_E_INVAL, "srv_create: slots <= 32, small_n <= 24, max_pack <= 65536");
     }
