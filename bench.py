@@ -10,6 +10,12 @@ flush is needed between steps.
 metric value = 2^n * (original gates) * steps / device time   ("gate" amplitude updates/s)
 pass updates = 2^n * (fused blocks) * steps / device time      (roofline basis, 16 B/amp/pass)
 
+Default arithmetic: blocks of up to 5 qubits; 5-qubit blocks on tensor cores in 3xFP16 split
+precision (FP32 accumulate, error vs the oracle ~1e-6 on this workload), narrower blocks in
+FP32 on CUDA cores.  The same JSON line also reports the FP32-only path (blocks of up to 4
+qubits) and a bounded serving run (200 random circuits, n in 16..30, served concurrently vs one
+at a time).
+
 --impl reference times the CPU oracle (complex128, gate by gate) on the host cores on a bounded
 sample of the same workload (the first gates of the circuit on the full 30-qubit state).
 Multi-GPU (torchrun): independent replicas, one circuit per rank (seed = rank), no collective
@@ -40,16 +46,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--kmax", type=int, default=4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "tf32x3", "tf32"],
+    ap.add_argument("--kmax", type=int, default=5)
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "tf32x3", "tf32"],
                     help="arithmetic of blocks with k >= 5 (narrower blocks always run FP32 on CUDA cores)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
+    ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-circuits", type=int, default=200)
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
-                         "apply k=4 (targets >= bit 5, then mixed), k=2, a high-bit permutation and a "
-                         "reduction, each twice, then exit; meant to run under ncu")
+                         "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16, "
+                         "high then mixed targets), a high-bit permutation and a reduction, each "
+                         "twice, then exit; meant to run under ncu")
     return ap.parse_args()
 
 
@@ -142,6 +152,45 @@ def cpu_baseline(circ, sample_gates: int, steps: int = 1):
             "sample": f"first {sample_gates} of {circ.n_gates} gates of {circ.name} on the full "
                       f"2^{circ.n_qubits} complex128 state, {steps} run(s)",
             "seconds": sum(times)}
+
+
+def serving_run(count: int, device: int):
+    """Serve `count` random circuits (qubits uniform in 16..30, 8..20 cycles) all submitted at
+    once, and run the same circuits one at a time through sim_*; report circuits/s and the
+    served latency distribution."""
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+
+    stream = si.serving_stream(count, base_seed=1000, rate_hz=1e9)
+    circs = [c for _, c in stream]
+    gates = [pkg.gates_array(c) for c in circs]
+    import torch
+    torch.cuda.synchronize()
+    handles = {}
+    t0 = time.perf_counter()
+    for c, g in zip(circs, gates):
+        h = handles.get(c.n_qubits)
+        if h is None:
+            h = handles[c.n_qubits] = pkg.sim_create(c.n_qubits, 0, device=device)
+        p = pkg.sim_plan_create(c.n_qubits, g, kmax=5 if c.n_qubits <= 24 else 4)
+        pkg.sim_reset(h)
+        pkg.sim_apply_plan(h, p)
+        pkg.sim_reduce(h)
+        pkg.sim_plan_destroy(p)
+    seq_s = time.perf_counter() - t0
+    for h in handles.values():
+        pkg.sim_destroy(h)
+    srv = pkg.srv_create(device=device)
+    t0 = time.perf_counter()
+    tickets = [pkg.srv_submit(srv, c.n_qubits, g) for c, g in zip(circs, gates)]
+    for t in tickets:
+        pkg.srv_wait(srv, t)
+    served_s = time.perf_counter() - t0
+    st = pkg.srv_stats(srv)
+    pkg.srv_destroy(srv)
+    return {"circuits": count, "qubits": "16..30", "cycles": "8..20", "arrivals": "all at t=0 (saturated)",
+            "circuits_per_s": count / served_s, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "one_at_a_time_circuits_per_s": count / seq_s, "arithmetic": "fp32"}
 
 
 def run_reference(args):
@@ -247,6 +296,37 @@ def run_ours(args):
     value = total_updates / (ms_max / 1e3)
     pass_updates = float(amps) * nblocks * args.steps * ws / (ms_max / 1e3)
 
+    # the FP32-only path on the same state and timing method (blocks of <= 4 qubits)
+    fp32_path = None
+    if not args.no_fp32_path:
+        def step32():
+            plan = pkg.sim_plan_create(n, gates, kmax=4, precision=pkg.SIM_FP32)
+            pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plan)
+            out = pkg.sim_reduce(h)
+            nb = pkg.sim_plan_info(plan)[0]
+            pkg.sim_plan_destroy(plan)
+            return out, nb
+        for _ in range(args.warmup):
+            step32()
+        pkg.sim_profile_enable(h, True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            (n32, s32, _), nb32 = step32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        c32, a32_ms, a32_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
+        pkg.sim_profile_enable(h, False)
+        peak32, _ = measured_peaks()
+        ach32 = a32_bytes / (a32_ms / 1e3) / 1e9
+        fp32_path = {"value": float(amps) * circ.n_gates * args.steps / (ms32 / 1e3), "unit": UNIT,
+                     "ms_per_step": ms32 / args.steps, "kmax": 4, "fused_blocks": nb32,
+                     "norm": n32, "porter_thomas_2n_sum_p2": s32,
+                     "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak32, "unit": "GB/s",
+                                  "frac": ach32 / peak32, "launches": c32}}
+
     # end to end through the public API with host buffers: gate records from pinned host
     # memory in, all 2^n amplitudes out to pinned host memory, every step
     gates_pinned = pkg.pinned_array(gates.size, dtype=pkg._native.GATE_DTYPE)
@@ -299,7 +379,7 @@ def run_ours(args):
         "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
-                     "kernel": "fused apply (k_apply_direct/k_apply_tiled)",
+                     "kernel": "fused apply, all launches (k_apply_mma_f16x3 / k_apply_reg / k_apply_direct)",
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "launches": a_n, "avg_launch_ms": a_ms / max(a_n, 1)},
         "breakdown_ms_per_step": {"apply": a_ms / args.steps, "reduce": r_ms / args.steps,
@@ -308,6 +388,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps},
         "clocks": clk.summary(),
     }
+    if fp32_path:
+        line["fp32_path"] = fp32_path
+    if ws == 1 and not args.no_serving:
+        line["serving"] = serving_run(args.serving_circuits, local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(circ, args.cpu_sample_gates)
     _ = sanity
@@ -328,6 +412,10 @@ def kernel_case():
         u = si.random_unitary(len(t), 1)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u)
+    for t in ([12, 13, 14, 15, 16], [1, 3, 14, 20, 25]):
+        u = si.random_unitary(len(t), 2)
+        for _ in range(2):
+            pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3)
     perm = list(range(n))
     for a, b in ((25, 10), (26, 11), (27, 12)):
         perm[a], perm[b] = b, a

@@ -288,7 +288,10 @@ int sim_phases_info(const sim_phases_t *ph, int *n_phases, int *total_blocks);
 int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **plan);
 
 /* Run every phase in order (sim_run_phase); the handle's sets must be the
- * phases' sets.  Asynchronous. */
+ * phases' sets.  On a device-resident handle created with slice_bits > 0, each
+ * phase first permutes its sliced set into the top slice_bits physical bits
+ * (sim_permute), so the gates of the phase act on local bits only -- the
+ * in-memory analogue of Sect. 4's reorganisation between phases.  Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
 /* ---- serving: many circuits on one GPU (no counterpart in the paper) --------

@@ -369,6 +369,30 @@ int sim_run_phases(sim_t *h, const sim_phases_t *ph)
                 return fail(h, SIM_E_INVAL, "sim_run_phases: sliced sets differ from the handle's");
     }
     for (size_t i = 0; i < ph->plans.size(); i++) {
+        if (h->store == SIM_STORE_DEVICE && h->s > 0) {
+            // Resident state with sliced top bits (Sect. 4 in device memory): before the phase,
+            // move the phase's sliced set into the top slice_bits physical bits, exchanging them
+            // with whatever qubits hold those bits (an in-place bit permutation).
+            if (ph->s != h->s) return fail(h, SIM_E_INVAL, "sim_run_phases: slice_bits differ");
+            const int *X = ph->set_of[i] == 0 ? ph->set_a : ph->set_b;
+            int perm[kMaxQubits];
+            for (int q = 0; q < h->n; q++) perm[q] = h->bit_of[q];
+            bool moved = false;
+            for (int j = 0; j < ph->s; j++) {
+                const int want = h->n - h->s + j, q = X[j];
+                if (perm[q] == want) continue;
+                int other = -1;
+                for (int r = 0; r < h->n; r++)
+                    if (perm[r] == want) other = r;
+                perm[other] = perm[q];
+                perm[q] = want;
+                moved = true;
+            }
+            if (moved) {
+                const int rc = sim_permute(h, perm);
+                if (rc != SIM_OK) return rc;
+            }
+        }
         const int rc = sim_run_phase(h, ph->set_of[i], ph->plans[i]);
         if (rc != SIM_OK) return rc;
     }

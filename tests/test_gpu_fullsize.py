@@ -1,0 +1,109 @@
+"""GPU at the workloads' full sizes.
+
+* 30 qubits, 20 cycles (5x6 grid; 8 GiB complex64 state): every amplitude against the oracle
+  (complex128, gate by gate, all host cores), for the FP32 plan (k <= 4) and the tensor-core
+  plan (k <= 5, 3xFP16).  Bound ||psi - psi_oracle||_2 <= 1e-5.
+* 33 qubits (6x6 minus three corners; 64 GiB) held as 8 slices over the 3 top bits, run as
+  alternating phases with in-place bit permutations between them (Sect. 4 in device memory):
+  norm and Porter-Thomas, no oracle fits.  Its 28-qubit sub-lattice circuit (4x7, same depth)
+  goes through the same sliced machinery and is compared with the oracle; the measured error of
+  each arithmetic mode is printed.
+* Small sliced-phase case against the oracle, and the layout moves it makes.
+"""
+import numpy as np
+import pytest
+
+import syc_inputs as si
+
+pytestmark = pytest.mark.gpu
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1910_09534_gb300 import build
+    build.build()
+    import paper_1910_09534_gb300 as p
+    return p
+
+
+def chunked_err(got64, want128, chunk=1 << 26):
+    s = 0.0
+    for a in range(0, want128.size, chunk):
+        d = got64[a:a + chunk].astype(np.complex128) - want128[a:a + chunk]
+        s += float(np.vdot(d, d).real)
+    return s ** 0.5
+
+
+def run_sliced_phases(pkg, circ, s, precision, kmax):
+    n = circ.n_qubits
+    set_a, set_b = list(range(s)), list(range(n - s, n))
+    ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=kmax, precision=precision)
+    h = pkg.sim_create(n, s)
+    try:
+        pkg.sim_profile_enable(h, True)
+        pkg.sim_run_phases(h, ph)
+        perms = pkg.sim_profile_read(h, pkg.SIM_PROF_PERMUTE)[0]
+        pkg.sim_profile_enable(h, False)
+        out = pkg.sim_amplitudes(h)
+        red = pkg.sim_reduce(h)
+        nph = pkg.sim_phases_info(ph)[0]
+    finally:
+        pkg.sim_destroy(h)
+        pkg.sim_phases_destroy(ph)
+    return out, red, perms, nph
+
+
+def test_resident_sliced_phases_match_oracle(pkg, oracle_mod):
+    circ = si.sycamore_circuit(si.Grid(4, 5), cycles=12, seed=6)
+    out, (norm, _, _), perms, nph = run_sliced_phases(pkg, circ, 3, pkg.SIM_FP32, 4)
+    assert nph >= 2 and perms >= nph - 1  # every phase change moves the sliced set to the top bits
+    assert np.linalg.norm(out.astype(np.complex128) - oracle_mod.run_circuit(circ)) <= TOL_FP32
+
+
+@pytest.mark.slow
+def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
+    circ = si.workload_circuit("syc30_5x6_d20", seed=0)
+    n = circ.n_qubits
+    results = {}
+    h = pkg.sim_create(n)
+    try:
+        for name, kmax, prec in (("fp32_k4", 4, pkg.SIM_FP32), ("fp16x3_k5", 5, pkg.SIM_FP16X3)):
+            plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=kmax, precision=prec)
+            pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plan)
+            pkg.sim_plan_destroy(plan)
+            results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
+    finally:
+        pkg.sim_destroy(h)
+    import os
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    want = oracle_mod.run_circuit(circ)
+    onorm, os2, _ = oracle_mod.reduce(want)
+    assert abs(onorm - 1) < 1e-10 and abs(os2 - 2) < 0.05  # Porter-Thomas at 30 qubits
+    for name, (amps, (norm, s2, xeb)) in results.items():
+        err = chunked_err(amps, want)
+        print(f"30q {name}: ||psi - psi_oracle||_2 = {err:.3e}, norm {norm:.9f}, 2^n sum p^2 {s2:.5f}")
+        assert err <= TOL_FP32, (name, err)
+        assert abs(s2 - os2) < 1e-3
+
+
+@pytest.mark.slow
+def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
+    # 33 qubits, 8 slices over 3 top bits, phases with permutations: norm and Porter-Thomas
+    circ33 = si.workload_circuit("syc33_6x6m3_d20", seed=0)
+    _, (norm, s2, _), perms, nph = run_sliced_phases(pkg, circ33, 3, pkg.SIM_FP16X3, 5)
+    print(f"33q sliced: {nph} phases, {perms} permutation passes, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}")
+    assert abs(norm - 1) < 2e-5 and abs(s2 - 2) < 0.05
+    # 28-qubit sub-lattice (4x7, 20 cycles) through the same machinery, every mode vs oracle
+    circ28 = si.workload_circuit("syc28_4x7_d20", seed=0)
+    import os
+    oracle_mod.set_threads(os.cpu_count() or 1)
+    want = oracle_mod.run_circuit(circ28)
+    bounds = {"fp32": 1e-5, "fp16x3": 1e-5, "tf32x3": 1e-5, "tf32": 5e-2}
+    for name, prec, kmax in (("fp32", pkg.SIM_FP32, 4), ("fp16x3", pkg.SIM_FP16X3, 5),
+                             ("tf32x3", pkg.SIM_TF32X3, 5), ("tf32", pkg.SIM_TF32, 5)):
+        out, _, _, _ = run_sliced_phases(pkg, circ28, 3, prec, kmax)
+        err = chunked_err(out, want)
+        print(f"28q sub-lattice {name} (kmax {kmax}): ||psi - psi_oracle||_2 = {err:.3e}")
+        assert err <= bounds[name], (name, err)
