@@ -121,6 +121,21 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time."""
+    return units_per_rank * world_size / seconds_max
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -288,13 +303,9 @@ def run_ours(args):
     r_n, r_ms, r_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_REDUCE)
     pkg.sim_profile_enable(h, False)
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_updates = float(amps) * circ.n_gates * args.steps * ws
-    value = total_updates / (ms_max / 1e3)
-    pass_updates = float(amps) * nblocks * args.steps * ws / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(float(amps) * circ.n_gates * args.steps, ws, ms_max / 1e3)
+    pass_updates = whole_job_rate(float(amps) * nblocks * args.steps, ws, ms_max / 1e3)
 
     # the FP32-only path on the same state and timing method (blocks of <= 4 qubits)
     fp32_path = None
@@ -341,11 +352,8 @@ def run_ours(args):
         pkg.sim_amplitudes(h, out=out)
         pkg.sim_plan_destroy(plan)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    et = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = float(amps) * circ.n_gates * args.e2e_steps * ws / max(float(et.item()), 1e-9)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = whole_job_rate(float(amps) * circ.n_gates * args.e2e_steps, ws, max(e2e_s, 1e-9))
     matrix_bytes = 0
     plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
     for i in range(pkg.sim_plan_info(plan)[0]):
