@@ -74,7 +74,15 @@ __device__ __forceinline__ uint64_t insert_zero_bits_t(uint64_t x, const int *po
     return x;
 }
 
-constexpr int mma_min_blocks(int k) { return k <= 5 ? 2 : 1; }
+// Tuning constants (overridable at build time): CTAs per SM each width is compiled for, and
+// the n-tiles per output chunk.
+#ifndef SYCSIM_MMA_MINB5
+#define SYCSIM_MMA_MINB5 3
+#endif
+#ifndef SYCSIM_MMA_NC
+#define SYCSIM_MMA_NC 2
+#endif
+constexpr int mma_min_blocks(int k) { return k <= 4 ? 2 : (k == 5 ? SYCSIM_MMA_MINB5 : 1); }
 
 template <int K, bool kSplit>
 __global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma(MmaGeom g)
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma(MmaGeom g)
     constexpr int D = 1 << K;
     constexpr int KS = D / 4;  // k-steps (4 input members each)
     constexpr int NT = D / 4;  // n-tiles (4 output members each)
-    constexpr int NC = NT < 4 ? NT : 4;  // n-tiles per output chunk (bounds the accumulators)
+    constexpr int NC = NT < SYCSIM_MMA_NC ? NT : SYCSIM_MMA_NC;  // n-tiles per output chunk
     constexpr int NSPLIT = kSplit ? 2 : 1;
     constexpr int FRAG_WORDS = KS * NT * 64;
     extern __shared__ uint32_t sb[];
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(256, mma_min_blocks(K)) k_apply_mma_f16x3(MmaG
     constexpr int D = 1 << K;
     constexpr int KS = D / 8;  // k-steps (8 input members each)
     constexpr int NT = D / 4;  // n-tiles (4 output members each)
-    constexpr int NC = NT < 4 ? NT : 4;
+    constexpr int NC = NT < SYCSIM_MMA_NC ? NT : SYCSIM_MMA_NC;
     constexpr int FRAG_WORDS = KS * NT * 64;
     extern __shared__ uint32_t sb[];
     for (int i = threadIdx.x; i < 2 * FRAG_WORDS; i += blockDim.x) sb[i] = g.bfrag[i];
