@@ -569,6 +569,15 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st)
 {
+    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k)) {
+        const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
+        const int rc = launch_apply_tcgen05(h, psi, nbits, k, tpos, mat, st);
+        prof_end(h, ps, st);
+        if (rc != 0)
+            return fail(h, SIM_E_CUDA, "apply (tcgen05): launch failed: %s",
+                        cudaGetErrorString(cudaGetLastError()));
+        return SIM_OK;
+    }
     if (precision != SIM_FP32 && tc_eligible(nbits, k, tpos)) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
         const int rc = launch_apply_tc(h, psi, nbits, k, tpos, mat, precision, st);
@@ -604,7 +613,7 @@ int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int preci
     return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, precision, h->stream);
 }
 
-bool precision_ok(int precision) { return precision >= SIM_FP32 && precision <= SIM_FP16X3; }
+bool precision_ok(int precision) { return precision >= SIM_FP32 && precision <= SIM_FP16X3_TMEM; }
 
 }  // namespace sycsim
 

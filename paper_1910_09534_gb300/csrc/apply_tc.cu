@@ -417,7 +417,7 @@ int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, co
     uint32_t *hf = h->h_frag + sim_s::kFragWords * slot;
     uint32_t *df = h->d_frag + sim_s::kFragWords * slot;
     cudaEvent_t ev = h->frag_ev[slot];
-    if (precision == SIM_FP16X3) {
+    if (precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM) {
         switch (k) {
         case 4: return launch_f16x3_k<4>(psi, nbits, tpos, mat, st, hf, df, ev);
         case 5: return launch_f16x3_k<5>(psi, nbits, tpos, mat, st, hf, df, ev);

@@ -54,6 +54,8 @@ struct sim_s {
     cudaEvent_t mat6_ev[kMat6Slots] = {};
     int mat6_next = 0;
 
+    int *d_errflag = nullptr;  // set by kernels whose bounded waits ran out
+
     // tensor-core B fragments (fragment-major R^T, hi/lo) go through a device ring
     static constexpr int kFragSlots = 8;
     static constexpr int kFragWords = 2 * 16 * 16 * 64;  // k = 6, split: 128 KiB
@@ -142,6 +144,11 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
 int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);
 
 bool precision_ok(int precision);
+
+// ---- apply_tcgen05.cu (5th-generation tensor cores, TMEM) ----
+bool tcgen05_eligible(int nbits, int k);
+int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                         cudaStream_t st);
 
 // ---- apply_tc.cu (tensor cores) ----
 bool tc_eligible(int nbits, int k, const int *tpos);

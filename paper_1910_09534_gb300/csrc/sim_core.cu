@@ -94,6 +94,7 @@ static void release(sim_t *h)
     for (auto &e : h->mat6_ev)
         if (e) cudaEventDestroy(e);
     if (h->d_frag) cudaFree(h->d_frag);
+    if (h->d_errflag) cudaFree(h->d_errflag);
     if (h->h_frag) cudaFreeHost(h->h_frag);
     for (auto &e : h->frag_ev)
         if (e) cudaEventDestroy(e);
@@ -195,6 +196,8 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
                              cudaHostAllocDefault),
                SIM_E_NOMEM_HOST);
     for (auto &e : h->frag_ev) CREATE_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), SIM_E_CUDA);
+    CREATE_TRY(cudaMalloc(&h->d_errflag, sizeof(int)), SIM_E_NOMEM_DEV);
+    CREATE_TRY(cudaMemset(h->d_errflag, 0, sizeof(int)), SIM_E_CUDA);
 #undef CREATE_TRY
 
     int rc = sim_reset(h, 0);
@@ -250,6 +253,18 @@ int sim_reset(sim_t *h, uint64_t basis)
                           cudaGetErrorString(cudaGetLastError()));
 }
 
+// After the handle's streams are idle: report (and clear) a kernel's bounded wait running out.
+static int check_device_error(sim_t *h)
+{
+    int flag = 0;
+    SIM_CUDA_TRY(h, cudaMemcpy(&flag, h->d_errflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        SIM_CUDA_TRY(h, cudaMemset(h->d_errflag, 0, sizeof(int)));
+        return fail(h, SIM_E_TIMEOUT, "a tensor-core apply gave up waiting for its MMAs; state is invalid");
+    }
+    return SIM_OK;
+}
+
 int sim_sync(sim_t *h, int timeout_ms)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_sync: NULL handle");
@@ -258,14 +273,14 @@ int sim_sync(sim_t *h, int timeout_ms)
         if (h->st_in) SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
         SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         if (h->st_out) SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_out));
-        return SIM_OK;
+        return check_device_error(h);
     }
     auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(h->stream);
         if (e == cudaSuccess && h->st_in) e = cudaStreamQuery(h->st_in);
         if (e == cudaSuccess && h->st_out) e = cudaStreamQuery(h->st_out);
-        if (e == cudaSuccess) return SIM_OK;
+        if (e == cudaSuccess) return check_device_error(h);
         if (e != cudaErrorNotReady)
             return fail(h, SIM_E_CUDA, "sim_sync: %s", cudaGetErrorString(e));
         auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(

@@ -1,4 +1,4 @@
-"""GPU: tensor-core apply (SIM_TF32, SIM_TF32X3, SIM_FP16X3) against the oracle.
+"""GPU: tensor-core apply (SIM_TF32, SIM_TF32X3, SIM_FP16X3, SIM_FP16X3_TMEM) against the oracle.
 
 Tolerances (unit-norm states): 3xTF32 and 3xFP16 (per-tile power-of-two scale) recover ~21-22
 mantissa bits, so they are held to the FP32 bound 1e-5; plain TF32 keeps 10 mantissa bits (2^-11 ~ 4.9e-4 relative per rounded input), and
@@ -12,7 +12,7 @@ import syc_inputs as si
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "tf32": 5e-3}
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "fp16x3_tmem": 1e-5, "tf32": 5e-3}
 
 
 @pytest.fixture(scope="module")
@@ -24,10 +24,11 @@ def pkg():
 
 
 def mode(pkg, name):
-    return {"fp32": pkg.SIM_FP32, "tf32": pkg.SIM_TF32, "tf32x3": pkg.SIM_TF32X3, "fp16x3": pkg.SIM_FP16X3}[name]
+    return {"fp32": pkg.SIM_FP32, "tf32": pkg.SIM_TF32, "tf32x3": pkg.SIM_TF32X3, "fp16x3": pkg.SIM_FP16X3,
+            "fp16x3_tmem": pkg.SIM_FP16X3_TMEM}[name]
 
 
-@pytest.mark.parametrize("name", ["tf32x3", "fp16x3", "tf32"])
+@pytest.mark.parametrize("name", ["tf32x3", "fp16x3", "fp16x3_tmem", "tf32"])
 @pytest.mark.parametrize("n,targets", [(14, [6, 13, 9, 4, 10]), (20, [19, 5, 12, 8, 16]), (16, [4, 5, 6, 7, 8, 9]),
                                        (21, [20, 6, 14, 9, 17, 11]), (12, [0, 1, 2, 3, 4]), (15, [3, 0, 9, 1, 14]),
                                        (18, [0, 1, 2, 3, 4, 5]), (17, [16, 2, 8, 0, 11, 5]), (9, [0, 2, 4, 6, 8]),
@@ -51,7 +52,7 @@ def test_tensor_core_apply_matches_oracle(pkg, oracle_mod, name, n, targets):
 
 
 @pytest.mark.parametrize("name,kmax,tol", [("tf32x3", 5, 1e-5), ("tf32x3", 6, 1e-5), ("fp16x3", 5, 1e-5),
-                                          ("fp16x3", 6, 1e-5), ("tf32", 5, 3e-2)])
+                                          ("fp16x3", 6, 1e-5), ("fp16x3_tmem", 5, 1e-5), ("tf32", 5, 3e-2)])
 def test_tensor_core_circuit_matches_oracle(pkg, oracle_mod, name, kmax, tol):
     circ = si.sycamore_circuit(si.Grid(4, 5), cycles=14, seed=8)
     plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax, precision=mode(pkg, name))
@@ -86,3 +87,23 @@ def test_fp16x3_tiny_and_zero_amplitudes(pkg, oracle_mod):
     assert np.linalg.norm(got - want) <= 1e-5
     tiny = np.abs(want) < 1e-15
     assert np.all(np.abs(got[tiny] - want[tiny]) <= 1e-5 * np.abs(want[tiny]) + 1e-30)
+
+
+@pytest.mark.parametrize("n,targets", [(12, [4, 5, 6, 7]), (13, [0, 12, 3, 7, 9]), (22, [21, 5, 13, 8, 17]),
+                                       (16, [15, 8, 4, 11])])
+def test_tcgen05_tiles_match_oracle(pkg, oracle_mod, n, targets):
+    # the tcgen05 path needs >= 2^(k+7) amplitudes (128-group tiles); k = 4 and 5
+    k = len(targets)
+    u = si.random_unitary(k, seed=n + 3 * k)
+    psi = si.random_state(n, seed=2 * n)
+    h = pkg.sim_create(n)
+    try:
+        pkg.sim_load_amplitudes(h, psi)
+        pkg.sim_apply_fused(h, targets, u, precision=pkg.SIM_FP16X3_TMEM)
+        pkg.sim_sync(h)
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_destroy(h)
+    want = psi.astype(np.complex128)
+    oracle_mod.apply_kq(want, targets, u)
+    assert np.linalg.norm(got - want) <= 1e-5
