@@ -10,9 +10,9 @@ flush is needed between steps.
 metric value = 2^n * (original gates) * steps / device time   ("gate" amplitude updates/s)
 pass updates = 2^n * (fused blocks) * steps / device time      (roofline basis, 16 B/amp/pass)
 
-Default arithmetic: blocks of up to 5 qubits; 5-qubit blocks on tensor cores in 3xFP16 split
-precision (FP32 accumulate, error vs the oracle ~1e-6 on this workload), narrower blocks in
-FP32 on CUDA cores.  The same JSON line also reports the FP32-only path (blocks of up to 4
+Default configuration: chosen by the library's autotuner before the timed region among the
+block widths and the FP32-equivalent arithmetic (FP32 CUDA cores; 3xFP16 or 3xTF32 tensor-core
+splits for 5- and 6-qubit blocks, FP32 accumulate, error vs the oracle ~1e-6 on this workload).  The same JSON line also reports the FP32-only path (blocks of up to 4
 qubits) and a bounded serving run (200 random circuits, n in 16..30, served concurrently vs one
 at a time).
 
@@ -46,9 +46,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--kmax", type=int, default=5)
+    ap.add_argument("--kmax", type=int, default=0,
+                    help="block width; 0 = autotune (sim_autotune, FP32-equivalent arithmetic only), "
+                         "measured before the timed region")
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "tf32x3", "tf32"],
-                    help="arithmetic of blocks with k >= 5 (narrower blocks always run FP32 on CUDA cores)")
+                    help="arithmetic of blocks with k >= 5 when --kmax is given (narrower blocks always "
+                         "run FP32 on CUDA cores)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
@@ -268,6 +271,14 @@ def run_ours(args):
 
     prec = {"fp32": pkg.SIM_FP32, "fp16x3": pkg.SIM_FP16X3, "tf32x3": pkg.SIM_TF32X3,
             "tf32": pkg.SIM_TF32}[args.precision]
+    tuned = None
+    if args.kmax == 0:
+        kmax, prec, tune_ms = pkg.sim_autotune(h, gates, pkg.SIM_TUNE_FP32_EQUIVALENT)
+        args.kmax = kmax
+        args.precision = {pkg.SIM_FP32: "fp32", pkg.SIM_FP16X3: "fp16x3", pkg.SIM_TF32X3: "tf32x3",
+                          pkg.SIM_TF32: "tf32"}[prec]
+        tuned = {"by": "sim_autotune (FP32-equivalent arithmetic)", "kmax": kmax,
+                 "precision": args.precision, "tuning_run_ms": tune_ms}
 
     def step():
         plan = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec)
@@ -383,6 +394,7 @@ def run_ours(args):
                    "state_bytes": amps * 8, "l2": "state 8 GiB > 129 MB L2: no flush needed",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
         "pass_updates_per_s": pass_updates,
+        "autotune": tuned,
         "gpu_launches": launches,
         "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -251,6 +251,20 @@ int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *mat
 /* Apply every block of the plan in order (each as sim_apply_fused).  Async. */
 int sim_apply_plan(sim_t *h, const sim_plan_t *p);
 
+/* Autotuner (not in the paper; Sect. 5 fixes k_max = 5 for its CPUs): plans the
+ * given circuit with every candidate block width (k_max 3..6) and arithmetic the
+ * accuracy class allows -- SIM_TUNE_FP32: FP32 only; SIM_TUNE_FP32_EQUIVALENT:
+ * also the split tensor-core modes (3xFP16, 3xTF32); SIM_TUNE_ANY: also plain
+ * TF32 -- runs each from |0...0> on h's state (twice; the second run is timed
+ * with CUDA events) and writes the fastest options to *best (and its time in
+ * ms to *best_ms, may be NULL).  Synchronous; leaves h in |0...0>.  Needs a
+ * device-resident handle without sliced bits. */
+#define SIM_TUNE_FP32 0
+#define SIM_TUNE_FP32_EQUIVALENT 1
+#define SIM_TUNE_ANY 2
+int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim_plan_opts *best,
+                 double *best_ms);
+
 /* ---- secondary storage: slices and phases (Sect. 4) ------------------------ */
 
 /* Move slice `value` of sliced set `set` (0 = A, 1 = B; value's bit i is the value

@@ -118,6 +118,8 @@ _SIGS = {
     "sim_plan_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "sim_apply_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "sim_stream_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                         ctypes.c_int]),
     "sim_slot_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -356,6 +358,20 @@ def sim_plan_block(p, i: int):
 
 def sim_apply_plan(h, p) -> None:
     _check(lib().sim_apply_plan(h, p), h)
+
+
+SIM_TUNE_FP32 = 0
+SIM_TUNE_FP32_EQUIVALENT = 1
+SIM_TUNE_ANY = 2
+
+
+def sim_autotune(h, gates: np.ndarray, accuracy: int = SIM_TUNE_FP32_EQUIVALENT):
+    """(kmax, precision, ms) of the fastest plan for this circuit on h's device."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    o = PlanOpts()
+    ms = ctypes.c_double()
+    _check(lib().sim_autotune(h, int(g.size), _ptr(g), accuracy, ctypes.byref(o), ctypes.byref(ms)), h)
+    return o.kmax, o.precision, ms.value
 
 
 def sim_stream_slice(h, set_: int, value: int, direction: int, slot: int) -> None:

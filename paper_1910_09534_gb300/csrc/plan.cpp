@@ -240,6 +240,61 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
     return SIM_OK;
 }
 
+// ---- autotuner: measure candidate widths and arithmetic on the device ----
+
+int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim_plan_opts *best,
+                 double *best_ms)
+{
+    if (!h || !best) return fail(h, SIM_E_INVAL, "sim_autotune: NULL argument");
+    if (h->store != SIM_STORE_DEVICE || h->s != 0)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_autotune: needs a device-resident, unsliced handle");
+    if (accuracy != SIM_TUNE_FP32 && accuracy != SIM_TUNE_FP32_EQUIVALENT && accuracy != SIM_TUNE_ANY)
+        return fail(h, SIM_E_INVAL, "sim_autotune: accuracy class %d", accuracy);
+    std::vector<int> precs = {SIM_FP32};
+    if (accuracy != SIM_TUNE_FP32) {
+        precs.push_back(SIM_FP16X3);
+        precs.push_back(SIM_TF32X3);
+    }
+    if (accuracy == SIM_TUNE_ANY) precs.push_back(SIM_TF32);
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaEvent_t e0, e1;
+    SIM_CUDA_TRY(h, cudaEventCreate(&e0));
+    SIM_CUDA_TRY(h, cudaEventCreate(&e1));
+    double best_t = 1e300;
+    sim_plan_opts pick{};
+    int rc = SIM_OK;
+    for (int prec : precs)
+        for (int kmax = 3; kmax <= kMaxK && rc == SIM_OK; kmax++) {
+            if (prec != SIM_FP32 && kmax < 5) continue;  // tensor cores only take blocks of k >= 5
+            sim_plan_opts o{};
+            o.kmax = kmax;
+            o.precision = prec;
+            sim_plan_t *p = nullptr;
+            rc = sim_plan_create(h->n, n_gates, gates, &o, &p);
+            if (rc != SIM_OK) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == SIM_OK; rep++) {  // first run warms up
+                rc = sim_reset(h, 0);
+                if (rc == SIM_OK) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+                if (rc == SIM_OK) rc = sim_apply_plan(h, p);
+                if (rc == SIM_OK) rc = cudaEventRecord(e1, h->stream) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+                if (rc == SIM_OK) rc = cudaEventSynchronize(e1) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+                if (rc == SIM_OK) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            sim_plan_destroy(p);
+            if (rc == SIM_OK && ms < best_t) {
+                best_t = ms;
+                pick = o;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SIM_OK) return rc;
+    *best = pick;
+    if (best_ms) *best_ms = best_t;
+    return sim_reset(h, 0);
+}
+
 // ---- phases over two alternating sliced sets (Sect. 4) ----
 
 int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,

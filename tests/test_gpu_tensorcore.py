@@ -107,3 +107,25 @@ def test_tcgen05_tiles_match_oracle(pkg, oracle_mod, n, targets):
     want = psi.astype(np.complex128)
     oracle_mod.apply_kq(want, targets, u)
     assert np.linalg.norm(got - want) <= 1e-5
+
+
+@pytest.mark.parametrize("accuracy", ["fp32", "fp32_equivalent"])
+def test_autotune_picks_a_valid_plan(pkg, oracle_mod, accuracy):
+    circ = si.sycamore_circuit(si.Grid(4, 5), cycles=10, seed=12)
+    acc = {"fp32": pkg.SIM_TUNE_FP32, "fp32_equivalent": pkg.SIM_TUNE_FP32_EQUIVALENT}[accuracy]
+    h = pkg.sim_create(circ.n_qubits)
+    try:
+        kmax, prec, ms = pkg.sim_autotune(h, pkg.gates_array(circ), acc)
+        assert 3 <= kmax <= 6 and ms > 0
+        if accuracy == "fp32":
+            assert prec == pkg.SIM_FP32
+        else:
+            assert prec in (pkg.SIM_FP32, pkg.SIM_FP16X3, pkg.SIM_TF32X3)
+        assert pkg.sim_amplitudes(h, count=2)[0] == 1  # left in |0...0>
+        plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax, precision=prec)
+        pkg.sim_apply_plan(h, plan)
+        pkg.sim_plan_destroy(plan)
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_destroy(h)
+    assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= 1e-5
