@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--kmax", type=int, default=0,
                     help="block width; 0 = autotune (sim_autotune, FP32-equivalent arithmetic only), "
                          "measured before the timed region")
-    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "tf32x3", "tf32"],
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "fp16x3_tmem", "tf32x3", "tf32"],
                     help="arithmetic of blocks with k >= 5 when --kmax is given (narrower blocks always "
                          "run FP32 on CUDA cores)")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -60,9 +60,9 @@ def parse():
     ap.add_argument("--serving-circuits", type=int, default=200)
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
-                         "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16, "
-                         "high then mixed targets), a high-bit permutation and a reduction, each "
-                         "twice, then exit; meant to run under ncu")
+                         "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
+                         "mma.sync, high then mixed targets; with tcgen05, 256- then 128-group tiles), a "
+                         "high-bit permutation and a reduction, each twice, then exit; meant to run under ncu")
     return ap.parse_args()
 
 
@@ -269,14 +269,14 @@ def run_ours(args):
     _, stream_ptr = pkg.sim_state_ptr(h)
     stream = torch.cuda.ExternalStream(stream_ptr)
 
-    prec = {"fp32": pkg.SIM_FP32, "fp16x3": pkg.SIM_FP16X3, "tf32x3": pkg.SIM_TF32X3,
-            "tf32": pkg.SIM_TF32}[args.precision]
+    prec = {"fp32": pkg.SIM_FP32, "fp16x3": pkg.SIM_FP16X3, "fp16x3_tmem": pkg.SIM_FP16X3_TMEM,
+            "tf32x3": pkg.SIM_TF32X3, "tf32": pkg.SIM_TF32}[args.precision]
     tuned = None
     if args.kmax == 0:
         kmax, prec, tune_ms = pkg.sim_autotune(h, gates, pkg.SIM_TUNE_FP32_EQUIVALENT)
         args.kmax = kmax
-        args.precision = {pkg.SIM_FP32: "fp32", pkg.SIM_FP16X3: "fp16x3", pkg.SIM_TF32X3: "tf32x3",
-                          pkg.SIM_TF32: "tf32"}[prec]
+        args.precision = {pkg.SIM_FP32: "fp32", pkg.SIM_FP16X3: "fp16x3", pkg.SIM_FP16X3_TMEM: "fp16x3_tmem",
+                          pkg.SIM_TF32X3: "tf32x3", pkg.SIM_TF32: "tf32"}[prec]
         tuned = {"by": "sim_autotune (FP32-equivalent arithmetic)", "kmax": kmax,
                  "precision": args.precision, "tuning_run_ms": tune_ms}
 
@@ -399,7 +399,10 @@ def run_ours(args):
         "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
-                     "kernel": "fused apply, all launches (k_apply_mma_f16x3 / k_apply_reg / k_apply_direct)",
+                     "kernel": "fused apply, all launches (" + {
+                         "fp16x3_tmem": "k_apply_tcgen05 / k_apply_mma_f16x3 / k_apply_reg / k_apply_direct",
+                         "fp32": "k_apply_reg / k_apply_direct / k_apply_tiled"}.get(
+                         args.precision, "k_apply_mma_f16x3 / k_apply_reg / k_apply_direct") + ")",
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "launches": a_n, "avg_launch_ms": a_ms / max(a_n, 1)},
         "breakdown_ms_per_step": {"apply": a_ms / args.steps, "reduce": r_ms / args.steps,
@@ -436,6 +439,11 @@ def kernel_case():
         u = si.random_unitary(len(t), 2)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3)
+    # tcgen05: 256-group tiles stored from registers, then 128-group tiles with bulk stores
+    for t in ([12, 13, 14, 15, 16], [4, 9, 14, 20, 25]):
+        u = si.random_unitary(len(t), 2)
+        for _ in range(2):
+            pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3_TMEM)
     perm = list(range(n))
     for a, b in ((25, 10), (26, 11), (27, 12)):
         perm[a], perm[b] = b, a

@@ -52,10 +52,11 @@ extern "C" {
 #define SIM_TF32 1   /* tensor cores, TF32 inputs, FP32 accumulate (~1e-3 relative per pass) */
 #define SIM_TF32X3 2 /* tensor cores, 3xTF32 split (hi*hi + hi*lo + lo*hi), ~FP32 accuracy */
 #define SIM_FP16X3 3 /* tensor cores, 3xFP16 split with a per-tile power-of-two scale, ~FP32 accuracy */
-#define SIM_FP16X3_TMEM 4 /* 3xFP16 on tcgen05.mma with tensor-memory accumulators (k = 4, 5 and at
-                             least 2^(k+7) amplitudes; other blocks as SIM_FP16X3) */
-/* The tensor-core modes apply to blocks with k >= 5 (measured: for k <= 4 the CUDA-core FP32
- * kernel is faster); narrower blocks run on CUDA cores in FP32. */
+#define SIM_FP16X3_TMEM 4 /* 3xFP16 on tcgen05.mma with tensor-memory accumulators, operands moved
+                             by bulk copies (k = 4 or 5, no target below bit 4, at least 2^(k+7)
+                             amplitudes); other blocks as SIM_FP16X3 */
+/* The mma.sync tensor-core modes apply to blocks with k >= 5 (measured: for k <= 4 the CUDA-core
+ * FP32 kernel is faster); narrower blocks run on CUDA cores in FP32. */
 
 /* ---- amplitude dtypes for readout/load ------------------------------- */
 #define SIM_C64 0    /* complex64: 2 x float32, interleaved */
@@ -254,7 +255,7 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p);
 /* Autotuner (not in the paper; Sect. 5 fixes k_max = 5 for its CPUs): plans the
  * given circuit with every candidate block width (k_max 3..6) and arithmetic the
  * accuracy class allows -- SIM_TUNE_FP32: FP32 only; SIM_TUNE_FP32_EQUIVALENT:
- * also the split tensor-core modes (3xFP16, 3xTF32); SIM_TUNE_ANY: also plain
+ * also the split tensor-core modes (3xFP16 on mma.sync and on tcgen05, 3xTF32); SIM_TUNE_ANY: also plain
  * TF32 -- runs each from |0...0> on h's state (twice; the second run is timed
  * with CUDA events) and writes the fastest options to *best (and its time in
  * ms to *best_ms, may be NULL).  Synchronous; leaves h in |0...0>.  Needs a

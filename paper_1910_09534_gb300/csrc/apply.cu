@@ -569,7 +569,7 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st)
 {
-    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k)) {
+    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k, tpos)) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
         const int rc = launch_apply_tcgen05(h, psi, nbits, k, tpos, mat, st);
         prof_end(h, ps, st);

@@ -2,25 +2,41 @@
 // (tcgen05.mma, accumulators in tensor memory), 3xFP16 split precision, k = 4 and 5.
 //
 // Same real-embedded GEMM as apply_tc.cu (W^T = V^T . R^T with R = [[Re M, -Im M],
-// [Im M, Re M]]), as one tcgen05.mma M = 128 (groups) x N = 2^(k+1) (output reals) x K = 16
-// per step:
-//  * thread t of the 128-thread CTA owns row t = one group: it loads the group's 2^k
-//    amplitudes, scales them by a power of two (largest component < 2^14, so FP16 keeps them
-//    normal), splits hi = fp16(a), lo = fp16(a - hi) and writes both to shared memory in the
-//    K-major core-matrix layout (8 rows x 16 bytes per core matrix; 128 B between the two K
-//    halves of a 16-wide slice, 256 B between 8-row groups);
-//  * K (input reals) is interleaved: column 2m + p is part p (Re, Im) of member m, so a row's
-//    16-byte chunk is four consecutive members; N likewise, so a row of the result is the
-//    group's outputs (Re, Im) in member order;
-//  * one thread issues the MMAs: the main products hi*hi chained through one TMEM accumulator,
-//    the corrections hi*lo + lo*hi through a second (their truncation bias is 2^-11 smaller),
-//    then commits them to an mbarrier;
-//  * while they run, every thread issues the loads of its next tile;
-//  * the epilogue reads both accumulators (tcgen05.ld 32x32b: warp w sees TMEM lanes
-//    32w..32w+31), adds them in FP32, removes the row's scale and stores the amplitudes.
-// R^T (hi, lo; FP16, the same core-matrix layout) is built on the host and staged in shared
-// memory once per CTA.  The wait on the mbarrier is bounded; on timeout the kernel records the
-// failure in an error word, stops, and still frees its tensor memory.
+// [Im M, Re M]]), as tcgen05.mma steps of M = 128 (groups) x N = 2^(k+1) (output reals) x
+// K = 16.  A tile is 128 consecutive groups: 2^(k+7) amplitudes whose addresses differ only in
+// the tile's free bits, the k targets and the 7 lowest other bits.  Those always include bits
+// 0..6, so a tile is at most 2^k runs of >= 128 contiguous amplitudes, moved by the bulk-copy
+// (TMA) engine into shared memory in address order.  Where bit 7 is not a target the runs are
+// only 1 KiB, and the kernel takes 256-group tiles (two M = 128 sub-tiles, row bit 7 = sub-tile)
+// so that every copy moves 2 KiB (measured: 1 KiB copies cap the kernel at ~74% of the 2 KiB
+// rate).
+//
+// One persistent CTA per SM, warp-specialised, tiles pipelined through a ring of S shared-memory
+// stages (one tile each, 128 x 2^k complex64):
+//  * warp 8 loads tile i into stage i % S with cp.async.bulk (a run per lane), completing on an
+//    mbarrier by byte count, as soon as the stage's previous tile has been drained;
+//  * converter warps 0-7: thread = (row, half of the members).  It reads its half-row (staging
+//    index = row bits | member bits in address order: no bank conflicts while no target is
+//    below bit 4), the two halves combine their maxima, and the row is scaled by a power of two
+//    (largest component < 2^14, so FP16 stays normal), split hi = fp16(a), lo = fp16(a - hi)
+//    and written in place as the MMA's A operand (K-major core matrices: 8 rows x 16 bytes;
+//    128 B between the two K halves of a 16-wide slice, 256 B between 8-row groups);
+//  * warp 9 (one thread) issues the MMAs: hi*hi chained through one TMEM accumulator, the
+//    corrections hi*lo + lo*hi through a second (their rounding is 2^-11 smaller), and commits
+//    them to the stage's mbarrier;
+//  * drainer warps 10-17 read both accumulators (tcgen05.ld 32x32b: warp w sees TMEM lanes
+//    32 (w % 4) ..), add them and undo the row's scale.  With a deep stage ring the amplitudes
+//    go back into the stage and the lanes of warp 10 store its runs with bulk copies; with the
+//    3-stage ring of 64 KiB tiles they are stored from registers (no target below bit 4: 16
+//    consecutive rows are 128 contiguous bytes), which frees the stage as soon as TMEM is read.
+// K (input reals) is interleaved, column 2m + p is part p (Re, Im) of member m, so a row's
+// 16-byte chunk is four consecutive members; N likewise.  R^T (hi, lo; FP16, core-matrix layout)
+// is built on the host and staged in shared memory once per CTA.  Two TMEM accumulator sets let
+// tile i + 1 be multiplied while tile i is drained.
+//
+// Every wait is bounded in time (%globaltimer): a timeout records the failure in an error word
+// and a shared abort flag that ends every role's loop; the CTA then waits for its bulk copies in
+// flight and frees its tensor memory before returning.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -32,16 +48,30 @@
 namespace sycsim {
 namespace {
 
-constexpr int kRows = 128;           // groups per tile = MMA M
-constexpr long kWaitLimit = 1L << 26;  // mbarrier polls before giving up (far above any MMA)
+#ifndef SYCSIM_TC5_RUN_LOG2_MAX
+#define SYCSIM_TC5_RUN_LOG2_MAX 8  // 2 KiB copies: measured fastest (1 KiB: -26%, 4 KiB: -9%)
+#endif
+
+constexpr int kRows = 128;                     // groups per tile = MMA M
+constexpr unsigned long long kWaitNs = 4000000000ull;  // 4 s: far above any legitimate wait
+constexpr int kConv = 256;                     // converter threads: warps 0-7
+constexpr int kLoadWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kDrain = 256;                    // drainer threads: warps 10-17
+constexpr int kThreadsTc5 = kConv + 64 + kDrain;
 
 struct Tc5Geom {
     float2 *psi;
-    uint64_t n_tiles;        // 2^(nbits - k - 7)
-    int tpos[kMaxK];
-    uint64_t moff[32];
+    uint64_t n_tiles;        // 2^(nbits - k - 7) / R2
+    int tpos[kMaxK];         // target bit positions, ascending
+    int run_log2;            // L: a tile is 2^(k+7+log2 R2-L) runs of 2^L contiguous amplitudes
+    uint64_t off_run[32];    // address offset of run c (c's bits deposited on the free bits >= L)
+    uint32_t midx[32];       // staging index of member m in row 0 (row r: midx[m] | ridx(r))
+    uint32_t ridx[8];        // staging-index bit of row bit j (bit 7: sub-tile)
+    uint64_t roff[8];        // address offset of row bit j
+    uint64_t moff[32];       // address offset of member m
     const uint32_t *bmat;    // R^T hi then lo, FP16 core-matrix layout, as 32-bit words
-    int *err;                // set to 1 if an MMA wait timed out
+    int *err;                // set to 1 if a wait timed out
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -60,18 +90,6 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t da, uint64_t 
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
         "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t done = 0;
-    for (long it = 0; it < kWaitLimit && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-    return done != 0;
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t ta, float (&v)[16])
@@ -98,41 +116,160 @@ __device__ __forceinline__ uint64_t insert_zero_bits_g(uint64_t x, const int *po
     return x;
 }
 
-// Shared memory: A hi | A lo (KS slices of 4 KiB each) | B hi | B lo (KS slices of N*32 B each).
-template <int K>
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return done;
+}
+
+// Wait for the phase of the given parity, the thread suspended in between polls; gives up after
+// kWaitNs or once another role has aborted.
+__device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity, 0)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try(bar, parity, 20000)) return true;
+        if (*abort_flag || global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// Wait for work this thread issued itself (copies, MMAs) to land, even after an abort.
+__device__ __forceinline__ void mbar_wait_own(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    while (!mbar_try(bar, parity, 20000) && global_ns() - t0 <= kWaitNs) {
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Named barrier over n threads that also ANDs a predicate across them.
+__device__ __forceinline__ bool bar_and(int id, int n, bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// A tile is R2 sub-tiles of 128 groups (row bit 7 = sub-tile), one MMA M = 128 each.
+__device__ __forceinline__ void bulk_store(void *dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+
+// Shared memory: S stages of one tile each (raw amplitudes, then A hi | A lo of each sub-tile in
+// place, then the results), then B hi | B lo (KS slices of N x 16 FP16 each).
+template <int K, int R2>
 struct Tc5Layout {
     static constexpr int D = 1 << K;
-    static constexpr int KS = 2 * D / 16;       // K slices of 16 reals
-    static constexpr int N = 2 * D;             // output reals
-    static constexpr int A_SLICE = kRows * 32;  // bytes
+    static constexpr int KS = 2 * D / 16;         // K slices of 16 reals
+    static constexpr int N = 2 * D;               // output reals
+    static constexpr int A_SLICE = kRows * 32;    // bytes
     static constexpr int B_SLICE = N * 32;
-    static constexpr int A_BYTES = KS * A_SLICE;
+    static constexpr int A_BYTES = KS * A_SLICE;  // one of hi, lo, one sub-tile
     static constexpr int B_BYTES = KS * B_SLICE;
-    static constexpr int SMEM = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int TMEM_COLS = 2 * N;     // main + corrections
+    static constexpr int SUB = kRows * D * 8;     // one sub-tile = 2 * A_BYTES
+    static constexpr int STAGE = R2 * SUB;
+    static constexpr int S = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;  // stages
+    static constexpr int SMEM = S * STAGE + 2 * B_BYTES;
+    static constexpr int TMEM_SUB = 2 * N;        // main + corrections of one sub-tile
+    static constexpr int TMEM_SET = R2 * TMEM_SUB;
+    static constexpr int TMEM_COLS = 2 * TMEM_SET;  // two sets
+    static_assert(SUB == 2 * A_BYTES, "A hi/lo fill a sub-tile");
+    static_assert(S >= 3, "stage ring too short");
+    // results leave through the stage with bulk stores when the ring is deep enough to hold a
+    // stage until its store has read it; the 3-stage ring (64 KiB tiles) stores from registers so
+    // that a stage is free as soon as its accumulators are read (measured: +20% there, -8% at 6+)
+    static constexpr bool BULK_STORE = S >= 6;
+    static_assert(TMEM_COLS <= 512, "tensor memory");
 };
 
 __device__ __forceinline__ uint32_t cm_off(int row, int k) { return (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2; }
 
-template <int K>
-__global__ void __launch_bounds__(kRows) k_apply_tcgen05(Tc5Geom g)
+// Per tile i (local index; stage s = i % S, stage phase (i / S) & 1; TMEM set i % 2, set phase
+// (i / 2) & 1):
+//   loader: wait drained[s] of tile i - S, load the runs into stage s (loaded[s] counts bytes);
+//   converters: wait loaded[s], read the rows, combine the halves' maxima (barrier), write A and
+//     the row scales in place, arrive full[s];
+//   MMA thread: wait full[s] and tmem_free of tile i - 2, multiply, commit to mma_done[s];
+//   drainers: wait mma_done[s] and full[s], read the row scales and TMEM, arrive tmem_free; then
+//     either write the results into stage s, barrier, warp 10 stores the runs and, once the store
+//     of tile i - 1 has read its stage, arrives drained for it; or arrive drained[s] at once and
+//     store the results from registers.
+// A stage is reloaded only after its drain, and a TMEM set reused only after its read, so no
+// barrier can run a phase ahead of a waiter that still has to see the previous phase.
+template <int K, int R2>
+__global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 {
-    using L = Tc5Layout<K>;
-    constexpr int D = L::D, KS = L::KS, N = L::N;
+    using L = Tc5Layout<K, R2>;
+    constexpr int D = L::D, KS = L::KS, N = L::N, S = L::S, H = D / 2;  // H members per thread
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *aHi = sm, *aLo = sm + L::A_BYTES;
-    uint8_t *bHi = sm + 2 * L::A_BYTES, *bLo = bHi + L::B_BYTES;
-    __shared__ __align__(8) uint64_t mbar;
+    uint8_t *bHi = sm + S * L::STAGE, *bLo = bHi + L::B_BYTES;
+    __shared__ __align__(8) uint64_t loaded[S], full[S], mma_done[S], drained[S], tmem_free[2];
+    __shared__ float row_inv[S][R2][kRows];
+    __shared__ float amax_part[R2][2][kRows];
+    __shared__ uint64_t tile_base[S];
     __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int n_runs = (R2 << (K + 7)) >> g.run_log2;
+    const uint32_t run_bytes = 8u << g.run_log2;
 
     {
         const uint32_t *src = g.bmat;
         uint32_t *dst = reinterpret_cast<uint32_t *>(bHi);
-        for (int i = tid; i < (2 * L::B_BYTES) / 4; i += kRows) dst[i] = src[i];
+        for (int i = tid; i < (2 * L::B_BYTES) / 4; i += blockDim.x) dst[i] = src[i];
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // B is read by the MMA unit
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar)) : "memory");
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&loaded[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[st])), "r"(kConv) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mma_done[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&drained[st])),
+                         "r"(L::BULK_STORE ? 1 : kDrain)
+                         : "memory");
+        }
+        for (int st = 0; st < 2; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&tmem_free[st])), "r"(kDrain)
+                         : "memory");
+        abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -144,88 +281,208 @@ __global__ void __launch_bounds__(kRows) k_apply_tcgen05(Tc5Geom g)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-
-    uint64_t tile = blockIdx.x;
-    float2 x[D];
-    auto load = [&](uint64_t t) {
-        const float2 *p = g.psi + insert_zero_bits_g(t * kRows + tid, g.tpos, K);
-#pragma unroll
-        for (int m = 0; m < D; ++m) x[m] = __ldcs(p + g.moff[m]);
+    volatile int *ab = &abort_flag;
+    auto give_up = [&]() {
+        *ab = 1;
+        atomicExch(g.err, 1);
     };
-    if (tile < g.n_tiles) load(tile);
-    uint32_t parity = 0;
-    bool ok = true;
-    for (; tile < g.n_tiles && ok; tile += gridDim.x, parity ^= 1) {
-        // scale, split and stage this row
-        float amax = 0.f;
+
+    if (warp < kLoadWarp) {
+        // ---------------- converters ----------------
+        const int row = tid & (kRows - 1), half = tid >> 7;
+        uint32_t rx = 0;
 #pragma unroll
-        for (int m = 0; m < D; ++m) amax = fmaxf(amax, fmaxf(fabsf(x[m].x), fabsf(x[m].y)));
-        int e = 0;
-        frexpf(amax, &e);
-        const int sh = amax > 0.f ? max(-100, min(100, 14 - e)) : 0;
-        const float sc = ldexpf(1.f, sh), inv = ldexpf(1.f, -sh);
-#pragma unroll
-        for (int c = 0; c < D / 4; ++c) {  // 16-byte chunk c = members 4c..4c+3 = K columns 8c..8c+7
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float re = x[4 * c + j].x * sc, im = x[4 * c + j].y * sc;
-                const __half2 h = __floats2half2_rn(re, im);
-                const float2 hf = __half22float2(h);
-                const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
-                hi[j] = *reinterpret_cast<const uint32_t *>(&h);
-                lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+        for (int j = 0; j < 7; ++j)
+            if ((row >> j) & 1) rx |= g.ridx[j];
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int st = i % S;
+            const bool ok = mbar_wait_abort(smem_u32(&loaded[st]), (i / S) & 1, ab);
+            if (!bar_and(1, kConv, ok)) {
+                give_up();
+                break;
             }
-            const uint32_t off = (c >> 1) * L::A_SLICE + cm_off(tid, 8 * (c & 1));
-            *reinterpret_cast<uint4 *>(aHi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4 *>(aLo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (tid == 0) {
+            uint8_t *stage = sm + st * L::STAGE;
+            float2 x[R2][H];
 #pragma unroll
-            for (int s = 0; s < KS; ++s)
-                umma_f16(tmem, umma_desc(smem_u32(aHi + s * L::A_SLICE)), umma_desc(smem_u32(bHi + s * L::B_SLICE)),
-                         idesc, s > 0);
+            for (int u = 0; u < R2; ++u) {
+                const uint32_t rxu = u ? rx | g.ridx[7] : rx;
+                float amax = 0.f;
 #pragma unroll
-            for (int s = 0; s < KS; ++s) {
-                umma_f16(tmem + N, umma_desc(smem_u32(aHi + s * L::A_SLICE)),
-                         umma_desc(smem_u32(bLo + s * L::B_SLICE)), idesc, s > 0);
-                umma_f16(tmem + N, umma_desc(smem_u32(aLo + s * L::A_SLICE)),
-                         umma_desc(smem_u32(bHi + s * L::B_SLICE)), idesc, 1);
+                for (int m = 0; m < H; ++m) {
+                    x[u][m] = *reinterpret_cast<const float2 *>(stage + 8 * (g.midx[H * half + m] | rxu));
+                    amax = fmaxf(amax, fmaxf(fabsf(x[u][m].x), fabsf(x[u][m].y)));
+                }
+                amax_part[u][half][row] = amax;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_u32(&mbar))
-                         : "memory");
-        }
-        // this tile's addresses, then the next tile's loads while the MMAs run
-        float2 *const dst = g.psi + insert_zero_bits_g(tile * kRows + tid, g.tpos, K);
-        const uint64_t next = tile + gridDim.x;
-        if (next < g.n_tiles) load(next);
-        ok = __syncthreads_and(mbar_wait(smem_u32(&mbar), parity));  // one decision for the CTA
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (!ok) {
-            if (tid == 0) atomicExch(g.err, 1);
-            break;
-        }
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            bar_sync(1, kConv);  // every row read before A overwrites the stage; both halves' maxima
 #pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            float a[16], b[16];
-            tmem_ld16(lane_base + c0, a);
-            tmem_ld16(lane_base + N + c0, b);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            for (int u = 0; u < R2; ++u) {
+                const float amax = fmaxf(amax_part[u][0][row], amax_part[u][1][row]);
+                int e = 0;
+                frexpf(amax, &e);
+                const int sh = amax > 0.f ? max(-100, min(100, 14 - e)) : 0;
+                const float sc = ldexpf(1.f, sh);
+                if (half == 0) row_inv[st][u][row] = ldexpf(1.f, -sh);
+                uint8_t *aHi = stage + u * L::SUB, *aLo = aHi + L::A_BYTES;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                __stcs(dst + g.moff[c0 / 2 + j],
-                       make_float2((a[2 * j] + b[2 * j]) * inv, (a[2 * j + 1] + b[2 * j + 1]) * inv));
+                for (int cc = 0; cc < H / 4; ++cc) {
+                    const int c = half * (H / 4) + cc;  // 4-member chunk of the row
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float re = x[u][4 * cc + j].x * sc, im = x[u][4 * cc + j].y * sc;
+                        const __half2 h = __floats2half2_rn(re, im);
+                        const float2 hf = __half22float2(h);
+                        const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+                        hi[j] = *reinterpret_cast<const uint32_t *>(&h);
+                        lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+                    }
+                    const uint32_t off = (c >> 1) * L::A_SLICE + cm_off(row, 8 * (c & 1));
+                    *reinterpret_cast<uint4 *>(aHi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(aLo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(smem_u32(&full[st]));
         }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();  // TMEM read and A staging consumed before the next tile reuses them
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    } else if (warp == kLoadWarp) {
+        // ---------------- bulk loads (one run per lane) ----------------
+        const int lane = tid & 31;
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int st = i % S;
+            const bool ok = i < (uint32_t)S || mbar_wait_abort(smem_u32(&drained[st]), (i / S - 1) & 1, ab);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) give_up();
+                break;
+            }
+            const uint64_t base = insert_zero_bits_g(tile * (kRows * R2), g.tpos, K);
+            const uint32_t bar = smem_u32(&loaded[st]);
+            if (lane == 0) {
+                tile_base[st] = base;
+                mbar_expect_tx(bar, L::STAGE);  // before any of the copies can complete
+            }
+            __syncwarp();
+            const uint32_t dst = smem_u32(sm + st * L::STAGE);
+            for (int c = lane; c < n_runs; c += 32) bulk_load(dst + c * run_bytes, g.psi + base + g.off_run[c], run_bytes, bar);
+        }
+        // no load may still be writing the stages when the CTA leaves (matters after an abort)
+        if (lane == 0)
+            for (uint32_t j = i > (uint32_t)S ? i - S : 0; j < i; ++j) mbar_wait_own(smem_u32(&loaded[j % S]), (j / S) & 1);
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if ((tid & 31) == 0) {
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+            uint32_t i = 0;
+            for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const int st = i % S;
+                if (!mbar_wait_abort(smem_u32(&full[st]), (i / S) & 1, ab) ||
+                    (i >= 2 && !mbar_wait_abort(smem_u32(&tmem_free[i & 1]), (i / 2 - 1) & 1, ab))) {
+                    give_up();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+                for (int u = 0; u < R2; ++u) {
+                    const uint8_t *aHi = sm + st * L::STAGE + u * L::SUB, *aLo = aHi + L::A_BYTES;
+                    const uint32_t acc = tmem + (i & 1) * L::TMEM_SET + u * L::TMEM_SUB;
+#pragma unroll
+                    for (int s = 0; s < KS; ++s)
+                        umma_f16(acc, umma_desc(smem_u32(aHi + s * L::A_SLICE)),
+                                 umma_desc(smem_u32(bHi + s * L::B_SLICE)), idesc, s > 0);
+#pragma unroll
+                    for (int s = 0; s < KS; ++s) {
+                        umma_f16(acc + N, umma_desc(smem_u32(aHi + s * L::A_SLICE)),
+                                 umma_desc(smem_u32(bLo + s * L::B_SLICE)), idesc, s > 0);
+                        umma_f16(acc + N, umma_desc(smem_u32(aLo + s * L::A_SLICE)),
+                                 umma_desc(smem_u32(bHi + s * L::B_SLICE)), idesc, 1);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&mma_done[st]))
+                             : "memory");
+            }
+            // the tensor memory is freed only after the last MMA issued has completed
+            if (i > 0) mbar_wait_own(smem_u32(&mma_done[(i - 1) % S]), ((i - 1) / S) & 1);
+        }
+    } else {
+        // ---------------- drainers ----------------
+        const int q = warp & 3;                        // TMEM lane quarter this warp may read
+        const int half = (warp - kMmaWarp - 1) >> 2;   // warps 10-13: members 0..H-1; 14-17: H..D-1
+        const int row = 32 * q + (tid & 31);
+        const bool store_warp = warp == kMmaWarp + 1;  // bulk stores: its lanes store a run each
+        const int lane = tid & 31;
+        uint32_t rx = 0;  // staging index of this row
+        uint64_t ro = 0;  // address offset of this row within the tile (16 consecutive rows: 128 B)
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            if ((row >> j) & 1) {
+                rx |= g.ridx[j];
+                ro += g.roff[j];
+            }
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int st = i % S;
+            const bool ok = mbar_wait_abort(smem_u32(&mma_done[st]), (i / S) & 1, ab) &&
+                            mbar_wait_abort(smem_u32(&full[st]), (i / S) & 1, ab);
+            if (!bar_and(2, kDrain, ok)) {  // uniform: tcgen05.ld below needs whole warps
+                give_up();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint8_t *stage = sm + st * L::STAGE;
+            float2 *const dst = g.psi + tile_base[st] + ro;
+            float inv[R2];
+#pragma unroll
+            for (int u = 0; u < R2; ++u) inv[u] = row_inv[st][u][row];
+#pragma unroll
+            for (int u = 0; u < R2; ++u) {
+                const uint32_t lane_base =
+                    tmem + (i & 1) * L::TMEM_SET + u * L::TMEM_SUB + ((uint32_t)(32 * q) << 16) + half * (N / 2);
+                float a[N / 2], b[N / 2];
+#pragma unroll
+                for (int c0 = 0; c0 < N / 2; c0 += 16) {
+                    tmem_ld16(lane_base + c0, *reinterpret_cast<float(*)[16]>(a + c0));
+                    tmem_ld16(lane_base + N + c0, *reinterpret_cast<float(*)[16]>(b + c0));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (u == R2 - 1) {  // TMEM set read: release it (and, storing from registers, the stage)
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    mbar_arrive(smem_u32(&tmem_free[i & 1]));
+                    if constexpr (!L::BULK_STORE) mbar_arrive(smem_u32(&drained[st]));
+                }
+                if constexpr (L::BULK_STORE) {
+                    const uint32_t rxu = u ? rx | g.ridx[7] : rx;
+#pragma unroll
+                    for (int j = 0; j < H; ++j)
+                        *reinterpret_cast<float2 *>(stage + 8 * (g.midx[H * half + j] | rxu)) =
+                            make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]);
+                } else {
+                    float2 *const du = u ? dst + g.roff[7] : dst;
+#pragma unroll
+                    for (int j = 0; j < H; ++j)
+                        __stcs(du + g.moff[H * half + j],
+                               make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]));
+                }
+            }
+            if constexpr (L::BULK_STORE) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the bulk store reads it
+                bar_sync(2, kDrain);  // the whole tile is back in the stage
+                if (store_warp) {
+                    float2 *const tb = g.psi + tile_base[st];
+                    const uint32_t src = smem_u32(stage);
+                    for (int c = lane; c < n_runs; c += 32) bulk_store(tb + g.off_run[c], src + c * run_bytes, run_bytes);
+                    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                    if (i > 0) {
+                        asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");  // tile i - 1 read out
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&drained[(i - 1) % S]));
+                    }
+                }
+            }
+        }
+        if (L::BULK_STORE && store_warp) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -254,7 +511,7 @@ float half_value(uint16_t u)
 template <int K>
 void build_b(const float2 *mat, uint16_t *out)
 {
-    using L = Tc5Layout<K>;
+    using L = Tc5Layout<K, 1>;
     constexpr int D = L::D, N = L::N;
     uint16_t *hi = out, *lo = out + L::B_BYTES / 2;
     for (int n = 0; n < N; n++)
@@ -271,58 +528,99 @@ void build_b(const float2 *mat, uint16_t *out)
         }
 }
 
+// The tile's free address bits F (ascending): the targets and the `rows` lowest other bits.  The
+// staging index of an amplitude is its address bits on F, packed: bit i = address bit F[i].
+// Returns the length L of F's prefix 0, 1, .., L-1 (the contiguous run), or -1.
+template <int K>
+int tile_geometry(int nbits, const int *tpos, int rows, Tc5Geom &g)
+{
+    int is_target[64] = {0}, target_index[64];
+    for (int q = 0; q < K; q++) {
+        is_target[tpos[q]] = 1;
+        target_index[tpos[q]] = q;
+    }
+    int free_bits[kMaxK + 8], n_free = 0, rank = 0;
+    for (int b = 0; b < nbits && n_free < K + rows; b++) {
+        if (is_target[b]) {
+            free_bits[n_free++] = b;
+        } else if (rank < rows) {
+            g.roff[rank] = 1ull << b;
+            g.ridx[rank++] = 1u << n_free;
+            free_bits[n_free++] = b;
+        }
+    }
+    if (n_free != K + rows) return -1;
+    int run_log2 = 0;
+    while (run_log2 < n_free && free_bits[run_log2] == run_log2) run_log2++;
+    const int full_run = run_log2;
+    run_log2 = std::min(run_log2, SYCSIM_TC5_RUN_LOG2_MAX);  // longer runs go as several copies
+    g.run_log2 = run_log2;
+    for (int m = 0; m < (1 << K); m++) {
+        g.moff[m] = 0;
+        for (int q = 0; q < K; q++)
+            if ((m >> q) & 1) g.moff[m] += 1ull << tpos[q];
+        uint32_t mi = 0;
+        for (int i = 0; i < n_free; i++)
+            if (is_target[free_bits[i]] && ((m >> target_index[free_bits[i]]) & 1)) mi |= 1u << i;
+        g.midx[m] = mi;
+    }
+    for (int c = 0; c < (1 << (n_free - run_log2)); c++) {
+        uint64_t o = 0;
+        for (int i = run_log2; i < n_free; i++)
+            if ((c >> (i - run_log2)) & 1) o += 1ull << free_bits[i];
+        g.off_run[c] = o;
+    }
+    return full_run;
+}
+
+template <int K, int R2>
+int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
+{
+    using L = Tc5Layout<K, R2>;
+    auto kern = k_apply_tcgen05<K, R2>;
+    static int sms = 0;
+    if (!sms) {
+        // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps
+        // the resident CTAs' tensor memory within the SM's 512 columns
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) != cudaSuccess) return -1;
+    }
+    Tc5Geom gg = g;
+    gg.n_tiles = 1ull << (nbits - K - 7 - (R2 == 2));
+    const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)sms);
+    kern<<<(unsigned)grid, kThreadsTc5, L::SMEM, st>>>(gg);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int K>
 int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
                  uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
 {
-    using L = Tc5Layout<K>;
+    using L = Tc5Layout<K, 1>;
     build_b<K>(mat, reinterpret_cast<uint16_t *>(h_frag));
     if (cudaMemcpyAsync(d_frag, h_frag, 2 * L::B_BYTES, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
     if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
     Tc5Geom g{};
     g.psi = psi;
-    g.n_tiles = 1ull << (nbits - K - 7);
-    for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];
-    for (int j = 0; j < L::D; j++) {
-        uint64_t o = 0;
-        for (int b = 0; b < K; b++)
-            if ((j >> b) & 1) o += 1ull << tpos[b];
-        g.moff[j] = o;
-    }
+    for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];  // ascending
     g.bmat = d_frag;
     g.err = h->d_errflag;
-    auto kern = k_apply_tcgen05<K>;
-    static int occ = 0, sms = 0;
-    static size_t smem = 0;
-    if (!occ) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int smem_sm = 0, regs_sm = 0;
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-        // resident CTAs x TMEM columns must stay within the SM's 512 columns (an allocation
-        // beyond that would wait for a CTA that never leaves): size the shared-memory request so
-        // that at most 512 / TMEM_COLS CTAs fit on an SM
-        const int max_ctas = 512 / L::TMEM_COLS;
-        smem = std::max<size_t>(L::SMEM, (size_t)smem_sm / (max_ctas + 1) + 1024);
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return -1;
-        cudaFuncAttributes fa{};
-        if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return -1;
-        const int regs = ((fa.numRegs + 7) / 8) * 8;  // allocation granularity
-        const int by_regs = regs_sm / (regs * kRows);
-        const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
-        occ = std::max(1, std::min({by_regs, by_smem, max_ctas}));
-    }
-    const uint64_t grid = std::min<uint64_t>(g.n_tiles, (uint64_t)sms * occ);
-    kern<<<(unsigned)grid, kRows, smem, st>>>(g);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    // 128-group tiles when their runs reach 2 KiB (bit 7 is a target); otherwise 256-group tiles,
+    // whose 8th row bit is bit 7, so that every bulk copy moves at least 2 KiB
+    const int run = tile_geometry<K>(nbits, tpos, 7, g);
+    if (run < 0) return -1;
+    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1>(g, nbits, st);
+    if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
+    return launch_tc5_kr<K, 2>(g, nbits, st);
 }
 
 }  // namespace
 
-bool tcgen05_eligible(int nbits, int k) { return (k == 4 || k == 5) && nbits >= k + 7; }
+// 128-group tiles; no target below bit 4, so that 16 consecutive rows of one member sit in 16
+// distinct bank pairs of the address-ordered stage
+bool tcgen05_eligible(int nbits, int k, const int *tpos) { return (k == 4 || k == 5) && nbits >= k + 7 && tpos[0] >= 4; }
 
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                          cudaStream_t st)

@@ -146,7 +146,7 @@ int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int preci
 bool precision_ok(int precision);
 
 // ---- apply_tcgen05.cu (5th-generation tensor cores, TMEM) ----
-bool tcgen05_eligible(int nbits, int k);
+bool tcgen05_eligible(int nbits, int k, const int *tpos);
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                          cudaStream_t st);
 

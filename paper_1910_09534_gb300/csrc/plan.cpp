@@ -253,6 +253,7 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
     std::vector<int> precs = {SIM_FP32};
     if (accuracy != SIM_TUNE_FP32) {
         precs.push_back(SIM_FP16X3);
+        precs.push_back(SIM_FP16X3_TMEM);
         precs.push_back(SIM_TF32X3);
     }
     if (accuracy == SIM_TUNE_ANY) precs.push_back(SIM_TF32);
@@ -265,7 +266,8 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
     int rc = SIM_OK;
     for (int prec : precs)
         for (int kmax = 3; kmax <= kMaxK && rc == SIM_OK; kmax++) {
-            if (prec != SIM_FP32 && kmax < 5) continue;  // tensor cores only take blocks of k >= 5
+            // mma.sync tensor-core paths take blocks of k >= 5, the tcgen05 path k >= 4
+            if (prec != SIM_FP32 && kmax < (prec == SIM_FP16X3_TMEM ? 4 : 5)) continue;
             sim_plan_opts o{};
             o.kmax = kmax;
             o.precision = prec;

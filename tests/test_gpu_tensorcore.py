@@ -89,10 +89,17 @@ def test_fp16x3_tiny_and_zero_amplitudes(pkg, oracle_mod):
     assert np.all(np.abs(got[tiny] - want[tiny]) <= 1e-5 * np.abs(want[tiny]) + 1e-30)
 
 
-@pytest.mark.parametrize("n,targets", [(12, [4, 5, 6, 7]), (13, [0, 12, 3, 7, 9]), (22, [21, 5, 13, 8, 17]),
-                                       (16, [15, 8, 4, 11])])
+@pytest.mark.parametrize("n,targets", [
+    # tcgen05 path (no target below bit 4).  128-group tiles (bit 7 a target or inside the run):
+    (12, [4, 5, 6, 7]), (22, [21, 5, 13, 8, 17]), (16, [15, 8, 4, 11]), (20, [4, 5, 6, 7, 8]),
+    (21, [5, 9, 10, 15, 20]), (24, [23, 6, 11, 7, 16]),
+    # 256-group tiles (two M = 128 sub-tiles; bit 7 becomes a row bit), one tile at 13 qubits; at
+    # 24 and 25 qubits every CTA takes many tiles, so the stage ring and both TMEM sets wrap
+    (25, [9, 10, 11, 12]), (20, [12, 13, 14, 15, 16]), (13, [8, 9, 10, 11, 12]), (19, [8, 10, 12, 14]),
+    # a target below bit 4: the same mode runs on the mma.sync 3xFP16 kernel (k = 5) or CUDA cores
+    (13, [0, 12, 3, 7, 9]), (23, [0, 1, 2, 3, 4]), (22, [0, 2, 4, 6]), (24, [23, 2, 11, 7, 16])])
 def test_tcgen05_tiles_match_oracle(pkg, oracle_mod, n, targets):
-    # the tcgen05 path needs >= 2^(k+7) amplitudes (128-group tiles); k = 4 and 5
+    # the tcgen05 path needs >= 2^(k+7) amplitudes (128-group tiles), k = 4 or 5
     k = len(targets)
     u = si.random_unitary(k, seed=n + 3 * k)
     psi = si.random_state(n, seed=2 * n)
