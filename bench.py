@@ -139,6 +139,9 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
     return units_per_rank * world_size / seconds_max
 
 
+TCGEN05_TRAFFIC_GB = 4 * (2.148283 + 2.088019)  # k_apply_tcgen05<5, 2>, ncu at 2^28 amplitudes
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -398,7 +401,12 @@ def run_ours(args):
         "gpu_launches": launches,
         "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None,
+                     # DRAM read + write of the dominant kernel, per launch on 2^30 amplitudes (GB),
+                     # from an ncu capture of that kernel on 2^28 amplitudes, x 4, against 17.18 GB
+                     # algorithmic; null for configurations without that capture
+                     "traffic": (TCGEN05_TRAFFIC_GB if args.precision == "fp16x3_tmem" and n == 30 else None),
+                     "traffic_kernel": "k_apply_tcgen05<5, 2>" if args.precision == "fp16x3_tmem" else None,
                      "kernel": "fused apply, all launches (" + {
                          "fp16x3_tmem": "k_apply_tcgen05 / k_apply_mma_f16x3 / k_apply_reg / k_apply_direct",
                          "fp32": "k_apply_reg / k_apply_direct / k_apply_tiled"}.get(

@@ -2,7 +2,7 @@
 
 * 30 qubits, 20 cycles (5x6 grid; 8 GiB complex64 state): every amplitude against the oracle
   (complex128, gate by gate, all host cores), for the FP32 plan (k <= 4) and the tensor-core
-  plan (k <= 5, 3xFP16).  Bound ||psi - psi_oracle||_2 <= 1e-5.
+  plans (k <= 5, 3xFP16 on mma.sync and on tcgen05).  Bound ||psi - psi_oracle||_2 <= 1e-5.
 * 33 qubits (6x6 minus three corners; 64 GiB) held as 8 slices over the 3 top bits, run as
   alternating phases with in-place bit permutations between them (Sect. 4 in device memory):
   norm and Porter-Thomas, no oracle fits.  Its 28-qubit sub-lattice circuit (4x7, same depth)
@@ -68,7 +68,8 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
     results = {}
     h = pkg.sim_create(n)
     try:
-        for name, kmax, prec in (("fp32_k4", 4, pkg.SIM_FP32), ("fp16x3_k5", 5, pkg.SIM_FP16X3)):
+        for name, kmax, prec in (("fp32_k4", 4, pkg.SIM_FP32), ("fp16x3_k5", 5, pkg.SIM_FP16X3),
+                                 ("fp16x3_tmem_k5", 5, pkg.SIM_FP16X3_TMEM)):
             plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=kmax, precision=prec)
             pkg.sim_reset(h)
             pkg.sim_apply_plan(h, plan)
@@ -92,7 +93,7 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
 def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
     # 33 qubits, 8 slices over 3 top bits, phases with permutations: norm and Porter-Thomas
     circ33 = si.workload_circuit("syc33_6x6m3_d20", seed=0)
-    _, (norm, s2, _), perms, nph = run_sliced_phases(pkg, circ33, 3, pkg.SIM_FP16X3, 5)
+    _, (norm, s2, _), perms, nph = run_sliced_phases(pkg, circ33, 3, pkg.SIM_FP16X3_TMEM, 5)
     print(f"33q sliced: {nph} phases, {perms} permutation passes, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}")
     assert abs(norm - 1) < 2e-5 and abs(s2 - 2) < 0.05
     # 28-qubit sub-lattice (4x7, 20 cycles) through the same machinery, every mode vs oracle
@@ -100,9 +101,10 @@ def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
     import os
     oracle_mod.set_threads(os.cpu_count() or 1)
     want = oracle_mod.run_circuit(circ28)
-    bounds = {"fp32": 1e-5, "fp16x3": 1e-5, "tf32x3": 1e-5, "tf32": 5e-2}
+    bounds = {"fp32": 1e-5, "fp16x3": 1e-5, "fp16x3_tmem": 1e-5, "tf32x3": 1e-5, "tf32": 5e-2}
     for name, prec, kmax in (("fp32", pkg.SIM_FP32, 4), ("fp16x3", pkg.SIM_FP16X3, 5),
-                             ("tf32x3", pkg.SIM_TF32X3, 5), ("tf32", pkg.SIM_TF32, 5)):
+                             ("fp16x3_tmem", pkg.SIM_FP16X3_TMEM, 5), ("tf32x3", pkg.SIM_TF32X3, 5),
+                             ("tf32", pkg.SIM_TF32, 5)):
         out, _, _, _ = run_sliced_phases(pkg, circ28, 3, prec, kmax)
         err = chunked_err(out, want)
         print(f"28q sub-lattice {name} (kmax {kmax}): ||psi - psi_oracle||_2 = {err:.3e}")
