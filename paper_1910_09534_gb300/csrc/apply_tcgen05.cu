@@ -17,7 +17,8 @@
 //    mbarrier by byte count, as soon as the stage's previous tile has been drained;
 //  * converter warps 0-7: thread = (row, half of the members).  It reads its half-row (staging
 //    index = row bits | member bits in address order: no bank conflicts while no target is
-//    below bit 4), the two halves combine their maxima, and the row is scaled by a power of two
+//    below bit 4; with one such target each row XORs its member index by one of its own row
+//    bits, which restores that), the two halves combine their maxima, and the row is scaled by a power of two
 //    (largest component < 2^14, so FP16 stays normal), split hi = fp16(a), lo = fp16(a - hi)
 //    and written in place as the MMA's A operand (K-major core matrices: 8 rows x 16 bytes;
 //    128 B between the two K halves of a 16-wide slice, 256 B between 8-row groups);
@@ -27,8 +28,9 @@
 //  * drainer warps 10-17 read both accumulators (tcgen05.ld 32x32b: warp w sees TMEM lanes
 //    32 (w % 4) ..), add them and undo the row's scale.  With a deep stage ring the amplitudes
 //    go back into the stage and the lanes of warp 10 store its runs with bulk copies; with the
-//    3-stage ring of 64 KiB tiles they are stored from registers (no target below bit 4: 16
-//    consecutive rows are 128 contiguous bytes), which frees the stage as soon as TMEM is read.
+//    3-stage ring of 64 KiB tiles, or a target below bit 4, they are stored from registers (16
+//    consecutive rows cover 64-128 contiguous bytes), which frees the stage as soon as TMEM is
+//    read.  Blocks with two or more targets below bit 4 are left to the other kernels.
 // K (input reals) is interleaved, column 2m + p is part p (Re, Im) of member m, so a row's
 // 16-byte chunk is four consecutive members; N likewise.  R^T (hi, lo; FP16, core-matrix layout)
 // is built on the host and staged in shared memory once per CTA.  Two TMEM accumulator sets let
@@ -65,6 +67,7 @@ struct Tc5Geom {
     uint64_t n_tiles;        // 2^(nbits - k - 7) / R2
     int tpos[kMaxK];         // target bit positions, ascending
     int run_log2;            // L: a tile is 2^(k+7+log2 R2-L) runs of 2^L contiguous amplitudes
+    int nlow;                // targets below bit 4 (they are member bits 0 .. nlow-1)
     uint64_t off_run[32];    // address offset of run c (c's bits deposited on the free bits >= L)
     uint32_t midx[32];       // staging index of member m in row 0 (row r: midx[m] | ridx(r))
     uint32_t ridx[8];        // staging-index bit of row bit j (bit 7: sub-tile)
@@ -220,6 +223,13 @@ struct Tc5Layout {
     static_assert(TMEM_COLS <= 512, "tensor memory");
 };
 
+__device__ __forceinline__ void swap_u32(uint32_t &a, uint32_t &b)
+{
+    const uint32_t t = a;
+    a = b;
+    b = t;
+}
+
 __device__ __forceinline__ uint32_t cm_off(int row, int k) { return (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2; }
 
 // Per tile i (local index; stage s = i % S, stage phase (i / S) & 1; TMEM set i % 2, set phase
@@ -234,10 +244,11 @@ __device__ __forceinline__ uint32_t cm_off(int row, int k) { return (row >> 3) *
 //     store the results from registers.
 // A stage is reloaded only after its drain, and a TMEM set reused only after its read, so no
 // barrier can run a phase ahead of a waiter that still has to see the previous phase.
-template <int K, int R2>
+template <int K, int R2, bool LOWT>
 __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 {
     using L = Tc5Layout<K, R2>;
+    constexpr bool BULK = L::BULK_STORE && !LOWT;  // results back through the stage
     constexpr int D = L::D, KS = L::KS, N = L::N, S = L::S, H = D / 2;  // H members per thread
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *bHi = sm + S * L::STAGE, *bLo = bHi + L::B_BYTES;
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[st])), "r"(kConv) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mma_done[st])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&drained[st])),
-                         "r"(L::BULK_STORE ? 1 : kDrain)
+                         "r"(BULK ? 1 : kDrain)
                          : "memory");
         }
         for (int st = 0; st < 2; ++st)
@@ -294,6 +305,17 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 #pragma unroll
         for (int j = 0; j < 7; ++j)
             if ((row >> j) & 1) rx |= g.ridx[j];
+        // With targets below bit 4 (member bits 0 .. nlow-1; the launcher takes nlow <= 1) the
+        // rows of one member do not cover 16 bank pairs; register j of this thread then holds
+        // member (H half + j) ^ mu, with mu taken from the row bits that do not reach address
+        // bits 0..3, so that the 16 rows of a half-warp read 16 distinct bank pairs.
+        uint32_t mu = 0, mux = 0;
+        if constexpr (LOWT) {
+            mu = (row >> (4 - g.nlow)) & ((1u << g.nlow) - 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((mu >> q) & 1) mux ^= g.midx[1 << q];
+        }
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
             const int st = i % S;
@@ -310,7 +332,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                 float amax = 0.f;
 #pragma unroll
                 for (int m = 0; m < H; ++m) {
-                    x[u][m] = *reinterpret_cast<const float2 *>(stage + 8 * (g.midx[H * half + m] | rxu));
+                    x[u][m] = *reinterpret_cast<const float2 *>(stage + 8 * ((g.midx[H * half + m] ^ mux) | rxu));
                     amax = fmaxf(amax, fmaxf(fabsf(x[u][m].x), fabsf(x[u][m].y)));
                 }
                 amax_part[u][half][row] = amax;
@@ -327,7 +349,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                 uint8_t *aHi = stage + u * L::SUB, *aLo = aHi + L::A_BYTES;
 #pragma unroll
                 for (int cc = 0; cc < H / 4; ++cc) {
-                    const int c = half * (H / 4) + cc;  // 4-member chunk of the row
+                    const int c = (half * (H / 4) + cc) ^ (int)(mu >> 2);  // 4-member chunk of the row
                     uint32_t hi[4], lo[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -337,6 +359,16 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                         const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
                         hi[j] = *reinterpret_cast<const uint32_t *>(&h);
                         lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+                    }
+                    if constexpr (LOWT) {  // position p of the chunk takes register p ^ (mu & 3)
+                        if (mu & 1) {
+                            swap_u32(hi[0], hi[1]), swap_u32(hi[2], hi[3]);
+                            swap_u32(lo[0], lo[1]), swap_u32(lo[2], lo[3]);
+                        }
+                        if (mu & 2) {
+                            swap_u32(hi[0], hi[2]), swap_u32(hi[1], hi[3]);
+                            swap_u32(lo[0], lo[2]), swap_u32(lo[1], lo[3]);
+                        }
                     }
                     const uint32_t off = (c >> 1) * L::A_SLICE + cm_off(row, 8 * (c & 1));
                     *reinterpret_cast<uint4 *>(aHi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -450,23 +482,24 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                 if (u == R2 - 1) {  // TMEM set read: release it (and, storing from registers, the stage)
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                     mbar_arrive(smem_u32(&tmem_free[i & 1]));
-                    if constexpr (!L::BULK_STORE) mbar_arrive(smem_u32(&drained[st]));
+                    if constexpr (!BULK) mbar_arrive(smem_u32(&drained[st]));
                 }
-                if constexpr (L::BULK_STORE) {
+                float2 o[H];
+#pragma unroll
+                for (int j = 0; j < H; ++j)
+                    o[j] = make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]);
+                if constexpr (BULK) {
                     const uint32_t rxu = u ? rx | g.ridx[7] : rx;
 #pragma unroll
                     for (int j = 0; j < H; ++j)
-                        *reinterpret_cast<float2 *>(stage + 8 * (g.midx[H * half + j] | rxu)) =
-                            make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]);
+                        *reinterpret_cast<float2 *>(stage + 8 * (g.midx[H * half + j] | rxu)) = o[j];
                 } else {
                     float2 *const du = u ? dst + g.roff[7] : dst;
 #pragma unroll
-                    for (int j = 0; j < H; ++j)
-                        __stcs(du + g.moff[H * half + j],
-                               make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]));
+                    for (int j = 0; j < H; ++j) __stcs(du + g.moff[H * half + j], o[j]);
                 }
             }
-            if constexpr (L::BULK_STORE) {
+            if constexpr (BULK) {
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the bulk store reads it
                 bar_sync(2, kDrain);  // the whole tile is back in the stage
                 if (store_warp) {
@@ -482,7 +515,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                 }
             }
         }
-        if (L::BULK_STORE && store_warp) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+        if (BULK && store_warp) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -573,11 +606,11 @@ int tile_geometry(int nbits, const int *tpos, int rows, Tc5Geom &g)
     return full_run;
 }
 
-template <int K, int R2>
+template <int K, int R2, bool LOWT>
 int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
 {
     using L = Tc5Layout<K, R2>;
-    auto kern = k_apply_tcgen05<K, R2>;
+    auto kern = k_apply_tcgen05<K, R2, LOWT>;
     static int sms = 0;
     if (!sms) {
         // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps
@@ -607,20 +640,36 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];  // ascending
     g.bmat = d_frag;
     g.err = h->d_errflag;
-    // 128-group tiles when their runs reach 2 KiB (bit 7 is a target); otherwise 256-group tiles,
-    // whose 8th row bit is bit 7, so that every bulk copy moves at least 2 KiB
+    g.nlow = 0;
+    while (g.nlow < K && tpos[g.nlow] < 4) g.nlow++;
+    if (g.nlow > 1) return -2;  // not eligible (see tcgen05_eligible)
+    // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below it);
+    // otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy moves at
+    // least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take 128 groups.
     const int run = tile_geometry<K>(nbits, tpos, 7, g);
     if (run < 0) return -1;
-    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1>(g, nbits, st);
+    if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
     if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
-    return launch_tc5_kr<K, 2>(g, nbits, st);
+    return launch_tc5_kr<K, 2, false>(g, nbits, st);
 }
 
 }  // namespace
 
-// 128-group tiles; no target below bit 4, so that 16 consecutive rows of one member sit in 16
-// distinct bank pairs of the address-ordered stage
-bool tcgen05_eligible(int nbits, int k, const int *tpos) { return (k == 4 || k == 5) && nbits >= k + 7 && tpos[0] >= 4; }
+// At least one 128-group tile, and at most one target below bit 4.  Measured: with one such
+// target the per-row member XOR keeps the row reads conflict-free and the register stores
+// sector-efficient (16 rows cover 64-128 contiguous bytes), as fast as the high-target case;
+// with two or more the stores scatter (each row's members fill the low address bits, so the
+// lanes of a store instruction hit 2^t lines: up to one L2 request per lane), and routing them
+// through the stage instead costs more instructions (register permutations) than it saves.
+// Those blocks run on the mma.sync 3xFP16 kernel (k = 5) or CUDA cores (k = 4).
+bool tcgen05_eligible(int nbits, int k, const int *tpos)
+{
+    if ((k != 4 && k != 5) || nbits < k + 7) return false;
+    int low = 0;
+    for (int q = 0; q < k; q++) low += tpos[q] < 4;
+    return low <= 1;
+}
 
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                          cudaStream_t st)
