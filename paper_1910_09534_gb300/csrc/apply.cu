@@ -578,7 +578,8 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
                         cudaGetErrorString(cudaGetLastError()));
         return SIM_OK;
     }
-    if (precision != SIM_FP32 && tc_eligible(nbits, k, tpos)) {
+    if (precision != SIM_FP32 &&
+        (tc_eligible(nbits, k, tpos) || (precision == SIM_FP16X3_TMEM && tc_eligible_low4(nbits, k)))) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
         const int rc = launch_apply_tc(h, psi, nbits, k, tpos, mat, precision, st);
         prof_end(h, ps, st);

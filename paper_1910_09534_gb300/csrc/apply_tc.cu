@@ -408,6 +408,11 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
 // 3.3 ms vs 7.0 ms).  Any target set works: groups map to amplitude offsets by bit insertion.
 bool tc_eligible(int nbits, int k, const int *) { return k >= 5 && k <= 6 && nbits >= k + 4; }
 
+// In SIM_FP16X3_TMEM mode the blocks the tcgen05 kernel leaves (targets in the low bits) come
+// here for k = 4 too: measured on 2^30 amplitudes, targets {0,1,2,3}: 2.73 ms (CUDA-core FP32
+// 4.27 ms), {0,2,6,8}: 2.59 ms (3.57), {1,6,7,12}: 2.60 ms (3.24).
+bool tc_eligible_low4(int nbits, int k) { return k == 4 && nbits >= k + 4; }
+
 int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                     int precision, cudaStream_t st)
 {

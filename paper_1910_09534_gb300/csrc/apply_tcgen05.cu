@@ -648,7 +648,11 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     // least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take 128 groups.
     const int run = tile_geometry<K>(nbits, tpos, 7, g);
     if (run < 0) return -1;
-    if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+    if constexpr (K == 5) {
+        if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+    } else if (g.nlow > 0) {
+        return -2;
+    }
     if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
     if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
     return launch_tc5_kr<K, 2, false>(g, nbits, st);
@@ -656,19 +660,20 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
 
 }  // namespace
 
-// At least one 128-group tile, and at most one target below bit 4.  Measured: with one such
-// target the per-row member XOR keeps the row reads conflict-free and the register stores
-// sector-efficient (16 rows cover 64-128 contiguous bytes), as fast as the high-target case;
-// with two or more the stores scatter (each row's members fill the low address bits, so the
-// lanes of a store instruction hit 2^t lines: up to one L2 request per lane), and routing them
-// through the stage instead costs more instructions (register permutations) than it saves.
-// Those blocks run on the mma.sync 3xFP16 kernel (k = 5) or CUDA cores (k = 4).
+// At least one 128-group tile, and at most one target below bit 4 (k = 5) or none (k = 4).
+// Measured on 2^30 amplitudes: with one such target the per-row member XOR keeps the row reads
+// conflict-free and the register stores sector-efficient (16 rows cover 64-128 contiguous
+// bytes), as fast as the high-target case for k = 5 (k = 4: 3.27 ms, the mma.sync kernel
+// 2.60 ms); with two or more the stores scatter (each row's members fill the low address bits,
+// so the lanes of a store instruction hit 2^t lines: up to one L2 request per lane), and
+// routing them through the stage instead costs more instructions (register permutations) than
+// it saves.  Those blocks run on the mma.sync 3xFP16 kernel.
 bool tcgen05_eligible(int nbits, int k, const int *tpos)
 {
     if ((k != 4 && k != 5) || nbits < k + 7) return false;
     int low = 0;
     for (int q = 0; q < k; q++) low += tpos[q] < 4;
-    return low <= 1;
+    return low <= (k == 5 ? 1 : 0);
 }
 
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,

@@ -152,6 +152,7 @@ int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpo
 
 // ---- apply_tc.cu (tensor cores) ----
 bool tc_eligible(int nbits, int k, const int *tpos);
+bool tc_eligible_low4(int nbits, int k);
 int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                     int precision, cudaStream_t st);
 

@@ -96,11 +96,12 @@ def test_fp16x3_tiny_and_zero_amplitudes(pkg, oracle_mod):
     # 256-group tiles (two M = 128 sub-tiles; bit 7 becomes a row bit), one tile at 13 qubits; at
     # 24 and 25 qubits every CTA takes many tiles, so the stage ring and both TMEM sets wrap
     (25, [9, 10, 11, 12]), (20, [12, 13, 14, 15, 16]), (13, [8, 9, 10, 11, 12]), (19, [8, 10, 12, 14]),
-    # one target below bit 4: rows read through the per-row member XOR, results stored from
-    # registers
-    (24, [23, 2, 11, 7, 16]), (20, [3, 4, 5, 7, 8]), (19, [1, 6, 7, 12]),
-    # two or more below bit 4: the same mode runs on the mma.sync 3xFP16 kernel (k = 5) or on
-    # CUDA cores (k = 4); one tile at 11 qubits
+    # k = 5 with one target below bit 4: rows read through the per-row member XOR, results
+    # stored from registers
+    (24, [23, 2, 11, 7, 16]), (20, [3, 4, 5, 7, 8]),
+    # more targets below bit 4 (k = 5), or any (k = 4): the same mode runs on the mma.sync 3xFP16
+    # kernel; one tile at 11 qubits
+    (19, [1, 6, 7, 12]),
     (13, [0, 12, 3, 7, 9]), (23, [0, 1, 2, 3, 4]), (22, [0, 2, 4, 6]), (11, [0, 1, 2, 3]),
     (21, [1, 2, 3, 12, 13])])
 def test_tcgen05_tiles_match_oracle(pkg, oracle_mod, n, targets):
