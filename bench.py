@@ -4,17 +4,19 @@ fSim(pi/2, pi/6), random sqrt(X/Y/W)) on one GB300 and report amplitude updates 
 
 One step = one pass of the whole hot path over one circuit: aggregation planning and FP64
 composition (host), reset to |0...0>, every fused block applied on the device, and the
-norm / Porter-Thomas / XEB reduction.  The state (8 GiB complex64) is larger than L2, so no
+norm / Porter-Thomas / XEB reduction.  Each step's plan is built on the host while the previous
+step's last blocks run on the device.  The state (8 GiB complex64) is larger than L2, so no
 flush is needed between steps.
 
 metric value = 2^n * (original gates) * steps / device time   ("gate" amplitude updates/s)
 pass updates = 2^n * (fused blocks) * steps / device time      (roofline basis, 16 B/amp/pass)
 
 Default configuration: chosen by the library's autotuner before the timed region among the
-block widths and the FP32-equivalent arithmetic (FP32 CUDA cores; 3xFP16 or 3xTF32 tensor-core
-splits for 5- and 6-qubit blocks, FP32 accumulate, error vs the oracle ~1e-6 on this workload).  The same JSON line also reports the FP32-only path (blocks of up to 4
-qubits) and a bounded serving run (200 random circuits, n in 16..30, served concurrently vs one
-at a time).
+block widths and the FP32-equivalent arithmetic (FP32 CUDA cores; 3xFP16 on tcgen05 or
+mma.sync, or 3xTF32, for blocks of 4-6 qubits; FP32 accumulate; error vs the oracle ~1e-6 on
+this workload).  The same JSON line also reports the FP32-only path (blocks of up to 4 qubits)
+and a bounded serving run (200 random circuits, n in 16..30, served concurrently vs one at a
+time).
 
 --impl reference times the CPU oracle (complex128, gate by gate) on the host cores on a bounded
 sample of the same workload (the first gates of the circuit on the full 30-qubit state).
@@ -52,7 +54,7 @@ def parse():
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "fp16x3_tmem", "tf32x3", "tf32"],
                     help="arithmetic of blocks with k >= 5 when --kmax is given (narrower blocks always "
                          "run FP32 on CUDA cores)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
     ap.add_argument("--no-fp32-path", action="store_true")
@@ -283,17 +285,22 @@ def run_ours(args):
         tuned = {"by": "sim_autotune (FP32-equivalent arithmetic)", "kmax": kmax,
                  "precision": args.precision, "tuning_run_ms": tune_ms}
 
-    def step():
+    def run_steps(k):
+        # k circuit runs; each plan (host: grouping + FP64 composition) is built while the
+        # previous run's blocks are still executing (sim_apply_plan returns once the last blocks
+        # are queued; sim_reduce waits for the result)
         plan = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec)
-        pkg.sim_reset(h)
-        pkg.sim_apply_plan(h, plan)
-        out = pkg.sim_reduce(h)
-        nb = pkg.sim_plan_info(plan)[0]
-        pkg.sim_plan_destroy(plan)
+        for s in range(k):
+            pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plan)
+            nxt = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec) if s + 1 < k else None
+            out = pkg.sim_reduce(h)
+            nb = pkg.sim_plan_info(plan)[0]
+            pkg.sim_plan_destroy(plan)
+            plan = nxt
         return out, nb
 
-    for _ in range(args.warmup):
-        (norm, s2, xeb), nblocks = step()
+    (norm, s2, xeb), nblocks = run_steps(args.warmup)
 
     def barrier():
         if dist:
@@ -306,8 +313,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
-            (norm, s2, xeb), nblocks = step()
+        (norm, s2, xeb), nblocks = run_steps(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -353,21 +359,33 @@ def run_ours(args):
                                   "frac": ach32 / peak32, "launches": c32}}
 
     # end to end through the public API with host buffers: gate records from pinned host
-    # memory in, all 2^n amplitudes out to pinned host memory, every step
+    # memory in, all 2^n amplitudes out to pinned host memory, every step.  Two handles
+    # alternate, so that the readout of step i (8 GiB at the ~190 GB/s of the host link) runs
+    # while step i + 1 computes; the last readout is inside the timed region too.
     gates_pinned = pkg.pinned_array(gates.size, dtype=pkg._native.GATE_DTYPE)
     gates_pinned[:] = gates
-    out = pkg.pinned_array(amps, dtype=np.complex64)
+    h2 = pkg.sim_create(n, 0, device=local)
+    outs = [pkg.pinned_array(amps, dtype=np.complex64), pkg.pinned_array(amps, dtype=np.complex64)]
+    hs = [h, h2]
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
-        pkg.sim_reset(h)
-        pkg.sim_apply_plan(h, plan)
-        pkg.sim_amplitudes(h, out=out)
+    plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
+    for s_ in range(args.e2e_steps):
+        hc = hs[s_ % 2]
+        pkg.sim_reset(hc)
+        pkg.sim_apply_plan(hc, plan)
+        nxt = (pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
+               if s_ + 1 < args.e2e_steps else None)
+        pkg.sim_amplitudes_async(hc, outs[s_ % 2])
+        if s_ > 0:
+            pkg.sim_sync(hs[(s_ - 1) % 2])  # the previous circuit's amplitudes are in host memory
         pkg.sim_plan_destroy(plan)
+        plan = nxt
+    pkg.sim_sync(hs[(args.e2e_steps - 1) % 2])
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e_value = whole_job_rate(float(amps) * circ.n_gates * args.e2e_steps, ws, max(e2e_s, 1e-9))
+    out = outs[(args.e2e_steps - 1) % 2]
     matrix_bytes = 0
     plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
     for i in range(pkg.sim_plan_info(plan)[0]):
@@ -375,8 +393,10 @@ def run_ours(args):
         matrix_bytes += 8 * (1 << (2 * len(tg)))
     pkg.sim_plan_destroy(plan)
     sanity = out[:4].copy()
-    pkg.sim_host_free(out.ctypes.data)
+    for o in outs:
+        pkg.sim_host_free(o.ctypes.data)
     pkg.sim_host_free(gates_pinned.ctypes.data)
+    pkg.sim_destroy(h2)
     pkg.sim_destroy(h)
 
     if rank != 0:
@@ -416,7 +436,8 @@ def run_ours(args):
         "breakdown_ms_per_step": {"apply": a_ms / args.steps, "reduce": r_ms / args.steps,
                                   "other": ms_max / args.steps - (a_ms + r_ms) / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes + matrix_bytes),
-                "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps},
+                "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps,
+                "pipelined": "two handles: the readout of step i overlaps the compute of step i+1"},
         "clocks": clk.summary(),
     }
     if fp32_path:

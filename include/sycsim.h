@@ -149,6 +149,16 @@ int sim_permute(sim_t *h, const int *perm);
 int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtype,
                    int physical_order);
 
+/* Readout without waiting (not in the paper: it lets a caller overlap reading one circuit's
+ * result with computing the next on another handle).  Enqueues the copy of `count`
+ * complex64 amplitudes starting at `first` into host memory `out` on the handle's stream and
+ * returns.  out must stay valid until sim_sync(h) returns, and should be pinned (pageable
+ * memory makes the copy synchronous).  Logical order requires the identity layout (no
+ * permutation pending); physical_order = 1 always works.  SIM_E_UNSUPPORTED for host-store
+ * handles or a logical read of a permuted layout (use sim_amplitudes); SIM_E_INVAL for a bad
+ * range or NULL out.  Later calls on h are ordered after the copy. */
+int sim_amplitudes_async(sim_t *h, uint64_t first, uint64_t count, void *out, int physical_order);
+
 /* Overwrite `count` amplitudes starting at `first` with complex64 values from
  * host memory `src` (logical or physical order as above).  Synchronous. */
 int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *src,

@@ -98,6 +98,8 @@ _SIGS = {
     "sim_permute": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sim_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sim_amplitudes_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_int]),
     "sim_load_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                            ctypes.c_void_p, ctypes.c_int]),
     "sim_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -244,6 +246,14 @@ def sim_amplitudes(h, first: int = 0, count: int | None = None, dtype: int = SIM
         out = np.empty(count, dtype=npdt)
     assert out.dtype == npdt and out.size >= count and out.flags.c_contiguous
     _check(lib().sim_amplitudes(h, first, count, _ptr(out), dtype, int(physical_order)), h)
+    return out
+
+
+def sim_amplitudes_async(h, out: np.ndarray, first: int = 0, physical_order: bool = False) -> np.ndarray:
+    """Enqueue the readout of out.size complex64 amplitudes into `out` (keep it alive and
+    untouched until sim_sync(h)); pinned memory (pinned_array) keeps the copy asynchronous."""
+    assert out.dtype == np.complex64 and out.flags.c_contiguous
+    _check(lib().sim_amplitudes_async(h, first, out.size, _ptr(out), int(physical_order)), h)
     return out
 
 

@@ -19,40 +19,47 @@ using namespace sycsim;
 
 namespace {
 
-// U <- G U, G acting on local bits (l0) or (l0, l1) of a k-qubit block matrix U.
-void left_multiply(std::vector<double> &U, int k, const double *G, int dg, int l0, int l1)
+// U <- G U, G (GD x GD, GD = 2 or 4) acting on local bits (l0) or (l0, l1) of the D x D
+// matrix U (row-major, complex as interleaved doubles).
+template <int GD>
+void left_multiply_t(double *U, int D, const double *G, int l0, int l1)
 {
-    const int D = 1 << k;
-    const int gd = dg;  // 2 or 4
-    std::vector<int> rows(gd);
-    std::vector<double> tmp(2 * gd);
     for (int base = 0; base < D; base++) {
         if ((base >> l0) & 1) continue;
-        if (gd == 4 && ((base >> l1) & 1)) continue;
+        if (GD == 4 && ((base >> l1) & 1)) continue;
+        int rows[GD];
         rows[0] = base;
         rows[1] = base | (1 << l0);
-        if (gd == 4) {
+        if (GD == 4) {
             rows[2] = base | (1 << l1);
             rows[3] = base | (1 << l0) | (1 << l1);
         }
         for (int c = 0; c < D; c++) {
-            for (int r = 0; r < gd; r++) {
-                double re = 0, im = 0;
-                for (int x = 0; x < gd; x++) {
-                    const double gr = G[2 * (r * gd + x)], gi = G[2 * (r * gd + x) + 1];
-                    const double ur = U[2 * (rows[x] * D + c)], ui = U[2 * (rows[x] * D + c) + 1];
-                    re += gr * ur - gi * ui;
-                    im += gr * ui + gi * ur;
-                }
-                tmp[2 * r] = re;
-                tmp[2 * r + 1] = im;
+            double ur[GD], ui[GD];
+            for (int x = 0; x < GD; x++) {
+                ur[x] = U[2 * (rows[x] * D + c)];
+                ui[x] = U[2 * (rows[x] * D + c) + 1];
             }
-            for (int r = 0; r < gd; r++) {
-                U[2 * (rows[r] * D + c)] = tmp[2 * r];
-                U[2 * (rows[r] * D + c) + 1] = tmp[2 * r + 1];
+            for (int r = 0; r < GD; r++) {
+                double re = 0, im = 0;
+                for (int x = 0; x < GD; x++) {
+                    const double gr = G[2 * (r * GD + x)], gi = G[2 * (r * GD + x) + 1];
+                    re += gr * ur[x] - gi * ui[x];
+                    im += gr * ui[x] + gi * ur[x];
+                }
+                U[2 * (rows[r] * D + c)] = re;
+                U[2 * (rows[r] * D + c) + 1] = im;
             }
         }
     }
+}
+
+void left_multiply(std::vector<double> &U, int k, const double *G, int dg, int l0, int l1)
+{
+    if (dg == 4)
+        left_multiply_t<4>(U.data(), 1 << k, G, l0, l1);
+    else
+        left_multiply_t<2>(U.data(), 1 << k, G, l0, -1);
 }
 
 }  // namespace
@@ -140,7 +147,9 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
 
     // Pass 2: greedy grouping of the units into blocks of at most kmax qubits.
     std::vector<int> last(n_qubits, -1);
-    for (const Unit &u : units) {
+    std::vector<std::vector<int>> block_units;  // units of each block, in order
+    for (int ui = 0; ui < (int)units.size(); ui++) {
+        const Unit &u = units[ui];
         const int nq = u.nq;
         const int *Q = u.q;
         int lo = -1;
@@ -157,8 +166,10 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
             if (grown(p->blocks[b]) <= opts.kmax) chosen = b;
         if (chosen < 0) {
             p->blocks.emplace_back();
+            block_units.emplace_back();
             chosen = (int)p->blocks.size() - 1;
         }
+        block_units[chosen].push_back(ui);
         PlanBlock &b = p->blocks[chosen];
         for (int i = 0; i < nq; i++)
             if (std::find(b.qubits.begin(), b.qubits.end(), Q[i]) == b.qubits.end())
@@ -166,20 +177,36 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
         b.gates.insert(b.gates.end(), u.gates.begin(), u.gates.end());
         for (int i = 0; i < nq; i++) last[Q[i]] = chosen;
     }
-    // compose each block in FP64
-    for (auto &b : p->blocks) {
+    // compose each block in FP64: each unit's gates first into one 2x2 or 4x4 matrix (local bit 0
+    // = the unit's first qubit), then that matrix into the block
+    for (size_t bi = 0; bi < p->blocks.size(); bi++) {
+        PlanBlock &b = p->blocks[bi];
         std::sort(b.qubits.begin(), b.qubits.end());
         const int k = (int)b.qubits.size(), D = 1 << k;
         b.mat.assign(2 * D * D, 0.0);
         for (int i = 0; i < D; i++) b.mat[2 * (i * D + i)] = 1.0;
-        for (int gi : b.gates) {
-            const sim_gate &g = gates[gi];
-            const int d = gate_matrix(g, G);
-            const int l0 = (int)(std::find(b.qubits.begin(), b.qubits.end(), g.q0) - b.qubits.begin());
-            const int l1 = d == 4 ? (int)(std::find(b.qubits.begin(), b.qubits.end(), g.q1) -
-                                          b.qubits.begin())
-                                  : -1;
-            left_multiply(b.mat, k, G, d, l0, l1);
+        for (int ui : block_units[bi]) {
+            const Unit &u = units[ui];
+            const int ud = u.nq == 2 ? 4 : 2;
+            double Mu[32] = {0};
+            for (int i = 0; i < ud; i++) Mu[2 * (i * ud + i)] = 1.0;
+            for (int gi : u.gates) {
+                const sim_gate &g = gates[gi];
+                const int d = gate_matrix(g, G);
+                if (d == 4) {
+                    const bool same = g.q0 == u.q[0];  // the gate's bit 0 on the unit's bit 0?
+                    left_multiply_t<4>(Mu, 4, G, same ? 0 : 1, same ? 1 : 0);
+                } else {
+                    left_multiply_t<2>(Mu, ud, G, g.q0 == u.q[0] ? 0 : 1, -1);
+                }
+            }
+            const int l0 = (int)(std::find(b.qubits.begin(), b.qubits.end(), u.q[0]) - b.qubits.begin());
+            if (u.nq == 2) {
+                const int l1 = (int)(std::find(b.qubits.begin(), b.qubits.end(), u.q[1]) - b.qubits.begin());
+                left_multiply_t<4>(b.mat.data(), D, Mu, l0, l1);
+            } else {
+                left_multiply_t<2>(b.mat.data(), D, Mu, l0, -1);
+            }
         }
     }
     *out = p;

@@ -342,6 +342,25 @@ int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtyp
     return SIM_OK;
 }
 
+int sim_amplitudes_async(sim_t *h, uint64_t first, uint64_t count, void *out, int physical_order)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_amplitudes_async: NULL handle");
+    if (first > h->amps || count > h->amps - first)
+        return fail(h, SIM_E_INVAL, "sim_amplitudes_async: range [%llu, +%llu) outside 2^%d",
+                    (unsigned long long)first, (unsigned long long)count, h->n);
+    if (count == 0) return SIM_OK;
+    if (!out) return fail(h, SIM_E_INVAL, "sim_amplitudes_async: out is NULL");
+    if (h->store == SIM_STORE_HOST)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_amplitudes_async: host-store handle (use sim_amplitudes)");
+    if (!physical_order && !layout_is_identity(h))
+        return fail(h, SIM_E_UNSUPPORTED,
+                    "sim_amplitudes_async: logical order of a permuted layout (use sim_amplitudes)");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_state + first, count * sizeof(float2), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    return SIM_OK;
+}
+
 int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *src,
                         int physical_order)
 {

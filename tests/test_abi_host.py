@@ -54,6 +54,7 @@ def test_errors_without_touching_device(pkg):
     assert L.sim_create(0, 0, None, ctypes.byref(h)) == pkg.SIM_E_INVAL
     assert b"n_qubits" in L.sim_last_error(None)
     assert L.sim_create(10, 10, None, ctypes.byref(h)) == pkg.SIM_E_INVAL
+    assert L.sim_amplitudes_async(None, 0, 1, None, 0) == pkg.SIM_E_INVAL
     assert L.sim_destroy(None) == pkg.SIM_E_INVAL
     assert L.sim_apply_fused(None, 1, None, None, 0) == pkg.SIM_E_INVAL
     assert L.sim_plan_create(4, 1, None, None, ctypes.byref(h)) == pkg.SIM_E_INVAL

@@ -223,6 +223,47 @@ def test_load_readout_roundtrip_bit_exact(pkg):
     assert np.array_equal(part128, psi[5:14].astype(np.complex128))
 
 
+def test_async_readout_bit_exact_and_overlapping(pkg):
+    # two handles: the readout of one is enqueued while the other is being computed
+    n = 18
+    psi = si.random_state(n, 11)
+    ha, hb = pkg.sim_create(n), pkg.sim_create(n)
+    outs = [pkg.pinned_array(1 << n), pkg.pinned_array(1 << n)]
+    part = pkg.pinned_array(300)
+    try:
+        pkg.sim_load_amplitudes(ha, psi)
+        pkg.sim_amplitudes_async(ha, outs[0])
+        pkg.sim_amplitudes_async(ha, part, first=4000)
+        pkg.sim_reset(hb)
+        circ = si.sycamore_circuit(si.Grid(3, 6), cycles=6, seed=3)
+        plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+        pkg.sim_apply_plan(hb, plan)
+        pkg.sim_plan_destroy(plan)
+        pkg.sim_amplitudes_async(hb, outs[1])
+        pkg.sim_sync(ha)
+        assert np.array_equal(outs[0].view(np.uint64), psi.view(np.uint64))
+        assert np.array_equal(part, psi[4000:4300])
+        pkg.sim_sync(hb)
+        assert np.array_equal(outs[1].view(np.uint64), pkg.sim_amplitudes(hb).view(np.uint64))
+        # logical order of a permuted layout is refused; physical order is fine
+        perm = si.random_permutation(n, 5)
+        pkg.sim_permute(ha, perm)
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_amplitudes_async(ha, outs[0])
+        assert e.value.code == pkg.SIM_E_UNSUPPORTED
+        pkg.sim_amplitudes_async(ha, outs[0], physical_order=True)
+        pkg.sim_sync(ha)
+        assert np.array_equal(outs[0].view(np.uint64), pkg.sim_amplitudes(ha, physical_order=True).view(np.uint64))
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_amplitudes_async(ha, part, first=(1 << n) - 10)
+        assert e.value.code == pkg.SIM_E_INVAL
+    finally:
+        pkg.sim_destroy(ha)
+        pkg.sim_destroy(hb)
+        for a in outs + [part]:
+            pkg.sim_host_free(a.ctypes.data)
+
+
 def test_argument_errors(pkg):
     h = pkg.sim_create(8)
     try:
