@@ -339,8 +339,8 @@ typedef struct srv_opts {
     int slots;           /* concurrent circuits above small_n (0 = 6, max 32) */
     int small_n;         /* circuits with n <= small_n are packed (0 = 20, max 24) */
     int max_pack;        /* most circuits per packed launch (0 = 1024) */
-    int kmax;            /* aggregation width (0 = 5 for n <= 24, else 4) */
-    int precision;       /* circuits above small_n: SIM_FP32, SIM_TF32, SIM_TF32X3, SIM_FP16X3 */
+    int kmax;            /* aggregation width (0 = 5, or 4 for n > 24 in SIM_FP32) */
+    int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_FP16X3_TMEM */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
     int reserved[8];
 } srv_opts;

@@ -589,20 +589,22 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
         return SIM_OK;
     }
     const float2 *mat6 = nullptr;
+    int slot6 = -1;
     if (k == 6) {
-        const int slot = h->mat6_next;
+        const int slot = slot6 = h->mat6_next;
         h->mat6_next = (slot + 1) % sim_s::kMat6Slots;
         SIM_CUDA_TRY(h, cudaEventSynchronize(h->mat6_ev[slot]));  // host staging slot free
         std::memcpy(h->h_mat6 + 4096 * slot, mat, sizeof(float2) * 4096);
         float2 *dst = h->d_mat6 + 4096 * slot;
         SIM_CUDA_TRY(h, cudaMemcpyAsync(dst, h->h_mat6 + 4096 * slot, sizeof(float2) * 4096,
                                         cudaMemcpyHostToDevice, st));
-        SIM_CUDA_TRY(h, cudaEventRecord(h->mat6_ev[slot], st));
         mat6 = dst;
     }
     const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
     const int rc = launch_apply_fp32(h, psi, nbits, k, tpos, mat, mat6, st);
     prof_end(h, ps, st);
+    // the matrix slot is free again once this kernel, which reads it, has run (on any stream)
+    if (slot6 >= 0) SIM_CUDA_TRY(h, cudaEventRecord(h->mat6_ev[slot6], st));
     if (rc != 0)
         return fail(h, SIM_E_CUDA, "apply: kernel launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));

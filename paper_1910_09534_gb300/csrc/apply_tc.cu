@@ -293,7 +293,6 @@ int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, c
             }
     const size_t bytes = sizeof(uint32_t) * 2 * FRAG_WORDS;
     if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
-    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
     MmaGeom g{};
     g.psi = psi;
     g.n_mtiles = 1ull << (nbits - K - 4);
@@ -320,7 +319,10 @@ int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, c
     const uint64_t need = (g.n_mtiles + 7) / 8;
     const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    const bool launched = cudaGetLastError() == cudaSuccess;
+    // the staging slot is free again once this kernel, which reads it, has run (on any stream)
+    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
+    return launched ? 0 : -1;
 }
 
 // Round an FP32 value to TF32 (nearest, ties away from zero, as cvt.rna), host side.
@@ -369,7 +371,6 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
             }
     const size_t bytes = sizeof(uint32_t) * NSPLIT * FRAG_WORDS;
     if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
-    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
 
     MmaGeom g{};
     g.psi = psi;
@@ -398,7 +399,10 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
     (void)h;
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    const bool launched = cudaGetLastError() == cudaSuccess;
+    // the staging slot is free again once this kernel, which reads it, has run (on any stream)
+    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
+    return launched ? 0 : -1;
 }
 
 }  // namespace

@@ -634,7 +634,6 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     using L = Tc5Layout<K, 1>;
     build_b<K>(mat, reinterpret_cast<uint16_t *>(h_frag));
     if (cudaMemcpyAsync(d_frag, h_frag, 2 * L::B_BYTES, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
-    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
     Tc5Geom g{};
     g.psi = psi;
     for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];  // ascending
@@ -647,15 +646,18 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     // otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy moves at
     // least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take 128 groups.
     const int run = tile_geometry<K>(nbits, tpos, 7, g);
-    if (run < 0) return -1;
-    if constexpr (K == 5) {
-        if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+    int rc = -1;
+    if (run < 0) {
     } else if (g.nlow > 0) {
-        return -2;
+        if constexpr (K == 5) rc = launch_tc5_kr<K, 1, true>(g, nbits, st);
+    } else if (run >= 8 || nbits < K + 8) {
+        rc = launch_tc5_kr<K, 1, false>(g, nbits, st);
+    } else if (tile_geometry<K>(nbits, tpos, 8, g) >= 8) {
+        rc = launch_tc5_kr<K, 2, false>(g, nbits, st);
     }
-    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
-    if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
-    return launch_tc5_kr<K, 2, false>(g, nbits, st);
+    // the staging slot is free again once this kernel, which reads it, has run (on any stream)
+    if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
+    return rc;
 }
 
 }  // namespace

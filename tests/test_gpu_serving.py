@@ -61,6 +61,21 @@ def test_served_results_match_oracle_and_alone_equals_mix(pkg, oracle_mod):
         assert abs(norm - 1.0) < 1e-5 and abs(s2 - os2) < 1e-3 * os2 and lat > 0
 
 
+def test_tensor_core_modes_on_concurrent_streams(pkg, oracle_mod):
+    # stream-path circuits on several slot streams at once, in the tcgen05 and mma.sync 3xFP16
+    # modes: the shared matrix-staging rings must not be overwritten under a kernel still queued
+    # on another stream; served alone and in a mix must agree bit for bit
+    circuits = [si.sycamore_circuit(si.near_square_grid(n), d, seed=300 + i)
+                for i, (n, d) in enumerate([(16, 12), (18, 10), (17, 14), (19, 8), (16, 16), (18, 12)])]
+    for prec in (pkg.SIM_FP16X3_TMEM, pkg.SIM_FP16X3):
+        mix, res, stats = serve(pkg, circuits, True, small_n=12, slots=4, kmax=5, precision=prec)
+        alone, _, _ = serve(pkg, circuits, False, small_n=12, slots=4, kmax=5, precision=prec)
+        assert stats["completed"] == len(circuits)
+        for c, a, b, (norm, s2, lat) in zip(circuits, mix, alone, res):
+            assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), (prec, c.name)
+            assert np.linalg.norm(a.astype(np.complex128) - oracle_mod.run_circuit(c)) <= TOL_FP32, (prec, c.name)
+
+
 def test_admission_respects_hbm_budget(pkg, oracle_mod):
     # 20-qubit states are 8 MiB; a 20 MiB budget admits two at a time
     circuits = [si.sycamore_circuit(si.near_square_grid(20), 6, seed=s) for s in range(5)]
