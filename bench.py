@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
                          "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
-                         "mma.sync, high then mixed targets; with tcgen05, 256- then 128-group tiles), a "
-                         "high-bit permutation and a reduction, each twice, then exit; meant to run under ncu")
+                         "mma.sync, high then mixed targets; with tcgen05, 256- and 128-group tiles and one "
+                         "target below bit 4), k=4 on bits 0-3 in the default mode, a high-bit permutation "
+                         "and a reduction, each twice, then exit; meant to run under ncu")
     return ap.parse_args()
 
 
@@ -141,7 +142,7 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
     return units_per_rank * world_size / seconds_max
 
 
-TCGEN05_TRAFFIC_GB = 4 * (2.148283 + 2.088019)  # k_apply_tcgen05<5, 2>, ncu at 2^28 amplitudes
+TCGEN05_TRAFFIC_GB = 4 * (2.147897 + 2.088273)  # k_apply_tcgen05<5, 2, 0>, ncu at 2^28 amplitudes
 
 
 def measured_peaks():
@@ -434,7 +435,7 @@ def run_ours(args):
                      # from an ncu capture of that kernel on 2^28 amplitudes, x 4, against 17.18 GB
                      # algorithmic; null for configurations without that capture
                      "traffic": (TCGEN05_TRAFFIC_GB if args.precision == "fp16x3_tmem" and n == 30 else None),
-                     "traffic_kernel": "k_apply_tcgen05<5, 2>" if args.precision == "fp16x3_tmem" else None,
+                     "traffic_kernel": "k_apply_tcgen05<5, 2, 0>" if args.precision == "fp16x3_tmem" else None,
                      "kernel": "fused apply, all launches (" + {
                          "fp16x3_tmem": "k_apply_tcgen05 / k_apply_mma_f16x3 / k_apply_reg / k_apply_direct",
                          "fp32": "k_apply_reg / k_apply_direct / k_apply_tiled"}.get(
@@ -476,8 +477,9 @@ def kernel_case():
         u = si.random_unitary(len(t), 2)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3)
-    # tcgen05: 256-group tiles stored from registers, then 128-group tiles with bulk stores
-    for t in ([12, 13, 14, 15, 16], [4, 9, 14, 20, 25]):
+    # default mode: tcgen05 with 256-group tiles stored from registers, 128-group tiles with bulk
+    # stores, one target below bit 4; then a 4-qubit block on bits 0-3 (mma.sync, k = 4)
+    for t in ([12, 13, 14, 15, 16], [4, 9, 14, 20, 25], [3, 4, 5, 7, 8], [0, 1, 2, 3]):
         u = si.random_unitary(len(t), 2)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3_TMEM)
