@@ -437,18 +437,22 @@ __global__ void __launch_bounds__(256, reg_min_blocks(K, kLow)) k_apply_reg(RegG
 template <int K, bool kLow>
 int launch_reg_kernel(const RegGeom &g, const MatP<K> &M, cudaStream_t st)
 {
-    static int occ = 0;  // resident CTAs per SM for this instantiation
-    static int sms = 0;
     auto kern = k_apply_reg<K, kLow>;
-    if (!occ) {
+    // resident CTAs per SM for this instantiation (function-local static: initialised once,
+    // thread-safe)
+    static const LaunchCfg cfg = [&] {
+        LaunchCfg c;
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1)
-            occ = 1;
-    }
+        if (cudaGetDevice(&dev) != cudaSuccess) return c;
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, 256, 0) != cudaSuccess || c.occ < 1)
+            c.occ = 1;
+        c.ok = true;
+        return c;
+    }();
+    if (!cfg.ok) return -1;
     const uint64_t need = (g.n_wtiles + 7) / 8;  // 8 warps per CTA
-    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)cfg.sms * cfg.occ);
     kern<<<(unsigned)grid, 256, 0, st>>>(g, M);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -565,11 +569,31 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
     return prepare_block_map(h, k, targets, matrix, h->bit_of, h->n - h->s, tpos, mat);
 }
 
+// Which kernel family takes a block: the one place that decides it.
+BlockPath block_path(int nbits, int k, const int *tpos, int precision)
+{
+    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k, tpos)) return BlockPath::Tcgen05;
+    if (precision != SIM_FP32 &&
+        (tc_eligible(nbits, k, tpos) || (precision == SIM_FP16X3_TMEM && tc_eligible_low4(nbits, k))))
+        return BlockPath::MmaSync;
+    return BlockPath::CudaCore;
+}
+
+bool staging_slot_free(sim_t *h, int nbits, int k, const int *tpos, int precision)
+{
+    // an event never recorded counts as complete
+    if (block_path(nbits, k, tpos, precision) != BlockPath::CudaCore)
+        return cudaEventQuery(h->frag_ev[h->frag_next]) != cudaErrorNotReady;
+    if (k == 6) return cudaEventQuery(h->mat6_ev[h->mat6_next]) != cudaErrorNotReady;
+    return true;
+}
+
 // Enqueue one prepared block on a buffer of 2^nbits amplitudes, on stream st.
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st)
 {
-    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k, tpos)) {
+    const BlockPath path = block_path(nbits, k, tpos, precision);
+    if (path == BlockPath::Tcgen05) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
         const int rc = launch_apply_tcgen05(h, psi, nbits, k, tpos, mat, st);
         prof_end(h, ps, st);
@@ -578,8 +602,7 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
                         cudaGetErrorString(cudaGetLastError()));
         return SIM_OK;
     }
-    if (precision != SIM_FP32 &&
-        (tc_eligible(nbits, k, tpos) || (precision == SIM_FP16X3_TMEM && tc_eligible_low4(nbits, k)))) {
+    if (path == BlockPath::MmaSync) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
         const int rc = launch_apply_tc(h, psi, nbits, k, tpos, mat, precision, st);
         prof_end(h, ps, st);

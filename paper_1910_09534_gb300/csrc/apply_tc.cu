@@ -305,19 +305,22 @@ int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, c
     }
     g.bfrag = d_frag;
     auto kern = k_apply_mma_f16x3<K>;
-    static int occ = 0, sms = 0;
-    if (!occ) {
+    static const LaunchCfg cfg = [&] {  // once per instantiation, thread-safe
+        LaunchCfg c;
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) return c;
         if (bytes > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return -1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, bytes) != cudaSuccess || occ < 1)
-            occ = 1;
-    }
+            return c;
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, 256, bytes) != cudaSuccess || c.occ < 1)
+            c.occ = 1;
+        c.ok = true;
+        return c;
+    }();
+    if (!cfg.ok) return -1;
     const uint64_t need = (g.n_mtiles + 7) / 8;
-    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)cfg.sms * cfg.occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
     const bool launched = cudaGetLastError() == cudaSuccess;
     // the staging slot is free again once this kernel, which reads it, has run (on any stream)
@@ -384,19 +387,22 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     }
     g.bfrag = d_frag;
     auto kern = k_apply_mma<K, kSplit>;
-    static int occ = 0, sms = 0;
-    if (!occ) {
+    static const LaunchCfg cfg = [&] {  // once per instantiation, thread-safe
+        LaunchCfg c;
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) return c;
         if (bytes > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return -1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, bytes) != cudaSuccess || occ < 1)
-            occ = 1;
-    }
+            return c;
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, 256, bytes) != cudaSuccess || c.occ < 1)
+            c.occ = 1;
+        c.ok = true;
+        return c;
+    }();
+    if (!cfg.ok) return -1;
     const uint64_t need = (g.n_mtiles + 7) / 8;
-    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)sms * occ);
+    const uint64_t grid = std::min<uint64_t>(need, (uint64_t)cfg.sms * cfg.occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
     (void)h;
     const bool launched = cudaGetLastError() == cudaSuccess;

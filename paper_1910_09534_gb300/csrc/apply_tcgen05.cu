@@ -611,18 +611,21 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
 {
     using L = Tc5Layout<K, R2>;
     auto kern = k_apply_tcgen05<K, R2, LOWT>;
-    static int sms = 0;
-    if (!sms) {
-        // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps
-        // the resident CTAs' tensor memory within the SM's 512 columns
+    // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps the
+    // resident CTAs' tensor memory within the SM's 512 columns (initialised once, thread-safe)
+    static const LaunchCfg cfg = [&] {
+        LaunchCfg c;
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) != cudaSuccess) return -1;
-    }
+        if (cudaGetDevice(&dev) != cudaSuccess) return c;
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) != cudaSuccess) return c;
+        c.ok = true;
+        return c;
+    }();
+    if (!cfg.ok) return -1;
     Tc5Geom gg = g;
     gg.n_tiles = 1ull << (nbits - K - 7 - (R2 == 2));
-    const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)sms);
+    const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)cfg.sms);
     kern<<<(unsigned)grid, kThreadsTc5, L::SMEM, st>>>(gg);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

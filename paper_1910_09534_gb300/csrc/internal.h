@@ -139,6 +139,17 @@ void prof_end(sim_t *h, int slot, cudaStream_t st);
 int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
                       int nlocal, int *tpos, float2 *mat, int nq = -1);
 int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat);
+// One-time launch configuration of a kernel instantiation (kept in a function-local static).
+struct LaunchCfg {
+    int sms = 0;
+    int occ = 1;  // resident CTAs per SM
+    bool ok = false;
+};
+
+enum class BlockPath { CudaCore, MmaSync, Tcgen05 };
+BlockPath block_path(int nbits, int k, const int *tpos, int precision);
+// true if enqueue_block_on would not have to wait for a matrix-staging slot (non-blocking check)
+bool staging_slot_free(sim_t *h, int nbits, int k, const int *tpos, int precision);
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st);
 int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);

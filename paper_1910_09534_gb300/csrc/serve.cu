@@ -12,7 +12,9 @@
 //    whole circuit -- reset, every block, the reduction -- with the block matrix in shared
 //    memory, so a batch of small circuits costs one kernel launch instead of one per block;
 //  * runs larger circuits on one of several slot streams with stream-ordered allocation, so
-//    circuits of different sizes overlap on the device;
+//    circuits of different sizes overlap on the device; their blocks are enqueued a few at a
+//    time, as far as the slot's matrix-staging ring has free slots, so the scheduler never
+//    waits on device progress;
 //  * detects completion by polling events, frees memory and budget, and wakes waiters.
 // Results (norm, 2^n sum p^2, XEB; optionally all amplitudes into the caller's buffer) and
 // latencies (submit -> completion seen) are recorded; srv_stats reports p50/p99 and circuits/s.
@@ -176,6 +178,8 @@ struct Req {
     // in flight (unpacked)
     int slot = -1;
     float2 *d_state = nullptr;
+    size_t next_block = 0;   // blocks enqueued so far
+    bool launched = false;   // everything enqueued and ev recorded
     cudaEvent_t ev = nullptr;
     double *h_res = nullptr;  // pinned pair
 };
@@ -261,18 +265,41 @@ void finish(srv_t *s, const std::shared_ptr<Req> &r, int status, double a, doubl
     s->any_done = true;
 }
 
-// Launch one unpacked request on slot i (scheduler thread, lock held).
-int launch_unpacked(srv_t *s, int i, const std::shared_ptr<Req> &r)
+// Start one unpacked request on slot i (scheduler thread, lock held): state and |0...0>.
+int start_unpacked(srv_t *s, int i, const std::shared_ptr<Req> &r)
 {
     sim_t *h = s->slots[i];
     cudaStream_t st = h->stream;
     const uint64_t amps = 1ull << r->n;
-    if (cudaMallocAsync(&r->d_state, sizeof(float2) * amps, st) != cudaSuccess) return SIM_E_NOMEM_DEV;
+    r->slot = i;
+    r->next_block = 0;
+    r->launched = false;
+    s->slot_req[i] = r;
+    if (cudaMallocAsync(&r->d_state, sizeof(float2) * amps, st) != cudaSuccess) {
+        r->d_state = nullptr;
+        return SIM_E_NOMEM_DEV;
+    }
     if (cudaMemsetAsync(r->d_state, 0, sizeof(float2) * amps, st) != cudaSuccess) return SIM_E_CUDA;
     if (launch_set_basis(r->d_state, amps, 0, st) != 0) return SIM_E_CUDA;
-    for (const Prepared &b : r->blocks) {
+    return SIM_OK;
+}
+
+// Enqueue as many of the request's blocks as go without waiting for a matrix-staging slot (the
+// slot of a tensor-core block is free once the kernel that last read it has run), then, after
+// the last block, the reduction, the copies out and the completion event.  Never blocks the
+// scheduler on device progress.  *progressed is set if anything was enqueued.
+int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
+{
+    sim_t *h = s->slots[r->slot];
+    cudaStream_t st = h->stream;
+    const uint64_t amps = 1ull << r->n;
+    while (r->next_block < r->blocks.size()) {
+        const Prepared &b = r->blocks[r->next_block];
+        if (!staging_slot_free(h, r->n, b.k, b.tpos, r->precision)) return SIM_OK;
         const int rc = enqueue_block_on(h, r->d_state, r->n, b.k, b.tpos, b.mat.data(), r->precision, st);
         if (rc != SIM_OK) return rc;
+        r->next_block++;
+        *progressed = true;
     }
     if (launch_reduce(h, r->d_state, amps, h->d_partials, h->d_result, st) != 0) return SIM_E_CUDA;
     if (cudaMemcpyAsync(r->h_res, h->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -281,10 +308,22 @@ int launch_unpacked(srv_t *s, int i, const std::shared_ptr<Req> &r)
         cudaMemcpyAsync(r->out_amps, r->d_state, sizeof(float2) * amps, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SIM_E_CUDA;
     if (cudaFreeAsync(r->d_state, st) != cudaSuccess) return SIM_E_CUDA;
+    r->d_state = nullptr;
     if (cudaEventRecord(r->ev, st) != cudaSuccess) return SIM_E_CUDA;
-    r->slot = i;
-    s->slot_req[i] = r;
+    r->launched = true;
+    *progressed = true;
     return SIM_OK;
+}
+
+// A request on slot i failed before its completion event was recorded: release what it holds.
+void abort_unpacked(srv_t *s, int i, int rc)
+{
+    auto r = s->slot_req[i];
+    if (r->d_state) cudaFreeAsync(r->d_state, s->slots[i]->stream);
+    r->d_state = nullptr;
+    s->slot_req[i].reset();
+    finish(s, r, rc, 0.0, 0.0);
+    s->cv_done.notify_all();
 }
 
 // Launch one packed batch of small requests (scheduler thread, lock held).
@@ -364,7 +403,7 @@ void scheduler(srv_t *s)
         // completions: unpacked slots
         for (size_t i = 0; i < s->slots.size(); i++) {
             auto &r = s->slot_req[i];
-            if (!r) continue;
+            if (!r || !r->launched) continue;
             const cudaError_t e = cudaEventQuery(r->ev);
             if (e == cudaErrorNotReady) continue;
             finish(s, r, e == cudaSuccess ? SIM_OK : SIM_E_CUDA, r->h_res[0], r->h_res[1]);
@@ -405,11 +444,8 @@ void scheduler(srv_t *s)
                     for (size_t i = 0; i < s->slots.size(); i++)
                         if (!s->slot_req[i]) {
                             s->used += r->bytes;
-                            const int rc = launch_unpacked(s, (int)i, r);
-                            if (rc != SIM_OK) {
-                                finish(s, r, rc, 0.0, 0.0);
-                                s->cv_done.notify_all();
-                            }
+                            const int rc = start_unpacked(s, (int)i, r);
+                            if (rc != SIM_OK) abort_unpacked(s, (int)i, rc);
                             admitted = true;
                             break;
                         }
@@ -423,6 +459,16 @@ void scheduler(srv_t *s)
             }
             if (!first_blocked) first_blocked = r;
             ++it;
+        }
+        // stream-path requests: enqueue what the staging rings allow
+        for (size_t i = 0; i < s->slots.size(); i++) {
+            auto r = s->slot_req[i];
+            if (!r || r->launched) continue;
+            const int rc = advance_unpacked(s, r, &progressed);
+            if (rc != SIM_OK) {
+                abort_unpacked(s, (int)i, rc);
+                progressed = true;
+            }
         }
         // packed launch: whenever a batch stream is free
         if (!pack_pending.empty())
