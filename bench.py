@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
     ap.add_argument("--no-fp32-path", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--serving-circuits", type=int, default=200)
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
@@ -220,6 +221,40 @@ def serving_run(count: int, device: int):
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
             "one_at_a_time_p99_ms": statistics.quantiles(seq_done, n=100)[98],
             "arithmetic": "fp16x3_tmem (k_max 5; circuits of <= 20 qubits packed one per CTA in FP32)"}
+
+
+def graph_replay_run(device: int, runs: int = 30):
+    """The same circuit run `runs` times from |0...0> (20 and 24 qubits, 20 cycles, k_max 5,
+    SIM_FP16X3_TMEM): each run through sim_apply_plan vs a replay of its CUDA graph; wall time
+    per run, measured after a warm-up run of each."""
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+
+    out = []
+    for grid in (si.Grid(4, 5), si.Grid(4, 6)):
+        circ = si.sycamore_circuit(grid, cycles=20, seed=7)
+        n = circ.n_qubits
+        plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+        h = pkg.sim_create(n, 0, device=device)
+        g = pkg.sim_graph_create(h, plan)
+        res = {"circuit": f"{grid.rows}x{grid.cols} grid ({n} qubits), 20 cycles, k_max 5, fp16x3_tmem",
+               "blocks": pkg.sim_plan_info(plan)[0], "runs": runs}
+        for name, run in (("direct_ms_per_run", lambda: pkg.sim_apply_plan(h, plan)),
+                          ("graph_ms_per_run", lambda: pkg.sim_graph_launch(h, g))):
+            pkg.sim_reset(h)
+            run()
+            pkg.sim_sync(h)
+            t0 = time.perf_counter()
+            for _ in range(runs):
+                pkg.sim_reset(h)
+                run()
+            pkg.sim_sync(h)
+            res[name] = (time.perf_counter() - t0) * 1e3 / runs
+        pkg.sim_graph_destroy(g)
+        pkg.sim_destroy(h)
+        pkg.sim_plan_destroy(plan)
+        out.append(res)
+    return out
 
 
 def run_reference(args):
@@ -457,6 +492,8 @@ def run_ours(args):
         line["fp32_path"] = fp32_path
     if ws == 1 and not args.no_serving:
         line["serving"] = serving_run(args.serving_circuits, local)
+    if ws == 1 and not args.no_graphs:
+        line["graph_replay"] = graph_replay_run(local)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(circ, args.cpu_sample_gates)
     _ = sanity

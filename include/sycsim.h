@@ -263,6 +263,22 @@ int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *mat
 /* Apply every block of the plan in order (each as sim_apply_fused).  Async. */
 int sim_apply_plan(sim_t *h, const sim_plan_t *p);
 
+/* ---- CUDA graphs (not in the paper) ----------------------------------------
+ * Capture the block launches of a plan on h once and replay them.  For a plan run many times
+ * (the same circuit from several initial states, repeated runs) a replay skips the per-block host
+ * work -- matrix rounding, operand staging, the launch itself -- which dominates below ~2^24
+ * amplitudes.  Every block's staged operands (tensor-core B fragments, 6-qubit matrices) are
+ * uploaded once into device memory that the graph owns.  A graph is bound to h (its state
+ * buffer, stream and layout): sim_graph_launch refuses with SIM_E_INVAL on another handle or
+ * once h's layout has changed (sim_permute), and a graph must be destroyed before its handle.
+ * SIM_E_UNSUPPORTED for host-store handles or a handle on the legacy default stream.
+ * sim_graph_create is synchronous (uploads, captures, instantiates); it does not touch the
+ * state.  sim_graph_launch is asynchronous on h's stream, like sim_apply_plan. */
+typedef struct sim_graph_s sim_graph_t;
+int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out);
+int sim_graph_launch(sim_t *h, const sim_graph_t *g);
+int sim_graph_destroy(sim_graph_t *g);
+
 /* Autotuner (not in the paper; Sect. 5 fixes k_max = 5 for its CPUs): plans the
  * given circuit with every candidate block width (k_max 3..6) and arithmetic the
  * accuracy class allows -- SIM_TUNE_FP32: FP32 only; SIM_TUNE_FP32_EQUIVALENT:

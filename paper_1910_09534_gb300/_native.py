@@ -120,6 +120,9 @@ _SIGS = {
     "sim_plan_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "sim_apply_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_graph_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "sim_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p]),
     "sim_stream_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
@@ -368,6 +371,21 @@ def sim_plan_block(p, i: int):
 
 def sim_apply_plan(h, p) -> None:
     _check(lib().sim_apply_plan(h, p), h)
+
+
+def sim_graph_create(h, p):
+    """CUDA graph of the plan's block launches on h (replay with sim_graph_launch)."""
+    g = ctypes.c_void_p()
+    _check(lib().sim_graph_create(h, p, ctypes.byref(g)), h)
+    return g
+
+
+def sim_graph_launch(h, g) -> None:
+    _check(lib().sim_graph_launch(h, g), h)
+
+
+def sim_graph_destroy(g) -> None:
+    _check(lib().sim_graph_destroy(g))
 
 
 SIM_TUNE_FP32 = 0

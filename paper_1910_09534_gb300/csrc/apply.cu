@@ -588,6 +588,47 @@ bool staging_slot_free(sim_t *h, int nbits, int k, const int *tpos, int precisio
     return true;
 }
 
+// Operands of a block staged once in device memory (CUDA graphs): tensor-core B fragments, or
+// the matrix of a 6-qubit block on CUDA cores; nothing for narrower CUDA-core blocks, whose
+// matrix travels as kernel parameters.
+size_t block_staged_bytes(int nbits, int k, const int *tpos, int precision)
+{
+    switch (block_path(nbits, k, tpos, precision)) {
+    case BlockPath::Tcgen05: return tcgen05_staged_bytes(k);
+    case BlockPath::MmaSync: return tc_staged_bytes(k, precision);
+    default: return k == 6 ? sizeof(float2) * 4096 : 0;
+    }
+}
+
+void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, int precision, void *h_out)
+{
+    switch (block_path(nbits, k, tpos, precision)) {
+    case BlockPath::Tcgen05: tcgen05_build_staged(k, mat, h_out); break;
+    case BlockPath::MmaSync: tc_build_staged(k, mat, precision, h_out); break;
+    default:
+        if (k == 6) std::memcpy(h_out, mat, sizeof(float2) * 4096);
+        break;
+    }
+}
+
+int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                        int precision, const void *d_staged, cudaStream_t st)
+{
+    h->launches++;
+    int rc;
+    switch (block_path(nbits, k, tpos, precision)) {
+    case BlockPath::Tcgen05: rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, d_staged, st); break;
+    case BlockPath::MmaSync: rc = tc_launch_staged(psi, nbits, k, tpos, precision, d_staged, st); break;
+    default:
+        rc = launch_apply_fp32(h, psi, nbits, k, tpos, mat, k == 6 ? static_cast<const float2 *>(d_staged) : nullptr,
+                               st);
+        break;
+    }
+    if (rc != 0)
+        return fail(h, SIM_E_CUDA, "apply (staged): launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return SIM_OK;
+}
+
 // Enqueue one prepared block on a buffer of 2^nbits amplitudes, on stream st.
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st)

@@ -263,8 +263,11 @@ uint32_t pack_half2(float lo, float hi)
 }
 
 template <int K>
-int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
-                   uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+constexpr size_t f16x3_bytes() { return sizeof(uint32_t) * 2 * ((1 << K) / 8) * ((1 << K) / 4) * 64; }
+
+// Host: the B fragments (hi, lo) of one block, as the kernel reads them.
+template <int K>
+void build_f16x3(const float2 *mat, uint32_t *h_frag)
 {
     constexpr int D = 1 << K, KS = D / 8, NT = D / 4;
     constexpr int FRAG_WORDS = KS * NT * 64;
@@ -291,8 +294,14 @@ int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, c
                         pack_half2(re_in - __half2float(hr), im_in - __half2float(hm));
                 }
             }
-    const size_t bytes = sizeof(uint32_t) * 2 * FRAG_WORDS;
-    if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+}
+
+// Launch with the fragments already in device memory.
+template <int K>
+int launch_f16x3_staged(float2 *psi, int nbits, const int *tpos, const uint32_t *d_frag, cudaStream_t st)
+{
+    constexpr int D = 1 << K;
+    constexpr size_t bytes = f16x3_bytes<K>();
     MmaGeom g{};
     g.psi = psi;
     g.n_mtiles = 1ull << (nbits - K - 4);
@@ -322,10 +331,19 @@ int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, c
     const uint64_t need = (g.n_mtiles + 7) / 8;
     const uint64_t grid = std::min<uint64_t>(need, (uint64_t)cfg.sms * cfg.occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
-    const bool launched = cudaGetLastError() == cudaSuccess;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int K>
+int launch_f16x3_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
+                   uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+{
+    build_f16x3<K>(mat, h_frag);
+    if (cudaMemcpyAsync(d_frag, h_frag, f16x3_bytes<K>(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    const int rc = launch_f16x3_staged<K>(psi, nbits, tpos, d_frag, st);
     // the staging slot is free again once this kernel, which reads it, has run (on any stream)
     if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
-    return launched ? 0 : -1;
+    return rc;
 }
 
 // Round an FP32 value to TF32 (nearest, ties away from zero, as cvt.rna), host side.
@@ -346,10 +364,13 @@ float tf32_value(uint32_t u)
 }
 
 template <int K, bool kSplit>
-int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
-                 uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+constexpr size_t mma_bytes() { return sizeof(uint32_t) * (kSplit ? 2 : 1) * ((1 << K) / 4) * ((1 << K) / 4) * 64; }
+
+// Host: the B fragments (TF32; with the split, hi then lo) of one block.
+template <int K, bool kSplit>
+void build_mma(const float2 *mat, uint32_t *h_frag)
 {
-    constexpr int D = 1 << K, KS = D / 4, NT = D / 4, NSPLIT = kSplit ? 2 : 1;
+    constexpr int D = 1 << K, KS = D / 4, NT = D / 4;
     constexpr int FRAG_WORDS = KS * NT * 64;
     // B[k][n] = R^T, permuted: k = (step s, column c): member 4s + (c & 3), Re for c < 4, Im for
     // c >= 4; n = (tile m, column c'): member 4m + c'/2, Re for even c', Im for odd c'.
@@ -372,9 +393,13 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
                     h_frag[FRAG_WORDS + idx + 1] = host_tf32(b1 - tf32_value(h1));
                 }
             }
-    const size_t bytes = sizeof(uint32_t) * NSPLIT * FRAG_WORDS;
-    if (cudaMemcpyAsync(d_frag, h_frag, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+}
 
+template <int K, bool kSplit>
+int launch_mma_staged(float2 *psi, int nbits, const int *tpos, const uint32_t *d_frag, cudaStream_t st)
+{
+    constexpr int D = 1 << K;
+    constexpr size_t bytes = mma_bytes<K, kSplit>();
     MmaGeom g{};
     g.psi = psi;
     g.n_mtiles = 1ull << (nbits - K - 4);
@@ -404,11 +429,19 @@ int launch_mma_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     const uint64_t need = (g.n_mtiles + 7) / 8;
     const uint64_t grid = std::min<uint64_t>(need, (uint64_t)cfg.sms * cfg.occ);
     kern<<<(unsigned)grid, 256, bytes, st>>>(g);
-    (void)h;
-    const bool launched = cudaGetLastError() == cudaSuccess;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int K, bool kSplit>
+int launch_mma_k(float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
+                 uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+{
+    build_mma<K, kSplit>(mat, h_frag);
+    if (cudaMemcpyAsync(d_frag, h_frag, mma_bytes<K, kSplit>(), cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    const int rc = launch_mma_staged<K, kSplit>(psi, nbits, tpos, d_frag, st);
     // the staging slot is free again once this kernel, which reads it, has run (on any stream)
     if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
-    return launched ? 0 : -1;
+    return rc;
 }
 
 }  // namespace
@@ -422,6 +455,48 @@ bool tc_eligible(int nbits, int k, const int *) { return k >= 5 && k <= 6 && nbi
 // here for k = 4 too: measured on 2^30 amplitudes, targets {0,1,2,3}: 2.73 ms (CUDA-core FP32
 // 4.27 ms), {0,2,6,8}: 2.59 ms (3.57), {1,6,7,12}: 2.60 ms (3.24).
 bool tc_eligible_low4(int nbits, int k) { return k == 4 && nbits >= k + 4; }
+
+size_t tc_staged_bytes(int k, int precision)
+{
+    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    switch (k) {
+    case 4: return f16 ? f16x3_bytes<4>() : (split ? mma_bytes<4, true>() : mma_bytes<4, false>());
+    case 5: return f16 ? f16x3_bytes<5>() : (split ? mma_bytes<5, true>() : mma_bytes<5, false>());
+    case 6: return f16 ? f16x3_bytes<6>() : (split ? mma_bytes<6, true>() : mma_bytes<6, false>());
+    default: return 0;
+    }
+}
+
+void tc_build_staged(int k, const float2 *mat, int precision, void *h_out)
+{
+    uint32_t *o = static_cast<uint32_t *>(h_out);
+    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    switch (k) {
+    case 4: f16 ? build_f16x3<4>(mat, o) : (split ? build_mma<4, true>(mat, o) : build_mma<4, false>(mat, o)); break;
+    case 5: f16 ? build_f16x3<5>(mat, o) : (split ? build_mma<5, true>(mat, o) : build_mma<5, false>(mat, o)); break;
+    case 6: f16 ? build_f16x3<6>(mat, o) : (split ? build_mma<6, true>(mat, o) : build_mma<6, false>(mat, o)); break;
+    default: break;
+    }
+}
+
+int tc_launch_staged(float2 *psi, int nbits, int k, const int *tpos, int precision, const void *d_staged,
+                     cudaStream_t st)
+{
+    const uint32_t *d = static_cast<const uint32_t *>(d_staged);
+    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    switch (k) {
+    case 4: return f16 ? launch_f16x3_staged<4>(psi, nbits, tpos, d, st)
+                       : (split ? launch_mma_staged<4, true>(psi, nbits, tpos, d, st)
+                                : launch_mma_staged<4, false>(psi, nbits, tpos, d, st));
+    case 5: return f16 ? launch_f16x3_staged<5>(psi, nbits, tpos, d, st)
+                       : (split ? launch_mma_staged<5, true>(psi, nbits, tpos, d, st)
+                                : launch_mma_staged<5, false>(psi, nbits, tpos, d, st));
+    case 6: return f16 ? launch_f16x3_staged<6>(psi, nbits, tpos, d, st)
+                       : (split ? launch_mma_staged<6, true>(psi, nbits, tpos, d, st)
+                                : launch_mma_staged<6, false>(psi, nbits, tpos, d, st));
+    default: return -1;
+    }
+}
 
 int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                     int precision, cudaStream_t st)
@@ -442,12 +517,12 @@ int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, co
     }
     const bool split = precision == SIM_TF32X3;
     switch (k) {
-    case 4: return split ? launch_mma_k<4, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
-                         : launch_mma_k<4, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
-    case 5: return split ? launch_mma_k<5, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
-                         : launch_mma_k<5, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
-    case 6: return split ? launch_mma_k<6, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
-                         : launch_mma_k<6, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 4: return split ? launch_mma_k<4, true>(psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<4, false>(psi, nbits, tpos, mat, st, hf, df, ev);
+    case 5: return split ? launch_mma_k<5, true>(psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<5, false>(psi, nbits, tpos, mat, st, hf, df, ev);
+    case 6: return split ? launch_mma_k<6, true>(psi, nbits, tpos, mat, st, hf, df, ev)
+                         : launch_mma_k<6, false>(psi, nbits, tpos, mat, st, hf, df, ev);
     default: return -1;
     }
 }

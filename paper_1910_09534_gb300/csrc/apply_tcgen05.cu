@@ -630,17 +630,14 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Geometry of the block and launch, B (hi, lo) already in device memory at d_b.
 template <int K>
-int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
-                 uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const uint32_t *d_b, cudaStream_t st)
 {
-    using L = Tc5Layout<K, 1>;
-    build_b<K>(mat, reinterpret_cast<uint16_t *>(h_frag));
-    if (cudaMemcpyAsync(d_frag, h_frag, 2 * L::B_BYTES, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
     Tc5Geom g{};
     g.psi = psi;
     for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];  // ascending
-    g.bmat = d_frag;
+    g.bmat = d_b;
     g.err = h->d_errflag;
     g.nlow = 0;
     while (g.nlow < K && tpos[g.nlow] < 4) g.nlow++;
@@ -649,15 +646,24 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
     // otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy moves at
     // least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take 128 groups.
     const int run = tile_geometry<K>(nbits, tpos, 7, g);
-    int rc = -1;
-    if (run < 0) {
-    } else if (g.nlow > 0) {
-        if constexpr (K == 5) rc = launch_tc5_kr<K, 1, true>(g, nbits, st);
-    } else if (run >= 8 || nbits < K + 8) {
-        rc = launch_tc5_kr<K, 1, false>(g, nbits, st);
-    } else if (tile_geometry<K>(nbits, tpos, 8, g) >= 8) {
-        rc = launch_tc5_kr<K, 2, false>(g, nbits, st);
+    if (run < 0) return -1;
+    if (g.nlow > 0) {
+        if constexpr (K == 5) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+        return -2;
     }
+    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
+    if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
+    return launch_tc5_kr<K, 2, false>(g, nbits, st);
+}
+
+template <int K>
+int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
+                 uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
+{
+    using L = Tc5Layout<K, 1>;
+    build_b<K>(mat, reinterpret_cast<uint16_t *>(h_frag));
+    if (cudaMemcpyAsync(d_frag, h_frag, 2 * L::B_BYTES, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
+    const int rc = launch_tc5_staged<K>(h, psi, nbits, tpos, d_frag, st);
     // the staging slot is free again once this kernel, which reads it, has run (on any stream)
     if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
     return rc;
@@ -679,6 +685,28 @@ bool tcgen05_eligible(int nbits, int k, const int *tpos)
     int low = 0;
     for (int q = 0; q < k; q++) low += tpos[q] < 4;
     return low <= (k == 5 ? 1 : 0);
+}
+
+size_t tcgen05_staged_bytes(int k)
+{
+    return k == 4 ? 2 * Tc5Layout<4, 1>::B_BYTES : (k == 5 ? 2 * Tc5Layout<5, 1>::B_BYTES : 0);
+}
+
+void tcgen05_build_staged(int k, const float2 *mat, void *h_out)
+{
+    if (k == 4) build_b<4>(mat, static_cast<uint16_t *>(h_out));
+    if (k == 5) build_b<5>(mat, static_cast<uint16_t *>(h_out));
+}
+
+int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const void *d_staged,
+                          cudaStream_t st)
+{
+    const uint32_t *d_b = static_cast<const uint32_t *>(d_staged);
+    switch (k) {
+    case 4: return launch_tc5_staged<4>(h, psi, nbits, tpos, d_b, st);
+    case 5: return launch_tc5_staged<5>(h, psi, nbits, tpos, d_b, st);
+    default: return -1;
+    }
 }
 
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,

@@ -98,6 +98,15 @@ struct PlanBlock {
     std::vector<double> mat;  // 2 * D * D, row-major interleaved
 };
 
+struct sim_graph_s {
+    sim_t *h = nullptr;
+    void *d_staged = nullptr;  // every block's staged operands
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> bit_of;  // layout the targets were resolved with
+    int n_blocks = 0;
+};
+
 struct sim_plan_s {
     int n = 0, n_gates = 0, kmax = 0, precision = 0;
     std::vector<PlanBlock> blocks;
@@ -150,6 +159,10 @@ enum class BlockPath { CudaCore, MmaSync, Tcgen05 };
 BlockPath block_path(int nbits, int k, const int *tpos, int precision);
 // true if enqueue_block_on would not have to wait for a matrix-staging slot (non-blocking check)
 bool staging_slot_free(sim_t *h, int nbits, int k, const int *tpos, int precision);
+size_t block_staged_bytes(int nbits, int k, const int *tpos, int precision);
+void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, int precision, void *h_out);
+int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+                        int precision, const void *d_staged, cudaStream_t st);
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st);
 int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);
@@ -158,12 +171,21 @@ bool precision_ok(int precision);
 
 // ---- apply_tcgen05.cu (5th-generation tensor cores, TMEM) ----
 bool tcgen05_eligible(int nbits, int k, const int *tpos);
+// operands staged once in device memory (CUDA graphs): B hi/lo of one block
+size_t tcgen05_staged_bytes(int k);
+void tcgen05_build_staged(int k, const float2 *mat, void *h_out);
+int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const void *d_staged,
+                          cudaStream_t st);
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                          cudaStream_t st);
 
 // ---- apply_tc.cu (tensor cores) ----
 bool tc_eligible(int nbits, int k, const int *tpos);
 bool tc_eligible_low4(int nbits, int k);
+size_t tc_staged_bytes(int k, int precision);
+void tc_build_staged(int k, const float2 *mat, int precision, void *h_out);
+int tc_launch_staged(float2 *psi, int nbits, int k, const int *tpos, int precision, const void *d_staged,
+                     cudaStream_t st);
 int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                     int precision, cudaStream_t st);
 

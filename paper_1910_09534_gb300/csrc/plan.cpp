@@ -267,6 +267,96 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
     return SIM_OK;
 }
 
+// ---- CUDA graphs of a plan ----
+
+int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out)
+{
+    if (!h || !p || !out) return fail(h, SIM_E_INVAL, "sim_graph_create: NULL argument");
+    *out = nullptr;
+    if (p->n != h->n) return fail(h, SIM_E_INVAL, "sim_graph_create: plan has %d qubits, handle %d", p->n, h->n);
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_graph_create: host-store handle (use sim_run_phase)");
+    if (h->stream == nullptr)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_graph_create: the legacy default stream cannot be captured");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    struct Staged {
+        int k;
+        int tpos[kMaxK];
+        std::vector<float2> mat;
+        size_t off, bytes;
+    };
+    std::vector<Staged> blocks(p->blocks.size());
+    static thread_local float2 mat[4096];
+    size_t total = 0;
+    for (size_t i = 0; i < p->blocks.size(); i++) {
+        const PlanBlock &b = p->blocks[i];
+        Staged &sb = blocks[i];
+        sb.k = (int)b.qubits.size();
+        const int rc = prepare_block(h, sb.k, b.qubits.data(), b.mat.data(), sb.tpos, mat);
+        if (rc != SIM_OK) return rc;
+        sb.mat.assign(mat, mat + (1 << (2 * sb.k)));
+        sb.bytes = block_staged_bytes(h->n, sb.k, sb.tpos, p->precision);
+        sb.off = total;
+        total += (sb.bytes + 255) & ~size_t(255);
+    }
+    auto *g = new sim_graph_s();
+    g->h = h;
+    g->n_blocks = (int)blocks.size();
+    g->bit_of.assign(h->bit_of, h->bit_of + h->n);
+    auto cleanup = [&](int code, const char *what) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->d_staged) cudaFree(g->d_staged);
+        delete g;
+        return fail(h, code, "sim_graph_create: %s: %s", what, cudaGetErrorString(cudaGetLastError()));
+    };
+    if (total) {
+        std::vector<char> host(total);
+        for (auto &sb : blocks)
+            if (sb.bytes) block_build_staged(h->n, sb.k, sb.tpos, sb.mat.data(), p->precision, host.data() + sb.off);
+        if (cudaMalloc(&g->d_staged, total) != cudaSuccess) return cleanup(SIM_E_NOMEM_DEV, "staging buffer");
+        if (cudaMemcpy(g->d_staged, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(SIM_E_CUDA, "staging upload");
+    }
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cleanup(SIM_E_CUDA, "begin capture");
+    int rc = SIM_OK;
+    for (auto &sb : blocks) {
+        rc = launch_block_staged(h, h->d_state, h->n, sb.k, sb.tpos, sb.mat.data(), p->precision,
+                                 static_cast<char *>(g->d_staged) + sb.off, h->stream);
+        if (rc != SIM_OK) break;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &g->graph);  // always ends the capture
+    if (rc != SIM_OK || ec != cudaSuccess) return cleanup(rc != SIM_OK ? rc : SIM_E_CUDA, "capture");
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) return cleanup(SIM_E_CUDA, "instantiate");
+    h->launches -= (uint64_t)blocks.size();  // captured, not run
+    *out = g;
+    return SIM_OK;
+}
+
+int sim_graph_launch(sim_t *h, const sim_graph_t *g)
+{
+    if (!h || !g) return fail(h, SIM_E_INVAL, "sim_graph_launch: NULL argument");
+    if (g->h != h) return fail(h, SIM_E_INVAL, "sim_graph_launch: the graph belongs to another handle");
+    if (!std::equal(g->bit_of.begin(), g->bit_of.end(), h->bit_of))
+        return fail(h, SIM_E_INVAL, "sim_graph_launch: the layout changed since the graph was created");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_CUDA_TRY(h, cudaGraphLaunch(g->exec, h->stream));
+    h->launches += (uint64_t)g->n_blocks;
+    return SIM_OK;
+}
+
+int sim_graph_destroy(sim_graph_t *g)
+{
+    if (!g) return fail(nullptr, SIM_E_INVAL, "sim_graph_destroy: NULL graph");
+    cudaSetDevice(g->h->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->d_staged) cudaFree(g->d_staged);
+    delete g;
+    return SIM_OK;
+}
+
 // ---- autotuner: measure candidate widths and arithmetic on the device ----
 
 int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim_plan_opts *best,
