@@ -84,7 +84,12 @@ typedef struct sim_opts {
     int slots;          /* SIM_STORE_HOST: device slice buffers, 2..4 (0 = 3) */
     int set_a[8];       /* SIM_STORE_HOST: the two sliced qubit sets A and B (Sect. 4: the */
     int set_b[8];       /* sliced qubits alternate between two sets); slice_bits qubits each, disjoint */
-    int reserved[8];
+    int store_device_regions; /* SIM_STORE_HOST: of the 2^slice_bits regions of the store (one per
+                           value of set A), how many (the highest values of A) live in device
+                           memory instead of pinned host memory, for states larger than the
+                           host's memory; 0 = all on the host.  Slice copies then mix
+                           host->device and device->device moves. */
+    int reserved[7];
 } sim_opts;
 
 /* Message for the last failure on h (h == NULL: the calling thread's last failure

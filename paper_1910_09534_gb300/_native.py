@@ -55,7 +55,7 @@ class SimOpts(ctypes.Structure):
     _fields_ = [("store", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("ext_state", ctypes.c_void_p), ("ext_bytes", ctypes.c_uint64),
                 ("slots", ctypes.c_int), ("set_a", ctypes.c_int * 8), ("set_b", ctypes.c_int * 8),
-                ("reserved", ctypes.c_int * 8)]
+                ("store_device_regions", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class PlanOpts(ctypes.Structure):
@@ -187,8 +187,9 @@ def sim_version() -> str:
 
 def sim_create(n_qubits: int, slice_bits: int = 0, device: int = 0, stream: int | None = None,
                ext_state: int | None = None, ext_bytes: int = 0, store: int = SIM_STORE_DEVICE,
-               set_a=(), set_b=(), slots: int = 0):
+               set_a=(), set_b=(), slots: int = 0, store_device_regions: int = 0):
     o = SimOpts()
+    o.store_device_regions = store_device_regions
     o.store = store
     o.device = device
     o.stream = stream

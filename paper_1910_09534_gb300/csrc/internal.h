@@ -78,7 +78,9 @@ struct sim_s {
     // host store (SIM_STORE_HOST, Sect. 4 secondary storage): pinned 2^n amplitudes in the
     // host layout [rest qubits | set B | set A] and device slots of 2^(n - s) amplitudes
     static constexpr int kMaxSlots = 4;
-    float2 *h_store = nullptr;
+    float2 *h_store = nullptr;   // pinned: the store's regions 0 .. host_regions-1
+    float2 *d_store = nullptr;   // device: regions host_regions .. 2^s - 1 (hybrid store)
+    uint64_t host_regions = 0;   // regions (one per value of set A, 2^(n-s) amplitudes each) on the host
     int nslots = 0;
     float2 *d_slot[kMaxSlots] = {};
     cudaStream_t st_in = nullptr, st_out = nullptr;

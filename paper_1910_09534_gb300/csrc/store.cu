@@ -1,6 +1,8 @@
 // store.cu -- secondary storage (Sect. 4): the state in pinned host memory, organised so that
 // the "logical files" indexed by the sliced qubits are contiguous, streamed through device
-// slots one slice at a time.
+// slots one slice at a time.  For states larger than the host's memory the store can keep its
+// top regions (one per value of set A) in device memory instead: a hybrid store whose slice
+// copies mix host->device and device->device moves.
 //
 // Layout of the host store (bit 0 first): the qubits in neither sliced set, ascending; then
 // set B in the given order; then set A in the given order.  A file is one run of
@@ -46,6 +48,50 @@ void parallel_for(uint64_t n, F f)
 
 int s_of(const sim_t *h) { return h->s; }
 
+// Region v of the store (the amplitudes with set A = v): pinned host memory, or device memory
+// for the top regions of a hybrid store.  Copies use cudaMemcpyDefault, so both kinds move
+// through the same calls.
+float2 *region(const sim_t *h, uint64_t v)
+{
+    const uint64_t slice = 1ull << (h->n - h->s);
+    return v < h->host_regions ? h->h_store + v * slice : h->d_store + (v - h->host_regions) * slice;
+}
+
+// Host-addressable view of every region for element-wise access (reset, readout, load): host
+// regions as they are, each device region through a host copy (one region at most, per call,
+// is the cost of a hybrid store there).  write_back puts the copies back.
+struct HostView {
+    std::vector<float2 *> ptr;
+    std::vector<std::vector<float2>> copies;
+};
+
+int host_view(sim_t *h, HostView &hv, bool fetch)
+{
+    const uint64_t nreg = 1ull << h->s, slice = 1ull << (h->n - h->s);
+    hv.ptr.resize(nreg);
+    hv.copies.resize(nreg - h->host_regions);
+    for (uint64_t v = 0; v < nreg; v++) {
+        if (v < h->host_regions) {
+            hv.ptr[v] = region(h, v);
+            continue;
+        }
+        auto &c = hv.copies[v - h->host_regions];
+        c.resize(slice);
+        if (fetch) SIM_CUDA_TRY(h, cudaMemcpy(c.data(), region(h, v), sizeof(float2) * slice, cudaMemcpyDeviceToHost));
+        hv.ptr[v] = c.data();
+    }
+    return SIM_OK;
+}
+
+int host_view_write_back(sim_t *h, HostView &hv)
+{
+    const uint64_t slice = 1ull << (h->n - h->s);
+    for (uint64_t v = h->host_regions; v < (1ull << h->s); v++)
+        SIM_CUDA_TRY(h, cudaMemcpy(region(h, v), hv.copies[v - h->host_regions].data(), sizeof(float2) * slice,
+                                   cudaMemcpyHostToDevice));
+    return SIM_OK;
+}
+
 }  // namespace
 
 int host_store_create(sim_t *h, const sim_opts &o)
@@ -81,13 +127,28 @@ int host_store_create(sim_t *h, const sim_opts &o)
     if (h->nslots < 2 || h->nslots > sim_s::kMaxSlots)
         return fail(nullptr, SIM_E_INVAL, "sim_create(host store): slots=%d outside 2..%d", h->nslots,
                     sim_s::kMaxSlots);
-    cudaError_t e = cudaHostAlloc(&h->h_store, sizeof(float2) * h->amps, cudaHostAllocDefault);
-    if (e != cudaSuccess) {
-        h->h_store = nullptr;
-        return fail(nullptr, SIM_E_NOMEM_HOST, "sim_create(host store): pinning %llu bytes: %s",
-                    (unsigned long long)(sizeof(float2) * h->amps), cudaGetErrorString(e));
+    const uint64_t slice = 1ull << (n - s), nreg = 1ull << s;
+    if (o.store_device_regions < 0 || (uint64_t)o.store_device_regions > nreg)
+        return fail(nullptr, SIM_E_INVAL, "sim_create(host store): store_device_regions=%d outside 0..%llu",
+                    o.store_device_regions, (unsigned long long)nreg);
+    h->host_regions = nreg - (uint64_t)o.store_device_regions;
+    cudaError_t e = cudaSuccess;
+    if (h->host_regions) {
+        e = cudaHostAlloc(&h->h_store, sizeof(float2) * slice * h->host_regions, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            h->h_store = nullptr;
+            return fail(nullptr, SIM_E_NOMEM_HOST, "sim_create(host store): pinning %llu bytes: %s",
+                        (unsigned long long)(sizeof(float2) * slice * h->host_regions), cudaGetErrorString(e));
+        }
     }
-    const uint64_t slice = 1ull << (n - s);
+    if (o.store_device_regions) {
+        e = cudaMalloc(&h->d_store, sizeof(float2) * slice * (uint64_t)o.store_device_regions);
+        if (e != cudaSuccess) {
+            h->d_store = nullptr;
+            return fail(nullptr, SIM_E_NOMEM_DEV, "sim_create(host store): %d device regions: %s",
+                        o.store_device_regions, cudaGetErrorString(e));
+        }
+    }
     for (int i = 0; i < h->nslots; i++) {
         e = cudaMalloc(&h->d_slot[i], sizeof(float2) * slice);
         if (e != cudaSuccess)
@@ -124,6 +185,7 @@ void host_store_release(sim_t *h)
     if (h->st_in) cudaStreamDestroy(h->st_in);
     if (h->st_out) cudaStreamDestroy(h->st_out);
     if (h->h_store) cudaFreeHost(h->h_store);
+    if (h->d_store) cudaFree(h->d_store);
     if (h->h_partials) cudaFreeHost(h->h_partials);
 }
 
@@ -145,12 +207,12 @@ static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int sl
             if (h->out_set[i] >= 0 && (h->out_set[i] != set || h->out_val[i] == value))
                 SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_out[i], 0));
         if (set == 0) {
-            SIM_CUDA_TRY(h, cudaMemcpyAsync(dev, h->h_store + value * slice, sizeof(float2) * slice,
-                                            cudaMemcpyHostToDevice, h->st_in));
+            SIM_CUDA_TRY(h, cudaMemcpyAsync(dev, region(h, value), sizeof(float2) * slice, cudaMemcpyDefault,
+                                            h->st_in));
         } else {
             for (uint64_t v = 0; v < (1ull << s); v++)
-                SIM_CUDA_TRY(h, cudaMemcpyAsync(dev + v * file, h->h_store + v * slice + value * file,
-                                                sizeof(float2) * file, cudaMemcpyHostToDevice, h->st_in));
+                SIM_CUDA_TRY(h, cudaMemcpyAsync(dev + v * file, region(h, v) + value * file, sizeof(float2) * file,
+                                                cudaMemcpyDefault, h->st_in));
         }
         SIM_CUDA_TRY(h, cudaEventRecord(h->ev_in[slot], h->st_in));
         SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0));
@@ -158,12 +220,12 @@ static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int sl
         SIM_CUDA_TRY(h, cudaEventRecord(h->ev_done[slot], h->stream));
         SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_out, h->ev_done[slot], 0));
         if (set == 0) {
-            SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_store + value * slice, dev, sizeof(float2) * slice,
-                                            cudaMemcpyDeviceToHost, h->st_out));
+            SIM_CUDA_TRY(h, cudaMemcpyAsync(region(h, value), dev, sizeof(float2) * slice, cudaMemcpyDefault,
+                                            h->st_out));
         } else {
             for (uint64_t v = 0; v < (1ull << s); v++)
-                SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_store + v * slice + value * file, dev + v * file,
-                                                sizeof(float2) * file, cudaMemcpyDeviceToHost, h->st_out));
+                SIM_CUDA_TRY(h, cudaMemcpyAsync(region(h, v) + value * file, dev + v * file, sizeof(float2) * file,
+                                                cudaMemcpyDefault, h->st_out));
         }
         SIM_CUDA_TRY(h, cudaEventRecord(h->ev_out[slot], h->st_out));
         h->out_set[slot] = set;
@@ -184,9 +246,16 @@ int host_reset(sim_t *h, uint64_t basis)
 {
     int rc = host_sync_all(h);
     if (rc != SIM_OK) return rc;
-    float2 *st = h->h_store;
-    parallel_for(h->amps, [st](uint64_t a, uint64_t b) { std::memset(st + a, 0, sizeof(float2) * (b - a)); });
-    st[logical_to_physical(h, basis)] = make_float2(1.f, 0.f);
+    const uint64_t slice = 1ull << (h->n - h->s), nreg = 1ull << h->s;
+    if (h->host_regions) {
+        float2 *st = h->h_store;
+        parallel_for(slice * h->host_regions,
+                     [st](uint64_t a, uint64_t b) { std::memset(st + a, 0, sizeof(float2) * (b - a)); });
+    }
+    if (h->d_store) SIM_CUDA_TRY(h, cudaMemset(h->d_store, 0, sizeof(float2) * slice * (nreg - h->host_regions)));
+    const uint64_t p = logical_to_physical(h, basis);
+    const float2 one = make_float2(1.f, 0.f);
+    SIM_CUDA_TRY(h, cudaMemcpy(region(h, p / slice) + p % slice, &one, sizeof(float2), cudaMemcpyDefault));
     return SIM_OK;
 }
 
@@ -194,17 +263,24 @@ int host_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dty
 {
     int rc = host_sync_all(h);
     if (rc != SIM_OK) return rc;
-    const float2 *st = h->h_store;
+    HostView hv;
+    if ((rc = host_view(h, hv, true)) != SIM_OK) return rc;
+    const int lb = h->n - h->s;
+    const uint64_t mask = (1ull << lb) - 1;
+    auto at = [&](uint64_t j) {
+        const uint64_t p = physical ? first + j : logical_to_physical(h, first + j);
+        return hv.ptr[p >> lb][p & mask];
+    };
     if (dtype == SIM_C64) {
         float2 *o = (float2 *)out;
         parallel_for(count, [&](uint64_t a, uint64_t b) {
-            for (uint64_t j = a; j < b; j++) o[j] = st[physical ? first + j : logical_to_physical(h, first + j)];
+            for (uint64_t j = a; j < b; j++) o[j] = at(j);
         });
     } else {
         double *o = (double *)out;
         parallel_for(count, [&](uint64_t a, uint64_t b) {
             for (uint64_t j = a; j < b; j++) {
-                const float2 v = st[physical ? first + j : logical_to_physical(h, first + j)];
+                const float2 v = at(j);
                 o[2 * j] = v.x;
                 o[2 * j + 1] = v.y;
             }
@@ -217,12 +293,19 @@ int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int phy
 {
     int rc = host_sync_all(h);
     if (rc != SIM_OK) return rc;
-    float2 *st = h->h_store;
+    HostView hv;
+    // device regions are only partly overwritten unless the range covers them: fetch them first
+    if ((rc = host_view(h, hv, true)) != SIM_OK) return rc;
+    const int lb = h->n - h->s;
+    const uint64_t mask = (1ull << lb) - 1;
     const float2 *in = (const float2 *)src;
     parallel_for(count, [&](uint64_t a, uint64_t b) {
-        for (uint64_t j = a; j < b; j++) st[physical ? first + j : logical_to_physical(h, first + j)] = in[j];
+        for (uint64_t j = a; j < b; j++) {
+            const uint64_t p = physical ? first + j : logical_to_physical(h, first + j);
+            hv.ptr[p >> lb][p & mask] = in[j];
+        }
     });
-    return SIM_OK;
+    return host_view_write_back(h, hv);
 }
 
 int host_reduce(sim_t *h, double *s1, double *s2)

@@ -32,11 +32,14 @@ def expected_slice(oracle_mod, psi, n, sliced, other, value):
     return oracle_mod.permute(sl, perm)
 
 
-@pytest.mark.parametrize("n,s,set_a,set_b,slots", [(10, 2, [3, 8], [0, 6], 2), (14, 3, [13, 1, 7], [4, 11, 2], 3),
-                                                   (12, 1, [11], [10], 4)])
-def test_slice_streaming_bit_exact(pkg, oracle_mod, n, s, set_a, set_b, slots):
+@pytest.mark.parametrize("n,s,set_a,set_b,slots,dev_regions", [
+    (10, 2, [3, 8], [0, 6], 2, 0), (14, 3, [13, 1, 7], [4, 11, 2], 3, 0), (12, 1, [11], [10], 4, 0),
+    # hybrid stores: the top regions (values of set A) in device memory, up to all of them
+    (10, 2, [3, 8], [0, 6], 2, 1), (14, 3, [13, 1, 7], [4, 11, 2], 3, 5), (12, 1, [11], [10], 4, 2)])
+def test_slice_streaming_bit_exact(pkg, oracle_mod, n, s, set_a, set_b, slots, dev_regions):
     psi = si.random_state(n, n)
-    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=slots)
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=slots,
+                       store_device_regions=dev_regions)
     try:
         pkg.sim_load_amplitudes(h, psi)
         assert np.array_equal(pkg.sim_amplitudes(h).view(np.uint64), psi.view(np.uint64))
@@ -57,8 +60,8 @@ def test_slice_streaming_bit_exact(pkg, oracle_mod, n, s, set_a, set_b, slots):
         pkg.sim_destroy(h)
 
 
-@pytest.mark.parametrize("grid,cycles,s", [((4, 4), 10, 2), ((4, 6), 12, 3)])
-def test_streamed_phases_equal_resident_bit_exact(pkg, oracle_mod, grid, cycles, s):
+@pytest.mark.parametrize("grid,cycles,s,dev_regions", [((4, 4), 10, 2, 0), ((4, 6), 12, 3, 0), ((4, 6), 12, 3, 5)])
+def test_streamed_phases_equal_resident_bit_exact(pkg, oracle_mod, grid, cycles, s, dev_regions):
     # Streaming only moves data: with the resident state stored in the host store's bit
     # layout, every block sees the same target order, matrix and kernel, so the two runs agree
     # bit for bit.
@@ -67,7 +70,8 @@ def test_streamed_phases_equal_resident_bit_exact(pkg, oracle_mod, grid, cycles,
     set_a, set_b = list(range(s)), list(range(n - s, n))  # the two ends of the lattice
     ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=4)
     hr = pkg.sim_create(n)
-    hh = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b)
+    hh = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b,
+                        store_device_regions=dev_regions)
     try:
         assert pkg.sim_phases_info(ph)[0] >= 2
         pkg.sim_permute(hr, list(pkg.sim_info(hh)[2]))
@@ -98,6 +102,25 @@ def test_streamed_phases_scrambled_sets_match_oracle(pkg, oracle_mod):
         pkg.sim_destroy(h)
         pkg.sim_phases_destroy(ph)
     assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= TOL_FP32
+
+
+def test_hybrid_store_tensor_core_phases_match_oracle(pkg, oracle_mod):
+    # the default arithmetic through a hybrid store: 3 of 8 regions on the device
+    circ = si.sycamore_circuit(si.Grid(4, 6), cycles=14, seed=4)
+    n, s = circ.n_qubits, 3
+    set_a, set_b = [0, 1, 2], [21, 22, 23]
+    ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3, store_device_regions=3)
+    try:
+        pkg.sim_run_phases(h, ph)
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+        norm, s2, _ = pkg.sim_reduce(h)
+    finally:
+        pkg.sim_destroy(h)
+        pkg.sim_phases_destroy(ph)
+    want = oracle_mod.run_circuit(circ)
+    assert np.linalg.norm(got - want) <= TOL_FP32
+    assert abs(norm - 1.0) < 1e-5
 
 
 def test_host_store_rejects_sliced_targets_and_device_calls(pkg):
