@@ -61,12 +61,15 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--serving-circuits", type=int, default=200)
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the CPU oracle on one and on all host cores for the 12-, 30- (sample), "
+                         "28- (sample) and 24-qubit circuits, print one JSON line, and exit")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
                          "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
                          "mma.sync, high then mixed targets; with tcgen05, 256- and 128-group tiles and one "
-                         "target below bit 4), k=4 on bits 0-3 in the default mode, a high-bit permutation "
-                         "and a reduction, each twice, then exit; meant to run under ncu")
+                         "target below bit 4), k=4 on bits 0-3 in the default mode, a high-bit and a "
+                         "low<->top permutation and a reduction, each twice, then exit; meant to run under ncu")
     return ap.parse_args()
 
 
@@ -177,6 +180,40 @@ def cpu_baseline(circ, sample_gates: int, steps: int = 1):
             "sample": f"first {sample_gates} of {circ.n_gates} gates of {circ.name} on the full "
                       f"2^{circ.n_qubits} complex128 state, {steps} run(s)",
             "seconds": sum(times)}
+
+
+def oracle_table():
+    """The oracle (complex128, gate by gate) on one host thread and on all of them, for the
+    12-qubit circuit, samples of the 30-qubit circuit and of the 28-qubit sub-lattice circuit,
+    and a 24-qubit serving-size circuit: wall time and amplitude updates/s."""
+    import oracle
+    import syc_inputs as si
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    try:
+        cpu = next((ln.split(":", 1)[1].strip() for ln in subprocess.run(
+            ["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines()
+            if ln.startswith("Model name")), "unknown")
+    except Exception:
+        cpu = "unknown"
+    cases = [("12 qubits, 3x4 grid, 8 cycles (whole circuit)", si.workload_circuit("syc12_3x4_d8", 0), None),
+             ("30 qubits, 5x6 grid, 20 cycles (first 12 gates)", si.workload_circuit("syc30_5x6_d20", 0), 12),
+             ("28 qubits, 4x7 grid, 20 cycles (first 24 gates)", si.workload_circuit("syc28_4x7_d20", 0), 24),
+             ("24 qubits, 4x6 grid, 14 cycles (whole circuit)", si.sycamore_circuit(si.Grid(4, 6), 14, seed=5), None)]
+    rows = []
+    for threads in sorted({1, cores}):
+        oracle.set_threads(threads)
+        for name, circ, g in cases:
+            sample = circ if g is None else si.Circuit(circ.n_qubits, circ.gates[:g], name=circ.name)
+            psi = oracle.basis_state(circ.n_qubits, 0)
+            t0 = time.perf_counter()
+            oracle.apply_gates(psi, sample)
+            dt = time.perf_counter() - t0
+            del psi
+            rows.append({"case": name, "threads": threads, "gates": sample.n_gates, "seconds": dt,
+                         "amp_updates_per_s": float(1 << circ.n_qubits) * sample.n_gates / dt})
+    return {"cpu": cpu, "cores": cores, "rows": rows}
 
 
 def serving_run(count: int, device: int):
@@ -524,11 +561,12 @@ def kernel_case():
         u = si.random_unitary(len(t), 2)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3_TMEM)
-    perm = list(range(n))
-    for a, b in ((25, 10), (26, 11), (27, 12)):
-        perm[a], perm[b] = b, a
-    pkg.sim_permute(h, perm)
-    pkg.sim_permute(h, list(range(n)))
+    for pairs in (((25, 10), (26, 11), (27, 12)), ((0, 25), (1, 26), (2, 27))):  # high-high, low<->top
+        perm = list(range(n))
+        for a, b in pairs:
+            perm[a], perm[b] = b, a
+        pkg.sim_permute(h, perm)
+        pkg.sim_permute(h, list(range(n)))
     pkg.sim_reduce(h)
     pkg.sim_reduce(h)
     pkg.sim_destroy(h)
@@ -539,6 +577,8 @@ def main():
     args = parse()
     if args.kernel_case:
         kernel_case()
+    elif args.oracle_table:
+        print(json.dumps(oracle_table()), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -19,14 +19,14 @@
 
 #include "internal.h"
 
-// Measured on 2^30 amplitudes: 16-byte accesses 13-17 % faster on every pattern; minimum tiles of
-// 2^11-2^12 amplitudes help tiles that permute in place a little and tile pairs much less
-// (persistent CTAs looping over tile pairs were slower still).
-#ifndef SYCSIM_PERM_VEC
-#define SYCSIM_PERM_VEC 1
-#endif
+// Measured on 2^30 amplitudes: 16-byte accesses 13-17 % faster than 8-byte on every pattern;
+// minimum tiles of 2^11-2^12 amplitudes help tiles that permute in place a little and tile pairs
+// much less (persistent CTAs looping over tile pairs were slower still).
 #ifndef SYCSIM_PERM_TILE
 #define SYCSIM_PERM_TILE 10  // minimum tile: 2^SYCSIM_PERM_TILE amplitudes
+#endif
+#ifndef SYCSIM_PERM_TILE_SAME
+#define SYCSIM_PERM_TILE_SAME 12  // the same when no tile pairs swap (measured best of 10..13)
 #endif
 
 namespace sycsim {
@@ -43,6 +43,10 @@ struct PermGeom {
     int trivial_in;               // sig is the identity
     uint32_t fsw[1 << kMaxRow];   // row r -> XOR applied to its low index (bank spreading)
     uint64_t rowoff[1 << kMaxRow];
+    // the in-tile maps are XOR-linear in the local index p: their values on each single bit
+    uint64_t lin_off[16];   // global offset of p (row offset + low index)
+    uint32_t lin_sidx[16];  // shared-memory slot of p (row-XOR swizzle)
+    uint32_t lin_src[16];   // shared-memory slot of the amplitude that lands at p (swizzle o sig)
 };
 
 __device__ __forceinline__ uint64_t insert_zero_bits_p(uint64_t x, const int *pos, int cnt)
@@ -68,85 +72,77 @@ __global__ void __launch_bounds__(256) k_permute_pass(PermGeom g)
     const bool same = baseA == baseB;
     if (same && g.trivial_in) return;  // nothing in this tile moves
 
-    const int T = 1 << (g.LB + g.q);
-    const uint32_t lbmask = (1u << g.LB) - 1;
-    auto sidx = [&](uint32_t p) {
-        const uint32_t r = p >> g.LB;
-        return (r << g.LB) | ((p & lbmask) ^ g.fsw[r]);
-    };
-#if SYCSIM_PERM_VEC
-    // two amplitudes per global access (rows are >= 32 amplitudes and start at multiples of
-    // 2^LB, so an even in-tile index is 16-byte aligned); shared memory per amplitude
-    const int nloc = g.LB + g.q;
-    auto sig = [&](uint32_t p) {
-        uint32_t s = 0;
-        for (int x = 0; x < nloc; ++x) s |= ((p >> x) & 1u) << g.sig[x];
-        return s;
-    };
-    for (int p = 2 * threadIdx.x; p < T; p += 2 * blockDim.x) {
-        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
+    // Thread t handles the amplitude pairs p = 2t + j * 2 * blockDim: the part of each map that
+    // depends on 2t is computed once, the part that depends on j is uniform across the warp.
+    const int nloc = g.LB + g.q, T = 1 << nloc;
+    const uint32_t step = 2 * blockDim.x, p0 = 2 * threadIdx.x;
+    int sbits = 0;
+    while ((1u << sbits) < step) ++sbits;
+    uint64_t off0 = 0;
+    uint32_t ld0 = 0, st0 = 0;
+    for (int x = 1; x < sbits && x < nloc; ++x)
+        if ((p0 >> x) & 1) {
+            off0 += g.lin_off[x];
+            ld0 ^= g.lin_sidx[x];
+            st0 ^= g.lin_src[x];
+        }
+    const uint32_t ld1 = g.lin_sidx[0], st1 = g.lin_src[0];  // the odd amplitude of the pair
+    for (uint32_t hi = 0; p0 + hi < (uint32_t)T; hi += step) {
+        uint64_t offj = 0;
+        uint32_t ldj = 0;
+        for (int x = sbits; x < nloc; ++x)
+            if ((hi >> x) & 1) {
+                offj += g.lin_off[x];
+                ldj ^= g.lin_sidx[x];
+            }
+        const uint64_t off = off0 + offj;
+        const uint32_t l = ld0 ^ ldj;
         const float4 a = __ldcs(reinterpret_cast<const float4 *>(g.psi + baseA + off));
-        sm[sidx(p)] = make_float2(a.x, a.y);
-        sm[sidx(p + 1)] = make_float2(a.z, a.w);
+        sm[l] = make_float2(a.x, a.y);
+        sm[l ^ ld1] = make_float2(a.z, a.w);
         if (!same) {
             const float4 b = __ldcs(reinterpret_cast<const float4 *>(g.psi + baseB + off));
-            sm[T + sidx(p)] = make_float2(b.x, b.y);
-            sm[T + sidx(p + 1)] = make_float2(b.z, b.w);
+            sm[T + l] = make_float2(b.x, b.y);
+            sm[T + (l ^ ld1)] = make_float2(b.z, b.w);
         }
     }
     __syncthreads();
-    for (int p = 2 * threadIdx.x; p < T; p += 2 * blockDim.x) {
-        const uint32_t s0 = sig(p), s1 = sig(p + 1);
-        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
-        const float2 x = sm[sidx(s0)], y = sm[sidx(s1)];
+    for (uint32_t hi = 0; p0 + hi < (uint32_t)T; hi += step) {
+        uint64_t offj = 0;
+        uint32_t stj = 0;
+        for (int x = sbits; x < nloc; ++x)
+            if ((hi >> x) & 1) {
+                offj += g.lin_off[x];
+                stj ^= g.lin_src[x];
+            }
+        const uint64_t off = off0 + offj;
+        const uint32_t s0 = st0 ^ stj, s1 = s0 ^ st1;
+        const float2 x = sm[s0], y = sm[s1];
         if (same) {
             __stcs(reinterpret_cast<float4 *>(g.psi + baseA + off), make_float4(x.x, x.y, y.x, y.y));
         } else {
-            const float2 u = sm[T + sidx(s0)], v = sm[T + sidx(s1)];
+            const float2 u = sm[T + s0], v = sm[T + s1];
             __stcs(reinterpret_cast<float4 *>(g.psi + baseB + off), make_float4(x.x, x.y, y.x, y.y));
             __stcs(reinterpret_cast<float4 *>(g.psi + baseA + off), make_float4(u.x, u.y, v.x, v.y));
         }
     }
-#else
-    for (int p = threadIdx.x; p < T; p += blockDim.x) {
-        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
-        sm[sidx(p)] = __ldcs(g.psi + baseA + off);
-        if (!same) sm[T + sidx(p)] = __ldcs(g.psi + baseB + off);
-    }
-    __syncthreads();
-    const int nloc = g.LB + g.q;
-    for (int p = threadIdx.x; p < T; p += blockDim.x) {
-        uint32_t s = 0;
-        for (int x = 0; x < nloc; ++x) s |= ((p >> x) & 1u) << g.sig[x];
-        const uint64_t off = g.rowoff[p >> g.LB] + (p & lbmask);
-        if (same) {
-            __stcs(g.psi + baseA + off, sm[sidx(s)]);
-        } else {
-            __stcs(g.psi + baseB + off, sm[sidx(s)]);
-            __stcs(g.psi + baseA + off, sm[T + sidx(s)]);
-        }
-    }
-#endif
 }
 
 // One involution pass; inv[b] = partner of bit b (inv[b] == b: fixed).
-int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
+// Geometry of one involution pass for tiles of at least 2^min_tile amplitudes.
+int build_geom(float2 *psi, int nbits, const int *inv, int min_tile, PermGeom &g)
 {
-    bool any = false;
-    for (int b = 0; b < nbits; b++) any |= inv[b] != b;
-    if (!any) return 0;
-
-    // low block: smallest LB >= min(5, nbits) with LB + q >= min(SYCSIM_PERM_TILE, nbits)
+    // low block: smallest LB >= min(5, nbits) with LB + q >= min(min_tile, nbits)
     int LB = std::min(5, nbits), q = 0;
     for (;; LB++) {
         q = 0;
         for (int b = 0; b < LB; b++)
             if (inv[b] >= LB) q++;
-        if (LB + q >= std::min(SYCSIM_PERM_TILE, nbits) || LB == nbits) break;
+        if (LB + q >= std::min(min_tile, nbits) || LB == nbits) break;
     }
     if (q > kMaxRow) return -2;
 
-    PermGeom g{};
+    g = PermGeom{};
     g.psi = psi;
     g.LB = LB;
     g.q = q;
@@ -191,6 +187,35 @@ int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
         g.rowoff[r] = o;
         g.fsw[r] = f & ((1u << LB) - 1);
     }
+    // values of the XOR-linear in-tile maps on each single local bit
+    const int nloc = LB + q;
+    auto sidx_h = [&](uint32_t p) {
+        const uint32_t r = p >> LB;
+        return (r << LB) | ((p & ((1u << LB) - 1)) ^ g.fsw[r]);
+    };
+    for (int x = 0; x < nloc; x++) {
+        const uint32_t p = 1u << x;
+        g.lin_off[x] = x < LB ? (uint64_t)p : g.rowoff[p >> LB];
+        g.lin_sidx[x] = sidx_h(p);
+        g.lin_src[x] = sidx_h(1u << g.sig[x]);  // the amplitude landing at p came from slot sig(p)
+    }
+    return 0;
+}
+
+int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
+{
+    bool any = false;
+    for (int b = 0; b < nbits; b++) any |= inv[b] != b;
+    if (!any) return 0;
+    PermGeom g;
+    const int rc = build_geom(psi, nbits, inv, SYCSIM_PERM_TILE, g);
+    if (rc != 0) return rc;
+    // tiles that only permute in place (no tile pairs) gain from more work per CTA
+    if (g.nhh == 0 && SYCSIM_PERM_TILE_SAME > SYCSIM_PERM_TILE) {
+        PermGeom big;
+        if (build_geom(psi, nbits, inv, SYCSIM_PERM_TILE_SAME, big) == 0) g = big;
+    }
+    const int LB = g.LB, q = g.q;
     const uint64_t tiles = 1ull << (nbits - LB - q);
     const size_t smem = (g.nhh ? 2 : 1) * sizeof(float2) << (LB + q);  // a tile pair, or one tile
     if (smem > 48 * 1024 &&
