@@ -614,7 +614,6 @@ void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, in
 int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                         int precision, const void *d_staged, cudaStream_t st)
 {
-    h->launches++;
     int rc;
     switch (block_path(nbits, k, tpos, precision)) {
     case BlockPath::Tcgen05: rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, d_staged, st); break;

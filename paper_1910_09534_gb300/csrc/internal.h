@@ -81,6 +81,10 @@ struct sim_s {
     float2 *h_store = nullptr;   // pinned: the store's regions 0 .. host_regions-1
     float2 *d_store = nullptr;   // device: regions host_regions .. 2^s - 1 (hybrid store)
     uint64_t host_regions = 0;   // regions (one per value of set A, 2^(n-s) amplitudes each) on the host
+    cudaEvent_t ev_inplace = nullptr;  // after the latest in-place compute on a device region
+    char *h_ops = nullptr;             // pinned: a phase's staged block operands, uploaded once
+    size_t h_ops_bytes = 0;
+    cudaEvent_t ev_ops = nullptr;      // after the upload from h_ops
     int nslots = 0;
     float2 *d_slot[kMaxSlots] = {};
     cudaStream_t st_in = nullptr, st_out = nullptr;

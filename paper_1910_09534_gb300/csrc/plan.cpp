@@ -329,7 +329,6 @@ int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out)
     const cudaError_t ec = cudaStreamEndCapture(h->stream, &g->graph);  // always ends the capture
     if (rc != SIM_OK || ec != cudaSuccess) return cleanup(rc != SIM_OK ? rc : SIM_E_CUDA, "capture");
     if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) return cleanup(SIM_E_CUDA, "instantiate");
-    h->launches -= (uint64_t)blocks.size();  // captured, not run
     *out = g;
     return SIM_OK;
 }

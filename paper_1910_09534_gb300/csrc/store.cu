@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <thread>
 #include <vector>
@@ -165,6 +166,10 @@ int host_store_create(sim_t *h, const sim_opts &o)
                             cudaGetErrorString(e));
             cudaEventRecord(*ev, h->stream);
         }
+    if ((e = cudaEventCreateWithFlags(&h->ev_inplace, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_ops, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(nullptr, SIM_E_CUDA, "sim_create(host store): events: %s", cudaGetErrorString(e));
+    cudaEventRecord(h->ev_inplace, h->stream);
     e = cudaHostAlloc(&h->h_partials, sizeof(double) * 2 * ((size_t)1 << s), cudaHostAllocDefault);
     if (e != cudaSuccess) {
         h->h_partials = nullptr;
@@ -182,6 +187,12 @@ void host_store_release(sim_t *h)
         for (cudaEvent_t ev : {h->ev_in[i], h->ev_done[i], h->ev_out[i]})
             if (ev) cudaEventDestroy(ev);
     }
+    if (h->ev_inplace) cudaEventDestroy(h->ev_inplace);
+    if (h->ev_ops) {
+        cudaEventSynchronize(h->ev_ops);
+        cudaEventDestroy(h->ev_ops);
+    }
+    if (h->h_ops) cudaFreeHost(h->h_ops);
     if (h->st_in) cudaStreamDestroy(h->st_in);
     if (h->st_out) cudaStreamDestroy(h->st_out);
     if (h->h_store) cudaFreeHost(h->h_store);
@@ -206,6 +217,8 @@ static int enqueue_slice_copy(sim_t *h, int set, uint64_t value, int dir, int sl
         for (int i = 0; i < h->nslots; i++)
             if (h->out_set[i] >= 0 && (h->out_set[i] != set || h->out_val[i] == value))
                 SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_out[i], 0));
+        // and no device region it reads may still be computed on in place (by an earlier phase)
+        SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->st_in, h->ev_inplace, 0));
         if (set == 0) {
             SIM_CUDA_TRY(h, cudaMemcpyAsync(dev, region(h, value), sizeof(float2) * slice, cudaMemcpyDefault,
                                             h->st_in));
@@ -396,8 +409,10 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         int k;
         int tpos[kMaxK];
         std::vector<float2> mat;
+        size_t bytes = 0, off = 0;  // staged operands
     };
     std::vector<Prepared> blocks(p->blocks.size());
+    size_t staged_total = 0;
     for (size_t i = 0; i < p->blocks.size(); i++) {
         const PlanBlock &b = p->blocks[i];
         Prepared &pb = blocks[i];
@@ -406,20 +421,84 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         int rc = prepare_block_map(h, pb.k, b.qubits.data(), b.mat.data(), h->slice_phys[set], nl,
                                    pb.tpos, pb.mat.data());
         if (rc != SIM_OK) return rc;
+        pb.bytes = block_staged_bytes(nl, pb.k, pb.tpos, p->precision);
+        pb.off = staged_total;
+        staged_total += (pb.bytes + 255) & ~size_t(255);
     }
-    const uint64_t nsl = 1ull << h->s;
-    for (uint64_t v = 0; v < nsl; v++) {
-        const int slot = (int)(v % h->nslots);
-        int rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
-        if (rc != SIM_OK) return rc;
+    // Every slice gets the same blocks: their tensor-core operands (and 6-qubit matrices) are
+    // uploaded once for the phase, not once per block and slice -- such small copies would queue
+    // behind the slice transfers on the copy engines and hold back every kernel.
+    char *d_staged = nullptr;
+    if (staged_total) {
+        // pinned source, reused once its previous upload is done (no wait on the device's work)
+        SIM_CUDA_TRY(h, cudaEventSynchronize(h->ev_ops));
+        if (staged_total > h->h_ops_bytes) {
+            if (h->h_ops) cudaFreeHost(h->h_ops);
+            h->h_ops = nullptr;
+            h->h_ops_bytes = 0;
+            if (cudaHostAlloc(reinterpret_cast<void **>(&h->h_ops), 2 * staged_total, cudaHostAllocDefault) != cudaSuccess) {
+                h->h_ops = nullptr;
+                return fail(h, SIM_E_NOMEM_HOST, "sim_run_phase: staging buffer");
+            }
+            h->h_ops_bytes = 2 * staged_total;
+        }
+        for (const Prepared &pb : blocks)
+            if (pb.bytes) block_build_staged(nl, pb.k, pb.tpos, pb.mat.data(), p->precision, h->h_ops + pb.off);
+        SIM_CUDA_TRY(h, cudaMallocAsync(reinterpret_cast<void **>(&d_staged), staged_total, h->stream));
+        SIM_CUDA_TRY(h, cudaMemcpyAsync(d_staged, h->h_ops, staged_total, cudaMemcpyHostToDevice, h->stream));
+        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_ops, h->stream));
+    }
+    auto release = [&](int rc) {  // the staged operands go once the phase's last kernel is queued
+        if (d_staged) cudaFreeAsync(d_staged, h->stream);
+        return rc;
+    };
+    auto apply_blocks = [&](float2 *psi) {
         for (const Prepared &pb : blocks) {
-            rc = enqueue_block_on(h, h->d_slot[slot], nl, pb.k, pb.tpos, pb.mat.data(), p->precision,
-                                  h->stream);
+            const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nl), h->stream);
+            const int rc = launch_block_staged(h, psi, nl, pb.k, pb.tpos, pb.mat.data(), p->precision,
+                                               d_staged + pb.off, h->stream);
+            prof_end(h, ps, h->stream);
             if (rc != SIM_OK) return rc;
         }
-        rc = enqueue_slice_copy(h, set, v, SIM_D2H, slot);
-        if (rc != SIM_OK) return rc;
+        return (int)SIM_OK;
+    };
+    const uint64_t nsl = 1ull << h->s;
+    // With set A sliced, a slice is one region of the store, laid out [rest | B] like a slot: the
+    // regions in device memory are computed in place (no copies), interleaved with the host
+    // slices so that host-link copies overlap that compute.  With set B sliced every slice
+    // gathers a file from every region and goes through a slot.
+    const bool inplace = set == 0 && h->host_regions < nsl;
+    std::vector<uint64_t> order;
+    if (inplace) {
+        // the previous phase's copy-outs may have written into the device regions
+        for (int i = 0; i < h->nslots; i++)
+            if (cudaStreamWaitEvent(h->stream, h->ev_out[i], 0) != cudaSuccess) return release(fail(h, SIM_E_CUDA, "sim_run_phase: event wait"));
+        for (uint64_t i = 0; i < nsl; i++) {
+            if (h->host_regions + i < nsl) order.push_back(h->host_regions + i);  // a device region
+            if (i < h->host_regions) order.push_back(i);
+        }
+    } else {
+        for (uint64_t v = 0; v < nsl; v++) order.push_back(v);
     }
+    int next_slot = 0;
+    for (const uint64_t v : order) {
+        if (inplace && v >= h->host_regions) {
+            const int rc = apply_blocks(region(h, v));
+            if (rc != SIM_OK) return release(rc);
+            continue;
+        }
+        const int slot = next_slot;
+        next_slot = (next_slot + 1) % h->nslots;
+        int rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
+        if (rc != SIM_OK) return release(rc);
+        if ((rc = apply_blocks(h->d_slot[slot])) != SIM_OK) return release(rc);
+        rc = enqueue_slice_copy(h, set, v, SIM_D2H, slot);
+        if (rc != SIM_OK) return release(rc);
+    }
+    release(SIM_OK);
+    // copy-ins from now on (the next phase reads every region) follow the in-place computes; this
+    // phase's own copy-ins read host regions only and did not wait for them
+    if (inplace) SIM_CUDA_TRY(h, cudaEventRecord(h->ev_inplace, h->stream));
     // later work on the handle's stream (and sim_sync) follows the last copy-out
     for (int i = 0; i < h->nslots; i++) SIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_out[i], 0));
     return SIM_OK;
