@@ -332,6 +332,18 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p);
 typedef struct sim_phases_s sim_phases_t;
 int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
                       int slice_bits, const int *set_a, const int *set_b, sim_phases_t **out);
+/* Choose the two sliced sets for a circuit (not spelled out in the paper, which fixes them by
+ * hand at the two ends of the lattice, Sect. 4): every pair of disjoint windows of slice_bits
+ * consecutive qubit numbers (on a row-major lattice: the two ends, the middle rows, ...) that no
+ * gate couples is split into phases as sim_phases_create does, each phase grouped into fused blocks
+ * (o->kmax, default 4), and scored phases * phase_weight + blocks; the best pair is written to
+ * set_a / set_b (slice_bits entries each), its phase and block counts to *n_phases / *n_blocks
+ * (either may be NULL).  phase_weight is the cost of streaming the state out and back once, in
+ * fused passes (<= 0: 32, about HBM / host-link bandwidth on a GB300 node).  Host only; no device
+ * is touched.  SIM_E_INVAL for bad arguments or when no pair can phase the circuit. */
+int sim_phases_choose_sets(int n_qubits, int n_gates, const sim_gate *gates, int slice_bits,
+                           const sim_plan_opts *o, double phase_weight, int *set_a, int *set_b, int *n_phases,
+                           int *n_blocks);
 int sim_phases_destroy(sim_phases_t *ph);
 int sim_phases_info(const sim_phases_t *ph, int *n_phases, int *total_blocks);
 int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **plan);

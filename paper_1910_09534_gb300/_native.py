@@ -133,6 +133,9 @@ _SIGS = {
     "sim_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_phases_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_phases_choose_sets": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sim_phases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_phases_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_phases_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -438,6 +441,21 @@ def sim_phases_create(n_qubits: int, gates: np.ndarray, slice_bits: int, set_a, 
     _check(lib().sim_phases_create(n_qubits, int(g.size), _ptr(g), ctypes.byref(o), slice_bits, _ptr(a),
                                    _ptr(b), ctypes.byref(p)))
     return p
+
+
+def sim_phases_choose_sets(n_qubits: int, gates: np.ndarray, slice_bits: int, kmax: int = 4,
+                           phase_weight: float = 0.0):
+    """(set_a, set_b, n_phases, n_blocks) chosen for the circuit; host only."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    o = PlanOpts()
+    o.kmax = kmax
+    a = np.zeros(slice_bits, dtype=np.int32)
+    b = np.zeros(slice_bits, dtype=np.int32)
+    nph, nbl = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_phases_choose_sets(n_qubits, int(g.size), _ptr(g), slice_bits, ctypes.byref(o),
+                                        float(phase_weight), _ptr(a), _ptr(b), ctypes.byref(nph),
+                                        ctypes.byref(nbl)))
+    return [int(x) for x in a], [int(x) for x in b], nph.value, nbl.value
 
 
 def sim_phases_destroy(ph) -> None:

@@ -62,6 +62,139 @@ void left_multiply(std::vector<double> &U, int k, const double *G, int dg, int l
         left_multiply_t<2>(U.data(), 1 << k, G, l0, -1);
 }
 
+// Passes 1 and 2 of the planner over the gates gates[idx[0]], gates[idx[1]], ... (circuit order):
+// the units (a two-qubit gate with the single-qubit gates folded into it) and their greedy grouping
+// into blocks of at most kmax qubits (block qubits in order of first use).  Returns 0, or 1 with
+// *bad = the gate of unknown kind, or 2 with *bad = the gate with bad qubits.
+struct Unit {
+    int q[2];
+    int nq;
+    std::vector<int> gates;  // indices into the full gate list
+};
+
+struct Grouping {
+    std::vector<Unit> units;
+    std::vector<std::vector<int>> qubits;       // per block
+    std::vector<std::vector<int>> block_units;  // per block, in order
+};
+
+int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx, int kmax, Grouping &gr, int *bad)
+{
+    // Pass 1 (Sect. 3: single-qubit gates can be aggregated with neighbouring two-qubit gates):
+    // each single-qubit gate joins the next two-qubit gate on its qubit, or the previous one
+    // when none follows; a qubit without two-qubit gates keeps its own unit.
+    std::vector<Unit> &units = gr.units;
+    std::vector<std::vector<int>> pending(n_qubits);
+    std::vector<int> last2q(n_qubits, -1);
+    double G[32];
+    for (const int gi : idx) {
+        const sim_gate &g = gates[gi];
+        const int d = gate_matrix(g, G);
+        if (!d) {
+            *bad = gi;
+            return 1;
+        }
+        const int nq = d == 2 ? 1 : 2;
+        const int Q[2] = {g.q0, g.q1};
+        for (int i = 0; i < nq; i++)
+            if (Q[i] < 0 || Q[i] >= n_qubits || (i == 1 && Q[1] == Q[0])) {
+                *bad = gi;
+                return 2;
+            }
+        if (nq == 1) {
+            pending[g.q0].push_back(gi);
+            continue;
+        }
+        Unit u{{g.q0, g.q1}, 2, {}};
+        for (int i = 0; i < 2; i++) {
+            u.gates.insert(u.gates.end(), pending[Q[i]].begin(), pending[Q[i]].end());
+            pending[Q[i]].clear();
+            last2q[Q[i]] = (int)units.size();
+        }
+        u.gates.push_back(gi);
+        units.push_back(std::move(u));
+    }
+    for (int q = 0; q < n_qubits; q++) {
+        if (pending[q].empty()) continue;
+        if (last2q[q] >= 0) {
+            auto &gl = units[last2q[q]].gates;
+            gl.insert(gl.end(), pending[q].begin(), pending[q].end());
+        } else {
+            units.push_back(Unit{{q, -1}, 1, pending[q]});
+        }
+    }
+
+    // Pass 2: greedy grouping of the units into blocks of at most kmax qubits.
+    std::vector<int> last(n_qubits, -1);
+    for (int ui = 0; ui < (int)units.size(); ui++) {
+        const Unit &u = units[ui];
+        const int nq = u.nq;
+        const int *Q = u.q;
+        int lo = -1;
+        for (int i = 0; i < nq; i++) lo = std::max(lo, last[Q[i]]);
+        auto grown = [&](const std::vector<int> &bq) {
+            int add = 0;
+            for (int i = 0; i < nq; i++) add += std::find(bq.begin(), bq.end(), Q[i]) == bq.end();
+            return (int)bq.size() + add;
+        };
+        int chosen = -1;
+        if (lo >= 0 && grown(gr.qubits[lo]) <= kmax) chosen = lo;
+        for (int b = std::max(lo + 1, 0); chosen < 0 && b < (int)gr.qubits.size(); b++)
+            if (grown(gr.qubits[b]) <= kmax) chosen = b;
+        if (chosen < 0) {
+            gr.qubits.emplace_back();
+            gr.block_units.emplace_back();
+            chosen = (int)gr.qubits.size() - 1;
+        }
+        gr.block_units[chosen].push_back(ui);
+        std::vector<int> &bq = gr.qubits[chosen];
+        for (int i = 0; i < nq; i++)
+            if (std::find(bq.begin(), bq.end(), Q[i]) == bq.end()) bq.push_back(Q[i]);
+        for (int i = 0; i < nq; i++) last[Q[i]] = chosen;
+    }
+    return 0;
+}
+
+// Greedy phase split (Sect. 4): in a phase with set X sliced (which[q] == X), apply, in order,
+// every remaining gate that avoids X and every qubit already holding a deferred gate; the
+// deferred gates form the next phase's input, with the other set sliced.  Returns false if some
+// gates can never be applied (a gate coupling the two sets).
+bool split_phases(int n_qubits, int n_gates, const sim_gate *gates, const std::vector<int> &which, int first,
+                  std::vector<std::pair<int, std::vector<int>>> &phases)
+{
+    double G[32];
+    std::vector<int> rem(n_gates);
+    for (int g = 0; g < n_gates; g++) rem[g] = g;
+    int cur = first, idle = 0;
+    while (!rem.empty() && idle < 2) {
+        std::vector<char> blocked(n_qubits, 0);
+        for (int q = 0; q < n_qubits; q++) blocked[q] = which[q] == cur;
+        std::vector<int> take, defer;
+        for (int g : rem) {
+            const int d = gate_matrix(gates[g], G);
+            const int Q[2] = {gates[g].q0, gates[g].q1};
+            const int nq = d == 2 ? 1 : 2;
+            bool ok = true;
+            for (int i = 0; i < nq; i++) ok &= !blocked[Q[i]];
+            if (ok) {
+                take.push_back(g);
+            } else {
+                defer.push_back(g);
+                for (int i = 0; i < nq; i++) blocked[Q[i]] = 1;
+            }
+        }
+        if (take.empty()) {
+            idle++;
+        } else {
+            idle = 0;
+            phases.push_back({cur, take});
+        }
+        rem.swap(defer);
+        cur = 1 - cur;
+    }
+    return rem.empty();
+}
+
 }  // namespace
 
 extern "C" {
@@ -96,86 +229,27 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
     p->n_gates = n_gates;
     p->kmax = opts.kmax;
     p->precision = opts.precision;
-    // Pass 1 (Sect. 3: single-qubit gates can be aggregated with neighbouring two-qubit gates):
-    // each single-qubit gate joins the next two-qubit gate on its qubit, or the previous one
-    // when none follows; a qubit without two-qubit gates keeps its own unit.
-    struct Unit {
-        int q[2];
-        int nq;
-        std::vector<int> gates;
-    };
-    std::vector<Unit> units;
-    std::vector<std::vector<int>> pending(n_qubits);
-    std::vector<int> last2q(n_qubits, -1);
+    Grouping gr;
+    std::vector<int> idx(n_gates);
+    for (int i = 0; i < n_gates; i++) idx[i] = i;
+    int bad = 0;
+    const int grc = group_gates(n_qubits, gates, idx, opts.kmax, gr, &bad);
+    if (grc) {
+        delete p;
+        return fail(nullptr, SIM_E_INVAL, grc == 1 ? "sim_plan_create: gate %d has unknown kind %d"
+                                                   : "sim_plan_create: gate %d has bad qubits",
+                    bad, gates[bad].kind);
+    }
+    const std::vector<Unit> &units = gr.units;
+    const std::vector<std::vector<int>> &block_units = gr.block_units;
     double G[32];
-    for (int gi = 0; gi < n_gates; gi++) {
-        const sim_gate &g = gates[gi];
-        const int d = gate_matrix(g, G);
-        if (!d) {
-            delete p;
-            return fail(nullptr, SIM_E_INVAL, "sim_plan_create: gate %d has unknown kind %d", gi, g.kind);
+    p->blocks.resize(gr.qubits.size());
+    for (size_t bi = 0; bi < gr.qubits.size(); bi++) {
+        p->blocks[bi].qubits = gr.qubits[bi];
+        for (int ui : block_units[bi]) {
+            const auto &ug = units[ui].gates;
+            p->blocks[bi].gates.insert(p->blocks[bi].gates.end(), ug.begin(), ug.end());
         }
-        const int nq = d == 2 ? 1 : 2;
-        const int Q[2] = {g.q0, g.q1};
-        for (int i = 0; i < nq; i++)
-            if (Q[i] < 0 || Q[i] >= n_qubits || (i == 1 && Q[1] == Q[0])) {
-                delete p;
-                return fail(nullptr, SIM_E_INVAL, "sim_plan_create: gate %d has bad qubits", gi);
-            }
-        if (nq == 1) {
-            pending[g.q0].push_back(gi);
-            continue;
-        }
-        Unit u{{g.q0, g.q1}, 2, {}};
-        for (int i = 0; i < 2; i++) {
-            u.gates.insert(u.gates.end(), pending[Q[i]].begin(), pending[Q[i]].end());
-            pending[Q[i]].clear();
-            last2q[Q[i]] = (int)units.size();
-        }
-        u.gates.push_back(gi);
-        units.push_back(std::move(u));
-    }
-    for (int q = 0; q < n_qubits; q++) {
-        if (pending[q].empty()) continue;
-        if (last2q[q] >= 0) {
-            auto &gl = units[last2q[q]].gates;
-            gl.insert(gl.end(), pending[q].begin(), pending[q].end());
-        } else {
-            units.push_back(Unit{{q, -1}, 1, pending[q]});
-        }
-    }
-
-    // Pass 2: greedy grouping of the units into blocks of at most kmax qubits.
-    std::vector<int> last(n_qubits, -1);
-    std::vector<std::vector<int>> block_units;  // units of each block, in order
-    for (int ui = 0; ui < (int)units.size(); ui++) {
-        const Unit &u = units[ui];
-        const int nq = u.nq;
-        const int *Q = u.q;
-        int lo = -1;
-        for (int i = 0; i < nq; i++) lo = std::max(lo, last[Q[i]]);
-        auto grown = [&](const PlanBlock &b) {
-            int add = 0;
-            for (int i = 0; i < nq; i++)
-                add += std::find(b.qubits.begin(), b.qubits.end(), Q[i]) == b.qubits.end();
-            return (int)b.qubits.size() + add;
-        };
-        int chosen = -1;
-        if (lo >= 0 && grown(p->blocks[lo]) <= opts.kmax) chosen = lo;
-        for (int b = std::max(lo + 1, 0); chosen < 0 && b < (int)p->blocks.size(); b++)
-            if (grown(p->blocks[b]) <= opts.kmax) chosen = b;
-        if (chosen < 0) {
-            p->blocks.emplace_back();
-            block_units.emplace_back();
-            chosen = (int)p->blocks.size() - 1;
-        }
-        block_units[chosen].push_back(ui);
-        PlanBlock &b = p->blocks[chosen];
-        for (int i = 0; i < nq; i++)
-            if (std::find(b.qubits.begin(), b.qubits.end(), Q[i]) == b.qubits.end())
-                b.qubits.push_back(Q[i]);
-        b.gates.insert(b.gates.end(), u.gates.begin(), u.gates.end());
-        for (int i = 0; i < nq; i++) last[Q[i]] = chosen;
     }
     // compose each block in FP64: each unit's gates first into one 2x2 or 4x4 matrix (local bit 0
     // = the unit's first qubit), then that matrix into the block
@@ -439,43 +513,9 @@ int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const si
             return fail(nullptr, SIM_E_NONLOCAL,
                         "sim_phases_create: gate %d couples set A and set B; no phase can apply it", g);
     }
-    // Greedy: in a phase with set X sliced, apply (in order) every remaining gate that avoids X
-    // and every qubit already holding a deferred gate; the deferred gates form the next
-    // phase's input, with the other set sliced.  Both starting sets are tried.
-    auto run = [&](int first, std::vector<std::pair<int, std::vector<int>>> &phases) {
-        std::vector<int> rem(n_gates);
-        for (int g = 0; g < n_gates; g++) rem[g] = g;
-        int cur = first, idle = 0;
-        while (!rem.empty() && idle < 2) {
-            std::vector<char> blocked(n_qubits, 0);
-            for (int q = 0; q < n_qubits; q++) blocked[q] = which[q] == cur;
-            std::vector<int> take, defer;
-            for (int g : rem) {
-                const int d = gate_matrix(gates[g], G);
-                const int Q[2] = {gates[g].q0, gates[g].q1};
-                const int nq = d == 2 ? 1 : 2;
-                bool ok = true;
-                for (int i = 0; i < nq; i++) ok &= !blocked[Q[i]];
-                if (ok) {
-                    take.push_back(g);
-                } else {
-                    defer.push_back(g);
-                    for (int i = 0; i < nq; i++) blocked[Q[i]] = 1;
-                }
-            }
-            if (take.empty()) {
-                idle++;
-            } else {
-                idle = 0;
-                phases.push_back({cur, take});
-            }
-            rem.swap(defer);
-            cur = 1 - cur;
-        }
-        return rem.empty();
-    };
     std::vector<std::pair<int, std::vector<int>>> best, alt;
-    const bool ok0 = run(0, best), ok1 = run(1, alt);
+    const bool ok0 = split_phases(n_qubits, n_gates, gates, which, 0, best),
+               ok1 = split_phases(n_qubits, n_gates, gates, which, 1, alt);
     if (!ok0 && !ok1) return fail(nullptr, SIM_E_INVAL, "sim_phases_create: circuit cannot be phased");
     if (!ok0 || (ok1 && alt.size() < best.size())) best.swap(alt);
 
@@ -499,6 +539,76 @@ int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const si
         ph->plans.push_back(plan);
     }
     *out = ph;
+    return SIM_OK;
+}
+
+int sim_phases_choose_sets(int n_qubits, int n_gates, const sim_gate *gates, int slice_bits,
+                           const sim_plan_opts *o, double phase_weight, int *set_a, int *set_b, int *n_phases,
+                           int *n_blocks)
+{
+    if (n_qubits < 2 || n_qubits > kMaxQubits || slice_bits < 1 || slice_bits > 8 || 2 * slice_bits >= n_qubits ||
+        n_gates < 0 || (n_gates > 0 && !gates) || !set_a || !set_b)
+        return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: bad arguments");
+    const int kmax = o && o->kmax ? o->kmax : 4;
+    if (kmax < 2 || kmax > kMaxK) return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: kmax=%d", kmax);
+    if (!(phase_weight > 0.0)) phase_weight = 32.0;
+    double G[32];
+    for (int g = 0; g < n_gates; g++) {
+        const int d = gate_matrix(gates[g], G);
+        if (!d || gates[g].q0 < 0 || gates[g].q0 >= n_qubits ||
+            (d == 4 && (gates[g].q1 < 0 || gates[g].q1 >= n_qubits || gates[g].q1 == gates[g].q0)))
+            return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: gate %d is malformed", g);
+    }
+    const int s = slice_bits;
+    double best_cost = 1e300;
+    int best_i = -1, best_j = -1, best_ph = 0, best_bl = 0;
+    std::vector<int> which(n_qubits);
+    for (int i = 0; i + s <= n_qubits; i++)
+        for (int j = i + s; j + s <= n_qubits; j++) {
+            std::fill(which.begin(), which.end(), -1);
+            for (int t = 0; t < s; t++) {
+                which[i + t] = 0;
+                which[j + t] = 1;
+            }
+            bool coupled = false;
+            for (int g = 0; g < n_gates && !coupled; g++)
+                coupled = gate_matrix(gates[g], G) == 4 && which[gates[g].q0] >= 0 && which[gates[g].q1] >= 0 &&
+                          which[gates[g].q0] != which[gates[g].q1];
+            if (coupled) continue;
+            int cand_ph = 0, cand_bl = 0;
+            double cand_cost = 1e300;
+            for (int first = 0; first < 2; first++) {
+                std::vector<std::pair<int, std::vector<int>>> phases;
+                if (!split_phases(n_qubits, n_gates, gates, which, first, phases)) continue;
+                int blocks = 0;
+                for (auto &ph : phases) {
+                    Grouping gr;
+                    int bad = 0;
+                    if (group_gates(n_qubits, gates, ph.second, kmax, gr, &bad)) return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: gate %d", bad);
+                    blocks += (int)gr.qubits.size();
+                }
+                const double cost = phase_weight * (double)phases.size() + blocks;
+                if (cost < cand_cost) {
+                    cand_cost = cost;
+                    cand_ph = (int)phases.size();
+                    cand_bl = blocks;
+                }
+            }
+            if (cand_cost < best_cost) {
+                best_cost = cand_cost;
+                best_i = i;
+                best_j = j;
+                best_ph = cand_ph;
+                best_bl = cand_bl;
+            }
+        }
+    if (best_i < 0) return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: no pair of sets can phase the circuit");
+    for (int t = 0; t < s; t++) {
+        set_a[t] = best_i + t;
+        set_b[t] = best_j + t;
+    }
+    if (n_phases) *n_phases = best_ph;
+    if (n_blocks) *n_blocks = best_bl;
     return SIM_OK;
 }
 

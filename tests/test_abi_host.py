@@ -192,3 +192,51 @@ def test_phases_reject_gate_across_sets(pkg):
     with pytest.raises(pkg.SimError) as e:
         pkg.sim_phases_create(8, recs, 1, [0], [5])
     assert e.value.code == pkg.SIM_E_NONLOCAL
+
+
+def _phase_cost(pkg, circ, s, a, b, kmax, weight):
+    try:
+        ph = pkg.sim_phases_create(circ.n_qubits, pkg.gates_array(circ), s, a, b, kmax=kmax)
+    except pkg.SimError:
+        return None
+    nph, nbl = pkg.sim_phases_info(ph)
+    pkg.sim_phases_destroy(ph)
+    return weight * nph + nbl, nph, nbl
+
+
+@pytest.mark.parametrize("grid,cycles,s,kmax", [((3, 4), 8, 2, 4), ((4, 4), 10, 2, 5), ((3, 5), 12, 3, 4)])
+def test_phase_set_choice_is_the_best_window_pair(pkg, grid, cycles, s, kmax):
+    # brute force over every pair of disjoint windows of s consecutive qubits, through
+    # sim_phases_create: the chooser's cost must be the minimum, and its pair must reach it
+    circ = si.sycamore_circuit(si.Grid(*grid), cycles=cycles, seed=21)
+    n, weight = circ.n_qubits, 32.0
+    a, b, nph, nbl = pkg.sim_phases_choose_sets(n, pkg.gates_array(circ), s, kmax=kmax, phase_weight=weight)
+    assert len(set(a) | set(b)) == 2 * s
+    costs = []
+    for i in range(n - s + 1):
+        for j in range(i + s, n - s + 1):
+            c = _phase_cost(pkg, circ, s, list(range(i, i + s)), list(range(j, j + s)), kmax, weight)
+            if c is not None:
+                costs.append(c[0])
+    chosen = _phase_cost(pkg, circ, s, a, b, kmax, weight)
+    assert chosen == (weight * nph + nbl, nph, nbl)
+    assert chosen[0] == min(costs)
+    ends = _phase_cost(pkg, circ, s, list(range(s)), list(range(n - s, n)), kmax, weight)
+    assert ends is None or chosen[0] <= ends[0]
+
+
+def test_phase_set_choice_weights_and_errors(pkg):
+    circ = si.sycamore_circuit(si.Grid(4, 5), cycles=12, seed=3)
+    n = circ.n_qubits
+    # a huge phase weight minimises the number of phases first
+    _, _, nph_heavy, _ = pkg.sim_phases_choose_sets(n, pkg.gates_array(circ), 2, kmax=4, phase_weight=1e9)
+    best = None
+    for i in range(n - 1):
+        for j in range(i + 2, n - 1):
+            c = _phase_cost(pkg, circ, 2, [i, i + 1], [j, j + 1], 4, 1.0)
+            if c is not None and (best is None or c[1] < best):
+                best = c[1]
+    assert nph_heavy == best
+    for bad in ((n, 0), (n, 9), (1, 1)):
+        with pytest.raises(pkg.SimError):
+            pkg.sim_phases_choose_sets(bad[0], pkg.gates_array(circ), bad[1])

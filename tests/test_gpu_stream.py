@@ -123,6 +123,23 @@ def test_hybrid_store_tensor_core_phases_match_oracle(pkg, oracle_mod):
     assert abs(norm - 1.0) < 1e-5
 
 
+def test_chosen_sets_stream_to_the_oracle(pkg, oracle_mod):
+    # sets picked by sim_phases_choose_sets, streamed through a host store
+    circ = si.sycamore_circuit(si.Grid(4, 5), cycles=14, seed=8)
+    n, s = circ.n_qubits, 2
+    set_a, set_b, nph, nbl = pkg.sim_phases_choose_sets(n, pkg.gates_array(circ), s, kmax=5)
+    ph = pkg.sim_phases_create(n, pkg.gates_array(circ), s, set_a, set_b, kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    assert pkg.sim_phases_info(ph) == (nph, nbl)
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3)
+    try:
+        pkg.sim_run_phases(h, ph)
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_destroy(h)
+        pkg.sim_phases_destroy(ph)
+    assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= TOL_FP32
+
+
 def test_host_store_rejects_sliced_targets_and_device_calls(pkg):
     n, s = 10, 2
     h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=[0, 1], set_b=[8, 9])
