@@ -46,6 +46,7 @@ extern "C" {
 #define SIM_E_TIMEOUT (-6)    /* a bounded wait ran out */
 #define SIM_E_BUSY (-7)       /* resource exhausted right now (e.g. serving budget) */
 #define SIM_E_UNSUPPORTED (-8)/* valid request this build does not implement */
+#define SIM_E_IO (-9)         /* a file could not be opened, read or written */
 
 /* ---- arithmetic of the gate apply ------------------------------------ */
 #define SIM_FP32 0   /* CUDA-core FP32 FMA (the default) */
@@ -354,6 +355,19 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * (sim_permute), so the gates of the phase act on local bits only -- the
  * in-memory analogue of Sect. 4's reorganisation between phases.  Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
+
+/* ---- checkpoint / resume (not in the paper) --------------------------------
+ * Save the whole state to a file, and load it back, e.g. at a phase boundary of a long streamed
+ * run (sim_phases_get + sim_run_phase), to resume it in another process.  The file holds a header
+ * (n, slice_bits, the sliced sets, the physical layout) and the 2^n complex64 amplitudes in
+ * physical order: a host store's regions, device regions included, or the device state.
+ * sim_state_load needs the same n and slice_bits; a device-store handle takes the file's layout,
+ * a host-store handle must have the layout of the file (the same sliced sets).  Both are
+ * synchronous: they wait for h's work and move the data through a bounded pinned buffer.
+ * SIM_E_IO if the file cannot be opened, read or written, SIM_E_INVAL if it is not a state file
+ * or does not fit h. */
+int sim_state_save(sim_t *h, const char *path);
+int sim_state_load(sim_t *h, const char *path);
 
 /* ---- serving: many circuits on one GPU (no counterpart in the paper) --------
  * A continuous-batching server.  srv_submit plans the circuit (aggregation as

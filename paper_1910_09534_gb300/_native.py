@@ -25,6 +25,7 @@ SIM_E_CUDA = -5
 SIM_E_TIMEOUT = -6
 SIM_E_BUSY = -7
 SIM_E_UNSUPPORTED = -8
+SIM_E_IO = -9
 
 SIM_FP32 = 0
 SIM_TF32 = 1
@@ -136,6 +137,8 @@ _SIGS = {
     "sim_phases_choose_sets": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sim_state_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "sim_state_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_phases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_phases_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_phases_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -456,6 +459,14 @@ def sim_phases_choose_sets(n_qubits: int, gates: np.ndarray, slice_bits: int, km
                                         float(phase_weight), _ptr(a), _ptr(b), ctypes.byref(nph),
                                         ctypes.byref(nbl)))
     return [int(x) for x in a], [int(x) for x in b], nph.value, nbl.value
+
+
+def sim_state_save(h, path: str) -> None:
+    _check(lib().sim_state_save(h, os.fsencode(path)), h)
+
+
+def sim_state_load(h, path: str) -> None:
+    _check(lib().sim_state_load(h, os.fsencode(path)), h)
 
 
 def sim_phases_destroy(ph) -> None:

@@ -517,7 +517,20 @@ int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const si
     const bool ok0 = split_phases(n_qubits, n_gates, gates, which, 0, best),
                ok1 = split_phases(n_qubits, n_gates, gates, which, 1, alt);
     if (!ok0 && !ok1) return fail(nullptr, SIM_E_INVAL, "sim_phases_create: circuit cannot be phased");
-    if (!ok0 || (ok1 && alt.size() < best.size())) best.swap(alt);
+    // of the two starting sets, the one with the least phases * 32 + fused blocks (the cost
+    // sim_phases_choose_sets uses)
+    const int kmax_g = o && o->kmax ? o->kmax : 4;
+    auto cost = [&](const std::vector<std::pair<int, std::vector<int>>> &phs) {
+        double blocks = 0;
+        for (auto &ph : phs) {
+            Grouping gr;
+            int bad = 0;
+            if (group_gates(n_qubits, gates, ph.second, std::max(2, std::min(kmax_g, kMaxK)), gr, &bad)) return 1e300;
+            blocks += (double)gr.qubits.size();
+        }
+        return 32.0 * (double)phs.size() + blocks;
+    };
+    if (!ok0 || (ok1 && cost(alt) < cost(best))) best.swap(alt);
 
     auto *ph = new sim_phases_s();
     ph->n = n_qubits;

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -350,7 +351,172 @@ int host_reduce(sim_t *h, double *s1, double *s2)
     return SIM_OK;
 }
 
+// ---- checkpoint / resume ----
+
+namespace {
+
+struct StateFileHeader {
+    char magic[8];  // "SYCSTATE"
+    uint32_t version;
+    int32_t n, s, store;
+    int32_t set_a[8], set_b[8];
+    int32_t bit_of[kMaxQubits];
+    uint64_t amps;
+    uint64_t reserved[4];
+};
+
+constexpr uint32_t kStateFileVersion = 1;
+constexpr size_t kCkptChunk = 64ull << 20;  // bytes through the pinned buffer at a time
+
+// The state as runs of device or host memory in physical order.
+std::vector<std::pair<float2 *, uint64_t>> state_runs(sim_t *h)
+{
+    std::vector<std::pair<float2 *, uint64_t>> runs;
+    if (h->store != SIM_STORE_HOST) {
+        runs.push_back({h->d_state, h->amps});
+        return runs;
+    }
+    const uint64_t slice = 1ull << (h->n - h->s);
+    for (uint64_t v = 0; v < (1ull << h->s); v++) runs.push_back({region(h, v), slice});
+    return runs;
+}
+
+struct PinnedChunk {
+    char *p = nullptr;
+    ~PinnedChunk()
+    {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+int sync_state(sim_t *h)
+{
+    if (h->store == SIM_STORE_HOST) return host_sync_all(h);
+    SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SIM_OK;
+}
+
+}  // namespace
+
 }  // namespace sycsim
+
+using namespace sycsim;
+
+extern "C" int sim_state_save(sim_t *h, const char *path)
+{
+    if (!h || !path) return fail(h, SIM_E_INVAL, "sim_state_save: NULL argument");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    int rc = sync_state(h);
+    if (rc != SIM_OK) return rc;
+    StateFileHeader hd{};
+    std::memcpy(hd.magic, "SYCSTATE", 8);
+    hd.version = kStateFileVersion;
+    hd.n = h->n;
+    hd.s = h->s;
+    hd.store = h->store;
+    for (int i = 0; i < 8; i++) {
+        hd.set_a[i] = h->set[0][i];
+        hd.set_b[i] = h->set[1][i];
+    }
+    for (int q = 0; q < h->n; q++) hd.bit_of[q] = h->bit_of[q];
+    hd.amps = h->amps;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(h, SIM_E_IO, "sim_state_save: cannot open %s for writing", path);
+    PinnedChunk buf;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&buf.p), kCkptChunk, cudaHostAllocDefault) != cudaSuccess) {
+        buf.p = nullptr;
+        std::fclose(f);
+        return fail(h, SIM_E_NOMEM_HOST, "sim_state_save: staging buffer");
+    }
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+    for (auto &run : state_runs(h)) {
+        const char *src = reinterpret_cast<const char *>(run.first);
+        cudaPointerAttributes at{};
+        const bool on_device = cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        for (uint64_t off = 0, total = run.second * sizeof(float2); ok && off < total; off += kCkptChunk) {
+            const size_t len = (size_t)std::min<uint64_t>(kCkptChunk, total - off);
+            const char *from = src + off;
+            if (on_device) {
+                if (cudaMemcpy(buf.p, from, len, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    std::fclose(f);
+                    return fail(h, SIM_E_CUDA, "sim_state_save: %s", cudaGetErrorString(cudaGetLastError()));
+                }
+                from = buf.p;
+            }
+            ok = std::fwrite(from, 1, len, f) == len;
+        }
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SIM_OK : fail(h, SIM_E_IO, "sim_state_save: writing %s failed", path);
+}
+
+extern "C" int sim_state_load(sim_t *h, const char *path)
+{
+    if (!h || !path) return fail(h, SIM_E_INVAL, "sim_state_load: NULL argument");
+    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    int rc = sync_state(h);
+    if (rc != SIM_OK) return rc;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(h, SIM_E_IO, "sim_state_load: cannot open %s", path);
+    StateFileHeader hd{};
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "SYCSTATE", 8) != 0 ||
+        hd.version != kStateFileVersion) {
+        std::fclose(f);
+        return fail(h, SIM_E_INVAL, "sim_state_load: %s is not a state file", path);
+    }
+    if (hd.n != h->n || hd.s != h->s || hd.amps != h->amps) {
+        std::fclose(f);
+        return fail(h, SIM_E_INVAL, "sim_state_load: the file holds n=%d, slice_bits=%d; the handle n=%d, slice_bits=%d",
+                    hd.n, hd.s, h->n, h->s);
+    }
+    bool perm_ok = true;
+    std::vector<char> seen(h->n, 0);
+    for (int q = 0; q < h->n; q++) {
+        const int b = hd.bit_of[q];
+        perm_ok &= b >= 0 && b < h->n && !seen[b];
+        if (b >= 0 && b < h->n) seen[b] = 1;
+    }
+    if (!perm_ok) {
+        std::fclose(f);
+        return fail(h, SIM_E_INVAL, "sim_state_load: corrupt layout in %s", path);
+    }
+    if (h->store == SIM_STORE_HOST) {
+        for (int q = 0; q < h->n; q++)
+            if (hd.bit_of[q] != h->bit_of[q]) {
+                std::fclose(f);
+                return fail(h, SIM_E_INVAL, "sim_state_load: the host store's layout (its sliced sets) differs from the file's");
+            }
+    }
+    PinnedChunk buf;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&buf.p), kCkptChunk, cudaHostAllocDefault) != cudaSuccess) {
+        buf.p = nullptr;
+        std::fclose(f);
+        return fail(h, SIM_E_NOMEM_HOST, "sim_state_load: staging buffer");
+    }
+    bool ok = true;
+    for (auto &run : state_runs(h)) {
+        char *dst = reinterpret_cast<char *>(run.first);
+        cudaPointerAttributes at{};
+        const bool on_device = cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        for (uint64_t off = 0, total = run.second * sizeof(float2); ok && off < total; off += kCkptChunk) {
+            const size_t len = (size_t)std::min<uint64_t>(kCkptChunk, total - off);
+            char *to = on_device ? buf.p : dst + off;
+            ok = std::fread(to, 1, len, f) == len;
+            if (ok && on_device && cudaMemcpy(dst + off, buf.p, len, cudaMemcpyHostToDevice) != cudaSuccess) {
+                std::fclose(f);
+                return fail(h, SIM_E_CUDA, "sim_state_load: %s", cudaGetErrorString(cudaGetLastError()));
+            }
+        }
+    }
+    std::fclose(f);
+    if (!ok) return fail(h, SIM_E_IO, "sim_state_load: %s is truncated", path);
+    if (h->store != SIM_STORE_HOST)  // the device state takes the file's layout
+        for (int q = 0; q < h->n; q++) {
+            h->bit_of[q] = hd.bit_of[q];
+            h->qubit_at[hd.bit_of[q]] = q;
+        }
+    return SIM_OK;
+}
 
 using namespace sycsim;
 
