@@ -7,7 +7,9 @@ does, and it shares no code with the CUDA path.
 The arithmetic lives in ``oracle.c`` (plain C, complex128, gate by gate); this
 module only loads it with ctypes and converts numpy arrays.  Every function is
 pinned in ``tests/test_oracle_pins.py`` against closed forms, invariants and
-brute-force full-operator products.
+brute-force full-operator products; the contraction-deferral tensors (``split_tensors``,
+``contract``) against full-operator products of detuned (qubit-order-sensitive) circuits,
+outer products, the EI copy structure and the tensors' norms.
 """
 from __future__ import annotations
 
@@ -59,6 +61,9 @@ def lib():
         L.orc_slice_move.argtypes = [P, P, i32, i32, P, u64, i32, i32]
         L.orc_slice_move.restype = i32
         L.orc_reduce.argtypes = [P, i32, P, P, P]
+        L.orc_split_tensors.argtypes = [i32, i32, P, P, P, P, P, P, P, P, P, P, P]
+        L.orc_split_tensors.restype = i32
+        L.orc_contract.argtypes = [P, i32, P, i32, i32, P, P, P]
         _lib = L
     return _lib
 
@@ -172,3 +177,52 @@ def reduce(psi: np.ndarray):
     vals = (ctypes.c_double(), ctypes.c_double(), ctypes.c_double())
     lib().orc_reduce(_ptr(psi), _nq(psi), *[ctypes.byref(v) for v in vals])
     return tuple(v.value for v in vals)
+
+
+def _gate_columns(gates):
+    """(kind, q0, q1, theta, phi, dplus, dminus, dminus_off) columns from a syc_inputs
+    Circuit (no detuning) or from a sequence of 8-tuples."""
+    if hasattr(gates, "arrays"):
+        kind, q0, q1, theta, phi = gates.arrays()
+        z = np.zeros(kind.size, dtype=np.float64)
+        return kind, q0, q1, theta, phi, z, z.copy(), z.copy()
+    g = list(gates)
+    cols = [np.array([x[i] for x in g], dtype=np.int32) for i in range(3)]
+    cols += [np.array([x[i] if len(x) > i else 0.0 for x in g], dtype=np.float64) for i in range(3, 8)]
+    return tuple(cols)
+
+
+def split_tensors(n: int, gates, side):
+    """Tensors 1 and 2 of the contraction-deferral split (Sect. 2; Appendix, EI and E2Q).
+
+    Returns (t1, t2, c): c bridging gates; t1 over the side-0 qubits (increasing order) then
+    the 2c entanglement bits, pair j's (a', a) at n1 + 2j, n1 + 2j + 1; t2 likewise."""
+    cols = _gate_columns(gates)
+    sd = np.ascontiguousarray(side, dtype=np.int32)
+    ptrs = [_ptr(np.ascontiguousarray(a)) for a in cols]
+    c = lib().orc_split_tensors(int(n), int(cols[0].size), *ptrs, _ptr(sd), None, None)
+    if c < 0:
+        raise ValueError(f"bad split input ({c})")
+    n1 = int((sd == 0).sum())
+    n2 = n - n1
+    t1 = np.empty(1 << (n1 + 2 * c), dtype=np.complex128)
+    t2 = np.empty(1 << (n2 + 2 * c), dtype=np.complex128)
+    rc = lib().orc_split_tensors(int(n), int(cols[0].size), *ptrs, _ptr(sd), _ptr(t1), _ptr(t2))
+    if rc != c:
+        raise ValueError(f"split failed ({rc})")
+    return t1, t2, c
+
+
+def contract(t1: np.ndarray, t2: np.ndarray, n1: int, n2: int, qa, qb) -> np.ndarray:
+    """psi over n1 + n2 qubits (logical order) = the sum over the shared entanglement bits of
+    t1 * t2; qa / qb: qubit at each qubit position of t1 / t2."""
+    t1 = np.ascontiguousarray(t1, dtype=np.complex128)
+    t2 = np.ascontiguousarray(t2, dtype=np.complex128)
+    e = _nq(t1) - n1
+    if e < 0 or _nq(t2) - n2 != e or len(qa) != n1 or len(qb) != n2:
+        raise ValueError("tensor shapes do not match")
+    a = np.ascontiguousarray(qa, dtype=np.int32)
+    b = np.ascontiguousarray(qb, dtype=np.int32)
+    psi = np.empty(1 << (n1 + n2), dtype=np.complex128)
+    lib().orc_contract(_ptr(t1), int(n1), _ptr(t2), int(n2), int(e), _ptr(a), _ptr(b), _ptr(psi))
+    return psi

@@ -11,6 +11,9 @@
  * aggregation, slicing, qubit reorganisation, secondary storage) reaches up to
  * rounding: psi = U_G ... U_1 |0...0>, each gate applied one at a time to the
  * full state vector (the "Schroedinger approach", Sect. 2), in complex128.
+ * For contraction deferral (Sect. 2; Appendix, EI and E2Q) it also builds the two
+ * subcircuit tensors with their entanglement indices, index by index from the
+ * Appendix's equations, and the contraction that removes those indices.
  *
  * Conventions: qubit q is bit q of the amplitude index (little-endian).  A
  * k-qubit matrix is 2^k x 2^k, row-major; bit j of its row/column index is the
@@ -261,4 +264,150 @@ void orc_reduce(const cplx *psi, int n, double *norm, double *sum_p2_scaled, dou
     *norm = s1;
     *sum_p2_scaled = ldexp(s2, n);
     *xeb = *sum_p2_scaled - 1.0;
+}
+
+/*
+ * Contraction deferral (Sect. 2) with the synthesized operations EI and E2Q
+ * defined in the Appendix.
+ *
+ * side[q] = 0 puts qubit q in tensor 1, side[q] = 1 in tensor 2.  Each tensor
+ * starts as |0..0> over its own qubits, qubit positions 0.. in increasing qubit
+ * order.  Gates are taken in list order.  A gate whose qubits are all on one
+ * side acts on that side's tensor at its qubits' positions (orc_apply_1q /
+ * orc_apply_2q).  A two-qubit gate G that bridges qubit a (side 0) and qubit b
+ * (side 1) is the j-th bridging gate: it appends two indices to each tensor, at
+ * positions m and m + 1 where m is the tensor's index count before the gate, and
+ *   EI  (tensor 1): T1'[.., a'' at p(a), a' at m, a at m+1]
+ *                     = delta(a'', a') T1[.., a at p(a)]
+ *   E2Q (tensor 2): T2'[.., b'' at p(b), a' at m, a at m+1]
+ *                     = sum_b G[a', b''; a, b] T2[.., b at p(b)]
+ * where G[x'', y''; x, y] is the gate's matrix element from input (x, y) to
+ * output (x'', y'') with x the value of qubit a and y that of qubit b (the gate's
+ * own index is b(q0) + 2 b(q1), whichever of a, b is q0).  Qubit a keeps position
+ * p(a) for its new index a''.  So tensor 1 ends with its n1 qubits at positions
+ * 0..n1-1 and pair j's (a', a) at n1 + 2j, n1 + 2j + 1; tensor 2 likewise.
+ *
+ * t1, t2: room for 2^(n1 + 2c) and 2^(n2 + 2c) amplitudes, c = number of
+ * bridging gates; with t1 == NULL only c is computed.  dp, dm, dmoff (fSim
+ * detunings) may be NULL for zero.  Returns c, or -(1 + g) for a bad gate g, or
+ * -1000000 for a bad side vector.
+ */
+static int64_t put_bit(int64_t i, int p, int v)
+{
+    return (i & ~((int64_t)1 << p)) | ((int64_t)v << p);
+}
+
+int orc_split_tensors(int n, int ngates, const int *kind, const int *q0, const int *q1,
+                      const double *theta, const double *phi, const double *dp,
+                      const double *dm, const double *dmoff, const int *side, cplx *t1,
+                      cplx *t2)
+{
+    int pos[64], bits[2] = {0, 0}, c = 0;
+    if (n < 1 || n > 62) return -1000000;
+    for (int q = 0; q < n; q++) {
+        if (side[q] != 0 && side[q] != 1) return -1000000;
+        pos[q] = bits[side[q]]++;
+    }
+    if (bits[0] == 0 || bits[1] == 0) return -1000000;
+    for (int g = 0; g < ngates; g++) { /* validate and count the bridging gates first */
+        cplx u[16];
+        int d = orc_gate_matrix(kind[g], theta[g], phi[g], 0.0, 0.0, 0.0, u);
+        if (d == 0 || q0[g] < 0 || q0[g] >= n) return -(1 + g);
+        if (d == 4) {
+            if (q1[g] < 0 || q1[g] >= n || q1[g] == q0[g]) return -(1 + g);
+            if (side[q0[g]] != side[q1[g]]) c++;
+        }
+    }
+    if (!t1) return c;
+    cplx *T[2] = {t1, t2};
+    for (int s = 0; s < 2; s++) {
+        memset(T[s], 0, sizeof(cplx) << bits[s]);
+        T[s][0] = 1.0;
+    }
+    cplx *tmp = NULL;
+    for (int g = 0; g < ngates; g++) {
+        cplx u[16];
+        int d = orc_gate_matrix(kind[g], theta[g], phi[g], dp ? dp[g] : 0.0, dm ? dm[g] : 0.0,
+                                dmoff ? dmoff[g] : 0.0, u);
+        if (d == 2) {
+            int s = side[q0[g]];
+            orc_apply_1q(T[s], bits[s], pos[q0[g]], u);
+            continue;
+        }
+        int sa = side[q0[g]], sb = side[q1[g]];
+        if (sa == sb) {
+            orc_apply_2q(T[sa], bits[sa], pos[q0[g]], pos[q1[g]], u);
+            continue;
+        }
+        const int a_is_q0 = sa == 0;
+        const int a = a_is_q0 ? q0[g] : q1[g], b = a_is_q0 ? q1[g] : q0[g];
+        /* EI on tensor 1 */
+        {
+            const int m = bits[0], pa = pos[a];
+            const int64_t dim = (int64_t)1 << (m + 2);
+            tmp = (cplx *)realloc(tmp, sizeof(cplx) * (size_t)dim);
+            if (!tmp) return -2000000;
+            for (int64_t i = 0; i < dim; i++) {
+                const int64_t low = i & (((int64_t)1 << m) - 1);
+                const int app = (int)((low >> pa) & 1); /* a'' */
+                const int ap = (int)((i >> m) & 1);     /* a'  */
+                const int av = (int)((i >> (m + 1)) & 1); /* a */
+                tmp[i] = app == ap ? T[0][put_bit(low, pa, av)] : 0.0;
+            }
+            memcpy(T[0], tmp, sizeof(cplx) * (size_t)dim);
+            bits[0] = m + 2;
+        }
+        /* E2Q on tensor 2 */
+        {
+            const int m = bits[1], pb = pos[b];
+            const int64_t dim = (int64_t)1 << (m + 2);
+            tmp = (cplx *)realloc(tmp, sizeof(cplx) * (size_t)dim);
+            if (!tmp) return -2000000;
+            for (int64_t i = 0; i < dim; i++) {
+                const int64_t low = i & (((int64_t)1 << m) - 1);
+                const int bpp = (int)((low >> pb) & 1); /* b'' */
+                const int ap = (int)((i >> m) & 1);     /* a'  */
+                const int av = (int)((i >> (m + 1)) & 1); /* a */
+                const int row = a_is_q0 ? ap + 2 * bpp : bpp + 2 * ap;
+                cplx acc = 0.0;
+                for (int bv = 0; bv < 2; bv++) {
+                    const int col = a_is_q0 ? av + 2 * bv : bv + 2 * av;
+                    acc += u[row * 4 + col] * T[1][put_bit(low, pb, bv)];
+                }
+                tmp[i] = acc;
+            }
+            memcpy(T[1], tmp, sizeof(cplx) * (size_t)dim);
+            bits[1] = m + 2;
+        }
+    }
+    free(tmp);
+    return c;
+}
+
+/*
+ * The contraction that removes the entanglement indices (Appendix: the sum over
+ * every pair's (a', a) of the product of the two tensors).  t1 holds n1 qubit
+ * indices at positions 0..n1-1 followed by e entanglement bits, t2 likewise with
+ * n2 qubits and the same e bits in the same order.  qa[i] / qb[j] name the qubit
+ * at position i of t1 / j of t2.  Writes psi (n1 + n2 qubits, logical order):
+ *   psi[sum_i x_i 2^qa[i] + sum_j y_j 2^qb[j]] = sum_k t1[x + k 2^n1] t2[y + k 2^n2].
+ */
+void orc_contract(const cplx *t1, int n1, const cplx *t2, int n2, int e, const int *qa,
+                  const int *qb, cplx *psi)
+{
+    const int64_t X = (int64_t)1 << n1, Y = (int64_t)1 << n2, E = (int64_t)1 << e;
+#pragma omp parallel for schedule(static)
+    for (int64_t y = 0; y < Y; y++) {
+        int64_t ly = 0;
+        for (int j = 0; j < n2; j++)
+            if ((y >> j) & 1) ly |= (int64_t)1 << qb[j];
+        for (int64_t x = 0; x < X; x++) {
+            int64_t lx = 0;
+            for (int i = 0; i < n1; i++)
+                if ((x >> i) & 1) lx |= (int64_t)1 << qa[i];
+            cplx acc = 0.0;
+            for (int64_t k = 0; k < E; k++) acc += t1[x + k * X] * t2[y + k * Y];
+            psi[lx | ly] = acc;
+        }
+    }
 }

@@ -357,3 +357,132 @@ def test_threads_do_not_change_results(oracle_mod):
     b = oracle_mod.run_circuit(circ)
     oracle_mod.set_threads(os.cpu_count() or 1)
     assert np.array_equal(a, b)
+
+
+# ---- contraction deferral: EI / E2Q tensors and the contraction (Sect. 2; Appendix) ----
+
+def _detuned_circuit(n, n_gates, seed):
+    """Random gate list of 8-tuples with fSim detunings, so the gate is not symmetric under
+    exchanging its qubits (a swapped role of a and b then changes the result)."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(n_gates):
+        if rng.random() < 0.5:
+            gates.append((int(rng.integers(3)), int(rng.integers(n)), -1, 0.0, 0.0))
+        else:
+            q0, q1 = (int(x) for x in rng.choice(n, 2, replace=False))
+            gates.append((si.FSIM, q0, q1, *(float(x) for x in rng.uniform(-np.pi, np.pi, 5))))
+    return gates
+
+
+def _plain_by_operators(oracle_mod, n, gates):
+    """psi = U_G ... U_1 |0>, each gate as its full 2^n x 2^n operator (definition)."""
+    psi = np.zeros(1 << n, dtype=complex)
+    psi[0] = 1.0
+    for g in gates:
+        kind, q0, q1 = g[0], g[1], g[2]
+        u = oracle_mod.gate_matrix(kind, *g[3:])
+        psi = full_operator(n, [q0] if kind != si.FSIM else [q0, q1], u) @ psi
+    return psi
+
+
+def _contract_logical(oracle_mod, n, side, t1, t2):
+    qa = [q for q in range(n) if side[q] == 0]
+    qb = [q for q in range(n) if side[q] == 1]
+    return oracle_mod.contract(t1, t2, len(qa), len(qb), qa, qb)
+
+
+@pytest.mark.parametrize("n,n_gates,seed", [(2, 6, 0), (4, 14, 1), (5, 18, 2), (6, 16, 3)])
+def test_split_contraction_equals_full_operator_product(oracle_mod, n, n_gates, seed):
+    gates = _detuned_circuit(n, n_gates, seed)
+    rng = np.random.default_rng(100 + seed)
+    side = [0] * n
+    while len(set(side)) < 2:
+        side = [int(x) for x in rng.integers(0, 2, n)]
+    t1, t2, c = oracle_mod.split_tensors(n, gates, side)
+    assert c == sum(1 for g in gates if g[0] == si.FSIM and side[g[1]] != side[g[2]])
+    assert c > 0
+    psi = _contract_logical(oracle_mod, n, side, t1, t2)
+    assert np.allclose(psi, _plain_by_operators(oracle_mod, n, gates), atol=1e-12)
+
+
+def test_split_sycamore_prefix_equals_plain_run(oracle_mod):
+    # 3 x 4 grid split between columns 1 and 2: the first two cycles (patterns A, B) bridge
+    # the cut with 1 + 2 gates, the next four (C, D, C, D) stay on either side.
+    circ = si.sycamore_circuit(si.Grid(3, 4), cycles=6, seed=4)
+    side = [0 if (q % 4) < 2 else 1 for q in range(12)]
+    t1, t2, c = oracle_mod.split_tensors(12, circ, side)
+    assert c == 3
+    assert t1.size == 1 << (6 + 6) and t2.size == 1 << (6 + 6)
+    psi = _contract_logical(oracle_mod, 12, side, t1, t2)
+    assert np.allclose(psi, oracle_mod.run_circuit(circ), atol=1e-12)
+
+
+def test_split_without_bridging_gates_is_an_outer_product(oracle_mod):
+    # gates never cross the cut: psi = T1 (x) T2 with the qubits placed by the sides
+    n = 5
+    side = [0, 1, 1, 0, 1]
+    gates = [(0, 0, -1, 0, 0), (si.FSIM, 0, 3, 0.3, 0.2, 0.1, -0.4, 0.7), (1, 2, -1, 0, 0),
+             (si.FSIM, 4, 1, 1.1, -0.5, 0.2, 0.3, -0.1), (2, 3, -1, 0, 0), (si.FSIM, 2, 4, 0.7, 0.9)]
+    t1, t2, c = oracle_mod.split_tensors(n, gates, side)
+    assert c == 0 and t1.size == 4 and t2.size == 8
+    psi = _contract_logical(oracle_mod, n, side, t1, t2)
+    assert np.allclose(psi, _plain_by_operators(oracle_mod, n, gates), atol=1e-13)
+    # the same from numpy: kron over qubit order 4, 3, 2, 1, 0 (little-endian)
+    t1q = {0: 0, 3: 1}
+    t2q = {1: 0, 2: 1, 4: 2}
+    full = np.einsum("ab,cde->abcde", t1.reshape(2, 2).T, t2.reshape(2, 2, 2).transpose(2, 1, 0))
+    # full[a0, a3, b1, b2, b4] -> psi index sum q bit_q 2^q
+    psi2 = np.zeros(1 << n, dtype=complex)
+    for i in range(1 << n):
+        b = [(i >> q) & 1 for q in range(n)]
+        psi2[i] = full[b[0], b[3], b[1], b[2], b[4]]
+    assert t1q and t2q and np.allclose(psi, psi2, atol=1e-15)
+
+
+def test_split_ei_structure_and_norms(oracle_mod):
+    # EI copies a'' = a' (entries with a'' != a' vanish right after it) and doubles the squared
+    # norm; E2Q also doubles it (sum over a of |G (e_a x chi)|^2 = 2 |chi|^2 for unitary G).
+    n = 2
+    gates = [(0, 0, -1, 0, 0), (2, 1, -1, 0, 0), (si.FSIM, 1, 0, 0.8, 0.4, 0.3, 0.6, -0.2)]
+    t1, t2, c = oracle_mod.split_tensors(n, gates, [0, 1])
+    assert c == 1 and t1.size == 8 and t2.size == 8
+    for i in range(8):
+        app, ap = i & 1, (i >> 1) & 1
+        if app != ap:
+            assert t1[i] == 0
+    phi = oracle_mod.gate_matrix(0)[:, 0]  # sqrt(X)|0>
+    for a in range(2):
+        for v in range(2):
+            assert t1[v + 2 * v + 4 * a] == pytest.approx(phi[a], abs=1e-15)
+    assert np.vdot(t1, t1).real == pytest.approx(2.0, abs=1e-13)
+    assert np.vdot(t2, t2).real == pytest.approx(2.0, abs=1e-13)
+    circ = si.sycamore_circuit(si.Grid(3, 4), cycles=6, seed=5)
+    side = [0 if (q % 4) < 2 else 1 for q in range(12)]
+    t1, t2, c = oracle_mod.split_tensors(12, circ, side)
+    assert np.vdot(t1, t1).real == pytest.approx(2.0 ** c, rel=1e-12)
+    assert np.vdot(t2, t2).real == pytest.approx(2.0 ** c, rel=1e-12)
+
+
+def test_contract_matches_einsum(oracle_mod):
+    rng = np.random.default_rng(7)
+    n1, n2, e = 3, 2, 4
+    t1 = rng.normal(size=1 << (n1 + e)) + 1j * rng.normal(size=1 << (n1 + e))
+    t2 = rng.normal(size=1 << (n2 + e)) + 1j * rng.normal(size=1 << (n2 + e))
+    qa, qb = [4, 0, 2], [3, 1]
+    psi = oracle_mod.contract(t1, t2, n1, n2, qa, qb)
+    m = np.einsum("kx,ky->xy", t1.reshape(1 << e, 1 << n1), t2.reshape(1 << e, 1 << n2))
+    for x in range(1 << n1):
+        for y in range(1 << n2):
+            li = sum(((x >> i) & 1) << qa[i] for i in range(n1)) + sum(((y >> j) & 1) << qb[j] for j in range(n2))
+            assert psi[li] == pytest.approx(m[x, y], abs=1e-12)
+
+
+def test_split_rejects_bad_sides(oracle_mod):
+    gates = [(0, 0, -1, 0, 0)]
+    with pytest.raises(ValueError):
+        oracle_mod.split_tensors(2, gates, [0, 0])
+    with pytest.raises(ValueError):
+        oracle_mod.split_tensors(2, gates, [0, 2])
+    with pytest.raises(ValueError):
+        oracle_mod.split_tensors(2, [(si.FSIM, 0, 0, 1.0, 1.0)], [0, 1])
