@@ -204,12 +204,15 @@ int sim_sync(sim_t *h, int timeout_ms);
  * launch that follows with a pair of CUDA events; sim_profile_read() waits for
  * the stream and returns, for one kernel class, the number of launches, their
  * summed device time in ms and their algorithmic bytes (apply: 16 B per
- * amplitude; permute: 16 B per amplitude moved; reduce: 8 B per amplitude).
+ * amplitude; permute: 16 B per amplitude moved; reduce: 8 B per amplitude;
+ * contract (sim_contract's GEMM, compute-bound): the field holds its algorithmic
+ * FLOPs instead, 8 per complex multiply-add).
  * sim_launch_count() is the number of kernels the handle has launched. */
 #define SIM_PROF_APPLY 0
 #define SIM_PROF_PERMUTE 1
 #define SIM_PROF_REDUCE 2
 #define SIM_PROF_OTHER 3
+#define SIM_PROF_CONTRACT 4
 int sim_profile_enable(sim_t *h, int on);
 int sim_profile_read(sim_t *h, int cls, uint64_t *launches, double *total_ms, double *alg_bytes);
 int sim_launch_count(const sim_t *h, uint64_t *n);
@@ -355,6 +358,54 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * (sim_permute), so the gates of the phase act on local bits only -- the
  * in-memory analogue of Sect. 4's reorganisation between phases.  Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
+
+/* ---- contraction deferral: two subcircuits joined by entanglement indices -----
+ * Sect. 2 (contraction deferral: subcircuits simulated separately, each with the Schroedinger
+ * approach, bridging gates deferred) and the Appendix (the synthesized operations EI and E2Q and
+ * the contraction that eliminates the entanglement indices).  side[q] = 0 puts qubit q in
+ * tensor 1, 1 in tensor 2 (both sides non-empty).  Gates within one side act on that side's
+ * tensor.  The j-th gate G bridging qubit a (side 0) and qubit b (side 1) adds the pair of
+ * entanglement indices (a'_j, a_j) to both tensors:
+ *   EI on tensor 1:  T1'[a'', a', a] = delta(a'', a') T1[a]
+ *   E2Q on tensor 2: T2'[b'', a', a] = sum_b G[a', b''; a, b] T2[b]
+ * (G[x'', y''; x, y]: the gate's element from input (a = x, b = y) to output (x'', y'')) and
+ *   psi[.., a'', b'', ..] = sum over all pairs (a'_j, a_j) of T1' T2'.
+ *
+ * sim_split_create turns this into two ordinary gate lists over "wires", which the planner and
+ * every apply path run like any circuit on a handle with n_wires[t] qubits started in |0..0>:
+ * tensor t has its side's qubits (wires 0.., in increasing qubit order) plus two fresh wires per
+ * bridging gate.  EI is a fan-out gate (SIM_GATE_U2 whose first column is |00> + |11>) on two
+ * fresh wires: the first becomes qubit a's wire, the second holds a', and a's previous wire now
+ * holds a.  E2Q is the same fan-out on two fresh wires followed by G with the first of them in
+ * the role of qubit a: afterwards it holds a' and the second holds a.  Each tensor's canonical
+ * layout puts its side's qubits at positions 0 .. n_side[t]-1 (increasing qubit order) and pair j
+ * at n_side[t] + 2j (a'_j) and n_side[t] + 2j + 1 (a_j).  Host only; the split copies its inputs.
+ *   sim_split_info: n_side[2] qubits per side, n_wires[2] = n_side + 2 * n_pairs, n_pairs
+ *     bridging gates, n_gates[2] records per tensor (any pointer may be NULL).
+ *   sim_split_gates: tensor t's gate records (n_gates[t] of them) into out.
+ *   sim_split_canonical: wire_at[p] = the wire at canonical position p of tensor t
+ *     (n_wires[t] entries).
+ * SIM_E_INVAL for a bad side vector or gate, or more than 40 wires on a side. */
+typedef struct sim_split_s sim_split_t;
+int sim_split_create(int n_qubits, int n_gates, const sim_gate *gates, const int *side, sim_split_t **out);
+int sim_split_info(const sim_split_t *s, int *n_side, int *n_wires, int *n_pairs, int *n_gates);
+int sim_split_gates(const sim_split_t *s, int t, sim_gate *out);
+int sim_split_canonical(const sim_split_t *s, int t, int *wire_at);
+int sim_split_destroy(sim_split_t *s);
+
+/* The contraction (Appendix: the sum over the entanglement indices): psi = sum_pairs T1 T2 into
+ * `out`.  t1 / t2: device-resident handles of n_wires[0] / n_wires[1] qubits holding the two
+ * tensors (their gate lists applied); out: a device-resident handle of n_qubits qubits, not
+ * sliced, distinct from both.  First permutes t1 and t2 into their canonical layouts (on their
+ * own streams; the tensors' logical content is unchanged); then, on out's stream after both, one
+ * complex GEMM over the 4^n_pairs entanglement values writes psi with the physical layout
+ * side-0 qubits at bits 0 .. n_side[0]-1 and side-1 qubits above (out's layout map is set to
+ * that).  t1's and t2's streams wait for the GEMM before any later work on them.
+ * precision: SIM_FP32 (CUDA cores, FP32 products and sums), or SIM_FP16X3 / SIM_FP16X3_TMEM
+ * (tcgen05 tensor cores: each tensor scaled by one power of two, split into FP16 hi + lo, the
+ * products hi*hi + hi*lo + lo*hi summed in FP32; needs n_side[0] >= 7 and n_side[1] >= 7,
+ * otherwise the FP32 kernel runs).  Asynchronous.  SIM_E_INVAL for handles that do not fit s. */
+int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision);
 
 /* ---- checkpoint / resume (not in the paper) --------------------------------
  * Save the whole state to a file, and load it back, e.g. at a phase boundary of a long streamed

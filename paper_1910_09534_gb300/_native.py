@@ -137,6 +137,15 @@ _SIGS = {
     "sim_phases_choose_sets": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sim_split_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "sim_split_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "sim_split_gates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sim_split_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_contract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int]),
     "sim_state_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_state_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_phases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -292,6 +301,7 @@ SIM_PROF_APPLY = 0
 SIM_PROF_PERMUTE = 1
 SIM_PROF_REDUCE = 2
 SIM_PROF_OTHER = 3
+SIM_PROF_CONTRACT = 4
 
 
 def sim_profile_enable(h, on: bool = True) -> None:
@@ -459,6 +469,49 @@ def sim_phases_choose_sets(n_qubits: int, gates: np.ndarray, slice_bits: int, km
                                         float(phase_weight), _ptr(a), _ptr(b), ctypes.byref(nph),
                                         ctypes.byref(nbl)))
     return [int(x) for x in a], [int(x) for x in b], nph.value, nbl.value
+
+
+def sim_split_create(n_qubits: int, gates: np.ndarray, side):
+    """Contraction-deferral split of a gate list (side[q] = 0: tensor 1, 1: tensor 2)."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    sd = np.ascontiguousarray(side, dtype=np.int32)
+    if sd.size != n_qubits:
+        raise ValueError("side needs one entry per qubit")
+    p = ctypes.c_void_p()
+    _check(lib().sim_split_create(n_qubits, int(g.size), _ptr(g), _ptr(sd), ctypes.byref(p)))
+    return p
+
+
+def sim_split_info(s):
+    """(n_side[2], n_wires[2], n_pairs, n_gates[2])."""
+    ns = np.zeros(2, dtype=np.int32)
+    nw = np.zeros(2, dtype=np.int32)
+    ng = np.zeros(2, dtype=np.int32)
+    npairs = ctypes.c_int()
+    _check(lib().sim_split_info(s, _ptr(ns), _ptr(nw), ctypes.byref(npairs), _ptr(ng)))
+    return [int(x) for x in ns], [int(x) for x in nw], npairs.value, [int(x) for x in ng]
+
+
+def sim_split_gates(s, t: int) -> np.ndarray:
+    ng = sim_split_info(s)[3][t]
+    out = np.zeros(ng, dtype=GATE_DTYPE)
+    _check(lib().sim_split_gates(s, t, _ptr(out) if ng else _ptr(np.zeros(1, dtype=GATE_DTYPE))))
+    return out
+
+
+def sim_split_canonical(s, t: int):
+    nw = sim_split_info(s)[1][t]
+    out = np.zeros(nw, dtype=np.int32)
+    _check(lib().sim_split_canonical(s, t, _ptr(out)))
+    return [int(x) for x in out]
+
+
+def sim_split_destroy(s) -> None:
+    _check(lib().sim_split_destroy(s))
+
+
+def sim_contract(out, t1, t2, s, precision: int = SIM_FP32) -> None:
+    _check(lib().sim_contract(out, t1, t2, s, precision), out)
 
 
 def sim_state_save(h, path: str) -> None:

@@ -125,6 +125,16 @@ struct sim_phases_s {
     std::vector<sim_plan_t *> plans;  // blocks of each phase
 };
 
+// Contraction deferral (split.cpp builds it, contract.cu reads it).
+struct sim_split_s {
+    int n = 0;
+    int n_side[2] = {0, 0};
+    int n_pairs = 0;
+    std::vector<int> side;            // side of each qubit
+    std::vector<sim_gate> gates[2];   // each tensor's gate list over its wires
+    std::vector<int> wire_at[2];      // canonical position -> wire
+};
+
 namespace sycsim {
 
 // Record an error on h (or the thread when h is null) and return `code`.

@@ -1,0 +1,159 @@
+// split.cpp -- contraction deferral: the two subcircuit gate lists of Sect. 2, with the
+// Appendix's EI and E2Q operations written as ordinary gates on fresh wires.
+//
+// A tensor is simulated as a state over "wires": its side's qubits plus two wires per bridging
+// gate, all starting in |0>.  EI on qubit a: a fan-out gate F (first column |00> + |11>) on two
+// fresh wires (w1, w2) makes delta(w1, w2); w1 carries qubit a from then on, w2 is the pair's
+// a', and a's previous wire, which no later gate touches, is the pair's a.  E2Q on qubit b: F on
+// two fresh wires (v1, v2) gives sum_x |x>_v1 |x>_v2; the bridging gate G then acts on (v1, b)
+// with v1 in the role of qubit a, so v1 ends as a' = G's output for a, v2 keeps a = G's input,
+// and b's wire holds b''.  Both tensors number their pairs in the order of the bridging gates.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace sycsim;
+
+namespace {
+
+// 4x4 fan-out, index b(q0) + 2 b(q1): |00> -> |00> + |11>.  The other columns (never reached
+// from fresh wires) complete sqrt(2) times an orthogonal matrix so fused blocks stay well scaled.
+void fanout_gate(int w0, int w1, sim_gate &g)
+{
+    std::memset(&g, 0, sizeof g);
+    g.kind = SIM_GATE_U2;
+    g.q0 = w0;
+    g.q1 = w1;
+    static const double m[4][4] = {{1, 0, 0, 1}, {0, 1, 1, 0}, {0, 1, -1, 0}, {1, 0, 0, -1}};
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) g.u[2 * (4 * r + c)] = m[r][c];
+}
+
+}  // namespace
+
+extern "C" int sim_split_create(int n_qubits, int n_gates, const sim_gate *gates, const int *side,
+                                sim_split_t **out)
+{
+    if (!out) return fail(nullptr, SIM_E_INVAL, "sim_split_create: NULL out");
+    *out = nullptr;
+    if (n_qubits < 2 || n_qubits > kMaxQubits || !side || n_gates < 0 || (n_gates > 0 && !gates))
+        return fail(nullptr, SIM_E_INVAL, "sim_split_create: bad arguments");
+    int n_side[2] = {0, 0}, live[kMaxQubits];
+    for (int q = 0; q < n_qubits; ++q) {
+        if (side[q] != 0 && side[q] != 1)
+            return fail(nullptr, SIM_E_INVAL, "sim_split_create: side[%d] = %d is not 0 or 1", q, side[q]);
+        live[q] = n_side[side[q]]++;
+    }
+    if (n_side[0] == 0 || n_side[1] == 0)
+        return fail(nullptr, SIM_E_INVAL, "sim_split_create: both sides need qubits");
+    int pairs = 0;
+    for (int i = 0; i < n_gates; ++i) {
+        const sim_gate &g = gates[i];
+        double m[32];
+        const int d = gate_matrix(g, m);
+        if (d == 0 || g.q0 < 0 || g.q0 >= n_qubits)
+            return fail(nullptr, SIM_E_INVAL, "sim_split_create: bad gate %d", i);
+        if (d == 4) {
+            if (g.q1 < 0 || g.q1 >= n_qubits || g.q1 == g.q0)
+                return fail(nullptr, SIM_E_INVAL, "sim_split_create: bad qubits in gate %d", i);
+            if (side[g.q0] != side[g.q1]) ++pairs;
+        }
+    }
+    for (int t = 0; t < 2; ++t)
+        if (n_side[t] + 2 * pairs > kMaxQubits)
+            return fail(nullptr, SIM_E_INVAL, "sim_split_create: tensor %d needs %d wires (limit %d)", t + 1,
+                        n_side[t] + 2 * pairs, kMaxQubits);
+
+    sim_split_s *s = new (std::nothrow) sim_split_s;
+    if (!s) return fail(nullptr, SIM_E_NOMEM_HOST, "sim_split_create: out of host memory");
+    s->n = n_qubits;
+    s->n_side[0] = n_side[0];
+    s->n_side[1] = n_side[1];
+    s->n_pairs = pairs;
+    s->side.assign(side, side + n_qubits);
+    std::vector<int> pair_ap[2], pair_a[2];  // wires of a'_j, a_j in each tensor
+    int j = 0;
+    for (int i = 0; i < n_gates; ++i) {
+        sim_gate g = gates[i];
+        double m[32];
+        const bool two = gate_matrix(g, m) == 4;
+        if (!two || side[g.q0] == side[g.q1]) {
+            const int t = side[g.q0];
+            g.q0 = live[g.q0];
+            if (two) g.q1 = live[g.q1];
+            s->gates[t].push_back(g);
+            continue;
+        }
+        const bool a_is_q0 = side[g.q0] == 0;
+        const int a = a_is_q0 ? g.q0 : g.q1, b = a_is_q0 ? g.q1 : g.q0;
+        sim_gate f;
+        // EI on tensor 1
+        const int w1 = n_side[0] + 2 * j, w2 = w1 + 1;
+        fanout_gate(w1, w2, f);
+        s->gates[0].push_back(f);
+        pair_ap[0].push_back(w2);
+        pair_a[0].push_back(live[a]);
+        live[a] = w1;
+        // E2Q on tensor 2
+        const int v1 = n_side[1] + 2 * j, v2 = v1 + 1;
+        fanout_gate(v1, v2, f);
+        s->gates[1].push_back(f);
+        if (a_is_q0) {
+            g.q0 = v1;
+            g.q1 = live[b];
+        } else {
+            g.q0 = live[b];
+            g.q1 = v1;
+        }
+        s->gates[1].push_back(g);
+        pair_ap[1].push_back(v1);
+        pair_a[1].push_back(v2);
+        ++j;
+    }
+    for (int t = 0; t < 2; ++t) {
+        std::vector<int> &w = s->wire_at[t];
+        for (int q = 0; q < n_qubits; ++q)
+            if (side[q] == t) w.push_back(live[q]);
+        for (int p = 0; p < pairs; ++p) {
+            w.push_back(pair_ap[t][p]);
+            w.push_back(pair_a[t][p]);
+        }
+    }
+    *out = s;
+    return SIM_OK;
+}
+
+extern "C" int sim_split_info(const sim_split_t *s, int *n_side, int *n_wires, int *n_pairs, int *n_gates)
+{
+    if (!s) return fail(nullptr, SIM_E_INVAL, "sim_split_info: NULL split");
+    for (int t = 0; t < 2; ++t) {
+        if (n_side) n_side[t] = s->n_side[t];
+        if (n_wires) n_wires[t] = s->n_side[t] + 2 * s->n_pairs;
+        if (n_gates) n_gates[t] = (int)s->gates[t].size();
+    }
+    if (n_pairs) *n_pairs = s->n_pairs;
+    return SIM_OK;
+}
+
+extern "C" int sim_split_gates(const sim_split_t *s, int t, sim_gate *out)
+{
+    if (!s || (t != 0 && t != 1) || !out) return fail(nullptr, SIM_E_INVAL, "sim_split_gates: bad arguments");
+    if (!s->gates[t].empty()) std::memcpy(out, s->gates[t].data(), s->gates[t].size() * sizeof(sim_gate));
+    return SIM_OK;
+}
+
+extern "C" int sim_split_canonical(const sim_split_t *s, int t, int *wire_at)
+{
+    if (!s || (t != 0 && t != 1) || !wire_at)
+        return fail(nullptr, SIM_E_INVAL, "sim_split_canonical: bad arguments");
+    for (size_t p = 0; p < s->wire_at[t].size(); ++p) wire_at[p] = s->wire_at[t][p];
+    return SIM_OK;
+}
+
+extern "C" int sim_split_destroy(sim_split_t *s)
+{
+    delete s;
+    return SIM_OK;
+}

@@ -240,3 +240,99 @@ def test_phase_set_choice_weights_and_errors(pkg):
     for bad in ((n, 0), (n, 9), (1, 1)):
         with pytest.raises(pkg.SimError):
             pkg.sim_phases_choose_sets(bad[0], pkg.gates_array(circ), bad[1])
+
+
+# ---- contraction deferral: the split's gate lists against the oracle's EI / E2Q tensors ----
+
+def _records_from_tuples(pkg, gates):
+    recs = np.zeros(len(gates), dtype=pkg._native.GATE_DTYPE)
+    for i, g in enumerate(gates):
+        recs[i]["kind"], recs[i]["q0"], recs[i]["q1"] = g[0], g[1], g[2]
+        for j, f in enumerate(("theta", "phi", "dplus", "dminus", "dminus_off")):
+            recs[i][f] = g[3 + j] if len(g) > 3 + j else 0.0
+    return recs
+
+
+def _run_records_on_oracle(pkg, oracle_mod, n, recs):
+    """The oracle applies a gate-record list one gate at a time (matrices of the standard kinds
+    from the oracle; caller-given U1/U2 matrices as stored in the records)."""
+    psi = oracle_mod.basis_state(n, 0)
+    for r in recs:
+        kind = int(r["kind"])
+        if kind == pkg.SIM_GATE_U2:
+            oracle_mod.apply_2q(psi, int(r["q0"]), int(r["q1"]), r["u"].view(np.complex128).reshape(4, 4))
+        elif kind == pkg.SIM_GATE_U1:
+            oracle_mod.apply_1q(psi, int(r["q0"]), r["u"][:8].view(np.complex128).reshape(2, 2))
+        elif kind == si.FSIM:
+            u = oracle_mod.gate_matrix(kind, r["theta"], r["phi"], r["dplus"], r["dminus"], r["dminus_off"])
+            oracle_mod.apply_2q(psi, int(r["q0"]), int(r["q1"]), u)
+        else:
+            oracle_mod.apply_1q(psi, int(r["q0"]), oracle_mod.gate_matrix(kind))
+    return psi
+
+
+def _split_cases():
+    rng = np.random.default_rng(11)
+    cases = []
+    for seed, n in ((0, 4), (1, 6), (2, 7)):
+        gates = []
+        for _ in range(3 * n):
+            if rng.random() < 0.4:
+                gates.append((int(rng.integers(3)), int(rng.integers(n)), -1))
+            else:
+                q0, q1 = (int(x) for x in rng.choice(n, 2, replace=False))
+                gates.append((si.FSIM, q0, q1, *(float(x) for x in rng.uniform(-3, 3, 5))))
+        side = [int(x) for x in rng.permutation([0] * (n // 2) + [1] * (n - n // 2))]
+        cases.append((n, gates, side))
+    circ = si.sycamore_circuit(si.Grid(3, 4), cycles=6, seed=4)
+    cases.append((12, [tuple(g) for g in circ.gates], [0 if (q % 4) < 2 else 1 for q in range(12)]))
+    return cases
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_split_gate_lists_reproduce_oracle_tensors(pkg, oracle_mod, case):
+    n, gates, side = _split_cases()[case]
+    recs = _records_from_tuples(pkg, gates)
+    s = pkg.sim_split_create(n, recs, side)
+    try:
+        n_side, n_wires, pairs, n_gates = pkg.sim_split_info(s)
+        o1, o2, c = oracle_mod.split_tensors(n, gates, side)
+        assert pairs == c and n_side == [side.count(0), side.count(1)]
+        assert n_wires == [n_side[0] + 2 * c, n_side[1] + 2 * c]
+        for t, want in ((0, o1), (1, o2)):
+            tg = pkg.sim_split_gates(s, t)
+            assert tg.size == n_gates[t]
+            wire_at = pkg.sim_split_canonical(s, t)
+            assert sorted(wire_at) == list(range(n_wires[t]))
+            perm = [0] * n_wires[t]
+            for p, w in enumerate(wire_at):
+                perm[w] = p
+            got = oracle_mod.permute(_run_records_on_oracle(pkg, oracle_mod, n_wires[t], tg), perm)
+            assert np.linalg.norm(got - want) < 1e-12 * max(1.0, np.linalg.norm(want))
+            # and through the aggregation planner: fused blocks of the tensor's gate list
+            plan = pkg.sim_plan_create(n_wires[t], tg, kmax=4)
+            psi = oracle_mod.basis_state(n_wires[t], 0)
+            for tt, m in plan_blocks(pkg, plan):
+                oracle_mod.apply_kq(psi, tt, m)
+            pkg.sim_plan_destroy(plan)
+            assert np.linalg.norm(oracle_mod.permute(psi, perm) - want) < 1e-11 * max(1.0, np.linalg.norm(want))
+    finally:
+        pkg.sim_split_destroy(s)
+
+
+def test_split_rejects_bad_input(pkg):
+    recs = _records_from_tuples(pkg, [(0, 0, -1), (si.FSIM, 0, 1, 1.0, 0.5)])
+    for side in ([0, 0], [1, 1], [0, 2], [-1, 1]):
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_split_create(2, recs, side)
+        assert e.value.code == pkg.SIM_E_INVAL
+    bad = _records_from_tuples(pkg, [(si.FSIM, 1, 1, 1.0, 0.5)])
+    with pytest.raises(pkg.SimError):
+        pkg.sim_split_create(2, bad, [0, 1])
+    # 20 bridging gates on one pair of qubits: 1 + 40 wires per tensor exceeds the 40-qubit limit
+    many = _records_from_tuples(pkg, [(si.FSIM, 0, 1, 1.0, 0.5)] * 20)
+    with pytest.raises(pkg.SimError):
+        pkg.sim_split_create(2, many, [0, 1])
+    L = pkg.lib()
+    assert L.sim_contract(None, None, None, None, 0) == pkg.SIM_E_INVAL
+    assert L.sim_split_info(None, None, None, None, None) == pkg.SIM_E_INVAL

@@ -2,7 +2,9 @@
 
 * 30 qubits, 20 cycles (5x6 grid; 8 GiB complex64 state): every amplitude against the oracle
   (complex128, gate by gate, all host cores), for the FP32 plan (k <= 4) and the tensor-core
-  plans (k <= 5, 3xFP16 on mma.sync and on tcgen05).  Bound ||psi - psi_oracle||_2 <= 1e-5.
+  plans (k <= 5, 3xFP16 on mma.sync and on tcgen05), and the contraction-deferral pipeline (the
+  first 6 cycles as two tensors contracted into the state, FP32 and tcgen05), every amplitude.
+  Bound ||psi - psi_oracle||_2 <= 1e-5.
 * 33 qubits (6x6 minus three corners; 64 GiB) held as 8 slices over the 3 top bits, run as
   alternating phases with in-place bit permutations between them (Sect. 4 in device memory):
   norm and Porter-Thomas, no oracle fits.  Its 28-qubit sub-lattice circuit (4x7, same depth)
@@ -72,6 +74,33 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
                                  ("fp16x3_tmem_k5", 5, pkg.SIM_FP16X3_TMEM)):
             plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=kmax, precision=prec)
             pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plan)
+            pkg.sim_plan_destroy(plan)
+            results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
+        # contraction deferral (Sect. 2): the first 6 cycles as two 15-qubit tensors split between
+        # lattice columns 2 and 3 (patterns A, B bridge the cut 5 times: 4^5 entanglement
+        # values), contracted into the state, the remaining gates as fused blocks on it
+        grid = si.Grid(5, 6)
+        front = sum(n + len(grid.pattern(si.PATTERN_ORDER[t % 8])) for t in range(6))
+        side = [0 if c < 3 else 1 for (r, c) in grid.sites()]
+        gates = pkg.gates_array(circ)
+        for name, kmax, prec in (("split6_fp32_k4", 4, pkg.SIM_FP32),
+                                 ("split6_fp16x3_tmem_k5", 5, pkg.SIM_FP16X3_TMEM)):
+            s = pkg.sim_split_create(n, gates[:front], side)
+            _, n_wires, pairs, _ = pkg.sim_split_info(s)
+            assert pairs == 5 and n_wires == [25, 25]
+            hs = []
+            for t in range(2):
+                ht = pkg.sim_create(n_wires[t])
+                plan = pkg.sim_plan_create(n_wires[t], pkg.sim_split_gates(s, t), kmax=kmax, precision=prec)
+                pkg.sim_apply_plan(ht, plan)
+                pkg.sim_plan_destroy(plan)
+                hs.append(ht)
+            pkg.sim_contract(h, hs[0], hs[1], s, prec)
+            for ht in hs:
+                pkg.sim_destroy(ht)
+            pkg.sim_split_destroy(s)
+            plan = pkg.sim_plan_create(n, gates[front:], kmax=kmax, precision=prec)
             pkg.sim_apply_plan(h, plan)
             pkg.sim_plan_destroy(plan)
             results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
