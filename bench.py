@@ -2,11 +2,16 @@
 """Benchmark: simulate the 30-qubit, 20-cycle Sycamore-pattern circuit (5x6 grid, ABCDCDAB,
 fSim(pi/2, pi/6), random sqrt(X/Y/W)) on one GB300 and report amplitude updates per second.
 
-One step = one pass of the whole hot path over one circuit: aggregation planning and FP64
-composition (host), reset to |0...0>, every fused block applied on the device, and the
-norm / Porter-Thomas / XEB reduction.  Each step's plan is built on the host while the previous
-step's last blocks run on the device.  The state (8 GiB complex64) is larger than L2, so no
-flush is needed between steps.
+One step = one pass of the whole hot path over one circuit, in the paper's order: the first
+phase by contraction deferral (Sect. 2 and Sect. 4's subcircuits 1 and 2: the gates up to the
+sixth one that crosses the lattice's middle column cut run as two 15-qubit tensors with
+entanglement indices, EI / E2Q of the Appendix, then one tensor-core contraction writes the
+2^30-amplitude state), then aggregation planning and FP64 composition (host) of the remaining
+gates and every fused block applied on the device, and the norm / Porter-Thomas / XEB
+reduction.  Each step's plan is built on the host while the previous step's last blocks run on
+the device; the split and its two tensors' plans are built once.  The state (8 GiB complex64) is
+larger than L2, so no flush is needed between steps.  The JSON line also reports the same
+circuit without the split ("plain_path": fused blocks from |0...0>).
 
 metric value = 2^n * (original gates) * steps / device time   ("gate" amplitude updates/s)
 pass updates = 2^n * (fused blocks) * steps / device time      (roofline basis, 16 B/amp/pass)
@@ -54,6 +59,10 @@ def parse():
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "fp16x3_tmem", "tf32x3", "tf32"],
                     help="arithmetic of blocks with k >= 5 when --kmax is given (narrower blocks always "
                          "run FP32 on CUDA cores)")
+    ap.add_argument("--front-pairs", type=int, default=5,
+                    help="contraction deferral (Sect. 2): the longest prefix of the circuit that "
+                         "bridges the lattice's middle column cut at most this many times runs as "
+                         "two tensors and their contraction; 0 = plain fused blocks only")
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
@@ -149,12 +158,15 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
 TCGEN05_TRAFFIC_GB = 4 * (2.147897 + 2.088273)  # k_apply_tcgen05<5, 2, 0>, ncu at 2^28 amplitudes
 
 
-def measured_peaks():
+def measured_peaks(key: str = "hbm_gbs"):
+    """A measured peak from MEASURED_PEAKS.json (HBM copy GB/s, or bf16 TFLOP/s), else the
+    profiling recipe's fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs"), "measured"
-    return 6800.0, "fallback"
+        if d.get(key):
+            return d[key], "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key], "fallback"
 
 
 def cpu_baseline(circ, sample_gates: int, steps: int = 1):
@@ -328,6 +340,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def front_cut(circ, grid, max_pairs: int):
+    """Sides (lattice columns left / right of the middle) and the length of the longest prefix
+    of the gate list whose two-qubit gates bridge the cut at most max_pairs times."""
+    cols = max(c for (_, c) in grid.sites()) + 1
+    side = [0 if c < cols // 2 else 1 for (_, c) in grid.sites()]
+    pairs = 0
+    for i, (kind, q0, q1, _, _) in enumerate(circ.gates):
+        if q1 >= 0 and side[q0] != side[q1]:
+            if pairs == max_pairs:
+                return side, i, pairs
+            pairs += 1
+    return side, len(circ.gates), pairs
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -363,15 +389,48 @@ def run_ours(args):
         tuned = {"by": "sim_autotune (FP32-equivalent arithmetic)", "kmax": kmax,
                  "precision": args.precision, "tuning_run_ms": tune_ms}
 
+    # contraction deferral (Sect. 2, the paper's first phase): the circuit's first gates, up to
+    # the (front_pairs + 1)-th gate across the middle column cut, as two half-lattice tensors
+    # with entanglement indices, contracted into the state; the rest as fused blocks on it
+    front = None
+    n_front, front_info = 0, None
+    if args.front_pairs > 0:
+        side, n_front, pairs = front_cut(circ, si.WORKLOADS[args.workload]["grid"], args.front_pairs)
+        split = pkg.sim_split_create(n, gates[:n_front], side)
+        n_side, n_wires, _, n_tg = pkg.sim_split_info(split)
+        front = {}
+
+        def front_for(hh):
+            if hh.value not in front:
+                front[hh.value] = pkg.sim_front_create(hh, split, kmax=args.kmax, precision=prec)
+            return front[hh.value]
+        tplans = [pkg.sim_plan_create(n_wires[t], pkg.sim_split_gates(split, t), kmax=args.kmax,
+                                      precision=prec) for t in range(2)]
+        front_info = {"gates": n_front, "bridging_gates": pairs, "entanglement_values": 4 ** pairs,
+                      "sides": "lattice columns < C/2 | >= C/2", "qubits_per_side": n_side,
+                      "tensor_qubits": n_wires,
+                      "tensor_blocks": [pkg.sim_plan_info(p)[0] for p in tplans],
+                      "contraction": "tcgen05 3xFP16" if prec in (pkg.SIM_FP16X3, pkg.SIM_FP16X3_TMEM)
+                      else "FP32 CUDA cores"}
+        for p in tplans:
+            pkg.sim_plan_destroy(p)
+    rest = gates[n_front:]
+
+    def start(hh):
+        if front is None:
+            pkg.sim_reset(hh)
+        else:
+            pkg.sim_front_run(hh, front_for(hh))
+
     def run_steps(k):
         # k circuit runs; each plan (host: grouping + FP64 composition) is built while the
         # previous run's blocks are still executing (sim_apply_plan returns once the last blocks
         # are queued; sim_reduce waits for the result)
-        plan = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec)
+        plan = pkg.sim_plan_create(n, rest, kmax=args.kmax, precision=prec)
         for s in range(k):
-            pkg.sim_reset(h)
+            start(h)
             pkg.sim_apply_plan(h, plan)
-            nxt = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec) if s + 1 < k else None
+            nxt = pkg.sim_plan_create(n, rest, kmax=args.kmax, precision=prec) if s + 1 < k else None
             out = pkg.sim_reduce(h)
             nb = pkg.sim_plan_info(plan)[0]
             pkg.sim_plan_destroy(plan)
@@ -399,6 +458,7 @@ def run_ours(args):
     launches = pkg.sim_launch_count(h) - launches0
     a_n, a_ms, a_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
     r_n, r_ms, r_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_REDUCE)
+    c_n, c_ms, c_flops = pkg.sim_profile_read(h, pkg.SIM_PROF_CONTRACT)
     pkg.sim_profile_enable(h, False)
 
     ms_max = max_over_ranks(ms, dist)
@@ -414,21 +474,22 @@ def run_ours(args):
     h2 = pkg.sim_create(n, 0, device=local)
     outs = [pkg.pinned_array(amps, dtype=np.complex64), pkg.pinned_array(amps, dtype=np.complex64)]
     hs = [h, h2]
+    rest_pinned = gates_pinned[n_front:]
     for hw, ow in zip(hs, outs):  # one untimed end-to-end step on each handle (warm-up)
-        pw = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
-        pkg.sim_reset(hw)
+        pw = pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
+        start(hw)
         pkg.sim_apply_plan(hw, pw)
         pkg.sim_amplitudes_async(hw, ow)
         pkg.sim_sync(hw)
         pkg.sim_plan_destroy(pw)
     barrier()
     t0 = time.perf_counter()
-    plan = pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
+    plan = pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
     for s_ in range(args.e2e_steps):
         hc = hs[s_ % 2]
-        pkg.sim_reset(hc)
+        start(hc)
         pkg.sim_apply_plan(hc, plan)
-        nxt = (pkg.sim_plan_create(n, gates_pinned, kmax=args.kmax, precision=prec)
+        nxt = (pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
                if s_ + 1 < args.e2e_steps else None)
         pkg.sim_amplitudes_async(hc, outs[s_ % 2])
         if s_ > 0:
@@ -443,7 +504,33 @@ def run_ours(args):
     for o in outs:
         pkg.sim_host_free(o.ctypes.data)
     pkg.sim_host_free(gates_pinned.ctypes.data)
+    if front is not None:
+        for hv in list(front):
+            if hv == h2.value:
+                pkg.sim_front_destroy(front.pop(hv))
     pkg.sim_destroy(h2)
+    # the same circuit without the split (plain fused blocks from |0...0>), same timing method
+    plain_path = None
+    if front is not None:
+        def step_plain():
+            plan = pkg.sim_plan_create(n, gates, kmax=args.kmax, precision=prec)
+            pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plan)
+            out = pkg.sim_reduce(h)
+            nb = pkg.sim_plan_info(plan)[0]
+            pkg.sim_plan_destroy(plan)
+            return out, nb
+        for _ in range(args.warmup):
+            step_plain()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            _, nbp = step_plain()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msp = e0.elapsed_time(e1)
+        plain_path = {"value": float(amps) * circ.n_gates * args.steps / (msp / 1e3), "unit": UNIT,
+                      "ms_per_step": msp / args.steps, "fused_blocks": nbp}
     # the FP32-only path on the same state and timing method (blocks of <= 4 qubits)
     fp32_path = None
     if not args.no_fp32_path:
@@ -481,6 +568,10 @@ def run_ours(args):
         tg, _ = pkg.sim_plan_block(plan, i)
         matrix_bytes += 8 * (1 << (2 * len(tg)))
     pkg.sim_plan_destroy(plan)
+    if front is not None:
+        for f in front.values():
+            pkg.sim_front_destroy(f)
+        pkg.sim_split_destroy(split)
     pkg.sim_destroy(h)
 
     if rank != 0:
@@ -518,12 +609,29 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "launches": a_n, "avg_launch_ms": a_ms / max(a_n, 1)},
         "breakdown_ms_per_step": {"apply": a_ms / args.steps, "reduce": r_ms / args.steps,
-                                  "other": ms_max / args.steps - (a_ms + r_ms) / args.steps},
+                                  "contract": c_ms / args.steps,
+                                  "other": ms_max / args.steps - (a_ms + r_ms + c_ms) / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes + matrix_bytes),
                 "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps,
                 "pipelined": "two handles: the readout of step i overlaps the compute of step i+1"},
         "clocks": clk.summary(),
     }
+    if front_info is not None:
+        line["config"]["front"] = front_info
+        bf16, bf16_kind = measured_peaks("bf16_tflops")
+        ach_c = c_flops / (c_ms / 1e3) / 1e12 if c_ms > 0 else None
+        # the contraction's tensor roofline: algorithmic complex-GEMM FLOPs (8 per complex
+        # multiply-add) per launch / its CUDA-event time; 3xFP16 issues 3 FP16 MMA FLOPs per
+        # algorithmic FLOP, so the tensor pipe runs at 3 x achieved
+        line["contract_roofline"] = {
+            "bound": "tensor", "kernel": "k_contract_tcgen05" if "tcgen05" in front_info["contraction"]
+            else "k_contract_fp32", "achieved": ach_c, "peak": bf16, "unit": "TFLOP/s",
+            "frac": ach_c / bf16 if ach_c else None, "mma_flops_per_alg_flop": 3,
+            "tensor_pipe_frac": 3 * ach_c / bf16 if ach_c else None,
+            "peak_source": f"{bf16_kind} bf16_tflops (FP16 runs at the BF16 rate)",
+            "launches": c_n, "avg_launch_ms": c_ms / max(c_n, 1),
+            "alg_flops_per_launch": c_flops / max(c_n, 1)}
+        line["plain_path"] = plain_path
     if fp32_path:
         line["fp32_path"] = fp32_path
     if ws == 1 and not args.no_serving:

@@ -398,14 +398,28 @@ int sim_split_destroy(sim_split_t *s);
  * tensors (their gate lists applied); out: a device-resident handle of n_qubits qubits, not
  * sliced, distinct from both.  First permutes t1 and t2 into their canonical layouts (on their
  * own streams; the tensors' logical content is unchanged); then, on out's stream after both, one
- * complex GEMM over the 4^n_pairs entanglement values writes psi with the physical layout
- * side-0 qubits at bits 0 .. n_side[0]-1 and side-1 qubits above (out's layout map is set to
- * that).  t1's and t2's streams wait for the GEMM before any later work on them.
+ * complex GEMM over the 4^n_pairs entanglement values writes every amplitude of psi, in out's
+ * current layout (out's layout map is unchanged; its previous amplitudes are overwritten).
+ * t1's and t2's streams wait for the GEMM before any later work on them.
  * precision: SIM_FP32 (CUDA cores, FP32 products and sums), or SIM_FP16X3 / SIM_FP16X3_TMEM
  * (tcgen05 tensor cores: each tensor scaled by one power of two, split into FP16 hi + lo, the
  * products hi*hi + hi*lo + lo*hi summed in FP32; needs n_side[0] >= 7 and n_side[1] >= 7,
  * otherwise the FP32 kernel runs).  Asynchronous.  SIM_E_INVAL for handles that do not fit s. */
 int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision);
+
+/* A split made ready to run (Sect. 2's subcircuits 1 and 2 and their contraction as one reusable
+ * unit).  sim_front_create plans both tensors' gate lists (o as for sim_plan_create; NULL: k_max
+ * 4, SIM_FP32) and creates their device states (2^n_wires[t] amplitudes each) on out's device and
+ * stream; it keeps its own copy of the split.  sim_front_run enqueues on out's stream: both tensors
+ * reset to |0..0>, their blocks applied, and sim_contract into out -- on the tensor cores
+ * (SIM_FP16X3_TMEM) when o->precision is SIM_FP16X3 or SIM_FP16X3_TMEM, else in FP32.  out must
+ * have the split's n_qubits qubits, be device-resident and not sliced, and live on the front's
+ * device.  Asynchronous like sim_apply_plan; the tensors' kernels count in out's
+ * sim_launch_count.  sim_front_destroy waits for the front's work. */
+typedef struct sim_front_s sim_front_t;
+int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan_opts *o, sim_front_t **f);
+int sim_front_run(sim_t *out, sim_front_t *f);
+int sim_front_destroy(sim_front_t *f);
 
 /* ---- checkpoint / resume (not in the paper) --------------------------------
  * Save the whole state to a file, and load it back, e.g. at a phase boundary of a long streamed

@@ -146,6 +146,10 @@ _SIGS = {
     "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_contract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int]),
+    "sim_front_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "sim_front_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_front_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_state_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_state_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_phases_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -512,6 +516,24 @@ def sim_split_destroy(s) -> None:
 
 def sim_contract(out, t1, t2, s, precision: int = SIM_FP32) -> None:
     _check(lib().sim_contract(out, t1, t2, s, precision), out)
+
+
+def sim_front_create(out, s, kmax: int = 4, precision: int = SIM_FP32):
+    """Both tensors of split s planned and allocated on out's device and stream."""
+    o = PlanOpts()
+    o.kmax = kmax
+    o.precision = precision
+    f = ctypes.c_void_p()
+    _check(lib().sim_front_create(out, s, ctypes.byref(o), ctypes.byref(f)), out)
+    return f
+
+
+def sim_front_run(out, f) -> None:
+    _check(lib().sim_front_run(out, f), out)
+
+
+def sim_front_destroy(f) -> None:
+    _check(lib().sim_front_destroy(f))
 
 
 def sim_state_save(h, path: str) -> None:

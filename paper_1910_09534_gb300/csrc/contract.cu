@@ -4,7 +4,9 @@
 // With both tensors in their canonical layouts (side qubits at the low bits, the 2c
 // entanglement bits above, in the same order in both), tensor 1 is a matrix T1[e][x] and tensor
 // 2 a matrix T2[e][y] (x, y contiguous), and
-//     psi[x + y 2^n1] = sum_e T1[e][x] T2[e][y],   e < 4^c.
+//     psi[P(x, y)] = sum_e T1[e][x] T2[e][y],   e < 4^c,
+// where P places x's bits on the side-0 qubits and y's on the side-1 qubits in the output
+// handle's current physical layout.
 // Two kernels compute it:
 //  * k_contract_fp32 (CUDA cores): 64 x 64 output tiles, 4 x 4 per thread, FP32 products and
 //    sums, operands staged through shared memory 16 entanglement values at a time;
@@ -38,15 +40,36 @@ namespace {
 
 constexpr int kFx = 64, kFy = 64, kFk = 16;  // FP32 kernel: tile x, tile y, entanglement chunk
 
+// Where psi lands: bit i of x (side-0 qubit i, increasing qubit order) adds xbit[i] to the
+// physical index, bit j of y adds ybit[j] (powers of two from the output handle's layout).
+struct CtOut {
+    uint64_t xbit[kMaxQubits];
+    uint64_t ybit[kMaxQubits];
+};
+
+__device__ __forceinline__ uint64_t ct_dep(uint64_t v, const uint64_t *bit, int nb)
+{
+    uint64_t o = 0;
+    for (int i = 0; i < nb; ++i)
+        if ((v >> i) & 1) o += bit[i];
+    return o;
+}
+
 __global__ void __launch_bounds__(256) k_contract_fp32(const float2 *__restrict__ t1, const float2 *__restrict__ t2,
-                                                       float2 *__restrict__ psi, int n1, int n2, uint64_t n_e)
+                                                       float2 *__restrict__ psi, int n1, int n2, uint64_t n_e,
+                                                       const __grid_constant__ CtOut o)
 {
     __shared__ __align__(16) float2 sa[kFk][kFx];
     __shared__ __align__(16) float2 sb[kFk][kFy];
+    __shared__ uint64_t xoff[kFx], yoff[kFy];
     const uint64_t X = 1ull << n1, Y = 1ull << n2;
     const uint64_t tiles_x = (X + kFx - 1) / kFx;
     const uint64_t x0 = (blockIdx.x % tiles_x) * kFx, y0 = (blockIdx.x / tiles_x) * kFy;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid < kFx)
+        xoff[tid] = ct_dep(x0 + tid, o.xbit, n1);
+    else if (tid < kFx + kFy)
+        yoff[tid - kFx] = ct_dep(y0 + tid - kFx, o.ybit, n2);
     float2 acc[4][4];  // [y][x]
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -85,18 +108,18 @@ __global__ void __launch_bounds__(256) k_contract_fp32(const float2 *__restrict_
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const uint64_t x = x0 + 4 * tx + i;
-            if (x < X) psi[x + y * X] = acc[j][i];
+            if (x < X) psi[xoff[4 * tx + i] + yoff[4 * ty + j]] = acc[j][i];
         }
     }
 }
 
 int launch_contract_fp32(const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                         cudaStream_t st)
+                         const CtOut &o, cudaStream_t st)
 {
     const uint64_t X = 1ull << n1, Y = 1ull << n2;
     const uint64_t blocks = ((X + kFx - 1) / kFx) * ((Y + kFy - 1) / kFy);
     if (blocks > 0x7fffffffull) return -1;
-    k_contract_fp32<<<(unsigned)blocks, 256, 0, st>>>(t1, t2, psi, n1, n2, 1ull << e_bits);
+    k_contract_fp32<<<(unsigned)blocks, 256, 0, st>>>(t1, t2, psi, n1, n2, 1ull << e_bits, o);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -116,7 +139,7 @@ struct CtArgs {
     const uint8_t *aimg;  // tensor 1 as the A operand: [x tile][k-step] blocks of 16 KiB
     const uint8_t *bimg;  // tensor 2 as the B operand: [y tile][k-step] blocks of 16 KiB
     float2 *psi;
-    int n1;               // psi index = x + y 2^n1
+    int n1, n2;           // psi's physical index: CtOut offsets of x (n1 bits) plus of y (n2 bits)
     uint32_t ks;          // k-steps (16 entanglement values each) per tile
     uint32_t tiles_x, tiles_y;
     const float *amax;    // largest |component| of tensor 1, tensor 2
@@ -305,10 +328,11 @@ __global__ void __launch_bounds__(256) k_contract_image(const float2 *__restrict
 //   MMA thread: before a tile's first step wait acc_empty of tile tl - 1; wait full[stage], issue
 //     the 6 MMAs, commit to empty[stage]; after the last step commit to acc_full;
 //   epilogue: wait acc_full (phase tl), read, store, arrive acc_empty.
-__global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g)
+__global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g, const __grid_constant__ CtOut o)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ __align__(8) uint64_t full[kCtStages], empty[kCtStages], acc_full, acc_empty;
+    __shared__ uint64_t xoff[128], yoff[128];  // offsets of x, y within a tile (bits 0-6)
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -412,9 +436,16 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g)
         const int q = warp & 3;                 // TMEM lane quarter this warp may read
         const int half = (warp - 2) >> 2;       // warps 2-5: y 0..63 of the tile, 6-9: y 64..127
         const int row = 32 * q + lane;          // x within the tile
-        const uint64_t X = 1ull << g.n1;
         const float inv = ldexpf(1.f, -(ct_shift(g.amax[0]) + ct_shift(g.amax[1])));
         const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+        {
+            const int e = tid - 64;
+            if (e < 128)
+                xoff[e] = ct_dep(e, o.xbit, 7);
+            else
+                yoff[e - 128] = ct_dep(e - 128, o.ybit, 7);
+            ct_bar_and(1, kCtEpi, true);  // tables written before any store reads them
+        }
         uint32_t tl = 0;
         for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tl) {
             const bool ok = ct_wait(ct_smem(&acc_full), tl & 1, ab);
@@ -425,7 +456,8 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g)
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             uint32_t tx, ty;
             ct_tile(tile, g.tiles_x, g.tiles_y, tx, ty);
-            float2 *dst = g.psi + (uint64_t)tx * 128 + row + (uint64_t)ty * 128 * X;
+            float2 *dst = g.psi + ct_dep((uint64_t)tx << 7, o.xbit, g.n1) + ct_dep((uint64_t)ty << 7, o.ybit, g.n2) +
+                          xoff[row];
 #pragma unroll 1
             for (int c = 0; c < 64; c += 16) {
                 const int y0 = half * 64 + c;
@@ -437,7 +469,7 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g)
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    __stcs(dst + (uint64_t)(y0 + j) * X, make_float2((xr[j] - yi[j]) * inv, (xi[j] + yr[j]) * inv));
+                    __stcs(dst + yoff[y0 + j], make_float2((xr[j] - yi[j]) * inv, (xi[j] + yr[j]) * inv));
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             ct_arrive(ct_smem(&acc_empty));
@@ -451,7 +483,7 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g)
 
 // Images, then the GEMM, all on st; the scratch (images + maxima) is stream-ordered memory.
 int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                            cudaStream_t st)
+                            const CtOut &o, cudaStream_t st)
 {
     static const LaunchCfg cfg = [] {
         LaunchCfg c;
@@ -487,6 +519,7 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         g.bimg = scratch + a_bytes;
         g.psi = psi;
         g.n1 = n1;
+        g.n2 = n2;
         g.ks = ks;
         g.tiles_x = (uint32_t)(X / 128);
         g.tiles_y = (uint32_t)(Y / 128);
@@ -494,7 +527,7 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         g.err = h->d_errflag;
         const uint64_t grid = std::min<uint64_t>((uint64_t)g.tiles_x * g.tiles_y, (uint64_t)cfg.sms);
         const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * (double)X * (double)Y * (double)n_e, st);
-        k_contract_tcgen05<<<(unsigned)grid, kCtThreads, kCtStages * kCtStage, st>>>(g);
+        k_contract_tcgen05<<<(unsigned)grid, kCtThreads, kCtStages * kCtStage, st>>>(g, o);
         prof_end(h, ps, st);
         if (cudaGetLastError() != cudaSuccess) rc = -1;
     }
@@ -549,12 +582,19 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         destroy();
         return fail(out, SIM_E_CUDA, "sim_contract: stream ordering failed");
     }
+    // psi goes straight into out's current layout
+    CtOut o{};
+    int b[2] = {0, 0};
+    for (int q = 0; q < s->n; ++q) {
+        const int t = s->side[q];
+        (t == 0 ? o.xbit : o.ybit)[b[t]++] = 1ull << out->bit_of[q];
+    }
     int rc;
     if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7) {
-        rc = launch_contract_tcgen05(out, t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, out->stream);
+        rc = launch_contract_tcgen05(out, t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, o, out->stream);
     } else {
         const int ps = prof_begin(out, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, n1 + n2 + e_bits), out->stream);
-        rc = launch_contract_fp32(t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, out->stream);
+        rc = launch_contract_fp32(t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, o, out->stream);
         prof_end(out, ps, out->stream);
     }
     if (rc != 0) {
@@ -567,12 +607,5 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         return fail(out, SIM_E_CUDA, "sim_contract: stream ordering failed");
     }
     destroy();
-    // out's layout: side-0 qubits at bits 0 .. n1-1, side-1 qubits above, each in increasing order
-    int b[2] = {0, n1};
-    for (int q = 0; q < s->n; ++q) {
-        const int p = b[s->side[q]]++;
-        out->bit_of[q] = p;
-        out->qubit_at[p] = q;
-    }
     return SIM_OK;
 }

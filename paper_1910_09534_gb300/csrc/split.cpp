@@ -10,6 +10,7 @@
 // and b's wire holds b''.  Both tensors number their pairs in the order of the bridging gates.
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -156,4 +157,78 @@ extern "C" int sim_split_destroy(sim_split_t *s)
 {
     delete s;
     return SIM_OK;
+}
+
+struct sim_front_s {
+    sim_split_s split;
+    sim_t *t[2] = {nullptr, nullptr};
+    sim_plan_t *p[2] = {nullptr, nullptr};
+    int device = 0;
+    int contract_precision = SIM_FP32;
+};
+
+extern "C" int sim_front_destroy(sim_front_t *f)
+{
+    if (!f) return fail(nullptr, SIM_E_INVAL, "sim_front_destroy: NULL front");
+    for (int t = 0; t < 2; ++t) {
+        if (f->p[t]) sim_plan_destroy(f->p[t]);
+        if (f->t[t]) sim_destroy(f->t[t]);
+    }
+    delete f;
+    return SIM_OK;
+}
+
+extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan_opts *o, sim_front_t **f)
+{
+    if (!f) return fail(out, SIM_E_INVAL, "sim_front_create: NULL out pointer");
+    *f = nullptr;
+    if (!out || !s) return fail(out, SIM_E_INVAL, "sim_front_create: NULL argument");
+    sim_plan_opts po{};
+    po.kmax = 4;
+    po.precision = SIM_FP32;
+    if (o) po = *o;
+    sim_front_s *fr = new (std::nothrow) sim_front_s;
+    if (!fr) return fail(out, SIM_E_NOMEM_HOST, "sim_front_create: out of host memory");
+    fr->split = *s;
+    fr->device = out->device;
+    fr->contract_precision =
+        (po.precision == SIM_FP16X3 || po.precision == SIM_FP16X3_TMEM) ? SIM_FP16X3_TMEM : SIM_FP32;
+    for (int t = 0; t < 2; ++t) {
+        const int nw = s->n_side[t] + 2 * s->n_pairs;
+        int rc = sim_plan_create(nw, (int)s->gates[t].size(), s->gates[t].data(), &po, &fr->p[t]);
+        if (rc == SIM_OK) {
+            sim_opts so{};
+            so.store = SIM_STORE_DEVICE;
+            so.device = out->device;
+            so.stream = out->stream;
+            rc = sim_create(nw, 0, &so, &fr->t[t]);
+        }
+        if (rc != SIM_OK) {
+            const std::string msg = thread_error();
+            sim_front_destroy(fr);
+            return fail(out, rc, "sim_front_create: tensor %d: %s", t + 1, msg.c_str());
+        }
+        // the tensor lives in its canonical layout from the start (its state is reset before
+        // every run), so each run applies the same kernels and the contraction permutes nothing
+        for (int p = 0; p < nw; ++p) {
+            fr->t[t]->bit_of[s->wire_at[t][p]] = p;
+            fr->t[t]->qubit_at[p] = s->wire_at[t][p];
+        }
+    }
+    *f = fr;
+    return SIM_OK;
+}
+
+extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
+{
+    if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
+    if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
+    for (int t = 0; t < 2; ++t) {
+        const uint64_t before = f->t[t]->launches;
+        int rc = sim_reset(f->t[t], 0);
+        if (rc == SIM_OK) rc = sim_apply_plan(f->t[t], f->p[t]);
+        out->launches += f->t[t]->launches - before;  // the front's kernels count as out's
+        if (rc != SIM_OK) return fail(out, rc, "sim_front_run: tensor %d: %s", t + 1, f->t[t]->err.c_str());
+    }
+    return sim_contract(out, f->t[0], f->t[1], &f->split, f->contract_precision);
 }

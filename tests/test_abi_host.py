@@ -335,4 +335,7 @@ def test_split_rejects_bad_input(pkg):
         pkg.sim_split_create(2, many, [0, 1])
     L = pkg.lib()
     assert L.sim_contract(None, None, None, None, 0) == pkg.SIM_E_INVAL
+    assert L.sim_front_create(None, None, None, None) == pkg.SIM_E_INVAL
+    assert L.sim_front_run(None, None) == pkg.SIM_E_INVAL
+    assert L.sim_front_destroy(None) == pkg.SIM_E_INVAL
     assert L.sim_split_info(None, None, None, None, None) == pkg.SIM_E_INVAL

@@ -213,3 +213,37 @@ def test_contract_rejects_mismatched_handles(pkg):
         for h in (h1, h2, wrong, out):
             pkg.sim_destroy(h)
         pkg.sim_split_destroy(s)
+
+
+@pytest.mark.parametrize("cprec", ["fp32", "tmem"])
+def test_front_runner_into_permuted_layout(pkg, oracle_mod, cprec):
+    # sim_front_run writes psi in out's current layout (here a random permutation, left as it is),
+    # the rest of the circuit then runs on it; a second run gives the same bits (deterministic)
+    grid = si.Grid(4, 5)
+    circ = si.sycamore_circuit(grid, cycles=9, seed=12)
+    n = grid.n_qubits
+    f = front_length(grid, 6)
+    gates = pkg.gates_array(circ)
+    prec, kmax = (pkg.SIM_FP32, 4) if cprec == "fp32" else (pkg.SIM_FP16X3_TMEM, 5)
+    s = pkg.sim_split_create(n, gates[:f], column_sides(grid, 2))
+    out = pkg.sim_create(n)
+    perm = [int(x) for x in np.random.default_rng(3).permutation(n)]
+    pkg.sim_permute(out, perm)
+    fr = pkg.sim_front_create(out, s, kmax=kmax, precision=prec)
+    plan = pkg.sim_plan_create(n, gates[f:], kmax=kmax, precision=prec)
+    try:
+        runs = []
+        for _ in range(2):
+            pkg.sim_front_run(out, fr)
+            pkg.sim_apply_plan(out, plan)
+            assert [int(b) for b in pkg.sim_info(out)[2]] == perm
+            runs.append(pkg.sim_amplitudes(out))
+    finally:
+        pkg.sim_plan_destroy(plan)
+        pkg.sim_front_destroy(fr)
+        pkg.sim_destroy(out)
+        pkg.sim_split_destroy(s)
+    assert np.array_equal(runs[0], runs[1])
+    e = err2(runs[0], oracle_mod.run_circuit(circ))
+    print(f"front runner into a permuted layout ({cprec}): ||dpsi|| = {e:.2e}")
+    assert e <= TOL
