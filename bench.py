@@ -676,6 +676,17 @@ def kernel_case():
         pkg.sim_permute(h, list(range(n)))
     pkg.sim_reduce(h)
     pkg.sim_reduce(h)
+    # contraction deferral on the 28-qubit workload: its gates up to the sixth one across the
+    # middle column cut (12 + 16 qubits, 4^5 entanglement values), front run twice
+    circ = si.workload_circuit("syc28_4x7_d20", seed=0)
+    side, nf, _ = front_cut(circ, si.WORKLOADS["syc28_4x7_d20"]["grid"], 5)
+    s = pkg.sim_split_create(n, pkg.gates_array(circ)[:nf], side)
+    f = pkg.sim_front_create(h, s, kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    for _ in range(2):
+        pkg.sim_front_run(h, f)
+    pkg.sim_sync(h)
+    pkg.sim_front_destroy(f)
+    pkg.sim_split_destroy(s)
     pkg.sim_destroy(h)
     print("kernel case done", flush=True)
 
