@@ -500,6 +500,12 @@ def run_ours(args):
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e_value = whole_job_rate(float(amps) * circ.n_gates * args.e2e_steps, ws, max(e2e_s, 1e-9))
+    # the host link right after: one 8 GiB readout alone (other tenants of the node share the
+    # host memory and its link; this says how fast it was during the end-to-end leg)
+    t1 = time.perf_counter()
+    pkg.sim_amplitudes_async(h, outs[0])
+    pkg.sim_sync(h)
+    readout_ms = 1e3 * (time.perf_counter() - t1)
     sanity = outs[(args.e2e_steps - 1) % 2][:4].copy()
     for o in outs:
         pkg.sim_host_free(o.ctypes.data)
@@ -613,7 +619,8 @@ def run_ours(args):
                                   "other": ms_max / args.steps - (a_ms + r_ms + c_ms) / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes + matrix_bytes),
                 "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps,
-                "pipelined": "two handles: the readout of step i overlaps the compute of step i+1"},
+                "pipelined": "two handles: the readout of step i overlaps the compute of step i+1",
+                "readout_alone_ms": readout_ms, "readout_alone_gbs": amps * 8 / (readout_ms / 1e3) / 1e9},
         "clocks": clk.summary(),
     }
     if front_info is not None:

