@@ -283,6 +283,24 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p);
  * SIM_E_UNSUPPORTED for host-store handles or a handle on the legacy default stream.
  * sim_graph_create is synchronous (uploads, captures, instantiates); it does not touch the
  * state.  sim_graph_launch is asynchronous on h's stream, like sim_apply_plan. */
+/* Where the qubits should sit for a plan (not in the paper).  The fused-apply kernels' speed on
+ * GB300 depends on which physical bits a block targets: in SIM_FP16X3_TMEM, 5- and 6-qubit blocks
+ * with two or more targets below bit 4 (and 4-qubit blocks with one) leave the tcgen05 kernel for
+ * a slower one, and tcgen05 blocks with no target below bit 8 move their tiles in 1 KiB pieces
+ * instead of 2 KiB; in SIM_FP32 targets below bit 5 cost register exchanges.  sim_plan_layout
+ * searches layouts (pairwise swaps from several seeded starts) for the smallest sum over the
+ * plan's blocks of a per-pass time estimate (measured per kernel path on 2^30 amplitudes; other
+ * precisions: every layout costs the same and the identity is returned), and writes perm[q] = the
+ * physical bit for qubit q (a bijection on 0..n-1, as sim_permute takes) and, if est_ms is not
+ * NULL, the estimate for that layout and for the identity (est_ms[0], est_ms[1]).  Host only. */
+int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms);
+
+/* Relabel the physical bits without moving any amplitude (perm as for sim_permute): the logical
+ * state changes, so this belongs before sim_reset, sim_front_run or sim_contract, which overwrite
+ * every amplitude -- the way to start a plan in the layout sim_plan_layout chose without a
+ * permutation pass.  Device-store handles that are not sliced; SIM_E_INVAL otherwise. */
+int sim_set_layout(sim_t *h, const int *perm);
+
 typedef struct sim_graph_s sim_graph_t;
 int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out);
 int sim_graph_launch(sim_t *h, const sim_graph_t *g);
@@ -396,8 +414,11 @@ int sim_split_destroy(sim_split_t *s);
 /* The contraction (Appendix: the sum over the entanglement indices): psi = sum_pairs T1 T2 into
  * `out`.  t1 / t2: device-resident handles of n_wires[0] / n_wires[1] qubits holding the two
  * tensors (their gate lists applied); out: a device-resident handle of n_qubits qubits, not
- * sliced, distinct from both.  First permutes t1 and t2 into their canonical layouts (on their
- * own streams; the tensors' logical content is unchanged); then, on out's stream after both, one
+ * sliced, distinct from both.  First permutes t1 and t2 (on their own streams; the tensors' logical
+ * content is unchanged) so that each side's qubits sit at bits 0 .. n_side-1 in the order of their
+ * physical bits in out and the pairs above in pair order (the canonical layout when out's layout
+ * is the identity), which keeps psi's stores coalesced in any layout of out; then, on out's
+ * stream after both, one
  * complex GEMM over the 4^n_pairs entanglement values writes every amplitude of psi, in out's
  * current layout (out's layout map is unchanged; its previous amplitudes are overwritten).
  * t1's and t2's streams wait for the GEMM before any later work on them.

@@ -121,6 +121,8 @@ _SIGS = {
     "sim_plan_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "sim_apply_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_plan_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_set_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sim_graph_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "sim_graph_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sim_graph_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -388,6 +390,19 @@ def sim_plan_block(p, i: int):
     m = np.zeros((1 << k.value, 1 << k.value), dtype=np.complex128)
     _check(lib().sim_plan_block(p, i, None, _ptr(t), _ptr(m)))
     return t, m
+
+
+def sim_plan_layout(p, n_qubits: int):
+    """(perm, estimated ms for it, estimated ms for the identity layout) of a plan on n_qubits."""
+    perm = np.zeros(n_qubits, dtype=np.int32)
+    est = np.zeros(2, dtype=np.float64)
+    _check(lib().sim_plan_layout(p, _ptr(perm), _ptr(est)))
+    return [int(x) for x in perm], float(est[0]), float(est[1])
+
+
+def sim_set_layout(h, perm) -> None:
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    _check(lib().sim_set_layout(h, _ptr(pm)), h)
 
 
 def sim_apply_plan(h, p) -> None:

@@ -68,11 +68,11 @@ struct Tc5Geom {
     int tpos[kMaxK];         // target bit positions, ascending
     int run_log2;            // L: a tile is 2^(k+7+log2 R2-L) runs of 2^L contiguous amplitudes
     int nlow;                // targets below bit 4 (they are member bits 0 .. nlow-1)
-    uint64_t off_run[32];    // address offset of run c (c's bits deposited on the free bits >= L)
-    uint32_t midx[32];       // staging index of member m in row 0 (row r: midx[m] | ridx(r))
+    uint64_t off_run[64];    // address offset of run c (c's bits deposited on the free bits >= L)
+    uint32_t midx[64];       // staging index of member m in row 0 (row r: midx[m] | ridx(r))
     uint32_t ridx[8];        // staging-index bit of row bit j (bit 7: sub-tile)
     uint64_t roff[8];        // address offset of row bit j
-    uint64_t moff[32];       // address offset of member m
+    uint64_t moff[64];       // address offset of member m
     const uint32_t *bmat;    // R^T hi then lo, FP16 core-matrix layout, as 32-bit words
     int *err;                // set to 1 if a wait timed out
 };
@@ -209,13 +209,15 @@ struct Tc5Layout {
     static constexpr int B_BYTES = KS * B_SLICE;
     static constexpr int SUB = kRows * D * 8;     // one sub-tile = 2 * A_BYTES
     static constexpr int STAGE = R2 * SUB;
-    static constexpr int S = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;  // stages
+    // stages: K <= 5 within 200 KiB (at most 8); K = 6 (64 KiB tiles, 64 KiB of B hi/lo) fits 2
+    static constexpr int S = K == 6 ? 2 : ((200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8);
     static constexpr int SMEM = S * STAGE + 2 * B_BYTES;
     static constexpr int TMEM_SUB = 2 * N;        // main + corrections of one sub-tile
     static constexpr int TMEM_SET = R2 * TMEM_SUB;
     static constexpr int TMEM_COLS = 2 * TMEM_SET;  // two sets
     static_assert(SUB == 2 * A_BYTES, "A hi/lo fill a sub-tile");
-    static_assert(S >= 3, "stage ring too short");
+    static_assert(S >= (K == 6 ? 2 : 3), "stage ring too short");
+    static_assert(K < 6 || R2 == 1, "6-qubit blocks: one 128-group sub-tile (tensor memory)");
     // results leave through the stage with bulk stores when the ring is deep enough to hold a
     // stage until its store has read it; the 3-stage ring (64 KiB tiles) stores from registers so
     // that a stage is free as soon as its accumulators are read (measured: +20% there, -8% at 6+)
@@ -468,6 +470,28 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
             float inv[R2];
 #pragma unroll
             for (int u = 0; u < R2; ++u) inv[u] = row_inv[st][u][row];
+            if constexpr (K == 6) {
+                // 64 output reals per thread: read, add, unscale and store 16 columns at a time
+                // (registers), releasing the tensor memory and the stage after the last read
+                const uint32_t lane_base = tmem + (i & 1) * L::TMEM_SET + ((uint32_t)(32 * q) << 16) + half * (N / 2);
+#pragma unroll
+                for (int c0 = 0; c0 < N / 2; c0 += 16) {
+                    float a[16], b[16];
+                    tmem_ld16(lane_base + c0, a);
+                    tmem_ld16(lane_base + N + c0, b);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    if (c0 == N / 2 - 16) {
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        mbar_arrive(smem_u32(&tmem_free[i & 1]));
+                        mbar_arrive(smem_u32(&drained[st]));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        __stcs(dst + g.moff[H * half + c0 / 2 + j],
+                               make_float2((a[2 * j] + b[2 * j]) * inv[0], (a[2 * j + 1] + b[2 * j + 1]) * inv[0]));
+                }
+                continue;
+            }
 #pragma unroll
             for (int u = 0; u < R2; ++u) {
                 const uint32_t lane_base =
@@ -641,19 +665,26 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
     g.err = h->d_errflag;
     g.nlow = 0;
     while (g.nlow < K && tpos[g.nlow] < 4) g.nlow++;
-    if (g.nlow > 1) return -2;  // not eligible (see tcgen05_eligible)
-    // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below it);
-    // otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy moves at
-    // least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take 128 groups.
-    const int run = tile_geometry<K>(nbits, tpos, 7, g);
-    if (run < 0) return -1;
-    if (g.nlow > 0) {
-        if constexpr (K == 5) return launch_tc5_kr<K, 1, true>(g, nbits, st);
-        return -2;
+    if (g.nlow > (K >= 5 ? 1 : 0)) return -2;  // not eligible (see tcgen05_eligible)
+    if constexpr (K == 6) {  // 128-group tiles only: two 256-column accumulator sets fill the TMEM
+        if (tile_geometry<K>(nbits, tpos, 7, g) < 0) return -1;
+        if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+        return launch_tc5_kr<K, 1, false>(g, nbits, st);
+    } else {
+        // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below
+        // it); otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy
+        // moves at least 2 KiB.  A target below bit 4 always lengthens the run: those blocks take
+        // 128 groups.
+        const int run = tile_geometry<K>(nbits, tpos, 7, g);
+        if (run < 0) return -1;
+        if (g.nlow > 0) {
+            if constexpr (K == 5) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+            return -2;
+        }
+        if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
+        if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
+        return launch_tc5_kr<K, 2, false>(g, nbits, st);
     }
-    if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
-    if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
-    return launch_tc5_kr<K, 2, false>(g, nbits, st);
 }
 
 template <int K>
@@ -681,21 +712,27 @@ int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2
 // it saves.  Those blocks run on the mma.sync 3xFP16 kernel.
 bool tcgen05_eligible(int nbits, int k, const int *tpos)
 {
-    if ((k != 4 && k != 5) || nbits < k + 7) return false;
+    if (k < 4 || k > 6 || nbits < k + 7) return false;
     int low = 0;
     for (int q = 0; q < k; q++) low += tpos[q] < 4;
-    return low <= (k == 5 ? 1 : 0);
+    return low <= (k >= 5 ? 1 : 0);
 }
 
 size_t tcgen05_staged_bytes(int k)
 {
-    return k == 4 ? 2 * Tc5Layout<4, 1>::B_BYTES : (k == 5 ? 2 * Tc5Layout<5, 1>::B_BYTES : 0);
+    switch (k) {
+    case 4: return 2 * Tc5Layout<4, 1>::B_BYTES;
+    case 5: return 2 * Tc5Layout<5, 1>::B_BYTES;
+    case 6: return 2 * Tc5Layout<6, 1>::B_BYTES;
+    default: return 0;
+    }
 }
 
 void tcgen05_build_staged(int k, const float2 *mat, void *h_out)
 {
     if (k == 4) build_b<4>(mat, static_cast<uint16_t *>(h_out));
     if (k == 5) build_b<5>(mat, static_cast<uint16_t *>(h_out));
+    if (k == 6) build_b<6>(mat, static_cast<uint16_t *>(h_out));
 }
 
 int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const void *d_staged,
@@ -705,6 +742,7 @@ int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tp
     switch (k) {
     case 4: return launch_tc5_staged<4>(h, psi, nbits, tpos, d_b, st);
     case 5: return launch_tc5_staged<5>(h, psi, nbits, tpos, d_b, st);
+    case 6: return launch_tc5_staged<6>(h, psi, nbits, tpos, d_b, st);
     default: return -1;
     }
 }
@@ -721,6 +759,7 @@ int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpo
     switch (k) {
     case 4: return launch_tc5_k<4>(h, psi, nbits, tpos, mat, st, hf, df, ev);
     case 5: return launch_tc5_k<5>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 6: return launch_tc5_k<6>(h, psi, nbits, tpos, mat, st, hf, df, ev);
     default: return -1;
     }
 }

@@ -537,6 +537,30 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
 
 }  // namespace
 
+namespace sycsim {
+
+// Where each wire of tensor t must sit for a contraction into out: the side's qubits at bits
+// 0 .. n_side-1 in the order of their physical bits in out (so a warp's 32 consecutive x, or the
+// y of one thread, land on the lowest physical bits the side holds), the entanglement pairs above
+// in pair order.  bit_of_wire[w] = the physical bit of wire w; side_qubit[i] = the qubit at bit i.
+void contract_layout(const sim_split_s *s, const sim_t *out, int t, int *bit_of_wire, int *side_qubit)
+{
+    const int ns = s->n_side[t];
+    int order[kMaxQubits], q_of[kMaxQubits];  // canonical position p < ns -> qubit
+    int c = 0;
+    for (int q = 0; q < s->n; ++q)
+        if (s->side[q] == t) q_of[c++] = q;
+    for (int p = 0; p < ns; ++p) order[p] = p;
+    std::sort(order, order + ns, [&](int a, int b) { return out->bit_of[q_of[a]] < out->bit_of[q_of[b]]; });
+    for (int i = 0; i < ns; ++i) {
+        bit_of_wire[s->wire_at[t][order[i]]] = i;
+        if (side_qubit) side_qubit[i] = q_of[order[i]];
+    }
+    for (int p = ns; p < (int)s->wire_at[t].size(); ++p) bit_of_wire[s->wire_at[t][p]] = p;
+}
+
+}  // namespace sycsim
+
 extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision)
 {
     if (!out || !t1 || !t2 || !s) return fail(out, SIM_E_INVAL, "sim_contract: NULL argument");
@@ -555,16 +579,15 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
                     out->n, t1->n, t2->n, s->n, n1 + e_bits, n2 + e_bits);
     SIM_CUDA_TRY(out, cudaSetDevice(out->device));
 
-    // canonical layouts: wire wire_at[p] to physical bit p
+    // each tensor into the layout that matches out's (contract_layout)
     sim_t *tens[2] = {t1, t2};
+    int side_qubit[2][kMaxQubits];
     for (int t = 0; t < 2; ++t) {
         sim_t *h = tens[t];
         int perm[kMaxQubits];
+        contract_layout(s, out, t, perm, side_qubit[t]);
         bool same = true;
-        for (int p = 0; p < h->n; ++p) {
-            perm[s->wire_at[t][p]] = p;
-            same = same && h->bit_of[s->wire_at[t][p]] == p;
-        }
+        for (int w = 0; w < h->n; ++w) same = same && h->bit_of[w] == perm[w];
         if (!same) {
             const int rc = sim_permute(h, perm);
             if (rc != SIM_OK) return fail(out, rc, "sim_contract: permuting tensor %d: %s", t + 1, h->err.c_str());
@@ -582,13 +605,10 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         destroy();
         return fail(out, SIM_E_CUDA, "sim_contract: stream ordering failed");
     }
-    // psi goes straight into out's current layout
+    // psi goes straight into out's current layout: bit i of x is side-0 qubit side_qubit[0][i]
     CtOut o{};
-    int b[2] = {0, 0};
-    for (int q = 0; q < s->n; ++q) {
-        const int t = s->side[q];
-        (t == 0 ? o.xbit : o.ybit)[b[t]++] = 1ull << out->bit_of[q];
-    }
+    for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out->bit_of[side_qubit[0][i]];
+    for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out->bit_of[side_qubit[1][j]];
     int rc;
     if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7) {
         rc = launch_contract_tcgen05(out, t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, o, out->stream);

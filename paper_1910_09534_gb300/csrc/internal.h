@@ -232,6 +232,11 @@ int host_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dty
 int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int physical);
 int host_reduce(sim_t *h, double *s1, double *s2);
 
+// ---- contract.cu ----
+// Physical bit of each wire of tensor t for a contraction into out (and the side qubit at each of
+// the side's bits, if side_qubit is not NULL).
+void contract_layout(const sim_split_s *s, const sim_t *out, int t, int *bit_of_wire, int *side_qubit);
+
 // ---- gates.cpp ----
 // Matrix of a gate record (2x2 or 4x4 complex128, row-major); returns the dimension or 0.
 int gate_matrix(const sim_gate &g, double *out /* 32 doubles */);

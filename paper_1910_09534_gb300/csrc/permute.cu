@@ -299,3 +299,22 @@ extern "C" int sim_permute(sim_t *h, const int *perm)
     }
     return SIM_OK;
 }
+
+extern "C" int sim_set_layout(sim_t *h, const int *perm)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_set_layout: NULL handle");
+    if (!perm) return fail(h, SIM_E_INVAL, "sim_set_layout: NULL perm");
+    if (h->store != SIM_STORE_DEVICE || h->s != 0)
+        return fail(h, SIM_E_INVAL, "sim_set_layout: device-store handles that are not sliced only");
+    bool used[kMaxQubits] = {};
+    for (int q = 0; q < h->n; q++) {
+        if (perm[q] < 0 || perm[q] >= h->n || used[perm[q]])
+            return fail(h, SIM_E_INVAL, "sim_set_layout: perm is not a bijection on 0..%d", h->n - 1);
+        used[perm[q]] = true;
+    }
+    for (int q = 0; q < h->n; q++) {
+        h->bit_of[q] = perm[q];
+        h->qubit_at[perm[q]] = q;
+    }
+    return SIM_OK;
+}

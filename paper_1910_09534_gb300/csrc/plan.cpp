@@ -373,6 +373,117 @@ int sim_plan_block(const sim_plan_t *p, int i, int *k, int *targets, double *mat
     return SIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Estimated time of one fused pass over 2^30 amplitudes (ms) on the kernel a block of k targets at
+// physical bits tpos takes, from CUDA-event timings of each kernel path on GB300; the layout search
+// only compares sums of these.
+double pass_ms(int k, const int *tpos, int precision)
+{
+    int low4 = 0, low5 = 0;
+    bool le7 = false;
+    for (int i = 0; i < k; i++) {
+        low4 += tpos[i] < 4;
+        low5 += tpos[i] < 5;
+        le7 = le7 || tpos[i] <= 7;
+    }
+    if (precision == SIM_FP16X3_TMEM) {
+        // tcgen05 with <= 1 target below bit 4 (k = 5, 6) or none (k = 4), else mma.sync 3xFP16;
+        // tcgen05 tiles move 2 KiB runs once a target sits at bit 7 or below, else 1 KiB (k = 6)
+        // or twice the groups (k = 4, 5)
+        if (k == 6) return low4 >= 2 ? 5.10 : (le7 ? 2.85 : 3.41);
+        if (k == 5) return low4 >= 2 ? 2.70 : (le7 ? 2.55 : 2.63);
+        if (k == 4) return low4 >= 1 ? 2.68 : 2.55;
+        return 2.45;
+    }
+    if (precision == SIM_FP32) {
+        // register kernel: each target below bit 5 costs warp exchanges (k = 4: 2.79 ms with none,
+        // 3.3 mixed, 4.3 all low); k >= 5 is FP32-ALU bound whatever the targets
+        if (k >= 5) return 6.9;
+        if (k == 4) return low5 == 0 ? 2.79 : (low5 >= 4 ? 4.29 : 3.30);
+        return low5 == 0 ? 2.45 : 2.90;
+    }
+    return 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
+{
+    if (!p || !perm) return fail(nullptr, SIM_E_INVAL, "sim_plan_layout: NULL argument");
+    const int n = p->n, nb = (int)p->blocks.size();
+    std::vector<std::vector<int>> of_qubit(n);  // blocks holding each qubit
+    for (int b = 0; b < nb; b++)
+        for (int q : p->blocks[b].qubits) of_qubit[q].push_back(b);
+    std::vector<int> pos(n);  // pos[q] = physical bit of qubit q
+    auto block_cost = [&](int b) {
+        int tpos[kMaxK];
+        const auto &qs = p->blocks[b].qubits;
+        for (size_t i = 0; i < qs.size(); i++) tpos[i] = pos[qs[i]];
+        return pass_ms((int)qs.size(), tpos, p->precision);
+    };
+    auto total = [&]() {
+        double t = 0;
+        for (int b = 0; b < nb; b++) t += block_cost(b);
+        return t;
+    };
+    for (int q = 0; q < n; q++) pos[q] = q;
+    const double ident = total();
+    std::vector<int> best = pos;
+    double best_cost = ident;
+    const bool modelled = p->precision == SIM_FP16X3_TMEM || p->precision == SIM_FP32;
+    uint64_t rs = 0x9E3779B97F4A7C15ull;  // SplitMix64 state for the seeded starts
+    auto next = [&]() {
+        uint64_t z = (rs += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<char> mark(nb, 0);
+    for (int start = 0; modelled && start < 16; start++) {
+        for (int q = 0; q < n; q++) pos[q] = q;
+        for (int q = n - 1; start > 0 && q > 0; q--) std::swap(pos[q], pos[next() % (uint64_t)(q + 1)]);
+        double cost = total();
+        for (int sweep = 0; sweep < 64; sweep++) {
+            bool improved = false;
+            for (int a = 0; a < n; a++)
+                for (int c = a + 1; c < n; c++) {
+                    std::vector<int> touched;
+                    for (int b : of_qubit[a])
+                        if (!mark[b]) mark[b] = 1, touched.push_back(b);
+                    for (int b : of_qubit[c])
+                        if (!mark[b]) mark[b] = 1, touched.push_back(b);
+                    double before = 0, after = 0;
+                    for (int b : touched) before += block_cost(b);
+                    std::swap(pos[a], pos[c]);
+                    for (int b : touched) after += block_cost(b);
+                    for (int b : touched) mark[b] = 0;
+                    if (after < before - 1e-9) {
+                        cost += after - before;
+                        improved = true;
+                    } else {
+                        std::swap(pos[a], pos[c]);
+                    }
+                }
+            if (!improved) break;
+        }
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = pos;
+        }
+    }
+    for (int q = 0; q < n; q++) perm[q] = best[q];
+    if (est_ms) {
+        est_ms[0] = best_cost;
+        est_ms[1] = ident;
+    }
+    return SIM_OK;
+}
+
 int sim_apply_plan(sim_t *h, const sim_plan_t *p)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_plan: NULL handle");

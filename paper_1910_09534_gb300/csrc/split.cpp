@@ -208,12 +208,6 @@ extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan
             sim_front_destroy(fr);
             return fail(out, rc, "sim_front_create: tensor %d: %s", t + 1, msg.c_str());
         }
-        // the tensor lives in its canonical layout from the start (its state is reset before
-        // every run), so each run applies the same kernels and the contraction permutes nothing
-        for (int p = 0; p < nw; ++p) {
-            fr->t[t]->bit_of[s->wire_at[t][p]] = p;
-            fr->t[t]->qubit_at[p] = s->wire_at[t][p];
-        }
     }
     *f = fr;
     return SIM_OK;
@@ -224,6 +218,14 @@ extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
     if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
     if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
     for (int t = 0; t < 2; ++t) {
+        // relabel the tensor (free: its state is reset next) into the layout the contraction into
+        // out wants, so that no run permutes
+        int lay[kMaxQubits];
+        contract_layout(&f->split, out, t, lay, nullptr);
+        for (int w = 0; w < f->t[t]->n; ++w) {
+            f->t[t]->bit_of[w] = lay[w];
+            f->t[t]->qubit_at[lay[w]] = w;
+        }
         const uint64_t before = f->t[t]->launches;
         int rc = sim_reset(f->t[t], 0);
         if (rc == SIM_OK) rc = sim_apply_plan(f->t[t], f->p[t]);

@@ -339,3 +339,24 @@ def test_split_rejects_bad_input(pkg):
     assert L.sim_front_run(None, None) == pkg.SIM_E_INVAL
     assert L.sim_front_destroy(None) == pkg.SIM_E_INVAL
     assert L.sim_split_info(None, None, None, None, None) == pkg.SIM_E_INVAL
+
+
+def test_plan_layout_is_a_bijection_no_worse_than_identity(pkg):
+    circ = si.workload_circuit("syc30_5x6_d20", seed=0)
+    g = pkg.gates_array(circ)
+    for kmax, prec in ((6, pkg.SIM_FP16X3_TMEM), (5, pkg.SIM_FP16X3_TMEM), (4, pkg.SIM_FP32), (5, pkg.SIM_TF32X3)):
+        plan = pkg.sim_plan_create(30, g, kmax=kmax, precision=prec)
+        try:
+            perm, est, ident = pkg.sim_plan_layout(plan, 30)
+            assert sorted(perm) == list(range(30))
+            assert est <= ident + 1e-9
+            if prec == pkg.SIM_TF32X3:  # no cost model: identity
+                assert perm == list(range(30)) and est == ident
+            if kmax == 6:
+                assert est < 0.9 * ident  # the 6-qubit blocks gain from leaving bits 0-3
+            assert pkg.sim_plan_layout(plan, 30)[0] == perm  # deterministic
+        finally:
+            pkg.sim_plan_destroy(plan)
+    L = pkg.lib()
+    assert L.sim_plan_layout(None, None, None) == pkg.SIM_E_INVAL
+    assert L.sim_set_layout(None, None) == pkg.SIM_E_INVAL

@@ -52,7 +52,8 @@ def test_tensor_core_apply_matches_oracle(pkg, oracle_mod, name, n, targets):
 
 
 @pytest.mark.parametrize("name,kmax,tol", [("tf32x3", 5, 1e-5), ("tf32x3", 6, 1e-5), ("fp16x3", 5, 1e-5),
-                                          ("fp16x3", 6, 1e-5), ("fp16x3_tmem", 5, 1e-5), ("tf32", 5, 3e-2)])
+                                          ("fp16x3", 6, 1e-5), ("fp16x3_tmem", 5, 1e-5), ("fp16x3_tmem", 6, 1e-5),
+                                          ("tf32", 5, 3e-2)])
 def test_tensor_core_circuit_matches_oracle(pkg, oracle_mod, name, kmax, tol):
     circ = si.sycamore_circuit(si.Grid(4, 5), cycles=14, seed=8)
     plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax, precision=mode(pkg, name))
@@ -103,9 +104,17 @@ def test_fp16x3_tiny_and_zero_amplitudes(pkg, oracle_mod):
     # kernel; one tile at 11 qubits
     (19, [1, 6, 7, 12]),
     (13, [0, 12, 3, 7, 9]), (23, [0, 1, 2, 3, 4]), (22, [0, 2, 4, 6]), (11, [0, 1, 2, 3]),
-    (21, [1, 2, 3, 12, 13])])
+    (21, [1, 2, 3, 12, 13]),
+    # k = 6 (128-group tiles, 2-stage ring, results drained 16 columns at a time): one tile at
+    # 13 qubits; all targets above bit 7 (1 KiB runs); mixed; targets from bit 4 up; many tiles
+    # per CTA at 24-25 qubits
+    (13, [7, 8, 9, 10, 11, 12]), (24, [23, 16, 12, 10, 9, 8]), (22, [21, 5, 13, 8, 17, 10]),
+    (20, [4, 5, 6, 7, 8, 9]), (25, [4, 9, 14, 19, 22, 24]),
+    # k = 6 with one target below bit 4 (per-row member XOR), and with two (mma.sync 3xFP16)
+    (22, [2, 8, 11, 15, 19, 21]), (20, [3, 4, 5, 7, 8, 9]), (25, [0, 9, 13, 17, 21, 24]),
+    (19, [2, 3, 9, 11, 14, 18])])
 def test_tcgen05_tiles_match_oracle(pkg, oracle_mod, n, targets):
-    # the tcgen05 path takes k = 4 or 5 and >= 2^(k+7) amplitudes (one 128-group tile)
+    # the tcgen05 path takes k = 4, 5 or 6 and >= 2^(k+7) amplitudes (one 128-group tile)
     k = len(targets)
     u = si.random_unitary(k, seed=n + 3 * k)
     psi = si.random_state(n, seed=2 * n)
@@ -142,3 +151,30 @@ def test_autotune_picks_a_valid_plan(pkg, oracle_mod, accuracy):
     finally:
         pkg.sim_destroy(h)
     assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= 1e-5
+
+
+@pytest.mark.parametrize("name,kmax", [("fp16x3_tmem", 6), ("fp16x3_tmem", 5), ("fp32", 4)])
+def test_chosen_layout_runs_the_same_circuit(pkg, oracle_mod, name, kmax):
+    # sim_plan_layout picks where the qubits sit; sim_set_layout relabels without moving data, so
+    # it goes before the reset; the plan then runs in that layout and reads out in logical order
+    circ = si.sycamore_circuit(si.Grid(4, 5), cycles=14, seed=8)
+    n = circ.n_qubits
+    plan = pkg.sim_plan_create(n, pkg.gates_array(circ), kmax=kmax, precision=mode(pkg, name))
+    perm, est, est_identity = pkg.sim_plan_layout(plan, n)
+    assert sorted(perm) == list(range(n)) and est <= est_identity
+    h = pkg.sim_create(n)
+    try:
+        pkg.sim_set_layout(h, perm)
+        pkg.sim_reset(h)
+        pkg.sim_apply_plan(h, plan)
+        assert [int(b) for b in pkg.sim_info(h)[2]] == perm
+        got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+        pkg.sim_permute(h, list(range(n)))  # back to the identity: the same state, bit for bit
+        again = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_destroy(h)
+        pkg.sim_plan_destroy(plan)
+    assert np.array_equal(got, again)
+    err = np.linalg.norm(got - oracle_mod.run_circuit(circ))
+    print(f"{name} kmax {kmax}, chosen layout (estimate {est:.1f} vs {est_identity:.1f}): err {err:.2e}")
+    assert err <= 1e-5
