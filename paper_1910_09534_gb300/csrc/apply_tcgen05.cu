@@ -240,12 +240,14 @@ __device__ __forceinline__ uint32_t cm_off(int row, int k) { return (row >> 3) *
 //   converters: wait loaded[s], read the rows, combine the halves' maxima (barrier), write A and
 //     the row scales in place, arrive full[s];
 //   MMA thread: wait full[s] and tmem_free of tile i - 2, multiply, commit to mma_done[s];
-//   drainers: wait mma_done[s] and full[s], read the row scales and TMEM, arrive tmem_free; then
-//     either write the results into stage s, barrier, warp 10 stores the runs and, once the store
-//     of tile i - 1 has read its stage, arrives drained for it; or arrive drained[s] at once and
-//     store the results from registers.
-// A stage is reloaded only after its drain, and a TMEM set reused only after its read, so no
-// barrier can run a phase ahead of a waiter that still has to see the previous phase.
+//   drainers: wait mma_done[s] and full[s], take the row scales and the tile base into registers;
+//     storing from registers, arrive drained[s] right then (the MMAs have read the stage), read
+//     TMEM, arrive tmem_free and store; with bulk stores, read TMEM, arrive tmem_free, write the
+//     results into stage s, barrier, and warp 10 stores the runs and, once the store of tile
+//     i - 1 has read its stage, arrives drained for it.
+// A stage is reloaded only after every drainer has passed its waits for it and taken what it
+// needs, and a TMEM set reused only after its read, so no barrier can run a phase ahead of a
+// waiter that still has to see the previous phase.
 template <int K, int R2, bool LOWT>
 __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 {
@@ -470,6 +472,10 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
             float inv[R2];
 #pragma unroll
             for (int u = 0; u < R2; ++u) inv[u] = row_inv[st][u][row];
+            // storing from registers, the stage is dead once the MMAs have read it (mma_done): with
+            // its row scales and base in registers, release it now so the next tile's copies start
+            // while this one is drained
+            if constexpr (!BULK) mbar_arrive(smem_u32(&drained[st]));
             if constexpr (K == 6) {
                 // 64 output reals per thread: read, add, unscale and store 16 columns at a time
                 // (registers), releasing the tensor memory and the stage after the last read
@@ -483,7 +489,6 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                     if (c0 == N / 2 - 16) {
                         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                         mbar_arrive(smem_u32(&tmem_free[i & 1]));
-                        mbar_arrive(smem_u32(&drained[st]));
                     }
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
@@ -503,10 +508,9 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                     tmem_ld16(lane_base + N + c0, *reinterpret_cast<float(*)[16]>(b + c0));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                if (u == R2 - 1) {  // TMEM set read: release it (and, storing from registers, the stage)
+                if (u == R2 - 1) {  // TMEM set read: release it
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                     mbar_arrive(smem_u32(&tmem_free[i & 1]));
-                    if constexpr (!BULK) mbar_arrive(smem_u32(&drained[st]));
                 }
                 float2 o[H];
 #pragma unroll
