@@ -707,6 +707,12 @@ def kernel_case():
         u = si.random_unitary(len(t), 2)
         for _ in range(2):
             pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3_TMEM)
+    # 6-qubit blocks on tcgen05: a target at bit 7 (2 KiB copies), all above bit 7 (1 KiB), one
+    # below bit 4
+    for t in ([7, 12, 14, 18, 22, 26], [12, 13, 14, 15, 16, 17], [3, 9, 14, 20, 25, 27]):
+        u = si.random_unitary(len(t), 3)
+        for _ in range(2):
+            pkg.sim_apply_fused(h, t, u, precision=pkg.SIM_FP16X3_TMEM)
     for pairs in (((25, 10), (26, 11), (27, 12)), ((0, 25), (1, 26), (2, 27))):  # high-high, low<->top
         perm = list(range(n))
         for a, b in pairs:
