@@ -3,7 +3,9 @@
 * 30 qubits, 20 cycles (5x6 grid; 8 GiB complex64 state): every amplitude against the oracle
   (complex128, gate by gate, all host cores), for the FP32 plan (k <= 4) and the tensor-core
   plans (k <= 5, 3xFP16 on mma.sync and on tcgen05), and the contraction-deferral pipeline (the
-  first 6 cycles as two tensors contracted into the state, FP32 and tcgen05), every amplitude.
+  first 6 cycles as two tensors contracted into the state, FP32 and tcgen05), and the bench's
+  configuration (that front, blocks of <= 6 qubits on tcgen05 in the chosen layout), every
+  amplitude.
   Bound ||psi - psi_oracle||_2 <= 1e-5.
 * 33 qubits (6x6 minus three corners; 64 GiB) held as 8 slices over the 3 top bits, run as
   alternating phases with in-place bit permutations between them (Sect. 4 in device memory):
@@ -104,6 +106,20 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
             pkg.sim_apply_plan(h, plan)
             pkg.sim_plan_destroy(plan)
             results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
+        # the bench's configuration: the same front through the front runner, the rest as blocks of
+        # <= 6 qubits on tcgen05, the state written in the layout sim_plan_layout chose for them
+        s = pkg.sim_split_create(n, gates[:front], side)
+        fr = pkg.sim_front_create(h, s, kmax=6, precision=pkg.SIM_FP16X3_TMEM)
+        plan = pkg.sim_plan_create(n, gates[front:], kmax=6, precision=pkg.SIM_FP16X3_TMEM)
+        perm, _, _ = pkg.sim_plan_layout(plan, n)
+        pkg.sim_set_layout(h, perm)
+        pkg.sim_front_run(h, fr)
+        pkg.sim_apply_plan(h, plan)
+        assert [int(b) for b in pkg.sim_info(h)[2]] == perm
+        results["bench_split6_k6_layout"] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
+        pkg.sim_plan_destroy(plan)
+        pkg.sim_front_destroy(fr)
+        pkg.sim_split_destroy(s)
     finally:
         pkg.sim_destroy(h)
     import os
