@@ -288,7 +288,7 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p);
  * with two or more targets below bit 4 (and 4-qubit blocks with one) leave the tcgen05 kernel for
  * a slower one, and tcgen05 blocks with no target below bit 8 move their tiles in 1 KiB pieces
  * instead of 2 KiB; in SIM_FP32 targets below bit 5 cost register exchanges.  sim_plan_layout
- * searches layouts (pairwise swaps from several seeded starts) for the smallest sum over the
+ * searches layouts (pairwise swaps from 4 seeded starts) for the smallest sum over the
  * plan's blocks of a per-pass time estimate (measured per kernel path on 2^30 amplitudes; other
  * precisions: every layout costs the same and the identity is returned), and writes perm[q] = the
  * physical bit for qubit q (a bijection on 0..n-1, as sim_permute takes) and, if est_ms is not
@@ -472,7 +472,9 @@ typedef struct srv_opts {
     int slots;           /* concurrent circuits above small_n (0 = 6, max 32) */
     int small_n;         /* circuits with n <= small_n are packed (0 = 20, max 24) */
     int max_pack;        /* most circuits per packed launch (0 = 1024) */
-    int kmax;            /* aggregation width (0 = 5, or 4 for n > 24 in SIM_FP32) */
+    int kmax;            /* aggregation width (0 = 6 in SIM_FP16X3_TMEM, else 5, or 4 for n > 24
+                          * in SIM_FP32); circuits above small_n run in the qubit layout
+                          * sim_plan_layout picks and are permuted back before a readout */
     int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_FP16X3_TMEM */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
     int reserved[8];

@@ -170,7 +170,8 @@ struct Req {
     bool packed = false;
     void *out_amps = nullptr;
     std::vector<Prepared> blocks;
-    uint64_t bytes = 0;  // admission footprint
+    std::vector<int> back;  // unpacked: the permutation from the chosen layout back to the identity
+    uint64_t bytes = 0;     // admission footprint
     Clock::time_point t_submit, t_done;
     int status = 1;  // 1 pending, 0 ok, < 0 error
     double norm = 0.0, s2 = 0.0;
@@ -243,11 +244,15 @@ int srv_fail(srv_t *s, int code, const char *fmt, ...)
 }
 
 // kmax by size: launch-bound small and mid-size states gain from fewer, wider blocks;
-// HBM-bound large states from the width whose pass stays HBM-bound on CUDA cores (4) or, with
-// a tensor-core arithmetic, on the tensor cores (5, measured fastest on 30 qubits).
+// HBM-bound large states from the width whose pass stays HBM-bound on CUDA cores (4) or on the
+// tensor cores: 6 with tcgen05 (its 6-qubit pass costs 1.05-1.15 times a 5-qubit one and saves a
+// quarter of the passes on 30-qubit circuits, once the layout keeps low targets out of them), 5
+// with the mma.sync arithmetic.
 int auto_kmax(int n, bool packed, int precision)
 {
-    if (packed || precision != SIM_FP32) return 5;
+    if (packed) return 5;
+    if (precision == SIM_FP16X3_TMEM) return 6;
+    if (precision != SIM_FP32) return 5;
     return n <= 24 ? 5 : 4;
 }
 
@@ -304,6 +309,8 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
     if (launch_reduce(h, r->d_state, amps, h->d_partials, h->d_result, st) != 0) return SIM_E_CUDA;
     if (cudaMemcpyAsync(r->h_res, h->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SIM_E_CUDA;
+    if (r->out_amps && !r->back.empty() && launch_permute(h, r->d_state, r->n, r->back.data(), st) != 0)
+        return SIM_E_CUDA;  // amplitudes leave in logical order
     if (r->out_amps &&
         cudaMemcpyAsync(r->out_amps, r->d_state, sizeof(float2) * amps, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SIM_E_CUDA;
@@ -616,15 +623,26 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
         s->rejected++;
         return srv_fail(s, rc, "srv_submit: %s", sim_last_error(nullptr));
     }
-    int ident[kMaxQubits];
-    for (int q = 0; q < kMaxQubits; q++) ident[q] = q;
+    // where the qubits sit: the identity for packed circuits (one CTA each, no HBM passes); for
+    // the others the layout sim_plan_layout picks, the state permuted back before a readout
+    int phys[kMaxQubits];
+    for (int q = 0; q < kMaxQubits; q++) phys[q] = q;
+    if (!r->packed) {
+        sim_plan_layout(plan, phys, nullptr);
+        bool ident = true;
+        for (int q = 0; q < n_qubits; q++) ident = ident && phys[q] == q;
+        if (!ident && out_amps) {
+            r->back.assign(n_qubits, 0);
+            for (int q = 0; q < n_qubits; q++) r->back[phys[q]] = q;
+        }
+    }
     r->blocks.resize(plan->blocks.size());
     for (size_t i = 0; i < plan->blocks.size(); i++) {
         const PlanBlock &b = plan->blocks[i];
         Prepared &pb = r->blocks[i];
         pb.k = (int)b.qubits.size();
         pb.mat.resize((size_t)1 << (2 * pb.k));
-        rc = prepare_block_map(s->slots[0], pb.k, b.qubits.data(), b.mat.data(), ident, n_qubits, pb.tpos,
+        rc = prepare_block_map(s->slots[0], pb.k, b.qubits.data(), b.mat.data(), phys, n_qubits, pb.tpos,
                                pb.mat.data(), n_qubits);
         if (rc != SIM_OK) break;
     }

@@ -76,6 +76,22 @@ def test_tensor_core_modes_on_concurrent_streams(pkg, oracle_mod):
             assert np.linalg.norm(a.astype(np.complex128) - oracle_mod.run_circuit(c)) <= TOL_FP32, (prec, c.name)
 
 
+def test_default_tcgen05_mode_blocks_of_six_in_a_chosen_layout(pkg, oracle_mod):
+    # circuits above small_n in SIM_FP16X3_TMEM with the automatic width (6) run in the layout
+    # sim_plan_layout picks and are permuted back before the readout: logical-order amplitudes,
+    # the same alone and in a mix
+    circuits = [si.sycamore_circuit(si.near_square_grid(n), d, seed=500 + i)
+                for i, (n, d) in enumerate([(21, 10), (22, 8), (23, 12), (21, 14)])]
+    mix, res, stats = serve(pkg, circuits, True, slots=3, precision=pkg.SIM_FP16X3_TMEM)
+    alone, _, _ = serve(pkg, circuits, False, slots=3, precision=pkg.SIM_FP16X3_TMEM)
+    assert stats["completed"] == len(circuits)
+    for c, a, b, (norm, s2, lat) in zip(circuits, mix, alone, res):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
+        err = np.linalg.norm(a.astype(np.complex128) - oracle_mod.run_circuit(c))
+        print(f"served {c.n_qubits} qubits, {len(c.gates)} gates (tcgen05, k <= 6, chosen layout): err {err:.2e}")
+        assert err <= TOL_FP32 and abs(norm - 1.0) < 1e-5
+
+
 def test_admission_respects_hbm_budget(pkg, oracle_mod):
     # 20-qubit states are 8 MiB; a 20 MiB budget admits two at a time
     circuits = [si.sycamore_circuit(si.near_square_grid(20), 6, seed=s) for s in range(5)]
