@@ -374,7 +374,11 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * phases' sets.  On a device-resident handle created with slice_bits > 0, each
  * phase first permutes its sliced set into the top slice_bits physical bits
  * (sim_permute), so the gates of the phase act on local bits only -- the
- * in-memory analogue of Sect. 4's reorganisation between phases.  Asynchronous. */
+ * in-memory analogue of Sect. 4's reorganisation between phases.  The same pass
+ * also exchanges pairs of the other bits where the per-pass estimates of
+ * sim_plan_layout say the phase's blocks run faster (disjoint exchanges, so still
+ * one pass; without a sliced-set move only if they save more than a pass).
+ * Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
 /* ---- contraction deferral: two subcircuits joined by entanglement indices -----
