@@ -160,6 +160,7 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
 
 
 TCGEN05_TRAFFIC_GB = 4 * (2.147897 + 2.088273)  # k_apply_tcgen05<5, 2, 0>, ncu at 2^28 amplitudes
+TCGEN05_K6_TRAFFIC_GB = 4 * (2.147802 + 2.085992)  # k_apply_tcgen05<6, 1, 0>, ncu at 2^28 amplitudes
 
 
 def measured_peaks(key: str = "hbm_gbs"):
@@ -639,11 +640,13 @@ def run_ours(args):
         "check": {"norm": norm, "porter_thomas_2n_sum_p2": s2, "xeb": xeb},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
-                     # DRAM read + write of the dominant kernel, per launch on 2^30 amplitudes (GB),
-                     # from an ncu capture of that kernel on 2^28 amplitudes, x 4, against 17.18 GB
-                     # algorithmic; null for configurations without that capture
-                     "traffic": (TCGEN05_TRAFFIC_GB if args.precision == "fp16x3_tmem" and n == 30 else None),
-                     "traffic_kernel": "k_apply_tcgen05<5, 2, 0>" if args.precision == "fp16x3_tmem" else None,
+                     # DRAM read + write of the dominant kernel family, per launch on 2^30 amplitudes
+                     # (GB), from an ncu capture of that kernel on 2^28 amplitudes, x 4, against
+                     # 17.18 GB algorithmic; null for configurations without that capture
+                     "traffic": ((TCGEN05_K6_TRAFFIC_GB if args.kmax == 6 else TCGEN05_TRAFFIC_GB)
+                                 if args.precision == "fp16x3_tmem" and n == 30 else None),
+                     "traffic_kernel": (("k_apply_tcgen05<6, 1, 0>" if args.kmax == 6 else "k_apply_tcgen05<5, 2, 0>")
+                                        if args.precision == "fp16x3_tmem" else None),
                      "kernel": "fused apply, all launches (" + {
                          "fp16x3_tmem": "k_apply_tcgen05 / k_apply_mma_f16x3 / k_apply_reg / k_apply_direct",
                          "fp32": "k_apply_reg / k_apply_direct / k_apply_tiled"}.get(
