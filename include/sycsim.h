@@ -54,9 +54,9 @@ extern "C" {
 #define SIM_TF32X3 2 /* tensor cores, 3xTF32 split (hi*hi + hi*lo + lo*hi), ~FP32 accuracy */
 #define SIM_FP16X3 3 /* tensor cores, 3xFP16 split with a per-tile power-of-two scale, ~FP32 accuracy */
 #define SIM_FP16X3_TMEM 4 /* 3xFP16 on tcgen05.mma with tensor-memory accumulators, operands moved
-                             by bulk copies (k = 5 with at most one target below bit 4, k = 4
-                             with none; at least 2^(k+7) amplitudes); other blocks of k = 4..6
-                             as SIM_FP16X3 on mma.sync, narrower ones on CUDA cores */
+                             by bulk copies (k = 5 and 6 with at most one target below bit 4,
+                             k = 4 with none; at least 2^(k+7) amplitudes); other blocks of
+                             k = 4..6 as SIM_FP16X3 on mma.sync, narrower ones on CUDA cores */
 /* The mma.sync tensor-core modes apply to blocks with k >= 5 (measured: for k <= 4 the CUDA-core
  * FP32 kernel is faster); narrower blocks run on CUDA cores in FP32. */
 

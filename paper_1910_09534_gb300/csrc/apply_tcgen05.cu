@@ -1,5 +1,5 @@
 // apply_tcgen05.cu -- aggregated k-qubit gate apply on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in tensor memory), 3xFP16 split precision, k = 4 and 5.
+// (tcgen05.mma, accumulators in tensor memory), 3xFP16 split precision, k = 4, 5 and 6.
 //
 // Same real-embedded GEMM as apply_tc.cu (W^T = V^T . R^T with R = [[Re M, -Im M],
 // [Im M, Re M]]), as tcgen05.mma steps of M = 128 (groups) x N = 2^(k+1) (output reals) x
@@ -9,7 +9,8 @@
 // (TMA) engine into shared memory in address order.  Where bit 7 is not a target the runs are
 // only 1 KiB, and the kernel takes 256-group tiles (two M = 128 sub-tiles, row bit 7 = sub-tile)
 // so that every copy moves 2 KiB (measured: 1 KiB copies cap the kernel at ~74% of the 2 KiB
-// rate).
+// rate).  6-qubit blocks keep 128-group tiles (two accumulator sets of 256 columns fill the tensor
+// memory) in a 2-stage ring beside 64 KiB of R^T.
 //
 // One persistent CTA per SM, warp-specialised, tiles pipelined through a ring of S shared-memory
 // stages (one tile each, 128 x 2^k complex64):

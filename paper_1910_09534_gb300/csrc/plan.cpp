@@ -131,7 +131,7 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
     // units (the earliest seed on ties).  Taking units from anywhere in the circuit, not only
     // the next ones in gate order, lets a block run ahead on its qubits while other parts of the
     // lattice wait: on the 30-qubit, 20-cycle circuit 49 blocks of <= 5 qubits instead of 69
-    // in plain gate order (56 with the earliest ready unit as every block's seed).
+    // in plain gate order (56 with the earliest ready unit as every block's seed), 37 of <= 6.
     const int nu = (int)units.size();
     std::vector<std::vector<int>> succ(nu);
     std::vector<int> indeg(nu, 0), lastu(n_qubits, -1);
