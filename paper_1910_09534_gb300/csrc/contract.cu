@@ -481,7 +481,9 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g, co
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
 
-// Images, then the GEMM, all on st; the scratch (images + maxima) is stream-ordered memory.
+// Images, then the GEMM, all on st.  The scratch (images + maxima) belongs to the output handle
+// and is kept between calls: allocating it per call from the stream-ordered pool re-mapped it
+// every time the pool trimmed at a synchronisation, on the host's critical path.
 int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
                             const CtOut &o, cudaStream_t st)
 {
@@ -501,8 +503,15 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
     const uint32_t ks = (uint32_t)((n_e + 15) / 16);
     const uint64_t X = 1ull << n1, Y = 1ull << n2;
     const size_t a_bytes = (size_t)(X / 128) * ks * kCtSlab, b_bytes = (size_t)(Y / 128) * ks * kCtSlab;
-    uint8_t *scratch = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&scratch), a_bytes + b_bytes + 256, st) != cudaSuccess) return -1;
+    const size_t need = a_bytes + b_bytes + 256;
+    if (h->contract_bytes < need) {  // grow: cudaFree waits for the kernels still reading the old one
+        if (h->d_contract) cudaFree(h->d_contract);
+        h->d_contract = nullptr;
+        h->contract_bytes = 0;
+        if (cudaMalloc(reinterpret_cast<void **>(&h->d_contract), need) != cudaSuccess) return -1;
+        h->contract_bytes = need;
+    }
+    uint8_t *scratch = h->d_contract;
     float *amax = reinterpret_cast<float *>(scratch + a_bytes + b_bytes);
     int rc = 0;
     if (cudaMemsetAsync(amax, 0, 2 * sizeof(float), st) != cudaSuccess) rc = -1;
@@ -531,7 +540,6 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         prof_end(h, ps, st);
         if (cudaGetLastError() != cudaSuccess) rc = -1;
     }
-    if (cudaFreeAsync(scratch, st) != cudaSuccess) rc = -1;
     return rc;
 }
 

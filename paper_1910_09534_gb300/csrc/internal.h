@@ -56,6 +56,11 @@ struct sim_s {
 
     int *d_errflag = nullptr;  // set by kernels whose bounded waits ran out
 
+    // tensor-core contraction into this handle: FP16 operand images and the two scales, kept
+    // between calls (grown when a larger split needs more)
+    uint8_t *d_contract = nullptr;
+    size_t contract_bytes = 0;
+
     // tensor-core B fragments (fragment-major R^T, hi/lo) go through a device ring
     static constexpr int kFragSlots = 8;
     static constexpr int kFragWords = 2 * 16 * 16 * 64;  // k = 6, split: 128 KiB

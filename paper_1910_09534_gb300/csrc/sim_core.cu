@@ -95,6 +95,7 @@ static void release(sim_t *h)
         if (e) cudaEventDestroy(e);
     if (h->d_frag) cudaFree(h->d_frag);
     if (h->d_errflag) cudaFree(h->d_errflag);
+    if (h->d_contract) cudaFree(h->d_contract);
     if (h->h_frag) cudaFreeHost(h->h_frag);
     for (auto &e : h->frag_ev)
         if (e) cudaEventDestroy(e);
