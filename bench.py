@@ -63,8 +63,8 @@ def parse():
                          "run FP32 on CUDA cores)")
     ap.add_argument("--front-pairs", type=int, default=5,
                     help="contraction deferral (Sect. 2): the longest prefix of the circuit that "
-                         "bridges the lattice's middle column cut at most this many times runs as "
-                         "two tensors and their contraction; 0 = plain fused blocks only")
+                         "crosses the bipartition sim_split_choose picks at most this many times "
+                         "runs as two tensors and their contraction; 0 = plain fused blocks only")
     ap.add_argument("--no-layout", action="store_true",
                     help="keep the identity qubit layout instead of the one sim_plan_layout chooses")
     ap.add_argument("--e2e-steps", type=int, default=6)
@@ -350,20 +350,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def front_cut(circ, grid, max_pairs: int):
-    """Sides (lattice columns left / right of the middle) and the length of the longest prefix
-    of the gate list whose two-qubit gates bridge the cut at most max_pairs times."""
-    cols = max(c for (_, c) in grid.sites()) + 1
-    side = [0 if c < cols // 2 else 1 for (_, c) in grid.sites()]
-    pairs = 0
-    for i, (kind, q0, q1, _, _) in enumerate(circ.gates):
-        if q1 >= 0 and side[q0] != side[q1]:
-            if pairs == max_pairs:
-                return side, i, pairs
-            pairs += 1
-    return side, len(circ.gates), pairs
-
-
 def run_ours(args):
     import numpy as np
     import torch
@@ -405,9 +391,9 @@ def run_ours(args):
     front = None
     n_front, front_info = 0, None
     if args.front_pairs > 0:
-        side, n_front, pairs = front_cut(circ, si.WORKLOADS[args.workload]["grid"], args.front_pairs)
+        side, n_front = pkg.sim_split_choose(n, gates, args.front_pairs)
         split = pkg.sim_split_create(n, gates[:n_front], side)
-        n_side, n_wires, _, n_tg = pkg.sim_split_info(split)
+        n_side, n_wires, pairs, n_tg = pkg.sim_split_info(split)
         front = {}
 
         def front_for(hh):
@@ -417,7 +403,7 @@ def run_ours(args):
         tplans = [pkg.sim_plan_create(n_wires[t], pkg.sim_split_gates(split, t), kmax=args.kmax,
                                       precision=prec) for t in range(2)]
         front_info = {"gates": n_front, "bridging_gates": pairs, "entanglement_values": 4 ** pairs,
-                      "sides": "lattice columns < C/2 | >= C/2", "qubits_per_side": n_side,
+                      "sides": "sim_split_choose (the 5x6 lattice's middle column)", "qubits_per_side": n_side,
                       "tensor_qubits": n_wires,
                       "tensor_blocks": [pkg.sim_plan_info(p)[0] for p in tplans],
                       "contraction": "tcgen05 3xFP16" if prec in (pkg.SIM_FP16X3, pkg.SIM_FP16X3_TMEM)
@@ -732,7 +718,7 @@ def kernel_case():
     # contraction deferral on the 28-qubit workload: its gates up to the sixth one across the
     # middle column cut (12 + 16 qubits, 4^5 entanglement values), front run twice
     circ = si.workload_circuit("syc28_4x7_d20", seed=0)
-    side, nf, _ = front_cut(circ, si.WORKLOADS["syc28_4x7_d20"]["grid"], 5)
+    side, nf = pkg.sim_split_choose(n, pkg.gates_array(circ), 5)
     s = pkg.sim_split_create(n, pkg.gates_array(circ)[:nf], side)
     f = pkg.sim_front_create(h, s, kmax=5, precision=pkg.SIM_FP16X3_TMEM)
     for _ in range(2):

@@ -415,6 +415,18 @@ int sim_split_gates(const sim_split_t *s, int t, sim_gate *out);
 int sim_split_canonical(const sim_split_t *s, int t, int *wire_at);
 int sim_split_destroy(sim_split_t *s);
 
+/* Choose the bipartition and the first phase for contraction deferral (the paper draws its
+ * partitions by hand).  Among splits whose sides have at least min_side qubits (<= 0: 7, the
+ * tensor-core contraction's minimum; clamped to n_qubits / 2) and lie within max(1, n/8) qubits
+ * of an even split, searches -- from a half grown breadth-first over the circuit's couplings
+ * around every qubit, then the best single-qubit moves and exchanges while they help -- for the
+ * longest prefix of the gate list that crosses the split at most max_pairs times (ties: the later
+ * following crossings, then the more even split).  Writes side[q] (0 or 1) and *n_front: gates
+ * [0, n_front) are the split's gate list for sim_split_create, the rest run on the contracted
+ * state.  Host only.  SIM_E_INVAL for bad arguments. */
+int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side, int *side,
+                     int *n_front);
+
 /* The contraction (Appendix: the sum over the entanglement indices): psi = sum_pairs T1 T2 into
  * `out`.  t1 / t2: device-resident handles of n_wires[0] / n_wires[1] qubits holding the two
  * tensors (their gate lists applied); out: a device-resident handle of n_qubits qubits, not

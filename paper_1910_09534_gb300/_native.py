@@ -146,6 +146,8 @@ _SIGS = {
     "sim_split_gates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_split_choose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "sim_contract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_int]),
     "sim_front_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -523,6 +525,15 @@ def sim_split_canonical(s, t: int):
     out = np.zeros(nw, dtype=np.int32)
     _check(lib().sim_split_canonical(s, t, _ptr(out)))
     return [int(x) for x in out]
+
+
+def sim_split_choose(n_qubits: int, gates: np.ndarray, max_pairs: int = 5, min_side: int = 0):
+    """(side, n_front): a bipartition and the gate-list prefix for contraction deferral."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    side = np.zeros(n_qubits, dtype=np.int32)
+    nf = ctypes.c_int()
+    _check(lib().sim_split_choose(n_qubits, int(g.size), _ptr(g), max_pairs, min_side, _ptr(side), ctypes.byref(nf)))
+    return [int(x) for x in side], nf.value
 
 
 def sim_split_destroy(s) -> None:

@@ -8,6 +8,8 @@
 // two fresh wires (v1, v2) gives sum_x |x>_v1 |x>_v2; the bridging gate G then acts on (v1, b)
 // with v1 in the role of qubit a, so v1 ends as a' = G's output for a, v2 keeps a = G's input,
 // and b's wire holds b''.  Both tensors number their pairs in the order of the bridging gates.
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -233,4 +235,124 @@ extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
         if (rc != SIM_OK) return fail(out, rc, "sim_front_run: tensor %d: %s", t + 1, f->t[t]->err.c_str());
     }
     return sim_contract(out, f->t[0], f->t[1], &f->split, f->contract_precision);
+}
+
+namespace {
+
+// Positions of the (max_pairs + 1)-th .. (max_pairs + 4)-th gates that cross the split (n_gates
+// where there are fewer), then the negated imbalance: larger is better, compared in order.
+struct SplitScore {
+    int pos[4];
+    int balance;
+    bool operator>(const SplitScore &o) const
+    {
+        for (int i = 0; i < 4; ++i)
+            if (pos[i] != o.pos[i]) return pos[i] > o.pos[i];
+        return balance > o.balance;
+    }
+};
+
+SplitScore split_score(const std::vector<std::pair<int, int>> &two, const std::vector<int> &gate_index,
+                       int n_gates, const std::vector<char> &side, int max_pairs, int n)
+{
+    SplitScore sc{{n_gates, n_gates, n_gates, n_gates}, 0};
+    int pairs = 0, k = 0;
+    for (size_t i = 0; i < two.size() && k < 4; ++i)
+        if (side[two[i].first] != side[two[i].second] && ++pairs > max_pairs) sc.pos[k++] = gate_index[i];
+    int a = 0;
+    for (int q = 0; q < n; ++q) a += side[q] == 0;
+    sc.balance = -std::abs(2 * a - n);
+    return sc;
+}
+
+}  // namespace
+
+extern "C" int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side,
+                                int *side, int *n_front)
+{
+    if (n_qubits < 2 || n_qubits > kMaxQubits || n_gates < 0 || (n_gates > 0 && !gates) || max_pairs < 0 || !side ||
+        !n_front)
+        return fail(nullptr, SIM_E_INVAL, "sim_split_choose: bad arguments");
+    const int n = n_qubits;
+    if (min_side <= 0) min_side = 7;
+    min_side = std::min(min_side, n / 2);
+    const int slack = std::max(1, n / 8);
+    const int lo = std::max(min_side, n / 2 - slack), hi = std::min(n - min_side, (n + 1) / 2 + slack);
+    // the two-qubit gates in order, and the couplings between qubits
+    std::vector<std::pair<int, int>> two;
+    std::vector<int> gate_index;
+    std::vector<std::vector<int>> adj(n);
+    for (int i = 0; i < n_gates; ++i) {
+        double m[32];
+        const int d = gate_matrix(gates[i], m);
+        if (d == 0 || gates[i].q0 < 0 || gates[i].q0 >= n)
+            return fail(nullptr, SIM_E_INVAL, "sim_split_choose: bad gate %d", i);
+        if (d != 4) continue;
+        const int a = gates[i].q0, b = gates[i].q1;
+        if (b < 0 || b >= n || a == b) return fail(nullptr, SIM_E_INVAL, "sim_split_choose: bad qubits in gate %d", i);
+        two.push_back({a, b});
+        gate_index.push_back(i);
+        if (std::find(adj[a].begin(), adj[a].end(), b) == adj[a].end()) {
+            adj[a].push_back(b);
+            adj[b].push_back(a);
+        }
+    }
+    for (auto &v : adj) std::sort(v.begin(), v.end());
+    std::vector<char> best_side;
+    SplitScore best{};
+    bool have = false;
+    for (int seed = 0; seed < n; ++seed) {
+        // a half grown breadth-first from the seed over the couplings, topped up in qubit order
+        std::vector<char> sd(n, 1);
+        std::vector<int> order{seed};
+        sd[seed] = 0;
+        int cnt = 1;
+        for (size_t qi = 0; qi < order.size() && cnt < n / 2; ++qi)
+            for (int v : adj[order[qi]])
+                if (sd[v] == 1 && cnt < n / 2) {
+                    sd[v] = 0;
+                    ++cnt;
+                    order.push_back(v);
+                }
+        for (int q = 0; q < n && cnt < n / 2; ++q)
+            if (sd[q] == 1) sd[q] = 0, ++cnt;
+        SplitScore cur = split_score(two, gate_index, n_gates, sd, max_pairs, n);
+        for (int iter = 0; iter < 4 * n; ++iter) {  // best improving move, until none
+            SplitScore bm{};
+            int ba = -1, bb = -1;
+            bool found = false;
+            for (int a = 0; a < n; ++a) {  // one qubit to the other side
+                const int size0 = cnt + (sd[a] ? 1 : -1);
+                if (size0 < lo || size0 > hi) continue;
+                sd[a] ^= 1;
+                const SplitScore g = split_score(two, gate_index, n_gates, sd, max_pairs, n);
+                sd[a] ^= 1;
+                if (g > cur && (!found || g > bm)) bm = g, ba = a, bb = -1, found = true;
+            }
+            for (int a = 0; a < n; ++a) {  // an exchange
+                if (sd[a] != 0) continue;
+                for (int b = 0; b < n; ++b) {
+                    if (sd[b] != 1) continue;
+                    sd[a] = 1, sd[b] = 0;
+                    const SplitScore g = split_score(two, gate_index, n_gates, sd, max_pairs, n);
+                    sd[a] = 0, sd[b] = 1;
+                    if (g > cur && (!found || g > bm)) bm = g, ba = a, bb = b, found = true;
+                }
+            }
+            if (!found) break;
+            if (bb < 0) cnt += sd[ba] ? 1 : -1;  // a move changes the sizes, an exchange does not
+            sd[ba] ^= 1;
+            if (bb >= 0) sd[bb] ^= 1;
+            cur = bm;
+        }
+        if (cnt >= lo && cnt <= hi && (!have || cur > best)) {
+            best = cur;
+            best_side = sd;
+            have = true;
+        }
+    }
+    if (!have) return fail(nullptr, SIM_E_INVAL, "sim_split_choose: no split with sides of >= %d qubits", min_side);
+    for (int q = 0; q < n; ++q) side[q] = best_side[q];
+    *n_front = best.pos[0];
+    return SIM_OK;
 }

@@ -360,3 +360,53 @@ def test_plan_layout_is_a_bijection_no_worse_than_identity(pkg):
     L = pkg.lib()
     assert L.sim_plan_layout(None, None, None) == pkg.SIM_E_INVAL
     assert L.sim_set_layout(None, None) == pkg.SIM_E_INVAL
+
+
+def _front_len(gates, side, max_pairs):
+    pairs = 0
+    for i, g in enumerate(gates):
+        if g[2] >= 0 and side[g[1]] != side[g[2]]:
+            if pairs == max_pairs:
+                return i
+            pairs += 1
+    return len(gates)
+
+
+@pytest.mark.parametrize("shape,cycles,seed,max_pairs", [((2, 4), 8, 1, 3), ((3, 3), 8, 2, 4), ((2, 5), 10, 3, 3),
+                                                         ((3, 4), 8, 4, 5), ((2, 6), 10, 5, 4)])
+def test_split_choice_matches_brute_force(pkg, shape, cycles, seed, max_pairs):
+    # the search's front equals the longest over every bipartition in the allowed size window
+    import itertools
+    circ = si.sycamore_circuit(si.Grid(*shape), cycles, seed)
+    n = circ.n_qubits
+    side, nf = pkg.sim_split_choose(n, pkg.gates_array(circ), max_pairs, min_side=3)
+    slack = max(1, n // 8)
+    lo, hi = max(min(3, n // 2), n // 2 - slack), min(n - min(3, n // 2), (n + 1) // 2 + slack)
+    assert lo <= side.count(0) <= hi
+    assert nf == _front_len(circ.gates, side, max_pairs)
+    best = 0
+    for k in range(lo, hi + 1):
+        for comb in itertools.combinations(range(n), k):
+            sd = [1] * n
+            for q in comb:
+                sd[q] = 0
+            best = max(best, _front_len(circ.gates, sd, max_pairs))
+    assert nf == best
+
+
+def test_split_choice_on_the_30_qubit_workload(pkg):
+    # the lattice's middle column: 5 crossings in the first 6 cycles, 284 gates
+    circ = si.workload_circuit("syc30_5x6_d20", seed=0)
+    side, nf = pkg.sim_split_choose(30, pkg.gates_array(circ), 5)
+    assert nf == 284 and side.count(0) == 15
+    bridging = [g for g in circ.gates[:nf] if g[2] >= 0 and side[g[1]] != side[g[2]]]
+    assert len(bridging) == 5
+    g = circ.gates[nf]
+    assert g[2] >= 0 and side[g[1]] != side[g[2]]  # the sixth crossing ends the front
+    s = pkg.sim_split_create(30, pkg.gates_array(circ)[:nf], side)
+    try:
+        assert pkg.sim_split_info(s)[2] == 5
+    finally:
+        pkg.sim_split_destroy(s)
+    L = pkg.lib()
+    assert L.sim_split_choose(1, 0, None, 5, 0, None, None) == pkg.SIM_E_INVAL
