@@ -279,7 +279,10 @@ def serving_run(count: int, device: int):
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
             "one_at_a_time_p99_ms": statistics.quantiles(seq_done, n=100)[98],
             "arithmetic": "fp16x3_tmem (k_max 6 in a chosen layout above 20 qubits; circuits of <= 20 "
-                          "qubits packed one per CTA in FP32, k_max 5)"}
+                          "qubits packed one per CTA in FP32, k_max 5)",
+            "server_front": "circuits of >= 26 qubits whose first 5 crossings of the chosen bipartition "
+                            "leave >= 30% of the gates in front run them as two tensors and one tcgen05 "
+                            "contraction; the one-at-a-time path runs every circuit plainly"}
 
 
 def graph_replay_run(device: int, runs: int = 30):

@@ -493,7 +493,12 @@ typedef struct srv_opts {
                           * sim_plan_layout picks and are permuted back before a readout */
     int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_FP16X3_TMEM */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
-    int reserved[8];
+    int front_pairs;     /* contraction deferral for circuits of >= 26 qubits in SIM_FP16X3_TMEM:
+                          * the gates up to the (front_pairs + 1)-th across the bipartition
+                          * sim_split_choose picks run as two tensors and one tensor-core
+                          * contraction when they are >= 30% of the circuit (0 = 5, < 0 = off);
+                          * the tensors and the contraction's scratch count in the footprint */
+    int reserved[7];
 } srv_opts;
 
 typedef struct srv_stats_t {

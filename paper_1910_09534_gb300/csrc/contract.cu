@@ -484,8 +484,14 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g, co
 // Images, then the GEMM, all on st.  The scratch (images + maxima) belongs to the output handle
 // and is kept between calls: allocating it per call from the stream-ordered pool re-mapped it
 // every time the pool trimmed at a synchronisation, on the host's critical path.
+size_t tcgen05_scratch_bytes(int n1, int n2, int e_bits)
+{
+    const uint64_t ks = ((1ull << e_bits) + 15) / 16;
+    return (size_t)((1ull << n1) / 128) * ks * kCtSlab + (size_t)((1ull << n2) / 128) * ks * kCtSlab + 256;
+}
+
 int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                            const CtOut &o, cudaStream_t st)
+                            const CtOut &o, cudaStream_t st, uint8_t *own_scratch = nullptr)
 {
     static const LaunchCfg cfg = [] {
         LaunchCfg c;
@@ -504,14 +510,14 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
     const uint64_t X = 1ull << n1, Y = 1ull << n2;
     const size_t a_bytes = (size_t)(X / 128) * ks * kCtSlab, b_bytes = (size_t)(Y / 128) * ks * kCtSlab;
     const size_t need = a_bytes + b_bytes + 256;
-    if (h->contract_bytes < need) {  // grow: cudaFree waits for the kernels still reading the old one
+    if (!own_scratch && h->contract_bytes < need) {  // grow: cudaFree waits for kernels still reading it
         if (h->d_contract) cudaFree(h->d_contract);
         h->d_contract = nullptr;
         h->contract_bytes = 0;
         if (cudaMalloc(reinterpret_cast<void **>(&h->d_contract), need) != cudaSuccess) return -1;
         h->contract_bytes = need;
     }
-    uint8_t *scratch = h->d_contract;
+    uint8_t *scratch = own_scratch ? own_scratch : h->d_contract;
     float *amax = reinterpret_cast<float *>(scratch + a_bytes + b_bytes);
     int rc = 0;
     if (cudaMemsetAsync(amax, 0, 2 * sizeof(float), st) != cudaSuccess) rc = -1;
@@ -551,7 +557,7 @@ namespace sycsim {
 // 0 .. n_side-1 in the order of their physical bits in out (so a warp's 32 consecutive x, or the
 // y of one thread, land on the lowest physical bits the side holds), the entanglement pairs above
 // in pair order.  bit_of_wire[w] = the physical bit of wire w; side_qubit[i] = the qubit at bit i.
-void contract_layout(const sim_split_s *s, const sim_t *out, int t, int *bit_of_wire, int *side_qubit)
+void contract_layout(const sim_split_s *s, const int *out_bit_of, int t, int *bit_of_wire, int *side_qubit)
 {
     const int ns = s->n_side[t];
     int order[kMaxQubits], q_of[kMaxQubits];  // canonical position p < ns -> qubit
@@ -559,12 +565,34 @@ void contract_layout(const sim_split_s *s, const sim_t *out, int t, int *bit_of_
     for (int q = 0; q < s->n; ++q)
         if (s->side[q] == t) q_of[c++] = q;
     for (int p = 0; p < ns; ++p) order[p] = p;
-    std::sort(order, order + ns, [&](int a, int b) { return out->bit_of[q_of[a]] < out->bit_of[q_of[b]]; });
+    std::sort(order, order + ns, [&](int a, int b) { return out_bit_of[q_of[a]] < out_bit_of[q_of[b]]; });
     for (int i = 0; i < ns; ++i) {
         bit_of_wire[s->wire_at[t][order[i]]] = i;
         if (side_qubit) side_qubit[i] = q_of[order[i]];
     }
     for (int p = ns; p < (int)s->wire_at[t].size(); ++p) bit_of_wire[s->wire_at[t][p]] = p;
+}
+
+size_t contraction_scratch_bytes(const sim_split_s *s)
+{
+    return tcgen05_scratch_bytes(s->n_side[0], s->n_side[1], 2 * s->n_pairs);
+}
+
+int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
+                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st)
+{
+    const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
+    int side_qubit[2][kMaxQubits], lay[kMaxQubits];
+    for (int t = 0; t < 2; ++t) contract_layout(s, out_bit_of, t, lay, side_qubit[t]);
+    CtOut o{};
+    for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out_bit_of[side_qubit[0][i]];
+    for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out_bit_of[side_qubit[1][j]];
+    if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7)
+        return launch_contract_tcgen05(h, t1, t2, psi, n1, n2, e_bits, o, st, scratch);
+    const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, n1 + n2 + e_bits), st);
+    const int rc = launch_contract_fp32(t1, t2, psi, n1, n2, e_bits, o, st);
+    prof_end(h, ps, st);
+    return rc;
 }
 
 }  // namespace sycsim
@@ -589,11 +617,10 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
 
     // each tensor into the layout that matches out's (contract_layout)
     sim_t *tens[2] = {t1, t2};
-    int side_qubit[2][kMaxQubits];
     for (int t = 0; t < 2; ++t) {
         sim_t *h = tens[t];
         int perm[kMaxQubits];
-        contract_layout(s, out, t, perm, side_qubit[t]);
+        contract_layout(s, out->bit_of, t, perm, nullptr);
         bool same = true;
         for (int w = 0; w < h->n; ++w) same = same && h->bit_of[w] == perm[w];
         if (!same) {
@@ -613,18 +640,9 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         destroy();
         return fail(out, SIM_E_CUDA, "sim_contract: stream ordering failed");
     }
-    // psi goes straight into out's current layout: bit i of x is side-0 qubit side_qubit[0][i]
-    CtOut o{};
-    for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out->bit_of[side_qubit[0][i]];
-    for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out->bit_of[side_qubit[1][j]];
-    int rc;
-    if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7) {
-        rc = launch_contract_tcgen05(out, t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, o, out->stream);
-    } else {
-        const int ps = prof_begin(out, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, n1 + n2 + e_bits), out->stream);
-        rc = launch_contract_fp32(t1->d_state, t2->d_state, out->d_state, n1, n2, e_bits, o, out->stream);
-        prof_end(out, ps, out->stream);
-    }
+    // psi goes straight into out's current layout
+    const int rc = enqueue_contraction(out, s, t1->d_state, t2->d_state, out->d_state, out->bit_of, precision,
+                                       nullptr, out->stream);
     if (rc != 0) {
         destroy();
         return fail(out, SIM_E_CUDA, "sim_contract: launch failed: %s", cudaGetErrorString(cudaGetLastError()));

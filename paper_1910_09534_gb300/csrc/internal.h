@@ -238,9 +238,20 @@ int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int phy
 int host_reduce(sim_t *h, double *s1, double *s2);
 
 // ---- contract.cu ----
-// Physical bit of each wire of tensor t for a contraction into out (and the side qubit at each of
-// the side's bits, if side_qubit is not NULL).
-void contract_layout(const sim_split_s *s, const sim_t *out, int t, int *bit_of_wire, int *side_qubit);
+// Physical bit of each wire of tensor t for a contraction into a state whose layout is out_bit_of
+// (and the side qubit at each of the side's bits, if side_qubit is not NULL).
+void contract_layout(const sim_split_s *s, const int *out_bit_of, int t, int *bit_of_wire, int *side_qubit);
+// sim_split_choose's search from max_seeds seed qubits spread over 0 .. n-1 (the public call
+// tries every qubit).
+int split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side, int *side,
+                 int *n_front, int max_seeds);
+// Device bytes of the tensor-core contraction's scratch (operand images, scales) for a split.
+size_t contraction_scratch_bytes(const sim_split_s *s);
+// psi (layout out_bit_of) = the contraction of the tensors t1, t2 (each in contract_layout), on
+// stream st: tcgen05 when precision is not SIM_FP32 and both sides have >= 7 qubits (scratch: a
+// buffer of contraction_scratch_bytes, or NULL for h's own), else the FP32 kernel.
+int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
+                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st);
 
 // ---- gates.cpp ----
 // Matrix of a gate record (2x2 or 4x4 complex128, row-major); returns the dimension or 0.

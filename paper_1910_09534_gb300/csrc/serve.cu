@@ -172,6 +172,14 @@ struct Req {
     std::vector<Prepared> blocks;
     std::vector<int> back;  // unpacked: the permutation from the chosen layout back to the identity
     uint64_t bytes = 0;     // admission footprint
+    // contraction deferral (unpacked): blocks[0 .. nt[0]) run on tensor 1, the next nt[1] on
+    // tensor 2, then the contraction writes the state (layout out_bit_of) and the rest follow
+    std::shared_ptr<sim_split_s> split;
+    int nt[2] = {0, 0}, nw[2] = {0, 0};
+    std::vector<int> out_bit_of;
+    float2 *d_t[2] = {nullptr, nullptr};
+    uint8_t *d_scratch = nullptr;
+    bool contracted = false;
     Clock::time_point t_submit, t_done;
     int status = 1;  // 1 pending, 0 ok, < 0 error
     double norm = 0.0, s2 = 0.0;
@@ -198,6 +206,8 @@ struct Batch {
 };
 
 constexpr int kMaxBypass = 64;
+constexpr int kFrontMinQubits = 26;      // smaller states: the passes a front saves are too short
+constexpr double kFrontMinShare = 0.3;   // a front with fewer of the gates is not worth a contraction
 constexpr int kResultRing = 1 << 16;
 
 }  // namespace
@@ -280,9 +290,27 @@ int start_unpacked(srv_t *s, int i, const std::shared_ptr<Req> &r)
     r->next_block = 0;
     r->launched = false;
     s->slot_req[i] = r;
+    r->contracted = false;
     if (cudaMallocAsync(&r->d_state, sizeof(float2) * amps, st) != cudaSuccess) {
         r->d_state = nullptr;
         return SIM_E_NOMEM_DEV;
+    }
+    if (r->split) {  // the two tensors from |0...0>; the contraction will write every amplitude
+        for (int t = 0; t < 2; ++t) {
+            const uint64_t ta = 1ull << r->nw[t];
+            if (cudaMallocAsync(&r->d_t[t], sizeof(float2) * ta, st) != cudaSuccess) {
+                r->d_t[t] = nullptr;
+                return SIM_E_NOMEM_DEV;
+            }
+            if (cudaMemsetAsync(r->d_t[t], 0, sizeof(float2) * ta, st) != cudaSuccess) return SIM_E_CUDA;
+            if (launch_set_basis(r->d_t[t], ta, 0, st) != 0) return SIM_E_CUDA;
+        }
+        if (cudaMallocAsync(reinterpret_cast<void **>(&r->d_scratch), contraction_scratch_bytes(r->split.get()), st) !=
+            cudaSuccess) {
+            r->d_scratch = nullptr;
+            return SIM_E_NOMEM_DEV;
+        }
+        return SIM_OK;
     }
     if (cudaMemsetAsync(r->d_state, 0, sizeof(float2) * amps, st) != cudaSuccess) return SIM_E_CUDA;
     if (launch_set_basis(r->d_state, amps, 0, st) != 0) return SIM_E_CUDA;
@@ -298,13 +326,39 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
     sim_t *h = s->slots[r->slot];
     cudaStream_t st = h->stream;
     const uint64_t amps = 1ull << r->n;
+    const size_t tensor_blocks = (size_t)r->nt[0] + r->nt[1];
+    auto contract = [&]() {  // after both tensors' blocks: the state from the two tensors
+        if (enqueue_contraction(h, r->split.get(), r->d_t[0], r->d_t[1], r->d_state, r->out_bit_of.data(),
+                                r->precision, r->d_scratch, st) != 0)
+            return SIM_E_CUDA;
+        for (auto &p : r->d_t) {
+            if (cudaFreeAsync(p, st) != cudaSuccess) return SIM_E_CUDA;
+            p = nullptr;
+        }
+        if (cudaFreeAsync(r->d_scratch, st) != cudaSuccess) return SIM_E_CUDA;
+        r->d_scratch = nullptr;
+        r->contracted = true;
+        *progressed = true;
+        return SIM_OK;
+    };
     while (r->next_block < r->blocks.size()) {
+        if (r->split && !r->contracted && r->next_block == tensor_blocks) {
+            const int rc = contract();
+            if (rc != SIM_OK) return rc;
+        }
         const Prepared &b = r->blocks[r->next_block];
-        if (!staging_slot_free(h, r->n, b.k, b.tpos, r->precision)) return SIM_OK;
-        const int rc = enqueue_block_on(h, r->d_state, r->n, b.k, b.tpos, b.mat.data(), r->precision, st);
+        const int t = r->next_block < (size_t)r->nt[0] ? 0 : (r->next_block < tensor_blocks ? 1 : -1);
+        float2 *buf = t < 0 || !r->split ? r->d_state : r->d_t[t];
+        const int nbits = t < 0 || !r->split ? r->n : r->nw[t];
+        if (!staging_slot_free(h, nbits, b.k, b.tpos, r->precision)) return SIM_OK;
+        const int rc = enqueue_block_on(h, buf, nbits, b.k, b.tpos, b.mat.data(), r->precision, st);
         if (rc != SIM_OK) return rc;
         r->next_block++;
         *progressed = true;
+    }
+    if (r->split && !r->contracted) {
+        const int rc = contract();
+        if (rc != SIM_OK) return rc;
     }
     if (launch_reduce(h, r->d_state, amps, h->d_partials, h->d_result, st) != 0) return SIM_E_CUDA;
     if (cudaMemcpyAsync(r->h_res, h->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -326,8 +380,13 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
 void abort_unpacked(srv_t *s, int i, int rc)
 {
     auto r = s->slot_req[i];
-    if (r->d_state) cudaFreeAsync(r->d_state, s->slots[i]->stream);
+    cudaStream_t st = s->slots[i]->stream;
+    if (r->d_state) cudaFreeAsync(r->d_state, st);
     r->d_state = nullptr;
+    for (auto &p : r->d_t)
+        if (p) cudaFreeAsync(p, st), p = nullptr;
+    if (r->d_scratch) cudaFreeAsync(r->d_scratch, st);
+    r->d_scratch = nullptr;
     s->slot_req[i].reset();
     finish(s, r, rc, 0.0, 0.0);
     s->cv_done.notify_all();
@@ -616,9 +675,41 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     po.kmax = s->o.kmax ? s->o.kmax : auto_kmax(n_qubits, r->packed, r->precision);
     if (r->packed) po.kmax = std::min(po.kmax, kPackMaxK);
     po.precision = r->precision;
-    sim_plan_t *plan = nullptr;
-    int rc = sim_plan_create(n_qubits, n_gates, gates, &po, &plan);
+    // contraction deferral (Sect. 2) for large circuits in the tcgen05 mode: the gates up to the
+    // (pairs + 1)-th across the bipartition split_choose picks run as two tensors and one
+    // tensor-core contraction, when that front holds a large enough share of the circuit
+    int front = 0;
+    std::vector<int> side(n_qubits, 0);
+    if (!r->packed && r->precision == SIM_FP16X3_TMEM && n_qubits >= kFrontMinQubits && s->o.front_pairs >= 0) {
+        int nf = 0;
+        if (split_choose(n_qubits, n_gates, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf,
+                         n_qubits) == SIM_OK &&
+            nf >= kFrontMinShare * n_gates)
+            front = nf;
+    }
+    sim_split_t *sp = nullptr;
+    if (front && sim_split_create(n_qubits, front, gates, side.data(), &sp) == SIM_OK) {
+        uint64_t extra = contraction_scratch_bytes(sp);
+        for (int t = 0; t < 2; t++) extra += sizeof(float2) << (sp->n_side[t] + 2 * sp->n_pairs);
+        if (r->bytes + extra <= s->budget) {
+            r->split.reset(sp, [](sim_split_s *p) { sim_split_destroy(p); });
+            r->bytes += extra;
+        } else {
+            sim_split_destroy(sp);
+        }
+    }
+    if (!r->split) front = 0;
+    sim_plan_t *plan = nullptr;  // the gates after the front (all of them without one)
+    int rc = sim_plan_create(n_qubits, n_gates - front, gates + front, &po, &plan);
+    sim_plan_t *tplan[2] = {nullptr, nullptr};
+    for (int t = 0; rc == SIM_OK && r->split && t < 2; t++) {
+        r->nw[t] = r->split->n_side[t] + 2 * r->split->n_pairs;
+        rc = sim_plan_create(r->nw[t], (int)r->split->gates[t].size(), r->split->gates[t].data(), &po, &tplan[t]);
+    }
     if (rc != SIM_OK) {
+        for (auto *tp : tplan)
+            if (tp) sim_plan_destroy(tp);
+        if (plan) sim_plan_destroy(plan);
         std::lock_guard<std::mutex> lk(s->mu);
         s->rejected++;
         return srv_fail(s, rc, "srv_submit: %s", sim_last_error(nullptr));
@@ -636,16 +727,32 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
             for (int q = 0; q < n_qubits; q++) r->back[phys[q]] = q;
         }
     }
-    r->blocks.resize(plan->blocks.size());
-    for (size_t i = 0; i < plan->blocks.size(); i++) {
-        const PlanBlock &b = plan->blocks[i];
-        Prepared &pb = r->blocks[i];
-        pb.k = (int)b.qubits.size();
-        pb.mat.resize((size_t)1 << (2 * pb.k));
-        rc = prepare_block_map(s->slots[0], pb.k, b.qubits.data(), b.mat.data(), phys, n_qubits, pb.tpos,
-                               pb.mat.data(), n_qubits);
-        if (rc != SIM_OK) break;
+    // blocks: tensor 1's, tensor 2's (each tensor laid out as the contraction into phys wants),
+    // then the rest's
+    auto prepare = [&](const sim_plan_t *p, const int *phys_of, int nq) {
+        for (const PlanBlock &b : p->blocks) {
+            Prepared pb;
+            pb.k = (int)b.qubits.size();
+            pb.mat.resize((size_t)1 << (2 * pb.k));
+            const int prc = prepare_block_map(s->slots[0], pb.k, b.qubits.data(), b.mat.data(), phys_of, nq, pb.tpos,
+                                              pb.mat.data(), nq);
+            if (prc != SIM_OK) return prc;
+            r->blocks.push_back(std::move(pb));
+        }
+        return (int)SIM_OK;
+    };
+    if (r->split) {
+        r->out_bit_of.assign(phys, phys + n_qubits);
+        for (int t = 0; rc == SIM_OK && t < 2; t++) {
+            int lay[kMaxQubits];
+            contract_layout(r->split.get(), phys, t, lay, nullptr);
+            rc = prepare(tplan[t], lay, r->nw[t]);
+            r->nt[t] = (int)tplan[t]->blocks.size();
+        }
     }
+    if (rc == SIM_OK) rc = prepare(plan, phys, n_qubits);
+    for (auto *tp : tplan)
+        if (tp) sim_plan_destroy(tp);
     sim_plan_destroy(plan);
     if (rc != SIM_OK) return srv_fail(s, rc, "srv_submit: block preparation failed");
     int prev_dev = 0;

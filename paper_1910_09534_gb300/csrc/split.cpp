@@ -223,7 +223,7 @@ extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
         // relabel the tensor (free: its state is reset next) into the layout the contraction into
         // out wants, so that no run permutes
         int lay[kMaxQubits];
-        contract_layout(&f->split, out, t, lay, nullptr);
+        contract_layout(&f->split, out->bit_of, t, lay, nullptr);
         for (int w = 0; w < f->t[t]->n; ++w) {
             f->t[t]->bit_of[w] = lay[w];
             f->t[t]->qubit_at[lay[w]] = w;
@@ -267,8 +267,22 @@ SplitScore split_score(const std::vector<std::pair<int, int>> &two, const std::v
 
 }  // namespace
 
+namespace sycsim {
+
+int split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side, int *side,
+                 int *n_front, int max_seeds);
+
+}  // namespace sycsim
+
 extern "C" int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side,
                                 int *side, int *n_front)
+{
+    return split_choose(n_qubits, n_gates, gates, max_pairs, min_side, side, n_front, n_qubits);
+}
+
+// The search of sim_split_choose from max_seeds seed qubits spread evenly over 0 .. n-1.
+int sycsim::split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs, int min_side, int *side,
+                         int *n_front, int max_seeds)
 {
     if (n_qubits < 2 || n_qubits > kMaxQubits || n_gates < 0 || (n_gates > 0 && !gates) || max_pairs < 0 || !side ||
         !n_front)
@@ -301,7 +315,9 @@ extern "C" int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates
     std::vector<char> best_side;
     SplitScore best{};
     bool have = false;
-    for (int seed = 0; seed < n; ++seed) {
+    const int seeds = std::max(1, std::min(max_seeds, n));
+    for (int si = 0; si < seeds; ++si) {
+        const int seed = (int)((int64_t)si * n / seeds);
         // a half grown breadth-first from the seed over the couplings, topped up in qubit order
         std::vector<char> sd(n, 1);
         std::vector<int> order{seed};

@@ -92,6 +92,30 @@ def test_default_tcgen05_mode_blocks_of_six_in_a_chosen_layout(pkg, oracle_mod):
         assert err <= TOL_FP32 and abs(norm - 1.0) < 1e-5
 
 
+def test_large_circuits_take_the_contraction_front(pkg, oracle_mod):
+    # >= 26 qubits in SIM_FP16X3_TMEM: the first gates as two tensors contracted on the tensor cores
+    # (when they are >= 30 % of the circuit), the rest in the chosen layout; logical-order
+    # amplitudes match the oracle and are the same alone and in a mix; with front_pairs < 0 the
+    # same circuits run without the front
+    circuits = [si.sycamore_circuit(si.near_square_grid(n), d, seed=700 + i)
+                for i, (n, d) in enumerate([(26, 9), (27, 11), (26, 14)])]
+    mix, res, stats = serve(pkg, circuits, True, slots=2, precision=pkg.SIM_FP16X3_TMEM)
+    alone, _, _ = serve(pkg, circuits, False, slots=2, precision=pkg.SIM_FP16X3_TMEM)
+    plain, _, _ = serve(pkg, circuits, False, slots=2, precision=pkg.SIM_FP16X3_TMEM, front_pairs=-1)
+    assert stats["completed"] == len(circuits)
+    for c, a, b, p, (norm, s2, lat) in zip(circuits, mix, alone, plain, res):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
+        want = oracle_mod.run_circuit(c)
+        err = np.linalg.norm(a.astype(np.complex128) - want)
+        err_plain = np.linalg.norm(p.astype(np.complex128) - want)
+        side, nf = pkg.sim_split_choose(c.n_qubits, pkg.gates_array(c), 5)
+        print(f"served {c.n_qubits} qubits, {len(c.gates)} gates, front of {nf}: err {err:.2e} "
+              f"(without the front {err_plain:.2e})")
+        assert nf >= 0.3 * len(c.gates)
+        assert err <= TOL_FP32 and err_plain <= TOL_FP32 and abs(norm - 1.0) < 1e-5
+        assert not np.array_equal(a, p)  # the front did run
+
+
 def test_admission_respects_hbm_budget(pkg, oracle_mod):
     # 20-qubit states are 8 MiB; a 20 MiB budget admits two at a time
     circuits = [si.sycamore_circuit(si.near_square_grid(20), 6, seed=s) for s in range(5)]
