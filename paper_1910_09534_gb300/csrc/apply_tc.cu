@@ -314,13 +314,12 @@ int launch_f16x3_staged(float2 *psi, int nbits, const int *tpos, const uint32_t 
     }
     g.bfrag = d_frag;
     auto kern = k_apply_mma_f16x3<K>;
+    static std::atomic<uint64_t> smem_done{0};
+    if (bytes > 48 * 1024 && !smem_opt_in(kern, (int)bytes, smem_done)) return -1;
     static const LaunchCfg cfg = [&] {  // once per instantiation, thread-safe
         LaunchCfg c;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return c;
-        if (bytes > 48 * 1024 &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return c;
         if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, 256, bytes) != cudaSuccess || c.occ < 1)
             c.occ = 1;
@@ -412,13 +411,12 @@ int launch_mma_staged(float2 *psi, int nbits, const int *tpos, const uint32_t *d
     }
     g.bfrag = d_frag;
     auto kern = k_apply_mma<K, kSplit>;
+    static std::atomic<uint64_t> smem_done{0};
+    if (bytes > 48 * 1024 && !smem_opt_in(kern, (int)bytes, smem_done)) return -1;
     static const LaunchCfg cfg = [&] {  // once per instantiation, thread-safe
         LaunchCfg c;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return c;
-        if (bytes > 48 * 1024 &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return c;
         if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.occ, kern, 256, bytes) != cudaSuccess || c.occ < 1)
             c.occ = 1;

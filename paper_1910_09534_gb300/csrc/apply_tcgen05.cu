@@ -642,12 +642,13 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
     auto kern = k_apply_tcgen05<K, R2, LOWT>;
     // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps the
     // resident CTAs' tensor memory within the SM's 512 columns (initialised once, thread-safe)
+    static std::atomic<uint64_t> smem_done{0};
+    if (!smem_opt_in(kern, L::SMEM, smem_done)) return -1;
     static const LaunchCfg cfg = [&] {
         LaunchCfg c;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return c;
         if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM) != cudaSuccess) return c;
         c.ok = true;
         return c;
     }();

@@ -493,14 +493,13 @@ size_t tcgen05_scratch_bytes(int n1, int n2, int e_bits)
 int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
                             const CtOut &o, cudaStream_t st, uint8_t *own_scratch = nullptr)
 {
+    static std::atomic<uint64_t> smem_done{0};
+    if (!smem_opt_in(k_contract_tcgen05, kCtStages * kCtStage, smem_done)) return -1;
     static const LaunchCfg cfg = [] {
         LaunchCfg c;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return c;
         if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
-        if (cudaFuncSetAttribute(k_contract_tcgen05, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kCtStages * kCtStage) != cudaSuccess)
-            return c;
         c.ok = true;
         return c;
     }();

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -169,6 +170,22 @@ void prof_end(sim_t *h, int slot, cudaStream_t st);
 int prepare_block_map(sim_t *h, int k, const int *targets, const double *matrix, const int *phys_of,
                       int nlocal, int *tpos, float2 *mat, int nq = -1);
 int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int *tpos, float2 *mat);
+// cudaFuncSetAttribute acts on the current device only: a kernel that needs more than 48 KiB of
+// dynamic shared memory is opted in once per device (bit d of `done` records device d < 64;
+// higher device numbers are opted in on every call), so a process driving several GPUs can
+// launch it on each.
+template <typename Kern>
+inline bool smem_opt_in(Kern kern, int bytes, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return true;
+}
+
 // One-time launch configuration of a kernel instantiation (kept in a function-local static).
 struct LaunchCfg {
     int sms = 0;
