@@ -25,6 +25,8 @@
  *    free or reuse it at once.  Output buffers belong to the caller.
  *  - Asynchronous calls are ordered on the handle's CUDA stream; sim_sync()
  *    waits for them.  A handle must not be used by two host threads at once.
+ *  - A call works on its handle's device whatever device is current on the
+ *    calling thread, and leaves the thread's current device as it found it.
  */
 #ifndef SYCSIM_H
 #define SYCSIM_H

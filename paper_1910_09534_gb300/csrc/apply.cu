@@ -697,6 +697,6 @@ extern "C" int sim_apply_fused(sim_t *h, int k, const int *targets, const double
     static thread_local float2 mat[4096];
     int rc = prepare_block(h, k, targets, matrix, tpos, mat);
     if (rc != SIM_OK) return rc;
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     return enqueue_block(h, k, tpos, mat, precision);
 }

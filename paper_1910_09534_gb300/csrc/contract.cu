@@ -612,7 +612,7 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
     if (out->n != s->n || t1->n != n1 + e_bits || t2->n != n2 + e_bits)
         return fail(out, SIM_E_INVAL, "sim_contract: qubit counts (%d, %d, %d) do not fit the split (%d, %d, %d)",
                     out->n, t1->n, t2->n, s->n, n1 + e_bits, n2 + e_bits);
-    SIM_CUDA_TRY(out, cudaSetDevice(out->device));
+    SIM_DEVICE_SCOPE(out, out->device);
 
     // each tensor into the layout that matches out's (contract_layout)
     sim_t *tens[2] = {t1, t2};

@@ -146,6 +146,32 @@ namespace sycsim {
 // Record an error on h (or the thread when h is null) and return `code`.
 int fail(sim_t *h, int code, const char *fmt, ...);
 
+// Makes device `dev` current for the rest of the enclosing scope and gives the calling thread
+// its previous current device back when the scope ends, so no call leaves the caller (another
+// framework, say) on a device it did not choose.
+struct DeviceScope {
+    int prev = -1;  // device to restore, or -1
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) err = cudaSetDevice(dev);
+        if (prev == dev || err != cudaSuccess) prev = -1;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
+
+#define SIM_DEVICE_SCOPE(h, dev)                                                              \
+    ::sycsim::DeviceScope dev_scope_(dev);                                                    \
+    if (dev_scope_.err != cudaSuccess)                                                        \
+    return ::sycsim::fail((h), SIM_E_CUDA, "cudaSetDevice(%d) failed: %s", (int)(dev),         \
+                          cudaGetErrorString(dev_scope_.err))
+
 #define SIM_CUDA_TRY(h, call)                                                           \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \

@@ -288,7 +288,7 @@ extern "C" int sim_permute(sim_t *h, const int *perm)
     // physical permutation: old bit bit_of[q] -> new bit perm[q]
     int phys[kMaxQubits];
     for (int q = 0; q < h->n; q++) phys[h->bit_of[q]] = perm[q];
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     int rc = launch_permute(h, h->d_state, h->n, phys, h->stream);
     if (rc != 0)
         return fail(h, SIM_E_CUDA, "sim_permute: launch failed (%d): %s", rc,

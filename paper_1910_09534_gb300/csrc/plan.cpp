@@ -555,7 +555,7 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
         return fail(h, SIM_E_INVAL, "sim_apply_plan: plan has %d qubits, handle %d", p->n, h->n);
     if (h->store != SIM_STORE_DEVICE)
         return fail(h, SIM_E_UNSUPPORTED, "sim_apply_plan: host-store state: use sim_run_phase");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     static thread_local float2 mat[4096];
     int tpos[kMaxK];
     for (auto &b : p->blocks) {
@@ -579,7 +579,7 @@ int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out)
         return fail(h, SIM_E_UNSUPPORTED, "sim_graph_create: host-store handle (use sim_run_phase)");
     if (h->stream == nullptr)
         return fail(h, SIM_E_UNSUPPORTED, "sim_graph_create: the legacy default stream cannot be captured");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     struct Staged {
         int k;
         int tpos[kMaxK];
@@ -640,7 +640,7 @@ int sim_graph_launch(sim_t *h, const sim_graph_t *g)
     if (g->h != h) return fail(h, SIM_E_INVAL, "sim_graph_launch: the graph belongs to another handle");
     if (!std::equal(g->bit_of.begin(), g->bit_of.end(), h->bit_of))
         return fail(h, SIM_E_INVAL, "sim_graph_launch: the layout changed since the graph was created");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     SIM_CUDA_TRY(h, cudaGraphLaunch(g->exec, h->stream));
     h->launches += (uint64_t)g->n_blocks;
     return SIM_OK;
@@ -649,7 +649,7 @@ int sim_graph_launch(sim_t *h, const sim_graph_t *g)
 int sim_graph_destroy(sim_graph_t *g)
 {
     if (!g) return fail(nullptr, SIM_E_INVAL, "sim_graph_destroy: NULL graph");
-    cudaSetDevice(g->h->device);
+    DeviceScope dev_scope(g->h->device);
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->d_staged) cudaFree(g->d_staged);
@@ -674,7 +674,7 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
         precs.push_back(SIM_TF32X3);
     }
     if (accuracy == SIM_TUNE_ANY) precs.push_back(SIM_TF32);
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     cudaEvent_t e0, e1;
     SIM_CUDA_TRY(h, cudaEventCreate(&e0));
     SIM_CUDA_TRY(h, cudaEventCreate(&e1));

@@ -568,7 +568,7 @@ void srv_release(srv_t *s)
         s->cv_work.notify_all();
         s->worker.join();
     }
-    cudaSetDevice(s->o.device);
+    DeviceScope dev_scope(s->o.device);
     for (auto &B : s->batches) {
         if (B.st) cudaStreamSynchronize(B.st);
         if (B.ev) cudaEventDestroy(B.ev);
@@ -601,7 +601,8 @@ int srv_create(const srv_opts *opts, srv_t **out)
         delete s;
         return srv_fail(nullptr, SIM_E_INVAL, "srv_create: slots <= 32, small_n <= 24, max_pack <= 65536");
     }
-    if (cudaSetDevice(s->o.device) != cudaSuccess) {
+    DeviceScope dev_scope(s->o.device);
+    if (dev_scope.err != cudaSuccess) {
         delete s;
         return srv_fail(nullptr, SIM_E_CUDA, "srv_create: device %d unavailable", s->o.device);
     }
@@ -755,11 +756,11 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
         if (tp) sim_plan_destroy(tp);
     sim_plan_destroy(plan);
     if (rc != SIM_OK) return srv_fail(s, rc, "srv_submit: block preparation failed");
-    int prev_dev = 0;
-    cudaGetDevice(&prev_dev);
-    cudaSetDevice(s->o.device);
-    const cudaError_t ee = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
-    cudaSetDevice(prev_dev);
+    cudaError_t ee;
+    {
+        DeviceScope dev_scope(s->o.device);
+        ee = dev_scope.err != cudaSuccess ? dev_scope.err : cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+    }
     if (ee != cudaSuccess) return srv_fail(s, SIM_E_CUDA, "srv_submit: event");
     {
         std::lock_guard<std::mutex> lk(s->mu);

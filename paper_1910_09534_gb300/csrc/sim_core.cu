@@ -77,7 +77,7 @@ void prof_end(sim_t *h, int slot, cudaStream_t st)
 static void release(sim_t *h)
 {
     if (!h) return;
-    cudaSetDevice(h->device);
+    DeviceScope dev_scope(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto &s : h->prof) {
         cudaEventDestroy(s.a);
@@ -153,7 +153,8 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
         }                                                                                 \
     } while (0)
 
-    CREATE_TRY(cudaSetDevice(h->device), SIM_E_CUDA);
+    DeviceScope dev_scope(h->device);
+    CREATE_TRY(dev_scope.err, SIM_E_CUDA);
     if (o.stream) {
         h->stream = (cudaStream_t)o.stream;
     } else {
@@ -243,7 +244,7 @@ int sim_reset(sim_t *h, uint64_t basis)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reset: NULL handle");
     if (h->n < 64 && (basis >> h->n) != 0)
         return fail(h, SIM_E_INVAL, "sim_reset: basis index has bits above n=%d", h->n);
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (h->store == SIM_STORE_HOST) return host_reset(h, basis);
     SIM_CUDA_TRY(h, cudaMemsetAsync(h->d_state, 0, h->amps * sizeof(float2), h->stream));
     const int ps = prof_begin(h, SIM_PROF_OTHER, 0.0, h->stream);
@@ -269,7 +270,7 @@ static int check_device_error(sim_t *h)
 int sim_sync(sim_t *h, int timeout_ms)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_sync: NULL handle");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (timeout_ms < 0) {
         if (h->st_in) SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
         SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -316,7 +317,7 @@ int sim_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtyp
                     (unsigned long long)first, (unsigned long long)count, h->n);
     if (count == 0) return SIM_OK;
     if (!out) return fail(h, SIM_E_INVAL, "sim_amplitudes: out is NULL");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (h->store == SIM_STORE_HOST) return host_amplitudes(h, first, count, out, dtype, physical_order);
     char *dst = (char *)out;
     if (physical_order || layout_is_identity(h)) {
@@ -356,7 +357,7 @@ int sim_amplitudes_async(sim_t *h, uint64_t first, uint64_t count, void *out, in
     if (!physical_order && !layout_is_identity(h))
         return fail(h, SIM_E_UNSUPPORTED,
                     "sim_amplitudes_async: logical order of a permuted layout (use sim_amplitudes)");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     SIM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_state + first, count * sizeof(float2), cudaMemcpyDeviceToHost,
                                     h->stream));
     return SIM_OK;
@@ -370,7 +371,7 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
         return fail(h, SIM_E_INVAL, "sim_load_amplitudes: range outside the state");
     if (count == 0) return SIM_OK;
     if (!src) return fail(h, SIM_E_INVAL, "sim_load_amplitudes: src is NULL");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (h->store == SIM_STORE_HOST) return host_load(h, first, count, src, physical_order);
     const char *s = (const char *)src;
     if (physical_order || layout_is_identity(h)) {
@@ -399,7 +400,7 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
 int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reduce: NULL handle");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (h->store == SIM_STORE_HOST) {
         double a = 0.0, b = 0.0;
         const int rc = host_reduce(h, &a, &b);
@@ -429,7 +430,7 @@ int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
 int sim_profile_enable(sim_t *h, int on)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_profile_enable: NULL handle");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->prof_on = on != 0;
     h->prof_used = 0;
@@ -439,7 +440,7 @@ int sim_profile_enable(sim_t *h, int on)
 int sim_profile_read(sim_t *h, int cls, uint64_t *launches, double *total_ms, double *alg_bytes)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_profile_read: NULL handle");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     SIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     uint64_t n = 0;
     double ms = 0.0, bytes = 0.0;

@@ -405,7 +405,7 @@ using namespace sycsim;
 extern "C" int sim_state_save(sim_t *h, const char *path)
 {
     if (!h || !path) return fail(h, SIM_E_INVAL, "sim_state_save: NULL argument");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     int rc = sync_state(h);
     if (rc != SIM_OK) return rc;
     StateFileHeader hd{};
@@ -453,7 +453,7 @@ extern "C" int sim_state_save(sim_t *h, const char *path)
 extern "C" int sim_state_load(sim_t *h, const char *path)
 {
     if (!h || !path) return fail(h, SIM_E_INVAL, "sim_state_load: NULL argument");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     int rc = sync_state(h);
     if (rc != SIM_OK) return rc;
     FILE *f = std::fopen(path, "rb");
@@ -531,7 +531,7 @@ int sim_stream_slice(sim_t *h, int set, uint64_t value, int dir, int slot)
         value >= (1ull << h->s))
         return fail(h, SIM_E_INVAL, "sim_stream_slice: set=%d value=%llu dir=%d slot=%d out of range",
                     set, (unsigned long long)value, dir, slot);
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     return enqueue_slice_copy(h, set, value, dir, slot);
 }
 
@@ -552,7 +552,7 @@ int sim_slot_read(sim_t *h, int slot, uint64_t first, uint64_t count, void *out)
     const uint64_t slice = 1ull << (h->n - h->s);
     if (first > slice || count > slice - first)
         return fail(h, SIM_E_INVAL, "sim_slot_read: range outside the slot");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     SIM_CUDA_TRY(h, cudaStreamSynchronize(h->st_in));
     SIM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_slot[slot] + first, sizeof(float2) * count,
                                     cudaMemcpyDeviceToHost, h->stream));
@@ -565,7 +565,7 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_run_phase: NULL handle");
     if (!p || p->n != h->n) return fail(h, SIM_E_INVAL, "sim_run_phase: plan missing or for another n");
     if (set < 0 || set > 1) return fail(h, SIM_E_INVAL, "sim_run_phase: set must be 0 (A) or 1 (B)");
-    SIM_CUDA_TRY(h, cudaSetDevice(h->device));
+    SIM_DEVICE_SCOPE(h, h->device);
     if (h->store != SIM_STORE_HOST) {
         // resident state: the phase's blocks apply to the whole state
         return sim_apply_plan(h, p);
