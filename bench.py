@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--serving-circuits", type=int, default=200)
+    ap.add_argument("--serving-rate", type=float, default=0.0,
+                    help="Poisson arrival rate of the serving leg in circuits/s (0: every circuit at "
+                         "t = 0, saturated)")
     ap.add_argument("--oracle-table", action="store_true",
                     help="time the CPU oracle on one and on all host cores for the 12-, 30- (sample), "
                          "28- (sample) and 24-qubit circuits, print one JSON line, and exit")
@@ -237,24 +240,33 @@ def oracle_table():
     return {"cpu": cpu, "cores": cores, "rows": rows}
 
 
-def serving_run(count: int, device: int):
-    """Serve `count` random circuits (qubits uniform in 16..30, 8..20 cycles) all submitted at
-    once, and run the same circuits one at a time through sim_*; report circuits/s and the
-    served latency distribution."""
+def serving_run(count: int, device: int, rate_hz: float = 0.0):
+    """Serve `count` random circuits (qubits uniform in 16..30, 8..20 cycles), all submitted at
+    once (rate_hz = 0) or each at its Poisson arrival time, and run the same circuits, arriving
+    the same way, one at a time through sim_*; report circuits/s and the latency distributions
+    (completion - arrival)."""
     import paper_1910_09534_gb300 as pkg
     import syc_inputs as si
 
-    stream = si.serving_stream(count, base_seed=1000, rate_hz=1e9)
+    stream = si.serving_stream(count, base_seed=1000, rate_hz=rate_hz if rate_hz > 0 else 1e9)
+    arrivals = [a if rate_hz > 0 else 0.0 for a, _ in stream]
     circs = [c for _, c in stream]
     gates = [pkg.gates_array(c) for c in circs]
+
+    def until(t0, at):  # sleep until `at` seconds after t0
+        dt = at - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+
     import torch
     torch.cuda.synchronize()
     handles = {}
     for n in sorted({c.n_qubits for c in circs}):  # states allocated before the clock starts
         handles[n] = pkg.sim_create(n, 0, device=device)
-    seq_done = []  # completion times from t0: every circuit arrived at t0
+    seq_done = []  # completion - arrival
     t0 = time.perf_counter()
-    for c, g in zip(circs, gates):
+    for at, c, g in zip(arrivals, circs, gates):
+        until(t0, at)
         # the server's policy above its packing size: blocks of <= 6 qubits in a chosen layout
         h = handles[c.n_qubits]
         big = c.n_qubits > 20
@@ -265,19 +277,24 @@ def serving_run(count: int, device: int):
         pkg.sim_apply_plan(h, p)
         pkg.sim_reduce(h)
         pkg.sim_plan_destroy(p)
-        seq_done.append((time.perf_counter() - t0) * 1e3)
+        seq_done.append((time.perf_counter() - t0 - at) * 1e3)
     seq_s = time.perf_counter() - t0
     for h in handles.values():
         pkg.sim_destroy(h)
     srv = pkg.srv_create(device=device, precision=pkg.SIM_FP16X3_TMEM)
     t0 = time.perf_counter()
-    tickets = [pkg.srv_submit(srv, c.n_qubits, g) for c, g in zip(circs, gates)]
+    tickets = []
+    for at, c, g in zip(arrivals, circs, gates):
+        until(t0, at)
+        tickets.append(pkg.srv_submit(srv, c.n_qubits, g))
     for t in tickets:
         pkg.srv_wait(srv, t)
     served_s = time.perf_counter() - t0
     st = pkg.srv_stats(srv)
     pkg.srv_destroy(srv)
-    return {"circuits": count, "qubits": "16..30", "cycles": "8..20", "arrivals": "all at t=0 (saturated)",
+    arr = ("all at t=0 (saturated)" if rate_hz <= 0 else
+           f"Poisson at {rate_hz:g} circuits/s (last arrival at {arrivals[-1]:.2f} s)")
+    return {"circuits": count, "qubits": "16..30", "cycles": "8..20", "arrivals": arr,
             "circuits_per_s": count / served_s, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "one_at_a_time_circuits_per_s": count / seq_s,
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
@@ -675,7 +692,7 @@ def run_ours(args):
     if fp32_path:
         line["fp32_path"] = fp32_path
     if ws == 1 and not args.no_serving:
-        line["serving"] = serving_run(args.serving_circuits, local)
+        line["serving"] = serving_run(args.serving_circuits, local, args.serving_rate)
     if ws == 1 and not args.no_graphs:
         line["graph_replay"] = graph_replay_run(local)
     if ws == 1 and not args.no_cpu_baseline:
