@@ -331,12 +331,16 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
         if (enqueue_contraction(h, r->split.get(), r->d_t[0], r->d_t[1], r->d_state, r->out_bit_of.data(),
                                 r->precision, r->d_scratch, st) != 0)
             return SIM_E_CUDA;
+        // each pointer is dropped before its status is checked: after a failed free, the abort
+        // path must not free it again
+        bool freed = true;
         for (auto &p : r->d_t) {
-            if (cudaFreeAsync(p, st) != cudaSuccess) return SIM_E_CUDA;
+            freed &= cudaFreeAsync(p, st) == cudaSuccess;
             p = nullptr;
         }
-        if (cudaFreeAsync(r->d_scratch, st) != cudaSuccess) return SIM_E_CUDA;
+        freed &= cudaFreeAsync(r->d_scratch, st) == cudaSuccess;
         r->d_scratch = nullptr;
+        if (!freed) return SIM_E_CUDA;
         r->contracted = true;
         *progressed = true;
         return SIM_OK;
@@ -368,8 +372,9 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
     if (r->out_amps &&
         cudaMemcpyAsync(r->out_amps, r->d_state, sizeof(float2) * amps, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return SIM_E_CUDA;
-    if (cudaFreeAsync(r->d_state, st) != cudaSuccess) return SIM_E_CUDA;
-    r->d_state = nullptr;
+    const cudaError_t fe = cudaFreeAsync(r->d_state, st);
+    r->d_state = nullptr;  // not freed twice by the abort path
+    if (fe != cudaSuccess) return SIM_E_CUDA;
     if (cudaEventRecord(r->ev, st) != cudaSuccess) return SIM_E_CUDA;
     r->launched = true;
     *progressed = true;
@@ -415,7 +420,18 @@ int launch_packed(srv_t *s, Batch &B)
         if (cudaHostAlloc(&B.h_stage, table_bytes * 2, cudaHostAllocDefault) != cudaSuccess) return SIM_E_NOMEM_HOST;
         B.stage_bytes = table_bytes * 2;
     }
-    if (cudaMallocAsync(&B.d_mem, total, B.st) != cudaSuccess) return SIM_E_NOMEM_DEV;
+    if (cudaMallocAsync(&B.d_mem, total, B.st) != cudaSuccess) {
+        B.d_mem = nullptr;
+        return SIM_E_NOMEM_DEV;
+    }
+    struct ReleaseOnError {  // an early return below gives the allocation back (stream-ordered)
+        Batch &b;
+        ~ReleaseOnError()
+        {
+            if (b.d_mem) cudaFreeAsync(b.d_mem, b.st);
+            b.d_mem = nullptr;
+        }
+    } release_on_error{B};
     char *d = (char *)B.d_mem;
     PackedJob *hj = (PackedJob *)(B.h_stage + off_jobs);
     PackedBlock *hb = (PackedBlock *)(B.h_stage + off_blk);
@@ -453,7 +469,9 @@ int launch_packed(srv_t *s, Batch &B)
             return SIM_E_CUDA;
         si += 1ull << r->n;
     }
-    if (cudaFreeAsync(B.d_mem, B.st) != cudaSuccess) return SIM_E_CUDA;
+    const cudaError_t fe = cudaFreeAsync(B.d_mem, B.st);  // released once the batch's work is done
+    B.d_mem = nullptr;
+    if (fe != cudaSuccess) return SIM_E_CUDA;
     if (cudaEventRecord(B.ev, B.st) != cudaSuccess) return SIM_E_CUDA;
     B.busy = true;
     return SIM_OK;
