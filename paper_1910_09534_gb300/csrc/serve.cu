@@ -417,7 +417,11 @@ int launch_packed(srv_t *s, Batch &B)
     if (B.stage_bytes < table_bytes) {
         if (B.h_stage) cudaFreeHost(B.h_stage);
         B.h_stage = nullptr;
-        if (cudaHostAlloc(&B.h_stage, table_bytes * 2, cudaHostAllocDefault) != cudaSuccess) return SIM_E_NOMEM_HOST;
+        B.stage_bytes = 0;  // a failed allocation leaves no buffer behind
+        if (cudaHostAlloc(&B.h_stage, table_bytes * 2, cudaHostAllocDefault) != cudaSuccess) {
+            B.h_stage = nullptr;
+            return SIM_E_NOMEM_HOST;
+        }
         B.stage_bytes = table_bytes * 2;
     }
     if (cudaMallocAsync(&B.d_mem, total, B.st) != cudaSuccess) {
