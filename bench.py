@@ -49,6 +49,16 @@ METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 
 
+# Configurations beyond one resident 30-qubit state (Sect. 4: sliced qubits, phases, a secondary
+# store): store kind, sliced bits, block width, store regions kept in HBM, and how the two
+# sliced sets are picked (the lattice ends, or sim_phases_choose_sets).
+LARGE_CASES = {
+    "syc33_6x6m3_d20": dict(store="device", slice_bits=3, kmax=6, device_regions=0, sets="ends"),
+    "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=5, device_regions=0, sets="chosen"),
+    "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=5, device_regions=8, sets="chosen"),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -84,6 +94,10 @@ def parse():
     ap.add_argument("--oracle-table", action="store_true",
                     help="time the CPU oracle on one and on all host cores for the 12-, 30- (sample), "
                          "28- (sample) and 24-qubit circuits, print one JSON line, and exit")
+    ap.add_argument("--large-case", default=None, choices=sorted(LARGE_CASES),
+                    help="run one configuration beyond the bench's 30 qubits instead (33 qubits resident "
+                         "in 8 slices with sliced phases; 34 and 35 qubits streamed through a host store, "
+                         "35 with half its regions in HBM), print one JSON line, and exit")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
                          "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
@@ -754,9 +768,71 @@ def kernel_case():
     print("kernel case done", flush=True)
 
 
+def large_case(name: str):
+    """One run of a configuration from LARGE_CASES in SIM_FP16X3_TMEM (the resident one after a
+    warm-up run; a streamed run takes seconds and runs once): wall time, gate updates/s, the apply
+    kernels' time and bandwidth, the permutation passes (resident) or the host link's combined
+    rate (streamed), and the final state's norm and 2^n sum p^2."""
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+    from paper_1910_09534_gb300 import build as pkg_build
+
+    pkg_build.build()
+    cfg = LARGE_CASES[name]
+    circ = si.workload_circuit(name, seed=0)
+    n, s, kmax = circ.n_qubits, cfg["slice_bits"], cfg["kmax"]
+    gates = pkg.gates_array(circ)
+    prec = pkg.SIM_FP16X3_TMEM
+    if cfg["sets"] == "chosen":
+        set_a, set_b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=kmax)
+    else:
+        set_a, set_b = list(range(s)), list(range(n - s, n))
+    ph = pkg.sim_phases_create(n, gates, s, set_a, set_b, kmax=kmax, precision=prec)
+    n_phases, n_blocks = pkg.sim_phases_info(ph)
+    host = cfg["store"] == "host"
+    if host:
+        h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3,
+                           store_device_regions=cfg["device_regions"])
+    else:
+        h = pkg.sim_create(n, s)
+        pkg.sim_reset(h)
+        pkg.sim_run_phases(h, ph)  # warm-up
+        pkg.sim_sync(h)
+    pkg.sim_reset(h)
+    pkg.sim_sync(h)
+    pkg.sim_profile_enable(h, True)
+    t0 = time.perf_counter()
+    pkg.sim_run_phases(h, ph)
+    pkg.sim_sync(h)
+    wall = time.perf_counter() - t0
+    a_n, a_ms, a_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
+    p_n, p_ms, p_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_PERMUTE)
+    pkg.sim_profile_enable(h, False)
+    norm, s2, _ = pkg.sim_reduce(h)
+    pkg.sim_destroy(h)
+    pkg.sim_phases_destroy(ph)
+    state_bytes = 8.0 * (1 << n)
+    line = {"case": name, "n_qubits": n, "gates": circ.n_gates,
+            "store": ("host" if host else "device") + (f", {cfg['device_regions']} of {1 << s} regions in HBM"
+                                                       if cfg["device_regions"] else ""),
+            "slice_bits": s, "set_a": set_a, "set_b": set_b, "sets": cfg["sets"], "kmax": kmax,
+            "precision": "fp16x3_tmem", "phases": n_phases, "blocks": n_blocks, "wall_s": wall,
+            "gate_updates_per_s": float(1 << n) * circ.n_gates / wall,
+            "apply": {"launches": a_n, "ms": a_ms, "gbs": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None},
+            "norm": norm, "porter_thomas_2n_sum_p2": s2}
+    if host:  # every phase moves the host regions out and back
+        moved = 2 * n_phases * state_bytes * (1 - cfg["device_regions"] / (1 << s))
+        line["host_link_gbs_combined"] = moved / wall / 1e9
+    else:
+        line["permute"] = {"passes": p_n, "ms": p_ms, "gbs_moved": p_bytes / (p_ms / 1e3) / 1e9 if p_ms else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.kernel_case:
+    if args.large_case:
+        large_case(args.large_case)
+    elif args.kernel_case:
         kernel_case()
     elif args.oracle_table:
         print(json.dumps(oracle_table()), flush=True)

@@ -73,3 +73,29 @@ def test_reference_arm_other_ranks_print_nothing(capsys, monkeypatch):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(types.SimpleNamespace(workload="syc12_3x4_d8", cpu_sample_gates=42, warmup=1, steps=1))
     assert capsys.readouterr().out == ""
+
+
+def test_large_cases_plan_on_the_host(monkeypatch):
+    """Each --large-case configuration parses, and its workload, sliced sets and phases plan on
+    the host (the GPU run itself is not part of this test)."""
+    import sys
+
+    import bench
+    import paper_1910_09534_gb300 as pkg
+    import syc_inputs as si
+    for name, cfg in bench.LARGE_CASES.items():
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--large-case", name])
+        assert bench.parse().large_case == name
+        circ = si.workload_circuit(name, seed=0)
+        n, s = circ.n_qubits, cfg["slice_bits"]
+        gates = pkg.gates_array(circ)
+        if cfg["sets"] == "chosen":
+            set_a, set_b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=cfg["kmax"])
+        else:
+            set_a, set_b = list(range(s)), list(range(n - s, n))
+        assert len(set_a) == len(set_b) == s and not set(set_a) & set(set_b)
+        assert 0 <= cfg["device_regions"] < (1 << s)
+        ph = pkg.sim_phases_create(n, gates, s, set_a, set_b, kmax=cfg["kmax"], precision=pkg.SIM_FP16X3_TMEM)
+        n_phases, n_blocks = pkg.sim_phases_info(ph)
+        pkg.sim_phases_destroy(ph)
+        assert n_phases == 4 and n_blocks > 0
