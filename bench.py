@@ -45,6 +45,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "syc30_5x6_d20"
+NOMINAL_DENSE_F16_TFLOPS = 2250.0  # GB300 dense FP16/BF16 tensor rate, datasheet (no sparsity)
 METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 
@@ -195,14 +196,32 @@ def measured_peaks(key: str = "hbm_gbs"):
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}[key], "fallback"
 
 
-def cpu_baseline(circ, sample_gates: int, steps: int = 1):
-    """Time the oracle (complex128, gate by gate, all host cores) on the first `sample_gates`
-    gates of the circuit applied to the full state."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or "unknown"."""
+    try:
+        return next((ln.split(":", 1)[1].strip() for ln in subprocess.run(
+            ["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines()
+            if ln.startswith("Model name")), "unknown")
+    except Exception:
+        return "unknown"
+
+
+def cpu_baseline(circ, sample_gates: int, steps: int = 1, single_thread_gates: int = 4):
+    """Time the oracle (complex128, gate by gate) on the first `sample_gates` gates of the circuit
+    applied to the full state on all host cores, and on the first `single_thread_gates` gates on
+    one thread."""
     import oracle
     import syc_inputs as si
 
     oracle.build()
     cores = os.cpu_count() or 1
+    amps = float(1 << circ.n_qubits)
+    psi = oracle.basis_state(circ.n_qubits, 0)
+    oracle.set_threads(1)
+    one = si.Circuit(circ.n_qubits, circ.gates[:single_thread_gates], name=circ.name)
+    t0 = time.perf_counter()
+    oracle.apply_gates(psi, one)
+    t_one = time.perf_counter() - t0
     oracle.set_threads(cores)
     sample = si.Circuit(circ.n_qubits, circ.gates[:sample_gates], name=circ.name)
     psi = oracle.basis_state(circ.n_qubits, 0)
@@ -212,12 +231,14 @@ def cpu_baseline(circ, sample_gates: int, steps: int = 1):
         oracle.apply_gates(psi, sample)
         times.append(time.perf_counter() - t0)
     del psi
-    amps = float(1 << circ.n_qubits)
     return {"value": amps * sample_gates * steps / sum(times), "unit": UNIT,
-            "cores": oracle.max_threads(), "kind": "oracle",
+            "cores": oracle.max_threads(), "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"first {sample_gates} of {circ.n_gates} gates of {circ.name} on the full "
                       f"2^{circ.n_qubits} complex128 state, {steps} run(s)",
-            "seconds": sum(times)}
+            "seconds": sum(times),
+            "single_thread": {"value": amps * single_thread_gates / t_one, "unit": UNIT, "cores": 1,
+                              "sample": f"first {single_thread_gates} gates, same state",
+                              "seconds": t_one}}
 
 
 def oracle_table():
@@ -229,12 +250,7 @@ def oracle_table():
 
     oracle.build()
     cores = os.cpu_count() or 1
-    try:
-        cpu = next((ln.split(":", 1)[1].strip() for ln in subprocess.run(
-            ["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines()
-            if ln.startswith("Model name")), "unknown")
-    except Exception:
-        cpu = "unknown"
+    cpu = cpu_model()
     cases = [("12 qubits, 3x4 grid, 8 cycles (whole circuit)", si.workload_circuit("syc12_3x4_d8", 0), None),
              ("30 qubits, 5x6 grid, 20 cycles (first 12 gates)", si.workload_circuit("syc30_5x6_d20", 0), 12),
              ("28 qubits, 4x7 grid, 20 cycles (first 24 gates)", si.workload_circuit("syc28_4x7_d20", 0), 24),
@@ -382,7 +398,7 @@ def run_reference(args):
             "config": {"workload": args.workload, "n_qubits": circ.n_qubits,
                        "sample": f"each step applies the first {g} gates of the circuit"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu_model": cpu_model(),
                              "sample": f"first {g} of {circ.n_gates} gates per step, full state"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -694,12 +710,24 @@ def run_ours(args):
         # the contraction's tensor roofline: algorithmic complex-GEMM FLOPs (8 per complex
         # multiply-add) per launch / its CUDA-event time; 3xFP16 issues 3 FP16 MMA FLOPs per
         # algorithmic FLOP, so the tensor pipe runs at 3 x achieved
+        # The measured cuBLAS bf16 burst is below what this kernel's tensor pipe sustains (3 x
+        # achieved exceeded it), so it is no ceiling here: the fraction is taken against the
+        # larger of it and the dense FP16/BF16 datasheet figure, and a pipe fraction above 1
+        # against the measured figure is flagged as a problem of that measurement.
+        peak_c = max(bf16, NOMINAL_DENSE_F16_TFLOPS)
+        pipe_meas = 3 * ach_c / bf16 if ach_c else None
         line["contract_roofline"] = {
             "bound": "tensor", "kernel": "k_contract_tcgen05" if "tcgen05" in front_info["contraction"]
-            else "k_contract_fp32", "achieved": ach_c, "peak": bf16, "unit": "TFLOP/s",
-            "frac": ach_c / bf16 if ach_c else None, "mma_flops_per_alg_flop": 3,
-            "tensor_pipe_frac": 3 * ach_c / bf16 if ach_c else None,
-            "peak_source": f"{bf16_kind} bf16_tflops (FP16 runs at the BF16 rate)",
+            else "k_contract_fp32", "achieved": ach_c, "peak": peak_c, "unit": "TFLOP/s",
+            "frac": ach_c / peak_c if ach_c else None, "mma_flops_per_alg_flop": 3,
+            "tensor_pipe_frac": 3 * ach_c / peak_c if ach_c else None,
+            "tensor_pipe_frac_of_measured_bf16": pipe_meas,
+            "measured_bf16_tflops": bf16,
+            "peak_source": (f"max of {bf16_kind} bf16_tflops {bf16:.1f} and the dense FP16/BF16 datasheet "
+                            f"figure {NOMINAL_DENSE_F16_TFLOPS:.0f} (FP16 runs at the BF16 rate)"),
+            "note": ("tensor pipe above the measured cuBLAS bf16 burst: that measurement is below the "
+                     "pipe's real ceiling" if pipe_meas and pipe_meas > 1 else None),
+            "sm_mhz_median": (clk.summary() or {}).get("sm_mhz"),
             "launches": c_n, "avg_launch_ms": c_ms / max(c_n, 1),
             "alg_flops_per_launch": c_flops / max(c_n, 1)}
         line["plain_path"] = plain_path
@@ -768,11 +796,12 @@ def kernel_case():
     print("kernel case done", flush=True)
 
 
-def large_case(name: str):
-    """One run of a configuration from LARGE_CASES in SIM_FP16X3_TMEM (the resident one after a
-    warm-up run; a streamed run takes seconds and runs once): wall time, gate updates/s, the apply
-    kernels' time and bandwidth, the permutation passes (resident) or the host link's combined
-    rate (streamed), and the final state's norm and 2^n sum p^2."""
+def large_case(name: str, precision: str = "fp16x3_tmem"):
+    """One run of a configuration from LARGE_CASES in SIM_FP16X3_TMEM at the case's block width, or
+    in SIM_FP32 at k_max 4 (the resident one after a warm-up run; a streamed run takes seconds and
+    runs once): wall time, gate updates/s, the apply kernels' time and bandwidth with their HBM
+    roofline, the permutation passes (resident) or the host link's combined rate (streamed), and
+    the final state's norm and 2^n sum p^2."""
     import paper_1910_09534_gb300 as pkg
     import syc_inputs as si
     from paper_1910_09534_gb300 import build as pkg_build
@@ -783,6 +812,8 @@ def large_case(name: str):
     n, s, kmax = circ.n_qubits, cfg["slice_bits"], cfg["kmax"]
     gates = pkg.gates_array(circ)
     prec = pkg.SIM_FP16X3_TMEM
+    if precision == "fp32":
+        prec, kmax = pkg.SIM_FP32, 4
     if cfg["sets"] == "chosen":
         set_a, set_b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=kmax)
     else:
@@ -812,13 +843,18 @@ def large_case(name: str):
     pkg.sim_destroy(h)
     pkg.sim_phases_destroy(ph)
     state_bytes = 8.0 * (1 << n)
+    peak, peak_kind = measured_peaks()
     line = {"case": name, "n_qubits": n, "gates": circ.n_gates,
             "store": ("host" if host else "device") + (f", {cfg['device_regions']} of {1 << s} regions in HBM"
                                                        if cfg["device_regions"] else ""),
             "slice_bits": s, "set_a": set_a, "set_b": set_b, "sets": cfg["sets"], "kmax": kmax,
-            "precision": "fp16x3_tmem", "phases": n_phases, "blocks": n_blocks, "wall_s": wall,
+            "precision": precision, "phases": n_phases, "blocks": n_blocks, "wall_s": wall,
             "gate_updates_per_s": float(1 << n) * circ.n_gates / wall,
-            "apply": {"launches": a_n, "ms": a_ms, "gbs": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None},
+            "apply": {"launches": a_n, "ms": a_ms, "gbs": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None,
+                      "roofline": {"bound": "hbm", "achieved": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None,
+                                   "peak": peak, "unit": "GB/s",
+                                   "frac": a_bytes / (a_ms / 1e3) / 1e9 / peak if a_ms else None,
+                                   "peak_source": f"{peak_kind} hbm_gbs"}},
             "norm": norm, "porter_thomas_2n_sum_p2": s2}
     if host:  # every phase moves the host regions out and back
         moved = 2 * n_phases * state_bytes * (1 - cfg["device_regions"] / (1 << s))
@@ -831,7 +867,7 @@ def large_case(name: str):
 def main():
     args = parse()
     if args.large_case:
-        large_case(args.large_case)
+        large_case(args.large_case, "fp32" if args.precision == "fp32" else "fp16x3_tmem")
     elif args.kernel_case:
         kernel_case()
     elif args.oracle_table:

@@ -187,14 +187,17 @@ int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb);
  * d_out[0] = sum p, d_out[1] = n_amps * sum p^2, d_out[2] = d_out[1] - 1, with
  * d_out a caller-owned device array of 3 doubles; asynchronous on `stream`
  * (cudaStream_t, NULL = legacy default stream) on the current device.
- * d_state: 16-byte aligned, n_amps even, 2 <= n_amps <= 2^40 (SIM_E_INVAL
- * otherwise).  It calls no allocator: its scratch is one fixed 9.5 KiB array
- * (1216 doubles, one pair per CTA) in the library's device memory, which every
- * GPU that loads the library holds until the process exits.  The first call on
- * a device looks up that array's device address (make that first call outside
- * any stream capture).  All calls share the array and fully overwrite what they
- * use, so nothing needs clearing; calls that overlap on the GPU (other streams,
- * other threads) race on it and must be serialised by the caller. */
+ * d_state: 16-byte aligned, n_amps even, 2 <= n_amps <= 2^40; d_out: 8-byte
+ * aligned (SIM_E_INVAL otherwise, before anything is launched).  It calls no
+ * allocator: its scratch is one fixed 9.5 KiB array (1216 doubles, one pair per
+ * CTA) in the library's device memory, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address and caches it for the process (make that first call
+ * outside any stream capture); a cudaDeviceReset of that device invalidates the
+ * cached address, so the call must not be used on a device after it has been
+ * reset.  All calls share the array and fully overwrite what they use, so
+ * nothing needs clearing; calls that overlap on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller. */
 int sim_reduce_noalloc(const void *d_state, uint64_t n_amps, double *d_out, void *stream);
 
 /* Wait for all work queued on the handle's stream, at most timeout_ms

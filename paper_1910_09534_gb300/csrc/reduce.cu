@@ -170,6 +170,8 @@ extern "C" int sim_reduce_noalloc(const void *d_state, uint64_t n_amps, double *
     if (!d_state || !d_out) return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: NULL buffer");
     if (((uintptr_t)d_state & 15) != 0)
         return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: state must be 16-byte aligned");
+    if (((uintptr_t)d_out & 7) != 0)
+        return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: d_out must be 8-byte aligned");
     if (n_amps < 2 || (n_amps & 1))
         return fail(nullptr, SIM_E_INVAL, "sim_reduce_noalloc: n_amps=%llu must be even and >= 2",
                     (unsigned long long)n_amps);

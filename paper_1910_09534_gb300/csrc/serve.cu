@@ -567,6 +567,10 @@ void scheduler(srv_t *s)
                     pack_pending.erase(pack_pending.begin(), pack_pending.begin() + take);
                     const int rc = launch_packed(s, B);
                     if (rc != SIM_OK) {
+                        // copies into the jobs' out_amps (and from the pinned staging buffer) may
+                        // already be queued on the batch stream: let them drain before any waiter
+                        // is told its request failed and reuses its buffer
+                        cudaStreamSynchronize(B.st);
                         for (auto &r : B.jobs) finish(s, r, rc, 0.0, 0.0);
                         B.jobs.clear();
                         B.busy = false;

@@ -595,6 +595,10 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
     // uploaded once for the phase, not once per block and slice -- such small copies would queue
     // behind the slice transfers on the copy engines and hold back every kernel.
     char *d_staged = nullptr;
+    auto release = [&](int rc) {  // the staged operands go once the phase's last kernel is queued
+        if (d_staged) cudaFreeAsync(d_staged, h->stream);
+        return rc;
+    };
     if (staged_total) {
         // pinned source, reused once its previous upload is done (no wait on the device's work)
         SIM_CUDA_TRY(h, cudaEventSynchronize(h->ev_ops));
@@ -610,14 +614,15 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         }
         for (const Prepared &pb : blocks)
             if (pb.bytes) block_build_staged(nl, pb.k, pb.tpos, pb.mat.data(), p->precision, h->h_ops + pb.off);
-        SIM_CUDA_TRY(h, cudaMallocAsync(reinterpret_cast<void **>(&d_staged), staged_total, h->stream));
-        SIM_CUDA_TRY(h, cudaMemcpyAsync(d_staged, h->h_ops, staged_total, cudaMemcpyHostToDevice, h->stream));
-        SIM_CUDA_TRY(h, cudaEventRecord(h->ev_ops, h->stream));
+        if (cudaMallocAsync(reinterpret_cast<void **>(&d_staged), staged_total, h->stream) != cudaSuccess) {
+            d_staged = nullptr;
+            return fail(h, SIM_E_NOMEM_DEV, "sim_run_phase: staged operands");
+        }
+        cudaError_t e = cudaMemcpyAsync(d_staged, h->h_ops, staged_total, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_ops, h->stream);
+        if (e != cudaSuccess)  // give the staging allocation back (stream-ordered) before failing
+            return release(fail(h, SIM_E_CUDA, "sim_run_phase: operand upload: %s", cudaGetErrorString(e)));
     }
-    auto release = [&](int rc) {  // the staged operands go once the phase's last kernel is queued
-        if (d_staged) cudaFreeAsync(d_staged, h->stream);
-        return rc;
-    };
     auto apply_blocks = [&](float2 *psi) {
         for (const Prepared &pb : blocks) {
             const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nl), h->stream);

@@ -1,4 +1,5 @@
-"""The allocation-free reduction entry point, checked through the C ABI against sim_reduce.
+"""The allocation-free reduction entry point, checked through the C ABI against the oracle's
+reduction and against sim_reduce.
 
 sim_reduce_noalloc is for callers that cannot allocate device memory themselves (their device
 memory belongs to another framework's pool, or they must avoid cudaMalloc's implicit device
@@ -9,6 +10,7 @@ also passes when run alone in a fresh process (the first call then does the per-
 import numpy as np
 import pytest
 
+import oracle
 import syc_inputs as si
 
 pytestmark = pytest.mark.gpu
@@ -37,10 +39,15 @@ def test_reduce_noalloc_matches_sim_reduce(pkg):
             pkg.sim_load_amplitudes(h, psi)
             norm, s2, xeb = pkg.sim_reduce(h)
             dptr, stream = pkg.sim_state_ptr(h)
+            # the oracle's FP64 reduction of the complex64 amplitudes the device holds
+            onorm, os2, oxeb = oracle.reduce(psi.astype(np.complex128))
             for _ in range(2):  # two calls in a row share (and reuse) the scratch array
                 pkg.sim_reduce_noalloc(dptr, 1 << n, out.data_ptr(), stream)
                 pkg.sim_sync(h)
                 got = out.cpu().numpy()
+                assert abs(got[0] - onorm) <= REL_NORM * onorm
+                assert abs(got[1] - os2) <= REL_S2 * os2
+                assert abs(got[2] - oxeb) <= REL_S2 * os2
                 assert abs(got[0] - norm) <= REL_NORM * norm
                 assert abs(got[1] - s2) <= REL_S2 * s2
                 assert abs(got[2] - xeb) <= REL_S2 * s2
@@ -55,4 +62,9 @@ def test_reduce_noalloc_rejects_bad_sizes(pkg):
     for n_amps in (0, 3, (1 << 40) + 2):
         with pytest.raises(pkg.SimError) as e:
             pkg.sim_reduce_noalloc(buf.data_ptr(), n_amps, out.data_ptr())
+        assert e.value.code == pkg.SIM_E_INVAL
+    # misaligned buffers are refused on the host before any launch
+    for d_state, d_out in ((buf.data_ptr() + 8, out.data_ptr()), (buf.data_ptr(), out.data_ptr() + 4)):
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_reduce_noalloc(d_state, 8, d_out)
         assert e.value.code == pkg.SIM_E_INVAL
