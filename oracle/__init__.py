@@ -54,7 +54,7 @@ def lib():
         L.orc_apply_kq.argtypes = [P, i32, i32, P, P]
         L.orc_apply_kq.restype = i32
         L.orc_basis_state.argtypes = [P, i32, u64]
-        L.orc_apply_gates.argtypes = [P, i32, i32, P, P, P, P, P]
+        L.orc_apply_gates.argtypes = [P, i32, i32, P, P, P, P, P, P, P, P]
         L.orc_apply_gates.restype = i32
         L.orc_permute.argtypes = [P, P, i32, P, i32]
         L.orc_permute.restype = i32
@@ -124,18 +124,19 @@ def basis_state(n: int, basis: int = 0) -> np.ndarray:
 
 
 def apply_gates(psi: np.ndarray, circuit) -> None:
-    """Apply a syc_inputs.Circuit gate by gate, in place."""
+    """Apply a syc_inputs.Circuit (or a sequence of gate tuples, fSim detunings D+, D-, D-,off
+    as elements 5..7 where present) gate by gate, in place."""
     assert psi.dtype == np.complex128 and psi.flags.c_contiguous
-    kind, q0, q1, theta, phi = circuit.arrays()
-    rc = lib().orc_apply_gates(_ptr(psi), _nq(psi), int(kind.size), _ptr(kind), _ptr(q0),
-                               _ptr(q1), _ptr(theta), _ptr(phi))
+    cols = [np.ascontiguousarray(c) for c in _gate_columns(circuit)]
+    kind = cols[0]
+    rc = lib().orc_apply_gates(_ptr(psi), _nq(psi), int(kind.size), *[_ptr(c) for c in cols])
     if rc != 0:
         raise ValueError(f"bad gate at index {-rc - 1}")
 
 
-def run_circuit(circuit, basis: int = 0) -> np.ndarray:
-    """psi = U_G ... U_1 |basis>, complex128."""
-    psi = basis_state(circuit.n_qubits, basis)
+def run_circuit(circuit, basis: int = 0, n_qubits: int | None = None) -> np.ndarray:
+    """psi = U_G ... U_1 |basis>, complex128 (n_qubits: needed for a plain gate sequence)."""
+    psi = basis_state(circuit.n_qubits if n_qubits is None else n_qubits, basis)
     apply_gates(psi, circuit)
     return psi
 
@@ -181,12 +182,8 @@ def reduce(psi: np.ndarray):
 
 def _gate_columns(gates):
     """(kind, q0, q1, theta, phi, dplus, dminus, dminus_off) columns from a syc_inputs
-    Circuit (no detuning) or from a sequence of 8-tuples."""
-    if hasattr(gates, "arrays"):
-        kind, q0, q1, theta, phi = gates.arrays()
-        z = np.zeros(kind.size, dtype=np.float64)
-        return kind, q0, q1, theta, phi, z, z.copy(), z.copy()
-    g = list(gates)
+    Circuit or from a sequence of 5- or 8-tuples (missing detunings are 0)."""
+    g = list(gates.gates if hasattr(gates, "gates") else gates)
     cols = [np.array([x[i] for x in g], dtype=np.int32) for i in range(3)]
     cols += [np.array([x[i] if len(x) > i else 0.0 for x in g], dtype=np.float64) for i in range(3, 8)]
     return tuple(cols)

@@ -171,13 +171,18 @@ void orc_basis_state(cplx *psi, int n, uint64_t basis)
 }
 
 /* Apply a gate list in order to psi (Sect. 3 circuits; q1 ignored for the
- * single-qubit kinds).  Returns 0, or -(1 + index) of the first bad gate. */
+ * single-qubit kinds).  dp, dm, dmoff: per-gate fSim detunings D+, D-, D-,off
+ * of Eq. 1 (Sect. 3: the two-qubit unitaries vary with location and depth);
+ * NULL means 0 for every gate.  Returns 0, or -(1 + index) of the first bad
+ * gate. */
 int orc_apply_gates(cplx *psi, int n, int ngates, const int *kind, const int *q0,
-                    const int *q1, const double *theta, const double *phi)
+                    const int *q1, const double *theta, const double *phi,
+                    const double *dp, const double *dm, const double *dmoff)
 {
     cplx u[16];
     for (int g = 0; g < ngates; g++) {
-        int d = orc_gate_matrix(kind[g], theta[g], phi[g], 0.0, 0.0, 0.0, u);
+        int d = orc_gate_matrix(kind[g], theta[g], phi[g], dp ? dp[g] : 0.0, dm ? dm[g] : 0.0,
+                                dmoff ? dmoff[g] : 0.0, u);
         if (d == 2) {
             if (q0[g] < 0 || q0[g] >= n) return -(1 + g);
             orc_apply_1q(psi, n, q0[g], u);

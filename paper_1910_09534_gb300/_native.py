@@ -348,12 +348,15 @@ def pinned_array(count: int, dtype=np.complex64):
 
 
 def gates_array(circuit) -> np.ndarray:
-    """struct sim_gate records of a syc_inputs.Circuit (or of (kind,q0,q1,theta,phi) tuples)."""
+    """struct sim_gate records of a syc_inputs.Circuit (or of (kind, q0, q1, theta, phi) tuples,
+    optionally followed by the fSim detunings dplus, dminus, dminus_off)."""
     gates = circuit.gates if hasattr(circuit, "gates") else circuit
     a = np.zeros(len(gates), dtype=GATE_DTYPE)
-    for i, (kind, q0, q1, th, ph) in enumerate(gates):
-        a[i]["kind"], a[i]["q0"], a[i]["q1"] = kind, q0, q1
-        a[i]["theta"], a[i]["phi"] = th, ph
+    for i, g in enumerate(gates):
+        a[i]["kind"], a[i]["q0"], a[i]["q1"] = g[0], g[1], g[2]
+        a[i]["theta"], a[i]["phi"] = g[3], g[4]
+        if len(g) > 5:
+            a[i]["dplus"], a[i]["dminus"], a[i]["dminus_off"] = g[5], g[6], g[7]
     return a
 
 

@@ -28,6 +28,15 @@ Readings taken where the paper is silent (its lattice figures are missing):
   uniform over the two gates that differ from the previous gate on that qubit;
 * pseudo-random numbers: SplitMix64 (Steele, Lea, Flood 2014) seeded with the
   circuit seed; an integer below m is ``(x * m) >> 64``.
+
+Per-location, per-depth two-qubit gates (Sect. 3: the hardware's two-qubit
+unitaries vary with both the coupler and the cycle; Eq. 1 gives their form):
+``detuned_sycamore_circuit`` emits the same gate structure as
+``sycamore_circuit`` for the same seed, but each fSim record carries its own
+draw of (theta, phi, D+, D-, D-,off) as an 8-tuple
+``(kind, q0, q1, theta, phi, dplus, dminus, dminus_off)``: theta = pi/2 + U(-0.1, 0.1),
+phi = pi/6 + U(-0.1, 0.1), each detuning U(-pi, pi), from a second SplitMix64
+stream seeded with ``seed ^ DETUNE_SEED_XOR``, drawn in gate order.
 """
 from __future__ import annotations
 
@@ -44,6 +53,7 @@ FSIM = 3
 KIND_NAMES = {SQRT_X: "sqrtX", SQRT_Y: "sqrtY", SQRT_W: "sqrtW", FSIM: "fSim"}
 
 PATTERN_ORDER = "ABCDCDAB"
+DETUNE_SEED_XOR = 0xD37D37D37D37D37D
 
 _MASK64 = (1 << 64) - 1
 
@@ -128,6 +138,12 @@ class Circuit:
         phi = np.array([x[4] for x in g], dtype=np.float64)
         return kind, q0, q1, theta, phi
 
+    def detunings(self):
+        """fSim detunings (dplus, dminus, dminus_off) as float64 columns (0 for 5-tuples)."""
+        g = self.gates
+        return tuple(np.array([x[i] if len(x) > i else 0.0 for x in g], dtype=np.float64)
+                     for i in (5, 6, 7))
+
     def count(self, kind: int) -> int:
         return sum(1 for x in self.gates if x[0] == kind)
 
@@ -156,6 +172,29 @@ def sycamore_circuit(grid: Grid, cycles: int, seed: int, theta: float = math.pi 
             gates.append((FSIM, a, b, float(theta), float(phi)))
     one_qubit_layer()
     return Circuit(n_qubits=n, gates=gates, name=name)
+
+
+def detuned_sycamore_circuit(grid: Grid, cycles: int, seed: int, theta_spread: float = 0.1,
+                             phi_spread: float = 0.1, name: str = "") -> Circuit:
+    """``sycamore_circuit(grid, cycles, seed)`` with every fSim gate's parameters drawn for that
+    gate instance (see the module docstring), so that its matrix depends on the coupler and the
+    cycle."""
+    base = sycamore_circuit(grid, cycles, seed, name=name)
+    rng = SplitMix64(seed ^ DETUNE_SEED_XOR)
+
+    def u(lo, hi):
+        return lo + (hi - lo) * rng.uniform()
+
+    gates = []
+    for g in base.gates:
+        if g[0] == FSIM:
+            th = math.pi / 2 + u(-theta_spread, theta_spread)
+            ph = math.pi / 6 + u(-phi_spread, phi_spread)
+            gates.append((FSIM, g[1], g[2], th, ph, u(-math.pi, math.pi), u(-math.pi, math.pi),
+                          u(-math.pi, math.pi)))
+        else:
+            gates.append(g)
+    return Circuit(n_qubits=base.n_qubits, gates=gates, name=name)
 
 
 # Named workloads (rows, cols, removed sites, cycles).

@@ -100,6 +100,21 @@ def test_planner_blocks_reproduce_circuit(pkg, oracle_mod, kmax):
         pkg.sim_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("kmax", [2, 4, 6])
+def test_planner_blocks_reproduce_detuned_circuit(pkg, oracle_mod, kmax):
+    # per-location, per-cycle detuned fSim gates (Sect. 3, Eq. 1): the planner's FP64 blocks
+    # reproduce the oracle's gate-by-gate run
+    circ = si.detuned_sycamore_circuit(si.Grid(3, 4), cycles=8, seed=6)
+    plan = pkg.sim_plan_create(circ.n_qubits, pkg.gates_array(circ), kmax=kmax)
+    try:
+        psi = oracle_mod.basis_state(circ.n_qubits, 0)
+        for t, m in plan_blocks(pkg, plan):
+            oracle_mod.apply_kq(psi, t, m)
+        assert np.linalg.norm(psi - oracle_mod.run_circuit(circ)) < 1e-12
+    finally:
+        pkg.sim_plan_destroy(plan)
+
+
 def test_planner_counts_on_30q_circuit(pkg):
     # Wider blocks -> fewer passes over the state (Sect. 5, Tables 1-2 count "5Q kernels").
     circ = si.workload_circuit("syc30_5x6_d20", seed=0)

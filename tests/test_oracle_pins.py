@@ -386,6 +386,43 @@ def _plain_by_operators(oracle_mod, n, gates):
     return psi
 
 
+@pytest.mark.parametrize("n,n_gates,seed", [(3, 12, 11), (5, 30, 12), (7, 40, 13)])
+def test_apply_gates_detuned_matches_operator_product(oracle_mod, n, n_gates, seed):
+    # Sect. 3 / Eq. 1 with per-gate detunings: the oracle's gate-by-gate run of 8-tuple records
+    # equals the product of the gates' full 2^n x 2^n operators (a dropped detuning, a swapped
+    # q0/q1 role or a wrong sign of one of them fails this: the detuned gate is not symmetric)
+    gates = _detuned_circuit(n, n_gates, seed)
+    psi = oracle_mod.run_circuit(gates, n_qubits=n)
+    assert np.allclose(psi, _plain_by_operators(oracle_mod, n, gates), atol=1e-12)
+
+
+def test_detuned_sycamore_circuit_by_operators(oracle_mod):
+    # the generator's per-location, per-cycle fSim records through the oracle, against full
+    # operators; and the detunings matter (the undetuned circuit gives another state)
+    circ = si.detuned_sycamore_circuit(si.Grid(2, 4), cycles=6, seed=3)
+    psi = oracle_mod.run_circuit(circ)
+    assert np.allclose(psi, _plain_by_operators(oracle_mod, 8, circ.gates), atol=1e-12)
+    plain = oracle_mod.run_circuit(si.sycamore_circuit(si.Grid(2, 4), cycles=6, seed=3))
+    assert np.linalg.norm(psi - plain) > 0.1
+
+
+def test_detuned_generator_structure():
+    # same gate structure as the undetuned generator for the seed; every fSim instance has its
+    # own parameters, inside the stated ranges; deterministic
+    grid = si.Grid(3, 4)
+    a = si.detuned_sycamore_circuit(grid, cycles=8, seed=9)
+    b = si.sycamore_circuit(grid, cycles=8, seed=9)
+    assert [g[:3] for g in a.gates] == [g[:3] for g in b.gates]
+    assert a.gates == si.detuned_sycamore_circuit(grid, cycles=8, seed=9).gates
+    fs = [g for g in a.gates if g[0] == si.FSIM]
+    assert len(fs) == 34 and all(len(g) == 8 for g in fs)
+    assert all(abs(g[3] - np.pi / 2) <= 0.1 and abs(g[4] - np.pi / 6) <= 0.1 for g in fs)
+    assert all(all(-np.pi <= x < np.pi for x in g[5:]) for g in fs)
+    assert len({g[3:] for g in fs}) == len(fs)
+    d = a.detunings()
+    assert d[0].shape == (a.n_gates,) and np.count_nonzero(d[0]) == len(fs)
+
+
 def _contract_logical(oracle_mod, n, side, t1, t2):
     qa = [q for q in range(n) if side[q] == 0]
     qb = [q for q in range(n) if side[q] == 1]
