@@ -59,6 +59,11 @@ extern "C" {
                              by bulk copies (k = 5 and 6 with at most one target below bit 4,
                              k = 4 with none; at least 2^(k+7) amplitudes); other blocks of
                              k = 4..6 as SIM_FP16X3 on mma.sync, narrower ones on CUDA cores */
+#define SIM_BF16X3 5 /* BF16x3 on tcgen05.mma: the FP32 operands split into BF16 pieces (8 significant
+                        bits each), hi*hi + hi*lo + lo*hi accumulated in FP32; the same kernels and
+                        blocks as SIM_FP16X3_TMEM, with what tcgen05 leaves as SIM_FP16X3.  About
+                        2^-16 relative per product instead of 3xFP16's 2^-22: a stated-bound mode
+                        like SIM_TF32, not FP32-equivalent (Sect. 5 stores FP32 amplitudes) */
 /* The mma.sync tensor-core modes apply to blocks with k >= 5 (measured: for k <= 4 the CUDA-core
  * FP32 kernel is faster); narrower blocks run on CUDA cores in FP32. */
 
@@ -136,7 +141,7 @@ int sim_reset(sim_t *h, uint64_t basis);
  * For every group of 2^k amplitudes that differ only in the target bits,
  * psi_g <- M psi_g, in place.  k in 1..6; targets: k distinct logical qubits, all
  * local (SIM_E_NONLOCAL otherwise); matrix: 2^k x 2^k complex128, row-major,
- * bit j of its index <-> targets[j]; precision: SIM_FP32, SIM_TF32, SIM_TF32X3 or SIM_FP16X3
+ * bit j of its index <-> targets[j]; precision: SIM_FP32 .. SIM_BF16X3
  * (Sect. 5 suggests GPUs for the matrix-vector products; the tensor-core modes
  * treat a tile of 16 groups as a real GEMM with [[Re M, -Im M], [Im M, Re M]]).
  * Asynchronous. */
@@ -446,7 +451,7 @@ int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_p
  * precision: SIM_FP32 (CUDA cores, FP32 products and sums), or SIM_FP16X3 / SIM_FP16X3_TMEM
  * (tcgen05 tensor cores: each tensor scaled by one power of two, split into FP16 hi + lo, the
  * products hi*hi + hi*lo + lo*hi summed in FP32; needs n_side[0] >= 7 and n_side[1] >= 7,
- * otherwise the FP32 kernel runs).  Asynchronous.  SIM_E_INVAL for handles that do not fit s. */
+ * otherwise the FP32 kernel runs), or SIM_BF16X3 (the same with BF16 pieces).  Asynchronous.  SIM_E_INVAL for handles that do not fit s. */
 int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision);
 
 /* A split made ready to run (Sect. 2's subcircuits 1 and 2 and their contraction as one reusable
@@ -454,7 +459,8 @@ int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int pre
  * 4, SIM_FP32) and creates their device states (2^n_wires[t] amplitudes each) on out's device and
  * stream; it keeps its own copy of the split.  sim_front_run enqueues on out's stream: both tensors
  * reset to |0..0>, their blocks applied, and sim_contract into out -- on the tensor cores
- * (SIM_FP16X3_TMEM) when o->precision is SIM_FP16X3 or SIM_FP16X3_TMEM, else in FP32.  out must
+ * (SIM_FP16X3_TMEM) when o->precision is SIM_FP16X3 or SIM_FP16X3_TMEM, in BF16x3 when it is
+ * SIM_BF16X3, else in FP32.  out must
  * have the split's n_qubits qubits, be device-resident and not sliced, and live on the front's
  * device.  Asynchronous like sim_apply_plan; the tensors' kernels count in out's
  * sim_launch_count.  sim_front_destroy waits for the front's work. */
@@ -493,12 +499,12 @@ typedef struct srv_opts {
     int slots;           /* concurrent circuits above small_n (0 = 6, max 32) */
     int small_n;         /* circuits with n <= small_n are packed (0 = 20, max 24) */
     int max_pack;        /* most circuits per packed launch (0 = 1024) */
-    int kmax;            /* aggregation width (0 = 6 in SIM_FP16X3_TMEM, else 5, or 4 for n > 24
+    int kmax;            /* aggregation width (0 = 6 in SIM_FP16X3_TMEM and SIM_BF16X3, else 5, or 4 for n > 24
                           * in SIM_FP32); circuits above small_n run in the qubit layout
                           * sim_plan_layout picks and are permuted back before a readout */
-    int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_FP16X3_TMEM */
+    int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_BF16X3 */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
-    int front_pairs;     /* contraction deferral for circuits of >= 26 qubits in SIM_FP16X3_TMEM:
+    int front_pairs;     /* contraction deferral for circuits of >= 26 qubits in SIM_FP16X3_TMEM or SIM_BF16X3:
                           * the gates up to the (front_pairs + 1)-th across the bipartition
                           * sim_split_choose picks run as two tensors and one tensor-core
                           * contraction when they are >= 30% of the circuit (0 = 5, < 0 = off);

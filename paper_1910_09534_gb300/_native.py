@@ -32,6 +32,7 @@ SIM_TF32 = 1
 SIM_TF32X3 = 2
 SIM_FP16X3 = 3
 SIM_FP16X3_TMEM = 4
+SIM_BF16X3 = 5
 SIM_C64 = 0
 SIM_C128 = 1
 SIM_STORE_DEVICE = 0

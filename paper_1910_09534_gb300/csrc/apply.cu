@@ -572,9 +572,8 @@ int prepare_block(sim_t *h, int k, const int *targets, const double *matrix, int
 // Which kernel family takes a block: the one place that decides it.
 BlockPath block_path(int nbits, int k, const int *tpos, int precision)
 {
-    if (precision == SIM_FP16X3_TMEM && tcgen05_eligible(nbits, k, tpos)) return BlockPath::Tcgen05;
-    if (precision != SIM_FP32 &&
-        (tc_eligible(nbits, k, tpos) || (precision == SIM_FP16X3_TMEM && tc_eligible_low4(nbits, k))))
+    if (tmem_mode(precision) && tcgen05_eligible(nbits, k, tpos)) return BlockPath::Tcgen05;
+    if (precision != SIM_FP32 && (tc_eligible(nbits, k, tpos) || (tmem_mode(precision) && tc_eligible_low4(nbits, k))))
         return BlockPath::MmaSync;
     return BlockPath::CudaCore;
 }
@@ -603,7 +602,7 @@ size_t block_staged_bytes(int nbits, int k, const int *tpos, int precision)
 void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, int precision, void *h_out)
 {
     switch (block_path(nbits, k, tpos, precision)) {
-    case BlockPath::Tcgen05: tcgen05_build_staged(k, mat, h_out); break;
+    case BlockPath::Tcgen05: tcgen05_build_staged(k, mat, precision == SIM_BF16X3, h_out); break;
     case BlockPath::MmaSync: tc_build_staged(k, mat, precision, h_out); break;
     default:
         if (k == 6) std::memcpy(h_out, mat, sizeof(float2) * 4096);
@@ -616,7 +615,9 @@ int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos
 {
     int rc;
     switch (block_path(nbits, k, tpos, precision)) {
-    case BlockPath::Tcgen05: rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, d_staged, st); break;
+    case BlockPath::Tcgen05:
+        rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, precision == SIM_BF16X3, d_staged, st);
+        break;
     case BlockPath::MmaSync: rc = tc_launch_staged(psi, nbits, k, tpos, precision, d_staged, st); break;
     default:
         rc = launch_apply_fp32(h, psi, nbits, k, tpos, mat, k == 6 ? static_cast<const float2 *>(d_staged) : nullptr,
@@ -635,7 +636,7 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
     const BlockPath path = block_path(nbits, k, tpos, precision);
     if (path == BlockPath::Tcgen05) {
         const int ps = prof_begin(h, SIM_PROF_APPLY, 16.0 * std::ldexp(1.0, nbits), st);
-        const int rc = launch_apply_tcgen05(h, psi, nbits, k, tpos, mat, st);
+        const int rc = launch_apply_tcgen05(h, psi, nbits, k, tpos, mat, precision == SIM_BF16X3, st);
         prof_end(h, ps, st);
         if (rc != 0)
             return fail(h, SIM_E_CUDA, "apply (tcgen05): launch failed: %s",
@@ -679,7 +680,7 @@ int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int preci
     return enqueue_block_on(h, h->d_state, h->n, k, tpos, mat, precision, h->stream);
 }
 
-bool precision_ok(int precision) { return precision >= SIM_FP32 && precision <= SIM_FP16X3_TMEM; }
+bool precision_ok(int precision) { return precision >= SIM_FP32 && precision <= SIM_BF16X3; }
 
 }  // namespace sycsim
 

@@ -456,7 +456,7 @@ bool tc_eligible_low4(int nbits, int k) { return k == 4 && nbits >= k + 4; }
 
 size_t tc_staged_bytes(int k, int precision)
 {
-    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    const bool f16 = f16x3_mode(precision), split = precision == SIM_TF32X3;
     switch (k) {
     case 4: return f16 ? f16x3_bytes<4>() : (split ? mma_bytes<4, true>() : mma_bytes<4, false>());
     case 5: return f16 ? f16x3_bytes<5>() : (split ? mma_bytes<5, true>() : mma_bytes<5, false>());
@@ -468,7 +468,7 @@ size_t tc_staged_bytes(int k, int precision)
 void tc_build_staged(int k, const float2 *mat, int precision, void *h_out)
 {
     uint32_t *o = static_cast<uint32_t *>(h_out);
-    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    const bool f16 = f16x3_mode(precision), split = precision == SIM_TF32X3;
     switch (k) {
     case 4: f16 ? build_f16x3<4>(mat, o) : (split ? build_mma<4, true>(mat, o) : build_mma<4, false>(mat, o)); break;
     case 5: f16 ? build_f16x3<5>(mat, o) : (split ? build_mma<5, true>(mat, o) : build_mma<5, false>(mat, o)); break;
@@ -481,7 +481,7 @@ int tc_launch_staged(float2 *psi, int nbits, int k, const int *tpos, int precisi
                      cudaStream_t st)
 {
     const uint32_t *d = static_cast<const uint32_t *>(d_staged);
-    const bool f16 = precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM, split = precision == SIM_TF32X3;
+    const bool f16 = f16x3_mode(precision), split = precision == SIM_TF32X3;
     switch (k) {
     case 4: return f16 ? launch_f16x3_staged<4>(psi, nbits, tpos, d, st)
                        : (split ? launch_mma_staged<4, true>(psi, nbits, tpos, d, st)
@@ -505,7 +505,7 @@ int launch_apply_tc(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, co
     uint32_t *hf = h->h_frag + sim_s::kFragWords * slot;
     uint32_t *df = h->d_frag + sim_s::kFragWords * slot;
     cudaEvent_t ev = h->frag_ev[slot];
-    if (precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM) {
+    if (f16x3_mode(precision)) {
         switch (k) {
         case 4: return launch_f16x3_k<4>(psi, nbits, tpos, mat, st, hf, df, ev);
         case 5: return launch_f16x3_k<5>(psi, nbits, tpos, mat, st, hf, df, ev);

@@ -37,9 +37,14 @@
 // is built on the host and staged in shared memory once per CTA.  Two TMEM accumulator sets let
 // tile i + 1 be multiplied while tile i is drained.
 //
+// BF16x3 (SIM_BF16X3) is the same pipeline with BF16 pieces (8 significant bits each instead of
+// FP16's 11): hi = bf16(a), lo = bf16(a - hi), the same three products, the operand format bits
+// of the instruction descriptor set to BF16.  The row scale is kept (a power of two, exact).
+//
 // Every wait is bounded in time (%globaltimer): a timeout records the failure in an error word
 // and a shared abort flag that ends every role's loop; the CTA then waits for its bulk copies in
 // flight and frees its tensor memory before returning.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -249,7 +254,7 @@ __device__ __forceinline__ uint32_t cm_off(int row, int k) { return (row >> 3) *
 // A stage is reloaded only after every drainer has passed its waits for it and taken what it
 // needs, and a TMEM set reused only after its read, so no barrier can run a phase ahead of a
 // waiter that still has to see the previous phase.
-template <int K, int R2, bool LOWT>
+template <int K, int R2, bool LOWT, bool BF>
 __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 {
     using L = Tc5Layout<K, R2>;
@@ -359,11 +364,19 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const float re = x[u][4 * cc + j].x * sc, im = x[u][4 * cc + j].y * sc;
-                        const __half2 h = __floats2half2_rn(re, im);
-                        const float2 hf = __half22float2(h);
-                        const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
-                        hi[j] = *reinterpret_cast<const uint32_t *>(&h);
-                        lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+                        if constexpr (BF) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+                            const float2 hf = __bfloat1622float2(h);
+                            const __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+                            hi[j] = *reinterpret_cast<const uint32_t *>(&h);
+                            lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+                        } else {
+                            const __half2 h = __floats2half2_rn(re, im);
+                            const float2 hf = __half22float2(h);
+                            const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+                            hi[j] = *reinterpret_cast<const uint32_t *>(&h);
+                            lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+                        }
                     }
                     if constexpr (LOWT) {  // position p of the chunk takes register p ^ (mu & 3)
                         if (mu & 1) {
@@ -410,7 +423,9 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if ((tid & 31) == 0) {
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+            // F32 accumulate; A and B FP16 (format 0) or BF16 (format 1, bits 7 and 10); K-major
+            const uint32_t idesc = (1u << 4) | (BF ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(N >> 3) << 17) |
+                                   ((uint32_t)(kRows >> 4) << 24);
             uint32_t i = 0;
             for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
                 const int st = i % S;
@@ -568,9 +583,24 @@ float half_value(uint16_t u)
     return __half2float(h);
 }
 
-// Host: R^T = B[n][k] (n = 2o + po output real, k = 2i + pi input real), split hi/lo in FP16,
-// written in the K-major core-matrix layout, KS slices of N x 16.
-template <int K>
+uint16_t bf16_bits(float f)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    uint16_t u;
+    std::memcpy(&u, &h, 2);
+    return u;
+}
+
+float bf16_value(uint16_t u)
+{
+    __nv_bfloat16 h;
+    std::memcpy(&h, &u, 2);
+    return __bfloat162float(h);
+}
+
+// Host: R^T = B[n][k] (n = 2o + po output real, k = 2i + pi input real), split hi/lo in FP16 (or
+// BF16), written in the K-major core-matrix layout, KS slices of N x 16.
+template <int K, bool BF>
 void build_b(const float2 *mat, uint16_t *out)
 {
     using L = Tc5Layout<K, 1>;
@@ -581,8 +611,8 @@ void build_b(const float2 *mat, uint16_t *out)
             const int o = n >> 1, po = n & 1, i = k >> 1, pi = k & 1;
             const float2 m = mat[o * D + i];
             const float v = po == 0 ? (pi == 0 ? m.x : -m.y) : (pi == 0 ? m.y : m.x);
-            const uint16_t h = half_bits(v);
-            const uint16_t l = half_bits(v - half_value(h));
+            const uint16_t h = BF ? bf16_bits(v) : half_bits(v);
+            const uint16_t l = BF ? bf16_bits(v - bf16_value(h)) : half_bits(v - half_value(h));
             const int s = k >> 4, kk = k & 15;
             const size_t off = ((size_t)s * L::B_SLICE + (n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) / 2;
             hi[off] = h;
@@ -635,11 +665,11 @@ int tile_geometry(int nbits, const int *tpos, int rows, Tc5Geom &g)
     return full_run;
 }
 
-template <int K, int R2, bool LOWT>
+template <int K, int R2, bool LOWT, bool BF>
 int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
 {
     using L = Tc5Layout<K, R2>;
-    auto kern = k_apply_tcgen05<K, R2, LOWT>;
+    auto kern = k_apply_tcgen05<K, R2, LOWT, BF>;
     // one CTA per SM: the stage ring takes most of the SM's shared memory, which also keeps the
     // resident CTAs' tensor memory within the SM's 512 columns (initialised once, thread-safe)
     static std::atomic<uint64_t> smem_done{0};
@@ -661,7 +691,7 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
 }
 
 // Geometry of the block and launch, B (hi, lo) already in device memory at d_b.
-template <int K>
+template <int K, bool BF>
 int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const uint32_t *d_b, cudaStream_t st)
 {
     Tc5Geom g{};
@@ -674,8 +704,8 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
     if (g.nlow > (K >= 5 ? 1 : 0)) return -2;  // not eligible (see tcgen05_eligible)
     if constexpr (K == 6) {  // 128-group tiles only: two 256-column accumulator sets fill the TMEM
         if (tile_geometry<K>(nbits, tpos, 7, g) < 0) return -1;
-        if (g.nlow > 0) return launch_tc5_kr<K, 1, true>(g, nbits, st);
-        return launch_tc5_kr<K, 1, false>(g, nbits, st);
+        if (g.nlow > 0) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st);
+        return launch_tc5_kr<K, 1, false, BF>(g, nbits, st);
     } else {
         // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below
         // it); otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy
@@ -684,23 +714,23 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
         const int run = tile_geometry<K>(nbits, tpos, 7, g);
         if (run < 0) return -1;
         if (g.nlow > 0) {
-            if constexpr (K == 5) return launch_tc5_kr<K, 1, true>(g, nbits, st);
+            if constexpr (K == 5) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st);
             return -2;
         }
-        if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false>(g, nbits, st);
+        if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false, BF>(g, nbits, st);
         if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
-        return launch_tc5_kr<K, 2, false>(g, nbits, st);
+        return launch_tc5_kr<K, 2, false, BF>(g, nbits, st);
     }
 }
 
-template <int K>
+template <int K, bool BF>
 int launch_tc5_k(sim_t *h, float2 *psi, int nbits, const int *tpos, const float2 *mat, cudaStream_t st,
                  uint32_t *h_frag, uint32_t *d_frag, cudaEvent_t ev)
 {
     using L = Tc5Layout<K, 1>;
-    build_b<K>(mat, reinterpret_cast<uint16_t *>(h_frag));
+    build_b<K, BF>(mat, reinterpret_cast<uint16_t *>(h_frag));
     if (cudaMemcpyAsync(d_frag, h_frag, 2 * L::B_BYTES, cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
-    const int rc = launch_tc5_staged<K>(h, psi, nbits, tpos, d_frag, st);
+    const int rc = launch_tc5_staged<K, BF>(h, psi, nbits, tpos, d_frag, st);
     // the staging slot is free again once this kernel, which reads it, has run (on any stream)
     if (cudaEventRecord(ev, st) != cudaSuccess) return -1;
     return rc;
@@ -734,26 +764,30 @@ size_t tcgen05_staged_bytes(int k)
     }
 }
 
-void tcgen05_build_staged(int k, const float2 *mat, void *h_out)
+void tcgen05_build_staged(int k, const float2 *mat, bool bf16, void *h_out)
 {
-    if (k == 4) build_b<4>(mat, static_cast<uint16_t *>(h_out));
-    if (k == 5) build_b<5>(mat, static_cast<uint16_t *>(h_out));
-    if (k == 6) build_b<6>(mat, static_cast<uint16_t *>(h_out));
+    uint16_t *o = static_cast<uint16_t *>(h_out);
+    if (k == 4) bf16 ? build_b<4, true>(mat, o) : build_b<4, false>(mat, o);
+    if (k == 5) bf16 ? build_b<5, true>(mat, o) : build_b<5, false>(mat, o);
+    if (k == 6) bf16 ? build_b<6, true>(mat, o) : build_b<6, false>(mat, o);
 }
 
-int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const void *d_staged,
-                          cudaStream_t st)
+int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, bool bf16,
+                          const void *d_staged, cudaStream_t st)
 {
     const uint32_t *d_b = static_cast<const uint32_t *>(d_staged);
     switch (k) {
-    case 4: return launch_tc5_staged<4>(h, psi, nbits, tpos, d_b, st);
-    case 5: return launch_tc5_staged<5>(h, psi, nbits, tpos, d_b, st);
-    case 6: return launch_tc5_staged<6>(h, psi, nbits, tpos, d_b, st);
+    case 4: return bf16 ? launch_tc5_staged<4, true>(h, psi, nbits, tpos, d_b, st)
+                        : launch_tc5_staged<4, false>(h, psi, nbits, tpos, d_b, st);
+    case 5: return bf16 ? launch_tc5_staged<5, true>(h, psi, nbits, tpos, d_b, st)
+                        : launch_tc5_staged<5, false>(h, psi, nbits, tpos, d_b, st);
+    case 6: return bf16 ? launch_tc5_staged<6, true>(h, psi, nbits, tpos, d_b, st)
+                        : launch_tc5_staged<6, false>(h, psi, nbits, tpos, d_b, st);
     default: return -1;
     }
 }
 
-int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat, bool bf16,
                          cudaStream_t st)
 {
     const int slot = h->frag_next;
@@ -763,9 +797,12 @@ int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpo
     uint32_t *df = h->d_frag + sim_s::kFragWords * slot;
     cudaEvent_t ev = h->frag_ev[slot];
     switch (k) {
-    case 4: return launch_tc5_k<4>(h, psi, nbits, tpos, mat, st, hf, df, ev);
-    case 5: return launch_tc5_k<5>(h, psi, nbits, tpos, mat, st, hf, df, ev);
-    case 6: return launch_tc5_k<6>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 4: return bf16 ? launch_tc5_k<4, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                        : launch_tc5_k<4, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 5: return bf16 ? launch_tc5_k<5, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                        : launch_tc5_k<5, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
+    case 6: return bf16 ? launch_tc5_k<6, true>(h, psi, nbits, tpos, mat, st, hf, df, ev)
+                        : launch_tc5_k<6, false>(h, psi, nbits, tpos, mat, st, hf, df, ev);
     default: return -1;
     }
 }

@@ -25,6 +25,7 @@
 //    groups of 8 y-tiles so the CTAs running together share operand blocks in L2.  Every wait
 //    is bounded in time (%globaltimer); a timeout sets the handle's error word and ends every
 //    role, and the CTA waits for its own copies and MMAs before releasing tensor memory.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -144,6 +145,7 @@ struct CtArgs {
     uint32_t tiles_x, tiles_y;
     const float *amax;    // largest |component| of tensor 1, tensor 2
     int *err;
+    int bf16;             // operand images in BF16 (SIM_BF16X3) instead of FP16
 };
 
 __device__ __forceinline__ uint32_t ct_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -280,16 +282,28 @@ __global__ void __launch_bounds__(256) k_absmax(const float2 *__restrict__ t, ui
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-__device__ __forceinline__ void ct_split(float v, __half &h, __half &l)
+// hi / lo pieces of v as FP16 (or BF16, SIM_BF16X3) bit patterns
+template <bool BF>
+__device__ __forceinline__ void ct_split(float v, uint16_t &h, uint16_t &l)
 {
-    h = __float2half_rn(v);
-    l = __float2half_rn(v - __half2float(h));
+    if constexpr (BF) {
+        const __nv_bfloat16 a = __float2bfloat16_rn(v);
+        const __nv_bfloat16 b = __float2bfloat16_rn(v - __bfloat162float(a));
+        h = __bfloat16_as_ushort(a);
+        l = __bfloat16_as_ushort(b);
+    } else {
+        const __half a = __float2half_rn(v);
+        const __half b = __float2half_rn(v - __half2float(a));
+        h = __half_as_ushort(a);
+        l = __half_as_ushort(b);
+    }
 }
 
 // Operand image of one tensor T[e][c] (c < 2^nside contiguous, e < n_e; e >= n_e reads as 0).
 // Thread = (tile, k-step, row r < 128, K half kh): 8 entanglement values of column c = 128 tile + r.
 // role 0 (A, tensor 1): slabs Re hi | Re lo | Im hi | Im lo, 128 rows x 16 each (4 KiB).
 // role 1 (B, tensor 2): slabs hi | lo, 256 rows x 16 each (8 KiB): row r = Re, row 128 + r = Im.
+template <bool BF>
 __global__ void __launch_bounds__(256) k_contract_image(const float2 *__restrict__ t, int nside, uint64_t n_e,
                                                         uint32_t ks, const float *amax, uint8_t *img, int role)
 {
@@ -300,13 +314,13 @@ __global__ void __launch_bounds__(256) k_contract_image(const float2 *__restrict
     const uint64_t ts = gid >> 8;  // tile * ks + k-step
     const uint64_t tile = ts / ks, step = ts % ks;
     const float sc = ldexpf(1.f, ct_shift(*amax));
-    __align__(16) __half rh[8], rl[8], ih[8], il[8];
+    __align__(16) uint16_t rh[8], rl[8], ih[8], il[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const uint64_t e = 16 * step + 8 * kh + j;
         const float2 v = e < n_e ? t[e * C + tile * 128 + r] : make_float2(0.f, 0.f);
-        ct_split(v.x * sc, rh[j], rl[j]);
-        ct_split(v.y * sc, ih[j], il[j]);
+        ct_split<BF>(v.x * sc, rh[j], rl[j]);
+        ct_split<BF>(v.y * sc, ih[j], il[j]);
     }
     uint8_t *base = img + ts * kCtSlab;
     const uint32_t off = (r >> 3) * 256 + kh * 128 + (r & 7) * 16;
@@ -396,7 +410,9 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_contract_tcgen05(CtArgs g, co
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            // F32 accumulate, A/B FP16 or BF16 (format bits 7 and 10), N = 256, M = 128
+            const uint32_t idesc = (1u << 4) | (g.bf16 ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(256 >> 3) << 17) |
+                                   ((uint32_t)(128 >> 4) << 24);
             uint32_t it = 0, tl = 0;
             bool stop = false;
             for (uint64_t tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x, ++tl) {
@@ -491,7 +507,7 @@ size_t tcgen05_scratch_bytes(int n1, int n2, int e_bits)
 }
 
 int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                            const CtOut &o, cudaStream_t st, uint8_t *own_scratch = nullptr)
+                            const CtOut &o, bool bf16, cudaStream_t st, uint8_t *own_scratch = nullptr)
 {
     static std::atomic<uint64_t> smem_done{0};
     if (!smem_opt_in(k_contract_tcgen05, kCtStages * kCtStage, smem_done)) return -1;
@@ -525,8 +541,9 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         k_absmax<<<blocks, 256, 0, st>>>(t1, X * n_e, reinterpret_cast<unsigned *>(amax));
         const unsigned blocks2 = (unsigned)std::min<uint64_t>(4ull * cfg.sms, (Y * n_e + 255) / 256);
         k_absmax<<<blocks2, 256, 0, st>>>(t2, Y * n_e, reinterpret_cast<unsigned *>(amax + 1));
-        k_contract_image<<<(unsigned)((X / 128) * ks), 256, 0, st>>>(t1, n1, n_e, ks, amax, scratch, 0);
-        k_contract_image<<<(unsigned)((Y / 128) * ks), 256, 0, st>>>(t2, n2, n_e, ks, amax + 1, scratch + a_bytes, 1);
+        auto image = bf16 ? k_contract_image<true> : k_contract_image<false>;
+        image<<<(unsigned)((X / 128) * ks), 256, 0, st>>>(t1, n1, n_e, ks, amax, scratch, 0);
+        image<<<(unsigned)((Y / 128) * ks), 256, 0, st>>>(t2, n2, n_e, ks, amax + 1, scratch + a_bytes, 1);
         h->launches += 4;
         CtArgs g{};
         g.aimg = scratch;
@@ -539,6 +556,7 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         g.tiles_y = (uint32_t)(Y / 128);
         g.amax = amax;
         g.err = h->d_errflag;
+        g.bf16 = bf16 ? 1 : 0;
         const uint64_t grid = std::min<uint64_t>((uint64_t)g.tiles_x * g.tiles_y, (uint64_t)cfg.sms);
         const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * (double)X * (double)Y * (double)n_e, st);
         k_contract_tcgen05<<<(unsigned)grid, kCtThreads, kCtStages * kCtStage, st>>>(g, o);
@@ -587,7 +605,7 @@ int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const 
     for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out_bit_of[side_qubit[0][i]];
     for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out_bit_of[side_qubit[1][j]];
     if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7)
-        return launch_contract_tcgen05(h, t1, t2, psi, n1, n2, e_bits, o, st, scratch);
+        return launch_contract_tcgen05(h, t1, t2, psi, n1, n2, e_bits, o, precision == SIM_BF16X3, st, scratch);
     const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, n1 + n2 + e_bits), st);
     const int rc = launch_contract_fp32(t1, t2, psi, n1, n2, e_bits, o, st);
     prof_end(h, ps, st);
@@ -600,9 +618,9 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
 {
     if (!out || !t1 || !t2 || !s) return fail(out, SIM_E_INVAL, "sim_contract: NULL argument");
     if (out == t1 || out == t2 || t1 == t2) return fail(out, SIM_E_INVAL, "sim_contract: handles must be distinct");
-    if (precision != SIM_FP32 && precision != SIM_FP16X3 && precision != SIM_FP16X3_TMEM)
-        return fail(out, SIM_E_INVAL, "sim_contract: precision %d is not SIM_FP32, SIM_FP16X3 or SIM_FP16X3_TMEM",
-                    precision);
+    if (precision != SIM_FP32 && precision != SIM_FP16X3 && precision != SIM_FP16X3_TMEM && precision != SIM_BF16X3)
+        return fail(out, SIM_E_INVAL,
+                    "sim_contract: precision %d is not SIM_FP32, SIM_FP16X3, SIM_FP16X3_TMEM or SIM_BF16X3", precision);
     const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
     for (sim_t *h : {out, t1, t2})
         if (h->store != SIM_STORE_DEVICE || h->s != 0 || !h->d_state)

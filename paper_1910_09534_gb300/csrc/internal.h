@@ -232,15 +232,22 @@ int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, c
 int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);
 
 bool precision_ok(int precision);
+// the modes whose 4- to 6-qubit blocks take the tcgen05 kernel where it is eligible
+inline bool tmem_mode(int precision) { return precision == SIM_FP16X3_TMEM || precision == SIM_BF16X3; }
+// the modes whose mma.sync blocks use the 3xFP16 kernel (BF16X3 hands it what tcgen05 leaves)
+inline bool f16x3_mode(int precision)
+{
+    return precision == SIM_FP16X3 || precision == SIM_FP16X3_TMEM || precision == SIM_BF16X3;
+}
 
 // ---- apply_tcgen05.cu (5th-generation tensor cores, TMEM) ----
 bool tcgen05_eligible(int nbits, int k, const int *tpos);
 // operands staged once in device memory (CUDA graphs): B hi/lo of one block
 size_t tcgen05_staged_bytes(int k);
-void tcgen05_build_staged(int k, const float2 *mat, void *h_out);
-int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const void *d_staged,
-                          cudaStream_t st);
-int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
+void tcgen05_build_staged(int k, const float2 *mat, bool bf16, void *h_out);
+int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, bool bf16,
+                          const void *d_staged, cudaStream_t st);
+int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat, bool bf16,
                          cudaStream_t st);
 
 // ---- apply_tc.cu (tensor cores) ----

@@ -393,7 +393,7 @@ double pass_ms(int k, const int *tpos, int precision)
         low5 += tpos[i] < 5;
         le7 = le7 || tpos[i] <= 7;
     }
-    if (precision == SIM_FP16X3_TMEM) {
+    if (tmem_mode(precision)) {
         // tcgen05 with <= 1 target below bit 4 (k = 5, 6) or none (k = 4), else mma.sync 3xFP16;
         // tcgen05 tiles move 2 KiB runs once a target sits at bit 7 or below, else 1 KiB (k = 6)
         // or twice the groups (k = 4, 5)
@@ -419,7 +419,7 @@ double pass_ms(int k, const int *tpos, int precision)
 // the plan's per-pass estimate most, until none does.  Returns the estimate's change (<= 0).
 double improve_by_disjoint_swaps(const sim_plan_s *p, std::vector<int> &pos, std::vector<char> &used, int top)
 {
-    if (p->precision != SIM_FP16X3_TMEM && p->precision != SIM_FP32) return 0.0;
+    if (!tmem_mode(p->precision) && p->precision != SIM_FP32) return 0.0;
     double gain = 0.0;
     const int n = p->n, nb = (int)p->blocks.size();
     std::vector<std::vector<int>> of_qubit(n);
@@ -494,7 +494,7 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
     const double ident = total();
     std::vector<int> best = pos;
     double best_cost = ident;
-    const bool modelled = p->precision == SIM_FP16X3_TMEM || p->precision == SIM_FP32;
+    const bool modelled = tmem_mode(p->precision) || p->precision == SIM_FP32;
     uint64_t rs = 0x9E3779B97F4A7C15ull;  // SplitMix64 state for the seeded starts
     auto next = [&]() {
         uint64_t z = (rs += 0x9E3779B97F4A7C15ull);
@@ -673,7 +673,10 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
         precs.push_back(SIM_FP16X3_TMEM);
         precs.push_back(SIM_TF32X3);
     }
-    if (accuracy == SIM_TUNE_ANY) precs.push_back(SIM_TF32);
+    if (accuracy == SIM_TUNE_ANY) {  // the stated-bound modes
+        precs.push_back(SIM_TF32);
+        precs.push_back(SIM_BF16X3);
+    }
     SIM_DEVICE_SCOPE(h, h->device);
     cudaEvent_t e0, e1;
     SIM_CUDA_TRY(h, cudaEventCreate(&e0));
@@ -684,7 +687,7 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
     for (int prec : precs)
         for (int kmax = 3; kmax <= kMaxK && rc == SIM_OK; kmax++) {
             // mma.sync tensor-core paths take blocks of k >= 5, the tcgen05 path k >= 4
-            if (prec != SIM_FP32 && kmax < (prec == SIM_FP16X3_TMEM ? 4 : 5)) continue;
+            if (prec != SIM_FP32 && kmax < (tmem_mode(prec) ? 4 : 5)) continue;
             sim_plan_opts o{};
             o.kmax = kmax;
             o.precision = prec;

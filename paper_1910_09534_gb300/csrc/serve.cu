@@ -261,7 +261,7 @@ int srv_fail(srv_t *s, int code, const char *fmt, ...)
 int auto_kmax(int n, bool packed, int precision)
 {
     if (packed) return 5;
-    if (precision == SIM_FP16X3_TMEM) return 6;
+    if (tmem_mode(precision)) return 6;
     if (precision != SIM_FP32) return 5;
     return n <= 24 ? 5 : 4;
 }
@@ -707,7 +707,7 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     // tensor-core contraction, when that front holds a large enough share of the circuit
     int front = 0;
     std::vector<int> side(n_qubits, 0);
-    if (!r->packed && r->precision == SIM_FP16X3_TMEM && n_qubits >= kFrontMinQubits && s->o.front_pairs >= 0) {
+    if (!r->packed && tmem_mode(r->precision) && n_qubits >= kFrontMinQubits && s->o.front_pairs >= 0) {
         int nf = 0;
         if (split_choose(n_qubits, n_gates, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf,
                          n_qubits) == SIM_OK &&

@@ -193,8 +193,9 @@ extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan
     if (!fr) return fail(out, SIM_E_NOMEM_HOST, "sim_front_create: out of host memory");
     fr->split = *s;
     fr->device = out->device;
-    fr->contract_precision =
-        (po.precision == SIM_FP16X3 || po.precision == SIM_FP16X3_TMEM) ? SIM_FP16X3_TMEM : SIM_FP32;
+    fr->contract_precision = po.precision == SIM_BF16X3 ? SIM_BF16X3
+                             : (po.precision == SIM_FP16X3 || po.precision == SIM_FP16X3_TMEM) ? SIM_FP16X3_TMEM
+                                                                                                : SIM_FP32;
     for (int t = 0; t < 2; ++t) {
         const int nw = s->n_side[t] + 2 * s->n_pairs;
         int rc = sim_plan_create(nw, (int)s->gates[t].size(), s->gates[t].data(), &po, &fr->p[t]);

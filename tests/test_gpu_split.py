@@ -95,7 +95,7 @@ def test_tensors_match_oracle(pkg, oracle_mod, precision):
         pkg.sim_split_destroy(s)
 
 
-@pytest.mark.parametrize("cprec", ["fp32", "tmem"])
+@pytest.mark.parametrize("cprec", ["fp32", "tmem", "bf16x3"])
 @pytest.mark.parametrize("shape,cycles,cut", [((3, 4), 6, 2), ((4, 4), 4, 2), ((4, 5), 6, 2), ((4, 6), 6, 3)])
 def test_contraction_matches_plain_simulation(pkg, oracle_mod, shape, cycles, cut, cprec):
     grid = si.Grid(*shape)
@@ -103,7 +103,7 @@ def test_contraction_matches_plain_simulation(pkg, oracle_mod, shape, cycles, cu
     n = grid.n_qubits
     side = column_sides(grid, cut)
     gates = pkg.gates_array(circ)
-    cp = pkg.SIM_FP32 if cprec == "fp32" else pkg.SIM_FP16X3_TMEM
+    cp = {"fp32": pkg.SIM_FP32, "tmem": pkg.SIM_FP16X3_TMEM, "bf16x3": pkg.SIM_BF16X3}[cprec]
     out, s = contracted_front(pkg, n, gates, side, 4, pkg.SIM_FP32, cp)
     try:
         pairs = pkg.sim_split_info(s)[2]
@@ -115,7 +115,10 @@ def test_contraction_matches_plain_simulation(pkg, oracle_mod, shape, cycles, cu
     want = oracle_mod.run_circuit(circ)
     e = err2(got, want)
     print(f"{shape} {cycles} cycles, {pairs} bridging gates, {cprec}: ||dpsi|| = {e:.2e}, norm {norm:.8f}")
-    assert pairs > 0 and e <= TOL and abs(norm - 1) < 1e-5
+    # BF16x3: pieces of 8 significant bits, about 2^-16 relative per product (measured 0.2-4.5e-6
+    # on these fronts; bound 2e-5 as for one BF16x3 pass)
+    tol = 2e-5 if cprec == "bf16x3" else TOL
+    assert pairs > 0 and e <= tol and abs(norm - 1) < (2e-5 if cprec == "bf16x3" else 1e-5)
 
 
 @pytest.mark.parametrize("cprec", ["fp32", "tmem"])
