@@ -46,6 +46,11 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "syc30_5x6_d20"
 NOMINAL_DENSE_F16_TFLOPS = 2250.0  # GB300 dense FP16/BF16 tensor rate, datasheet (no sparsity)
+# Poisson arrival rates of the 2000-circuit serving legs: about 70% of each server's saturated
+# rate on GB300 (all circuits at t = 0), so that the server keeps up and its latency is a queueing
+# figure, not a backlog
+SERVING_RATE_SPLIT = 87.5
+SERVING_RATE_FP32 = 30.0
 METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 
@@ -86,12 +91,20 @@ def parse():
                          "(default: a temporary file)")
     ap.add_argument("--cpu-sample-gates", type=int, default=42)
     ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--no-bf16-path", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--serving-circuits", type=int, default=200)
-    ap.add_argument("--serving-rate", type=float, default=0.0,
-                    help="Poisson arrival rate of the serving leg in circuits/s (0: every circuit at "
-                         "t = 0, saturated)")
+    ap.add_argument("--serving-circuits", type=int, default=2000)
+    ap.add_argument("--serving-rate", type=float, default=SERVING_RATE_SPLIT,
+                    help="Poisson arrival rate of the split-precision serving leg in circuits/s (0: every "
+                         "circuit at t = 0, saturated)")
+    ap.add_argument("--serving-rate-fp32", type=float, default=SERVING_RATE_FP32,
+                    help="Poisson arrival rate of the FP32 serving leg in circuits/s (0: saturated)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving leg in the --precision given (fp32, else the split mode) "
+                         "and print one JSON line")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 33-qubit sliced runs (64 GiB state) of the default line")
     ap.add_argument("--oracle-table", action="store_true",
                     help="time the CPU oracle on one and on all host cores for the 12-, 30- (sample), "
                          "28- (sample) and 24-qubit circuits, print one JSON line, and exit")
@@ -270,11 +283,14 @@ def oracle_table():
     return {"cpu": cpu, "cores": cores, "rows": rows}
 
 
-def serving_run(count: int, device: int, rate_hz: float = 0.0):
+def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = "fp16x3_tmem"):
     """Serve `count` random circuits (qubits uniform in 16..30, 8..20 cycles), all submitted at
     once (rate_hz = 0) or each at its Poisson arrival time, and run the same circuits, arriving
     the same way, one at a time through sim_*; report circuits/s and the latency distributions
-    (completion - arrival)."""
+    (completion - arrival).  precision: the server's arithmetic above its packing size
+    ("fp16x3_tmem": 3xFP16 on tcgen05, blocks of <= 6 qubits; "fp32": CUDA cores, blocks of <= 5
+    qubits up to 24 qubits and <= 4 above); the one-at-a-time path uses the same arithmetic,
+    block widths and layouts."""
     import paper_1910_09534_gb300 as pkg
     import syc_inputs as si
 
@@ -282,6 +298,11 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0):
     arrivals = [a if rate_hz > 0 else 0.0 for a, _ in stream]
     circs = [c for _, c in stream]
     gates = [pkg.gates_array(c) for c in circs]
+    fp32 = precision == "fp32"
+    prec = pkg.SIM_FP32 if fp32 else pkg.SIM_FP16X3_TMEM
+
+    def kmax_of(n):  # the server's width policy above its packing size
+        return (5 if n <= 24 else 4) if fp32 else 6
 
     def until(t0, at):  # sleep until `at` seconds after t0
         dt = at - (time.perf_counter() - t0)
@@ -297,10 +318,10 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0):
     t0 = time.perf_counter()
     for at, c, g in zip(arrivals, circs, gates):
         until(t0, at)
-        # the server's policy above its packing size: blocks of <= 6 qubits in a chosen layout
         h = handles[c.n_qubits]
         big = c.n_qubits > 20
-        p = pkg.sim_plan_create(c.n_qubits, g, kmax=6 if big else 5, precision=pkg.SIM_FP16X3_TMEM)
+        p = (pkg.sim_plan_create(c.n_qubits, g, kmax=kmax_of(c.n_qubits), precision=prec) if big else
+             pkg.sim_plan_create(c.n_qubits, g, kmax=5, precision=pkg.SIM_FP32 if fp32 else prec))
         if big:
             pkg.sim_set_layout(h, pkg.sim_plan_layout(p, c.n_qubits)[0])
         pkg.sim_reset(h)
@@ -311,7 +332,7 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0):
     seq_s = time.perf_counter() - t0
     for h in handles.values():
         pkg.sim_destroy(h)
-    srv = pkg.srv_create(device=device, precision=pkg.SIM_FP16X3_TMEM)
+    srv = pkg.srv_create(device=device, precision=prec)
     t0 = time.perf_counter()
     tickets = []
     for at, c, g in zip(arrivals, circs, gates):
@@ -324,16 +345,22 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0):
     pkg.srv_destroy(srv)
     arr = ("all at t=0 (saturated)" if rate_hz <= 0 else
            f"Poisson at {rate_hz:g} circuits/s (last arrival at {arrivals[-1]:.2f} s)")
+    if fp32:
+        arith = ("fp32 on CUDA cores (k_max 5 up to 24 qubits, 4 above, in a chosen layout above 20 "
+                 "qubits; circuits of <= 20 qubits packed one per CTA, k_max 5)")
+        front = "none (the contraction front runs in the tcgen05 modes only)"
+    else:
+        arith = ("fp16x3_tmem (k_max 6 in a chosen layout above 20 qubits; circuits of <= 20 "
+                 "qubits packed one per CTA in FP32, k_max 5)")
+        front = ("circuits of >= 26 qubits whose first 5 crossings of the chosen bipartition leave >= 30% "
+                 "of the gates in front run them as two tensors and one tcgen05 contraction; the "
+                 "one-at-a-time path runs every circuit plainly")
     return {"circuits": count, "qubits": "16..30", "cycles": "8..20", "arrivals": arr,
             "circuits_per_s": count / served_s, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "one_at_a_time_circuits_per_s": count / seq_s,
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
             "one_at_a_time_p99_ms": statistics.quantiles(seq_done, n=100)[98],
-            "arithmetic": "fp16x3_tmem (k_max 6 in a chosen layout above 20 qubits; circuits of <= 20 "
-                          "qubits packed one per CTA in FP32, k_max 5)",
-            "server_front": "circuits of >= 26 qubits whose first 5 crossings of the chosen bipartition "
-                            "leave >= 30% of the gates in front run them as two tensors and one tcgen05 "
-                            "contraction; the one-at-a-time path runs every circuit plainly"}
+            "arithmetic": arith, "server_front": front}
 
 
 def graph_replay_run(device: int, runs: int = 30):
@@ -645,6 +672,36 @@ def run_ours(args):
                      "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak32, "unit": "GB/s",
                                   "frac": ach32 / peak32, "launches": c32}}
 
+    # the same step in BF16x3 (the other split-precision mode: BF16 pieces, no better than 2^-16
+    # per product), same front, widths and timing, for the comparison of the two modes
+    bf16_path = None
+    if front is not None and prec == pkg.SIM_FP16X3_TMEM and not args.no_bf16_path:
+        fr_b = pkg.sim_front_create(h, split, kmax=args.kmax, precision=pkg.SIM_BF16X3)
+        layout_b, _ = choose_layout(rest, args.kmax, pkg.SIM_BF16X3)
+
+        def step_b():
+            plan = pkg.sim_plan_create(n, rest, kmax=args.kmax, precision=pkg.SIM_BF16X3)
+            if layout_b is not None:
+                pkg.sim_set_layout(h, layout_b)
+            pkg.sim_front_run(h, fr_b)
+            pkg.sim_apply_plan(h, plan)
+            out = pkg.sim_reduce(h)
+            pkg.sim_plan_destroy(plan)
+            return out
+        for _ in range(args.warmup):
+            step_b()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            nb_, sb_, _ = step_b()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msb = e0.elapsed_time(e1)
+        pkg.sim_front_destroy(fr_b)
+        bf16_path = {"value": float(amps) * circ.n_gates * args.steps / (msb / 1e3), "unit": UNIT,
+                     "ms_per_step": msb / args.steps, "precision": "bf16x3", "norm": nb_,
+                     "porter_thomas_2n_sum_p2": sb_, "norm_drift_per_pass": (nb_ - 1.0) / max(nblocks, 1)}
+
     matrix_bytes = 0
     plan = pkg.sim_plan_create(n, gates, kmax=args.kmax)
     for i in range(pkg.sim_plan_info(plan)[0]):
@@ -733,8 +790,18 @@ def run_ours(args):
         line["plain_path"] = plain_path
     if fp32_path:
         line["fp32_path"] = fp32_path
+    if bf16_path:
+        line["bf16x3_path"] = bf16_path
+    # a per-result error estimate that needs no oracle: the norm's drift from 1 per fused pass
+    line["check"]["norm_drift_per_pass"] = (norm - 1.0) / max(nblocks, 1)
+    if ws == 1 and not args.no_large:
+        # configuration 3: 33 qubits (64 GiB) held as 8 slices over 3 bits, phases with in-place
+        # permutation passes between them, in the default arithmetic and in FP32
+        line["syc33_sliced"] = {p: large_case_run("syc33_6x6m3_d20", p, local) for p in ("fp16x3_tmem", "fp32")}
     if ws == 1 and not args.no_serving:
-        line["serving"] = serving_run(args.serving_circuits, local, args.serving_rate)
+        # configuration 5: 2000 circuits, Poisson arrivals, each arithmetic beside its one-at-a-time run
+        line["serving"] = {p: serving_run(args.serving_circuits, local, r, p)
+                           for p, r in (("fp16x3_tmem", args.serving_rate), ("fp32", args.serving_rate_fp32))}
     if ws == 1 and not args.no_graphs:
         line["graph_replay"] = graph_replay_run(local)
     if ws == 1 and not args.no_cpu_baseline:
@@ -796,7 +863,7 @@ def kernel_case():
     print("kernel case done", flush=True)
 
 
-def large_case(name: str, precision: str = "fp16x3_tmem"):
+def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0) -> dict:
     """One run of a configuration from LARGE_CASES in SIM_FP16X3_TMEM at the case's block width, or
     in SIM_FP32 at k_max 4 (the resident one after a warm-up run; a streamed run takes seconds and
     runs once): wall time, gate updates/s, the apply kernels' time and bandwidth with their HBM
@@ -804,9 +871,7 @@ def large_case(name: str, precision: str = "fp16x3_tmem"):
     the final state's norm and 2^n sum p^2."""
     import paper_1910_09534_gb300 as pkg
     import syc_inputs as si
-    from paper_1910_09534_gb300 import build as pkg_build
 
-    pkg_build.build()
     cfg = LARGE_CASES[name]
     circ = si.workload_circuit(name, seed=0)
     n, s, kmax = circ.n_qubits, cfg["slice_bits"], cfg["kmax"]
@@ -823,9 +888,9 @@ def large_case(name: str, precision: str = "fp16x3_tmem"):
     host = cfg["store"] == "host"
     if host:
         h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3,
-                           store_device_regions=cfg["device_regions"])
+                           store_device_regions=cfg["device_regions"], device=device)
     else:
-        h = pkg.sim_create(n, s)
+        h = pkg.sim_create(n, s, device=device)
         pkg.sim_reset(h)
         pkg.sim_run_phases(h, ph)  # warm-up
         pkg.sim_sync(h)
@@ -844,30 +909,50 @@ def large_case(name: str, precision: str = "fp16x3_tmem"):
     pkg.sim_phases_destroy(ph)
     state_bytes = 8.0 * (1 << n)
     peak, peak_kind = measured_peaks()
+    ach = a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None
     line = {"case": name, "n_qubits": n, "gates": circ.n_gates,
             "store": ("host" if host else "device") + (f", {cfg['device_regions']} of {1 << s} regions in HBM"
                                                        if cfg["device_regions"] else ""),
             "slice_bits": s, "set_a": set_a, "set_b": set_b, "sets": cfg["sets"], "kmax": kmax,
             "precision": precision, "phases": n_phases, "blocks": n_blocks, "wall_s": wall,
             "gate_updates_per_s": float(1 << n) * circ.n_gates / wall,
-            "apply": {"launches": a_n, "ms": a_ms, "gbs": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None,
-                      "roofline": {"bound": "hbm", "achieved": a_bytes / (a_ms / 1e3) / 1e9 if a_ms else None,
-                                   "peak": peak, "unit": "GB/s",
-                                   "frac": a_bytes / (a_ms / 1e3) / 1e9 / peak if a_ms else None,
-                                   "peak_source": f"{peak_kind} hbm_gbs"}},
-            "norm": norm, "porter_thomas_2n_sum_p2": s2}
+            "apply": {"launches": a_n, "ms": a_ms, "gbs": ach,
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                   "frac": ach / peak if ach else None, "peak_source": f"{peak_kind} hbm_gbs",
+                                   "alg_bytes": a_bytes}},
+            "norm": norm, "porter_thomas_2n_sum_p2": s2,
+            "norm_drift_per_pass": (norm - 1.0) / max(n_blocks, 1)}
     if host:  # every phase moves the host regions out and back
         moved = 2 * n_phases * state_bytes * (1 - cfg["device_regions"] / (1 << s))
         line["host_link_gbs_combined"] = moved / wall / 1e9
     else:
         line["permute"] = {"passes": p_n, "ms": p_ms, "gbs_moved": p_bytes / (p_ms / 1e3) / 1e9 if p_ms else None}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def large_case(name: str, precision: str = "fp16x3_tmem"):
+    from paper_1910_09534_gb300 import build as pkg_build
+
+    pkg_build.build()
+    print(json.dumps(large_case_run(name, precision)), flush=True)
+
+
+def serving_case(args):
+    """Only the config-5 serving leg (no timed steps): one JSON line."""
+    from paper_1910_09534_gb300 import build as pkg_build
+
+    pkg_build.build()
+    prec = "fp32" if args.precision == "fp32" else "fp16x3_tmem"
+    rate = args.serving_rate if prec != "fp32" else args.serving_rate_fp32
+    print(json.dumps(serving_run(args.serving_circuits, 0, rate, prec)), flush=True)
 
 
 def main():
     args = parse()
     if args.large_case:
         large_case(args.large_case, "fp32" if args.precision == "fp32" else "fp16x3_tmem")
+    elif args.serving_only:
+        serving_case(args)
     elif args.kernel_case:
         kernel_case()
     elif args.oracle_table:

@@ -5,8 +5,8 @@
   plans (k <= 5, 3xFP16 on mma.sync and on tcgen05), and the contraction-deferral pipeline (the
   first 6 cycles as two tensors contracted into the state, FP32 and tcgen05), and the bench's
   configuration (that front, blocks of <= 6 qubits on tcgen05 in the chosen layout), every
-  amplitude.
-  Bound ||psi - psi_oracle||_2 <= 1e-5.
+  amplitude, and the same in BF16x3.
+  Bound ||psi - psi_oracle||_2 <= 1e-5 (BF16x3: its stated bound 1e-4).
 * 33 qubits (6x6 minus three corners; 64 GiB) held as 8 slices over the 3 top bits, run as
   alternating phases with in-place bit permutations between them (Sect. 4 in device memory):
   norm and Porter-Thomas, no oracle fits.  Its 28-qubit sub-lattice circuit (4x7, same depth)
@@ -21,6 +21,7 @@ import syc_inputs as si
 
 pytestmark = pytest.mark.gpu
 TOL_FP32 = 1e-5
+TOL_BF16X3 = 1e-4  # stated bound of the BF16x3 mode on whole circuits (about 2^-16 per product)
 
 
 @pytest.fixture(scope="module")
@@ -108,18 +109,21 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
             results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
         # the bench's configuration: the same front through the front runner, the rest as blocks of
         # <= 6 qubits on tcgen05, the state written in the layout sim_plan_layout chose for them
-        s = pkg.sim_split_create(n, gates[:front], side)
-        fr = pkg.sim_front_create(h, s, kmax=6, precision=pkg.SIM_FP16X3_TMEM)
-        plan = pkg.sim_plan_create(n, gates[front:], kmax=6, precision=pkg.SIM_FP16X3_TMEM)
-        perm, _, _ = pkg.sim_plan_layout(plan, n)
-        pkg.sim_set_layout(h, perm)
-        pkg.sim_front_run(h, fr)
-        pkg.sim_apply_plan(h, plan)
-        assert [int(b) for b in pkg.sim_info(h)[2]] == perm
-        results["bench_split6_k6_layout"] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
-        pkg.sim_plan_destroy(plan)
-        pkg.sim_front_destroy(fr)
-        pkg.sim_split_destroy(s)
+        # (and the same in BF16x3, the stated-bound split mode)
+        for name, prec in (("bench_split6_k6_layout", pkg.SIM_FP16X3_TMEM),
+                           ("bench_split6_k6_layout_bf16x3", pkg.SIM_BF16X3)):
+            s = pkg.sim_split_create(n, gates[:front], side)
+            fr = pkg.sim_front_create(h, s, kmax=6, precision=prec)
+            plan = pkg.sim_plan_create(n, gates[front:], kmax=6, precision=prec)
+            perm, _, _ = pkg.sim_plan_layout(plan, n)
+            pkg.sim_set_layout(h, perm)
+            pkg.sim_front_run(h, fr)
+            pkg.sim_apply_plan(h, plan)
+            assert [int(b) for b in pkg.sim_info(h)[2]] == perm
+            results[name] = (pkg.sim_amplitudes(h), pkg.sim_reduce(h))
+            pkg.sim_plan_destroy(plan)
+            pkg.sim_front_destroy(fr)
+            pkg.sim_split_destroy(s)
     finally:
         pkg.sim_destroy(h)
     import os
@@ -130,7 +134,7 @@ def test_30q_20cycles_every_amplitude_matches_oracle(pkg, oracle_mod):
     for name, (amps, (norm, s2, xeb)) in results.items():
         err = chunked_err(amps, want)
         print(f"30q {name}: ||psi - psi_oracle||_2 = {err:.3e}, norm {norm:.9f}, 2^n sum p^2 {s2:.5f}")
-        assert err <= TOL_FP32, (name, err)
+        assert err <= (TOL_BF16X3 if name.endswith("bf16x3") else TOL_FP32), (name, err)
         assert abs(s2 - os2) < 1e-3
 
 
@@ -146,10 +150,11 @@ def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
     import os
     oracle_mod.set_threads(os.cpu_count() or 1)
     want = oracle_mod.run_circuit(circ28)
-    bounds = {"fp32": 1e-5, "fp16x3": 1e-5, "fp16x3_tmem": 1e-5, "tf32x3": 1e-5, "tf32": 5e-2}
+    bounds = {"fp32": 1e-5, "fp16x3": 1e-5, "fp16x3_tmem": 1e-5, "tf32x3": 1e-5, "tf32": 5e-2,
+              "bf16x3": TOL_BF16X3}
     for name, prec, kmax in (("fp32", pkg.SIM_FP32, 4), ("fp16x3", pkg.SIM_FP16X3, 5),
                              ("fp16x3_tmem", pkg.SIM_FP16X3_TMEM, 5), ("tf32x3", pkg.SIM_TF32X3, 5),
-                             ("tf32", pkg.SIM_TF32, 5)):
+                             ("tf32", pkg.SIM_TF32, 5), ("bf16x3", pkg.SIM_BF16X3, 5)):
         out, _, _, _ = run_sliced_phases(pkg, circ28, 3, prec, kmax)
         err = chunked_err(out, want)
         print(f"28q sub-lattice {name} (kmax {kmax}): ||psi - psi_oracle||_2 = {err:.3e}")
