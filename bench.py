@@ -50,7 +50,7 @@ NOMINAL_DENSE_F16_TFLOPS = 2250.0  # GB300 dense FP16/BF16 tensor rate, datashee
 # rate on GB300 (all circuits at t = 0), so that the server keeps up and its latency is a queueing
 # figure, not a backlog
 SERVING_RATE_SPLIT = 87.5
-SERVING_RATE_FP32 = 30.0
+SERVING_RATE_FP32 = 35.0
 METRIC = "amplitude-updates/s"
 UNIT = "amp-updates/s"
 

@@ -9,8 +9,9 @@
 // (TMA) engine into shared memory in address order.  Where bit 7 is not a target the runs are
 // only 1 KiB, and the kernel takes 256-group tiles (two M = 128 sub-tiles, row bit 7 = sub-tile)
 // so that every copy moves 2 KiB (measured: 1 KiB copies cap the kernel at ~74% of the 2 KiB
-// rate).  6-qubit blocks keep 128-group tiles (two accumulator sets of 256 columns fill the tensor
-// memory) in a 2-stage ring beside 64 KiB of R^T.
+// rate).  6-qubit blocks keep 128-group tiles in a 2-stage ring beside 64 KiB of R^T; they run on
+// k_apply_tc6a below, which keeps their A operand in tensor memory so that a stage is free as soon
+// as it has been read (the pipeline described next is that of k = 4 and 5).
 //
 // One persistent CTA per SM, warp-specialised, tiles pipelined through a ring of S shared-memory
 // stages (one tile each, 128 x 2^k complex64):
@@ -55,6 +56,10 @@
 
 namespace sycsim {
 namespace {
+
+#ifndef SYCSIM_TC6_ATMEM
+#define SYCSIM_TC6_ATMEM 1  // 6-qubit blocks: A operand in tensor memory (k_apply_tc6a)
+#endif
 
 #ifndef SYCSIM_TC5_RUN_LOG2_MAX
 #define SYCSIM_TC5_RUN_LOG2_MAX 8  // 2 KiB copies: measured fastest (1 KiB: -26%, 4 KiB: -9%)
@@ -568,6 +573,278 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(L::TMEM_COLS));
 }
 
+// ---- 6-qubit blocks with the A operand in tensor memory ----------------------------------------
+// A 6-qubit tile (128 groups x 64 members) fills a 64 KiB stage, and R^T hi/lo take another 64 KiB,
+// so only two stages fit; writing the A operand back into the stage keeps each stage busy from its
+// load through the conversion and the MMAs.  Here the converters put A (hi, lo) into tensor memory
+// instead (tcgen05.st; one row per TMEM lane, column c = member c as a packed (re, im) pair, the
+// K order of R^T), and release the stage as soon as they have read it: the next tile's copies start
+// while this one is still being multiplied.  Tensor memory: A buffers for two tiles (hi 64 | lo 64
+// columns each) at columns 0-255, one accumulator set (main 128 | corrections 128) at 256-511.
+// Per tile i (stage i % 2, A buffer i % 2, scale slot i % 4):
+//   loader: wait stage_free of tile i - 2, load the runs (loaded counts bytes);
+//   converters: wait mma_done of tile i - 2 (A buffer free) and loaded, read the rows, combine the
+//     halves' maxima, arrive stage_free, write the row scales (arrive scales), split hi / lo into
+//     the A buffer, arrive a_full;
+//   MMA thread: wait a_full and tmem_free of tile i - 1, issue, commit to mma_done;
+//   drainers: wait mma_done and scales, read the accumulators 16 columns at a time, arrive tmem_free
+//     after the last read, store from registers.
+// Every barrier's next phase needs the waiter's own progress first (e.g. the converters of tile
+// i + 4 rewrite scale slot i % 4 only after the MMAs of tile i + 2, which wait for the drain of
+// tile i + 1), so no parity wait can miss a phase.
+constexpr int kTc6Stage = kRows * 64 * 8;        // 64 KiB of raw amplitudes
+constexpr int kTc6Stages = 2;
+constexpr int kTc6BBytes = 8 * (128 * 32);       // R^T hi (or lo): 8 K-slices of 128 x 16 FP16
+constexpr int kTc6Smem = kTc6Stages * kTc6Stage + 2 * kTc6BBytes;
+
+__device__ __forceinline__ void umma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                            uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+            ta),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+template <bool BF>
+__device__ __forceinline__ void split_pair(float re, float im, uint32_t &hi, uint32_t &lo)
+{
+    if constexpr (BF) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(re - hf.x, im - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(re, im);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(re - hf.x, im - hf.y);
+        hi = *reinterpret_cast<const uint32_t *>(&h);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+    }
+}
+
+template <bool LOWT, bool BF>
+__global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
+{
+    constexpr int D = 64, KS = 8, N = 128, S = kTc6Stages, H = D / 2;  // H members per thread
+    constexpr int B_SLICE = N * 32;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *bHi = sm + S * kTc6Stage, *bLo = bHi + kTc6BBytes;
+    __shared__ __align__(8) uint64_t loaded[S], stage_free[S], a_full[2], mma_done[2], tmem_free, scales[4];
+    __shared__ float row_inv[4][kRows];
+    __shared__ float amax_part[2][kRows];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n_runs = (1 << (6 + 7)) >> g.run_log2;
+    const uint32_t run_bytes = 8u << g.run_log2;
+
+    {
+        const uint32_t *src = g.bmat;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(bHi);
+        for (int i = tid; i < (2 * kTc6BBytes) / 4; i += blockDim.x) dst[i] = src[i];
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // B is read by the MMA unit
+    }
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&loaded[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&stage_free[st])), "r"(kConv)
+                         : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&a_full[b])), "r"(kConv) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mma_done[b])) : "memory");
+        }
+        for (int j = 0; j < 4; ++j)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&scales[j])), "r"(kConv) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&tmem_free)), "r"(kDrain) : "memory");
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(&tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    volatile int *ab = &abort_flag;
+    auto give_up = [&]() {
+        *ab = 1;
+        atomicExch(g.err, 1);
+    };
+
+    if (warp < kLoadWarp) {
+        // ---------------- converters: stage -> registers -> A (hi, lo) in tensor memory ----------------
+        const int row = tid & (kRows - 1), half = tid >> 7;
+        uint32_t rx = 0;
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            if ((row >> j) & 1) rx |= g.ridx[j];
+        // one target below bit 4 (member bit 0): register m holds member (H half + m) ^ mu for
+        // conflict-free stage reads; the pairs are swapped back before the columns are written
+        uint32_t mu = 0, mux = 0;
+        if constexpr (LOWT) {
+            mu = (row >> 3) & 1u;
+            if (mu) mux = g.midx[1];
+        }
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;  // this warp's TMEM lanes
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int st = i % S, b = i & 1, j = i & 3;
+            const bool ok = (i < 2 || mbar_wait_abort(smem_u32(&mma_done[b]), ((i - 2) >> 1) & 1, ab)) &&
+                            mbar_wait_abort(smem_u32(&loaded[st]), (i / S) & 1, ab);
+            if (!bar_and(1, kConv, ok)) {
+                give_up();
+                break;
+            }
+            const uint8_t *stage = sm + st * kTc6Stage;
+            float2 x[H];
+            float amax = 0.f;
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                x[m] = *reinterpret_cast<const float2 *>(stage + 8 * ((g.midx[H * half + m] ^ mux) | rx));
+                amax = fmaxf(amax, fmaxf(fabsf(x[m].x), fabsf(x[m].y)));
+            }
+            amax_part[half][row] = amax;
+            bar_sync(1, kConv);  // both halves' maxima; every row of the stage read
+            mbar_arrive(smem_u32(&stage_free[st]));
+            amax = fmaxf(amax_part[0][row], amax_part[1][row]);
+            int e = 0;
+            frexpf(amax, &e);
+            const int sh = amax > 0.f ? max(-100, min(100, 14 - e)) : 0;
+            const float sc = ldexpf(1.f, sh);
+            if (half == 0) row_inv[j][row] = ldexpf(1.f, -sh);
+            mbar_arrive(smem_u32(&scales[j]));
+            const uint32_t ta = tmem + lane_off + (uint32_t)(b * 128 + half * H);
+#pragma unroll
+            for (int c = 0; c < H / 16; ++c) {
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m) split_pair<BF>(x[16 * c + m].x * sc, x[16 * c + m].y * sc, hi[m], lo[m]);
+                if constexpr (LOWT) {
+                    if (mu) {
+#pragma unroll
+                        for (int m = 0; m < 16; m += 2) {
+                            swap_u32(hi[m], hi[m + 1]);
+                            swap_u32(lo[m], lo[m + 1]);
+                        }
+                    }
+                }
+                tmem_st16(ta + 16 * c, hi);
+                tmem_st16(ta + 64 + 16 * c, lo);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(smem_u32(&a_full[b]));
+        }
+    } else if (warp == kLoadWarp) {
+        // ---------------- bulk loads (one run per lane) ----------------
+        const int lane = tid & 31;
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int st = i % S;
+            const bool ok = i < (uint32_t)S || mbar_wait_abort(smem_u32(&stage_free[st]), (i / S - 1) & 1, ab);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) give_up();
+                break;
+            }
+            const uint64_t base = insert_zero_bits_g(tile * kRows, g.tpos, 6);
+            const uint32_t bar = smem_u32(&loaded[st]);
+            if (lane == 0) mbar_expect_tx(bar, kTc6Stage);  // before any of the copies can complete
+            __syncwarp();
+            const uint32_t dst = smem_u32(sm + st * kTc6Stage);
+            for (int c = lane; c < n_runs; c += 32) bulk_load(dst + c * run_bytes, g.psi + base + g.off_run[c], run_bytes, bar);
+        }
+        if (lane == 0)
+            for (uint32_t j = i > (uint32_t)S ? i - S : 0; j < i; ++j) mbar_wait_own(smem_u32(&loaded[j % S]), (j / S) & 1);
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer: A from tensor memory, B (R^T) from shared memory ----------------
+        if ((tid & 31) == 0) {
+            const uint32_t idesc = (1u << 4) | (BF ? (1u << 7) | (1u << 10) : 0u) | ((uint32_t)(N >> 3) << 17) |
+                                   ((uint32_t)(kRows >> 4) << 24);
+            const uint32_t acc = tmem + 256;  // main at 256, corrections at 256 + N
+            uint32_t i = 0;
+            for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+                const int b = i & 1;
+                if (!mbar_wait_abort(smem_u32(&a_full[b]), (i >> 1) & 1, ab) ||
+                    (i >= 1 && !mbar_wait_abort(smem_u32(&tmem_free), (i - 1) & 1, ab))) {
+                    give_up();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t aHi = tmem + b * 128, aLo = aHi + 64;  // 8 columns per K-slice of 16
+#pragma unroll
+                for (int s = 0; s < KS; ++s)
+                    umma_f16_ta(acc, aHi + 8 * s, umma_desc(smem_u32(bHi + s * B_SLICE)), idesc, s > 0);
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    umma_f16_ta(acc + N, aHi + 8 * s, umma_desc(smem_u32(bLo + s * B_SLICE)), idesc, s > 0);
+                    umma_f16_ta(acc + N, aLo + 8 * s, umma_desc(smem_u32(bHi + s * B_SLICE)), idesc, 1);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&mma_done[b]))
+                             : "memory");
+            }
+            if (i > 0) mbar_wait_own(smem_u32(&mma_done[(i - 1) & 1]), ((i - 1) >> 1) & 1);
+        }
+    } else {
+        // ---------------- drainers: accumulators -> registers -> global ----------------
+        const int q = warp & 3;                        // TMEM lane quarter this warp may read
+        const int half = (warp - kMmaWarp - 1) >> 2;   // warps 10-13: members 0..H-1; 14-17: H..D-1
+        const int row = 32 * q + (tid & 31);
+        uint64_t ro = 0;  // address offset of this row within the tile
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            if ((row >> j) & 1) ro += g.roff[j];
+        uint32_t i = 0;
+        for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
+            const int b = i & 1, j = i & 3;
+            const bool ok = mbar_wait_abort(smem_u32(&mma_done[b]), (i >> 1) & 1, ab) &&
+                            mbar_wait_abort(smem_u32(&scales[j]), (i >> 2) & 1, ab);
+            if (!bar_and(2, kDrain, ok)) {  // uniform: tcgen05.ld below needs whole warps
+                give_up();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            float2 *const dst = g.psi + insert_zero_bits_g(tile * kRows, g.tpos, 6) + ro;
+            const float inv = row_inv[j][row];
+            const uint32_t lane_base = tmem + 256 + ((uint32_t)(32 * q) << 16) + half * (N / 2);
+#pragma unroll
+            for (int c0 = 0; c0 < N / 2; c0 += 16) {
+                float a[16], c[16];
+                tmem_ld16(lane_base + c0, a);
+                tmem_ld16(lane_base + N + c0, c);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (c0 == N / 2 - 16) {
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    mbar_arrive(smem_u32(&tmem_free));
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    __stcs(dst + g.moff[H * half + c0 / 2 + m],
+                           make_float2((a[2 * m] + c[2 * m]) * inv, (a[2 * m + 1] + c[2 * m + 1]) * inv));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+}
+
 uint16_t half_bits(float f)
 {
     const __half h = __float2half_rn(f);
@@ -690,6 +967,28 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <bool LOWT, bool BF>
+int launch_tc6a(const Tc5Geom &g, int nbits, cudaStream_t st)
+{
+    auto kern = k_apply_tc6a<LOWT, BF>;
+    static std::atomic<uint64_t> smem_done{0};
+    if (!smem_opt_in(kern, kTc6Smem, smem_done)) return -1;
+    static const LaunchCfg cfg = [&] {
+        LaunchCfg c;
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return c;
+        if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return c;
+        c.ok = true;
+        return c;
+    }();
+    if (!cfg.ok) return -1;
+    Tc5Geom gg = g;
+    gg.n_tiles = 1ull << (nbits - 6 - 7);
+    const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)cfg.sms);
+    kern<<<(unsigned)grid, kThreadsTc5, kTc6Smem, st>>>(gg);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Geometry of the block and launch, B (hi, lo) already in device memory at d_b.
 template <int K, bool BF>
 int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const uint32_t *d_b, cudaStream_t st)
@@ -704,8 +1003,13 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
     if (g.nlow > (K >= 5 ? 1 : 0)) return -2;  // not eligible (see tcgen05_eligible)
     if constexpr (K == 6) {  // 128-group tiles only: two 256-column accumulator sets fill the TMEM
         if (tile_geometry<K>(nbits, tpos, 7, g) < 0) return -1;
+#if SYCSIM_TC6_ATMEM
+        if (g.nlow > 0) return launch_tc6a<true, BF>(g, nbits, st);
+        return launch_tc6a<false, BF>(g, nbits, st);
+#else
         if (g.nlow > 0) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st);
         return launch_tc5_kr<K, 1, false, BF>(g, nbits, st);
+#endif
     } else {
         // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below
         // it); otherwise 256-group tiles, whose 8th row bit is bit 7, so that every bulk copy
