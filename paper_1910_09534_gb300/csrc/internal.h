@@ -70,6 +70,14 @@ struct sim_s {
     cudaEvent_t frag_ev[kFragSlots] = {};
     int frag_next = 0;
 
+    // a whole plan's staged block operands (sim_apply_plan), uploaded in one copy: two slots, each
+    // a pinned source and its device copy, reused once the plan that last used it has run
+    char *h_plan[2] = {};
+    char *d_plan[2] = {};
+    size_t plan_bytes[2] = {};
+    cudaEvent_t plan_ev[2] = {};
+    int plan_next = 0;
+
     // profiling: CUDA-event pairs around kernel launches, per kernel class
     struct ProfSlot {
         cudaEvent_t a = nullptr, b = nullptr;

@@ -9,6 +9,7 @@
 // that adds the fewest new qubits while it fits in k_max qubits.  Block matrices are composed in
 // FP64 on the block's own qubits (ascending), later gates multiplying from the left.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -556,15 +557,80 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
     if (h->store != SIM_STORE_DEVICE)
         return fail(h, SIM_E_UNSUPPORTED, "sim_apply_plan: host-store state: use sim_run_phase");
     SIM_DEVICE_SCOPE(h, h->device);
-    static thread_local float2 mat[4096];
-    int tpos[kMaxK];
-    for (auto &b : p->blocks) {
-        const int k = (int)b.qubits.size();
-        int rc = prepare_block(h, k, b.qubits.data(), b.mat.data(), tpos, mat);
+    // Every block's operands (tensor-core R^T fragments, 6-qubit matrices) are built on the host and
+    // uploaded in one copy before the first launch, then every block is launched from them: the
+    // calling thread never waits for the device inside the plan (a per-block staging ring would make
+    // it wait for the block launched a ring's length earlier), and a plan costs one small copy.
+    struct Prep {
+        int k;
+        int tpos[kMaxK];
+        size_t moff, off, bytes;
+    };
+    static thread_local std::vector<Prep> prep;
+    static thread_local std::vector<float2> mats;
+    const size_t nb = p->blocks.size();
+    prep.resize(nb);
+    size_t mtot = 0, total = 0;
+    for (size_t i = 0; i < nb; i++) mtot += (size_t)1 << (2 * p->blocks[i].qubits.size());
+    mats.resize(mtot);
+    mtot = 0;
+    for (size_t i = 0; i < nb; i++) {
+        const PlanBlock &b = p->blocks[i];
+        Prep &pb = prep[i];
+        pb.k = (int)b.qubits.size();
+        pb.moff = mtot;
+        const int rc = prepare_block(h, pb.k, b.qubits.data(), b.mat.data(), pb.tpos, mats.data() + mtot);
         if (rc != SIM_OK) return rc;
-        rc = enqueue_block(h, k, tpos, mat, p->precision);
-        if (rc != SIM_OK) return rc;
+        mtot += (size_t)1 << (2 * pb.k);
+        pb.bytes = block_staged_bytes(h->n, pb.k, pb.tpos, p->precision);
+        pb.off = total;
+        total += (pb.bytes + 255) & ~size_t(255);
     }
+    char *d_ops = nullptr;
+    int slot = -1;
+    if (total) {
+        slot = h->plan_next;
+        h->plan_next ^= 1;
+        if (!h->plan_ev[slot]) SIM_CUDA_TRY(h, cudaEventCreateWithFlags(&h->plan_ev[slot], cudaEventDisableTiming));
+        // the plan that used this slot two calls ago has been uploaded and run
+        SIM_CUDA_TRY(h, cudaEventSynchronize(h->plan_ev[slot]));
+        if (h->plan_bytes[slot] < total) {
+            if (h->h_plan[slot]) cudaFreeHost(h->h_plan[slot]);
+            if (h->d_plan[slot]) cudaFree(h->d_plan[slot]);
+            h->h_plan[slot] = nullptr;
+            h->d_plan[slot] = nullptr;
+            h->plan_bytes[slot] = 0;
+            const size_t want = total + total / 2;
+            if (cudaHostAlloc(reinterpret_cast<void **>(&h->h_plan[slot]), want, cudaHostAllocDefault) != cudaSuccess) {
+                h->h_plan[slot] = nullptr;
+                return fail(h, SIM_E_NOMEM_HOST, "sim_apply_plan: staging buffer");
+            }
+            if (cudaMalloc(reinterpret_cast<void **>(&h->d_plan[slot]), want) != cudaSuccess) {
+                h->d_plan[slot] = nullptr;
+                return fail(h, SIM_E_NOMEM_DEV, "sim_apply_plan: staging buffer");
+            }
+            h->plan_bytes[slot] = want;
+        }
+        for (size_t i = 0; i < nb; i++)
+            if (prep[i].bytes)
+                block_build_staged(h->n, prep[i].k, prep[i].tpos, mats.data() + prep[i].moff, p->precision,
+                                   h->h_plan[slot] + prep[i].off);
+        SIM_CUDA_TRY(h, cudaMemcpyAsync(h->d_plan[slot], h->h_plan[slot], total, cudaMemcpyHostToDevice, h->stream));
+        d_ops = h->d_plan[slot];
+    }
+    const double pass_bytes = 16.0 * std::ldexp(1.0, h->n);
+    for (size_t i = 0; i < nb; i++) {
+        const Prep &pb = prep[i];
+        const int ps = prof_begin(h, SIM_PROF_APPLY, pass_bytes, h->stream);
+        const int rc = launch_block_staged(h, h->d_state, h->n, pb.k, pb.tpos, mats.data() + pb.moff, p->precision,
+                                           d_ops ? d_ops + pb.off : nullptr, h->stream);
+        prof_end(h, ps, h->stream);
+        if (rc != SIM_OK) {
+            if (slot >= 0) cudaEventRecord(h->plan_ev[slot], h->stream);
+            return rc;
+        }
+    }
+    if (slot >= 0) SIM_CUDA_TRY(h, cudaEventRecord(h->plan_ev[slot], h->stream));
     return SIM_OK;
 }
 

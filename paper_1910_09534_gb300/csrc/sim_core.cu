@@ -94,6 +94,11 @@ static void release(sim_t *h)
     for (auto &e : h->mat6_ev)
         if (e) cudaEventDestroy(e);
     if (h->d_frag) cudaFree(h->d_frag);
+    for (int i = 0; i < 2; i++) {
+        if (h->h_plan[i]) cudaFreeHost(h->h_plan[i]);
+        if (h->d_plan[i]) cudaFree(h->d_plan[i]);
+        if (h->plan_ev[i]) cudaEventDestroy(h->plan_ev[i]);
+    }
     if (h->d_errflag) cudaFree(h->d_errflag);
     if (h->d_contract) cudaFree(h->d_contract);
     if (h->h_frag) cudaFreeHost(h->h_frag);
