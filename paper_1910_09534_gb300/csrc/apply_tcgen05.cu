@@ -710,17 +710,18 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
                 give_up();
                 break;
             }
+            // two passes over this thread's half-row: the maximum first, then 16 members at a
+            // time converted straight from the stage (a register budget of 96 per thread: 18 warps
+            // share four 16,384-register sub-partitions, five warps on two of them)
             const uint8_t *stage = sm + st * kTc6Stage;
-            float2 x[H];
             float amax = 0.f;
 #pragma unroll
             for (int m = 0; m < H; ++m) {
-                x[m] = *reinterpret_cast<const float2 *>(stage + 8 * ((g.midx[H * half + m] ^ mux) | rx));
-                amax = fmaxf(amax, fmaxf(fabsf(x[m].x), fabsf(x[m].y)));
+                const float2 v = *reinterpret_cast<const float2 *>(stage + 8 * ((g.midx[H * half + m] ^ mux) | rx));
+                amax = fmaxf(amax, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
             amax_part[half][row] = amax;
-            bar_sync(1, kConv);  // both halves' maxima; every row of the stage read
-            mbar_arrive(smem_u32(&stage_free[st]));
+            bar_sync(1, kConv);  // both halves' maxima
             amax = fmaxf(amax_part[0][row], amax_part[1][row]);
             int e = 0;
             frexpf(amax, &e);
@@ -733,7 +734,11 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
             for (int c = 0; c < H / 16; ++c) {
                 uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int m = 0; m < 16; ++m) split_pair<BF>(x[16 * c + m].x * sc, x[16 * c + m].y * sc, hi[m], lo[m]);
+                for (int m = 0; m < 16; ++m) {
+                    const float2 v =
+                        *reinterpret_cast<const float2 *>(stage + 8 * ((g.midx[H * half + 16 * c + m] ^ mux) | rx));
+                    split_pair<BF>(v.x * sc, v.y * sc, hi[m], lo[m]);
+                }
                 if constexpr (LOWT) {
                     if (mu) {
 #pragma unroll
@@ -746,6 +751,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
                 tmem_st16(ta + 16 * c, hi);
                 tmem_st16(ta + 64 + 16 * c, lo);
             }
+            mbar_arrive(smem_u32(&stage_free[st]));  // the stage has been read for the last time
             asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(smem_u32(&a_full[b]));

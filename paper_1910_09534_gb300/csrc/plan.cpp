@@ -396,9 +396,10 @@ double pass_ms(int k, const int *tpos, int precision)
     }
     if (tmem_mode(precision)) {
         // tcgen05 with <= 1 target below bit 4 (k = 5, 6) or none (k = 4), else mma.sync 3xFP16;
-        // k = 6 (A operand in tensor memory) runs 2.69-2.73 ms whatever the pattern; k = 5 tiles
-        // move 2 KiB runs once a target sits at bit 7 or below, else twice the groups
-        if (k == 6) return low4 >= 2 ? 5.10 : 2.71;
+        // k = 6 (A operand in tensor memory) runs 2.65 ms with one target below bit 4 and
+        // 2.69-2.72 ms otherwise; k = 5 tiles move 2 KiB runs once a target sits at bit 7 or below,
+        // else twice the groups
+        if (k == 6) return low4 >= 2 ? 5.10 : (low4 == 1 ? 2.65 : 2.70);
         if (k == 5) return low4 >= 2 ? 2.70 : (le7 ? 2.55 : 2.63);
         if (k == 4) return low4 >= 1 ? 2.68 : 2.55;
         return 2.45;
