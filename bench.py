@@ -195,7 +195,7 @@ def whole_job_rate(units_per_rank: float, world_size: int, seconds_max: float) -
 
 
 TCGEN05_TRAFFIC_GB = 4 * (2.147897 + 2.088273)  # k_apply_tcgen05<5, 2, 0>, ncu at 2^28 amplitudes
-TCGEN05_K6_TRAFFIC_GB = 4 * (2.147802 + 2.085992)  # k_apply_tcgen05<6, 1, 0>, ncu at 2^28 amplitudes
+TCGEN05_K6_TRAFFIC_GB = 4 * (2.148062 + 2.087781)  # k_apply_tc6a<1, 0>, ncu at 2^28 amplitudes
 
 
 def measured_peaks(key: str = "hbm_gbs"):
@@ -742,7 +742,7 @@ def run_ours(args):
                      # 17.18 GB algorithmic; null for configurations without that capture
                      "traffic": ((TCGEN05_K6_TRAFFIC_GB if args.kmax == 6 else TCGEN05_TRAFFIC_GB)
                                  if args.precision == "fp16x3_tmem" and n == 30 else None),
-                     "traffic_kernel": (("k_apply_tcgen05<6, 1, 0>" if args.kmax == 6 else "k_apply_tcgen05<5, 2, 0>")
+                     "traffic_kernel": (("k_apply_tc6a<1, 0>" if args.kmax == 6 else "k_apply_tcgen05<5, 2, 0>")
                                         if args.precision == "fp16x3_tmem" else None),
                      "kernel": "fused apply, all launches (" + {
                          "fp16x3_tmem": "k_apply_tcgen05 / k_apply_mma_f16x3 / k_apply_reg / k_apply_direct",
