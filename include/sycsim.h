@@ -469,6 +469,27 @@ int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan_opts *o, s
 int sim_front_run(sim_t *out, sim_front_t *f);
 int sim_front_destroy(sim_front_t *f);
 
+/* ---- a state sharded over global qubits on 2^g ranks (Sect. 4) ------------------------------
+ * Sect. 4 splits the state over many memories by "global" qubits, applies gates to the local ones
+ * and reorganises the memory layout between phases with an all-to-all (the Appendix's `all2all`
+ * lines), so that the next phase's gates find their qubits local.  This call is the schedule of
+ * one such exchange; the data moves through the caller's collective library (NCCL or gloo
+ * all-to-all with per-rank split sizes) and, locally, sim_permute.
+ * Layout: position p < n - g is bit p of a rank's local index, position n - g + j bit j of the
+ * rank number.  bit_of[q] = current position of qubit q (a bijection on 0..n-1); next_global: the
+ * g qubits that must be global afterwards (any order).  Writes local_perm[p] (p < n - g): the new
+ * local position of the amplitude bit now at local position p -- apply it to every rank's local
+ * state first (the moving qubits O end at the top m local positions); bit_of_after[q]: the
+ * positions after the all-to-all; *chunk_mask (may be NULL): the rank bits R that change.  The
+ * all-to-all: a rank's local state is 2^m contiguous chunks of 2^(n-g-m) amplitudes; chunk c goes
+ * to the rank that equals the sender outside R and holds c in R (bits of c in R's ascending order),
+ * and the chunk from rank s is placed at index (s's bits in R); every other rank exchanges nothing.
+ * Returns m (0: nothing moves, no collective needed) or a negative SIM_E_* code (SIM_E_INVAL for a
+ * non-bijective bit_of, a repeated or out-of-range next_global entry, or g outside 0 .. n/2).
+ * Host only. */
+int sim_shard_exchange_plan(int n_qubits, int global_bits, const int *bit_of, const int *next_global,
+                            int *local_perm, int *bit_of_after, uint64_t *chunk_mask);
+
 /* ---- checkpoint / resume (not in the paper) --------------------------------
  * Save the whole state to a file, and load it back, e.g. at a phase boundary of a long streamed
  * run (sim_phases_get + sim_run_phase), to resume it in another process.  The file holds a header

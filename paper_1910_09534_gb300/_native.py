@@ -147,6 +147,8 @@ _SIGS = {
     "sim_split_gates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "sim_shard_exchange_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_split_choose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "sim_contract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -637,6 +639,18 @@ def srv_stats(srv) -> dict:
     st = SrvStats()
     _srv_check(lib().srv_stats(srv, ctypes.byref(st)), srv)
     return {f: getattr(st, f) for f, _ in SrvStats._fields_}
+
+
+def sim_shard_exchange_plan(n_qubits: int, global_bits: int, bit_of, next_global):
+    """Schedule of one exchange of a sharded state: (m, local_perm, bit_of_after, chunk_mask)."""
+    b = np.ascontiguousarray(bit_of, dtype=np.int32)
+    ng = np.ascontiguousarray(next_global, dtype=np.int32)
+    lp = np.zeros(max(n_qubits - global_bits, 1), dtype=np.int32)
+    after = np.zeros(n_qubits, dtype=np.int32)
+    mask = ctypes.c_uint64()
+    m = _check(lib().sim_shard_exchange_plan(n_qubits, global_bits, _ptr(b), _ptr(ng) if ng.size else None,
+                                             _ptr(lp), _ptr(after), ctypes.byref(mask)))
+    return m, [int(x) for x in lp[: n_qubits - global_bits]], [int(x) for x in after], int(mask.value)
 
 
 def exported_symbols() -> list:

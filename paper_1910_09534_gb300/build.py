@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsycsim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["sim_core.cu", "apply.cu", "permute.cu", "reduce.cu", "store.cu", "apply_tc.cu", "apply_tcgen05.cu", "serve.cu", "gates.cpp", "plan.cpp", "split.cpp", "contract.cu"]
+SOURCES = ["sim_core.cu", "apply.cu", "permute.cu", "reduce.cu", "store.cu", "apply_tc.cu", "apply_tcgen05.cu", "serve.cu", "gates.cpp", "plan.cpp", "split.cpp", "contract.cu",
+           "shard.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
                  "--expt-relaxed-constexpr", "-I" + INCLUDE]
