@@ -333,6 +333,15 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
     for h in handles.values():
         pkg.sim_destroy(h)
     srv = pkg.srv_create(device=device, precision=prec)
+    # the server's autotuner (srv_autotune), before the clock starts: one sample circuit per size
+    # above the packing size and depth class, seeds outside the stream's
+    tsamples = [si.sycamore_circuit(si.near_square_grid(n), d, seed=70000 + 31 * n + d)
+                for n in range(21, 31) for d in (10, 14, 18)]
+    t_tune = time.perf_counter()
+    picks = pkg.srv_autotune(srv, [(c.n_qubits, pkg.gates_array(c)) for c in tsamples])
+    t_tune = time.perf_counter() - t_tune
+    tuned = {f"{c.n_qubits}q_{c.n_gates}g": {"kmax": k, "front": f, "ms": round(ms, 3)}
+             for c, (k, f, ms) in zip(tsamples, picks)}
     t0 = time.perf_counter()
     tickets = []
     for at, c, g in zip(arrivals, circs, gates):
@@ -360,7 +369,10 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
             "one_at_a_time_circuits_per_s": count / seq_s,
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
             "one_at_a_time_p99_ms": statistics.quantiles(seq_done, n=100)[98],
-            "arithmetic": arith, "server_front": front}
+            "arithmetic": arith, "server_front": front,
+            "autotune": {"by": "srv_autotune: k_max 4-6 (and the front or not, tcgen05 modes) measured per size "
+                               "and depth class on one sample each, before the timed leg",
+                         "seconds": t_tune, "choices": tuned}}
 
 
 def graph_replay_run(device: int, runs: int = 30):

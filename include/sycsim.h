@@ -512,7 +512,8 @@ int sim_state_load(sim_t *h, const char *path);
  * circuits with n <= small_n are packed into one kernel launch (one thread block
  * per circuit: reset, every block, reduction); larger ones run on `slots`
  * streams with stream-ordered memory.  A circuit always takes the same path and
- * plan, so its result does not depend on what else is in flight. */
+ * plan, so its result does not depend on what else is in flight (srv_autotune fixes the
+ * choices for the sizes it measured before any is served). */
 typedef struct srv_s srv_t;
 
 typedef struct srv_opts {
@@ -560,6 +561,20 @@ int srv_wait(srv_t *s, uint64_t ticket, int timeout_ms, double *norm, double *su
 
 /* Counters and the latency distribution of completed circuits. */
 int srv_stats(srv_t *s, srv_stats_t *out);
+
+/* Autotuner of the server (not in the paper): for each sample circuit above small_n, measures on a
+ * scratch state of its size every candidate the server could run it with -- block width k_max 4,
+ * 5 and 6, and in SIM_FP16X3_TMEM / SIM_BF16X3 from 22 qubits also with and without the
+ * contraction-deferral front (unless front_pairs < 0) -- planned as srv_submit plans (the layout
+ * sim_plan_layout picks), each run twice from the start state, the second timed with CUDA events;
+ * the fastest is cached for the sample's (n, depth class) and used by every later srv_submit of a
+ * circuit of that size and class (depth class: gates per qubit < 18, < 24, or more; an explicit
+ * kmax in srv_opts still wins).  Writes the choice per sample (kmax_out, front_out: 0 / 1, ms_out:
+ * its device time; 0 for samples the server packs); any output may be NULL.  Synchronous; call it
+ * while the server is idle (its scratch states, 8 * 2^n bytes, are allocated outside the budget,
+ * and its timings assume an idle device).  gates[i] points at sample i's n_gates[i] records. */
+int srv_autotune(srv_t *s, int n_samples, const int *n_qubits, const int *n_gates, const sim_gate *const *gates,
+                 int *kmax_out, int *front_out, double *ms_out);
 
 #ifdef __cplusplus
 }

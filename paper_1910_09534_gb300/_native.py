@@ -147,6 +147,8 @@ _SIGS = {
     "sim_split_gates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_canonical": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "srv_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_shard_exchange_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_split_choose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -651,6 +653,23 @@ def sim_shard_exchange_plan(n_qubits: int, global_bits: int, bit_of, next_global
     m = _check(lib().sim_shard_exchange_plan(n_qubits, global_bits, _ptr(b), _ptr(ng) if ng.size else None,
                                              _ptr(lp), _ptr(after), ctypes.byref(mask)))
     return m, [int(x) for x in lp[: n_qubits - global_bits]], [int(x) for x in after], int(mask.value)
+
+
+def srv_autotune(s, circuits):
+    """circuits: (n_qubits, gate records) samples; returns [(kmax, front, ms)] per sample (0s for
+    circuits the server packs)."""
+    k = len(circuits)
+    nq = np.array([c[0] for c in circuits], dtype=np.int32)
+    arrs = [np.ascontiguousarray(c[1], dtype=GATE_DTYPE) for c in circuits]
+    ng = np.array([a.size for a in arrs], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * max(k, 1))(*[a.ctypes.data for a in arrs])
+    km = np.zeros(max(k, 1), dtype=np.int32)
+    fr = np.zeros(max(k, 1), dtype=np.int32)
+    ms = np.zeros(max(k, 1), dtype=np.float64)
+    rc = lib().srv_autotune(s, k, _ptr(nq), _ptr(ng), ptrs, _ptr(km), _ptr(fr), _ptr(ms))
+    if rc < 0:
+        raise SimError(rc, lib().srv_last_error(s).decode())
+    return [(int(km[i]), int(fr[i]), float(ms[i])) for i in range(k)]
 
 
 def exported_symbols() -> list:

@@ -28,6 +28,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -230,6 +231,14 @@ struct srv_s {
     std::thread worker;
     bool stop = false;
     std::string err;
+    // autotuned choices for circuits above small_n (srv_autotune): (n, gates-per-qubit bucket) ->
+    // block width and whether the contraction-deferral front runs
+    struct Tune {
+        int kmax = 0, front = 0;
+        double ms = 0.0;
+    };
+    std::map<std::pair<int, int>, Tune> tune;
+    std::mutex tune_mu;
     // stats
     uint64_t submitted = 0, completed = 0, rejected = 0;
     std::vector<double> lat_ms;
@@ -258,6 +267,14 @@ int srv_fail(srv_t *s, int code, const char *fmt, ...)
 // tensor cores: 6 with tcgen05 (its 6-qubit pass costs 1.05-1.15 times a 5-qubit one and saves a
 // quarter of the passes on 30-qubit circuits, once the layout keeps low targets out of them), 5
 // with the mma.sync arithmetic.
+// Depth class of a circuit for the autotuner's cache: gates per qubit, which for these circuits
+// is about 1.4 cycles + 1 (8-12 cycles: < 18, 12-16: < 24, deeper: the rest).
+int depth_bucket(int n_qubits, int n_gates)
+{
+    const int r = n_gates / std::max(n_qubits, 1);
+    return r < 18 ? 0 : (r < 24 ? 1 : 2);
+}
+
 int auto_kmax(int n, bool packed, int precision)
 {
     if (packed) return 5;
@@ -697,9 +714,20 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
         return srv_fail(s, SIM_E_BUSY, "srv_submit: %d qubits need %llu bytes, budget %llu", n_qubits,
                         (unsigned long long)r->bytes, (unsigned long long)s->budget);
     }
-    // plan on the caller's thread
+    // plan on the caller's thread, with the autotuned width and front choice for this size and
+    // depth class when srv_autotune measured one (an explicit kmax in the options still wins)
+    int tuned_front = -1;  // -1: the fixed rule below
+    int tuned_kmax = 0;
+    if (!r->packed) {
+        std::lock_guard<std::mutex> lk(s->tune_mu);
+        auto it = s->tune.find({n_qubits, depth_bucket(n_qubits, n_gates)});
+        if (it != s->tune.end()) {
+            tuned_kmax = it->second.kmax;
+            tuned_front = it->second.front;
+        }
+    }
     sim_plan_opts po{};
-    po.kmax = s->o.kmax ? s->o.kmax : auto_kmax(n_qubits, r->packed, r->precision);
+    po.kmax = s->o.kmax ? s->o.kmax : (tuned_kmax ? tuned_kmax : auto_kmax(n_qubits, r->packed, r->precision));
     if (r->packed) po.kmax = std::min(po.kmax, kPackMaxK);
     po.precision = r->precision;
     // contraction deferral (Sect. 2) for large circuits in the tcgen05 mode: the gates up to the
@@ -707,7 +735,8 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     // tensor-core contraction, when that front holds a large enough share of the circuit
     int front = 0;
     std::vector<int> side(n_qubits, 0);
-    if (!r->packed && tmem_mode(r->precision) && n_qubits >= kFrontMinQubits && s->o.front_pairs >= 0) {
+    const bool want_front = tuned_front >= 0 ? tuned_front == 1 : n_qubits >= kFrontMinQubits;
+    if (!r->packed && tmem_mode(r->precision) && want_front && s->o.front_pairs >= 0) {
         int nf = 0;
         if (split_choose(n_qubits, n_gates, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf,
                          n_qubits) == SIM_OK &&
@@ -825,6 +854,107 @@ int srv_wait(srv_t *s, uint64_t ticket, int timeout_ms, double *norm, double *su
     if (sum_p2_scaled) *sum_p2_scaled = std::ldexp(r->s2, r->n);
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
     return SIM_OK;
+}
+
+// One candidate of the autotuner on a scratch handle: plan as srv_submit would (block width kmax,
+// the contraction-deferral front or not, the layout sim_plan_layout picks), run it twice from the
+// start state and return the second run's device time in *ms.  SIM_E_UNSUPPORTED when the front
+// does not apply to this circuit.
+static int tune_candidate(srv_t *s, sim_t *h, int n, int ng, const sim_gate *gates, int kmax, bool front,
+                          cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    sim_plan_opts po{};
+    po.kmax = kmax;
+    po.precision = s->o.precision;
+    int nf = 0;
+    std::vector<int> side(n, 0);
+    sim_split_t *sp = nullptr;
+    sim_front_t *fr = nullptr;
+    sim_plan_t *plan = nullptr;
+    int rc = SIM_OK;
+    if (front) {
+        rc = split_choose(n, ng, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf, n);
+        if (rc == SIM_OK && nf < kFrontMinShare * ng) rc = SIM_E_UNSUPPORTED;
+        if (rc == SIM_OK) rc = sim_split_create(n, nf, gates, side.data(), &sp);
+        if (rc == SIM_OK) rc = sim_front_create(h, sp, &po, &fr);
+    }
+    if (rc == SIM_OK) rc = sim_plan_create(n, ng - nf, gates + nf, &po, &plan);
+    int perm[kMaxQubits];
+    if (rc == SIM_OK) rc = sim_plan_layout(plan, perm, nullptr);
+    for (int rep = 0; rep < 2 && rc == SIM_OK; rep++) {  // the first run warms up
+        rc = sim_set_layout(h, perm);
+        if (rc == SIM_OK) rc = cudaEventRecord(e0, h->stream) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+        if (rc == SIM_OK) rc = fr ? sim_front_run(h, fr) : sim_reset(h, 0);
+        if (rc == SIM_OK) rc = sim_apply_plan(h, plan);
+        if (rc == SIM_OK) rc = cudaEventRecord(e1, h->stream) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+        if (rc == SIM_OK) rc = cudaEventSynchronize(e1) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+        if (rc == SIM_OK) rc = cudaEventElapsedTime(ms, e0, e1) == cudaSuccess ? SIM_OK : SIM_E_CUDA;
+    }
+    if (plan) sim_plan_destroy(plan);
+    if (fr) sim_front_destroy(fr);
+    if (sp) sim_split_destroy(sp);
+    return rc;
+}
+
+int srv_autotune(srv_t *s, int n_samples, const int *n_qubits, const int *n_gates, const sim_gate *const *gates,
+                 int *kmax_out, int *front_out, double *ms_out)
+{
+    if (!s || n_samples < 0 || (n_samples > 0 && (!n_qubits || !n_gates || !gates)))
+        return srv_fail(s, SIM_E_INVAL, "srv_autotune: NULL argument");
+    DeviceScope dev_scope(s->o.device);
+    if (dev_scope.err != cudaSuccess) return srv_fail(s, SIM_E_CUDA, "srv_autotune: device unavailable");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return srv_fail(s, SIM_E_CUDA, "srv_autotune: events");
+    }
+    int rc = SIM_OK;
+    for (int i = 0; i < n_samples && rc == SIM_OK; i++) {
+        const int n = n_qubits[i], ng = n_gates[i];
+        if (kmax_out) kmax_out[i] = 0;
+        if (front_out) front_out[i] = 0;
+        if (ms_out) ms_out[i] = 0.0;
+        if (n <= s->o.small_n) continue;  // packed: one CTA per circuit, blocks of <= 5 qubits
+        sim_opts so{};
+        so.device = s->o.device;
+        sim_t *h = nullptr;
+        rc = sim_create(n, 0, &so, &h);
+        if (rc != SIM_OK) {
+            srv_fail(s, rc, "srv_autotune: scratch state of %d qubits: %s", n, sim_last_error(nullptr));
+            break;
+        }
+        srv_s::Tune best;
+        best.ms = 1e300;
+        const bool can_front = tmem_mode(s->o.precision) && n >= 22 && s->o.front_pairs >= 0;
+        for (int kmax = 4; kmax <= kMaxK && rc == SIM_OK; kmax++)
+            for (int front = 0; front <= (can_front ? 1 : 0) && rc == SIM_OK; front++) {
+                float ms = 0.f;
+                const int crc = tune_candidate(s, h, n, ng, gates[i], kmax, front == 1, e0, e1, &ms);
+                if (crc == SIM_E_UNSUPPORTED) continue;
+                if (crc != SIM_OK) {
+                    rc = srv_fail(s, crc, "srv_autotune: sample %d (k_max %d, front %d): %s", i, kmax, front,
+                                  h->err.c_str());
+                    break;
+                }
+                if (ms < best.ms) {
+                    best.ms = ms;
+                    best.kmax = kmax;
+                    best.front = front;
+                }
+            }
+        sim_destroy(h);
+        if (rc != SIM_OK) break;
+        {
+            std::lock_guard<std::mutex> lk(s->tune_mu);
+            s->tune[{n, depth_bucket(n, ng)}] = best;
+        }
+        if (kmax_out) kmax_out[i] = best.kmax;
+        if (front_out) front_out[i] = best.front;
+        if (ms_out) ms_out[i] = best.ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int srv_stats(srv_t *s, srv_stats_t *out)

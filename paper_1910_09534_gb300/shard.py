@@ -83,22 +83,31 @@ class ShardedState:
     process group over the 2^g ranks (NCCL).  Two buffers alternate: an exchange receives into the
     other one, whose handle then holds the state."""
 
-    def __init__(self, n: int, g: int, group=None, device: int = 0):
+    def __init__(self, n: int, g: int, group=None, device: int = 0, rank: int | None = None,
+                 world: int | None = None, all_to_all=None):
+        """all_to_all(dst, src, splits): the collective on int64 views of the buffers (one word per
+        amplitude); default torch.distributed.all_to_all_single over `group`, with rank and world
+        taken from it."""
         import torch
-        import torch.distributed as dist
 
-        self.torch, self.dist, self.group = torch, dist, group
+        self.torch, self.group = torch, group
         self.n, self.g = n, g
-        self.world = dist.get_world_size(group)
-        self.rank = dist.get_rank(group)
+        if all_to_all is None:
+            import torch.distributed as dist
+            self.world, self.rank = dist.get_world_size(group), dist.get_rank(group)
+            self.collective = lambda dst, src, splits: dist.all_to_all_single(dst, src, splits, splits, group=group)
+        else:
+            self.world, self.rank, self.collective = world, rank, all_to_all
         if self.world != 1 << g:
             raise ValueError(f"{self.world} ranks for {g} global qubits")
         amps = 1 << (n - g)
         dev = torch.device("cuda", device)
-        stream = torch.cuda.current_stream(dev).cuda_stream
-        self.bufs = [torch.zeros(amps, dtype=torch.complex64, device=dev) for _ in range(2)]
-        self.hs = [N.sim_create(n - g, 0, device=device, stream=stream, ext_state=b.data_ptr(), ext_bytes=amps * 8)
-                   for b in self.bufs]
+        # one stream orders the library's kernels, torch's buffer operations and the collective
+        self.stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(self.stream):
+            self.bufs = [torch.zeros(amps, dtype=torch.complex64, device=dev) for _ in range(2)]
+        self.hs = [N.sim_create(n - g, 0, device=device, stream=self.stream.cuda_stream, ext_state=b.data_ptr(),
+                                ext_bytes=amps * 8) for b in self.bufs]
         self.cur = 0
         self.identity = list(range(n - g))
         self.bit_of = list(range(n))
@@ -114,7 +123,8 @@ class ShardedState:
         if self.rank == 0:
             N.sim_reset(self.h, 0)
         else:
-            self.bufs[0].zero_()
+            with self.torch.cuda.stream(self.stream):
+                self.bufs[0].zero_()
 
     def _local_permute(self, perm):
         N.sim_permute(self.h, perm)
@@ -125,8 +135,8 @@ class ShardedState:
 
     def _all_to_all(self, splits):
         src, dst = self.bufs[self.cur], self.bufs[1 - self.cur]
-        self.dist.all_to_all_single(dst.view(self.torch.int64), src.view(self.torch.int64), splits, splits,
-                                    group=self.group)
+        with self.torch.cuda.stream(self.stream):
+            self.collective(dst.view(self.torch.int64), src.view(self.torch.int64), splits)
         self.cur = 1 - self.cur
         N.sim_set_layout(self.h, self.identity)
 
@@ -140,13 +150,22 @@ class ShardedState:
                                  self._all_to_all)
         return self.bit_of
 
+    def local_reduce(self):
+        """This rank's (sum p, sum p^2) from sim_reduce."""
+        norm, s2_local, _ = N.sim_reduce(self.h)
+        return norm, s2_local / (1 << (self.n - self.g))
+
     def reduce(self):
         """(norm, 2^n sum p^2) over all ranks: each rank's sim_reduce, then one all-reduce."""
-        norm, s2_local, _ = N.sim_reduce(self.h)
-        v = self.torch.tensor([norm, s2_local / (1 << (self.n - self.g))], dtype=self.torch.float64,
-                              device=self.bufs[0].device)
-        self.dist.all_reduce(v, group=self.group)
+        import torch.distributed as dist
+        with self.torch.cuda.stream(self.stream):
+            v = self.torch.tensor(self.local_reduce(), dtype=self.torch.float64, device=self.bufs[0].device)
+            dist.all_reduce(v, group=self.group)
         return float(v[0]), float(v[1]) * (1 << self.n)
+
+    def local_amplitudes(self):
+        """This rank's 2^(n-g) amplitudes (complex64, local index order) on the host."""
+        return N.sim_amplitudes(self.h, physical_order=True)
 
     def destroy(self):
         for h in self.hs:

@@ -164,3 +164,29 @@ def test_packed_path_many_small_circuits(pkg, oracle_mod):
     assert stats["completed"] == 300
     for i in range(0, 300, 37):
         assert np.linalg.norm(outs[i].astype(np.complex128) - oracle_mod.run_circuit(circuits[i])) <= TOL_FP32
+
+
+def test_autotuned_server_matches_oracle_and_alone_equals_mix(pkg, oracle_mod):
+    # srv_autotune measures the candidates per (size, depth class) once; every later circuit of a
+    # tuned class takes the cached choice, served alone or in a mix alike
+    samples = [si.sycamore_circuit(si.near_square_grid(n), d, seed=900 + n) for n, d in ((21, 10), (24, 10), (26, 14))]
+    srv = pkg.srv_create(small_n=20, slots=3, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        picks = pkg.srv_autotune(srv, [(c.n_qubits, pkg.gates_array(c)) for c in samples])
+        for c, (k, fr, ms) in zip(samples, picks):
+            print(f"tuned {c.n_qubits} qubits, {c.n_gates} gates: k_max {k}, front {fr}, {ms:.2f} ms")
+            assert 4 <= k <= 6 and fr in (0, 1) and ms > 0
+        circuits = [si.sycamore_circuit(si.near_square_grid(n), d, seed=950 + i)
+                    for i, (n, d) in enumerate(((21, 9), (24, 11), (26, 13), (18, 8), (21, 11)))]
+        outs = [np.zeros(1 << c.n_qubits, dtype=np.complex64) for c in circuits]
+        tickets = [pkg.srv_submit(srv, c.n_qubits, pkg.gates_array(c), o) for c, o in zip(circuits, outs)]
+        for t in tickets:
+            pkg.srv_wait(srv, t, timeout_ms=120000)
+        alone = [np.zeros_like(o) for o in outs]
+        for c, o in zip(circuits, alone):
+            pkg.srv_wait(srv, pkg.srv_submit(srv, c.n_qubits, pkg.gates_array(c), o), 120000)
+    finally:
+        pkg.srv_destroy(srv)
+    for c, a, b in zip(circuits, outs, alone):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
+        assert np.linalg.norm(a.astype(np.complex128) - oracle_mod.run_circuit(c)) <= TOL_FP32
