@@ -464,7 +464,7 @@ def run_ours(args):
     amps = 1 << n
     gates = pkg.gates_array(circ)
     h = pkg.sim_create(n, 0, device=local)
-    _, stream_ptr = pkg.sim_state_ptr(h)
+    stream_ptr = pkg.sim_stream(h)
     stream = torch.cuda.ExternalStream(stream_ptr)
 
     prec = {"fp32": pkg.SIM_FP32, "fp16x3": pkg.SIM_FP16X3, "fp16x3_tmem": pkg.SIM_FP16X3_TMEM,

@@ -129,7 +129,9 @@ int sim_destroy(sim_t *h);
 int sim_info(const sim_t *h, int *n_qubits, int *slice_bits, int *bit_of);
 
 /* Device pointer of the state buffer (physical order, complex64) and the
- * cudaStream_t the handle orders its work on. */
+ * cudaStream_t the handle orders its work on (either output may be NULL).  Once
+ * the state's address has been handed out, sim_reduce always reads the state
+ * (see sim_reduce). */
 int sim_state_ptr(const sim_t *h, void **dptr, void **stream);
 
 /* Set the state to the computational basis state |basis> (logical index),
@@ -181,7 +183,12 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
  * norm = sum p, sum_p2_scaled = 2^n sum p^2 (Porter-Thomas: about 2), and
  * xeb = 2^n sum p^2 - 1 (linear cross-entropy of the ideal distribution).
  * Per-thread partial sums in FP32 over 16 amplitudes, combined in FP64 in a
- * fixed order (deterministic).  Synchronous.  Any output pointer may be NULL. */
+ * fixed order (deterministic).  Synchronous.  Any output pointer may be NULL.
+ * When the last call that wrote the state was sim_apply_plan and its last block
+ * ran on tcgen05, that kernel has already summed its results (FP32 per tile and
+ * thread, FP64 per thread and CTA, a fixed order): only those CTA sums are
+ * combined.  That is skipped -- the state is read again -- for handles on a
+ * caller's buffer (ext_state) or whose state address sim_state_ptr handed out. */
 int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb);
 
 /* Allocation-free reduction (the paper has no counterpart; it serves callers that

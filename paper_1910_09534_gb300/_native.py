@@ -251,6 +251,13 @@ def sim_state_ptr(h):
     return p.value, st.value
 
 
+def sim_stream(h):
+    """The handle's cudaStream_t only (sim_state_ptr without asking for the state's address)."""
+    st = ctypes.c_void_p()
+    _check(lib().sim_state_ptr(h, None, ctypes.byref(st)), h)
+    return st.value
+
+
 def sim_reset(h, basis: int = 0) -> None:
     _check(lib().sim_reset(h, basis), h)
 

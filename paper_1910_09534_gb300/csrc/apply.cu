@@ -611,12 +611,13 @@ void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, in
 }
 
 int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
-                        int precision, const void *d_staged, cudaStream_t st)
+                        int precision, const void *d_staged, cudaStream_t st, double *red, int *red_grid)
 {
     int rc;
+    if (red_grid) *red_grid = 0;
     switch (block_path(nbits, k, tpos, precision)) {
     case BlockPath::Tcgen05:
-        rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, precision == SIM_BF16X3, d_staged, st);
+        rc = tcgen05_launch_staged(h, psi, nbits, k, tpos, precision == SIM_BF16X3, d_staged, st, red, red_grid);
         break;
     case BlockPath::MmaSync: rc = tc_launch_staged(psi, nbits, k, tpos, precision, d_staged, st); break;
     default:
@@ -690,6 +691,7 @@ extern "C" int sim_apply_fused(sim_t *h, int k, const int *targets, const double
                                int precision)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_fused: NULL handle");
+    state_written(h);
     if (h->store != SIM_STORE_DEVICE)
         return fail(h, SIM_E_UNSUPPORTED, "sim_apply_fused: host-store state: use sim_run_phase");
     if (!precision_ok(precision))

@@ -86,7 +86,38 @@ struct Tc5Geom {
     uint64_t moff[64];       // address offset of member m
     const uint32_t *bmat;    // R^T hi then lo, FP16 core-matrix layout, as 32-bit words
     int *err;                // set to 1 if a wait timed out
+    double *red;             // if set: this CTA's (sum p, sum p^2) of the results at red[2 blockIdx.x]
 };
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The drainers' fused reduction: each thread's FP64 sums of p = |psi_i|^2 and p^2 over the results
+// it stored (FP32 within a tile), combined in a fixed order into the CTA's pair (deterministic).
+// Called by all 256 drainer threads (dtid 0..255) after their last tile.
+__device__ __forceinline__ void drain_partials(double r1, double r2, int dtid, double (*part)[2], double *out)
+{
+    r1 = warp_sum_d(r1);
+    r2 = warp_sum_d(r2);
+    if ((dtid & 31) == 0) {
+        part[dtid >> 5][0] = r1;
+        part[dtid >> 5][1] = r2;
+    }
+    asm volatile("bar.sync 2, 256;\n" ::: "memory");
+    if (dtid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a += part[w][0];
+            b += part[w][1];
+        }
+        out[2 * blockIdx.x] = a;
+        out[2 * blockIdx.x + 1] = b;
+    }
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -270,6 +301,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
     __shared__ __align__(8) uint64_t loaded[S], full[S], mma_done[S], drained[S], tmem_free[2];
     __shared__ float row_inv[S][R2][kRows];
     __shared__ float amax_part[R2][2][kRows];
+    __shared__ double red_part[8][2];
     __shared__ uint64_t tile_base[S];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -478,6 +510,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                 rx |= g.ridx[j];
                 ro += g.roff[j];
             }
+        double r1 = 0.0, r2 = 0.0;  // fused reduction (g.red)
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
             const int st = i % S;
@@ -511,10 +544,18 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                         mbar_arrive(smem_u32(&tmem_free[i & 1]));
                     }
+                    float t1 = 0.f, t2 = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        __stcs(dst + g.moff[H * half + c0 / 2 + j],
-                               make_float2((a[2 * j] + b[2 * j]) * inv[0], (a[2 * j + 1] + b[2 * j + 1]) * inv[0]));
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 v =
+                            make_float2((a[2 * j] + b[2 * j]) * inv[0], (a[2 * j + 1] + b[2 * j + 1]) * inv[0]);
+                        const float p = fmaf(v.x, v.x, v.y * v.y);
+                        t1 += p;
+                        t2 = fmaf(p, p, t2);
+                        __stcs(dst + g.moff[H * half + c0 / 2 + j], v);
+                    }
+                    r1 += t1;
+                    r2 += t2;
                 }
                 continue;
             }
@@ -534,9 +575,16 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
                     mbar_arrive(smem_u32(&tmem_free[i & 1]));
                 }
                 float2 o[H];
+                float t1 = 0.f, t2 = 0.f;
 #pragma unroll
-                for (int j = 0; j < H; ++j)
+                for (int j = 0; j < H; ++j) {
                     o[j] = make_float2((a[2 * j] + b[2 * j]) * inv[u], (a[2 * j + 1] + b[2 * j + 1]) * inv[u]);
+                    const float p = fmaf(o[j].x, o[j].x, o[j].y * o[j].y);
+                    t1 += p;
+                    t2 = fmaf(p, p, t2);
+                }
+                r1 += t1;
+                r2 += t2;
                 if constexpr (BULK) {
                     const uint32_t rxu = u ? rx | g.ridx[7] : rx;
 #pragma unroll
@@ -565,6 +613,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tcgen05(Tc5Geom g)
             }
         }
         if (BULK && store_warp) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+        if (g.red) drain_partials(r1, r2, tid - (kConv + 64), red_part, g.red);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -644,6 +693,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
     __shared__ __align__(8) uint64_t loaded[S], stage_free[S], a_full[2], mma_done[2], tmem_free, scales[4];
     __shared__ float row_inv[4][kRows];
     __shared__ float amax_part[2][kRows];
+    __shared__ double red_part[8][2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -815,6 +865,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
 #pragma unroll
         for (int j = 0; j < 7; ++j)
             if ((row >> j) & 1) ro += g.roff[j];
+        double r1 = 0.0, r2 = 0.0;  // fused reduction (g.red)
         uint32_t i = 0;
         for (uint64_t tile = blockIdx.x; tile < g.n_tiles; tile += gridDim.x, ++i) {
             const int b = i & 1, j = i & 3;
@@ -828,6 +879,7 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
             float2 *const dst = g.psi + insert_zero_bits_g(tile * kRows, g.tpos, 6) + ro;
             const float inv = row_inv[j][row];
             const uint32_t lane_base = tmem + 256 + ((uint32_t)(32 * q) << 16) + half * (N / 2);
+            float t1 = 0.f, t2 = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < N / 2; c0 += 16) {
                 float a[16], c[16];
@@ -839,11 +891,18 @@ __global__ void __launch_bounds__(kThreadsTc5, 1) k_apply_tc6a(Tc5Geom g)
                     mbar_arrive(smem_u32(&tmem_free));
                 }
 #pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    __stcs(dst + g.moff[H * half + c0 / 2 + m],
-                           make_float2((a[2 * m] + c[2 * m]) * inv, (a[2 * m + 1] + c[2 * m + 1]) * inv));
+                for (int m = 0; m < 8; ++m) {
+                    const float2 v = make_float2((a[2 * m] + c[2 * m]) * inv, (a[2 * m + 1] + c[2 * m + 1]) * inv);
+                    const float p = fmaf(v.x, v.x, v.y * v.y);
+                    t1 += p;
+                    t2 = fmaf(p, p, t2);
+                    __stcs(dst + g.moff[H * half + c0 / 2 + m], v);
+                }
             }
+            r1 += t1;
+            r2 += t2;
         }
+        if (g.red) drain_partials(r1, r2, tid - (kConv + 64), red_part, g.red);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -949,7 +1008,7 @@ int tile_geometry(int nbits, const int *tpos, int rows, Tc5Geom &g)
 }
 
 template <int K, int R2, bool LOWT, bool BF>
-int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
+int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st, int *grid_out)
 {
     using L = Tc5Layout<K, R2>;
     auto kern = k_apply_tcgen05<K, R2, LOWT, BF>;
@@ -969,12 +1028,13 @@ int launch_tc5_kr(const Tc5Geom &g, int nbits, cudaStream_t st)
     Tc5Geom gg = g;
     gg.n_tiles = 1ull << (nbits - K - 7 - (R2 == 2));
     const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)cfg.sms);
+    if (grid_out) *grid_out = (int)grid;
     kern<<<(unsigned)grid, kThreadsTc5, L::SMEM, st>>>(gg);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <bool LOWT, bool BF>
-int launch_tc6a(const Tc5Geom &g, int nbits, cudaStream_t st)
+int launch_tc6a(const Tc5Geom &g, int nbits, cudaStream_t st, int *grid_out)
 {
     auto kern = k_apply_tc6a<LOWT, BF>;
     static std::atomic<uint64_t> smem_done{0};
@@ -991,16 +1051,19 @@ int launch_tc6a(const Tc5Geom &g, int nbits, cudaStream_t st)
     Tc5Geom gg = g;
     gg.n_tiles = 1ull << (nbits - 6 - 7);
     const uint64_t grid = std::min<uint64_t>(gg.n_tiles, (uint64_t)cfg.sms);
+    if (grid_out) *grid_out = (int)grid;
     kern<<<(unsigned)grid, kThreadsTc5, kTc6Smem, st>>>(gg);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Geometry of the block and launch, B (hi, lo) already in device memory at d_b.
 template <int K, bool BF>
-int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const uint32_t *d_b, cudaStream_t st)
+int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const uint32_t *d_b, cudaStream_t st,
+                      double *red = nullptr, int *grid_out = nullptr)
 {
     Tc5Geom g{};
     g.psi = psi;
+    g.red = red;
     for (int i = 0; i < K; i++) g.tpos[i] = tpos[i];  // ascending
     g.bmat = d_b;
     g.err = h->d_errflag;
@@ -1010,11 +1073,11 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
     if constexpr (K == 6) {  // 128-group tiles only: two 256-column accumulator sets fill the TMEM
         if (tile_geometry<K>(nbits, tpos, 7, g) < 0) return -1;
 #if SYCSIM_TC6_ATMEM
-        if (g.nlow > 0) return launch_tc6a<true, BF>(g, nbits, st);
-        return launch_tc6a<false, BF>(g, nbits, st);
+        if (g.nlow > 0) return launch_tc6a<true, BF>(g, nbits, st, grid_out);
+        return launch_tc6a<false, BF>(g, nbits, st, grid_out);
 #else
-        if (g.nlow > 0) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st);
-        return launch_tc5_kr<K, 1, false, BF>(g, nbits, st);
+        if (g.nlow > 0) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st, grid_out);
+        return launch_tc5_kr<K, 1, false, BF>(g, nbits, st, grid_out);
 #endif
     } else {
         // 128-group tiles when their runs reach 2 KiB (bit 7 is a target, or a target lies below
@@ -1024,12 +1087,12 @@ int launch_tc5_staged(sim_t *h, float2 *psi, int nbits, const int *tpos, const u
         const int run = tile_geometry<K>(nbits, tpos, 7, g);
         if (run < 0) return -1;
         if (g.nlow > 0) {
-            if constexpr (K == 5) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st);
+            if constexpr (K == 5) return launch_tc5_kr<K, 1, true, BF>(g, nbits, st, grid_out);
             return -2;
         }
-        if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false, BF>(g, nbits, st);
+        if (run >= 8 || nbits < K + 8) return launch_tc5_kr<K, 1, false, BF>(g, nbits, st, grid_out);
         if (tile_geometry<K>(nbits, tpos, 8, g) < 8) return -1;
-        return launch_tc5_kr<K, 2, false, BF>(g, nbits, st);
+        return launch_tc5_kr<K, 2, false, BF>(g, nbits, st, grid_out);
     }
 }
 
@@ -1083,16 +1146,16 @@ void tcgen05_build_staged(int k, const float2 *mat, bool bf16, void *h_out)
 }
 
 int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, bool bf16,
-                          const void *d_staged, cudaStream_t st)
+                          const void *d_staged, cudaStream_t st, double *red, int *grid_out)
 {
     const uint32_t *d_b = static_cast<const uint32_t *>(d_staged);
     switch (k) {
-    case 4: return bf16 ? launch_tc5_staged<4, true>(h, psi, nbits, tpos, d_b, st)
-                        : launch_tc5_staged<4, false>(h, psi, nbits, tpos, d_b, st);
-    case 5: return bf16 ? launch_tc5_staged<5, true>(h, psi, nbits, tpos, d_b, st)
-                        : launch_tc5_staged<5, false>(h, psi, nbits, tpos, d_b, st);
-    case 6: return bf16 ? launch_tc5_staged<6, true>(h, psi, nbits, tpos, d_b, st)
-                        : launch_tc5_staged<6, false>(h, psi, nbits, tpos, d_b, st);
+    case 4: return bf16 ? launch_tc5_staged<4, true>(h, psi, nbits, tpos, d_b, st, red, grid_out)
+                        : launch_tc5_staged<4, false>(h, psi, nbits, tpos, d_b, st, red, grid_out);
+    case 5: return bf16 ? launch_tc5_staged<5, true>(h, psi, nbits, tpos, d_b, st, red, grid_out)
+                        : launch_tc5_staged<5, false>(h, psi, nbits, tpos, d_b, st, red, grid_out);
+    case 6: return bf16 ? launch_tc5_staged<6, true>(h, psi, nbits, tpos, d_b, st, red, grid_out)
+                        : launch_tc5_staged<6, false>(h, psi, nbits, tpos, d_b, st, red, grid_out);
     default: return -1;
     }
 }

@@ -617,6 +617,7 @@ int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const 
 extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision)
 {
     if (!out || !t1 || !t2 || !s) return fail(out, SIM_E_INVAL, "sim_contract: NULL argument");
+    state_written(out);
     if (out == t1 || out == t2 || t1 == t2) return fail(out, SIM_E_INVAL, "sim_contract: handles must be distinct");
     if (precision != SIM_FP32 && precision != SIM_FP16X3 && precision != SIM_FP16X3_TMEM && precision != SIM_BF16X3)
         return fail(out, SIM_E_INVAL,

@@ -70,6 +70,14 @@ struct sim_s {
     cudaEvent_t frag_ev[kFragSlots] = {};
     int frag_next = 0;
 
+    // fused reduction: sim_apply_plan's last block (tcgen05) leaves each CTA's (sum p, sum p^2) in
+    // d_partials; sim_reduce then only combines them, while no call has written the state since
+    // (write_epoch counts the calls that may write it) and the state's memory is the handle's own
+    // and was never handed out (state_exposed: sim_state_ptr returned its address)
+    uint64_t write_epoch = 1, red_epoch = 0;
+    int red_blocks = 0;
+    mutable bool state_exposed = false;
+
     // a whole plan's staged block operands (sim_apply_plan), uploaded in one copy: two slots, each
     // a pinned source and its device copy, reused once the plan that last used it has run
     char *h_plan[2] = {};
@@ -233,13 +241,21 @@ BlockPath block_path(int nbits, int k, const int *tpos, int precision);
 bool staging_slot_free(sim_t *h, int nbits, int k, const int *tpos, int precision);
 size_t block_staged_bytes(int nbits, int k, const int *tpos, int precision);
 void block_build_staged(int nbits, int k, const int *tpos, const float2 *mat, int precision, void *h_out);
+// red / red_grid: as for tcgen05_launch_staged, taken only by tcgen05 blocks (*red_grid stays 0
+// for the others)
 int launch_block_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
-                        int precision, const void *d_staged, cudaStream_t st);
+                        int precision, const void *d_staged, cudaStream_t st, double *red = nullptr,
+                        int *red_grid = nullptr);
 int enqueue_block_on(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat,
                      int precision, cudaStream_t st);
 int enqueue_block(sim_t *h, int k, const int *tpos, const float2 *mat, int precision);
 
 bool precision_ok(int precision);
+// a call is about to write (or may write) the handle's state: partial sums left by a fused
+// reduction no longer describe it
+inline void state_written(sim_t *h) { h->write_epoch++; }
+// the final combine of the reduction over nblocks (sum p, sum p^2) pairs (reduce.cu)
+int launch_reduce_final(const double *partials, int nblocks, double *d_result, cudaStream_t st);
 // the modes whose 4- to 6-qubit blocks take the tcgen05 kernel where it is eligible
 inline bool tmem_mode(int precision) { return precision == SIM_FP16X3_TMEM || precision == SIM_BF16X3; }
 // the modes whose mma.sync blocks use the 3xFP16 kernel (BF16X3 hands it what tcgen05 leaves)
@@ -253,8 +269,10 @@ bool tcgen05_eligible(int nbits, int k, const int *tpos);
 // operands staged once in device memory (CUDA graphs): B hi/lo of one block
 size_t tcgen05_staged_bytes(int k);
 void tcgen05_build_staged(int k, const float2 *mat, bool bf16, void *h_out);
+// red (may be NULL): the kernel also writes each CTA's (sum p, sum p^2) of its results at
+// red[2 cta]; *grid_out (may be NULL) receives the number of CTAs
 int tcgen05_launch_staged(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, bool bf16,
-                          const void *d_staged, cudaStream_t st);
+                          const void *d_staged, cudaStream_t st, double *red = nullptr, int *grid_out = nullptr);
 int launch_apply_tcgen05(sim_t *h, float2 *psi, int nbits, int k, const int *tpos, const float2 *mat, bool bf16,
                          cudaStream_t st);
 

@@ -276,6 +276,7 @@ using namespace sycsim;
 extern "C" int sim_permute(sim_t *h, const int *perm)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_permute: NULL handle");
+    state_written(h);
     if (!perm) return fail(h, SIM_E_INVAL, "sim_permute: NULL perm");
     if (h->store != SIM_STORE_DEVICE)
         return fail(h, SIM_E_UNSUPPORTED, "sim_permute: the host store's layout is fixed by its sliced sets");
@@ -303,6 +304,7 @@ extern "C" int sim_permute(sim_t *h, const int *perm)
 extern "C" int sim_set_layout(sim_t *h, const int *perm)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_set_layout: NULL handle");
+    state_written(h);
     if (!perm) return fail(h, SIM_E_INVAL, "sim_set_layout: NULL perm");
     if (h->store != SIM_STORE_DEVICE || h->s != 0)
         return fail(h, SIM_E_INVAL, "sim_set_layout: device-store handles that are not sliced only");

@@ -552,6 +552,7 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
 int sim_apply_plan(sim_t *h, const sim_plan_t *p)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_apply_plan: NULL handle");
+    state_written(h);
     if (!p) return fail(h, SIM_E_INVAL, "sim_apply_plan: NULL plan");
     if (p->n != h->n)
         return fail(h, SIM_E_INVAL, "sim_apply_plan: plan has %d qubits, handle %d", p->n, h->n);
@@ -620,17 +621,26 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p)
         d_ops = h->d_plan[slot];
     }
     const double pass_bytes = 16.0 * std::ldexp(1.0, h->n);
+    // the last block, on tcgen05, also leaves its CTAs' (sum p, sum p^2): a following sim_reduce
+    // only combines them instead of reading the state again (handles whose state memory is their
+    // own and was never handed out: nobody else can write it in between)
+    const bool fuse = h->own_state && !h->state_exposed;
+    int red_grid = 0;
     for (size_t i = 0; i < nb; i++) {
         const Prep &pb = prep[i];
+        const bool last = i + 1 == nb;
         const int ps = prof_begin(h, SIM_PROF_APPLY, pass_bytes, h->stream);
         const int rc = launch_block_staged(h, h->d_state, h->n, pb.k, pb.tpos, mats.data() + pb.moff, p->precision,
-                                           d_ops ? d_ops + pb.off : nullptr, h->stream);
+                                           d_ops ? d_ops + pb.off : nullptr, h->stream,
+                                           last && fuse ? h->d_partials : nullptr, last && fuse ? &red_grid : nullptr);
         prof_end(h, ps, h->stream);
         if (rc != SIM_OK) {
             if (slot >= 0) cudaEventRecord(h->plan_ev[slot], h->stream);
             return rc;
         }
     }
+    h->red_blocks = red_grid;
+    h->red_epoch = red_grid > 0 ? h->write_epoch : 0;
     if (slot >= 0) SIM_CUDA_TRY(h, cudaEventRecord(h->plan_ev[slot], h->stream));
     return SIM_OK;
 }
@@ -704,6 +714,7 @@ int sim_graph_create(sim_t *h, const sim_plan_t *p, sim_graph_t **out)
 int sim_graph_launch(sim_t *h, const sim_graph_t *g)
 {
     if (!h || !g) return fail(h, SIM_E_INVAL, "sim_graph_launch: NULL argument");
+    state_written(h);
     if (g->h != h) return fail(h, SIM_E_INVAL, "sim_graph_launch: the graph belongs to another handle");
     if (!std::equal(g->bit_of.begin(), g->bit_of.end(), h->bit_of))
         return fail(h, SIM_E_INVAL, "sim_graph_launch: the layout changed since the graph was created");
@@ -730,6 +741,7 @@ int sim_autotune(sim_t *h, int n_gates, const sim_gate *gates, int accuracy, sim
                  double *best_ms)
 {
     if (!h || !best) return fail(h, SIM_E_INVAL, "sim_autotune: NULL argument");
+    state_written(h);
     if (h->store != SIM_STORE_DEVICE || h->s != 0)
         return fail(h, SIM_E_UNSUPPORTED, "sim_autotune: needs a device-resident, unsliced handle");
     if (accuracy != SIM_TUNE_FP32 && accuracy != SIM_TUNE_FP32_EQUIVALENT && accuracy != SIM_TUNE_ANY)
@@ -954,6 +966,7 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
 int sim_run_phases(sim_t *h, const sim_phases_t *ph)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_run_phases: NULL handle");
+    state_written(h);
     if (!ph || ph->n != h->n) return fail(h, SIM_E_INVAL, "sim_run_phases: phases missing or for another n");
     if (h->store == SIM_STORE_HOST) {
         if (ph->s != h->s) return fail(h, SIM_E_INVAL, "sim_run_phases: slice_bits differ");

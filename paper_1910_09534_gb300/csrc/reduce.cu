@@ -146,6 +146,12 @@ int launch_reduce(sim_t *, const float2 *psi, uint64_t amps, double *d_partials,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int launch_reduce_final(const double *partials, int nblocks, double *d_result, cudaStream_t st)
+{
+    k_reduce_final<<<1, 32, 0, st>>>(partials, nblocks, d_result);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_gather_logical(const float2 *psi, float2 *dst, uint64_t first, uint64_t count, int n,
                           const int *bit_of, int scatter, cudaStream_t st)
 {

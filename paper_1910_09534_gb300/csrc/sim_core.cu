@@ -239,7 +239,10 @@ int sim_state_ptr(const sim_t *h, void **dptr, void **stream)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_state_ptr: NULL handle");
     if (h->store != SIM_STORE_DEVICE)
         return fail(nullptr, SIM_E_UNSUPPORTED, "sim_state_ptr: state is in the host store (sim_slot_ptr)");
-    if (dptr) *dptr = h->d_state;
+    if (dptr) {
+        *dptr = h->d_state;
+        h->state_exposed = true;  // the caller may write it behind the handle's back
+    }
     if (stream) *stream = (void *)h->stream;
     return SIM_OK;
 }
@@ -247,6 +250,7 @@ int sim_state_ptr(const sim_t *h, void **dptr, void **stream)
 int sim_reset(sim_t *h, uint64_t basis)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reset: NULL handle");
+    state_written(h);
     if (h->n < 64 && (basis >> h->n) != 0)
         return fail(h, SIM_E_INVAL, "sim_reset: basis index has bits above n=%d", h->n);
     SIM_DEVICE_SCOPE(h, h->device);
@@ -372,6 +376,7 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
                         int physical_order)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_load_amplitudes: NULL handle");
+    state_written(h);
     if (first > h->amps || count > h->amps - first)
         return fail(h, SIM_E_INVAL, "sim_load_amplitudes: range outside the state");
     if (count == 0) return SIM_OK;
@@ -415,10 +420,17 @@ int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
         if (xeb) *xeb = ldexp(b, h->n) - 1.0;
         return SIM_OK;
     }
-    const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps, h->stream);
-    h->launches++;  // the reduction is two kernels (partials + final)
-    const int rc = launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, h->stream);
-    prof_end(h, ps, h->stream);
+    int rc;
+    if (h->red_epoch == h->write_epoch && h->red_blocks > 0) {
+        // the plan's last block left the partial sums of exactly this state: combine them
+        rc = launch_reduce_final(h->d_partials, h->red_blocks, h->d_result, h->stream);
+        h->launches++;
+    } else {
+        const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps, h->stream);
+        h->launches++;  // the reduction is two kernels (partials + final)
+        rc = launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, h->stream);
+        prof_end(h, ps, h->stream);
+    }
     if (rc != 0)
         return fail(h, SIM_E_CUDA, "sim_reduce: launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));

@@ -219,6 +219,7 @@ extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan
 extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
 {
     if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
+    state_written(out);
     if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
     for (int t = 0; t < 2; ++t) {
         // relabel the tensor (free: its state is reset next) into the layout the contraction into

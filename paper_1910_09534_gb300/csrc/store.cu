@@ -453,6 +453,7 @@ extern "C" int sim_state_save(sim_t *h, const char *path)
 extern "C" int sim_state_load(sim_t *h, const char *path)
 {
     if (!h || !path) return fail(h, SIM_E_INVAL, "sim_state_load: NULL argument");
+    state_written(h);
     SIM_DEVICE_SCOPE(h, h->device);
     int rc = sync_state(h);
     if (rc != SIM_OK) return rc;
@@ -525,6 +526,7 @@ extern "C" {
 int sim_stream_slice(sim_t *h, int set, uint64_t value, int dir, int slot)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_stream_slice: NULL handle");
+    state_written(h);
     if (h->store != SIM_STORE_HOST)
         return fail(h, SIM_E_UNSUPPORTED, "sim_stream_slice: handle has no host store");
     if (set < 0 || set > 1 || (dir != SIM_H2D && dir != SIM_D2H) || slot < 0 || slot >= h->nslots ||
@@ -563,6 +565,7 @@ int sim_slot_read(sim_t *h, int slot, uint64_t first, uint64_t count, void *out)
 int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_run_phase: NULL handle");
+    state_written(h);
     if (!p || p->n != h->n) return fail(h, SIM_E_INVAL, "sim_run_phase: plan missing or for another n");
     if (set < 0 || set > 1) return fail(h, SIM_E_INVAL, "sim_run_phase: set must be 0 (A) or 1 (B)");
     SIM_DEVICE_SCOPE(h, h->device);
