@@ -516,9 +516,11 @@ int sim_state_load(sim_t *h, const char *path);
  * admits queued circuits in arrival order while their device footprint
  * (8 * 2^n bytes + 64 KiB) fits the HBM budget -- a circuit that does not fit
  * can be overtaken by at most 64 later ones -- and runs them concurrently:
- * circuits with n <= small_n are packed into one kernel launch (one thread block
- * per circuit: reset, every block, reduction); larger ones run on `slots`
- * streams with stream-ordered memory.  A circuit always takes the same path and
+ * circuits with n <= small_n go through a device-side queue served by a
+ * persistent worker kernel (one thread block per circuit: reset, every block,
+ * reduction; circuits published while it runs are taken up without a new launch,
+ * and it ends after 200 us without work); larger ones run on `slots` streams with
+ * stream-ordered memory.  A circuit always takes the same path and
  * plan, so its result does not depend on what else is in flight (srv_autotune fixes the
  * choices for the sizes it measured before any is served). */
 typedef struct srv_s srv_t;

@@ -8,9 +8,12 @@
 //  * admits requests in arrival order while their device footprint (8 * 2^n bytes plus
 //    scratch) fits the HBM budget; a request that does not fit may be overtaken by smaller
 //    ones at most kMaxBypass times, after which admission waits for it (no starvation);
-//  * packs small circuits (n <= small_n) into one launch of k_circuit_cta: one CTA runs one
-//    whole circuit -- reset, every block, the reduction -- with the block matrix in shared
-//    memory, so a batch of small circuits costs one kernel launch instead of one per block;
+//  * runs small circuits (n <= small_n) through a device-side queue served by a persistent
+//    worker kernel (k_packed_worker): one CTA runs one whole circuit -- reset, every block, the
+//    reduction -- with the block matrix in shared memory; circuits are uploaded in units, published
+//    to the queue, claimed by idle CTAs of a worker already running (or of a new one when the
+//    running workers have fewer CTAs than jobs waiting), and a worker leaves after 200 us without
+//    new work, so small circuits that arrive while others run start without a new launch;
 //  * runs larger circuits on one of several slot streams with stream-ordered allocation, so
 //    circuits of different sizes overlap on the device; their blocks are enqueued a few at a
 //    time, as far as the slot's matrix-staging ring has free slots, so the scheduler never
@@ -96,14 +99,20 @@ __device__ __forceinline__ void cta_block(float2 *psi, int n, const int *tpos, c
     }
 }
 
-// One CTA = one whole small circuit.
-__global__ void __launch_bounds__(kPackThreads) k_circuit_cta(const PackedJob *jobs)
+struct PackShared {
+    float2 M[32 * 32];
+    uint32_t moff[32];
+    int tpos[kMaxK];
+    double red[2][kPackThreads / 32];
+};
+
+// One whole small circuit on one CTA: reset to |0...0>, every block with its matrix in shared
+// memory, then (sum p, sum p^2) into out[0..1].
+__device__ void run_circuit_cta(const PackedJob &J, PackShared &sh, double *out)
 {
-    __shared__ float2 M[32 * 32];
-    __shared__ uint32_t moff[32];
-    __shared__ int tpos[kMaxK];
-    __shared__ double red[2][kPackThreads / 32];
-    const PackedJob J = jobs[blockIdx.x];
+    float2 *M = sh.M;
+    uint32_t *moff = sh.moff;
+    int *tpos = sh.tpos;
     const uint64_t amps = 1ull << J.n;
     for (uint64_t i = threadIdx.x; i < amps; i += blockDim.x) J.psi[i] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -143,18 +152,87 @@ __global__ void __launch_bounds__(kPackThreads) k_circuit_cta(const PackedJob *j
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-        red[0][warp] = s1;
-        red[1][warp] = s2;
+        sh.red[0][warp] = s1;
+        sh.red[1][warp] = s2;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, c = 0.0;
         for (int w = 0; w < kPackThreads / 32; ++w) {
-            a += red[0][w];
-            c += red[1][w];
+            a += sh.red[0][w];
+            c += sh.red[1][w];
         }
-        J.out[0] = a;
-        J.out[1] = c;
+        out[0] = a;
+        out[1] = c;
+    }
+}
+
+// The packed jobs' queue, shared by the host and the worker kernel: entries in mapped pinned host
+// memory (the host writes a descriptor, the device its results and done flag), a published count
+// the host raises after writing descriptors, and a claim counter in device memory.
+struct QSlot {
+    PackedJob job;
+    double res[2];
+    uint32_t done;
+    uint32_t pad;
+};
+constexpr uint32_t kQueueCap = 4096;
+constexpr uint64_t kWorkerIdleNs = 200000;  // a worker CTA leaves after 200 us without a new job
+
+__device__ __forceinline__ uint64_t pack_now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent worker: each CTA claims the next published job (compare-and-swap on the claim
+// counter, so no claimed index is ever abandoned), runs it, publishes its results and done flag,
+// and looks for the next one; it leaves once no job has been published for kWorkerIdleNs.  Jobs
+// published while the kernel runs are picked up without a new launch.  The only wait is on the
+// host's published count, bounded by the idle time.
+__global__ void __launch_bounds__(kPackThreads) k_packed_worker(const uint32_t *published, QSlot *ring, uint32_t *head)
+{
+    __shared__ PackShared sh;
+    __shared__ PackedJob J;
+    __shared__ uint32_t job;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint32_t got = 0xffffffffu;
+            const uint64_t t0 = pack_now_ns();
+            for (;;) {
+                const uint32_t p = ld_acquire_sys(published);
+                const uint32_t h = atomicAdd(head, 0u);
+                if (h < p) {
+                    if (atomicCAS(head, h, h + 1) == h) {
+                        got = h;
+                        break;
+                    }
+                    continue;
+                }
+                if (pack_now_ns() - t0 > kWorkerIdleNs) break;
+                __nanosleep(1000);
+            }
+            job = got;
+            if (got != 0xffffffffu) J = ring[got % kQueueCap].job;
+        }
+        __syncthreads();
+        if (job == 0xffffffffu) break;
+        QSlot *slot = ring + job % kQueueCap;
+        run_circuit_cta(J, sh, slot->res);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system();  // results visible to the host before the flag
+            asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(&slot->done), "r"(1u) : "memory");
+        }
+        __syncthreads();  // job and J are rewritten by the next claim
     }
 }
 
@@ -194,16 +272,20 @@ struct Req {
     double *h_res = nullptr;  // pinned pair
 };
 
+// A unit of small circuits on their way through the worker queue: uploaded together (states and
+// tables in one stream-ordered allocation), published to the queue once the upload is done, their
+// amplitudes copied out once every job's done flag is set, retired after that copy.
 struct Batch {
+    enum State { Free, Uploading, Running, CopyingOut };
     std::vector<std::shared_ptr<Req>> jobs;
+    std::vector<double> res;        // (sum p, sum p^2) per job, taken from the queue
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    void *d_mem = nullptr;          // states + tables + results, one stream-ordered allocation
-    std::vector<char> h_table;      // pinned copy source lives in h_stage
-    char *h_stage = nullptr;        // pinned
+    cudaEvent_t ev = nullptr;       // upload done, then copy-out done
+    void *d_mem = nullptr;          // states + tables, one stream-ordered allocation
+    char *h_stage = nullptr;        // pinned copy source of the tables
     size_t stage_bytes = 0;
-    double *h_res = nullptr;        // pinned, 2 per job
-    bool busy = false;
+    uint64_t first = 0;             // queue index of the first job
+    State state = Free;
 };
 
 constexpr int kMaxBypass = 64;
@@ -227,6 +309,16 @@ struct srv_s {
     std::vector<sim_t *> slots;
     std::vector<std::shared_ptr<Req>> slot_req;
     std::vector<Batch> batches;
+    // the packed jobs' queue (see k_packed_worker): ring entries in mapped pinned memory, the
+    // published count beside them, the claim counter in device memory, up to two workers in flight
+    QSlot *ring = nullptr, *d_ring = nullptr;
+    uint32_t *ctl = nullptr, *d_ctl = nullptr;  // ctl[0]: published count
+    uint32_t *d_head = nullptr;
+    uint64_t next_index = 0, published = 0, retired = 0;
+    cudaStream_t wst[2] = {nullptr, nullptr};
+    cudaEvent_t wev[2] = {nullptr, nullptr};
+    int wctas[2] = {0, 0};  // CTAs of a worker still running (0: none)
+    int sms = 0;
     double *h_results = nullptr;  // pinned ring of result pairs for unpacked requests
     std::thread worker;
     bool stop = false;
@@ -414,8 +506,10 @@ void abort_unpacked(srv_t *s, int i, int rc)
     s->cv_done.notify_all();
 }
 
-// Launch one packed batch of small requests (scheduler thread, lock held).
-int launch_packed(srv_t *s, Batch &B)
+// Upload one unit of small requests (scheduler thread, lock held): tables and states in one
+// stream-ordered allocation, the tables copied from pinned staging, the queue descriptors written
+// (published later, once the upload is done: the worker may then run them at once).
+int upload_packed(srv_t *s, Batch &B)
 {
     size_t nblk = 0, nmat = 0, state_amps = 0;
     for (auto &r : B.jobs) {
@@ -425,11 +519,9 @@ int launch_packed(srv_t *s, Batch &B)
     }
     const size_t nj = B.jobs.size();
     auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t off_jobs = 0, off_blk = align(off_jobs + nj * sizeof(PackedJob));
-    const size_t off_mat = align(off_blk + nblk * sizeof(PackedBlock));
-    const size_t off_res = align(off_mat + nmat * sizeof(float2));
-    const size_t off_state = align(off_res + nj * 2 * sizeof(double));
-    const size_t table_bytes = off_res;
+    const size_t off_blk = 0, off_mat = align(off_blk + nblk * sizeof(PackedBlock));
+    const size_t off_state = align(off_mat + nmat * sizeof(float2));
+    const size_t table_bytes = off_state;
     const size_t total = off_state + state_amps * sizeof(float2);
     if (B.stage_bytes < table_bytes) {
         if (B.h_stage) cudaFreeHost(B.h_stage);
@@ -447,29 +539,33 @@ int launch_packed(srv_t *s, Batch &B)
     }
     struct ReleaseOnError {  // an early return below gives the allocation back (stream-ordered)
         Batch &b;
+        bool armed = true;
         ~ReleaseOnError()
         {
-            if (b.d_mem) cudaFreeAsync(b.d_mem, b.st);
-            b.d_mem = nullptr;
+            if (armed && b.d_mem) cudaFreeAsync(b.d_mem, b.st);
+            if (armed) b.d_mem = nullptr;
         }
     } release_on_error{B};
     char *d = (char *)B.d_mem;
-    PackedJob *hj = (PackedJob *)(B.h_stage + off_jobs);
     PackedBlock *hb = (PackedBlock *)(B.h_stage + off_blk);
     float2 *hm = (float2 *)(B.h_stage + off_mat);
     size_t bi = 0, mi = 0, si = 0;
+    B.first = s->next_index;
     for (size_t j = 0; j < nj; j++) {
         auto &r = B.jobs[j];
-        hj[j].psi = (float2 *)(d + off_state) + si;
-        hj[j].blocks = (const PackedBlock *)(d + off_blk) + bi;
-        hj[j].mats = (const float2 *)(d + off_mat);
-        hj[j].out = (double *)(d + off_res) + 2 * j;
-        hj[j].n = r->n;
-        hj[j].nblocks = (int)r->blocks.size();
+        QSlot &q = s->ring[(B.first + j) % kQueueCap];
+        q.job.psi = (float2 *)(d + off_state) + si;
+        q.job.blocks = (const PackedBlock *)(d + off_blk) + bi;
+        q.job.mats = (const float2 *)(d + off_mat);
+        q.job.out = nullptr;
+        q.job.n = r->n;
+        q.job.nblocks = (int)r->blocks.size();
+        q.res[0] = q.res[1] = 0.0;
+        q.done = 0;
         for (auto &b : r->blocks) {
             PackedBlock &pb = hb[bi++];
             pb.k = b.k;
-            for (int q = 0; q < kMaxK; q++) pb.tpos[q] = q < b.k ? b.tpos[q] : 0;
+            for (int t = 0; t < kMaxK; t++) pb.tpos[t] = t < b.k ? b.tpos[t] : 0;
             pb.mat_off = (uint32_t)mi;
             std::memcpy(hm + mi, b.mat.data(), b.mat.size() * sizeof(float2));
             mi += b.mat.size();
@@ -477,25 +573,61 @@ int launch_packed(srv_t *s, Batch &B)
         si += 1ull << r->n;
     }
     if (cudaMemcpyAsync(d, B.h_stage, table_bytes, cudaMemcpyHostToDevice, B.st) != cudaSuccess) return SIM_E_CUDA;
-    k_circuit_cta<<<(unsigned)nj, kPackThreads, 0, B.st>>>((const PackedJob *)d);
-    if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
-    if (cudaMemcpyAsync(B.h_res, d + off_res, nj * 2 * sizeof(double), cudaMemcpyDeviceToHost, B.st) != cudaSuccess)
-        return SIM_E_CUDA;
-    si = 0;
-    for (size_t j = 0; j < nj; j++) {
-        auto &r = B.jobs[j];
-        if (r->out_amps &&
-            cudaMemcpyAsync(r->out_amps, (float2 *)(d + off_state) + si, sizeof(float2) << r->n,
+    if (cudaEventRecord(B.ev, B.st) != cudaSuccess) return SIM_E_CUDA;
+    s->next_index += nj;
+    B.res.assign(2 * nj, 0.0);
+    B.state = Batch::Uploading;
+    release_on_error.armed = false;
+    return SIM_OK;
+}
+
+// After its jobs are done: each requested amplitude vector copied out, the allocation freed, the
+// event recorded (scheduler thread, lock held).
+int copy_out_packed(Batch &B)
+{
+    size_t si = 0;
+    const char *d = (const char *)B.d_mem;
+    size_t nblk = 0, nmat = 0;
+    for (auto &r : B.jobs) {
+        nblk += r->blocks.size();
+        for (auto &b : r->blocks) nmat += b.mat.size();
+    }
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t off_state = align(align(nblk * sizeof(PackedBlock)) + nmat * sizeof(float2));
+    int rc = SIM_OK;
+    for (auto &r : B.jobs) {
+        if (r->out_amps && rc == SIM_OK &&
+            cudaMemcpyAsync(r->out_amps, (const float2 *)(d + off_state) + si, sizeof(float2) << r->n,
                             cudaMemcpyDeviceToHost, B.st) != cudaSuccess)
-            return SIM_E_CUDA;
+            rc = SIM_E_CUDA;
         si += 1ull << r->n;
     }
-    const cudaError_t fe = cudaFreeAsync(B.d_mem, B.st);  // released once the batch's work is done
+    if (cudaFreeAsync(B.d_mem, B.st) != cudaSuccess) rc = SIM_E_CUDA;
     B.d_mem = nullptr;
-    if (fe != cudaSuccess) return SIM_E_CUDA;
-    if (cudaEventRecord(B.ev, B.st) != cudaSuccess) return SIM_E_CUDA;
-    B.busy = true;
-    return SIM_OK;
+    if (cudaEventRecord(B.ev, B.st) != cudaSuccess) rc = SIM_E_CUDA;
+    B.state = Batch::CopyingOut;
+    return rc;
+}
+
+// Jobs published and not yet seen done; launch a worker when they outnumber the CTAs of the
+// workers still running (scheduler thread, lock held).
+void manage_workers(srv_t *s, uint64_t not_done, bool *progressed)
+{
+    int running = 0;
+    for (int w = 0; w < 2; w++) {
+        if (s->wctas[w] && cudaEventQuery(s->wev[w]) != cudaErrorNotReady) s->wctas[w] = 0;
+        running += s->wctas[w];
+    }
+    if (not_done <= (uint64_t)running) return;
+    for (int w = 0; w < 2; w++)
+        if (!s->wctas[w]) {
+            const int ctas = (int)std::min<uint64_t>(not_done - running, (uint64_t)(2 * s->sms));
+            k_packed_worker<<<ctas, kPackThreads, 0, s->wst[w]>>>(s->d_ctl, s->d_ring, s->d_head);
+            if (cudaGetLastError() != cudaSuccess || cudaEventRecord(s->wev[w], s->wst[w]) != cudaSuccess) return;
+            s->wctas[w] = ctas;
+            *progressed = true;
+            return;
+        }
 }
 
 void scheduler(srv_t *s)
@@ -515,22 +647,70 @@ void scheduler(srv_t *s)
             r.reset();
             progressed = true;
         }
-        // completions: packed batches
+        // packed units: publish uploaded jobs to the worker queue, collect the done ones, retire
+        // them once their amplitudes are out
+        uint64_t not_done = 0;
         for (auto &B : s->batches) {
-            if (!B.busy) continue;
-            const cudaError_t e = cudaEventQuery(B.ev);
-            if (e == cudaErrorNotReady) continue;
-            for (size_t j = 0; j < B.jobs.size(); j++)
-                finish(s, B.jobs[j], e == cudaSuccess ? SIM_OK : SIM_E_CUDA, B.h_res[2 * j], B.h_res[2 * j + 1]);
-            B.jobs.clear();
-            B.busy = false;
-            progressed = true;
+            const size_t nj = B.jobs.size();
+            if (B.state == Batch::Uploading) {
+                const cudaError_t e = cudaEventQuery(B.ev);
+                if (e == cudaErrorNotReady) {
+                    continue;
+                } else if (e != cudaSuccess) {
+                    cudaStreamSynchronize(B.st);
+                    for (auto &r : B.jobs) finish(s, r, SIM_E_CUDA, 0.0, 0.0);
+                    s->retired += nj;
+                    B.jobs.clear();
+                    B.state = Batch::Free;
+                    progressed = true;
+                    continue;
+                }
+                s->published += nj;  // descriptors written before the upload: make them visible, then the count
+                std::atomic_thread_fence(std::memory_order_release);
+                __atomic_store_n(s->ctl, (uint32_t)s->published, __ATOMIC_RELEASE);
+                B.state = Batch::Running;
+                progressed = true;
+            }
+            if (B.state == Batch::Running) {
+                size_t done = 0;
+                for (size_t j = 0; j < nj; j++)
+                    done += __atomic_load_n(&s->ring[(B.first + j) % kQueueCap].done, __ATOMIC_ACQUIRE) != 0;
+                if (done < nj) {
+                    not_done += nj - done;
+                    continue;
+                }
+                for (size_t j = 0; j < nj; j++) {
+                    const QSlot &q = s->ring[(B.first + j) % kQueueCap];
+                    B.res[2 * j] = q.res[0];
+                    B.res[2 * j + 1] = q.res[1];
+                }
+                const int rc = copy_out_packed(B);
+                if (rc != SIM_OK) {  // the queued copies drain before the waiters learn of it
+                    cudaStreamSynchronize(B.st);
+                    for (auto &r : B.jobs) finish(s, r, rc, 0.0, 0.0);
+                    s->retired += nj;
+                    B.jobs.clear();
+                    B.state = Batch::Free;
+                }
+                progressed = true;
+            }
+            if (B.state == Batch::CopyingOut) {
+                const cudaError_t e = cudaEventQuery(B.ev);
+                if (e == cudaErrorNotReady) continue;
+                for (size_t j = 0; j < nj; j++)
+                    finish(s, B.jobs[j], e == cudaSuccess ? SIM_OK : SIM_E_CUDA, B.res[2 * j], B.res[2 * j + 1]);
+                s->retired += nj;
+                B.jobs.clear();
+                B.state = Batch::Free;
+                progressed = true;
+            }
         }
+        manage_workers(s, not_done, &progressed);
         if (progressed) s->cv_done.notify_all();
         if (s->stop && s->queue.empty()) {
             bool idle = pack_pending.empty();
             for (auto &r : s->slot_req) idle &= !r;
-            for (auto &B : s->batches) idle &= !B.busy;
+            for (auto &B : s->batches) idle &= B.state == Batch::Free;
             if (idle) break;
         }
         // admission, in arrival order; a request that does not fit may be overtaken by later ones
@@ -575,22 +755,24 @@ void scheduler(srv_t *s)
                 progressed = true;
             }
         }
-        // packed launch: whenever a batch stream is free
+        // packed upload: whenever a unit is free and the queue has room (a ring entry is reused only
+        // once its job has been retired)
         if (!pack_pending.empty())
             for (auto &B : s->batches)
-                if (!B.busy) {
-                    const size_t take = std::min(pack_pending.size(), (size_t)s->o.max_pack);
+                if (B.state == Batch::Free) {
+                    const uint64_t room = kQueueCap - (s->next_index - s->retired);
+                    const size_t take = std::min<size_t>({pack_pending.size(), (size_t)s->o.max_pack, (size_t)room});
+                    if (take == 0) break;
                     B.jobs.assign(pack_pending.begin(), pack_pending.begin() + take);
                     pack_pending.erase(pack_pending.begin(), pack_pending.begin() + take);
-                    const int rc = launch_packed(s, B);
+                    const int rc = upload_packed(s, B);
                     if (rc != SIM_OK) {
-                        // copies into the jobs' out_amps (and from the pinned staging buffer) may
-                        // already be queued on the batch stream: let them drain before any waiter
-                        // is told its request failed and reuses its buffer
+                        // a copy from the pinned staging buffer may already be queued: let it drain
+                        // before the staging is reused or any waiter is told its request failed
                         cudaStreamSynchronize(B.st);
                         for (auto &r : B.jobs) finish(s, r, rc, 0.0, 0.0);
                         B.jobs.clear();
-                        B.busy = false;
+                        B.state = Batch::Free;
                         s->cv_done.notify_all();
                     }
                     progressed = true;
@@ -612,13 +794,20 @@ void srv_release(srv_t *s)
         s->worker.join();
     }
     DeviceScope dev_scope(s->o.device);
+    for (int w = 0; w < 2; w++) {  // workers leave within their idle time once nothing is published
+        if (s->wst[w]) cudaStreamSynchronize(s->wst[w]);
+        if (s->wev[w]) cudaEventDestroy(s->wev[w]);
+        if (s->wst[w]) cudaStreamDestroy(s->wst[w]);
+    }
     for (auto &B : s->batches) {
         if (B.st) cudaStreamSynchronize(B.st);
         if (B.ev) cudaEventDestroy(B.ev);
         if (B.st) cudaStreamDestroy(B.st);
         if (B.h_stage) cudaFreeHost(B.h_stage);
-        if (B.h_res) cudaFreeHost(B.h_res);
     }
+    if (s->ring) cudaFreeHost(s->ring);
+    if (s->ctl) cudaFreeHost(s->ctl);
+    if (s->d_head) cudaFree(s->d_head);
     for (auto &kv : s->reqs)
         if (kv.second->ev) cudaEventDestroy(kv.second->ev);
     for (auto *h : s->slots) sim_destroy(h);
@@ -670,15 +859,33 @@ int srv_create(const srv_opts *opts, srv_t **out)
         s->slots.push_back(h);
     }
     s->slot_req.resize(s->slots.size());
-    s->batches.resize(2);
+    s->batches.resize(4);
     for (auto &B : s->batches) {
         if (cudaStreamCreateWithFlags(&B.st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaHostAlloc(&B.h_res, sizeof(double) * 2 * s->o.max_pack, cudaHostAllocDefault) != cudaSuccess) {
+            cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess) {
             srv_release(s);
-            return srv_fail(nullptr, SIM_E_CUDA, "srv_create: stream/pinned setup failed");
+            return srv_fail(nullptr, SIM_E_CUDA, "srv_create: stream setup failed");
         }
     }
+    // the packed jobs' queue: ring and published count in mapped pinned memory, claim counter on
+    // the device; two worker streams
+    bool qok = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->o.device) == cudaSuccess &&
+               cudaHostAlloc(reinterpret_cast<void **>(&s->ring), sizeof(QSlot) * kQueueCap, cudaHostAllocMapped) ==
+                   cudaSuccess &&
+               cudaHostAlloc(reinterpret_cast<void **>(&s->ctl), 128, cudaHostAllocMapped) == cudaSuccess &&
+               cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->d_ring), s->ring, 0) == cudaSuccess &&
+               cudaHostGetDevicePointer(reinterpret_cast<void **>(&s->d_ctl), s->ctl, 0) == cudaSuccess &&
+               cudaMalloc(reinterpret_cast<void **>(&s->d_head), sizeof(uint32_t)) == cudaSuccess &&
+               cudaMemset(s->d_head, 0, sizeof(uint32_t)) == cudaSuccess;
+    for (int w = 0; w < 2 && qok; w++)
+        qok = cudaStreamCreateWithFlags(&s->wst[w], cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s->wev[w], cudaEventDisableTiming) == cudaSuccess;
+    if (!qok) {
+        srv_release(s);
+        return srv_fail(nullptr, SIM_E_CUDA, "srv_create: packed-job queue setup failed");
+    }
+    std::memset(s->ring, 0, sizeof(QSlot) * kQueueCap);
+    std::memset(s->ctl, 0, 128);
     if (cudaHostAlloc(&s->h_results, sizeof(double) * 2 * kResultRing, cudaHostAllocDefault) != cudaSuccess) {
         s->h_results = nullptr;
         srv_release(s);
