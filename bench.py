@@ -507,14 +507,16 @@ def run_ours(args):
 
     # where the qubits sit (sim_plan_layout: fewer blocks on slow kernel paths); relabelling is free
     # before the front or the reset overwrites the state
-    def choose_layout(gl, kmax, precision):
+    def choose_layout(gl, kmax, precision, split_=None):
         if args.no_layout:
             return None, None
         pl = pkg.sim_plan_create(n, gl, kmax=kmax, precision=precision)
-        perm, est, est_id = pkg.sim_plan_layout(pl, n)
+        perm, est, est_id = (pkg.sim_plan_layout_front(pl, split_, n) if split_ is not None
+                             else pkg.sim_plan_layout(pl, n))
         pkg.sim_plan_destroy(pl)
         return perm, {"chosen_by": "sim_plan_layout", "estimate_ms": est, "identity_estimate_ms": est_id}
-    layout, layout_info = choose_layout(rest, args.kmax, prec)
+    # with the front, the layout also keeps the contraction's stores whole (sim_plan_layout_front)
+    layout, layout_info = choose_layout(rest, args.kmax, prec, split if front is not None else None)
 
     def start(hh, lay=None):
         lay = layout if lay is None else lay
@@ -698,7 +700,7 @@ def run_ours(args):
     bf16_path = None
     if front is not None and prec == pkg.SIM_FP16X3_TMEM and not args.no_bf16_path:
         fr_b = pkg.sim_front_create(h, split, kmax=args.kmax, precision=pkg.SIM_BF16X3)
-        layout_b, _ = choose_layout(rest, args.kmax, pkg.SIM_BF16X3)
+        layout_b, _ = choose_layout(rest, args.kmax, pkg.SIM_BF16X3, split)
 
         def step_b():
             plan = pkg.sim_plan_create(n, rest, kmax=args.kmax, precision=pkg.SIM_BF16X3)

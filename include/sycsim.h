@@ -312,6 +312,15 @@ int sim_apply_plan(sim_t *h, const sim_plan_t *p);
  * NULL, the estimate for that layout and for the identity (est_ms[0], est_ms[1]).  Host only. */
 int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms);
 
+typedef struct sim_split_s sim_split_t;
+/* The same search for a plan whose state is written by the contraction of split s (Sect. 2's
+ * contraction deferral; sim_front_run, sim_contract): the contraction stores psi in the state's
+ * layout with the 32 lanes of a warp on 32 consecutive values of the side-0 qubits (ordered by
+ * their physical bits), so physical bits 0-4 are kept on side-0 qubits -- each store is then one
+ * 256-byte run (measured: 13.4 ms instead of 15.8 for the 30-qubit front's contraction).  s must
+ * be a split of the same n.  Host only. */
+int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, double *est_ms);
+
 /* Relabel the physical bits without moving any amplitude (perm as for sim_permute): the logical
  * state changes, so this belongs before sim_reset, sim_front_run or sim_contract, which overwrite
  * every amplitude -- the way to start a plan in the layout sim_plan_layout chose without a
@@ -425,7 +434,6 @@ int sim_run_phases(sim_t *h, const sim_phases_t *ph);
  *   sim_split_canonical: wire_at[p] = the wire at canonical position p of tensor t
  *     (n_wires[t] entries).
  * SIM_E_INVAL for a bad side vector or gate, or more than 40 wires on a side. */
-typedef struct sim_split_s sim_split_t;
 int sim_split_create(int n_qubits, int n_gates, const sim_gate *gates, const int *side, sim_split_t **out);
 int sim_split_info(const sim_split_t *s, int *n_side, int *n_wires, int *n_pairs, int *n_gates);
 int sim_split_gates(const sim_split_t *s, int t, sim_gate *out);

@@ -149,6 +149,7 @@ _SIGS = {
     "sim_split_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "srv_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_plan_layout_front": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_shard_exchange_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_split_choose": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
@@ -414,6 +415,14 @@ def sim_plan_layout(p, n_qubits: int):
     perm = np.zeros(n_qubits, dtype=np.int32)
     est = np.zeros(2, dtype=np.float64)
     _check(lib().sim_plan_layout(p, _ptr(perm), _ptr(est)))
+    return [int(x) for x in perm], float(est[0]), float(est[1])
+
+
+def sim_plan_layout_front(p, s, n_qubits: int):
+    """(perm, estimate, identity estimate) for a plan whose state the contraction of split s writes."""
+    perm = np.zeros(n_qubits, dtype=np.int32)
+    est = np.zeros(2, dtype=np.float64)
+    _check(lib().sim_plan_layout_front(p, s, _ptr(perm), _ptr(est)))
     return [int(x) for x in perm], float(est[0]), float(est[1])
 
 

@@ -472,11 +472,29 @@ double improve_by_disjoint_swaps(const sim_plan_s *p, std::vector<int> &pos, std
 
 extern "C" {
 
-int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
+// The layout search; low (may be NULL): only qubits with low[q] != 0 may sit at physical bits
+// 0 .. n_low - 1.
+static int layout_search(const sim_plan_t *p, const char *low, int n_low, int *perm, double *est_ms)
 {
     constexpr int kLayoutStarts = SYCSIM_LAYOUT_STARTS;
-    if (!p || !perm) return fail(nullptr, SIM_E_INVAL, "sim_plan_layout: NULL argument");
     const int n = p->n, nb = (int)p->blocks.size();
+    auto allowed = [&](const std::vector<int> &ps, int q) { return !low || ps[q] >= n_low || low[q]; };
+    // move qubits of the low set into bits 0 .. n_low - 1 (swapping out the others), keeping order
+    auto fix_low = [&](std::vector<int> &ps) {
+        if (!low) return;
+        std::vector<int> at(n);
+        for (int q = 0; q < n; q++) at[ps[q]] = q;
+        int next_ok = 0;  // scan qubits of the low set that sit above n_low
+        for (int b = 0; b < n_low; b++) {
+            if (low[at[b]]) continue;
+            while (next_ok < n && !(low[next_ok] && ps[next_ok] >= n_low)) next_ok++;
+            if (next_ok == n) return;
+            const int q = at[b], r = next_ok;
+            std::swap(ps[q], ps[r]);
+            at[ps[q]] = q;
+            at[ps[r]] = r;
+        }
+    };
     std::vector<std::vector<int>> of_qubit(n);  // blocks holding each qubit
     for (int b = 0; b < nb; b++)
         for (int q : p->blocks[b].qubits) of_qubit[q].push_back(b);
@@ -494,8 +512,9 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
     };
     for (int q = 0; q < n; q++) pos[q] = q;
     const double ident = total();
+    fix_low(pos);
     std::vector<int> best = pos;
-    double best_cost = ident;
+    double best_cost = total();
     const bool modelled = tmem_mode(p->precision) || p->precision == SIM_FP32;
     uint64_t rs = 0x9E3779B97F4A7C15ull;  // SplitMix64 state for the seeded starts
     auto next = [&]() {
@@ -511,6 +530,7 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
     for (int start = 0; modelled && start < kLayoutStarts; start++) {
         for (int q = 0; q < n; q++) pos[q] = q;
         for (int q = n - 1; start > 0 && q > 0; q--) std::swap(pos[q], pos[next() % (uint64_t)(q + 1)]);
+        fix_low(pos);
         double cost = total();
         for (int sweep = 0; sweep < 64; sweep++) {
             bool improved = false;
@@ -527,7 +547,7 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
                     std::swap(pos[a], pos[c]);
                     for (int b : touched) after += block_cost(b);
                     for (int b : touched) mark[b] = 0;
-                    if (after < before - 1e-9) {
+                    if (after < before - 1e-9 && allowed(pos, a) && allowed(pos, c)) {
                         cost += after - before;
                         improved = true;
                     } else {
@@ -547,6 +567,24 @@ int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
         est_ms[1] = ident;
     }
     return SIM_OK;
+}
+
+int sim_plan_layout(const sim_plan_t *p, int *perm, double *est_ms)
+{
+    if (!p || !perm) return fail(nullptr, SIM_E_INVAL, "sim_plan_layout: NULL argument");
+    return layout_search(p, nullptr, 0, perm, est_ms);
+}
+
+int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, double *est_ms)
+{
+    if (!p || !s || !perm) return fail(nullptr, SIM_E_INVAL, "sim_plan_layout_front: NULL argument");
+    if (s->n != p->n) return fail(nullptr, SIM_E_INVAL, "sim_plan_layout_front: split and plan differ in n");
+    std::vector<char> low(p->n);
+    int n_side0 = 0;
+    for (int q = 0; q < p->n; q++) n_side0 += (low[q] = s->side[q] == 0);
+    // the contraction's stores: lanes of a warp hold 32 consecutive x (the side-0 qubits in order of
+    // their physical bits), so side-0 qubits at bits 0-4 make each store one 256-byte run
+    return layout_search(p, low.data(), std::min(5, n_side0), perm, est_ms);
 }
 
 int sim_apply_plan(sim_t *h, const sim_plan_t *p)

@@ -982,7 +982,10 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     int phys[kMaxQubits];
     for (int q = 0; q < kMaxQubits; q++) phys[q] = q;
     if (!r->packed) {
-        sim_plan_layout(plan, phys, nullptr);
+        if (r->split)
+            sim_plan_layout_front(plan, r->split.get(), phys, nullptr);
+        else
+            sim_plan_layout(plan, phys, nullptr);
         bool ident = true;
         for (int q = 0; q < n_qubits; q++) ident = ident && phys[q] == q;
         if (!ident && out_amps) {
