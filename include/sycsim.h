@@ -556,6 +556,7 @@ typedef struct srv_stats_t {
     double p50_ms, p99_ms, mean_ms; /* latency: submit -> completion */
     double circuits_per_s;          /* completed / (last completion - first submit) */
     uint64_t hbm_budget, hbm_used;
+    uint64_t graph_replays;         /* requests served by replaying a repeated circuit's CUDA graph */
 } srv_stats_t;
 
 int srv_create(const srv_opts *o, srv_t **out);

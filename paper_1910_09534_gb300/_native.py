@@ -75,7 +75,7 @@ class SrvStats(ctypes.Structure):
                 ("rejected", ctypes.c_uint64), ("in_flight", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("circuits_per_s", ctypes.c_double), ("hbm_budget", ctypes.c_uint64),
-                ("hbm_used", ctypes.c_uint64)]
+                ("hbm_used", ctypes.c_uint64), ("graph_replays", ctypes.c_uint64)]
 
 
 class SimError(RuntimeError):

@@ -242,6 +242,19 @@ struct Prepared {
     std::vector<float2> mat;
 };
 
+// A circuit submitted more than once (not packed, up to kGraphMaxQubits, no contraction front):
+// a handle holding its state in the layout the server chose for it and its plan captured once as a
+// CUDA graph (sim_graph_create); each repeat replays the graph there, one at a time.  The same
+// kernels, layout, reduction and readout as the stream path, so the results are bit-identical.
+struct GraphEntry {
+    sim_t *h = nullptr;
+    sim_plan_t *plan = nullptr;
+    sim_graph_t *g = nullptr;
+    std::vector<int> back;  // physical bit -> logical qubit for the readout (empty: identity)
+    uint64_t bytes = 0;     // device memory held (reserved from the budget)
+    bool busy = false;
+};
+
 struct Req {
     uint64_t ticket = 0;
     int n = 0;
@@ -263,6 +276,7 @@ struct Req {
     int status = 1;  // 1 pending, 0 ok, < 0 error
     double norm = 0.0, s2 = 0.0;
     int bypassed = 0;
+    std::shared_ptr<GraphEntry> graph;  // repeated circuit: replay this entry's graph
     // in flight (unpacked)
     int slot = -1;
     float2 *d_state = nullptr;
@@ -292,6 +306,8 @@ constexpr int kMaxBypass = 64;
 constexpr int kFrontMinQubits = 26;      // smaller states: the passes a front saves are too short
 constexpr double kFrontMinShare = 0.3;   // a front with fewer of the gates is not worth a contraction
 constexpr int kResultRing = 1 << 16;
+constexpr int kGraphMaxQubits = 24;  // graph entries hold their own state: 8 * 2^24 bytes at most
+constexpr int kGraphMaxEntries = 8;
 
 }  // namespace
 }  // namespace sycsim
@@ -309,6 +325,11 @@ struct srv_s {
     std::vector<sim_t *> slots;
     std::vector<std::shared_ptr<Req>> slot_req;
     std::vector<Batch> batches;
+    // repeated circuits (CUDA graphs): gate-list hash -> entry; hashes seen once
+    std::mutex graph_mu;
+    std::unordered_map<uint64_t, std::shared_ptr<GraphEntry>> graphs;
+    std::unordered_map<uint64_t, int> seen;
+    std::vector<std::shared_ptr<Req>> graph_inflight;
     // the packed jobs' queue (see k_packed_worker): ring entries in mapped pinned memory, the
     // published count beside them, the claim counter in device memory, up to two workers in flight
     QSlot *ring = nullptr, *d_ring = nullptr;
@@ -332,7 +353,7 @@ struct srv_s {
     std::map<std::pair<int, int>, Tune> tune;
     std::mutex tune_mu;
     // stats
-    uint64_t submitted = 0, completed = 0, rejected = 0;
+    uint64_t submitted = 0, completed = 0, rejected = 0, graph_replays = 0;
     std::vector<double> lat_ms;
     Clock::time_point t_first, t_last;
     bool any_done = false;
@@ -630,6 +651,27 @@ void manage_workers(srv_t *s, uint64_t not_done, bool *progressed)
         }
 }
 
+// Replay a repeated circuit's graph on its entry's handle (scheduler thread, lock held): reset,
+// the plan's blocks, the reduction and the readout, all enqueued on the entry's stream.
+int start_graph(srv_t *s, const std::shared_ptr<Req> &r)
+{
+    GraphEntry &E = *r->graph;
+    sim_t *h = E.h;
+    cudaStream_t st = h->stream;
+    if (sim_reset(h, 0) != SIM_OK || sim_graph_launch(h, E.g) != SIM_OK) return SIM_E_CUDA;
+    if (launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, st) != 0) return SIM_E_CUDA;
+    if (cudaMemcpyAsync(r->h_res, h->d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SIM_E_CUDA;
+    if (r->out_amps && !E.back.empty() && launch_permute(h, h->d_state, r->n, E.back.data(), st) != 0)
+        return SIM_E_CUDA;  // amplitudes leave in logical order (the next replay resets the state)
+    if (r->out_amps &&
+        cudaMemcpyAsync(r->out_amps, h->d_state, sizeof(float2) << r->n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SIM_E_CUDA;
+    if (cudaEventRecord(r->ev, st) != cudaSuccess) return SIM_E_CUDA;
+    (void)s;
+    return SIM_OK;
+}
+
 void scheduler(srv_t *s)
 {
     cudaSetDevice(s->o.device);
@@ -637,6 +679,19 @@ void scheduler(srv_t *s)
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         bool progressed = false;
+        // completions: graph replays
+        for (auto it = s->graph_inflight.begin(); it != s->graph_inflight.end();) {
+            auto r = *it;
+            const cudaError_t e = cudaEventQuery(r->ev);
+            if (e == cudaErrorNotReady) {
+                ++it;
+                continue;
+            }
+            finish(s, r, e == cudaSuccess ? SIM_OK : SIM_E_CUDA, r->h_res[0], r->h_res[1]);
+            r->graph->busy = false;
+            it = s->graph_inflight.erase(it);
+            progressed = true;
+        }
         // completions: unpacked slots
         for (size_t i = 0; i < s->slots.size(); i++) {
             auto &r = s->slot_req[i];
@@ -711,6 +766,7 @@ void scheduler(srv_t *s)
             bool idle = pack_pending.empty();
             for (auto &r : s->slot_req) idle &= !r;
             for (auto &B : s->batches) idle &= B.state == Batch::Free;
+            idle &= s->graph_inflight.empty();
             if (idle) break;
         }
         // admission, in arrival order; a request that does not fit may be overtaken by later ones
@@ -720,7 +776,20 @@ void scheduler(srv_t *s)
             if (first_blocked && first_blocked->bypassed >= kMaxBypass) break;
             auto r = *it;
             bool admitted = false;
-            if (s->used + r->bytes <= s->budget) {
+            if (r->graph) {  // its memory is the entry's: it waits only for the entry's previous replay
+                if (!r->graph->busy) {
+                    r->graph->busy = true;
+                    const int rc = start_graph(s, r);
+                    if (rc != SIM_OK) {
+                        r->graph->busy = false;
+                        finish(s, r, rc, 0.0, 0.0);
+                    } else {
+                        s->graph_inflight.push_back(r);
+                        s->graph_replays++;
+                    }
+                    admitted = true;
+                }
+            } else if (s->used + r->bytes <= s->budget) {
                 if (r->packed) {
                     s->used += r->bytes;
                     pack_pending.push_back(r);
@@ -810,6 +879,12 @@ void srv_release(srv_t *s)
     if (s->d_head) cudaFree(s->d_head);
     for (auto &kv : s->reqs)
         if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+    for (auto &kv : s->graphs) {
+        GraphEntry &E = *kv.second;
+        if (E.g) sim_graph_destroy(E.g);
+        if (E.plan) sim_plan_destroy(E.plan);
+        if (E.h) sim_destroy(E.h);
+    }
     for (auto *h : s->slots) sim_destroy(h);
     if (s->h_results) cudaFreeHost(s->h_results);
     delete s;
@@ -905,6 +980,10 @@ int srv_destroy(srv_t *s)
 
 const char *srv_last_error(const srv_t *s) { return s ? s->err.c_str() : thread_error(); }
 
+static int make_graph_entry(srv_t *s, uint64_t key, int n, int n_gates, const sim_gate *gates,
+                            const sim_plan_opts &po);
+static int enqueue_request(srv_t *s, const std::shared_ptr<Req> &r, uint64_t *ticket);
+
 int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void *out_amps, uint64_t *ticket)
 {
     if (!s || !ticket) return srv_fail(s, SIM_E_INVAL, "srv_submit: NULL argument");
@@ -943,6 +1022,31 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     int front = 0;
     std::vector<int> side(n_qubits, 0);
     const bool want_front = tuned_front >= 0 ? tuned_front == 1 : n_qubits >= kFrontMinQubits;
+    // a repeated circuit replays its CUDA graph (created at its second submission)
+    const bool graph_ok = !r->packed && n_qubits <= kGraphMaxQubits &&
+                          !(tmem_mode(r->precision) && want_front && s->o.front_pairs >= 0);
+    if (graph_ok) {
+        uint64_t key = 0xcbf29ce484222325ull;  // FNV-1a over the size, the options and the gate records
+        auto mix = [&](const void *p, size_t nb) {
+            const unsigned char *c = static_cast<const unsigned char *>(p);
+            for (size_t i = 0; i < nb; i++) key = (key ^ c[i]) * 0x100000001b3ull;
+        };
+        mix(&n_qubits, sizeof n_qubits);
+        mix(&po.kmax, sizeof po.kmax);
+        mix(&po.precision, sizeof po.precision);
+        mix(gates, sizeof(sim_gate) * (size_t)n_gates);
+        std::lock_guard<std::mutex> glk(s->graph_mu);
+        auto it = s->graphs.find(key);
+        if (it == s->graphs.end() && ++s->seen[key] >= 2 && (int)s->graphs.size() < kGraphMaxEntries) {
+            const int grc = make_graph_entry(s, key, n_qubits, n_gates, gates, po);
+            if (grc == SIM_OK) it = s->graphs.find(key);
+        }
+        if (it != s->graphs.end()) {
+            r->graph = it->second;
+            r->bytes = 0;  // the entry's memory was reserved when it was made
+            return enqueue_request(s, r, ticket);
+        }
+    }
     if (!r->packed && tmem_mode(r->precision) && want_front && s->o.front_pairs >= 0) {
         int nf = 0;
         if (split_choose(n_qubits, n_gates, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf,
@@ -1021,6 +1125,54 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
         if (tp) sim_plan_destroy(tp);
     sim_plan_destroy(plan);
     if (rc != SIM_OK) return srv_fail(s, rc, "srv_submit: block preparation failed");
+    return enqueue_request(s, r, ticket);
+}
+
+// Make the graph entry of a repeated circuit (caller's thread, graph_mu held): the plan as
+// srv_submit plans it without a front, a handle of n qubits in the layout sim_plan_layout picks,
+// the plan captured on it; its memory is taken from the budget.
+static int make_graph_entry(srv_t *s, uint64_t key, int n, int n_gates, const sim_gate *gates,
+                            const sim_plan_opts &po)
+{
+    const uint64_t bytes = (sizeof(float2) << n) + (1u << 20);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->used + bytes > s->budget) return SIM_E_BUSY;
+        s->budget -= bytes;
+    }
+    auto E = std::make_shared<GraphEntry>();
+    E->bytes = bytes;
+    int rc = sim_plan_create(n, n_gates, gates, &po, &E->plan);
+    int phys[kMaxQubits];
+    if (rc == SIM_OK) rc = sim_plan_layout(E->plan, phys, nullptr);
+    if (rc == SIM_OK) {
+        sim_opts so{};
+        so.device = s->o.device;
+        rc = sim_create(n, 0, &so, &E->h);
+    }
+    if (rc == SIM_OK) rc = sim_set_layout(E->h, phys);
+    if (rc == SIM_OK) rc = sim_graph_create(E->h, E->plan, &E->g);
+    if (rc != SIM_OK) {
+        if (E->g) sim_graph_destroy(E->g);
+        if (E->plan) sim_plan_destroy(E->plan);
+        if (E->h) sim_destroy(E->h);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->budget += bytes;
+        return rc;
+    }
+    bool ident = true;
+    for (int q = 0; q < n; q++) ident = ident && phys[q] == q;
+    if (!ident) {
+        E->back.assign(n, 0);
+        for (int q = 0; q < n; q++) E->back[phys[q]] = q;
+    }
+    s->graphs[key] = E;
+    return SIM_OK;
+}
+
+// Queue a planned (or graph-replay) request: its completion event, a ticket, the queue.
+static int enqueue_request(srv_t *s, const std::shared_ptr<Req> &r, uint64_t *ticket)
+{
     cudaError_t ee;
     {
         DeviceScope dev_scope(s->o.device);
@@ -1190,6 +1342,7 @@ int srv_stats(srv_t *s, srv_stats_t *out)
     }
     out->hbm_budget = s->budget;
     out->hbm_used = s->used;
+    out->graph_replays = s->graph_replays;
     return SIM_OK;
 }
 

@@ -70,6 +70,7 @@ static int layout(void)
     FIELD(srv_stats_t, circuits_per_s);
     FIELD(srv_stats_t, hbm_budget);
     FIELD(srv_stats_t, hbm_used);
+    FIELD(srv_stats_t, graph_replays);
     SIZE(srv_stats_t);
     return 0;
 }

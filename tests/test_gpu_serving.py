@@ -190,3 +190,33 @@ def test_autotuned_server_matches_oracle_and_alone_equals_mix(pkg, oracle_mod):
     for c, a, b in zip(circuits, outs, alone):
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
         assert np.linalg.norm(a.astype(np.complex128) - oracle_mod.run_circuit(c)) <= TOL_FP32
+
+
+def test_repeated_circuit_replays_its_graph_bit_identically(pkg, oracle_mod):
+    # the second submission of the same circuit makes a CUDA-graph entry; later ones replay it
+    # with the stream path's kernels, layout and reduction: every result bit-identical, also to the
+    # same circuit served once by a fresh server (stream path), and to the oracle within 1e-5
+    circ = si.sycamore_circuit(si.near_square_grid(22), 12, seed=777)
+    g = pkg.gates_array(circ)
+    once = np.zeros(1 << 22, dtype=np.complex64)
+    srv = pkg.srv_create(small_n=20, slots=2, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        pkg.srv_wait(srv, pkg.srv_submit(srv, 22, g, once), 120000)
+        assert pkg.srv_stats(srv)["graph_replays"] == 0
+    finally:
+        pkg.srv_destroy(srv)
+    srv = pkg.srv_create(small_n=20, slots=2, precision=pkg.SIM_FP16X3_TMEM)
+    outs = [np.zeros(1 << 22, dtype=np.complex64) for _ in range(5)]
+    try:
+        for o in outs[:2]:  # the first on the stream path, the second makes and replays the graph
+            pkg.srv_wait(srv, pkg.srv_submit(srv, 22, g, o), 120000)
+        tickets = [pkg.srv_submit(srv, 22, g, o) for o in outs[2:]]  # queued together: one replay at a time
+        res = [pkg.srv_wait(srv, t, 120000) for t in tickets]
+        stats = pkg.srv_stats(srv)
+    finally:
+        pkg.srv_destroy(srv)
+    assert stats["graph_replays"] == 4
+    for o in outs:
+        assert np.array_equal(o.view(np.uint64), once.view(np.uint64))
+    assert np.linalg.norm(once.astype(np.complex128) - oracle_mod.run_circuit(circ)) <= TOL_FP32
+    assert all(abs(norm - 1.0) < 1e-5 for norm, _, _ in res)
