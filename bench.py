@@ -104,7 +104,8 @@ def parse():
                     help="run only the serving leg in the --precision given (fp32, else the split mode) "
                          "and print one JSON line")
     ap.add_argument("--no-large", action="store_true",
-                    help="skip the 33-qubit sliced runs (64 GiB state) of the default line")
+                    help="skip the 33-qubit sliced runs (64 GiB state) and the 35-qubit streamed run "
+                         "(256 GiB store) of the default line")
     ap.add_argument("--oracle-table", action="store_true",
                     help="time the CPU oracle on one and on all host cores for the 12-, 30- (sample), "
                          "28- (sample) and 24-qubit circuits, print one JSON line, and exit")
@@ -823,6 +824,9 @@ def run_ours(args):
         # configuration 3: 33 qubits (64 GiB) held as 8 slices over 3 bits, phases with in-place
         # permutation passes between them, in the default arithmetic and in FP32
         line["syc33_sliced"] = {p: large_case_run("syc33_6x6m3_d20", p, local) for p in ("fp16x3_tmem", "fp32")}
+        # configuration 4: 35 qubits (256 GiB) in a secondary store, 8 of its 16 regions pinned on the
+        # host and 8 in HBM, streamed through device slots of 2^31 amplitudes phase by phase
+        line["syc35_store"] = large_case_run("syc35_5x7_d16", "fp16x3_tmem", local)
     if ws == 1 and not args.no_serving:
         # configuration 5: 2000 circuits, Poisson arrivals, each arithmetic beside its one-at-a-time run
         line["serving"] = {p: serving_run(args.serving_circuits, local, r, p)
