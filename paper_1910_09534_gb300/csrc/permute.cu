@@ -25,6 +25,9 @@
 #ifndef SYCSIM_PERM_TILE
 #define SYCSIM_PERM_TILE 10  // minimum tile: 2^SYCSIM_PERM_TILE amplitudes
 #endif
+#ifndef SYCSIM_PERM_BULK
+#define SYCSIM_PERM_BULK 1  // in-place tiles through bulk copies (k_permute_tile_bulk)
+#endif
 #ifndef SYCSIM_PERM_TILE_SAME
 #define SYCSIM_PERM_TILE_SAME 12  // the same when no tile pairs swap (measured best of 10..13)
 #endif
@@ -47,6 +50,9 @@ struct PermGeom {
     uint64_t lin_off[16];   // global offset of p (row offset + low index)
     uint32_t lin_sidx[16];  // shared-memory slot of p (row-XOR swizzle)
     uint32_t lin_src[16];   // shared-memory slot of the amplitude that lands at p (swizzle o sig)
+    // bulk in-place path: local bit of thread-index bit j (bits 0-4: the lanes of a warp, chosen so
+    // that p and sig(p) both spread over the shared-memory banks), then the iteration bits
+    int8_t tbit[8], ibit[16];
 };
 
 __device__ __forceinline__ uint64_t insert_zero_bits_p(uint64_t x, const int *pos, int cnt)
@@ -128,6 +134,125 @@ __global__ void __launch_bounds__(256) k_permute_pass(PermGeom g)
     }
 }
 
+// The global side done by the bulk-copy engine: one copy per row of 2^LB contiguous amplitudes
+// into shared memory (completion counted in bytes on an mbarrier) -- the tile, and for a tile
+// pair (high-high transpositions) its partner's rows too --, the threads swap the pairs
+// (p, sig(p)) the in-tile involution exchanges in each tile, and one bulk store per row writes
+// the tile back, or, for a pair, each tile to its partner's rows.  sig is XOR-linear in
+// the local index p: sig(p) = sig(p_thread) ^ sig(p_iter), the second from a per-CTA table.
+// The only wait (the copies' mbarrier) is bounded by %globaltimer: on a timeout the CTA records
+// the failure, writes nothing back and waits (again bounded) for its copies before leaving.
+__device__ __forceinline__ uint64_t perm_now_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_permute_tile_bulk(PermGeom g, int *err)
+{
+    extern __shared__ __align__(128) float2 tile[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t p_it[64], sig_it[64];  // the iteration part of p, and its image under sig
+    __shared__ int ok;
+    const int nloc = g.LB + g.q, T = 1 << nloc;
+    const uint32_t row_bytes = 8u << g.LB;
+    const uint64_t base = insert_zero_bits_p((uint64_t)blockIdx.x << g.LB, g.rowpos, g.q);
+    uint64_t baseB = base;
+    for (int i = 0; i < g.nhh; ++i) {
+        const uint64_t ba = (base >> g.hh_a[i]) & 1, bb = (base >> g.hh_b[i]) & 1;
+        if (ba != bb) baseB ^= (1ull << g.hh_a[i]) | (1ull << g.hh_b[i]);
+    }
+    if (baseB < base) return;  // the partner CTA moves this pair
+    const bool same = baseB == base;
+    if (same && g.trivial_in) return;  // nothing in this tile moves
+    const int ntile = same ? 1 : 2;
+    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(&bar);
+    const uint32_t stile = (uint32_t)__cvta_generic_to_shared(tile);
+    auto sig_of = [&](uint32_t p) {
+        uint32_t r = 0;
+        for (int x = 0; x < nloc; ++x)
+            if ((p >> x) & 1) r |= 1u << g.sig[x];
+        return r;
+    };
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sbar),
+                     "r"((uint32_t)(ntile * T) * 8u)
+                     : "memory");
+        for (int t = 0; t < ntile; ++t)
+            for (int r = 0; r < (1 << g.q); ++r)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                        stile + (uint32_t)t * T * 8u + r * row_bytes),
+                    "l"(g.psi + (t ? baseB : base) + g.rowoff[r]), "r"(row_bytes), "r"(sbar)
+                    : "memory");
+    }
+    for (int it = threadIdx.x; it < (T >> 8); it += blockDim.x) {
+        uint32_t p = 0;
+        for (int j = 0; j < nloc - 8; ++j)
+            if ((it >> j) & 1) p |= 1u << g.ibit[j];
+        p_it[it] = p;
+        sig_it[it] = sig_of(p);
+    }
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = perm_now_ns();
+        uint32_t done = 0;
+        while (!done) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, 20000;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}\n"
+                : "=r"(done)
+                : "r"(sbar)
+                : "memory");
+            if (!done && perm_now_ns() - t0 > 4000000000ull) break;
+        }
+        ok = done;
+        if (!done && err) atomicExch(err, 1);
+    }
+    __syncthreads();
+    if (ok) {
+        uint32_t p_t = 0;  // blockDim = 256: p = (thread bits deposited) | (iteration bits deposited)
+        for (int j = 0; j < 8; ++j)
+            if ((threadIdx.x >> j) & 1) p_t |= 1u << g.tbit[j];
+        const uint32_t s_t = sig_of(p_t);
+        for (int t = 0; t < ntile && !g.trivial_in; ++t) {
+            float2 *tt = tile + t * T;
+            for (int it = 0; it < (T >> 8); ++it) {
+                const uint32_t p = p_t | p_it[it], q = s_t ^ sig_it[it];
+                if (p < q) {
+                    const float2 a = tt[p], c = tt[q];
+                    tt[p] = c;
+                    tt[q] = a;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the bulk stores read the tile
+        __syncthreads();
+        if (threadIdx.x == 0) {  // a pair's tiles go to each other's rows
+            for (int t = 0; t < ntile; ++t)
+                for (int r = 0; r < (1 << g.q); ++r)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(
+                                     g.psi + ((t == 0) == same ? base : baseB) + g.rowoff[r]),
+                                 "r"(stile + (uint32_t)t * T * 8u + r * row_bytes), "r"(row_bytes)
+                                 : "memory");
+            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");  // the tile is read out
+        }
+    } else if (threadIdx.x == 0) {  // no copy may still be writing the tile when the CTA leaves
+        const uint64_t t0 = perm_now_ns();
+        uint32_t done = 0;
+        while (!done && perm_now_ns() - t0 <= 4000000000ull)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, 20000;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}\n"
+                : "=r"(done)
+                : "r"(sbar)
+                : "memory");
+    }
+}
+
 // One involution pass; inv[b] = partner of bit b (inv[b] == b: fixed).
 // Geometry of one involution pass for tiles of at least 2^min_tile amplitudes.
 int build_geom(float2 *psi, int nbits, const int *inv, int min_tile, PermGeom &g)
@@ -202,7 +327,47 @@ int build_geom(float2 *psi, int nbits, const int *inv, int min_tile, PermGeom &g
     return 0;
 }
 
-int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
+// Bits of the local index the 32 lanes of a warp run over in k_permute_tile_bulk: a warp reads
+// and writes both p and sig(p); with 8-byte elements the bank pair is bits 0-3 of the index, so a
+// set of lane bits costs max(2, 32 >> |bits in 0-3|) wavefronts for p, the same for sig(p).  The
+// cheapest 5-subset of the bits 0-4 and their images under sig is taken (ties: the lowest), then
+// three more bits for the warps and the rest for the iterations, ascending.
+void choose_lane_bits(PermGeom &g)
+{
+    const int nloc = g.LB + g.q;
+    int cand[16], nc = 0;
+    bool in[16] = {};
+    for (int x = 0; x < 5 && x < nloc; x++) {
+        for (int y : {x, g.sig[x]})
+            if (!in[y]) in[y] = true, cand[nc++] = y;
+    }
+    std::sort(cand, cand + nc);
+    auto wf = [](int low) { return std::max(2, 32 >> low); };
+    int best_cost = 1 << 30;
+    uint32_t best = 0;
+    for (uint32_t m = 0; m < (1u << nc); m++) {
+        if (__builtin_popcount(m) != 5) continue;
+        int lp = 0, ls = 0;
+        for (int i = 0; i < nc; i++)
+            if ((m >> i) & 1) {
+                lp += cand[i] < 4;
+                ls += g.sig[cand[i]] < 4;
+            }
+        const int cost = wf(lp) + wf(ls);
+        if (cost < best_cost) best_cost = cost, best = m;
+    }
+    bool used[16] = {};
+    int j = 0;
+    for (int i = 0; i < nc; i++)
+        if ((best >> i) & 1) g.tbit[j++] = (int8_t)cand[i], used[cand[i]] = true;
+    for (int x = 0; x < nloc && j < 8; x++)
+        if (!used[x]) g.tbit[j++] = (int8_t)x, used[x] = true;
+    int k = 0;
+    for (int x = 0; x < nloc; x++)
+        if (!used[x]) g.ibit[k++] = (int8_t)x;
+}
+
+int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st, int *err)
 {
     bool any = false;
     for (int b = 0; b < nbits; b++) any |= inv[b] != b;
@@ -217,6 +382,17 @@ int launch_involution(float2 *psi, int nbits, const int *inv, cudaStream_t st)
     }
     const int LB = g.LB, q = g.q;
     const uint64_t tiles = 1ull << (nbits - LB - q);
+    if (SYCSIM_PERM_BULK && LB >= 5 && LB + q >= 8 && LB + q <= 14 && ((uintptr_t)psi & 15) == 0 &&
+        (g.nhh == 0 ? 1 : 2) * (sizeof(float2) << (LB + q)) <= 128 * 1024) {
+        const size_t tsm = (g.nhh == 0 ? 1 : 2) * (sizeof(float2) << (LB + q));
+        if (tsm > 48 * 1024 &&
+            cudaFuncSetAttribute(k_permute_tile_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm) !=
+                cudaSuccess)
+            return -1;
+        choose_lane_bits(g);
+        k_permute_tile_bulk<<<(unsigned)tiles, 256, tsm, st>>>(g, err);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
     const size_t smem = (g.nhh ? 2 : 1) * sizeof(float2) << (LB + q);  // a tile pair, or one tile
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_permute_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -262,7 +438,7 @@ int launch_permute(sim_t *h, float2 *psi, int nbits, const int *perm, cudaStream
         const double frac = moved_fraction(nbits, inv);
         if (frac == 0.0) continue;
         const int ps = h ? prof_begin(h, SIM_PROF_PERMUTE, 16.0 * amps * frac, st) : -1;
-        rc = launch_involution(psi, nbits, inv, st);
+        rc = launch_involution(psi, nbits, inv, st, h ? h->d_errflag : nullptr);
         if (h) prof_end(h, ps, st);
         if (rc != 0) return rc;
     }
