@@ -103,6 +103,8 @@ def parse():
     ap.add_argument("--serving-only", action="store_true",
                     help="run only the serving leg in the --precision given (fp32, else the split mode) "
                          "and print one JSON line")
+    ap.add_argument("--serving-max-large", type=int, default=0,
+                    help="srv_opts.max_large of the serving-only run (0: the library's default)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 33-qubit sliced runs (64 GiB state) and the 35-qubit streamed run "
                          "(256 GiB store) of the default line")
@@ -284,7 +286,7 @@ def oracle_table():
     return {"cpu": cpu, "cores": cores, "rows": rows}
 
 
-def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = "fp16x3_tmem"):
+def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = "fp16x3_tmem", max_large: int = 0):
     """Serve `count` random circuits (qubits uniform in 16..30, 8..20 cycles), all submitted at
     once (rate_hz = 0) or each at its Poisson arrival time, and run the same circuits, arriving
     the same way, one at a time through sim_*; report circuits/s and the latency distributions
@@ -333,7 +335,7 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
     seq_s = time.perf_counter() - t0
     for h in handles.values():
         pkg.sim_destroy(h)
-    srv = pkg.srv_create(device=device, precision=prec)
+    srv = pkg.srv_create(device=device, precision=prec, max_large=max_large)
     # the server's autotuner (srv_autotune), before the clock starts: one sample circuit per size
     # above the packing size and depth class, seeds outside the stream's
     tsamples = [si.sycamore_circuit(si.near_square_grid(n), d, seed=70000 + 31 * n + d)
@@ -973,7 +975,7 @@ def serving_case(args):
     pkg_build.build()
     prec = "fp32" if args.precision == "fp32" else "fp16x3_tmem"
     rate = args.serving_rate if prec != "fp32" else args.serving_rate_fp32
-    print(json.dumps(serving_run(args.serving_circuits, 0, rate, prec)), flush=True)
+    print(json.dumps(serving_run(args.serving_circuits, 0, rate, prec, args.serving_max_large)), flush=True)
 
 
 def main():

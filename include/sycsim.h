@@ -548,7 +548,10 @@ typedef struct srv_opts {
                           * sim_split_choose picks run as two tensors and one tensor-core
                           * contraction when they are >= 30% of the circuit (0 = 5, < 0 = off);
                           * the tensors and the contraction's scratch count in the footprint */
-    int reserved[7];
+    int max_large;       /* most circuits of >= 27 qubits running at once (0: 1 in SIM_FP32, 2 in the
+                          * tensor-core modes -- each is HBM-bound, and sharing the bandwidth among
+                          * more of them only delays them all; < 0: unlimited) */
+    int reserved[6];
 } srv_opts;
 
 typedef struct srv_stats_t {

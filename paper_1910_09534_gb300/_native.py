@@ -67,7 +67,8 @@ class PlanOpts(ctypes.Structure):
 class SrvOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("slots", ctypes.c_int), ("small_n", ctypes.c_int),
                 ("max_pack", ctypes.c_int), ("kmax", ctypes.c_int), ("precision", ctypes.c_int),
-                ("hbm_budget", ctypes.c_uint64), ("front_pairs", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("hbm_budget", ctypes.c_uint64), ("front_pairs", ctypes.c_int), ("max_large", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class SrvStats(ctypes.Structure):
@@ -622,11 +623,12 @@ def _srv_check(rc: int, srv=None):
 
 
 def srv_create(device: int = 0, slots: int = 0, small_n: int = 0, max_pack: int = 0, kmax: int = 0,
-               precision: int = SIM_FP32, hbm_budget: int = 0, front_pairs: int = 0):
+               precision: int = SIM_FP32, hbm_budget: int = 0, front_pairs: int = 0, max_large: int = 0):
     o = SrvOpts()
     o.device, o.slots, o.small_n, o.max_pack, o.kmax, o.precision = device, slots, small_n, max_pack, kmax, precision
     o.hbm_budget = hbm_budget
     o.front_pairs = front_pairs
+    o.max_large = max_large
     srv = ctypes.c_void_p()
     _srv_check(lib().srv_create(ctypes.byref(o), ctypes.byref(srv)))
     return srv

@@ -58,6 +58,7 @@ static int layout(void)
     FIELD(srv_opts, precision);
     FIELD(srv_opts, hbm_budget);
     FIELD(srv_opts, front_pairs);
+    FIELD(srv_opts, max_large);
     FIELD(srv_opts, reserved);
     SIZE(srv_opts);
     FIELD(srv_stats_t, submitted);
