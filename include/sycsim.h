@@ -191,6 +191,17 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
  * caller's buffer (ext_state) or whose state address sim_state_ptr handed out. */
 int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb);
 
+/* sim_reduce without waiting (not in the paper: it lets a caller queue the next circuit on the
+ * handle before this one's result is back, so the device never idles between circuits).
+ * Enqueues on the handle's stream what sim_reduce computes, then the copy of {norm,
+ * 2^n sum p^2, xeb} into out (3 doubles of host memory, caller-owned; pinned memory keeps the
+ * call from waiting), and returns.  out holds the result once the stream has passed the copy:
+ * after sim_sync(h), or after an event the caller records on the handle's stream (sim_state_ptr
+ * gives the stream) after this call; it must stay valid until then.  Work queued later on h
+ * (a new circuit overwriting the state) does not change the result.  SIM_E_UNSUPPORTED for
+ * host-store handles (use sim_reduce); SIM_E_INVAL for NULL h or out. */
+int sim_reduce_async(sim_t *h, double *out);
+
 /* Allocation-free reduction (the paper has no counterpart; it serves callers that
  * cannot allocate device memory -- for example code running inside a framework
  * that owns all device memory through its own pool, or code that must not risk

@@ -106,6 +106,7 @@ _SIGS = {
     "sim_load_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                            ctypes.c_void_p, ctypes.c_int]),
     "sim_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_reduce_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sim_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sim_reduce_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                           ctypes.c_void_p]),
@@ -307,6 +308,14 @@ def sim_reduce(h):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().sim_reduce(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
     return a.value, b.value, c.value
+
+
+def sim_reduce_async(h, out: np.ndarray) -> None:
+    """Enqueue sim_reduce's result {norm, 2^n sum p^2, xeb} into out (3 float64, ideally pinned:
+    pinned_array); out is filled once the handle's stream has passed this point."""
+    if out.dtype != np.float64 or out.size < 3 or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a contiguous float64 array of at least 3 elements")
+    _check(lib().sim_reduce_async(h, _ptr(out)), h)
 
 
 def sim_reduce_noalloc(d_state: int, n_amps: int, d_out: int, stream: int | None = None) -> None:

@@ -270,12 +270,23 @@ __device__ __forceinline__ void ct_tile(uint64_t i, uint32_t tiles_x, uint32_t t
 
 // Largest |Re|, |Im| of n amplitudes into *out (a float's bits; non-negative floats order as
 // unsigned integers).  *out must be 0 before the launch.
-__global__ void __launch_bounds__(256) k_absmax(const float2 *__restrict__ t, uint64_t n, unsigned *out)
+// The tensor is read as pairs of amplitudes (16 bytes), four pairs in flight per thread.
+__global__ void __launch_bounds__(256) k_absmax(const float4 *__restrict__ t, uint64_t n4, unsigned *out)
 {
     float m = 0.f;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const float2 v = t[i];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = t[i + j * stride];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v[j].x), fabsf(v[j].y)), fmaxf(fabsf(v[j].z), fabsf(v[j].w))));
+    }
+    for (; i < n4; i += stride) {
+        const float4 v = t[i];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -537,10 +548,13 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
     int rc = 0;
     if (cudaMemsetAsync(amax, 0, 2 * sizeof(float), st) != cudaSuccess) rc = -1;
     if (rc == 0) {
-        const unsigned blocks = (unsigned)std::min<uint64_t>(4ull * cfg.sms, (X * n_e + 255) / 256);
-        k_absmax<<<blocks, 256, 0, st>>>(t1, X * n_e, reinterpret_cast<unsigned *>(amax));
-        const unsigned blocks2 = (unsigned)std::min<uint64_t>(4ull * cfg.sms, (Y * n_e + 255) / 256);
-        k_absmax<<<blocks2, 256, 0, st>>>(t2, Y * n_e, reinterpret_cast<unsigned *>(amax + 1));
+        // X, Y >= 128: whole pairs of amplitudes; tensor states start 256-byte aligned
+        const uint64_t n4a = X * n_e / 2, n4b = Y * n_e / 2;
+        const unsigned blocks = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4a + 255) / 256);
+        k_absmax<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(t1), n4a, reinterpret_cast<unsigned *>(amax));
+        const unsigned blocks2 = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4b + 255) / 256);
+        k_absmax<<<blocks2, 256, 0, st>>>(reinterpret_cast<const float4 *>(t2), n4b,
+                                          reinterpret_cast<unsigned *>(amax + 1));
         auto image = bf16 ? k_contract_image<true> : k_contract_image<false>;
         image<<<(unsigned)((X / 128) * ks), 256, 0, st>>>(t1, n1, n_e, ks, amax, scratch, 0);
         image<<<(unsigned)((Y / 128) * ks), 256, 0, st>>>(t2, n2, n_e, ks, amax + 1, scratch + a_bytes, 1);
@@ -590,17 +604,41 @@ void contract_layout(const sim_split_s *s, const int *out_bit_of, int t, int *bi
     for (int p = ns; p < (int)s->wire_at[t].size(); ++p) bit_of_wire[s->wire_at[t][p]] = p;
 }
 
+bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of)
+{
+    const int ns = s->n_side[t], nw = (int)s->wire_at[t].size();
+    int canon[kMaxQubits];
+    contract_layout(s, out_bit_of, t, canon, nullptr);
+    for (int p = ns; p < nw; ++p)
+        if (tensor_bit_of[s->wire_at[t][p]] != p) return false;
+    const int low = t == 0 ? std::min(5, ns) : 0;
+    for (int p = 0; p < ns; ++p) {
+        const int w = s->wire_at[t][p], b = tensor_bit_of[w];
+        if (b < 0 || b >= ns || (b < low) != (canon[w] < low)) return false;
+    }
+    return true;  // side wires on distinct bits: a handle's layout is a permutation
+}
+
 size_t contraction_scratch_bytes(const sim_split_s *s)
 {
     return tcgen05_scratch_bytes(s->n_side[0], s->n_side[1], 2 * s->n_pairs);
 }
 
 int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
-                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st)
+                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st,
+                        const int *const *tensor_bit_of)
 {
     const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
     int side_qubit[2][kMaxQubits], lay[kMaxQubits];
-    for (int t = 0; t < 2; ++t) contract_layout(s, out_bit_of, t, lay, side_qubit[t]);
+    for (int t = 0; t < 2; ++t) {
+        contract_layout(s, out_bit_of, t, lay, side_qubit[t]);
+        if (tensor_bit_of && tensor_bit_of[t]) {  // the side qubit on each of the tensor's bits
+            int q_of[kMaxQubits], c = 0;
+            for (int q = 0; q < s->n; ++q)
+                if (s->side[q] == t) q_of[c++] = q;
+            for (int p = 0; p < s->n_side[t]; ++p) side_qubit[t][tensor_bit_of[t][s->wire_at[t][p]]] = q_of[p];
+        }
+    }
     CtOut o{};
     for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out_bit_of[side_qubit[0][i]];
     for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out_bit_of[side_qubit[1][j]];
@@ -633,15 +671,14 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
                     out->n, t1->n, t2->n, s->n, n1 + e_bits, n2 + e_bits);
     SIM_DEVICE_SCOPE(out, out->device);
 
-    // each tensor into the layout that matches out's (contract_layout)
+    // each tensor into a layout the contraction into out can read (contract_ready), else into
+    // contract_layout's
     sim_t *tens[2] = {t1, t2};
     for (int t = 0; t < 2; ++t) {
         sim_t *h = tens[t];
         int perm[kMaxQubits];
         contract_layout(s, out->bit_of, t, perm, nullptr);
-        bool same = true;
-        for (int w = 0; w < h->n; ++w) same = same && h->bit_of[w] == perm[w];
-        if (!same) {
+        if (!contract_ready(s, out->bit_of, t, h->bit_of)) {
             const int rc = sim_permute(h, perm);
             if (rc != SIM_OK) return fail(out, rc, "sim_contract: permuting tensor %d: %s", t + 1, h->err.c_str());
         }
@@ -659,8 +696,9 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         return fail(out, SIM_E_CUDA, "sim_contract: stream ordering failed");
     }
     // psi goes straight into out's current layout
+    const int *tbits[2] = {t1->bit_of, t2->bit_of};
     const int rc = enqueue_contraction(out, s, t1->d_state, t2->d_state, out->d_state, out->bit_of, precision,
-                                       nullptr, out->stream);
+                                       nullptr, out->stream, tbits);
     if (rc != 0) {
         destroy();
         return fail(out, SIM_E_CUDA, "sim_contract: launch failed: %s", cudaGetErrorString(cudaGetLastError()));

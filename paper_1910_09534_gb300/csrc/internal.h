@@ -42,7 +42,7 @@ struct sim_s {
 
     // reduction scratch: per-CTA partials and the final (sum p, sum p^2)
     double *d_partials = nullptr;
-    double *d_result = nullptr;
+    double *d_result = nullptr;       // 8 doubles: [0..1] sums, [4..6] sim_reduce_async's outputs
     double *h_result = nullptr;  // pinned
 
     // staging for logical-order readout / load
@@ -256,6 +256,8 @@ bool precision_ok(int precision);
 inline void state_written(sim_t *h) { h->write_epoch++; }
 // the final combine of the reduction over nblocks (sum p, sum p^2) pairs (reduce.cu)
 int launch_reduce_final(const double *partials, int nblocks, double *d_result, cudaStream_t st);
+// d_result[4..6] = {d_result[0], scale * d_result[1], scale * d_result[1] - 1} (one thread)
+int launch_result3(double *d_result, double scale, cudaStream_t st);
 // the modes whose 4- to 6-qubit blocks take the tcgen05 kernel where it is eligible
 inline bool tmem_mode(int precision) { return precision == SIM_FP16X3_TMEM || precision == SIM_BF16X3; }
 // the modes whose mma.sync blocks use the 3xFP16 kernel (BF16X3 hands it what tcgen05 leaves)
@@ -323,11 +325,34 @@ int split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_pairs
                  int *n_front, int max_seeds);
 // Device bytes of the tensor-core contraction's scratch (operand images, scales) for a split.
 size_t contraction_scratch_bytes(const sim_split_s *s);
-// psi (layout out_bit_of) = the contraction of the tensors t1, t2 (each in contract_layout), on
-// stream st: tcgen05 when precision is not SIM_FP32 and both sides have >= 7 qubits (scratch: a
-// buffer of contraction_scratch_bytes, or NULL for h's own), else the FP32 kernel.
+// Whether tensor t, its wires at tensor_bit_of, can be contracted into a state of layout
+// out_bit_of as it is: its side wires on bits 0 .. n_side-1 in any order, the entanglement wires
+// above in pair order (as contract_layout places them), and for tensor 1 the same qubits on its
+// lowest min(5, n_side) bits as contract_layout puts there (a warp's 32 consecutive x then land on
+// 32 consecutive amplitudes of the output).
+bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of);
+// psi (layout out_bit_of) = the contraction of the tensors t1, t2, on stream st: tcgen05 when
+// precision is not SIM_FP32 and both sides have >= 7 qubits (scratch: a buffer of
+// contraction_scratch_bytes, or NULL for h's own), else the FP32 kernel.  tensor_bit_of[t] is
+// tensor t's layout (contract_ready), or NULL (or tensor_bit_of NULL) for contract_layout's.
 int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
-                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st);
+                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st,
+                        const int *const *tensor_bit_of = nullptr);
+
+// ---- split.cpp ----
+// Tensor t's layout (wire -> bit) for a contraction into a state of layout out_bit_of: the
+// layout contract_layout gives, with the 4 side wires on bits 0-3 chosen so that the tensor's
+// blocks (plan, over its wires) run on the fastest kernels (the tcgen05 applies take at most one
+// target below bit 4).  Tensor 1 keeps the same qubits on bits 0-4, so that the contraction's
+// stores stay whole; its choice is which of them sits on bit 4.  Tensor 2 may put any 4 of its
+// side wires there.  Scored by the plan's pass estimates; ties keep contract_layout's.  The
+// result satisfies contract_ready.
+void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay);
+
+// ---- plan.cpp ----
+// The plan's estimated time per 2^30 amplitudes (sum of its blocks' pass estimates, ms) with
+// qubit q on physical bit bit_of[q].
+double plan_estimate_ms(const sim_plan_s *p, const int *bit_of);
 
 // ---- gates.cpp ----
 // Matrix of a gate record (2x2 or 4x4 complex128, row-major); returns the dimension or 0.

@@ -470,6 +470,21 @@ double improve_by_disjoint_swaps(const sim_plan_s *p, std::vector<int> &pos, std
 
 }  // namespace
 
+namespace sycsim {
+
+double plan_estimate_ms(const sim_plan_s *p, const int *bit_of)
+{
+    double t = 0.0;
+    for (const auto &b : p->blocks) {
+        int tpos[kMaxK];
+        for (size_t i = 0; i < b.qubits.size(); i++) tpos[i] = bit_of[b.qubits[i]];
+        t += pass_ms((int)b.qubits.size(), tpos, p->precision);
+    }
+    return t;
+}
+
+}  // namespace sycsim
+
 extern "C" {
 
 // The layout search; low (may be NULL): only qubits with low[q] != 0 may sit at physical bits

@@ -82,6 +82,15 @@ __global__ void k_reduce_final(const double *partials, int nblocks, double *out)
     }
 }
 
+// r[4..6] = {sum p, scale * sum p^2, scale * sum p^2 - 1} from r[0..1] = (sum p, sum p^2)
+__global__ void k_result3(double *r, double scale)
+{
+    const double s2 = r[1] * scale;
+    r[4] = r[0];
+    r[5] = s2;
+    r[6] = s2 - 1.0;
+}
+
 struct BitMap {
     int bit_of[kMaxQubits];
 };
@@ -149,6 +158,12 @@ int launch_reduce(sim_t *, const float2 *psi, uint64_t amps, double *d_partials,
 int launch_reduce_final(const double *partials, int nblocks, double *d_result, cudaStream_t st)
 {
     k_reduce_final<<<1, 32, 0, st>>>(partials, nblocks, d_result);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_result3(double *d_result, double scale, cudaStream_t st)
+{
+    k_result3<<<1, 1, 0, st>>>(d_result, scale);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

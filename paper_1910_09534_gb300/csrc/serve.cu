@@ -269,6 +269,7 @@ struct Req {
     std::shared_ptr<sim_split_s> split;
     int nt[2] = {0, 0}, nw[2] = {0, 0};
     std::vector<int> out_bit_of;
+    std::vector<int> t_lay[2];  // each tensor's layout (front_tensor_layout)
     float2 *d_t[2] = {nullptr, nullptr};
     uint8_t *d_scratch = nullptr;
     bool contracted = false;
@@ -460,8 +461,9 @@ int advance_unpacked(srv_t *s, const std::shared_ptr<Req> &r, bool *progressed)
     const uint64_t amps = 1ull << r->n;
     const size_t tensor_blocks = (size_t)r->nt[0] + r->nt[1];
     auto contract = [&]() {  // after both tensors' blocks: the state from the two tensors
+        const int *tbits[2] = {r->t_lay[0].data(), r->t_lay[1].data()};
         if (enqueue_contraction(h, r->split.get(), r->d_t[0], r->d_t[1], r->d_state, r->out_bit_of.data(),
-                                r->precision, r->d_scratch, st) != 0)
+                                r->precision, r->d_scratch, st, tbits) != 0)
             return SIM_E_CUDA;
         // each pointer is dropped before its status is checked: after a failed free, the abort
         // path must not free it again
@@ -1142,7 +1144,8 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
         r->out_bit_of.assign(phys, phys + n_qubits);
         for (int t = 0; rc == SIM_OK && t < 2; t++) {
             int lay[kMaxQubits];
-            contract_layout(r->split.get(), phys, t, lay, nullptr);
+            front_tensor_layout(r->split.get(), tplan[t], t, phys, lay);
+            r->t_lay[t].assign(lay, lay + r->nw[t]);
             rc = prepare(tplan[t], lay, r->nw[t]);
             r->nt[t] = (int)tplan[t]->blocks.size();
         }

@@ -186,7 +186,7 @@ int sim_create(int n_qubits, int slice_bits, const sim_opts *opts, sim_t **out)
         h->own_state = true;
     }
     CREATE_TRY(cudaMalloc(&h->d_partials, sizeof(double) * 2 * kReduceBlocks), SIM_E_NOMEM_DEV);
-    CREATE_TRY(cudaMalloc(&h->d_result, sizeof(double) * 4), SIM_E_NOMEM_DEV);
+    CREATE_TRY(cudaMalloc(&h->d_result, sizeof(double) * 8), SIM_E_NOMEM_DEV);
     CREATE_TRY(cudaHostAlloc(&h->h_result, sizeof(double) * 4, cudaHostAllocDefault),
                SIM_E_NOMEM_HOST);
     const uint64_t stage = h->amps < kStageAmps ? h->amps : kStageAmps;
@@ -407,6 +407,43 @@ int sim_load_amplitudes(sim_t *h, uint64_t first, uint64_t count, const void *sr
     return SIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// (sum p, sum p^2) of h's state into d_result[0..1] on h's stream: the combine of the partial sums
+// the plan's last block left when they are of exactly this state, else the full reduction.
+int enqueue_reduce(sim_t *h)
+{
+    if (h->red_epoch == h->write_epoch && h->red_blocks > 0) {
+        h->launches++;
+        return launch_reduce_final(h->d_partials, h->red_blocks, h->d_result, h->stream);
+    }
+    const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps, h->stream);
+    h->launches++;  // the reduction is two kernels (partials + final)
+    const int rc = launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, h->stream);
+    prof_end(h, ps, h->stream);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_reduce_async(sim_t *h, double *out)
+{
+    if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reduce_async: NULL handle");
+    if (!out) return fail(h, SIM_E_INVAL, "sim_reduce_async: out is NULL");
+    if (h->store != SIM_STORE_DEVICE)
+        return fail(h, SIM_E_UNSUPPORTED, "sim_reduce_async: host-store state: use sim_reduce");
+    SIM_DEVICE_SCOPE(h, h->device);
+    if (enqueue_reduce(h) != 0 || launch_result3(h->d_result, std::ldexp(1.0, h->n), h->stream) != 0)
+        return fail(h, SIM_E_CUDA, "sim_reduce_async: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    h->launches++;
+    SIM_CUDA_TRY(h, cudaMemcpyAsync(out, h->d_result + 4, sizeof(double) * 3, cudaMemcpyDeviceToHost, h->stream));
+    return SIM_OK;
+}
+
 int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
 {
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_reduce: NULL handle");
@@ -420,18 +457,7 @@ int sim_reduce(sim_t *h, double *norm, double *sum_p2_scaled, double *xeb)
         if (xeb) *xeb = ldexp(b, h->n) - 1.0;
         return SIM_OK;
     }
-    int rc;
-    if (h->red_epoch == h->write_epoch && h->red_blocks > 0) {
-        // the plan's last block left the partial sums of exactly this state: combine them
-        rc = launch_reduce_final(h->d_partials, h->red_blocks, h->d_result, h->stream);
-        h->launches++;
-    } else {
-        const int ps = prof_begin(h, SIM_PROF_REDUCE, 8.0 * (double)h->amps, h->stream);
-        h->launches++;  // the reduction is two kernels (partials + final)
-        rc = launch_reduce(h, h->d_state, h->amps, h->d_partials, h->d_result, h->stream);
-        prof_end(h, ps, h->stream);
-    }
-    if (rc != 0)
+    if (enqueue_reduce(h) != 0)
         return fail(h, SIM_E_CUDA, "sim_reduce: launch failed: %s",
                     cudaGetErrorString(cudaGetLastError()));
     SIM_CUDA_TRY(h, cudaMemcpyAsync(h->h_result, h->d_result, sizeof(double) * 2,

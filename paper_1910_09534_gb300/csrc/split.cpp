@@ -167,7 +167,47 @@ struct sim_front_s {
     sim_plan_t *p[2] = {nullptr, nullptr};
     int device = 0;
     int contract_precision = SIM_FP32;
+    std::vector<int> lay_for;             // output layout the tensor layouts below were chosen for
+    int lay[2][kMaxQubits] = {};          // each tensor's layout (wire -> bit)
 };
+
+
+
+namespace sycsim {
+
+void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay)
+{
+    const int ns = s->n_side[t], nw = (int)s->wire_at[t].size();
+    contract_layout(s, out_bit_of, t, lay, nullptr);
+    if (ns < 5) return;
+    int wire_on[kMaxQubits];  // side wire on each of bits 0 .. ns-1 in contract_layout's order
+    for (int p = 0; p < ns; ++p) wire_on[lay[s->wire_at[t][p]]] = s->wire_at[t][p];
+    const int pool = t == 0 ? 5 : ns;  // the low-4 set is drawn from bits 0 .. pool-1
+    int cand[kMaxQubits];
+    std::copy(lay, lay + nw, cand);
+    double best = plan_estimate_ms(plan, lay);
+    int c[4] = {0, 1, 2, 3};
+    for (;;) {
+        // bits 0-3: the chosen four in their order; then the other side wires in order
+        int b = 4;
+        for (int j = 0; j < ns; ++j) {
+            const int *at = std::find(c, c + 4, j);
+            cand[wire_on[j]] = at != c + 4 ? (int)(at - c) : b++;
+        }
+        const double est = plan_estimate_ms(plan, cand);
+        if (est < best - 1e-9) {
+            best = est;
+            std::copy(cand, cand + nw, lay);
+        }
+        int i = 3;  // next 4-subset of 0 .. pool-1 in lexicographic order
+        while (i >= 0 && c[i] == pool - 4 + i) --i;
+        if (i < 0) break;
+        ++c[i];
+        for (int j = i + 1; j < 4; ++j) c[j] = c[j - 1] + 1;
+    }
+}
+
+}  // namespace sycsim
 
 extern "C" int sim_front_destroy(sim_front_t *f)
 {
@@ -221,11 +261,14 @@ extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
     if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
     state_written(out);
     if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
+    if (f->lay_for.size() != (size_t)out->n || !std::equal(f->lay_for.begin(), f->lay_for.end(), out->bit_of)) {
+        for (int t = 0; t < 2; ++t) front_tensor_layout(&f->split, f->p[t], t, out->bit_of, f->lay[t]);
+        f->lay_for.assign(out->bit_of, out->bit_of + out->n);
+    }
     for (int t = 0; t < 2; ++t) {
-        // relabel the tensor (free: its state is reset next) into the layout the contraction into
-        // out wants, so that no run permutes
-        int lay[kMaxQubits];
-        contract_layout(&f->split, out->bit_of, t, lay, nullptr);
+        // relabel the tensor (free: its state is reset next) into a layout the contraction into
+        // out reads as it is, so that no run permutes
+        const int *lay = f->lay[t];
         for (int w = 0; w < f->t[t]->n; ++w) {
             f->t[t]->bit_of[w] = lay[w];
             f->t[t]->qubit_at[lay[w]] = w;

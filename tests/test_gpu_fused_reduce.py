@@ -122,3 +122,55 @@ def test_single_tcgen05_block_plan_takes_the_shortcut(pkg, oracle_mod):
         pkg.sim_plan_destroy(plan)
     onorm, os2, _ = oracle_mod.reduce(amps)
     assert abs(norm - onorm) <= 1e-6 * onorm and abs(s2 - os2) <= 1e-5 * os2
+
+
+def test_reduce_async_matches_sync_and_oracle_when_pipelined(pkg, oracle_mod):
+    # two circuits back to back on one handle: the first's reduction is queued, the second circuit
+    # is queued behind it (overwriting the state) before the first result is read; each result must
+    # be its own circuit's, and equal what sim_reduce returns for the same state
+    torch = pytest.importorskip("torch")
+    circs = [si.sycamore_circuit(si.Grid(4, 5), 10, seed=21), si.sycamore_circuit(si.Grid(4, 5), 12, seed=22)]
+    n = circs[0].n_qubits
+    plans = [pkg.sim_plan_create(n, pkg.gates_array(c), kmax=6, precision=pkg.SIM_FP16X3_TMEM) for c in circs]
+    outs = [pkg.pinned_array(3, dtype=np.float64) for _ in range(3)]
+    h = pkg.sim_create(n)
+    try:
+        st = torch.cuda.ExternalStream(pkg.sim_stream(h))
+        evs = [torch.cuda.Event() for _ in range(2)]
+        for i in range(2):
+            pkg.sim_reset(h)
+            pkg.sim_apply_plan(h, plans[i])
+            pkg.sim_reduce_async(h, outs[i])  # the fused combine (last block on tcgen05)
+            evs[i].record(st)
+        evs[0].synchronize()
+        first = [float(x) for x in outs[0][:3]]
+        evs[1].synchronize()
+        second = [float(x) for x in outs[1][:3]]
+        sync2 = pkg.sim_reduce(h)  # the same state, waited for
+        pkg.sim_set_layout(h, list(range(n)))  # counts as a write: the full reduction next
+        pkg.sim_reduce_async(h, outs[2])
+        pkg.sim_sync(h)
+        full2 = [float(x) for x in outs[2][:3]]
+    finally:
+        pkg.sim_destroy(h)
+        for p in plans:
+            pkg.sim_plan_destroy(p)
+        for o in outs:
+            pkg.sim_host_free(o.ctypes.data)
+    for got, c in ((first, circs[0]), (second, circs[1])):
+        onorm, os2, oxeb = oracle_mod.reduce(oracle_mod.run_circuit(c))
+        assert abs(got[0] - onorm) < 1e-5 and abs(got[1] - os2) < 1e-3 and abs(got[2] - oxeb) < 1e-3
+        assert abs(got[2] - (got[1] - 1.0)) < 1e-12
+    assert all(abs(a - b) <= 1e-12 * max(1.0, abs(b)) for a, b in zip(second, sync2))
+    assert abs(full2[0] - sync2[0]) < 1e-6 and abs(full2[1] - sync2[1]) < 1e-5
+
+
+def test_reduce_async_rejects_bad_output(pkg):
+    h = pkg.sim_create(12)
+    try:
+        with pytest.raises(ValueError):
+            pkg.sim_reduce_async(h, np.zeros(2, dtype=np.float64))
+        assert pkg.lib().sim_reduce_async(h, None) == pkg.SIM_E_INVAL
+        assert pkg.lib().sim_reduce_async(None, None) == pkg.SIM_E_INVAL
+    finally:
+        pkg.sim_destroy(h)
