@@ -480,6 +480,22 @@ int sim_split_choose(int n_qubits, int n_gates, const sim_gate *gates, int max_p
  * otherwise the FP32 kernel runs), or SIM_BF16X3 (the same with BF16 pieces).  Asynchronous.  SIM_E_INVAL for handles that do not fit s. */
 int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision);
 
+/* The first phase of a sliced run with its state made by the contraction (Sect. 4: tensors 1
+ * and 2 are contracted slice by slice straight into the secondary-storage state of subcircuit 3).
+ * out: a host-store handle (sim_create with SIM_STORE_HOST); for every slice of set A, the slice
+ * of psi is contracted from t1 and t2 into a device slot (for a hybrid store's device regions, in
+ * place), the blocks of p are applied to it (a plan over qubits outside set A, as for
+ * sim_run_phase with set A; NULL for none), and it is written to the store once: no slice is
+ * read, and the store's earlier contents do not matter.  t1, t2, s, precision: as for
+ * sim_contract (each tensor is permuted first unless its layout already puts its side's set-A
+ * qubits on its top side bits in set-A order; sim_front_run_phase lays them out that way).
+ * With a device-resident out it is sim_contract followed by sim_apply_plan.  Asynchronous like
+ * sim_run_phase; the tensors must not change until sim_sync(out).  SIM_E_INVAL for NULL or
+ * shared handles, mismatched sizes or a plan for another qubit count; SIM_E_NONLOCAL for a plan
+ * with a block on a qubit of set A (nothing is queued then). */
+int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision,
+                       const sim_plan_t *p);
+
 /* A split made ready to run (Sect. 2's subcircuits 1 and 2 and their contraction as one reusable
  * unit).  sim_front_create plans both tensors' gate lists (o as for sim_plan_create; NULL: k_max
  * 4, SIM_FP32) and creates their device states (2^n_wires[t] amplitudes each) on out's device and
@@ -487,12 +503,21 @@ int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int pre
  * reset to |0..0>, their blocks applied, and sim_contract into out -- on the tensor cores
  * (SIM_FP16X3_TMEM) when o->precision is SIM_FP16X3 or SIM_FP16X3_TMEM, in BF16x3 when it is
  * SIM_BF16X3, else in FP32.  out must
- * have the split's n_qubits qubits, be device-resident and not sliced, and live on the front's
- * device.  Asynchronous like sim_apply_plan; the tensors' kernels count in out's
+ * have the split's n_qubits qubits and live on the front's device; it is device-resident, or a
+ * host store (the contraction then goes slice by slice into the store: sim_contract_phase with
+ * no plan).  Asynchronous like sim_apply_plan; the tensors' kernels count in out's
  * sim_launch_count.  sim_front_destroy waits for the front's work. */
 typedef struct sim_front_s sim_front_t;
 int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan_opts *o, sim_front_t **f);
 int sim_front_run(sim_t *out, sim_front_t *f);
+
+/* sim_front_run, then the blocks of p on the contracted state, in one pass when out is a host
+ * store: the contraction fills each slice of set A and p's blocks (qubits outside set A, as for
+ * sim_run_phase with set A) run on it before it is written (sim_contract_phase).  For a
+ * device-resident out: sim_front_run then sim_apply_plan.  p may be NULL.  The tensors' layouts
+ * keep each side's set-A qubits on their top side bits.  Errors as sim_front_run and
+ * sim_contract_phase. */
+int sim_front_run_phase(sim_t *out, sim_front_t *f, const sim_plan_t *p);
 int sim_front_destroy(sim_front_t *f);
 
 /* ---- a state sharded over global qubits on 2^g ranks (Sect. 4) ------------------------------

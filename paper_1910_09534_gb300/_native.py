@@ -161,6 +161,9 @@ _SIGS = {
     "sim_front_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "sim_front_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_front_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_contract_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_void_p]),
     "sim_front_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_state_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_state_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
@@ -590,6 +593,16 @@ def sim_front_create(out, s, kmax: int = 4, precision: int = SIM_FP32):
 
 def sim_front_run(out, f) -> None:
     _check(lib().sim_front_run(out, f), out)
+
+
+def sim_front_run_phase(out, f, plan=None) -> None:
+    """sim_front_run, then plan's blocks on the contracted state (one pass into a host store)."""
+    _check(lib().sim_front_run_phase(out, f, plan), out)
+
+
+def sim_contract_phase(out, t1, t2, s, precision: int = SIM_FP32, plan=None) -> None:
+    """Contraction slice by slice into a host store's set-A slices, plan's blocks on each, one write."""
+    _check(lib().sim_contract_phase(out, t1, t2, s, precision, plan), out)
 
 
 def sim_front_destroy(f) -> None:

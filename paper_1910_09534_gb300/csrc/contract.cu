@@ -56,9 +56,10 @@ __device__ __forceinline__ uint64_t ct_dep(uint64_t v, const uint64_t *bit, int 
     return o;
 }
 
+// t1 (t2): 2^n1 (2^n2) columns of each entanglement row, rows ld1 (ld2) amplitudes apart.
 __global__ void __launch_bounds__(256) k_contract_fp32(const float2 *__restrict__ t1, const float2 *__restrict__ t2,
                                                        float2 *__restrict__ psi, int n1, int n2, uint64_t n_e,
-                                                       const __grid_constant__ CtOut o)
+                                                       uint64_t ld1, uint64_t ld2, const __grid_constant__ CtOut o)
 {
     __shared__ __align__(16) float2 sa[kFk][kFx];
     __shared__ __align__(16) float2 sb[kFk][kFy];
@@ -81,8 +82,8 @@ __global__ void __launch_bounds__(256) k_contract_fp32(const float2 *__restrict_
         for (int r = 0; r < (kFk * kFx) / 256; ++r) {
             const int idx = tid + 256 * r, k = idx / kFx, c = idx % kFx;
             const uint64_t e = e0 + k;
-            sa[k][c] = (e < n_e && x0 + c < X) ? t1[x0 + c + e * X] : make_float2(0.f, 0.f);
-            sb[k][c] = (e < n_e && y0 + c < Y) ? t2[y0 + c + e * Y] : make_float2(0.f, 0.f);
+            sa[k][c] = (e < n_e && x0 + c < X) ? t1[x0 + c + e * ld1] : make_float2(0.f, 0.f);
+            sb[k][c] = (e < n_e && y0 + c < Y) ? t2[y0 + c + e * ld2] : make_float2(0.f, 0.f);
         }
         __syncthreads();
 #pragma unroll
@@ -114,13 +115,13 @@ __global__ void __launch_bounds__(256) k_contract_fp32(const float2 *__restrict_
     }
 }
 
-int launch_contract_fp32(const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                         const CtOut &o, cudaStream_t st)
+int launch_contract_fp32(const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits, uint64_t ld1,
+                         uint64_t ld2, const CtOut &o, cudaStream_t st)
 {
     const uint64_t X = 1ull << n1, Y = 1ull << n2;
     const uint64_t blocks = ((X + kFx - 1) / kFx) * ((Y + kFy - 1) / kFy);
     if (blocks > 0x7fffffffull) return -1;
-    k_contract_fp32<<<(unsigned)blocks, 256, 0, st>>>(t1, t2, psi, n1, n2, 1ull << e_bits, o);
+    k_contract_fp32<<<(unsigned)blocks, 256, 0, st>>>(t1, t2, psi, n1, n2, 1ull << e_bits, ld1, ld2, o);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -517,11 +518,8 @@ size_t tcgen05_scratch_bytes(int n1, int n2, int e_bits)
     return (size_t)((1ull << n1) / 128) * ks * kCtSlab + (size_t)((1ull << n2) / 128) * ks * kCtSlab + 256;
 }
 
-int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2 *psi, int n1, int n2, int e_bits,
-                            const CtOut &o, bool bf16, cudaStream_t st, uint8_t *own_scratch = nullptr)
+const LaunchCfg &ct_cfg()
 {
-    static std::atomic<uint64_t> smem_done{0};
-    if (!smem_opt_in(k_contract_tcgen05, kCtStages * kCtStage, smem_done)) return -1;
     static const LaunchCfg cfg = [] {
         LaunchCfg c;
         int dev = 0;
@@ -530,6 +528,16 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
         c.ok = true;
         return c;
     }();
+    return cfg;
+}
+
+// Scales and operand images of both (whole) tensors, on st, into the scratch (the output
+// handle's own, grown as needed, unless own_scratch is given).
+int prepare_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, int n1, int n2, int e_bits, bool bf16,
+                    cudaStream_t st, uint8_t *own_scratch, const uint8_t **aimg, const uint8_t **bimg,
+                    const float **amax_out)
+{
+    const LaunchCfg &cfg = ct_cfg();
     if (!cfg.ok) return -1;
     const uint64_t n_e = 1ull << e_bits;
     const uint32_t ks = (uint32_t)((n_e + 15) / 16);
@@ -545,39 +553,51 @@ int launch_contract_tcgen05(sim_t *h, const float2 *t1, const float2 *t2, float2
     }
     uint8_t *scratch = own_scratch ? own_scratch : h->d_contract;
     float *amax = reinterpret_cast<float *>(scratch + a_bytes + b_bytes);
-    int rc = 0;
-    if (cudaMemsetAsync(amax, 0, 2 * sizeof(float), st) != cudaSuccess) rc = -1;
-    if (rc == 0) {
-        // X, Y >= 128: whole pairs of amplitudes; tensor states start 256-byte aligned
-        const uint64_t n4a = X * n_e / 2, n4b = Y * n_e / 2;
-        const unsigned blocks = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4a + 255) / 256);
-        k_absmax<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(t1), n4a, reinterpret_cast<unsigned *>(amax));
-        const unsigned blocks2 = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4b + 255) / 256);
-        k_absmax<<<blocks2, 256, 0, st>>>(reinterpret_cast<const float4 *>(t2), n4b,
-                                          reinterpret_cast<unsigned *>(amax + 1));
-        auto image = bf16 ? k_contract_image<true> : k_contract_image<false>;
-        image<<<(unsigned)((X / 128) * ks), 256, 0, st>>>(t1, n1, n_e, ks, amax, scratch, 0);
-        image<<<(unsigned)((Y / 128) * ks), 256, 0, st>>>(t2, n2, n_e, ks, amax + 1, scratch + a_bytes, 1);
-        h->launches += 4;
-        CtArgs g{};
-        g.aimg = scratch;
-        g.bimg = scratch + a_bytes;
-        g.psi = psi;
-        g.n1 = n1;
-        g.n2 = n2;
-        g.ks = ks;
-        g.tiles_x = (uint32_t)(X / 128);
-        g.tiles_y = (uint32_t)(Y / 128);
-        g.amax = amax;
-        g.err = h->d_errflag;
-        g.bf16 = bf16 ? 1 : 0;
-        const uint64_t grid = std::min<uint64_t>((uint64_t)g.tiles_x * g.tiles_y, (uint64_t)cfg.sms);
-        const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * (double)X * (double)Y * (double)n_e, st);
-        k_contract_tcgen05<<<(unsigned)grid, kCtThreads, kCtStages * kCtStage, st>>>(g, o);
-        prof_end(h, ps, st);
-        if (cudaGetLastError() != cudaSuccess) rc = -1;
-    }
-    return rc;
+    if (cudaMemsetAsync(amax, 0, 2 * sizeof(float), st) != cudaSuccess) return -1;
+    // X, Y >= 128: whole pairs of amplitudes; tensor states start 256-byte aligned
+    const uint64_t n4a = X * n_e / 2, n4b = Y * n_e / 2;
+    const unsigned blocks = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4a + 255) / 256);
+    k_absmax<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4 *>(t1), n4a, reinterpret_cast<unsigned *>(amax));
+    const unsigned blocks2 = (unsigned)std::min<uint64_t>(8ull * cfg.sms, (n4b + 255) / 256);
+    k_absmax<<<blocks2, 256, 0, st>>>(reinterpret_cast<const float4 *>(t2), n4b, reinterpret_cast<unsigned *>(amax + 1));
+    auto image = bf16 ? k_contract_image<true> : k_contract_image<false>;
+    image<<<(unsigned)((X / 128) * ks), 256, 0, st>>>(t1, n1, n_e, ks, amax, scratch, 0);
+    image<<<(unsigned)((Y / 128) * ks), 256, 0, st>>>(t2, n2, n_e, ks, amax + 1, scratch + a_bytes, 1);
+    h->launches += 4;
+    *aimg = scratch;
+    *bimg = scratch + a_bytes;
+    *amax_out = amax;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// The GEMM for x tiles [x0t, x0t + 2^n1 / 128) and y tiles [y0t, y0t + 2^n2 / 128) of the images.
+int launch_gemm_tcgen05(sim_t *h, const uint8_t *aimg, const uint8_t *bimg, const float *amax, uint64_t n_e,
+                        uint64_t x0t, uint64_t y0t, float2 *psi, int n1, int n2, const CtOut &o, bool bf16,
+                        cudaStream_t st)
+{
+    static std::atomic<uint64_t> smem_done{0};
+    if (!smem_opt_in(k_contract_tcgen05, kCtStages * kCtStage, smem_done)) return -1;
+    const LaunchCfg &cfg = ct_cfg();
+    if (!cfg.ok) return -1;
+    const uint64_t X = 1ull << n1, Y = 1ull << n2;
+    const uint32_t ks = (uint32_t)((n_e + 15) / 16);
+    CtArgs g{};
+    g.aimg = aimg + x0t * ks * kCtSlab;
+    g.bimg = bimg + y0t * ks * kCtSlab;
+    g.psi = psi;
+    g.n1 = n1;
+    g.n2 = n2;
+    g.ks = ks;
+    g.tiles_x = (uint32_t)(X / 128);
+    g.tiles_y = (uint32_t)(Y / 128);
+    g.amax = amax;
+    g.err = h->d_errflag;
+    g.bf16 = bf16 ? 1 : 0;
+    const uint64_t grid = std::min<uint64_t>((uint64_t)g.tiles_x * g.tiles_y, (uint64_t)cfg.sms);
+    const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * (double)X * (double)Y * (double)n_e, st);
+    k_contract_tcgen05<<<(unsigned)grid, kCtThreads, kCtStages * kCtStage, st>>>(g, o);
+    prof_end(h, ps, st);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace
@@ -604,17 +624,18 @@ void contract_layout(const sim_split_s *s, const int *out_bit_of, int t, int *bi
     for (int p = ns; p < (int)s->wire_at[t].size(); ++p) bit_of_wire[s->wire_at[t][p]] = p;
 }
 
-bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of)
+bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of, int top)
 {
     const int ns = s->n_side[t], nw = (int)s->wire_at[t].size();
     int canon[kMaxQubits];
     contract_layout(s, out_bit_of, t, canon, nullptr);
     for (int p = ns; p < nw; ++p)
         if (tensor_bit_of[s->wire_at[t][p]] != p) return false;
-    const int low = t == 0 ? std::min(5, ns) : 0;
+    const int low = t == 0 ? std::min(5, ns - top) : 0;
     for (int p = 0; p < ns; ++p) {
         const int w = s->wire_at[t][p], b = tensor_bit_of[w];
         if (b < 0 || b >= ns || (b < low) != (canon[w] < low)) return false;
+        if ((b >= ns - top || canon[w] >= ns - top) && b != canon[w]) return false;
     }
     return true;  // side wires on distinct bits: a handle's layout is a permutation
 }
@@ -624,13 +645,19 @@ size_t contraction_scratch_bytes(const sim_split_s *s)
     return tcgen05_scratch_bytes(s->n_side[0], s->n_side[1], 2 * s->n_pairs);
 }
 
-int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
-                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st,
-                        const int *const *tensor_bit_of)
+int contract_job_prepare(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2,
+                         const int *const *tensor_bit_of, const int *out_bit_of, int precision, const int *top,
+                         uint8_t *scratch, cudaStream_t st, ContractJob *job)
 {
-    const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
+    ContractJob &j = *job;
+    j = ContractJob{};
+    j.e_bits = 2 * s->n_pairs;
+    j.t[0] = t1;
+    j.t[1] = t2;
     int side_qubit[2][kMaxQubits], lay[kMaxQubits];
     for (int t = 0; t < 2; ++t) {
+        j.n_side[t] = s->n_side[t];
+        j.n_free[t] = s->n_side[t] - (top ? top[t] : 0);
         contract_layout(s, out_bit_of, t, lay, side_qubit[t]);
         if (tensor_bit_of && tensor_bit_of[t]) {  // the side qubit on each of the tensor's bits
             int q_of[kMaxQubits], c = 0;
@@ -639,15 +666,39 @@ int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const 
             for (int p = 0; p < s->n_side[t]; ++p) side_qubit[t][tensor_bit_of[t][s->wire_at[t][p]]] = q_of[p];
         }
     }
+    for (int i = 0; i < j.n_free[0]; ++i) j.xbit[i] = 1ull << out_bit_of[side_qubit[0][i]];
+    for (int i = 0; i < j.n_free[1]; ++i) j.ybit[i] = 1ull << out_bit_of[side_qubit[1][i]];
+    j.tensor_cores = precision != SIM_FP32 && j.n_free[0] >= 7 && j.n_free[1] >= 7;
+    j.bf16 = precision == SIM_BF16X3;
+    j.ks = (uint32_t)(((1ull << j.e_bits) + 15) / 16);
+    if (!j.tensor_cores) return 0;
+    return prepare_tcgen05(h, t1, t2, j.n_side[0], j.n_side[1], j.e_bits, j.bf16, st, scratch, &j.img[0], &j.img[1],
+                           &j.amax);
+}
+
+int contract_job_launch(sim_t *h, const ContractJob &j, float2 *psi, uint64_t fix0, uint64_t fix1, cudaStream_t st)
+{
     CtOut o{};
-    for (int i = 0; i < n1; ++i) o.xbit[i] = 1ull << out_bit_of[side_qubit[0][i]];
-    for (int j = 0; j < n2; ++j) o.ybit[j] = 1ull << out_bit_of[side_qubit[1][j]];
-    if (precision != SIM_FP32 && n1 >= 7 && n2 >= 7)
-        return launch_contract_tcgen05(h, t1, t2, psi, n1, n2, e_bits, o, precision == SIM_BF16X3, st, scratch);
-    const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, n1 + n2 + e_bits), st);
-    const int rc = launch_contract_fp32(t1, t2, psi, n1, n2, e_bits, o, st);
+    std::copy(j.xbit, j.xbit + j.n_free[0], o.xbit);
+    std::copy(j.ybit, j.ybit + j.n_free[1], o.ybit);
+    const uint64_t x0 = fix0 << j.n_free[0], y0 = fix1 << j.n_free[1];  // first column of each side's range
+    if (j.tensor_cores)
+        return launch_gemm_tcgen05(h, j.img[0], j.img[1], j.amax, 1ull << j.e_bits, x0 / 128, y0 / 128, psi,
+                                   j.n_free[0], j.n_free[1], o, j.bf16, st);
+    const int ps = prof_begin(h, SIM_PROF_CONTRACT, 8.0 * std::ldexp(1.0, j.n_free[0] + j.n_free[1] + j.e_bits), st);
+    const int rc = launch_contract_fp32(j.t[0] + x0, j.t[1] + y0, psi, j.n_free[0], j.n_free[1], j.e_bits,
+                                        1ull << j.n_side[0], 1ull << j.n_side[1], o, st);
     prof_end(h, ps, st);
     return rc;
+}
+
+int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2, float2 *psi,
+                        const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st,
+                        const int *const *tensor_bit_of)
+{
+    ContractJob j;
+    const int rc = contract_job_prepare(h, s, t1, t2, tensor_bit_of, out_bit_of, precision, nullptr, scratch, st, &j);
+    return rc != 0 ? rc : contract_job_launch(h, j, psi, 0, 0, st);
 }
 
 }  // namespace sycsim

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -330,7 +331,28 @@ size_t contraction_scratch_bytes(const sim_split_s *s);
 // above in pair order (as contract_layout places them), and for tensor 1 the same qubits on its
 // lowest min(5, n_side) bits as contract_layout puts there (a warp's 32 consecutive x then land on
 // 32 consecutive amplitudes of the output).
-bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of);
+// With top > 0 the side's top `top` bits must also hold the wires contract_layout puts there (the
+// sliced qubits of a contraction into a store, which select the slice).
+bool contract_ready(const sim_split_s *s, const int *out_bit_of, int t, const int *tensor_bit_of, int top = 0);
+// A contraction prepared once and launched per slice: each side keeps its top top[t] bits fixed
+// per launch (the qubits that select a slice of the output), its other n_free[t] bits land at the
+// offsets xbit (side 0) / ybit (side 1) of the launch's output buffer.  contract_job_prepare
+// computes the scales and operand images (tcgen05) on st; the tensors and the scratch must stay
+// unchanged until the last launch has run.
+struct ContractJob {
+    bool tensor_cores = false, bf16 = false;
+    int n_side[2] = {0, 0}, n_free[2] = {0, 0}, e_bits = 0;
+    uint32_t ks = 0;                              // k-steps of 16 entanglement values
+    const float2 *t[2] = {nullptr, nullptr};
+    const uint8_t *img[2] = {nullptr, nullptr};   // operand images (tcgen05)
+    const float *amax = nullptr;                  // the two tensors' largest components (tcgen05)
+    uint64_t xbit[kMaxQubits] = {}, ybit[kMaxQubits] = {};
+};
+int contract_job_prepare(sim_t *h, const sim_split_s *s, const float2 *t1, const float2 *t2,
+                         const int *const *tensor_bit_of, const int *out_bit_of, int precision, const int *top,
+                         uint8_t *scratch, cudaStream_t st, ContractJob *job);
+// psi (the output buffer) = the slice with side 0's top bits = fix0 and side 1's = fix1.
+int contract_job_launch(sim_t *h, const ContractJob &job, float2 *psi, uint64_t fix0, uint64_t fix1, cudaStream_t st);
 // psi (layout out_bit_of) = the contraction of the tensors t1, t2, on stream st: tcgen05 when
 // precision is not SIM_FP32 and both sides have >= 7 qubits (scratch: a buffer of
 // contraction_scratch_bytes, or NULL for h's own), else the FP32 kernel.  tensor_bit_of[t] is
@@ -339,15 +361,23 @@ int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const 
                         const int *out_bit_of, int precision, uint8_t *scratch, cudaStream_t st,
                         const int *const *tensor_bit_of = nullptr);
 
+// ---- store.cu ----
+// One phase over a host store (sim_run_phase's body): fill, when given, makes each slice v of set
+// A in place of its copy-in ((*fill)(dst, v) enqueues it into dst on the handle's stream); p may
+// then be NULL (no blocks).
+int run_phase(sim_t *h, int set, const sim_plan_t *p, const std::function<int(float2 *, uint64_t)> *fill);
+
 // ---- split.cpp ----
 // Tensor t's layout (wire -> bit) for a contraction into a state of layout out_bit_of: the
 // layout contract_layout gives, with the 4 side wires on bits 0-3 chosen so that the tensor's
 // blocks (plan, over its wires) run on the fastest kernels (the tcgen05 applies take at most one
 // target below bit 4).  Tensor 1 keeps the same qubits on bits 0-4, so that the contraction's
 // stores stay whole; its choice is which of them sits on bit 4.  Tensor 2 may put any 4 of its
-// side wires there.  Scored by the plan's pass estimates; ties keep contract_layout's.  The
-// result satisfies contract_ready.
-void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay);
+// side wires there.  The top `top` side bits keep contract_layout's wires (a store's sliced
+// qubits).  Scored by the plan's pass estimates; ties keep contract_layout's.  The result
+// satisfies contract_ready(..., top).
+void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay,
+                         int top = 0);
 
 // ---- plan.cpp ----
 // The plan's estimated time per 2^30 amplitudes (sum of its blocks' pass estimates, ms) with

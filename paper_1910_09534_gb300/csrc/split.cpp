@@ -175,14 +175,14 @@ struct sim_front_s {
 
 namespace sycsim {
 
-void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay)
+void front_tensor_layout(const sim_split_s *s, const sim_plan_s *plan, int t, const int *out_bit_of, int *lay, int top)
 {
     const int ns = s->n_side[t], nw = (int)s->wire_at[t].size();
     contract_layout(s, out_bit_of, t, lay, nullptr);
-    if (ns < 5) return;
+    if (ns - top < 5) return;
     int wire_on[kMaxQubits];  // side wire on each of bits 0 .. ns-1 in contract_layout's order
     for (int p = 0; p < ns; ++p) wire_on[lay[s->wire_at[t][p]]] = s->wire_at[t][p];
-    const int pool = t == 0 ? 5 : ns;  // the low-4 set is drawn from bits 0 .. pool-1
+    const int pool = t == 0 ? 5 : ns - top;  // the low-4 set is drawn from bits 0 .. pool-1
     int cand[kMaxQubits];
     std::copy(lay, lay + nw, cand);
     double best = plan_estimate_ms(plan, lay);
@@ -256,14 +256,23 @@ extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan
     return SIM_OK;
 }
 
-extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
+extern "C" int sim_front_run_phase(sim_t *out, sim_front_t *f, const sim_plan_t *p)
 {
     if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
     state_written(out);
     if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
-    if (f->lay_for.size() != (size_t)out->n || !std::equal(f->lay_for.begin(), f->lay_for.end(), out->bit_of)) {
-        for (int t = 0; t < 2; ++t) front_tensor_layout(&f->split, f->p[t], t, out->bit_of, f->lay[t]);
+    if (out->n != f->split.n)
+        return fail(out, SIM_E_INVAL, "sim_front_run: out has %d qubits, the split %d", out->n, f->split.n);
+    // into a host store, each side's set-A qubits stay on its tensor's top side bits
+    int top[2] = {0, 0};
+    if (out->store == SIM_STORE_HOST)
+        for (int i = 0; i < out->s; i++) top[f->split.side[out->set[0][i]]]++;
+    if (f->lay_for.size() != (size_t)out->n + 2 || !std::equal(out->bit_of, out->bit_of + out->n, f->lay_for.begin()) ||
+        f->lay_for[out->n] != top[0] || f->lay_for[out->n + 1] != top[1]) {
+        for (int t = 0; t < 2; ++t) front_tensor_layout(&f->split, f->p[t], t, out->bit_of, f->lay[t], top[t]);
         f->lay_for.assign(out->bit_of, out->bit_of + out->n);
+        f->lay_for.push_back(top[0]);
+        f->lay_for.push_back(top[1]);
     }
     for (int t = 0; t < 2; ++t) {
         // relabel the tensor (free: its state is reset next) into a layout the contraction into
@@ -279,8 +288,10 @@ extern "C" int sim_front_run(sim_t *out, sim_front_t *f)
         out->launches += f->t[t]->launches - before;  // the front's kernels count as out's
         if (rc != SIM_OK) return fail(out, rc, "sim_front_run: tensor %d: %s", t + 1, f->t[t]->err.c_str());
     }
-    return sim_contract(out, f->t[0], f->t[1], &f->split, f->contract_precision);
+    return sim_contract_phase(out, f->t[0], f->t[1], &f->split, f->contract_precision, p);
 }
+
+extern "C" int sim_front_run(sim_t *out, sim_front_t *f) { return sim_front_run_phase(out, f, nullptr); }
 
 namespace {
 

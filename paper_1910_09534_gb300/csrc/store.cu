@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <thread>
 #include <vector>
 
@@ -573,6 +574,20 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         // resident state: the phase's blocks apply to the whole state
         return sim_apply_plan(h, p);
     }
+    return run_phase(h, set, p, nullptr);
+}
+
+}  // extern "C"
+
+namespace sycsim {
+
+// One phase over a host store: every slice of the sliced set goes through a device slot (or is
+// computed in place, for a hybrid store's device regions with set A sliced), gets the plan's
+// blocks (p may be NULL when fill is given) and is written back.  fill, when given, makes each
+// slice instead of copying it in: (*fill)(dst, v) enqueues slice v of set A into dst on the
+// handle's stream, and the store is written without being read.
+int run_phase(sim_t *h, int set, const sim_plan_t *p, const std::function<int(float2 *, uint64_t)> *fill)
+{
     const int nl = h->n - h->s;
     struct Prepared {
         int k;
@@ -580,9 +595,9 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
         std::vector<float2> mat;
         size_t bytes = 0, off = 0;  // staged operands
     };
-    std::vector<Prepared> blocks(p->blocks.size());
+    std::vector<Prepared> blocks(p ? p->blocks.size() : 0);
     size_t staged_total = 0;
-    for (size_t i = 0; i < p->blocks.size(); i++) {
+    for (size_t i = 0; i < blocks.size(); i++) {
         const PlanBlock &b = p->blocks[i];
         Prepared &pb = blocks[i];
         pb.k = (int)b.qubits.size();
@@ -643,6 +658,13 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
     // gathers a file from every region and goes through a slot.
     const bool inplace = set == 0 && h->host_regions < nsl;
     std::vector<uint64_t> order;
+    if (fill) {
+        // the slices are written without being read: every copy-in queued so far (earlier phases
+        // reading the regions) must be done before the first write
+        for (int i = 0; i < h->nslots; i++)
+            if (cudaStreamWaitEvent(h->stream, h->ev_in[i], 0) != cudaSuccess)
+                return release(fail(h, SIM_E_CUDA, "run_phase: event wait"));
+    }
     if (inplace) {
         // the previous phase's copy-outs may have written into the device regions
         for (int i = 0; i < h->nslots; i++)
@@ -657,13 +679,21 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
     int next_slot = 0;
     for (const uint64_t v : order) {
         if (inplace && v >= h->host_regions) {
-            const int rc = apply_blocks(region(h, v));
+            int rc = fill ? (*fill)(region(h, v), v) : (int)SIM_OK;
+            if (rc == SIM_OK) rc = apply_blocks(region(h, v));
             if (rc != SIM_OK) return release(rc);
             continue;
         }
         const int slot = next_slot;
         next_slot = (next_slot + 1) % h->nslots;
-        int rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
+        int rc;
+        if (fill) {  // the slot's previous slice must have left it
+            if (cudaStreamWaitEvent(h->stream, h->ev_out[slot], 0) != cudaSuccess)
+                return release(fail(h, SIM_E_CUDA, "run_phase: event wait"));
+            rc = (*fill)(h->d_slot[slot], v);
+        } else {
+            rc = enqueue_slice_copy(h, set, v, SIM_H2D, slot);
+        }
         if (rc != SIM_OK) return release(rc);
         if ((rc = apply_blocks(h->d_slot[slot])) != SIM_OK) return release(rc);
         rc = enqueue_slice_copy(h, set, v, SIM_D2H, slot);
@@ -678,4 +708,86 @@ int sim_run_phase(sim_t *h, int set, const sim_plan_t *p)
     return SIM_OK;
 }
 
-}  // extern "C"
+}  // namespace sycsim
+
+extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision,
+                                  const sim_plan_t *p)
+{
+    if (!out || !t1 || !t2 || !s) return fail(out, SIM_E_INVAL, "sim_contract_phase: NULL argument");
+    if (out->store != SIM_STORE_HOST) {  // a resident state: the contraction, then the blocks
+        int rc = sim_contract(out, t1, t2, s, precision);
+        if (rc == SIM_OK && p) rc = sim_apply_plan(out, p);
+        return rc;
+    }
+    state_written(out);
+    if (out == t1 || out == t2 || t1 == t2)
+        return fail(out, SIM_E_INVAL, "sim_contract_phase: handles must be distinct");
+    if (precision != SIM_FP32 && precision != SIM_FP16X3 && precision != SIM_FP16X3_TMEM && precision != SIM_BF16X3)
+        return fail(out, SIM_E_INVAL, "sim_contract_phase: precision %d is not SIM_FP32, SIM_FP16X3, "
+                                      "SIM_FP16X3_TMEM or SIM_BF16X3", precision);
+    if (p && p->n != out->n) return fail(out, SIM_E_INVAL, "sim_contract_phase: plan for another n");
+    if (p)
+        for (const PlanBlock &b : p->blocks)
+            for (int q : b.qubits)
+                if (out->slice_phys[0][q] < 0)
+                    return fail(out, SIM_E_NONLOCAL, "sim_contract_phase: the plan acts on qubit %d of set A", q);
+    const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
+    for (sim_t *h : {t1, t2})
+        if (h->store != SIM_STORE_DEVICE || h->s != 0 || !h->d_state)
+            return fail(out, SIM_E_INVAL, "sim_contract_phase: the tensors must be device-resident and not sliced");
+    if (t1->device != out->device || t2->device != out->device)
+        return fail(out, SIM_E_INVAL, "sim_contract_phase: handles on different devices");
+    if (out->n != s->n || t1->n != n1 + e_bits || t2->n != n2 + e_bits)
+        return fail(out, SIM_E_INVAL, "sim_contract_phase: qubit counts (%d, %d, %d) do not fit the split (%d, %d, %d)",
+                    out->n, t1->n, t2->n, s->n, n1 + e_bits, n2 + e_bits);
+    SIM_DEVICE_SCOPE(out, out->device);
+    // set A selects the slice: its qubits on each side sit on that tensor's top side bits (the
+    // store's layout puts set A highest, and contract_layout orders side qubits by it); bit i of a
+    // slice's value is set A's i-th qubit, bit r of a side's fixed value its r-th set-A qubit
+    int top[2] = {0, 0}, side_of[8] = {}, rank_of[8] = {};
+    for (int i = 0; i < out->s; i++) {
+        side_of[i] = s->side[out->set[0][i]];
+        rank_of[i] = top[side_of[i]]++;
+    }
+    sim_t *tens[2] = {t1, t2};
+    for (int t = 0; t < 2; ++t) {
+        sim_t *h = tens[t];
+        if (!contract_ready(s, out->bit_of, t, h->bit_of, top[t])) {
+            int perm[kMaxQubits];
+            contract_layout(s, out->bit_of, t, perm, nullptr);
+            const int rc = sim_permute(h, perm);
+            if (rc != SIM_OK)
+                return fail(out, rc, "sim_contract_phase: permuting tensor %d: %s", t + 1, h->err.c_str());
+        }
+    }
+    cudaEvent_t ev[3] = {};
+    for (auto &e : ev) SIM_CUDA_TRY(out, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    auto finish = [&](int rc) {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        return rc;
+    };
+    if (cudaEventRecord(ev[0], t1->stream) != cudaSuccess || cudaEventRecord(ev[1], t2->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(out->stream, ev[0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(out->stream, ev[1], 0) != cudaSuccess)
+        return finish(fail(out, SIM_E_CUDA, "sim_contract_phase: stream ordering failed"));
+    const int *tbits[2] = {t1->bit_of, t2->bit_of};
+    ContractJob job;
+    if (contract_job_prepare(out, s, t1->d_state, t2->d_state, tbits, out->bit_of, precision, top, nullptr,
+                             out->stream, &job) != 0)
+        return finish(fail(out, SIM_E_CUDA, "sim_contract_phase: operand images: %s",
+                           cudaGetErrorString(cudaGetLastError())));
+    const std::function<int(float2 *, uint64_t)> fill = [&](float2 *dst, uint64_t v) {
+        uint64_t fix[2] = {0, 0};
+        for (int i = 0; i < out->s; i++) fix[side_of[i]] |= ((v >> i) & 1ull) << rank_of[i];
+        if (contract_job_launch(out, job, dst, fix[0], fix[1], out->stream) != 0)
+            return fail(out, SIM_E_CUDA, "sim_contract_phase: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return (int)SIM_OK;
+    };
+    const int rc = run_phase(out, 0, p, &fill);
+    // the tensors stay untouched until the last slice has been contracted
+    if (cudaEventRecord(ev[2], out->stream) != cudaSuccess || cudaStreamWaitEvent(t1->stream, ev[2], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(t2->stream, ev[2], 0) != cudaSuccess)
+        return finish(rc != SIM_OK ? rc : fail(out, SIM_E_CUDA, "sim_contract_phase: stream ordering failed"));
+    return finish(rc);
+}

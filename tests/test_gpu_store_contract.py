@@ -1,0 +1,190 @@
+"""GPU: the contraction straight into a sliced host store (Sect. 4: tensors 1 and 2 are contracted
+slice by slice into the secondary-storage state of subcircuit 3).
+
+sim_contract_phase and sim_front_run_phase fill every slice of set A from the two tensors (in a
+device slot, or in place for a hybrid store's device regions), optionally run a phase's blocks on
+it, and write it once.  Every amplitude, read back in logical order, is compared with the
+oracle's plain simulation of the same gates: set A's qubits on both sides, on one side only (the
+side left too narrow for the tensor-core kernel takes the FP32 one), 2 and 3 sliced bits, a hybrid
+store, FP32 and 3xFP16 on tcgen05, with and without the fused phase, and a set-B phase after it.
+"""
+import numpy as np
+import pytest
+
+import syc_inputs as si
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1910_09534_gb300 import build
+    build.build()
+    import paper_1910_09534_gb300 as p
+    return p
+
+
+def front_length(grid, cycles):
+    """Gate records in the first `cycles` cycles (a 1q layer plus the cycle's pattern each)."""
+    n = grid.n_qubits
+    return sum(n + len(grid.pattern(si.PATTERN_ORDER[t % 8])) for t in range(cycles))
+
+
+def column_sides(grid, cut):
+    return [0 if c < cut else 1 for (r, c) in grid.sites()]
+
+
+def tensor_handles(pkg, s, kmax, precision):
+    _, n_wires, _, _ = pkg.sim_split_info(s)
+    hs = []
+    for t in range(2):
+        h = pkg.sim_create(n_wires[t])
+        plan = pkg.sim_plan_create(n_wires[t], pkg.sim_split_gates(s, t), kmax=kmax, precision=precision)
+        pkg.sim_apply_plan(h, plan)
+        pkg.sim_plan_destroy(plan)
+        hs.append(h)
+    return hs
+
+
+def avoiding(circ, start, count, qubits):
+    """Indices of up to `count` gates from `start` on that touch none of `qubits`."""
+    bad = set(qubits)
+    out = []
+    for i in range(start, len(circ.gates)):
+        g = circ.gates[i]
+        qs = {g[1]} if g[2] < 0 else {g[1], g[2]}  # one-qubit gates carry q1 = -1
+        if not qs & bad:
+            out.append(i)
+            if len(out) == count:
+                break
+    return out
+
+
+def err2(got, want):
+    d = got.astype(np.complex128) - want
+    return float(np.sqrt(np.vdot(d, d).real))
+
+
+GRID, CYCLES, CUT = (4, 5), 4, 2  # 20 qubits; side 0 = columns 0-1 (8 qubits), side 1 = 12 qubits
+
+
+@pytest.mark.parametrize("set_a,set_b,regions,prec", [
+    ([1, 13], [8, 12], 0, "tmem"),     # one set-A qubit per side, tcgen05 (7 + 11 free side bits)
+    ([1, 13], [8, 12], 0, "fp32"),     # the FP32 kernel on strided sub-ranges
+    ([13, 18], [2, 7], 2, "tmem"),     # both on side 1; hybrid store: 2 of 4 regions in place
+    ([0, 6], [13, 18], 0, "tmem"),     # both on side 0: 6 free bits there, the FP32 kernel
+    ([1, 13, 19], [7, 8, 12], 3, "tmem"),  # 3 sliced bits, 8 slices, 3 in device memory
+])
+def test_contraction_into_store_matches_oracle(pkg, oracle_mod, set_a, set_b, regions, prec):
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, CYCLES + 2, seed=31)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    precision = pkg.SIM_FP32 if prec == "fp32" else pkg.SIM_FP16X3_TMEM
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    t1, t2 = tensor_handles(pkg, s, 4, precision)
+    out = pkg.sim_create(n, len(set_a), store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=2,
+                         store_device_regions=regions)
+    try:
+        pkg.sim_contract_phase(out, t1, t2, s, precision)
+        pkg.sim_sync(out)
+        got = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+        norm, s2, _ = pkg.sim_reduce(out)
+    finally:
+        for h in (out, t1, t2):
+            pkg.sim_destroy(h)
+        pkg.sim_split_destroy(s)
+    want = oracle_mod.run_circuit(circ.gates[:nf], n_qubits=n)
+    assert err2(got, want) <= TOL
+    onorm, os2, _ = oracle_mod.reduce(want)
+    assert abs(norm - onorm) < 1e-5 and abs(s2 - os2) < 1e-4
+
+
+@pytest.mark.parametrize("regions", [0, 2])
+def test_fused_phase_then_set_b_phase_match_oracle(pkg, oracle_mod, regions):
+    # the front runner contracts into the store with the first phase's blocks (gates avoiding set
+    # A) fused; a set-B phase (gates avoiding set B) follows through sim_run_phase
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, CYCLES + 6, seed=32)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    set_a, set_b = [1, 13], [8, 12]
+    ph1 = avoiding(circ, nf, 60, set_a)
+    ph2 = avoiding(circ, ph1[-1] + 1, 60, set_b)
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    out = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3,
+                         store_device_regions=regions)
+    fr = pkg.sim_front_create(out, s, kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    p1 = pkg.sim_plan_create(n, gates[ph1], kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    p2 = pkg.sim_plan_create(n, gates[ph2], kmax=5, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        n0 = pkg.sim_launch_count(out)
+        pkg.sim_front_run_phase(out, fr, p1)
+        pkg.sim_run_phase(out, 1, p2)
+        pkg.sim_sync(out)
+        assert pkg.sim_launch_count(out) > n0
+        got = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_front_destroy(fr)
+        for p in (p1, p2):
+            pkg.sim_plan_destroy(p)
+        pkg.sim_destroy(out)
+        pkg.sim_split_destroy(s)
+    want = oracle_mod.run_circuit([circ.gates[i] for i in list(range(nf)) + ph1 + ph2], n_qubits=n)
+    assert err2(got, want) <= TOL
+
+
+def test_front_run_into_store_twice_overwrites(pkg, oracle_mod):
+    # the store's earlier contents do not matter: a second front run gives the same state
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, CYCLES, seed=33)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    out = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=[1, 13], set_b=[8, 12], slots=2)
+    fr = pkg.sim_front_create(out, s, kmax=4, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        pkg.sim_reset(out, 5)
+        pkg.sim_front_run(out, fr)
+        pkg.sim_sync(out)
+        first = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+        pkg.sim_front_run(out, fr)
+        pkg.sim_sync(out)
+        second = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_front_destroy(fr)
+        pkg.sim_destroy(out)
+        pkg.sim_split_destroy(s)
+    assert np.array_equal(first, second)
+    assert err2(first, oracle_mod.run_circuit(circ.gates[:nf], n_qubits=n)) <= TOL
+
+
+def test_plan_on_set_a_is_rejected_and_device_out_contracts(pkg, oracle_mod):
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, CYCLES + 1, seed=34)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    t1, t2 = tensor_handles(pkg, s, 4, pkg.SIM_FP16X3_TMEM)
+    store = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=[1, 13], set_b=[8, 12], slots=2)
+    dev = pkg.sim_create(n)
+    rest = gates[nf:]  # touches every qubit, set A's too
+    p = pkg.sim_plan_create(n, rest, kmax=4, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_contract_phase(store, t1, t2, s, pkg.SIM_FP16X3_TMEM, p)
+        assert e.value.code == pkg.SIM_E_NONLOCAL
+        # a device-resident out: the contraction, then the plan
+        pkg.sim_contract_phase(dev, t1, t2, s, pkg.SIM_FP16X3_TMEM, p)
+        got = pkg.sim_amplitudes(dev, dtype=pkg.SIM_C128)
+    finally:
+        for h in (store, dev, t1, t2):
+            pkg.sim_destroy(h)
+        pkg.sim_plan_destroy(p)
+        pkg.sim_split_destroy(s)
+    assert err2(got, oracle_mod.run_circuit(circ, n_qubits=n)) <= TOL
