@@ -60,8 +60,8 @@ UNIT = "amp-updates/s"
 # sliced sets are picked (the lattice ends, or sim_phases_choose_sets).
 LARGE_CASES = {
     "syc33_6x6m3_d20": dict(store="device", slice_bits=3, kmax=6, device_regions=0, sets="ends"),
-    "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=5, device_regions=0, sets="chosen"),
-    "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=5, device_regions=8, sets="chosen"),
+    "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=5, device_regions=0, sets="chosen", front_pairs=4),
+    "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=5, device_regions=8, sets="chosen", front_pairs=4),
 }
 
 
@@ -115,6 +115,11 @@ def parse():
                     help="run one configuration beyond the bench's 30 qubits instead (33 qubits resident "
                          "in 8 slices with sliced phases; 34 and 35 qubits streamed through a host store, "
                          "35 with half its regions in HBM), print one JSON line, and exit")
+    ap.add_argument("--large-kmax", type=int, default=0,
+                    help="with --large-case: block width (0: the case's own)")
+    ap.add_argument("--large-front-pairs", type=int, default=-1,
+                    help="with --large-case on a host store: bridging gates of the contraction-deferral "
+                         "front (-1: the case's own, 0: none, the whole circuit in phases)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
                          "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
@@ -907,7 +912,8 @@ def kernel_case():
     print("kernel case done", flush=True)
 
 
-def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0) -> dict:
+def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0, front_pairs: int = -1,
+                   kmax: int = 0) -> dict:
     """One run of a configuration from LARGE_CASES in SIM_FP16X3_TMEM at the case's block width, or
     in SIM_FP32 at k_max 4 (the resident one after a warm-up run; a streamed run takes seconds and
     runs once): wall time, gate updates/s, the apply kernels' time and bandwidth with their HBM
@@ -918,37 +924,72 @@ def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0) -
 
     cfg = LARGE_CASES[name]
     circ = si.workload_circuit(name, seed=0)
-    n, s, kmax = circ.n_qubits, cfg["slice_bits"], cfg["kmax"]
+    n, s, kmax = circ.n_qubits, cfg["slice_bits"], kmax or cfg["kmax"]
     gates = pkg.gates_array(circ)
     prec = pkg.SIM_FP16X3_TMEM
     if precision == "fp32":
         prec, kmax = pkg.SIM_FP32, 4
+    host = cfg["store"] == "host"
+    # into a host store, the circuit's first gates run as contraction deferral (Sect. 4's first
+    # phase): two tensors contracted slice by slice straight into the store, fused with the first
+    # phase's blocks; the sliced sets and phases are chosen for the remaining gates
+    split, n_front, front_info = None, 0, None
+    pairs_wanted = cfg.get("front_pairs", 0) if front_pairs < 0 else front_pairs
+    if host and pairs_wanted > 0:
+        side, n_front = pkg.sim_split_choose(n, gates, pairs_wanted)
+        split = pkg.sim_split_create(n, gates[:n_front], side)
+        n_side, n_wires, pairs, _ = pkg.sim_split_info(split)
+        front_info = {"gates": n_front, "bridging_gates": pairs, "qubits_per_side": [int(x) for x in n_side],
+                      "tensor_qubits": [int(x) for x in n_wires]}
+    rest = gates[n_front:]
     if cfg["sets"] == "chosen":
-        set_a, set_b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=kmax)
+        set_a, set_b, _, _ = pkg.sim_phases_choose_sets(n, rest, s, kmax=kmax)
     else:
         set_a, set_b = list(range(s)), list(range(n - s, n))
-    ph = pkg.sim_phases_create(n, gates, s, set_a, set_b, kmax=kmax, precision=prec)
+    ph = pkg.sim_phases_create(n, rest, s, set_a, set_b, kmax=kmax, precision=prec)
     n_phases, n_blocks = pkg.sim_phases_info(ph)
-    host = cfg["store"] == "host"
+    front = None
     if host:
         h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3,
                            store_device_regions=cfg["device_regions"], device=device)
+        if split is not None:
+            front = pkg.sim_front_create(h, split, kmax=kmax, precision=prec)
     else:
         h = pkg.sim_create(n, s, device=device)
         pkg.sim_reset(h)
         pkg.sim_run_phases(h, ph)  # warm-up
         pkg.sim_sync(h)
-    pkg.sim_reset(h)
+    fused = front is not None and pkg.sim_phases_get(ph, 0)[0] == 0
+
+    def run():
+        if front is None:
+            pkg.sim_run_phases(h, ph)
+            return
+        if fused:  # the contraction fills each set-A slice, the first phase's blocks run on it
+            pkg.sim_front_run_phase(h, front, pkg.sim_phases_get(ph, 0)[1])
+        else:
+            pkg.sim_front_run(h, front)
+        for i in range(1 if fused else 0, n_phases):
+            set_i, plan_i = pkg.sim_phases_get(ph, i)
+            pkg.sim_run_phase(h, set_i, plan_i)
+
+    if front is None:
+        pkg.sim_reset(h)
     pkg.sim_sync(h)
     pkg.sim_profile_enable(h, True)
     t0 = time.perf_counter()
-    pkg.sim_run_phases(h, ph)
+    run()
     pkg.sim_sync(h)
     wall = time.perf_counter() - t0
     a_n, a_ms, a_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
     p_n, p_ms, p_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_PERMUTE)
+    c_n, c_ms, _ = pkg.sim_profile_read(h, pkg.SIM_PROF_CONTRACT)
     pkg.sim_profile_enable(h, False)
     norm, s2, _ = pkg.sim_reduce(h)
+    if front is not None:
+        pkg.sim_front_destroy(front)
+        pkg.sim_split_destroy(split)
+        front_info.update({"first_phase_fused": fused, "contraction_launches": c_n, "contraction_ms": c_ms})
     pkg.sim_destroy(h)
     pkg.sim_phases_destroy(ph)
     state_bytes = 8.0 * (1 << n)
@@ -966,19 +1007,21 @@ def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0) -
                                    "alg_bytes": a_bytes}},
             "norm": norm, "porter_thomas_2n_sum_p2": s2,
             "norm_drift_per_pass": (norm - 1.0) / max(n_blocks, 1)}
-    if host:  # every phase moves the host regions out and back
-        moved = 2 * n_phases * state_bytes * (1 - cfg["device_regions"] / (1 << s))
+    if front_info is not None:
+        line["front"] = front_info
+    if host:  # every phase moves the host regions out and back (the fused first phase only out)
+        moved = (2 * n_phases - (1 if fused else 0)) * state_bytes * (1 - cfg["device_regions"] / (1 << s))
         line["host_link_gbs_combined"] = moved / wall / 1e9
     else:
         line["permute"] = {"passes": p_n, "ms": p_ms, "gbs_moved": p_bytes / (p_ms / 1e3) / 1e9 if p_ms else None}
     return line
 
 
-def large_case(name: str, precision: str = "fp16x3_tmem"):
+def large_case(name: str, precision: str = "fp16x3_tmem", front_pairs: int = -1, kmax: int = 0):
     from paper_1910_09534_gb300 import build as pkg_build
 
     pkg_build.build()
-    print(json.dumps(large_case_run(name, precision)), flush=True)
+    print(json.dumps(large_case_run(name, precision, front_pairs=front_pairs, kmax=kmax)), flush=True)
 
 
 def serving_case(args):
@@ -994,7 +1037,8 @@ def serving_case(args):
 def main():
     args = parse()
     if args.large_case:
-        large_case(args.large_case, "fp32" if args.precision == "fp32" else "fp16x3_tmem")
+        large_case(args.large_case, "fp32" if args.precision == "fp32" else "fp16x3_tmem", args.large_front_pairs,
+                   args.large_kmax)
     elif args.serving_only:
         serving_case(args)
     elif args.kernel_case:
