@@ -60,8 +60,8 @@ UNIT = "amp-updates/s"
 # sliced sets are picked (the lattice ends, or sim_phases_choose_sets).
 LARGE_CASES = {
     "syc33_6x6m3_d20": dict(store="device", slice_bits=3, kmax=6, device_regions=0, sets="ends"),
-    "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=5, device_regions=0, sets="chosen", front_pairs=4),
-    "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=5, device_regions=8, sets="chosen", front_pairs=4),
+    "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=6, device_regions=0, sets="chosen", front_pairs=4),
+    "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=6, device_regions=8, sets="chosen", front_pairs=4),
 }
 
 
