@@ -335,7 +335,10 @@ int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, 
 /* Relabel the physical bits without moving any amplitude (perm as for sim_permute): the logical
  * state changes, so this belongs before sim_reset, sim_front_run or sim_contract, which overwrite
  * every amplitude -- the way to start a plan in the layout sim_plan_layout chose without a
- * permutation pass.  Device-store handles that are not sliced; SIM_E_INVAL otherwise. */
+ * permutation pass.  Device-store handles that are not sliced, and host stores as long as perm
+ * keeps both sliced sets on the bits the store gives them (only the other qubits' order changes:
+ * the host layout and the slots' [others | B] / [others | A] layouts alike; sim_phases_layout
+ * chooses it); SIM_E_INVAL otherwise. */
 int sim_set_layout(sim_t *h, const int *perm);
 
 typedef struct sim_graph_s sim_graph_t;
@@ -418,6 +421,16 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
+/* Where the qubits outside the two sliced sets should sit in a host store that runs the phases
+ * ph (not in the paper; as sim_plan_layout, the fused kernels' speed depends on which qubits sit
+ * on the low physical bits).  perm[q] for every qubit: set B on bits n-2s .. n-s-1 and set A on
+ * n-s .. n-1 in set order (where a host store keeps them), the others on 0 .. n-2s-1 in the
+ * order that minimises the per-pass estimates summed over every phase's blocks (local search
+ * from the ascending order and from seeded random orders).  est_ms (may be NULL): {chosen,
+ * ascending}.  Apply it with sim_set_layout before the state is written (sim_reset,
+ * sim_front_run, sim_contract_phase).  Host only. */
+int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms);
+
 /* ---- contraction deferral: two subcircuits joined by entanglement indices -----
  * Sect. 2 (contraction deferral: subcircuits simulated separately, each with the Schroedinger
  * approach, bridging gates deferred) and the Appendix (the synthesized operations EI and E2Q and
@@ -482,18 +495,19 @@ int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int pre
 
 /* The first phase of a sliced run with its state made by the contraction (Sect. 4: tensors 1
  * and 2 are contracted slice by slice straight into the secondary-storage state of subcircuit 3).
- * out: a host-store handle (sim_create with SIM_STORE_HOST); for every slice of set A, the slice
- * of psi is contracted from t1 and t2 into a device slot (for a hybrid store's device regions, in
- * place), the blocks of p are applied to it (a plan over qubits outside set A, as for
- * sim_run_phase with set A; NULL for none), and it is written to the store once: no slice is
- * read, and the store's earlier contents do not matter.  t1, t2, s, precision: as for
- * sim_contract (each tensor is permuted first unless its layout already puts its side's set-A
- * qubits on its top side bits in set-A order; sim_front_run_phase lays them out that way).
- * With a device-resident out it is sim_contract followed by sim_apply_plan.  Asynchronous like
- * sim_run_phase; the tensors must not change until sim_sync(out).  SIM_E_INVAL for NULL or
- * shared handles, mismatched sizes or a plan for another qubit count; SIM_E_NONLOCAL for a plan
- * with a block on a qubit of set A (nothing is queued then). */
-int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision,
+ * out: a host-store handle (sim_create with SIM_STORE_HOST); for every slice of the sliced set
+ * `set` (0 = A, 1 = B, as for sim_run_phase), the slice of psi is contracted from t1 and t2 into
+ * a device slot (set A on a hybrid store: its device regions in place), the blocks of p are
+ * applied to it (a plan over qubits outside that set, as for sim_run_phase; NULL for none), and
+ * it is written to the store once: no slice is read, and the store's earlier contents do not
+ * matter.  t1, t2, s, precision: as for sim_contract (each tensor is permuted first unless its
+ * layout already puts its side's qubits of the sliced set on its top side bits, in set order;
+ * sim_front_run_phase lays them out that way).  With a device-resident out it is sim_contract
+ * followed by sim_apply_plan.  Asynchronous like sim_run_phase; the tensors must not change until
+ * sim_sync(out).  SIM_E_INVAL for NULL or shared handles, mismatched sizes, a set other than 0
+ * or 1 or a plan for another qubit count; SIM_E_NONLOCAL for a plan with a block on a qubit of
+ * the sliced set (nothing is queued then). */
+int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision, int set,
                        const sim_plan_t *p);
 
 /* A split made ready to run (Sect. 2's subcircuits 1 and 2 and their contraction as one reusable
@@ -512,12 +526,13 @@ int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan_opts *o, s
 int sim_front_run(sim_t *out, sim_front_t *f);
 
 /* sim_front_run, then the blocks of p on the contracted state, in one pass when out is a host
- * store: the contraction fills each slice of set A and p's blocks (qubits outside set A, as for
- * sim_run_phase with set A) run on it before it is written (sim_contract_phase).  For a
- * device-resident out: sim_front_run then sim_apply_plan.  p may be NULL.  The tensors' layouts
- * keep each side's set-A qubits on their top side bits.  Errors as sim_front_run and
- * sim_contract_phase. */
-int sim_front_run_phase(sim_t *out, sim_front_t *f, const sim_plan_t *p);
+ * store: the contraction fills each slice of sliced set `set` (0 = A, 1 = B) and p's blocks
+ * (qubits outside that set, as for sim_run_phase) run on it before it is written
+ * (sim_contract_phase) -- the first phase of sim_phases_create's list, whichever set it slices.
+ * For a device-resident out: sim_front_run then sim_apply_plan.  p may be NULL.  The tensors'
+ * layouts keep each side's qubits of the sliced set on their top side bits.  sim_front_run(out,
+ * f) is sim_front_run_phase(out, f, 0, NULL).  Errors as sim_front_run and sim_contract_phase. */
+int sim_front_run_phase(sim_t *out, sim_front_t *f, int set, const sim_plan_t *p);
 int sim_front_destroy(sim_front_t *f);
 
 /* ---- a state sharded over global qubits on 2^g ranks (Sect. 4) ------------------------------

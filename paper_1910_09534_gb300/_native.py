@@ -161,9 +161,10 @@ _SIGS = {
     "sim_front_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "sim_front_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
-    "sim_front_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_front_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sim_phases_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_contract_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_int, ctypes.c_void_p]),
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "sim_front_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "sim_state_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "sim_state_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
@@ -595,14 +596,16 @@ def sim_front_run(out, f) -> None:
     _check(lib().sim_front_run(out, f), out)
 
 
-def sim_front_run_phase(out, f, plan=None) -> None:
-    """sim_front_run, then plan's blocks on the contracted state (one pass into a host store)."""
-    _check(lib().sim_front_run_phase(out, f, plan), out)
+def sim_front_run_phase(out, f, set_: int = 0, plan=None) -> None:
+    """sim_front_run, then plan's blocks on the contracted state (one pass into a host store whose
+    phase slices set_: 0 = A, 1 = B)."""
+    _check(lib().sim_front_run_phase(out, f, set_, plan), out)
 
 
-def sim_contract_phase(out, t1, t2, s, precision: int = SIM_FP32, plan=None) -> None:
-    """Contraction slice by slice into a host store's set-A slices, plan's blocks on each, one write."""
-    _check(lib().sim_contract_phase(out, t1, t2, s, precision, plan), out)
+def sim_contract_phase(out, t1, t2, s, precision: int = SIM_FP32, set_: int = 0, plan=None) -> None:
+    """Contraction slice by slice into a host store's slices of set_ (0 = A, 1 = B), plan's blocks
+    on each, one write."""
+    _check(lib().sim_contract_phase(out, t1, t2, s, precision, set_, plan), out)
 
 
 def sim_front_destroy(f) -> None:
@@ -625,6 +628,14 @@ def sim_phases_info(ph):
     n, t = ctypes.c_int(), ctypes.c_int()
     _check(lib().sim_phases_info(ph, ctypes.byref(n), ctypes.byref(t)))
     return n.value, t.value
+
+
+def sim_phases_layout(ph, n_qubits: int):
+    """(perm, estimate, ascending estimate): the host-store order of the qubits outside the sliced sets."""
+    perm = np.zeros(n_qubits, dtype=np.int32)
+    est = np.zeros(2, dtype=np.float64)
+    _check(lib().sim_phases_layout(ph, _ptr(perm), _ptr(est)))
+    return [int(x) for x in perm], float(est[0]), float(est[1])
 
 
 def sim_phases_get(ph, i: int):

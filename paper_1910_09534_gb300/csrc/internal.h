@@ -362,9 +362,17 @@ int enqueue_contraction(sim_t *h, const sim_split_s *s, const float2 *t1, const 
                         const int *const *tensor_bit_of = nullptr);
 
 // ---- store.cu ----
-// One phase over a host store (sim_run_phase's body): fill, when given, makes each slice v of set
-// A in place of its copy-in ((*fill)(dst, v) enqueues it into dst on the handle's stream); p may
-// then be NULL (no blocks).
+// The layout a slice of sliced set `set` (0 = A, 1 = B) of host store h is written in, extended
+// to all n qubits: the others as in the store, the other set where the slot keeps it (bits
+// n-2s ..), the sliced set on top (n-s ..: its value selects the slice).  For set A it is the
+// store's own layout.
+void store_fill_layout(const sim_t *h, int set, int *lay);
+// Relabel a host store's qubits outside its sliced sets (perm as for sim_set_layout; sets A and B
+// must keep their bits, else false and nothing changes): the host layout and both slot layouts.
+bool host_store_relabel(sim_t *h, const int *perm);
+// One phase over a host store (sim_run_phase's body): fill, when given, makes each slice v of the
+// sliced set in place of its copy-in ((*fill)(dst, v) enqueues it into dst on the handle's stream);
+// p may then be NULL (no blocks).
 int run_phase(sim_t *h, int set, const sim_plan_t *p, const std::function<int(float2 *, uint64_t)> *fill);
 
 // ---- split.cpp ----

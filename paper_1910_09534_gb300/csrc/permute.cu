@@ -482,13 +482,18 @@ extern "C" int sim_set_layout(sim_t *h, const int *perm)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_set_layout: NULL handle");
     state_written(h);
     if (!perm) return fail(h, SIM_E_INVAL, "sim_set_layout: NULL perm");
-    if (h->store != SIM_STORE_DEVICE || h->s != 0)
-        return fail(h, SIM_E_INVAL, "sim_set_layout: device-store handles that are not sliced only");
+    if (h->store == SIM_STORE_DEVICE && h->s != 0)
+        return fail(h, SIM_E_INVAL, "sim_set_layout: not for sliced device-resident handles");
     bool used[kMaxQubits] = {};
     for (int q = 0; q < h->n; q++) {
         if (perm[q] < 0 || perm[q] >= h->n || used[perm[q]])
             return fail(h, SIM_E_INVAL, "sim_set_layout: perm is not a bijection on 0..%d", h->n - 1);
         used[perm[q]] = true;
+    }
+    if (h->store == SIM_STORE_HOST) {
+        if (!host_store_relabel(h, perm))
+            return fail(h, SIM_E_INVAL, "sim_set_layout: a host store keeps sets A and B on their bits");
+        return SIM_OK;
     }
     for (int q = 0; q < h->n; q++) {
         h->bit_of[q] = perm[q];

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <random>
 #include <vector>
 
 #include "internal.h"
@@ -600,6 +601,68 @@ int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, 
     // the contraction's stores: lanes of a warp hold 32 consecutive x (the side-0 qubits in order of
     // their physical bits), so side-0 qubits at bits 0-4 make each store one 256-byte run
     return layout_search(p, low.data(), std::min(5, n_side0), perm, est_ms);
+}
+
+int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms)
+{
+    if (!ph || !perm) return fail(nullptr, SIM_E_INVAL, "sim_phases_layout: NULL argument");
+    const int n = ph->n, s = ph->s, r = n - 2 * s;
+    std::vector<char> sliced(n, 0);
+    for (int i = 0; i < s; i++) sliced[ph->set_a[i]] = sliced[ph->set_b[i]] = 1;
+    std::vector<int> order;  // the others, position i -> qubit
+    for (int q = 0; q < n; q++)
+        if (!sliced[q]) order.push_back(q);
+    // a phase's slot: the others on 0 .. r-1, the set it does not slice on r .. r+s-1 (the sliced
+    // set's bits are never read: its blocks avoid it)
+    auto total = [&](const std::vector<int> &ord) {
+        int bit[kMaxQubits];
+        for (int q = 0; q < n; q++) bit[q] = -1;
+        for (int i = 0; i < r; i++) bit[ord[i]] = i;
+        double t = 0.0;
+        for (size_t i = 0; i < ph->plans.size(); i++) {
+            const int *hi = ph->set_of[i] == 0 ? ph->set_b : ph->set_a;
+            for (int j = 0; j < s; j++) bit[hi[j]] = r + j;
+            t += plan_estimate_ms(ph->plans[i], bit);
+        }
+        return t;
+    };
+    const double ascending = total(order);
+    double best = ascending;
+    std::vector<int> best_order = order;
+    std::mt19937 rng(12345);
+    for (int start = 0; start < SYCSIM_LAYOUT_STARTS; start++) {
+        std::vector<int> ord = order;
+        if (start > 0) std::shuffle(ord.begin(), ord.end(), rng);
+        double cost = total(ord);
+        for (bool improved = true; improved;) {  // pairwise exchanges while one lowers the estimate
+            improved = false;
+            for (int i = 0; i < r; i++)
+                for (int j = i + 1; j < r; j++) {
+                    std::swap(ord[i], ord[j]);
+                    const double c = total(ord);
+                    if (c < cost - 1e-9) {
+                        cost = c;
+                        improved = true;
+                    } else {
+                        std::swap(ord[i], ord[j]);
+                    }
+                }
+        }
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_order = ord;
+        }
+    }
+    for (int i = 0; i < r; i++) perm[best_order[i]] = i;
+    for (int i = 0; i < s; i++) {
+        perm[ph->set_b[i]] = r + i;
+        perm[ph->set_a[i]] = n - s + i;
+    }
+    if (est_ms) {
+        est_ms[0] = best;
+        est_ms[1] = ascending;
+    }
+    return SIM_OK;
 }
 
 int sim_apply_plan(sim_t *h, const sim_plan_t *p)

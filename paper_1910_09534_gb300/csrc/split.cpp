@@ -256,21 +256,27 @@ extern "C" int sim_front_create(sim_t *out, const sim_split_t *s, const sim_plan
     return SIM_OK;
 }
 
-extern "C" int sim_front_run_phase(sim_t *out, sim_front_t *f, const sim_plan_t *p)
+extern "C" int sim_front_run_phase(sim_t *out, sim_front_t *f, int set, const sim_plan_t *p)
 {
     if (!out || !f) return fail(out, SIM_E_INVAL, "sim_front_run: NULL argument");
     state_written(out);
     if (out->device != f->device) return fail(out, SIM_E_INVAL, "sim_front_run: out is on another device");
     if (out->n != f->split.n)
         return fail(out, SIM_E_INVAL, "sim_front_run: out has %d qubits, the split %d", out->n, f->split.n);
-    // into a host store, each side's set-A qubits stay on its tensor's top side bits
-    int top[2] = {0, 0};
-    if (out->store == SIM_STORE_HOST)
-        for (int i = 0; i < out->s; i++) top[f->split.side[out->set[0][i]]]++;
-    if (f->lay_for.size() != (size_t)out->n + 2 || !std::equal(out->bit_of, out->bit_of + out->n, f->lay_for.begin()) ||
+    if (set < 0 || set > 1) return fail(out, SIM_E_INVAL, "sim_front_run: set must be 0 (A) or 1 (B)");
+    // into a host store, the contraction writes slices of the sliced set in store_fill_layout's
+    // layout; each side's qubits of that set stay on its tensor's top side bits
+    int olay[kMaxQubits], top[2] = {0, 0};
+    if (out->store == SIM_STORE_HOST) {
+        store_fill_layout(out, set, olay);
+        for (int i = 0; i < out->s; i++) top[f->split.side[out->set[set][i]]]++;
+    } else {
+        std::copy(out->bit_of, out->bit_of + out->n, olay);
+    }
+    if (f->lay_for.size() != (size_t)out->n + 2 || !std::equal(olay, olay + out->n, f->lay_for.begin()) ||
         f->lay_for[out->n] != top[0] || f->lay_for[out->n + 1] != top[1]) {
-        for (int t = 0; t < 2; ++t) front_tensor_layout(&f->split, f->p[t], t, out->bit_of, f->lay[t], top[t]);
-        f->lay_for.assign(out->bit_of, out->bit_of + out->n);
+        for (int t = 0; t < 2; ++t) front_tensor_layout(&f->split, f->p[t], t, olay, f->lay[t], top[t]);
+        f->lay_for.assign(olay, olay + out->n);
         f->lay_for.push_back(top[0]);
         f->lay_for.push_back(top[1]);
     }
@@ -288,10 +294,10 @@ extern "C" int sim_front_run_phase(sim_t *out, sim_front_t *f, const sim_plan_t 
         out->launches += f->t[t]->launches - before;  // the front's kernels count as out's
         if (rc != SIM_OK) return fail(out, rc, "sim_front_run: tensor %d: %s", t + 1, f->t[t]->err.c_str());
     }
-    return sim_contract_phase(out, f->t[0], f->t[1], &f->split, f->contract_precision, p);
+    return sim_contract_phase(out, f->t[0], f->t[1], &f->split, f->contract_precision, set, p);
 }
 
-extern "C" int sim_front_run(sim_t *out, sim_front_t *f) { return sim_front_run_phase(out, f, nullptr); }
+extern "C" int sim_front_run(sim_t *out, sim_front_t *f) { return sim_front_run_phase(out, f, 0, nullptr); }
 
 namespace {
 

@@ -180,6 +180,33 @@ int host_store_create(sim_t *h, const sim_opts &o)
     return SIM_OK;
 }
 
+void store_fill_layout(const sim_t *h, int set, int *lay)
+{
+    const int n = h->n, s = h->s;
+    for (int q = 0; q < n; q++) lay[q] = h->bit_of[q];
+    for (int i = 0; i < s; i++) {
+        lay[h->set[1 - set][i]] = n - 2 * s + i;  // where the slot keeps the other set
+        lay[h->set[set][i]] = n - s + i;          // the sliced set on top: its value picks the slice
+    }
+}
+
+bool host_store_relabel(sim_t *h, const int *perm)
+{
+    const int n = h->n, s = h->s;
+    bool sliced[kMaxQubits] = {};
+    for (int w = 0; w < 2; w++)
+        for (int i = 0; i < s; i++) {
+            sliced[h->set[w][i]] = true;
+            if (perm[h->set[w][i]] != h->bit_of[h->set[w][i]]) return false;
+        }
+    for (int q = 0; q < n; q++) {
+        h->bit_of[q] = perm[q];
+        h->qubit_at[perm[q]] = q;
+        if (!sliced[q]) h->slice_phys[0][q] = h->slice_phys[1][q] = perm[q];  // slots: [others | B or A]
+    }
+    return true;
+}
+
 void host_store_release(sim_t *h)
 {
     if (h->st_in) cudaStreamSynchronize(h->st_in);
@@ -482,12 +509,14 @@ extern "C" int sim_state_load(sim_t *h, const char *path)
         std::fclose(f);
         return fail(h, SIM_E_INVAL, "sim_state_load: corrupt layout in %s", path);
     }
-    if (h->store == SIM_STORE_HOST) {
-        for (int q = 0; q < h->n; q++)
-            if (hd.bit_of[q] != h->bit_of[q]) {
-                std::fclose(f);
-                return fail(h, SIM_E_INVAL, "sim_state_load: the host store's layout (its sliced sets) differs from the file's");
-            }
+    if (h->store == SIM_STORE_HOST) {  // the same sliced sets in the same places; the others may differ
+        for (int w = 0; w < 2; w++)
+            for (int i = 0; i < h->s; i++)
+                if (hd.bit_of[h->set[w][i]] != h->bit_of[h->set[w][i]]) {
+                    std::fclose(f);
+                    return fail(h, SIM_E_INVAL,
+                                "sim_state_load: the host store's layout (its sliced sets) differs from the file's");
+                }
     }
     PinnedChunk buf;
     if (cudaHostAlloc(reinterpret_cast<void **>(&buf.p), kCkptChunk, cudaHostAllocDefault) != cudaSuccess) {
@@ -512,11 +541,16 @@ extern "C" int sim_state_load(sim_t *h, const char *path)
     }
     std::fclose(f);
     if (!ok) return fail(h, SIM_E_IO, "sim_state_load: %s is truncated", path);
-    if (h->store != SIM_STORE_HOST)  // the device state takes the file's layout
+    if (h->store != SIM_STORE_HOST) {  // the state takes the file's layout
         for (int q = 0; q < h->n; q++) {
             h->bit_of[q] = hd.bit_of[q];
             h->qubit_at[hd.bit_of[q]] = q;
         }
+    } else {
+        int perm[kMaxQubits];
+        std::copy(hd.bit_of, hd.bit_of + h->n, perm);
+        host_store_relabel(h, perm);  // sets checked above
+    }
     return SIM_OK;
 }
 
@@ -584,8 +618,8 @@ namespace sycsim {
 // One phase over a host store: every slice of the sliced set goes through a device slot (or is
 // computed in place, for a hybrid store's device regions with set A sliced), gets the plan's
 // blocks (p may be NULL when fill is given) and is written back.  fill, when given, makes each
-// slice instead of copying it in: (*fill)(dst, v) enqueues slice v of set A into dst on the
-// handle's stream, and the store is written without being read.
+// slice instead of copying it in: (*fill)(dst, v) enqueues slice v of the sliced set into dst on
+// the handle's stream, in the slot's layout, and the store is written without being read.
 int run_phase(sim_t *h, int set, const sim_plan_t *p, const std::function<int(float2 *, uint64_t)> *fill)
 {
     const int nl = h->n - h->s;
@@ -710,11 +744,12 @@ int run_phase(sim_t *h, int set, const sim_plan_t *p, const std::function<int(fl
 
 }  // namespace sycsim
 
-extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision,
+extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t *s, int precision, int set,
                                   const sim_plan_t *p)
 {
     if (!out || !t1 || !t2 || !s) return fail(out, SIM_E_INVAL, "sim_contract_phase: NULL argument");
     if (out->store != SIM_STORE_HOST) {  // a resident state: the contraction, then the blocks
+        if (set < 0 || set > 1) return fail(out, SIM_E_INVAL, "sim_contract_phase: set must be 0 (A) or 1 (B)");
         int rc = sim_contract(out, t1, t2, s, precision);
         if (rc == SIM_OK && p) rc = sim_apply_plan(out, p);
         return rc;
@@ -725,12 +760,13 @@ extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_sp
     if (precision != SIM_FP32 && precision != SIM_FP16X3 && precision != SIM_FP16X3_TMEM && precision != SIM_BF16X3)
         return fail(out, SIM_E_INVAL, "sim_contract_phase: precision %d is not SIM_FP32, SIM_FP16X3, "
                                       "SIM_FP16X3_TMEM or SIM_BF16X3", precision);
+    if (set < 0 || set > 1) return fail(out, SIM_E_INVAL, "sim_contract_phase: set must be 0 (A) or 1 (B)");
     if (p && p->n != out->n) return fail(out, SIM_E_INVAL, "sim_contract_phase: plan for another n");
     if (p)
         for (const PlanBlock &b : p->blocks)
             for (int q : b.qubits)
-                if (out->slice_phys[0][q] < 0)
-                    return fail(out, SIM_E_NONLOCAL, "sim_contract_phase: the plan acts on qubit %d of set A", q);
+                if (out->slice_phys[set][q] < 0)
+                    return fail(out, SIM_E_NONLOCAL, "sim_contract_phase: the plan acts on qubit %d of the sliced set", q);
     const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
     for (sim_t *h : {t1, t2})
         if (h->store != SIM_STORE_DEVICE || h->s != 0 || !h->d_state)
@@ -741,20 +777,23 @@ extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_sp
         return fail(out, SIM_E_INVAL, "sim_contract_phase: qubit counts (%d, %d, %d) do not fit the split (%d, %d, %d)",
                     out->n, t1->n, t2->n, s->n, n1 + e_bits, n2 + e_bits);
     SIM_DEVICE_SCOPE(out, out->device);
-    // set A selects the slice: its qubits on each side sit on that tensor's top side bits (the
-    // store's layout puts set A highest, and contract_layout orders side qubits by it); bit i of a
-    // slice's value is set A's i-th qubit, bit r of a side's fixed value its r-th set-A qubit
+    // the sliced set selects the slice: the slice is written in store_fill_layout's layout, where
+    // that set sits highest, so contract_layout puts its qubits on each tensor's top side bits; bit
+    // i of a slice's value is the set's i-th qubit, bit r of a side's fixed value its r-th qubit of
+    // the set
+    int olay[kMaxQubits];
+    store_fill_layout(out, set, olay);
     int top[2] = {0, 0}, side_of[8] = {}, rank_of[8] = {};
     for (int i = 0; i < out->s; i++) {
-        side_of[i] = s->side[out->set[0][i]];
+        side_of[i] = s->side[out->set[set][i]];
         rank_of[i] = top[side_of[i]]++;
     }
     sim_t *tens[2] = {t1, t2};
     for (int t = 0; t < 2; ++t) {
         sim_t *h = tens[t];
-        if (!contract_ready(s, out->bit_of, t, h->bit_of, top[t])) {
+        if (!contract_ready(s, olay, t, h->bit_of, top[t])) {
             int perm[kMaxQubits];
-            contract_layout(s, out->bit_of, t, perm, nullptr);
+            contract_layout(s, olay, t, perm, nullptr);
             const int rc = sim_permute(h, perm);
             if (rc != SIM_OK)
                 return fail(out, rc, "sim_contract_phase: permuting tensor %d: %s", t + 1, h->err.c_str());
@@ -773,8 +812,8 @@ extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_sp
         return finish(fail(out, SIM_E_CUDA, "sim_contract_phase: stream ordering failed"));
     const int *tbits[2] = {t1->bit_of, t2->bit_of};
     ContractJob job;
-    if (contract_job_prepare(out, s, t1->d_state, t2->d_state, tbits, out->bit_of, precision, top, nullptr,
-                             out->stream, &job) != 0)
+    if (contract_job_prepare(out, s, t1->d_state, t2->d_state, tbits, olay, precision, top, nullptr, out->stream,
+                             &job) != 0)
         return finish(fail(out, SIM_E_CUDA, "sim_contract_phase: operand images: %s",
                            cudaGetErrorString(cudaGetLastError())));
     const std::function<int(float2 *, uint64_t)> fill = [&](float2 *dst, uint64_t v) {
@@ -784,7 +823,7 @@ extern "C" int sim_contract_phase(sim_t *out, sim_t *t1, sim_t *t2, const sim_sp
             return fail(out, SIM_E_CUDA, "sim_contract_phase: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return (int)SIM_OK;
     };
-    const int rc = run_phase(out, 0, p, &fill);
+    const int rc = run_phase(out, set, p, &fill);
     // the tensors stay untouched until the last slice has been contracted
     if (cudaEventRecord(ev[2], out->stream) != cudaSuccess || cudaStreamWaitEvent(t1->stream, ev[2], 0) != cudaSuccess ||
         cudaStreamWaitEvent(t2->stream, ev[2], 0) != cudaSuccess)

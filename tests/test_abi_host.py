@@ -425,3 +425,25 @@ def test_split_choice_on_the_30_qubit_workload(pkg):
         pkg.sim_split_destroy(s)
     L = pkg.lib()
     assert L.sim_split_choose(1, 0, None, 5, 0, None, None) == pkg.SIM_E_INVAL
+
+
+@pytest.mark.parametrize("name,s,kmax", [("syc34_5x7m1_d16", 3, 6), ("syc35_5x7_d16", 4, 6)])
+def test_phases_layout_keeps_sliced_sets_and_lowers_estimate(pkg, name, s, kmax):
+    # the host-store order of the qubits outside the sliced sets: a bijection with set B on bits
+    # n-2s .. n-s-1 and set A on n-s .. n-1 in set order, never worse than the ascending order,
+    # and the same on every call (seeded)
+    circ = si.workload_circuit(name, seed=0)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    a, b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=kmax)
+    ph = pkg.sim_phases_create(n, gates, s, a, b, kmax=kmax, precision=pkg.SIM_FP16X3_TMEM)
+    try:
+        perm, est, est_asc = pkg.sim_phases_layout(ph, n)
+        again = pkg.sim_phases_layout(ph, n)
+    finally:
+        pkg.sim_phases_destroy(ph)
+    assert sorted(perm) == list(range(n))
+    assert [perm[q] for q in b] == list(range(n - 2 * s, n - s))
+    assert [perm[q] for q in a] == list(range(n - s, n))
+    assert est <= est_asc + 1e-9 and est < est_asc  # these circuits have blocks with low targets
+    assert again == (perm, est, est_asc)

@@ -1,12 +1,13 @@
 """GPU: the contraction straight into a sliced host store (Sect. 4: tensors 1 and 2 are contracted
 slice by slice into the secondary-storage state of subcircuit 3).
 
-sim_contract_phase and sim_front_run_phase fill every slice of set A from the two tensors (in a
-device slot, or in place for a hybrid store's device regions), optionally run a phase's blocks on
-it, and write it once.  Every amplitude, read back in logical order, is compared with the
-oracle's plain simulation of the same gates: set A's qubits on both sides, on one side only (the
-side left too narrow for the tensor-core kernel takes the FP32 one), 2 and 3 sliced bits, a hybrid
-store, FP32 and 3xFP16 on tcgen05, with and without the fused phase, and a set-B phase after it.
+sim_contract_phase and sim_front_run_phase fill every slice of the sliced set (A, or B) from the
+two tensors (in a device slot, or in place for a hybrid store's device regions), optionally run a
+phase's blocks on it, and write it once.  Every amplitude, read back in logical order, is compared
+with the oracle's plain simulation of the same gates: the sliced set's qubits on both sides, on one
+side only (the side left too narrow for the tensor-core kernel takes the FP32 one), 2 and 3 sliced
+bits, slices of set A and of set B, a hybrid store, FP32 and 3xFP16 on tcgen05, with and without
+the fused phase, the other phases after it, and a store laid out by sim_phases_layout.
 """
 import numpy as np
 import pytest
@@ -69,14 +70,16 @@ def err2(got, want):
 GRID, CYCLES, CUT = (4, 5), 4, 2  # 20 qubits; side 0 = columns 0-1 (8 qubits), side 1 = 12 qubits
 
 
-@pytest.mark.parametrize("set_a,set_b,regions,prec", [
-    ([1, 13], [8, 12], 0, "tmem"),     # one set-A qubit per side, tcgen05 (7 + 11 free side bits)
-    ([1, 13], [8, 12], 0, "fp32"),     # the FP32 kernel on strided sub-ranges
-    ([13, 18], [2, 7], 2, "tmem"),     # both on side 1; hybrid store: 2 of 4 regions in place
-    ([0, 6], [13, 18], 0, "tmem"),     # both on side 0: 6 free bits there, the FP32 kernel
-    ([1, 13, 19], [7, 8, 12], 3, "tmem"),  # 3 sliced bits, 8 slices, 3 in device memory
+@pytest.mark.parametrize("set_a,set_b,regions,prec,fill", [
+    ([1, 13], [8, 12], 0, "tmem", 0),     # one set-A qubit per side, tcgen05 (7 + 11 free side bits)
+    ([1, 13], [8, 12], 0, "fp32", 0),     # the FP32 kernel on strided sub-ranges
+    ([13, 18], [2, 7], 2, "tmem", 0),     # both on side 1; hybrid store: 2 of 4 regions in place
+    ([0, 6], [13, 18], 0, "tmem", 0),     # both on side 0: 6 free bits there, the FP32 kernel
+    ([1, 13, 19], [7, 8, 12], 3, "tmem", 0),  # 3 sliced bits, 8 slices, 3 in device memory
+    ([1, 13], [8, 12], 0, "tmem", 1),     # slices of set B: each slot scattered as files
+    ([13, 18], [2, 7], 2, "fp32", 1),     # set B's qubits both on side 1, hybrid store
 ])
-def test_contraction_into_store_matches_oracle(pkg, oracle_mod, set_a, set_b, regions, prec):
+def test_contraction_into_store_matches_oracle(pkg, oracle_mod, set_a, set_b, regions, prec, fill):
     grid = si.Grid(*GRID)
     circ = si.sycamore_circuit(grid, CYCLES + 2, seed=31)
     n = circ.n_qubits
@@ -88,7 +91,7 @@ def test_contraction_into_store_matches_oracle(pkg, oracle_mod, set_a, set_b, re
     out = pkg.sim_create(n, len(set_a), store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=2,
                          store_device_regions=regions)
     try:
-        pkg.sim_contract_phase(out, t1, t2, s, precision)
+        pkg.sim_contract_phase(out, t1, t2, s, precision, fill)
         pkg.sim_sync(out)
         got = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
         norm, s2, _ = pkg.sim_reduce(out)
@@ -122,7 +125,7 @@ def test_fused_phase_then_set_b_phase_match_oracle(pkg, oracle_mod, regions):
     p2 = pkg.sim_plan_create(n, gates[ph2], kmax=5, precision=pkg.SIM_FP16X3_TMEM)
     try:
         n0 = pkg.sim_launch_count(out)
-        pkg.sim_front_run_phase(out, fr, p1)
+        pkg.sim_front_run_phase(out, fr, 0, p1)
         pkg.sim_run_phase(out, 1, p2)
         pkg.sim_sync(out)
         assert pkg.sim_launch_count(out) > n0
@@ -177,10 +180,10 @@ def test_plan_on_set_a_is_rejected_and_device_out_contracts(pkg, oracle_mod):
     p = pkg.sim_plan_create(n, rest, kmax=4, precision=pkg.SIM_FP16X3_TMEM)
     try:
         with pytest.raises(pkg.SimError) as e:
-            pkg.sim_contract_phase(store, t1, t2, s, pkg.SIM_FP16X3_TMEM, p)
+            pkg.sim_contract_phase(store, t1, t2, s, pkg.SIM_FP16X3_TMEM, 0, p)
         assert e.value.code == pkg.SIM_E_NONLOCAL
         # a device-resident out: the contraction, then the plan
-        pkg.sim_contract_phase(dev, t1, t2, s, pkg.SIM_FP16X3_TMEM, p)
+        pkg.sim_contract_phase(dev, t1, t2, s, pkg.SIM_FP16X3_TMEM, 0, p)
         got = pkg.sim_amplitudes(dev, dtype=pkg.SIM_C128)
     finally:
         for h in (store, dev, t1, t2):
@@ -188,3 +191,65 @@ def test_plan_on_set_a_is_rejected_and_device_out_contracts(pkg, oracle_mod):
         pkg.sim_plan_destroy(p)
         pkg.sim_split_destroy(s)
     assert err2(got, oracle_mod.run_circuit(circ, n_qubits=n)) <= TOL
+
+
+@pytest.mark.parametrize("regions", [0, 1])
+def test_chosen_store_layout_front_and_phases_match_oracle(pkg, oracle_mod, regions, tmp_path):
+    # the whole circuit: the front contracted into a store laid out by sim_phases_layout, fused
+    # with the first phase, the other phases after it; then a checkpoint of that store loaded into
+    # a fresh store in the ascending layout (it takes the file's order of the other qubits)
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, 12, seed=35)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    rest = gates[nf:]
+    prec = pkg.SIM_FP16X3_TMEM
+    a, b, _, _ = pkg.sim_phases_choose_sets(n, rest, 2, kmax=5)
+    ph = pkg.sim_phases_create(n, rest, 2, a, b, kmax=5, precision=prec)
+    perm, est, est_asc = pkg.sim_phases_layout(ph, n)
+    assert est <= est_asc
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    out = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=2, store_device_regions=regions)
+    fresh = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=2)
+    fr = pkg.sim_front_create(out, s, kmax=5, precision=prec)
+    path = str(tmp_path / "store.ckpt")
+    try:
+        pkg.sim_set_layout(out, perm)
+        assert [int(x) for x in pkg.sim_info(out)[2]] == perm
+        n_phases, _ = pkg.sim_phases_info(ph)
+        set0, p0 = pkg.sim_phases_get(ph, 0)  # whichever set the first phase slices
+        pkg.sim_front_run_phase(out, fr, set0, p0)
+        for i in range(1, n_phases):
+            pkg.sim_run_phase(out, *pkg.sim_phases_get(ph, i))
+        pkg.sim_sync(out)
+        got = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+        pkg.sim_state_save(out, path)
+        pkg.sim_state_load(fresh, path)
+        assert [int(x) for x in pkg.sim_info(fresh)[2]] == perm
+        loaded = pkg.sim_amplitudes(fresh, dtype=pkg.SIM_C128)
+    finally:
+        pkg.sim_front_destroy(fr)
+        pkg.sim_destroy(out)
+        pkg.sim_destroy(fresh)
+        pkg.sim_split_destroy(s)
+        pkg.sim_phases_destroy(ph)
+    assert err2(got, oracle_mod.run_circuit(circ)) <= TOL
+    assert np.array_equal(got, loaded)
+
+
+def test_store_layout_must_keep_sliced_sets(pkg):
+    n = 20
+    out = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=[1, 13], set_b=[8, 12], slots=2)
+    try:
+        bits = [int(x) for x in pkg.sim_info(out)[2]]
+        moved = list(bits)
+        moved[1], moved[0] = bits[0], bits[1]  # qubit 1 (set A) trades bits with qubit 0
+        with pytest.raises(pkg.SimError):
+            pkg.sim_set_layout(out, moved)
+        swapped = list(bits)
+        swapped[0], swapped[2] = bits[2], bits[0]  # two qubits outside both sets: allowed
+        pkg.sim_set_layout(out, swapped)
+        assert [int(x) for x in pkg.sim_info(out)[2]] == swapped
+    finally:
+        pkg.sim_destroy(out)
