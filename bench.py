@@ -84,7 +84,7 @@ def parse():
                          "runs as two tensors and their contraction; 0 = plain fused blocks only")
     ap.add_argument("--no-layout", action="store_true",
                     help="keep the identity qubit layout instead of the one sim_plan_layout chooses")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi samples of the timed region in this file "

@@ -13,6 +13,9 @@
   goes through the same sliced machinery and is compared with the oracle; the measured error of
   each arithmetic mode is printed.
 * Small sliced-phase case against the oracle, and the layout moves it makes.
+* 34 qubits (5x7 minus one corner; a 128 GiB host store): the contraction into the store fused
+  with the first phase, in the layout sim_phases_layout chose, against every gate in phases, on
+  2^20 sampled amplitudes, with both runs' norm and Porter-Thomas sum (no oracle fits).
 """
 import numpy as np
 import pytest
@@ -159,3 +162,65 @@ def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
         err = chunked_err(out, want)
         print(f"28q sub-lattice {name} (kmax {kmax}): ||psi - psi_oracle||_2 = {err:.3e}")
         assert err <= bounds[name], (name, err)
+
+
+def run_store(pkg, circ, s, kmax, front_pairs, ranges):
+    """A host-store run of the whole circuit: with front_pairs, the circuit's first gates as two
+    tensors contracted slice by slice into a store laid out by sim_phases_layout, fused with the
+    first phase, then the other phases; without, every gate in phases from |0..0>.  Returns the
+    amplitudes at the given logical ranges (complex128) and the reduction."""
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    prec = pkg.SIM_FP16X3_TMEM
+    split, nf = None, 0
+    if front_pairs:
+        side, nf = pkg.sim_split_choose(n, gates, front_pairs)
+        split = pkg.sim_split_create(n, gates[:nf], side)
+    rest = gates[nf:]
+    a, b, _, _ = pkg.sim_phases_choose_sets(n, rest, s, kmax=kmax)
+    ph = pkg.sim_phases_create(n, rest, s, a, b, kmax=kmax, precision=prec)
+    nph = pkg.sim_phases_info(ph)[0]
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=3)
+    fr = None
+    try:
+        if split is not None:
+            perm, _, _ = pkg.sim_phases_layout(ph, n)
+            pkg.sim_set_layout(h, perm)
+            fr = pkg.sim_front_create(h, split, kmax=kmax, precision=prec)
+            pkg.sim_front_run_phase(h, fr, *pkg.sim_phases_get(ph, 0))
+            for i in range(1, nph):
+                pkg.sim_run_phase(h, *pkg.sim_phases_get(ph, i))
+        else:
+            pkg.sim_reset(h)
+            pkg.sim_run_phases(h, ph)
+        pkg.sim_sync(h)
+        samples = np.concatenate([pkg.sim_amplitudes(h, f, c, dtype=pkg.SIM_C128) for f, c in ranges])
+        red = pkg.sim_reduce(h)
+    finally:
+        if fr is not None:
+            pkg.sim_front_destroy(fr)
+        pkg.sim_destroy(h)
+        pkg.sim_phases_destroy(ph)
+        if split is not None:
+            pkg.sim_split_destroy(split)
+    return samples, red, nph
+
+
+def test_34q_store_front_agrees_with_plain_phases(pkg):
+    # 34 qubits (128 GiB host store): no oracle fits, so the two paths check each other on 2^20
+    # sampled amplitudes -- the contraction into the store (relabelled, fused first phase, 3
+    # phases after the front) against every gate in phases (4 phases, ascending store) -- and
+    # each run's norm and Porter-Thomas sum
+    circ = si.workload_circuit("syc34_5x7m1_d16", seed=0)
+    n = circ.n_qubits
+    rng = np.random.default_rng(7)
+    ranges = [(int(f) * 4096, 1 << 16) for f in rng.integers(0, (1 << n) // 4096 - 16, 16)]
+    got, (norm, s2, _), nph = run_store(pkg, circ, 3, 6, 4, ranges)
+    ref, (norm0, s20, _), nph0 = run_store(pkg, circ, 3, 6, 0, ranges)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"34q store: front {nph} phases, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}; plain {nph0} phases, "
+          f"norm {norm0:.7f}; sampled relative difference {rel:.2e}")
+    assert nph < nph0
+    for nn, ss in ((norm, s2), (norm0, s20)):
+        assert abs(nn - 1) < 2e-5 and abs(ss - 2) < 0.05
+    assert rel <= 2 * TOL_FP32
