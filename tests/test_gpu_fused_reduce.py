@@ -174,3 +174,10 @@ def test_reduce_async_rejects_bad_output(pkg):
         assert pkg.lib().sim_reduce_async(None, None) == pkg.SIM_E_INVAL
     finally:
         pkg.sim_destroy(h)
+    store = pkg.sim_create(12, 1, store=pkg.SIM_STORE_HOST, set_a=[0], set_b=[11], slots=2)
+    try:
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_reduce_async(store, pkg.pinned_array(3, dtype=np.float64))
+        assert e.value.code == pkg.SIM_E_UNSUPPORTED
+    finally:
+        pkg.sim_destroy(store)
