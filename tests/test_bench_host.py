@@ -1,4 +1,4 @@
-"""Host-side pieces of bench.py, no GPU: the clock record's verdict, the peak lookup and the
+"""Host-side pieces of bench.py, no GPU: whether a clock record is accepted, the peak lookup and the
 reference arm's JSON line (the oracle on a small workload)."""
 import json
 import types
