@@ -253,3 +253,30 @@ def test_store_layout_must_keep_sliced_sets(pkg):
         assert [int(x) for x in pkg.sim_info(out)[2]] == swapped
     finally:
         pkg.sim_destroy(out)
+
+
+@pytest.mark.parametrize("side0,set_a,set_b,prec,tol", [
+    ([0, 1], [0, 1], [18, 19], "fp32", TOL),          # side 0 entirely sliced: no free x bit
+    (None, [0, 1, 2, 3, 10, 11, 12, 13], [5, 6, 7, 8, 15, 16, 17, 18], "tmem", TOL),  # 8 sliced bits
+    (None, [1, 13], [8, 12], "bf16x3", 1e-4),          # BF16x3 into a store (its stated bound)
+])
+def test_store_contraction_edges(pkg, oracle_mod, side0, set_a, set_b, prec, tol):
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, CYCLES, seed=36)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    side = column_sides(grid, CUT) if side0 is None else [0 if q in side0 else 1 for q in range(n)]
+    precision = {"fp32": pkg.SIM_FP32, "tmem": pkg.SIM_FP16X3_TMEM, "bf16x3": pkg.SIM_BF16X3}[prec]
+    s = pkg.sim_split_create(n, gates[:nf], side)
+    t1, t2 = tensor_handles(pkg, s, 4, pkg.SIM_FP32 if prec == "fp32" else precision)
+    out = pkg.sim_create(n, len(set_a), store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=2)
+    try:
+        pkg.sim_contract_phase(out, t1, t2, s, precision)
+        pkg.sim_sync(out)
+        got = pkg.sim_amplitudes(out, dtype=pkg.SIM_C128)
+    finally:
+        for h in (out, t1, t2):
+            pkg.sim_destroy(h)
+        pkg.sim_split_destroy(s)
+    assert err2(got, oracle_mod.run_circuit(circ.gates[:nf], n_qubits=n)) <= tol
