@@ -59,7 +59,7 @@ UNIT = "amp-updates/s"
 # store): store kind, sliced bits, block width, store regions kept in HBM, and how the two
 # sliced sets are picked (the lattice ends, or sim_phases_choose_sets).
 LARGE_CASES = {
-    "syc33_6x6m3_d20": dict(store="device", slice_bits=3, kmax=6, device_regions=0, sets="ends"),
+    "syc33_6x6m3_d20": dict(store="device", slice_bits=3, kmax=6, device_regions=0, sets="ends", front_pairs=3),
     "syc34_5x7m1_d16": dict(store="host", slice_bits=3, kmax=6, device_regions=0, sets="chosen", front_pairs=4),
     "syc35_5x7_d16": dict(store="host", slice_bits=4, kmax=6, device_regions=8, sets="chosen", front_pairs=4),
 }
@@ -942,7 +942,7 @@ def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0, f
     # phase's blocks; the sliced sets and phases are chosen for the remaining gates
     split, n_front, front_info = None, 0, None
     pairs_wanted = cfg.get("front_pairs", 0) if front_pairs < 0 else front_pairs
-    if host and pairs_wanted > 0:
+    if pairs_wanted > 0:
         side, n_front = pkg.sim_split_choose(n, gates, pairs_wanted)
         split = pkg.sim_split_create(n, gates[:n_front], side)
         n_side, n_wires, pairs, _ = pkg.sim_split_info(split)
@@ -955,35 +955,44 @@ def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0, f
         set_a, set_b = list(range(s)), list(range(n - s, n))
     ph = pkg.sim_phases_create(n, rest, s, set_a, set_b, kmax=kmax, precision=prec)
     n_phases, n_blocks = pkg.sim_phases_info(ph)
-    front, layout_info = None, None
+    front, layout_info, perm = None, None, None
     if host:
         h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=set_a, set_b=set_b, slots=3,
                            store_device_regions=cfg["device_regions"], device=device)
-        # the order of the qubits outside the sliced sets (sim_phases_layout): fewer blocks with
-        # two targets below bit 4 in the slots; a relabelling, before anything is written
-        perm, est, est_asc = pkg.sim_phases_layout(ph, n)
-        pkg.sim_set_layout(h, perm)
-        layout_info = {"chosen_by": "sim_phases_layout", "estimate_ms": est, "ascending_estimate_ms": est_asc}
-        if split is not None:
-            front = pkg.sim_front_create(h, split, kmax=kmax, precision=prec)
     else:
         h = pkg.sim_create(n, s, device=device)
-        pkg.sim_reset(h)
-        pkg.sim_run_phases(h, ph)  # warm-up
-        pkg.sim_sync(h)
-    fused = front is not None
+    if host or split is not None:
+        # the order of the qubits outside the sliced sets (sim_phases_layout): fewer blocks with
+        # two targets below bit 4, and with a front side-0 qubits on bits 0-4 (the contraction's
+        # stores stay whole); resident, the first phase's sliced set already on top.  A
+        # relabelling, before anything is written
+        perm, est, est_asc = pkg.sim_phases_layout(ph, n, split, resident=not host)
+        pkg.sim_set_layout(h, perm)
+        layout_info = {"chosen_by": "sim_phases_layout", "estimate_ms": est, "starting_estimate_ms": est_asc}
+        if split is not None:
+            front = pkg.sim_front_create(h, split, kmax=kmax, precision=prec)
+    fused = host and front is not None
 
     def run():
         if front is None:
             pkg.sim_run_phases(h, ph)
-            return
-        # the contraction fills each slice of the first phase's sliced set, the phase's blocks
-        # run on it, and it is written once
-        pkg.sim_front_run_phase(h, front, *pkg.sim_phases_get(ph, 0))
-        for i in range(1, n_phases):
-            set_i, plan_i = pkg.sim_phases_get(ph, i)
-            pkg.sim_run_phase(h, set_i, plan_i)
+        elif fused:
+            # the contraction fills each slice of the first phase's sliced set, the phase's
+            # blocks run on it, and it is written once
+            pkg.sim_front_run_phase(h, front, *pkg.sim_phases_get(ph, 0))
+            for i in range(1, n_phases):
+                set_i, plan_i = pkg.sim_phases_get(ph, i)
+                pkg.sim_run_phase(h, set_i, plan_i)
+        else:  # resident: the contraction writes the whole state, the phases permute as they go
+            pkg.sim_set_layout(h, perm)
+            pkg.sim_front_run(h, front)
+            pkg.sim_run_phases(h, ph)
 
+    if not host:  # warm-up
+        if front is None:
+            pkg.sim_reset(h)
+        run()
+        pkg.sim_sync(h)
     if front is None:
         pkg.sim_reset(h)
     pkg.sim_sync(h)

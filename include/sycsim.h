@@ -335,10 +335,11 @@ int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, 
 /* Relabel the physical bits without moving any amplitude (perm as for sim_permute): the logical
  * state changes, so this belongs before sim_reset, sim_front_run or sim_contract, which overwrite
  * every amplitude -- the way to start a plan in the layout sim_plan_layout chose without a
- * permutation pass.  Device-store handles that are not sliced, and host stores as long as perm
- * keeps both sliced sets on the bits the store gives them (only the other qubits' order changes:
- * the host layout and the slots' [others | B] / [others | A] layouts alike; sim_phases_layout
- * chooses it); SIM_E_INVAL otherwise. */
+ * permutation pass.  Device-resident handles (with slice_bits > 0 the qubits then on the top bits
+ * are the sliced ones), and host stores as long as perm keeps both sliced sets on the bits the
+ * store gives them (only the other qubits' order changes: the host layout and the slots'
+ * [others | B] / [others | A] layouts alike; sim_phases_layout chooses it); SIM_E_INVAL
+ * otherwise. */
 int sim_set_layout(sim_t *h, const int *perm);
 
 typedef struct sim_graph_s sim_graph_t;
@@ -421,15 +422,20 @@ int sim_phases_get(const sim_phases_t *ph, int i, int *set, const sim_plan_t **p
  * Asynchronous. */
 int sim_run_phases(sim_t *h, const sim_phases_t *ph);
 
-/* Where the qubits outside the two sliced sets should sit in a host store that runs the phases
- * ph (not in the paper; as sim_plan_layout, the fused kernels' speed depends on which qubits sit
- * on the low physical bits).  perm[q] for every qubit: set B on bits n-2s .. n-s-1 and set A on
- * n-s .. n-1 in set order (where a host store keeps them), the others on 0 .. n-2s-1 in the
- * order that minimises the per-pass estimates summed over every phase's blocks (local search
- * from the ascending order and from seeded random orders).  est_ms (may be NULL): {chosen,
- * ascending}.  Apply it with sim_set_layout before the state is written (sim_reset,
- * sim_front_run, sim_contract_phase).  Host only. */
-int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms);
+/* Where the qubits outside the two sliced sets should sit for the phases ph (not in the paper;
+ * as sim_plan_layout, the fused kernels' speed depends on which qubits sit on the low physical
+ * bits).  perm[q] for every qubit: the others on 0 .. n-2s-1 in the order that minimises the
+ * per-pass estimates summed over every phase's blocks (local search from the ascending order and
+ * from seeded random orders), the two sets above them in set order: for a host store
+ * (resident = 0) set B on n-2s .. n-s-1 and set A on n-s .. n-1, where the store keeps them; for
+ * a device-resident handle with slice_bits = s (resident = 1) the first phase's sliced set on
+ * top, so that sim_run_phases needs no move before it, and the other set below.  front (may be
+ * NULL): a split whose contraction writes the state first (sim_front_run, sim_contract_phase);
+ * bits 0 .. 4 then hold side-0 qubits (as far as there are five outside the sets), so that the
+ * contraction's stores stay whole.  est_ms (may be NULL): {chosen, starting order}.  Apply it
+ * with sim_set_layout before the state is written (sim_reset, sim_front_run,
+ * sim_contract_phase).  Host only. */
+int sim_phases_layout(const sim_phases_t *ph, const sim_split_t *front, int resident, int *perm, double *est_ms);
 
 /* ---- contraction deferral: two subcircuits joined by entanglement indices -----
  * Sect. 2 (contraction deferral: subcircuits simulated separately, each with the Schroedinger

@@ -162,7 +162,8 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "sim_front_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sim_front_run_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
-    "sim_phases_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_phases_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     "sim_contract_phase": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "sim_front_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -630,11 +631,13 @@ def sim_phases_info(ph):
     return n.value, t.value
 
 
-def sim_phases_layout(ph, n_qubits: int):
-    """(perm, estimate, ascending estimate): the host-store order of the qubits outside the sliced sets."""
+def sim_phases_layout(ph, n_qubits: int, front=None, resident: bool = False):
+    """(perm, estimate, starting estimate): the order of the qubits outside the sliced sets for the
+    phases ph -- a host store's (resident False) or a device-resident sliced handle's (the first
+    phase's set on top); front: the split whose contraction writes the state first, or None."""
     perm = np.zeros(n_qubits, dtype=np.int32)
     est = np.zeros(2, dtype=np.float64)
-    _check(lib().sim_phases_layout(ph, _ptr(perm), _ptr(est)))
+    _check(lib().sim_phases_layout(ph, front, 1 if resident else 0, _ptr(perm), _ptr(est)))
     return [int(x) for x in perm], float(est[0]), float(est[1])
 
 

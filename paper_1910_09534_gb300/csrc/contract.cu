@@ -712,9 +712,10 @@ extern "C" int sim_contract(sim_t *out, sim_t *t1, sim_t *t2, const sim_split_t 
         return fail(out, SIM_E_INVAL,
                     "sim_contract: precision %d is not SIM_FP32, SIM_FP16X3, SIM_FP16X3_TMEM or SIM_BF16X3", precision);
     const int n1 = s->n_side[0], n2 = s->n_side[1], e_bits = 2 * s->n_pairs;
+    // out may be sliced: a resident state is one buffer, written whole in its layout
     for (sim_t *h : {out, t1, t2})
-        if (h->store != SIM_STORE_DEVICE || h->s != 0 || !h->d_state)
-            return fail(out, SIM_E_INVAL, "sim_contract: every handle must be device-resident and not sliced");
+        if (h->store != SIM_STORE_DEVICE || (h != out && h->s != 0) || !h->d_state)
+            return fail(out, SIM_E_INVAL, "sim_contract: every handle must be device-resident, the tensors not sliced");
     if (t1->device != out->device || t2->device != out->device)
         return fail(out, SIM_E_INVAL, "sim_contract: handles on different devices");
     if (out->n != s->n || t1->n != n1 + e_bits || t2->n != n2 + e_bits)

@@ -482,8 +482,6 @@ extern "C" int sim_set_layout(sim_t *h, const int *perm)
     if (!h) return fail(nullptr, SIM_E_INVAL, "sim_set_layout: NULL handle");
     state_written(h);
     if (!perm) return fail(h, SIM_E_INVAL, "sim_set_layout: NULL perm");
-    if (h->store == SIM_STORE_DEVICE && h->s != 0)
-        return fail(h, SIM_E_INVAL, "sim_set_layout: not for sliced device-resident handles");
     bool used[kMaxQubits] = {};
     for (int q = 0; q < h->n; q++) {
         if (perm[q] < 0 || perm[q] >= h->n || used[perm[q]])

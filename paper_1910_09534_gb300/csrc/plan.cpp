@@ -603,17 +603,37 @@ int sim_plan_layout_front(const sim_plan_t *p, const sim_split_t *s, int *perm, 
     return layout_search(p, low.data(), std::min(5, n_side0), perm, est_ms);
 }
 
-int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms)
+int sim_phases_layout(const sim_phases_t *ph, const sim_split_t *front, int resident, int *perm, double *est_ms)
 {
     if (!ph || !perm) return fail(nullptr, SIM_E_INVAL, "sim_phases_layout: NULL argument");
+    if (front && front->n != ph->n) return fail(nullptr, SIM_E_INVAL, "sim_phases_layout: split of another n");
     const int n = ph->n, s = ph->s, r = n - 2 * s;
+    // the two sets' bits: a host store keeps B on n-2s .. n-s-1 and A on top; a resident sliced
+    // state has the first phase's sliced set on top (no move before it) and the other below
+    const int first = ph->set_of.empty() ? 0 : ph->set_of[0];
+    const int *top = resident && first == 1 ? ph->set_b : ph->set_a;
+    const int *below = top == ph->set_a ? ph->set_b : ph->set_a;
     std::vector<char> sliced(n, 0);
     for (int i = 0; i < s; i++) sliced[ph->set_a[i]] = sliced[ph->set_b[i]] = 1;
-    std::vector<int> order;  // the others, position i -> qubit
-    for (int q = 0; q < n; q++)
-        if (!sliced[q]) order.push_back(q);
-    // a phase's slot: the others on 0 .. r-1, the set it does not slice on r .. r+s-1 (the sliced
-    // set's bits are never read: its blocks avoid it)
+    std::vector<int> order;  // the others, position i -> qubit; with a front, side-0 qubits first
+    for (int pass = 0; pass < 2; pass++)
+        for (int q = 0; q < n; q++)
+            if (!sliced[q] && (!front || (front->side[q] == 0) == (pass == 0)) && (front || pass == 0))
+                order.push_back(q);
+    // with a front, bits 0 .. low-1 keep side-0 qubits: the contraction's 32 lanes of a warp then
+    // write 32 consecutive amplitudes
+    int n_group0 = front ? 0 : r;
+    if (front)
+        for (int q = 0; q < n; q++) n_group0 += !sliced[q] && front->side[q] == 0;
+    const int low = front ? std::min(n_group0, 5) : 0;
+    auto allowed = [&](const std::vector<int> &ord) {
+        for (int i = 0; i < low; i++)
+            if (front->side[ord[i]] != 0) return false;
+        return true;
+    };
+    // a phase's layout: the others on 0 .. r-1, the set it does not slice on r .. r+s-1 (its
+    // sliced set's bits are never read: its blocks avoid it).  Host store: the slot's layout.
+    // Resident: the first phase's, as it runs; later phases move the sets, the others stay.
     auto total = [&](const std::vector<int> &ord) {
         int bit[kMaxQubits];
         for (int q = 0; q < n; q++) bit[q] = -1;
@@ -626,20 +646,25 @@ int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms)
         }
         return t;
     };
-    const double ascending = total(order);
+    std::vector<int> start0 = order;
+    if (!front) std::sort(start0.begin(), start0.end());
+    const double ascending = total(start0);
     double best = ascending;
-    std::vector<int> best_order = order;
+    std::vector<int> best_order = start0;
     std::mt19937 rng(12345);
     for (int start = 0; start < SYCSIM_LAYOUT_STARTS; start++) {
-        std::vector<int> ord = order;
-        if (start > 0) std::shuffle(ord.begin(), ord.end(), rng);
+        std::vector<int> ord = start0;
+        if (start > 0) {  // seeded shuffles: with a front within each group, else all
+            std::shuffle(ord.begin(), ord.begin() + n_group0, rng);
+            std::shuffle(ord.begin() + n_group0, ord.end(), rng);
+        }
         double cost = total(ord);
         for (bool improved = true; improved;) {  // pairwise exchanges while one lowers the estimate
             improved = false;
             for (int i = 0; i < r; i++)
                 for (int j = i + 1; j < r; j++) {
                     std::swap(ord[i], ord[j]);
-                    const double c = total(ord);
+                    const double c = allowed(ord) ? total(ord) : 1e300;
                     if (c < cost - 1e-9) {
                         cost = c;
                         improved = true;
@@ -655,8 +680,8 @@ int sim_phases_layout(const sim_phases_t *ph, int *perm, double *est_ms)
     }
     for (int i = 0; i < r; i++) perm[best_order[i]] = i;
     for (int i = 0; i < s; i++) {
-        perm[ph->set_b[i]] = r + i;
-        perm[ph->set_a[i]] = n - s + i;
+        perm[below[i]] = r + i;
+        perm[top[i]] = n - s + i;
     }
     if (est_ms) {
         est_ms[0] = best;

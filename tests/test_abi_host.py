@@ -437,13 +437,30 @@ def test_phases_layout_keeps_sliced_sets_and_lowers_estimate(pkg, name, s, kmax)
     gates = pkg.gates_array(circ)
     a, b, _, _ = pkg.sim_phases_choose_sets(n, gates, s, kmax=kmax)
     ph = pkg.sim_phases_create(n, gates, s, a, b, kmax=kmax, precision=pkg.SIM_FP16X3_TMEM)
+    side, nf = pkg.sim_split_choose(n, gates, 4)
+    sp = pkg.sim_split_create(n, gates[:nf], side)
     try:
         perm, est, est_asc = pkg.sim_phases_layout(ph, n)
         again = pkg.sim_phases_layout(ph, n)
+        pf, estf, _ = pkg.sim_phases_layout(ph, n, sp)
+        pr, _, _ = pkg.sim_phases_layout(ph, n, sp, resident=True)
+        first = pkg.sim_phases_get(ph, 0)[0]
     finally:
         pkg.sim_phases_destroy(ph)
-    assert sorted(perm) == list(range(n))
+        pkg.sim_split_destroy(sp)
+    for p_ in (perm, pf, pr):
+        assert sorted(p_) == list(range(n))
     assert [perm[q] for q in b] == list(range(n - 2 * s, n - s))
     assert [perm[q] for q in a] == list(range(n - s, n))
     assert est <= est_asc + 1e-9 and est < est_asc  # these circuits have blocks with low targets
     assert again == (perm, est, est_asc)
+    # with a front: the sets where a host store keeps them, side-0 qubits on bits 0-4
+    assert [pf[q] for q in a] == list(range(n - s, n))
+    low = sorted(range(n), key=lambda q: pf[q])[:5]
+    assert all(side[q] == 0 for q in low)
+    # resident: the first phase's sliced set on top, the other below, side-0 qubits low
+    top, below = (a, b) if first == 0 else (b, a)
+    assert [pr[q] for q in top] == list(range(n - s, n))
+    assert [pr[q] for q in below] == list(range(n - 2 * s, n - s))
+    assert all(side[q] == 0 for q in sorted(range(n), key=lambda q: pr[q])[:5])
+    assert estf < est_asc

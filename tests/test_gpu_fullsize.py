@@ -184,7 +184,7 @@ def run_store(pkg, circ, s, kmax, front_pairs, ranges):
     fr = None
     try:
         if split is not None:
-            perm, _, _ = pkg.sim_phases_layout(ph, n)
+            perm, _, _ = pkg.sim_phases_layout(ph, n, split)
             pkg.sim_set_layout(h, perm)
             fr = pkg.sim_front_create(h, split, kmax=kmax, precision=prec)
             pkg.sim_front_run_phase(h, fr, *pkg.sim_phases_get(ph, 0))

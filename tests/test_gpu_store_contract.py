@@ -207,9 +207,9 @@ def test_chosen_store_layout_front_and_phases_match_oracle(pkg, oracle_mod, regi
     prec = pkg.SIM_FP16X3_TMEM
     a, b, _, _ = pkg.sim_phases_choose_sets(n, rest, 2, kmax=5)
     ph = pkg.sim_phases_create(n, rest, 2, a, b, kmax=5, precision=prec)
-    perm, est, est_asc = pkg.sim_phases_layout(ph, n)
-    assert est <= est_asc
     s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    perm, est, est_asc = pkg.sim_phases_layout(ph, n, s)
+    assert est <= est_asc
     out = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=2, store_device_regions=regions)
     fresh = pkg.sim_create(n, 2, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=2)
     fr = pkg.sim_front_create(out, s, kmax=5, precision=prec)
@@ -280,3 +280,38 @@ def test_store_contraction_edges(pkg, oracle_mod, side0, set_a, set_b, prec, tol
             pkg.sim_destroy(h)
         pkg.sim_split_destroy(s)
     assert err2(got, oracle_mod.run_circuit(circ.gates[:nf], n_qubits=n)) <= tol
+
+
+def test_front_into_sliced_resident_state_then_phases(pkg, oracle_mod):
+    # a device-resident state with 2 sliced bits (Sect. 4 in HBM): the contraction writes the
+    # whole state in the layout sim_phases_layout chose (the first phase's sliced set already on
+    # top, so no move before it), then sim_run_phases runs the rest, against the oracle
+    grid = si.Grid(*GRID)
+    circ = si.sycamore_circuit(grid, 12, seed=37)
+    n = circ.n_qubits
+    gates = pkg.gates_array(circ)
+    nf = front_length(grid, CYCLES)
+    prec = pkg.SIM_FP16X3_TMEM
+    a, b = [0, 1], [18, 19]
+    ph = pkg.sim_phases_create(n, gates[nf:], 2, a, b, kmax=5, precision=prec)
+    s = pkg.sim_split_create(n, gates[:nf], column_sides(grid, CUT))
+    perm, _, _ = pkg.sim_phases_layout(ph, n, s, resident=True)
+    h = pkg.sim_create(n, 2)
+    fr = pkg.sim_front_create(h, s, kmax=5, precision=prec)
+    try:
+        n_phases, _ = pkg.sim_phases_info(ph)
+        for _ in range(2):  # twice: the layout is set again before each run
+            pkg.sim_set_layout(h, perm)
+            pkg.sim_profile_enable(h, True)
+            pkg.sim_front_run(h, fr)
+            pkg.sim_run_phases(h, ph)
+            perms = pkg.sim_profile_read(h, pkg.SIM_PROF_PERMUTE)[0]
+            pkg.sim_profile_enable(h, False)
+            got = pkg.sim_amplitudes(h, dtype=pkg.SIM_C128)
+            assert perms <= n_phases - 1  # no move before the first phase
+            assert err2(got, oracle_mod.run_circuit(circ)) <= TOL
+    finally:
+        pkg.sim_front_destroy(fr)
+        pkg.sim_destroy(h)
+        pkg.sim_split_destroy(s)
+        pkg.sim_phases_destroy(ph)
