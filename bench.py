@@ -365,7 +365,10 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
     if fp32:
         arith = ("fp32 on CUDA cores (k_max 5 up to 24 qubits, 4 above, in a chosen layout above 20 "
                  "qubits; circuits of <= 20 qubits packed one per CTA, k_max 5)")
-        front = "none (the contraction front runs in the tcgen05 modes only)"
+        front = ("circuits of >= 26 qubits (from 22 where the autotuner measured it faster) whose first "
+                 "2 crossings of the chosen bipartition leave >= 10% of the gates in front run them as "
+                 "two tensors and one FP32 contraction on CUDA cores; the one-at-a-time path runs every "
+                 "circuit plainly")
     else:
         arith = ("fp16x3_tmem (k_max 6 in a chosen layout above 20 qubits; circuits of <= 20 "
                  "qubits packed one per CTA in FP32, k_max 5)")
@@ -378,7 +381,7 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
             "one_at_a_time_p50_ms": statistics.quantiles(seq_done, n=100)[49],
             "one_at_a_time_p99_ms": statistics.quantiles(seq_done, n=100)[98],
             "arithmetic": arith, "server_front": front,
-            "autotune": {"by": "srv_autotune: k_max 4-6 (and the front or not, tcgen05 modes) measured per size "
+            "autotune": {"by": "srv_autotune: k_max 4-6 (and the front or not) measured per size "
                                "and depth class on one sample each, before the timed leg",
                          "seconds": t_tune, "choices": tuned}}
 
@@ -688,16 +691,21 @@ def run_ours(args):
         msp = e0.elapsed_time(e1)
         plain_path = {"value": float(amps) * circ.n_gates * args.steps / (msp / 1e3), "unit": UNIT,
                       "ms_per_step": msp / args.steps, "fused_blocks": nbp}
-    # the FP32-only path on the same state and timing method (blocks of <= 4 qubits)
+    # the FP32-only path on the same state and timing method (blocks of <= 4 qubits), its front of
+    # 2 bridging gates contracted in FP32 on CUDA cores (each bridging gate quadruples that cost)
     fp32_path = None
     if not args.no_fp32_path:
-        layout32, _ = choose_layout(gates, 4, pkg.SIM_FP32)
+        side32, nf32 = pkg.sim_split_choose(n, gates, 2)
+        split32 = pkg.sim_split_create(n, gates[:nf32], side32)
+        rest32 = gates[nf32:]
+        layout32, _ = choose_layout(rest32, 4, pkg.SIM_FP32, split32)
+        fr32 = pkg.sim_front_create(h, split32, kmax=4, precision=pkg.SIM_FP32)
 
         def step32():
-            plan = pkg.sim_plan_create(n, gates, kmax=4, precision=pkg.SIM_FP32)
+            plan = pkg.sim_plan_create(n, rest32, kmax=4, precision=pkg.SIM_FP32)
             if layout32 is not None:
                 pkg.sim_set_layout(h, layout32)
-            pkg.sim_reset(h)
+            pkg.sim_front_run(h, fr32)
             pkg.sim_apply_plan(h, plan)
             out = pkg.sim_reduce(h)
             nb = pkg.sim_plan_info(plan)[0]
@@ -714,11 +722,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms32 = e0.elapsed_time(e1)
         c32, a32_ms, a32_bytes = pkg.sim_profile_read(h, pkg.SIM_PROF_APPLY)
+        k32_n, k32_ms, _ = pkg.sim_profile_read(h, pkg.SIM_PROF_CONTRACT)
         pkg.sim_profile_enable(h, False)
+        pkg.sim_front_destroy(fr32)
+        pkg.sim_split_destroy(split32)
         peak32, _ = measured_peaks()
         ach32 = a32_bytes / (a32_ms / 1e3) / 1e9
         fp32_path = {"value": float(amps) * circ.n_gates * args.steps / (ms32 / 1e3), "unit": UNIT,
                      "ms_per_step": ms32 / args.steps, "kmax": 4, "fused_blocks": nb32,
+                     "front": {"gates": nf32, "bridging_gates": 2, "contraction": "FP32 CUDA cores",
+                               "contraction_ms": k32_ms / max(k32_n, 1)},
                      "norm": n32, "porter_thomas_2n_sum_p2": s32,
                      "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak32, "unit": "GB/s",
                                   "frac": ach32 / peak32, "launches": c32}}

@@ -600,11 +600,14 @@ typedef struct srv_opts {
                           * sim_plan_layout picks and are permuted back before a readout */
     int precision;       /* circuits above small_n: any SIM_FP32 .. SIM_BF16X3 */
     uint64_t hbm_budget; /* device bytes for states (0 = 80% of free memory at creation) */
-    int front_pairs;     /* contraction deferral for circuits of >= 26 qubits in SIM_FP16X3_TMEM or SIM_BF16X3:
-                          * the gates up to the (front_pairs + 1)-th across the bipartition
-                          * sim_split_choose picks run as two tensors and one tensor-core
-                          * contraction when they are >= 30% of the circuit (0 = 5, < 0 = off);
-                          * the tensors and the contraction's scratch count in the footprint */
+    int front_pairs;     /* contraction deferral for circuits of >= 26 qubits: the gates up to the
+                          * (front_pairs + 1)-th across the bipartition sim_split_choose picks run
+                          * as two tensors and one contraction -- in SIM_FP16X3_TMEM / SIM_BF16X3 on
+                          * the tensor cores when they are >= 30% of the circuit (0 = 5); in
+                          * SIM_FP32 on CUDA cores with at most 2 bridging gates when they are
+                          * >= 10% (its cost grows 4x per bridging gate); < 0 = off; none in the
+                          * other modes.  The tensors and the contraction's scratch count in the
+                          * footprint */
     int max_large;       /* most circuits of >= 27 qubits running at once (0: 1 in SIM_FP32, 2 in the
                           * tensor-core modes -- each is HBM-bound, and sharing the bandwidth among
                           * more of them only delays them all; < 0: unlimited) */
@@ -642,8 +645,8 @@ int srv_stats(srv_t *s, srv_stats_t *out);
 
 /* Autotuner of the server (not in the paper): for each sample circuit above small_n, measures on a
  * scratch state of its size every candidate the server could run it with -- block width k_max 4,
- * 5 and 6, and in SIM_FP16X3_TMEM / SIM_BF16X3 from 22 qubits also with and without the
- * contraction-deferral front (unless front_pairs < 0) -- planned as srv_submit plans (the layout
+ * 5 and 6, and in SIM_FP16X3_TMEM / SIM_BF16X3 / SIM_FP32 from 22 qubits also with and without
+ * the contraction-deferral front (unless front_pairs < 0) -- planned as srv_submit plans (the layout
  * sim_plan_layout picks), each run twice from the start state, the second timed with CUDA events;
  * the fastest is cached for the sample's (n, depth class) and used by every later srv_submit of a
  * circuit of that size and class (depth class: gates per qubit < 18, < 24, or more; an explicit

@@ -306,6 +306,8 @@ struct Batch {
 constexpr int kMaxBypass = 64;
 constexpr int kFrontMinQubits = 26;      // smaller states: the passes a front saves are too short
 constexpr double kFrontMinShare = 0.3;   // a front with fewer of the gates is not worth a contraction
+constexpr int kFp32FrontPairs = 2;       // FP32 fronts: their contraction (CUDA cores) grows 4x a pair
+constexpr double kFp32FrontMinShare = 0.1;
 constexpr int kResultRing = 1 << 16;
 constexpr int kGraphMaxQubits = 24;  // graph entries hold their own state: 8 * 2^24 bytes at most
 constexpr int kGraphMaxEntries = 8;
@@ -1013,6 +1015,21 @@ static int make_graph_entry(srv_t *s, uint64_t key, int n, int n_gates, const si
                             const sim_plan_opts &po);
 static int enqueue_request(srv_t *s, const std::shared_ptr<Req> &r, uint64_t *ticket);
 
+// Contraction deferral per arithmetic: the tensor-core modes contract on tcgen05 (o.front_pairs
+// bridging gates, 5 by default); FP32 contracts on CUDA cores, whose cost grows 4x per bridging
+// gate while an FP32 pass it saves costs 2.8-4.3 ms per 2^30 amplitudes, so at most 2 bridging
+// gates and a lower share of the circuit (measured on 28-30 qubits: 13-22 % less time); the other
+// modes run no front.  0: none.
+static int front_pairs_for(const srv_t *s, int precision)
+{
+    if (s->o.front_pairs < 0) return 0;
+    if (tmem_mode(precision)) return s->o.front_pairs ? s->o.front_pairs : 5;
+    if (precision == SIM_FP32) return s->o.front_pairs ? std::min(s->o.front_pairs, kFp32FrontPairs) : kFp32FrontPairs;
+    return 0;
+}
+
+static double front_min_share(int precision) { return precision == SIM_FP32 ? kFp32FrontMinShare : kFrontMinShare; }
+
 int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void *out_amps, uint64_t *ticket)
 {
     if (!s || !ticket) return srv_fail(s, SIM_E_INVAL, "srv_submit: NULL argument");
@@ -1045,15 +1062,16 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     po.kmax = s->o.kmax ? s->o.kmax : (tuned_kmax ? tuned_kmax : auto_kmax(n_qubits, r->packed, r->precision));
     if (r->packed) po.kmax = std::min(po.kmax, kPackMaxK);
     po.precision = r->precision;
-    // contraction deferral (Sect. 2) for large circuits in the tcgen05 mode: the gates up to the
-    // (pairs + 1)-th across the bipartition split_choose picks run as two tensors and one
-    // tensor-core contraction, when that front holds a large enough share of the circuit
+    // contraction deferral (Sect. 2) for large circuits: the gates up to the (pairs + 1)-th across
+    // the bipartition split_choose picks run as two tensors and one contraction (tcgen05 in the
+    // tensor-core modes, CUDA cores in FP32; front_pairs_for), when that front holds a large
+    // enough share of the circuit
     int front = 0;
     std::vector<int> side(n_qubits, 0);
-    const bool want_front = tuned_front >= 0 ? tuned_front == 1 : n_qubits >= kFrontMinQubits;
+    const int pairs = front_pairs_for(s, r->precision);
+    const bool want_front = pairs > 0 && (tuned_front >= 0 ? tuned_front == 1 : n_qubits >= kFrontMinQubits);
     // a repeated circuit replays its CUDA graph (created at its second submission)
-    const bool graph_ok = !r->packed && n_qubits <= kGraphMaxQubits &&
-                          !(tmem_mode(r->precision) && want_front && s->o.front_pairs >= 0);
+    const bool graph_ok = !r->packed && n_qubits <= kGraphMaxQubits && !want_front;
     if (graph_ok) {
         uint64_t key = 0xcbf29ce484222325ull;  // FNV-1a over the size, the options and the gate records
         auto mix = [&](const void *p, size_t nb) {
@@ -1076,11 +1094,10 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
             return enqueue_request(s, r, ticket);
         }
     }
-    if (!r->packed && tmem_mode(r->precision) && want_front && s->o.front_pairs >= 0) {
+    if (!r->packed && want_front) {
         int nf = 0;
-        if (split_choose(n_qubits, n_gates, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf,
-                         n_qubits) == SIM_OK &&
-            nf >= kFrontMinShare * n_gates)
+        if (split_choose(n_qubits, n_gates, gates, pairs, 7, side.data(), &nf, n_qubits) == SIM_OK &&
+            nf >= front_min_share(r->precision) * n_gates)
             front = nf;
     }
     sim_split_t *sp = nullptr;
@@ -1265,8 +1282,8 @@ static int tune_candidate(srv_t *s, sim_t *h, int n, int ng, const sim_gate *gat
     sim_plan_t *plan = nullptr;
     int rc = SIM_OK;
     if (front) {
-        rc = split_choose(n, ng, gates, s->o.front_pairs ? s->o.front_pairs : 5, 7, side.data(), &nf, n);
-        if (rc == SIM_OK && nf < kFrontMinShare * ng) rc = SIM_E_UNSUPPORTED;
+        rc = split_choose(n, ng, gates, front_pairs_for(s, s->o.precision), 7, side.data(), &nf, n);
+        if (rc == SIM_OK && nf < front_min_share(s->o.precision) * ng) rc = SIM_E_UNSUPPORTED;
         if (rc == SIM_OK) rc = sim_split_create(n, nf, gates, side.data(), &sp);
         if (rc == SIM_OK) rc = sim_front_create(h, sp, &po, &fr);
     }
@@ -1317,7 +1334,7 @@ int srv_autotune(srv_t *s, int n_samples, const int *n_qubits, const int *n_gate
         }
         srv_s::Tune best;
         best.ms = 1e300;
-        const bool can_front = tmem_mode(s->o.precision) && n >= 22 && s->o.front_pairs >= 0;
+        const bool can_front = front_pairs_for(s, s->o.precision) > 0 && n >= 22;
         for (int kmax = 4; kmax <= kMaxK && rc == SIM_OK; kmax++)
             for (int front = 0; front <= (can_front ? 1 : 0) && rc == SIM_OK; front++) {
                 float ms = 0.f;

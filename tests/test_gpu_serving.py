@@ -116,6 +116,29 @@ def test_large_circuits_take_the_contraction_front(pkg, oracle_mod):
         assert not np.array_equal(a, p)  # the front did run
 
 
+def test_large_fp32_circuits_take_a_two_pair_front(pkg, oracle_mod):
+    # >= 26 qubits in SIM_FP32: a front of at most 2 bridging gates (its contraction runs on CUDA
+    # cores and grows 4x per gate) when it holds >= 10 % of the circuit; amplitudes match the oracle,
+    # alone equals mix, and the result differs in its bits from the run without the front
+    circuits = [si.sycamore_circuit(si.near_square_grid(n), d, seed=750 + i)
+                for i, (n, d) in enumerate([(26, 12), (27, 16)])]
+    mix, res, stats = serve(pkg, circuits, True, slots=2, precision=pkg.SIM_FP32)
+    alone, _, _ = serve(pkg, circuits, False, slots=2, precision=pkg.SIM_FP32)
+    plain, _, _ = serve(pkg, circuits, False, slots=2, precision=pkg.SIM_FP32, front_pairs=-1)
+    assert stats["completed"] == len(circuits)
+    for c, a, b, p, (norm, s2, lat) in zip(circuits, mix, alone, plain, res):
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), c.name
+        want = oracle_mod.run_circuit(c)
+        err = np.linalg.norm(a.astype(np.complex128) - want)
+        err_plain = np.linalg.norm(p.astype(np.complex128) - want)
+        side, nf = pkg.sim_split_choose(c.n_qubits, pkg.gates_array(c), 2)
+        print(f"served FP32 {c.n_qubits} qubits, {len(c.gates)} gates, front of {nf}: err {err:.2e} "
+              f"(without the front {err_plain:.2e})")
+        assert nf >= 0.1 * len(c.gates)
+        assert err <= TOL_FP32 and err_plain <= TOL_FP32 and abs(norm - 1.0) < 1e-5
+        assert not np.array_equal(a, p)  # the front did run
+
+
 def test_admission_respects_hbm_budget(pkg, oracle_mod):
     # 20-qubit states are 8 MiB; a 20 MiB budget admits two at a time
     circuits = [si.sycamore_circuit(si.near_square_grid(20), 6, seed=s) for s in range(5)]
