@@ -257,6 +257,11 @@ bool precision_ok(int precision);
 inline void state_written(sim_t *h) { h->write_epoch++; }
 // the final combine of the reduction over nblocks (sum p, sum p^2) pairs (reduce.cu)
 int launch_reduce_final(const double *partials, int nblocks, double *d_result, cudaStream_t st);
+// Entries first .. first + count - 1 (logical indices through bit_of, or physical ones when bit_of
+// is NULL) whose physical index p lies in [lo, hi): buf[j] = base[p - lo] (scatter: the reverse);
+// the others untouched.  The device part of a hybrid host store's readout and load.
+int launch_gather_region(float2 *base, uint64_t lo, uint64_t hi, float2 *buf, uint64_t first, uint64_t count, int n,
+                         const int *bit_of, int scatter, cudaStream_t st);
 // d_result[4..6] = {d_result[0], scale * d_result[1], scale * d_result[1] - 1} (one thread)
 int launch_result3(double *d_result, double scale, cudaStream_t st);
 // the modes whose 4- to 6-qubit blocks take the tcgen05 kernel where it is eligible

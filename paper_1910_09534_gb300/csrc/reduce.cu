@@ -110,6 +110,25 @@ __global__ void k_gather_logical(float2 *psi, float2 *dst, uint64_t first, uint6
     }
 }
 
+// Entries first .. first + count - 1 (logical indices through m, or physical ones with the
+// identity map) whose physical index p lies in [lo, hi), between base[p - lo] and buf[j]: gathered
+// into buf, or scattered from it; the others are left alone (buf[j] for them is not written).
+__global__ void k_gather_region(float2 *base, uint64_t lo, uint64_t hi, float2 *buf, uint64_t first,
+                                uint64_t count, int n, BitMap m, int scatter)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = first + j;
+        uint64_t p = 0;
+        for (int q = 0; q < n; ++q) p |= ((i >> q) & 1ull) << m.bit_of[q];
+        if (p < lo || p >= hi) continue;
+        if (scatter)
+            base[p - lo] = buf[j];
+        else
+            buf[j] = base[p - lo];
+    }
+}
+
 __global__ void k_set_basis(float2 *psi, uint64_t phys) { psi[phys] = make_float2(1.f, 0.f); }
 
 // Final step of the allocation-free reduction: sum p, scale * sum p^2, and that minus 1.
@@ -164,6 +183,18 @@ int launch_reduce_final(const double *partials, int nblocks, double *d_result, c
 int launch_result3(double *d_result, double scale, cudaStream_t st)
 {
     k_result3<<<1, 1, 0, st>>>(d_result, scale);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_gather_region(float2 *base, uint64_t lo, uint64_t hi, float2 *buf, uint64_t first, uint64_t count, int n,
+                         const int *bit_of, int scatter, cudaStream_t st)
+{
+    BitMap m{};
+    for (int q = 0; q < n; q++) m.bit_of[q] = bit_of ? bit_of[q] : q;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks == 0) return 0;
+    k_gather_region<<<(unsigned)blocks, 256, 0, st>>>(base, lo, hi, buf, first, count, n, m, scatter);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

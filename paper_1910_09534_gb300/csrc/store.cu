@@ -60,41 +60,6 @@ float2 *region(const sim_t *h, uint64_t v)
     return v < h->host_regions ? h->h_store + v * slice : h->d_store + (v - h->host_regions) * slice;
 }
 
-// Host-addressable view of every region for element-wise access (reset, readout, load): host
-// regions as they are, each device region through a host copy (one region at most, per call,
-// is the cost of a hybrid store there).  write_back puts the copies back.
-struct HostView {
-    std::vector<float2 *> ptr;
-    std::vector<std::vector<float2>> copies;
-};
-
-int host_view(sim_t *h, HostView &hv, bool fetch)
-{
-    const uint64_t nreg = 1ull << h->s, slice = 1ull << (h->n - h->s);
-    hv.ptr.resize(nreg);
-    hv.copies.resize(nreg - h->host_regions);
-    for (uint64_t v = 0; v < nreg; v++) {
-        if (v < h->host_regions) {
-            hv.ptr[v] = region(h, v);
-            continue;
-        }
-        auto &c = hv.copies[v - h->host_regions];
-        c.resize(slice);
-        if (fetch) SIM_CUDA_TRY(h, cudaMemcpy(c.data(), region(h, v), sizeof(float2) * slice, cudaMemcpyDeviceToHost));
-        hv.ptr[v] = c.data();
-    }
-    return SIM_OK;
-}
-
-int host_view_write_back(sim_t *h, HostView &hv)
-{
-    const uint64_t slice = 1ull << (h->n - h->s);
-    for (uint64_t v = h->host_regions; v < (1ull << h->s); v++)
-        SIM_CUDA_TRY(h, cudaMemcpy(region(h, v), hv.copies[v - h->host_regions].data(), sizeof(float2) * slice,
-                                   cudaMemcpyHostToDevice));
-    return SIM_OK;
-}
-
 }  // namespace
 
 int host_store_create(sim_t *h, const sim_opts &o)
@@ -301,53 +266,87 @@ int host_reset(sim_t *h, uint64_t basis)
     return SIM_OK;
 }
 
+// Entries first .. first + count - 1 of a host store (logical or physical order): physical indices
+// below host_lim are in the pinned host regions and are read or written there in place; the rest,
+// a hybrid store's device regions, go through the device in chunks (k_gather_region), so no host
+// copy of a whole region is ever made.  for_chunk(c0, cnt, buf) is called per chunk with buf
+// holding (read) or to be filled with (write) the chunk's device-region entries.
+template <typename HostPart>
+int host_store_access(sim_t *h, uint64_t first, uint64_t count, int physical, bool write, HostPart host_part)
+{
+    const uint64_t host_lim = h->host_regions << (h->n - h->s);
+    if (!h->d_store) {  // every region on the host
+        parallel_for(count, [&](uint64_t a, uint64_t b) { host_part(a, b, 0, nullptr); });
+        return SIM_OK;
+    }
+    const uint64_t C = std::min<uint64_t>(count, 1ull << 24);
+    float2 *d_buf = nullptr;
+    if (C && cudaMalloc(reinterpret_cast<void **>(&d_buf), sizeof(float2) * C) != cudaSuccess)
+        return fail(h, SIM_E_NOMEM_DEV, "host store access: staging buffer");
+    std::vector<float2> buf(C);
+    const int *bits = physical ? nullptr : h->bit_of;
+    const uint64_t hi = 1ull << h->n;
+    int rc = SIM_OK;
+    for (uint64_t c0 = 0; c0 < count && rc == SIM_OK; c0 += C) {
+        const uint64_t cnt = std::min(C, count - c0);
+        if (write) {  // the host regions' entries in place, the rest scattered from the chunk
+            parallel_for(cnt, [&](uint64_t a, uint64_t b) { host_part(c0 + a, c0 + b, c0, buf.data()); });
+            if (cudaMemcpy(d_buf, buf.data(), sizeof(float2) * cnt, cudaMemcpyHostToDevice) != cudaSuccess ||
+                launch_gather_region(h->d_store, host_lim, hi, d_buf, first + c0, cnt, h->n, bits, 1, h->stream) != 0 ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess)
+                rc = fail(h, SIM_E_CUDA, "host store access: %s", cudaGetErrorString(cudaGetLastError()));
+        } else {
+            if (launch_gather_region(h->d_store, host_lim, hi, d_buf, first + c0, cnt, h->n, bits, 0, h->stream) != 0 ||
+                cudaMemcpyAsync(buf.data(), d_buf, sizeof(float2) * cnt, cudaMemcpyDeviceToHost, h->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess)
+                rc = fail(h, SIM_E_CUDA, "host store access: %s", cudaGetErrorString(cudaGetLastError()));
+            else
+                parallel_for(cnt, [&](uint64_t a, uint64_t b) { host_part(c0 + a, c0 + b, c0, buf.data()); });
+        }
+    }
+    if (d_buf) cudaFree(d_buf);
+    return rc;
+}
+
 int host_amplitudes(sim_t *h, uint64_t first, uint64_t count, void *out, int dtype, int physical)
 {
     int rc = host_sync_all(h);
     if (rc != SIM_OK) return rc;
-    HostView hv;
-    if ((rc = host_view(h, hv, true)) != SIM_OK) return rc;
-    const int lb = h->n - h->s;
-    const uint64_t mask = (1ull << lb) - 1;
-    auto at = [&](uint64_t j) {
-        const uint64_t p = physical ? first + j : logical_to_physical(h, first + j);
-        return hv.ptr[p >> lb][p & mask];
-    };
-    if (dtype == SIM_C64) {
-        float2 *o = (float2 *)out;
-        parallel_for(count, [&](uint64_t a, uint64_t b) {
-            for (uint64_t j = a; j < b; j++) o[j] = at(j);
-        });
-    } else {
-        double *o = (double *)out;
-        parallel_for(count, [&](uint64_t a, uint64_t b) {
-            for (uint64_t j = a; j < b; j++) {
-                const float2 v = at(j);
-                o[2 * j] = v.x;
-                o[2 * j + 1] = v.y;
+    const uint64_t host_lim = h->host_regions << (h->n - h->s);
+    const float2 *hs = h->h_store;
+    // entries j in [a, b): from the host regions, or from the chunk (starting at entry c0)
+    return host_store_access(h, first, count, physical, false, [&](uint64_t a, uint64_t b, uint64_t c0, const float2 *buf) {
+        for (uint64_t j = a; j < b; j++) {
+            const uint64_t p = physical ? first + j : logical_to_physical(h, first + j);
+            const float2 v = p < host_lim ? hs[p] : buf[j - c0];
+            if (dtype == SIM_C64) {
+                static_cast<float2 *>(out)[j] = v;
+            } else {
+                static_cast<double *>(out)[2 * j] = v.x;
+                static_cast<double *>(out)[2 * j + 1] = v.y;
             }
-        });
-    }
-    return SIM_OK;
+        }
+    });
 }
 
 int host_load(sim_t *h, uint64_t first, uint64_t count, const void *src, int physical)
 {
     int rc = host_sync_all(h);
     if (rc != SIM_OK) return rc;
-    HostView hv;
-    // device regions are only partly overwritten unless the range covers them: fetch them first
-    if ((rc = host_view(h, hv, true)) != SIM_OK) return rc;
-    const int lb = h->n - h->s;
-    const uint64_t mask = (1ull << lb) - 1;
-    const float2 *in = (const float2 *)src;
-    parallel_for(count, [&](uint64_t a, uint64_t b) {
+    const uint64_t host_lim = h->host_regions << (h->n - h->s);
+    float2 *hs = h->h_store;
+    const float2 *in = static_cast<const float2 *>(src);
+    // entries j in [a, b): into the host regions, or into the chunk for the device scatter
+    return host_store_access(h, first, count, physical, true, [&](uint64_t a, uint64_t b, uint64_t c0, float2 *buf) {
         for (uint64_t j = a; j < b; j++) {
             const uint64_t p = physical ? first + j : logical_to_physical(h, first + j);
-            hv.ptr[p >> lb][p & mask] = in[j];
+            if (p < host_lim)
+                hs[p] = in[j];
+            else
+                buf[j - c0] = in[j];
         }
     });
-    return host_view_write_back(h, hv);
 }
 
 int host_reduce(sim_t *h, double *s1, double *s2)

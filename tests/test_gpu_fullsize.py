@@ -12,10 +12,13 @@
   norm and Porter-Thomas, no oracle fits.  Its 28-qubit sub-lattice circuit (4x7, same depth)
   goes through the same sliced machinery and is compared with the oracle; the measured error of
   each arithmetic mode is printed.
+* The bench's 33-qubit configuration (the front contracted into the resident sliced state, then
+  3 phases) against every gate in phases, on 2^20 sampled amplitudes, with norm and Porter-Thomas.
 * Small sliced-phase case against the oracle, and the layout moves it makes.
-* 34 qubits (5x7 minus one corner; a 128 GiB host store): the contraction into the store fused
-  with the first phase, in the layout sim_phases_layout chose, against every gate in phases, on
-  2^20 sampled amplitudes, with both runs' norm and Porter-Thomas sum (no oracle fits).
+* 34 qubits (5x7 minus one corner; a 128 GiB host store) and 35 qubits (5x7; 256 GiB, half of the
+  store's regions in HBM): the contraction into the store fused with the first phase, in the
+  layout sim_phases_layout chose, against every gate in phases, on 2^20 sampled amplitudes, with
+  both runs' norm and Porter-Thomas sum (no oracle fits).
 """
 import numpy as np
 import pytest
@@ -164,7 +167,7 @@ def test_33q_sliced_phases_and_28q_sublattice(pkg, oracle_mod):
         assert err <= bounds[name], (name, err)
 
 
-def run_store(pkg, circ, s, kmax, front_pairs, ranges):
+def run_store(pkg, circ, s, kmax, front_pairs, ranges, device_regions=0):
     """A host-store run of the whole circuit: with front_pairs, the circuit's first gates as two
     tensors contracted slice by slice into a store laid out by sim_phases_layout, fused with the
     first phase, then the other phases; without, every gate in phases from |0..0>.  Returns the
@@ -180,7 +183,8 @@ def run_store(pkg, circ, s, kmax, front_pairs, ranges):
     a, b, _, _ = pkg.sim_phases_choose_sets(n, rest, s, kmax=kmax)
     ph = pkg.sim_phases_create(n, rest, s, a, b, kmax=kmax, precision=prec)
     nph = pkg.sim_phases_info(ph)[0]
-    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=3)
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=a, set_b=b, slots=3,
+                       store_device_regions=device_regions)
     fr = None
     try:
         if split is not None:
@@ -220,6 +224,79 @@ def test_34q_store_front_agrees_with_plain_phases(pkg):
     rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     print(f"34q store: front {nph} phases, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}; plain {nph0} phases, "
           f"norm {norm0:.7f}; sampled relative difference {rel:.2e}")
+    assert nph < nph0
+    for nn, ss in ((norm, s2), (norm0, s20)):
+        assert abs(nn - 1) < 2e-5 and abs(ss - 2) < 0.05
+    assert rel <= 2 * TOL_FP32
+
+
+def test_33q_front_in_resident_sliced_state_agrees_with_plain_phases(pkg):
+    # the bench's 33-qubit configuration: the first gates (3 bridging gates) contracted into the
+    # resident sliced state, laid out by sim_phases_layout(resident) so that the first phase needs
+    # no move, then the phases; against every gate in phases from |0..0>, on 2^20 sampled amplitudes
+    # (no oracle fits 33 qubits), with both runs' norm and Porter-Thomas sum
+    circ = si.workload_circuit("syc33_6x6m3_d20", seed=0)
+    n, s = circ.n_qubits, 3
+    gates = pkg.gates_array(circ)
+    prec = pkg.SIM_FP16X3_TMEM
+    set_a, set_b = list(range(s)), list(range(n - s, n))
+    rng = np.random.default_rng(9)
+    ranges = [(int(f) * 4096, 1 << 16) for f in rng.integers(0, (1 << n) // 4096 - 16, 16)]
+
+    def run(pairs):
+        split, nf = None, 0
+        if pairs:
+            side, nf = pkg.sim_split_choose(n, gates, pairs)
+            split = pkg.sim_split_create(n, gates[:nf], side)
+        ph = pkg.sim_phases_create(n, gates[nf:], s, set_a, set_b, kmax=6, precision=prec)
+        h = pkg.sim_create(n, s)
+        fr = None
+        try:
+            if split is not None:
+                perm, _, _ = pkg.sim_phases_layout(ph, n, split, resident=True)
+                pkg.sim_set_layout(h, perm)
+                fr = pkg.sim_front_create(h, split, kmax=6, precision=prec)
+                pkg.sim_front_run(h, fr)
+            else:
+                pkg.sim_reset(h)
+            pkg.sim_run_phases(h, ph)
+            pkg.sim_sync(h)
+            samples = np.concatenate([pkg.sim_amplitudes(h, f, c, dtype=pkg.SIM_C128) for f, c in ranges])
+            red = pkg.sim_reduce(h)
+            nph = pkg.sim_phases_info(ph)[0]
+        finally:
+            if fr is not None:
+                pkg.sim_front_destroy(fr)
+            pkg.sim_destroy(h)
+            pkg.sim_phases_destroy(ph)
+            if split is not None:
+                pkg.sim_split_destroy(split)
+        return samples, red, nph
+
+    got, (norm, s2, _), nph = run(3)
+    ref, (norm0, s20, _), nph0 = run(0)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"33q resident: front {nph} phases, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}; plain {nph0} phases; "
+          f"sampled relative difference {rel:.2e}")
+    assert nph < nph0
+    for nn, ss in ((norm, s2), (norm0, s20)):
+        assert abs(nn - 1) < 2e-5 and abs(ss - 2) < 0.05
+    assert rel <= 2 * TOL_FP32
+
+
+def test_35q_hybrid_store_front_agrees_with_plain_phases(pkg):
+    # the bench's 35-qubit configuration (256 GiB: 8 of 16 regions pinned on the host, 8 in HBM):
+    # the contraction into the store, fused with the first phase, against every gate in phases,
+    # on 2^20 sampled amplitudes, with both runs' norm and Porter-Thomas sum
+    circ = si.workload_circuit("syc35_5x7_d16", seed=0)
+    n = circ.n_qubits
+    rng = np.random.default_rng(11)
+    ranges = [(int(f) * 4096, 1 << 16) for f in rng.integers(0, (1 << n) // 4096 - 16, 16)]
+    got, (norm, s2, _), nph = run_store(pkg, circ, 4, 6, 4, ranges, device_regions=8)
+    ref, (norm0, s20, _), nph0 = run_store(pkg, circ, 4, 6, 0, ranges, device_regions=8)
+    rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"35q hybrid store: front {nph} phases, norm {norm:.7f}, 2^n sum p^2 {s2:.4f}; plain {nph0} "
+          f"phases, norm {norm0:.7f}; sampled relative difference {rel:.2e}")
     assert nph < nph0
     for nn, ss in ((norm, s2), (norm0, s20)):
         assert abs(nn - 1) < 2e-5 and abs(ss - 2) < 0.05

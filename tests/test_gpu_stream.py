@@ -183,3 +183,36 @@ def test_phase_boundaries_order_copies(pkg, oracle_mod, slots):
         pkg.sim_phases_destroy(ph)
     assert abs(norm - 1.0) < 1e-5
     assert np.linalg.norm(got - oracle_mod.run_circuit(circ)) <= TOL_FP32
+
+
+@pytest.mark.parametrize("physical", [False, True])
+def test_hybrid_store_load_and_readout_in_chunks(pkg, oracle_mod, physical):
+    # 26 qubits, 4 regions of 2^24 amplitudes, 2 of them in HBM, relabelled: a load and a readout
+    # of all 2^26 amplitudes (four staging chunks; the device regions' entries go through the
+    # device, the host regions' in place) and of a ragged range across the regions' boundary are
+    # bit-exact, in logical and in physical order
+    n, s = 26, 2
+    h = pkg.sim_create(n, s, store=pkg.SIM_STORE_HOST, set_a=[3, 17], set_b=[8, 21], slots=2,
+                       store_device_regions=2)
+    try:
+        bits = [int(x) for x in pkg.sim_info(h)[2]]
+        others = sorted(range(n), key=lambda q: bits[q])[:n - 2 * s]
+        perm = list(bits)
+        for q, b in zip(others, reversed(sorted(bits[q] for q in others))):
+            perm[q] = b  # the other qubits' order reversed: a relabelling the store allows
+        pkg.sim_set_layout(h, perm)
+        rng = np.random.default_rng(5)
+        psi = (rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)).astype(np.complex64)
+        pkg.sim_load_amplitudes(h, psi, physical_order=physical)
+        back = pkg.sim_amplitudes(h, dtype=pkg.SIM_C64, physical_order=physical)
+        assert np.array_equal(back.view(np.uint64), psi.view(np.uint64))
+        first, count = (1 << 25) - 12345, (1 << 24) + 777  # straddles the host / device boundary
+        part = pkg.sim_amplitudes(h, first, count, dtype=pkg.SIM_C64, physical_order=physical)
+        assert np.array_equal(part.view(np.uint64), psi[first:first + count].view(np.uint64))
+        patch = (rng.standard_normal(count) + 1j * rng.standard_normal(count)).astype(np.complex64)
+        pkg.sim_load_amplitudes(h, patch, first=first, physical_order=physical)
+        psi[first:first + count] = patch
+        back = pkg.sim_amplitudes(h, dtype=pkg.SIM_C64, physical_order=physical)
+        assert np.array_equal(back.view(np.uint64), psi.view(np.uint64))
+    finally:
+        pkg.sim_destroy(h)
