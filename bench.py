@@ -595,9 +595,9 @@ def run_ours(args):
     pass_updates = whole_job_rate(float(amps) * nblocks * args.steps, ws, ms_max / 1e3)
 
     # end to end through the public API with host buffers: gate records from pinned host
-    # memory in, all 2^n amplitudes out to pinned host memory, every step.  Two handles
-    # alternate, so that the readout of step i (8 GiB at the ~190 GB/s of the host link) runs
-    # while step i + 1 computes; the last readout is inside the timed region too.
+    # memory in, all 2^n amplitudes out to pinned host memory, every step; the last readout is
+    # inside the timed region too.  The schedule (readouts overlapping the next circuit's compute
+    # on two handles, or one after the other) is the faster of the two on a short untimed probe.
     gates_pinned = pkg.pinned_array(gates.size, dtype=pkg._native.GATE_DTYPE)
     gates_pinned[:] = gates
     h2 = pkg.sim_create(n, 0, device=local)
@@ -618,32 +618,49 @@ def run_ours(args):
     streams = [torch.cuda.ExternalStream(pkg.sim_stream(hh)) for hh in hs]
     rd_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
              for _ in range(args.e2e_steps)]
-    # the circuits compute one after another (each handle's stream waits for the other's last
-    # compute kernel, not for its readout), so one handle's readout always overlaps the other's
-    # compute: a step costs max(compute, readout) whichever of the two is longer
     computed = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def e2e_loop(k, overlap, rd=None):
+        # overlap: two handles, the circuits computing one after another (each handle's stream
+        # waits for the other's last compute kernel, not for its readout), so one handle's readout
+        # overlaps the other's compute and a step costs max(compute, readout).  Serial: one handle,
+        # each readout finished before the next circuit starts -- faster on hosts whose link, while
+        # the device streams HBM at its peak, moves data several times slower than alone
+        plan = pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
+        for s_ in range(k):
+            i = s_ % 2 if overlap else 0
+            hc = hs[i]
+            if overlap and s_ > 0:
+                streams[i].wait_event(computed[(s_ - 1) % 2])
+            start(hc)
+            pkg.sim_apply_plan(hc, plan)
+            if layout is not None:
+                pkg.sim_permute(hc, list(range(n)))  # logical order for the asynchronous readout
+            computed[i].record(streams[i])
+            nxt = pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec) if s_ + 1 < k else None
+            if rd is not None:
+                rd[s_][0].record(streams[i])
+            pkg.sim_amplitudes_async(hc, outs[i])
+            if rd is not None:
+                rd[s_][1].record(streams[i])
+            if not overlap:
+                pkg.sim_sync(hc)
+            elif s_ > 0:
+                pkg.sim_sync(hs[(s_ - 1) % 2])  # the previous circuit's amplitudes are in host memory
+            pkg.sim_plan_destroy(plan)
+            plan = nxt
+        pkg.sim_sync(hs[(k - 1) % 2] if overlap else hs[0])
+
+    # the schedule: both measured on 3 untimed steps, the faster one timed
+    probe = {}
+    for mode in (True, False):
+        tp = time.perf_counter()
+        e2e_loop(3, mode)
+        probe["overlapped" if mode else "serial"] = time.perf_counter() - tp
+    overlap = probe["overlapped"] <= probe["serial"]
     barrier()
     t0 = time.perf_counter()
-    plan = pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
-    for s_ in range(args.e2e_steps):
-        hc = hs[s_ % 2]
-        if s_ > 0:
-            streams[s_ % 2].wait_event(computed[(s_ - 1) % 2])
-        start(hc)
-        pkg.sim_apply_plan(hc, plan)
-        if layout is not None:
-            pkg.sim_permute(hc, list(range(n)))  # logical order for the asynchronous readout
-        computed[s_ % 2].record(streams[s_ % 2])
-        nxt = (pkg.sim_plan_create(n, rest_pinned, kmax=args.kmax, precision=prec)
-               if s_ + 1 < args.e2e_steps else None)
-        rd_ev[s_][0].record(streams[s_ % 2])
-        pkg.sim_amplitudes_async(hc, outs[s_ % 2])
-        rd_ev[s_][1].record(streams[s_ % 2])
-        if s_ > 0:
-            pkg.sim_sync(hs[(s_ - 1) % 2])  # the previous circuit's amplitudes are in host memory
-        pkg.sim_plan_destroy(plan)
-        plan = nxt
-    pkg.sim_sync(hs[(args.e2e_steps - 1) % 2])
+    e2e_loop(args.e2e_steps, overlap, rd_ev)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     torch.cuda.synchronize()
@@ -656,7 +673,7 @@ def run_ours(args):
     pkg.sim_amplitudes_async(h, outs[0])
     pkg.sim_sync(h)
     readout_ms = 1e3 * (time.perf_counter() - t1)
-    sanity = outs[(args.e2e_steps - 1) % 2][:4].copy()
+    sanity = outs[(args.e2e_steps - 1) % 2 if overlap else 0][:4].copy()
     for o in outs + results:
         pkg.sim_host_free(o.ctypes.data)
     pkg.sim_host_free(gates_pinned.ctypes.data)
@@ -819,7 +836,11 @@ def run_ours(args):
                                   "other": ms_max / args.steps - (a_ms + r_ms + c_ms) / args.steps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(gates.nbytes + matrix_bytes),
                 "d2h_bytes_per_step": int(amps * 8), "steps": args.e2e_steps,
-                "pipelined": "two handles, computes chained: the readout of step i overlaps the compute of step i+1",
+                "schedule": ("overlapped: two handles, computes chained, the readout of step i during the "
+                             "compute of step i+1" if overlap else
+                             "serial: one handle, each readout before the next compute (the link slows "
+                             "while the device streams HBM)"),
+                "schedule_probe_s": probe,
                 "readout_alone_ms": readout_ms, "readout_alone_gbs": amps * 8 / (readout_ms / 1e3) / 1e9,
                 "readout_in_loop_ms": {"median": rd_in_loop[len(rd_in_loop) // 2], "max": rd_in_loop[-1]},
                 "e2e_ms_per_step": 1e3 * e2e_s / args.e2e_steps},
