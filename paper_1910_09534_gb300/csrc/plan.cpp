@@ -55,14 +55,6 @@ void left_multiply_t(double *U, int D, const double *G, int l0, int l1)
     }
 }
 
-void left_multiply(std::vector<double> &U, int k, const double *G, int dg, int l0, int l1)
-{
-    if (dg == 4)
-        left_multiply_t<4>(U.data(), 1 << k, G, l0, l1);
-    else
-        left_multiply_t<2>(U.data(), 1 << k, G, l0, -1);
-}
-
 // Passes 1 and 2 of the planner over the gates gates[idx[0]], gates[idx[1]], ... (circuit order):
 // the units (a two-qubit gate with the single-qubit gates folded into it) and their greedy grouping
 // into blocks of at most kmax qubits (block qubits in order of first use).  Returns 0, or 1 with

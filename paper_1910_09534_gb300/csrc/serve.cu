@@ -941,8 +941,9 @@ int srv_create(const srv_opts *opts, srv_t **out)
     }
     DeviceScope dev_scope(s->o.device);
     if (dev_scope.err != cudaSuccess) {
+        const int device = s->o.device;
         delete s;
-        return srv_fail(nullptr, SIM_E_CUDA, "srv_create: device %d unavailable", s->o.device);
+        return srv_fail(nullptr, SIM_E_CUDA, "srv_create: device %d unavailable", device);
     }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
