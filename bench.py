@@ -118,8 +118,8 @@ def parse():
     ap.add_argument("--large-kmax", type=int, default=0,
                     help="with --large-case: block width (0: the case's own)")
     ap.add_argument("--large-front-pairs", type=int, default=-1,
-                    help="with --large-case on a host store: bridging gates of the contraction-deferral "
-                         "front (-1: the case's own, 0: none, the whole circuit in phases)")
+                    help="with --large-case: bridging gates of the contraction-deferral front (-1: the "
+                         "case's own, 0: none, the whole circuit in phases)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run only the small profiling case (2^28 amplitudes, 2 GiB > L2): fused "
                          "apply k=4 (targets >= bit 5, then mixed), k=2, k=5 on tensor cores (3xFP16 with "
