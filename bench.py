@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--no-bf16-path", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--no-per-gate", action="store_true",
+                    help="skip the plain per-gate baseline (every gate its own pass over the state)")
     ap.add_argument("--serving-circuits", type=int, default=2000)
     ap.add_argument("--serving-rate", type=float, default=SERVING_RATE_SPLIT,
                     help="Poisson arrival rate of the split-precision serving leg in circuits/s (0: every "
@@ -753,6 +755,30 @@ def run_ours(args):
                      "roofline": {"bound": "hbm", "achieved": ach32, "peak": peak32, "unit": "GB/s",
                                   "frac": ach32 / peak32, "launches": c32}}
 
+    # the plain per-gate apply (configuration 2's baseline): every gate its own FP32 pass over the
+    # state from |0...0>, its matrix from sim_gate_matrix, through sim_apply_fused
+    per_gate_path = None
+    if not args.no_per_gate:
+        per_gate = [([int(g["q0"])] if g["q1"] < 0 else [int(g["q0"]), int(g["q1"])], pkg.sim_gate_matrix(g))
+                    for g in gates]
+        pkg.sim_set_layout(h, list(range(n)))
+
+        def step_pg():
+            pkg.sim_reset(h)
+            for t, m in per_gate:
+                pkg.sim_apply_fused(h, t, m)
+            return pkg.sim_reduce(h)
+        step_pg()  # warm-up
+        barrier()
+        e0.record(stream)
+        npg, spg, _ = step_pg()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mspg = e0.elapsed_time(e1)
+        per_gate_path = {"value": float(amps) * circ.n_gates / (mspg / 1e3), "unit": UNIT, "ms_per_step": mspg,
+                         "passes": len(per_gate), "precision": "fp32", "norm": npg, "porter_thomas_2n_sum_p2": spg,
+                         "default_speedup": mspg / (ms_max / args.steps)}
+
     # the same step in BF16x3 (the other split-precision mode: BF16 pieces, no better than 2^-16
     # per product), same front, widths and timing, for the comparison of the two modes
     bf16_path = None
@@ -875,6 +901,8 @@ def run_ours(args):
             "launches": c_n, "avg_launch_ms": c_ms / max(c_n, 1),
             "alg_flops_per_launch": c_flops / max(c_n, 1)}
         line["plain_path"] = plain_path
+    if per_gate_path:
+        line["per_gate_path"] = per_gate_path
     if fp32_path:
         line["fp32_path"] = fp32_path
     if bf16_path:
