@@ -912,9 +912,10 @@ def run_ours(args):
     line["check"]["norm_drift_per_pass"] = (norm - 1.0) / max(nblocks, 1)
     if ws == 1 and not args.no_large:
         # configuration 3: 33 qubits (64 GiB) held as 8 slices over 3 bits, phases with in-place
-        # permutation passes between them, in the default arithmetic, in BF16x3 and in FP32
+        # permutation passes between them, in the default arithmetic, in BF16x3, in TF32 (mma.sync;
+        # its stated error is ~1e-3) and in FP32
         line["syc33_sliced"] = {p: large_case_run("syc33_6x6m3_d20", p, local)
-                                for p in ("fp16x3_tmem", "bf16x3", "fp32")}
+                                for p in ("fp16x3_tmem", "bf16x3", "tf32", "fp32")}
         # configuration 4: 35 qubits (256 GiB) in a secondary store, 8 of its 16 regions pinned on the
         # host and 8 in HBM, streamed through device slots of 2^31 amplitudes phase by phase
         line["syc35_store"] = large_case_run("syc35_5x7_d16", "fp16x3_tmem", local)
@@ -997,7 +998,7 @@ def large_case_run(name: str, precision: str = "fp16x3_tmem", device: int = 0, f
     circ = si.workload_circuit(name, seed=0)
     n, s, kmax = circ.n_qubits, cfg["slice_bits"], kmax or cfg["kmax"]
     gates = pkg.gates_array(circ)
-    prec = pkg.SIM_BF16X3 if precision == "bf16x3" else pkg.SIM_FP16X3_TMEM
+    prec = {"bf16x3": pkg.SIM_BF16X3, "tf32": pkg.SIM_TF32}.get(precision, pkg.SIM_FP16X3_TMEM)
     if precision == "fp32":
         prec, kmax = pkg.SIM_FP32, 4
     host = cfg["store"] == "host"
@@ -1123,7 +1124,7 @@ def serving_case(args):
 def main():
     args = parse()
     if args.large_case:
-        large_case(args.large_case, args.precision if args.precision in ("fp32", "bf16x3") else "fp16x3_tmem",
+        large_case(args.large_case, args.precision if args.precision in ("fp32", "bf16x3", "tf32") else "fp16x3_tmem",
                    args.large_front_pairs, args.large_kmax)
     elif args.serving_only:
         serving_case(args)
