@@ -331,8 +331,9 @@ def serving_run(count: int, device: int, rate_hz: float = 0.0, precision: str = 
         until(t0, at)
         h = handles[c.n_qubits]
         big = c.n_qubits > 20
-        p = (pkg.sim_plan_create(c.n_qubits, g, kmax=kmax_of(c.n_qubits), precision=prec) if big else
-             pkg.sim_plan_create(c.n_qubits, g, kmax=5, precision=pkg.SIM_FP32 if fp32 else prec))
+        # planned as the server plans a request: the greedy schedule (search=1)
+        p = (pkg.sim_plan_create(c.n_qubits, g, kmax=kmax_of(c.n_qubits), precision=prec, search=1) if big else
+             pkg.sim_plan_create(c.n_qubits, g, kmax=5, precision=pkg.SIM_FP32 if fp32 else prec, search=1))
         if big:
             pkg.sim_set_layout(h, pkg.sim_plan_layout(p, c.n_qubits)[0])
         pkg.sim_reset(h)

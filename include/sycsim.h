@@ -278,7 +278,9 @@ typedef struct sim_plan_s sim_plan_t;
 typedef struct sim_plan_opts {
     int kmax;      /* largest block width, 1..6 (Sect. 5 uses k_max = 5) */
     int precision; /* arithmetic for the blocks' apply: SIM_FP32, SIM_TF32, SIM_TF32X3, SIM_FP16X3 */
-    int reserved[6];
+    int search;    /* beam width of the block search, 0..256: 0 = the default (16), 1 = the greedy
+                      schedule alone; wider searches may find fewer blocks and take longer */
+    int reserved[5];
 } sim_plan_opts;
 
 /* Aggregation planner (Sect. 5: gates grouped into blocks of at most k_max

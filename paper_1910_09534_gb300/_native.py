@@ -61,7 +61,8 @@ class SimOpts(ctypes.Structure):
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("kmax", ctypes.c_int), ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+    _fields_ = [("kmax", ctypes.c_int), ("precision", ctypes.c_int), ("search", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class SrvOpts(ctypes.Structure):
@@ -396,11 +397,12 @@ def sim_gate_matrix(gate) -> np.ndarray:
     return out[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
 
 
-def sim_plan_create(n_qubits: int, gates: np.ndarray, kmax: int = 4, precision: int = SIM_FP32):
+def sim_plan_create(n_qubits: int, gates: np.ndarray, kmax: int = 4, precision: int = SIM_FP32, search: int = 0):
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     o = PlanOpts()
     o.kmax = kmax
     o.precision = precision
+    o.search = search
     p = ctypes.c_void_p()
     _check(lib().sim_plan_create(n_qubits, int(g.size), _ptr(g), ctypes.byref(o), ctypes.byref(p)))
     return p
@@ -503,13 +505,14 @@ def sim_run_phase(h, set_: int, plan) -> None:
 
 
 def sim_phases_create(n_qubits: int, gates: np.ndarray, slice_bits: int, set_a, set_b, kmax: int = 4,
-                      precision: int = SIM_FP32):
+                      precision: int = SIM_FP32, search: int = 0):
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     a = np.ascontiguousarray(set_a, dtype=np.int32)
     b = np.ascontiguousarray(set_b, dtype=np.int32)
     o = PlanOpts()
     o.kmax = kmax
     o.precision = precision
+    o.search = search
     p = ctypes.c_void_p()
     _check(lib().sim_phases_create(n_qubits, int(g.size), _ptr(g), ctypes.byref(o), slice_bits, _ptr(a),
                                    _ptr(b), ctypes.byref(p)))
@@ -517,11 +520,12 @@ def sim_phases_create(n_qubits: int, gates: np.ndarray, slice_bits: int, set_a, 
 
 
 def sim_phases_choose_sets(n_qubits: int, gates: np.ndarray, slice_bits: int, kmax: int = 4,
-                           phase_weight: float = 0.0):
+                           phase_weight: float = 0.0, search: int = 0):
     """(set_a, set_b, n_phases, n_blocks) chosen for the circuit; host only."""
     g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     o = PlanOpts()
     o.kmax = kmax
+    o.search = search
     a = np.zeros(slice_bits, dtype=np.int32)
     b = np.zeros(slice_bits, dtype=np.int32)
     nph, nbl = ctypes.c_int(), ctypes.c_int()

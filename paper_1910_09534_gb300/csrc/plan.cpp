@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <random>
 #include <vector>
 
@@ -55,6 +56,14 @@ void left_multiply_t(double *U, int D, const double *G, int l0, int l1)
     }
 }
 
+// Beam width of the block search (sim_plan_opts.search; 0 = the default, 1 = the greedy
+// schedule alone).
+constexpr int kPlanSearchDefault = 16, kPlanSearchMax = 256;
+int search_width(int search)
+{
+    return search > 0 ? std::min(search, kPlanSearchMax) : kPlanSearchDefault;
+}
+
 // Passes 1 and 2 of the planner over the gates gates[idx[0]], gates[idx[1]], ... (circuit order):
 // the units (a two-qubit gate with the single-qubit gates folded into it) and their greedy grouping
 // into blocks of at most kmax qubits (block qubits in order of first use).  Returns 0, or 1 with
@@ -71,7 +80,8 @@ struct Grouping {
     std::vector<std::vector<int>> block_units;  // per block, in order
 };
 
-int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx, int kmax, Grouping &gr, int *bad)
+int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx, int kmax, int width,
+                Grouping &gr, int *bad)
 {
     // Pass 1 (Sect. 3: single-qubit gates can be aggregated with neighbouring two-qubit gates):
     // each single-qubit gate joins the next two-qubit gate on its qubit, or the previous one
@@ -126,6 +136,7 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
     // the next ones in gate order, lets a block run ahead on its qubits while other parts of the
     // lattice wait: on the 30-qubit, 20-cycle circuit 49 blocks of <= 5 qubits instead of 69
     // in plain gate order (56 with the earliest ready unit as every block's seed), 37 of <= 6.
+    // With width > 1 a beam search over the seeds follows (below).
     const int nu = (int)units.size();
     std::vector<std::vector<int>> succ(nu);
     std::vector<int> indeg(nu, 0), lastu(n_qubits, -1);
@@ -142,12 +153,14 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             lastu[u.q[i]] = ui;
         }
     }
-    std::vector<int> ready;
+    std::vector<int> ready0;
     for (int ui = 0; ui < nu; ui++)
-        if (indeg[ui] == 0) ready.push_back(ui);
-    // Fill one block starting from `seed` (an element of rd); rd and indeg are updated, the
-    // taken units appended to `taken` and the block's qubits to `bq`.
-    auto fill = [&](int seed, std::vector<int> &rd, std::vector<int> &taken, std::vector<int> &bq) {
+        if (indeg[ui] == 0) ready0.push_back(ui);
+    // Fill one block starting from `seed` (an element of rd); rd and ind (the unplaced
+    // predecessor counts) are updated, the taken units appended to `taken` and the block's
+    // qubits to `bq`.
+    auto fill = [&](int seed, std::vector<int> &rd, std::vector<int> &ind, std::vector<int> &taken,
+                    std::vector<int> &bq) {
         int next = seed;
         for (;;) {
             int pos = -1;
@@ -175,29 +188,88 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             for (int i = 0; i < u.nq; i++)
                 if (std::find(bq.begin(), bq.end(), u.q[i]) == bq.end()) bq.push_back(u.q[i]);
             for (const int sx : succ[ui])
-                if (--indeg[sx] == 0) rd.push_back(sx);
+                if (--ind[sx] == 0) rd.push_back(sx);
         }
     };
-    int placed = 0;
     std::vector<int> rd, taken, bq;
-    while (placed < nu) {
-        int best_seed = -1, best_n = -1;
-        for (const int seed : ready) {  // trial fills, undone afterwards
-            rd = ready;
+    // the greedy schedule: every block's seed is the ready unit whose fill takes the most units
+    std::vector<int> seeds;
+    {
+        std::vector<int> ready = ready0, ind = indeg;
+        int placed = 0;
+        while (placed < nu) {
+            int best_seed = -1, best_n = -1;
+            for (const int seed : ready) {  // trial fills, undone afterwards
+                rd = ready;
+                taken.clear();
+                bq.clear();
+                fill(seed, rd, ind, taken, bq);
+                for (const int ui : taken)
+                    for (const int sx : succ[ui]) ind[sx]++;
+                if ((int)taken.size() > best_n || ((int)taken.size() == best_n && seed < best_seed)) {
+                    best_n = (int)taken.size();
+                    best_seed = seed;
+                }
+            }
+            seeds.push_back(best_seed);
             taken.clear();
             bq.clear();
-            fill(seed, rd, taken, bq);
-            for (const int ui : taken)
-                for (const int sx : succ[ui]) indeg[sx]++;
-            if ((int)taken.size() > best_n || ((int)taken.size() == best_n && seed < best_seed)) {
-                best_n = (int)taken.size();
-                best_seed = seed;
-            }
+            fill(best_seed, ready, ind, taken, bq);
+            placed += (int)taken.size();
         }
-        gr.qubits.emplace_back();
-        gr.block_units.emplace_back();
-        fill(best_seed, ready, gr.block_units.back(), gr.qubits.back());
-        placed += (int)gr.block_units.back().size();
+    }
+    // Beam search (width > 1) for a schedule of fewer blocks: after each block, keep the `width`
+    // partial schedules that have placed the most units (earlier ones on ties).  A partial
+    // schedule is identified by its ready units, which fix the placed ones (the units not
+    // placed are exactly those at or after a ready unit), so two that reach the same ready
+    // units are one.  The first schedule to place every unit in fewer blocks than the greedy
+    // one replaces it.
+    if (width > 1) {
+        struct Partial {
+            int placed;
+            std::vector<int> ready, ind, seeds;
+        };
+        std::vector<Partial> cur, next;
+        cur.push_back(Partial{0, ready0, indeg, {}});
+        std::map<std::vector<int>, int> seen;
+        std::vector<int> key;
+        bool done = false;
+        for (int depth = 1; depth < (int)seeds.size() && !done && !cur.empty(); depth++) {
+            next.clear();
+            seen.clear();
+            for (size_t pi = 0; pi < cur.size() && !done; pi++) {
+                const Partial &p = cur[pi];
+                for (const int seed : p.ready) {
+                    Partial c{p.placed, p.ready, p.ind, p.seeds};
+                    taken.clear();
+                    bq.clear();
+                    fill(seed, c.ready, c.ind, taken, bq);
+                    c.placed += (int)taken.size();
+                    c.seeds.push_back(seed);
+                    if (c.placed == nu) {
+                        seeds = std::move(c.seeds);
+                        done = true;
+                        break;
+                    }
+                    key = c.ready;
+                    std::sort(key.begin(), key.end());
+                    if (seen.emplace(key, (int)next.size()).second) next.push_back(std::move(c));
+                }
+            }
+            std::stable_sort(next.begin(), next.end(),
+                             [](const Partial &a, const Partial &b) { return a.placed > b.placed; });
+            if ((int)next.size() > width) next.resize(width);
+            cur.swap(next);
+        }
+    }
+    // the blocks of the chosen schedule
+    {
+        std::vector<int> ready = ready0, ind = indeg;
+        for (const int seed : seeds) {
+            gr.qubits.emplace_back();
+            gr.block_units.emplace_back();
+            fill(seed, ready, ind, gr.block_units.back(), gr.qubits.back());
+        }
     }
     return 0;
 }
@@ -270,6 +342,8 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
         return fail(nullptr, SIM_E_INVAL, "sim_plan_create: kmax=%d outside 2..%d", opts.kmax, kMaxK);
     if (!precision_ok(opts.precision))
         return fail(nullptr, SIM_E_INVAL, "sim_plan_create: precision %d", opts.precision);
+    if (opts.search < 0 || opts.search > kPlanSearchMax)
+        return fail(nullptr, SIM_E_INVAL, "sim_plan_create: search=%d outside 0..%d", opts.search, kPlanSearchMax);
 
     auto *p = new sim_plan_s();
     p->n = n_qubits;
@@ -280,7 +354,7 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
     std::vector<int> idx(n_gates);
     for (int i = 0; i < n_gates; i++) idx[i] = i;
     int bad = 0;
-    const int grc = group_gates(n_qubits, gates, idx, opts.kmax, gr, &bad);
+    const int grc = group_gates(n_qubits, gates, idx, opts.kmax, search_width(opts.search), gr, &bad);
     if (grc) {
         delete p;
         return fail(nullptr, SIM_E_INVAL, grc == 1 ? "sim_plan_create: gate %d has unknown kind %d"
@@ -961,13 +1035,14 @@ int sim_phases_create(int n_qubits, int n_gates, const sim_gate *gates, const si
     if (!ok0 && !ok1) return fail(nullptr, SIM_E_INVAL, "sim_phases_create: circuit cannot be phased");
     // of the two starting sets, the one with the least phases * 32 + fused blocks (the cost
     // sim_phases_choose_sets uses)
-    const int kmax_g = o && o->kmax ? o->kmax : 4;
+    const int kmax_g = o && o->kmax ? o->kmax : 4, width = search_width(o ? o->search : 0);
     auto cost = [&](const std::vector<std::pair<int, std::vector<int>>> &phs) {
         double blocks = 0;
         for (auto &ph : phs) {
             Grouping gr;
             int bad = 0;
-            if (group_gates(n_qubits, gates, ph.second, std::max(2, std::min(kmax_g, kMaxK)), gr, &bad)) return 1e300;
+            if (group_gates(n_qubits, gates, ph.second, std::max(2, std::min(kmax_g, kMaxK)), width, gr, &bad))
+                return 1e300;
             blocks += (double)gr.qubits.size();
         }
         return 32.0 * (double)phs.size() + blocks;
@@ -1004,7 +1079,7 @@ int sim_phases_choose_sets(int n_qubits, int n_gates, const sim_gate *gates, int
     if (n_qubits < 2 || n_qubits > kMaxQubits || slice_bits < 1 || slice_bits > 8 || 2 * slice_bits >= n_qubits ||
         n_gates < 0 || (n_gates > 0 && !gates) || !set_a || !set_b)
         return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: bad arguments");
-    const int kmax = o && o->kmax ? o->kmax : 4;
+    const int kmax = o && o->kmax ? o->kmax : 4, width = search_width(o ? o->search : 0);
     if (kmax < 2 || kmax > kMaxK) return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: kmax=%d", kmax);
     if (!(phase_weight > 0.0)) phase_weight = 32.0;
     double G[32];
@@ -1039,7 +1114,8 @@ int sim_phases_choose_sets(int n_qubits, int n_gates, const sim_gate *gates, int
                 for (auto &ph : phases) {
                     Grouping gr;
                     int bad = 0;
-                    if (group_gates(n_qubits, gates, ph.second, kmax, gr, &bad)) return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: gate %d", bad);
+                    if (group_gates(n_qubits, gates, ph.second, kmax, width, gr, &bad))
+                        return fail(nullptr, SIM_E_INVAL, "sim_phases_choose_sets: gate %d", bad);
                     blocks += (int)gr.qubits.size();
                 }
                 const double cost = phase_weight * (double)phases.size() + blocks;

@@ -308,6 +308,8 @@ constexpr int kFrontMinQubits = 26;      // smaller states: the passes a front s
 constexpr double kFrontMinShare = 0.3;   // a front with fewer of the gates is not worth a contraction
 constexpr int kFp32FrontPairs = 2;       // FP32 fronts: their contraction (CUDA cores) grows 4x a pair
 constexpr double kFp32FrontMinShare = 0.1;
+constexpr int kSrvPlanSearch = 1;  // requests are planned on the submitting thread: the greedy
+                                   // schedule (a beam search adds milliseconds a circuit)
 constexpr int kResultRing = 1 << 16;
 constexpr int kGraphMaxQubits = 24;  // graph entries hold their own state: 8 * 2^24 bytes at most
 constexpr int kGraphMaxEntries = 8;
@@ -1063,6 +1065,7 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     po.kmax = s->o.kmax ? s->o.kmax : (tuned_kmax ? tuned_kmax : auto_kmax(n_qubits, r->packed, r->precision));
     if (r->packed) po.kmax = std::min(po.kmax, kPackMaxK);
     po.precision = r->precision;
+    po.search = kSrvPlanSearch;
     // contraction deferral (Sect. 2) for large circuits: the gates up to the (pairs + 1)-th across
     // the bipartition split_choose picks run as two tensors and one contraction (tcgen05 in the
     // tensor-core modes, CUDA cores in FP32; front_pairs_for), when that front holds a large
@@ -1276,6 +1279,7 @@ static int tune_candidate(srv_t *s, sim_t *h, int n, int ng, const sim_gate *gat
     sim_plan_opts po{};
     po.kmax = kmax;
     po.precision = s->o.precision;
+    po.search = kSrvPlanSearch;
     int nf = 0;
     std::vector<int> side(n, 0);
     sim_split_t *sp = nullptr;

@@ -48,6 +48,7 @@ static int layout(void)
     SIZE(sim_opts);
     FIELD(sim_plan_opts, kmax);
     FIELD(sim_plan_opts, precision);
+    FIELD(sim_plan_opts, search);
     FIELD(sim_plan_opts, reserved);
     SIZE(sim_plan_opts);
     FIELD(srv_opts, device);

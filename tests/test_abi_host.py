@@ -127,6 +127,51 @@ def test_planner_counts_on_30q_circuit(pkg):
     assert counts[2] > counts[3] > counts[4] > counts[5] >= counts[6]
 
 
+@pytest.mark.parametrize("grid,cycles,kmax", [((3, 4), 12, 5), ((4, 4), 12, 3), ((3, 5), 20, 5)])
+def test_planner_search_finds_fewer_blocks_that_reproduce_circuit(pkg, oracle_mod, grid, cycles, kmax):
+    # the beam search over block seeds (sim_plan_opts.search): never more blocks than the greedy
+    # schedule (search=1), fewer on these circuits at the default width, and its blocks still
+    # reproduce the gate-by-gate run
+    circ = si.sycamore_circuit(si.Grid(*grid), cycles=cycles, seed=8)
+    g = pkg.gates_array(circ)
+    want = oracle_mod.run_circuit(circ)
+    counts = {}
+    for w in (1, 2, 16, 64, 0):
+        plan = pkg.sim_plan_create(circ.n_qubits, g, kmax=kmax, search=w)
+        try:
+            nb, ng, mk = pkg.sim_plan_info(plan)
+            assert ng == circ.n_gates and mk <= kmax
+            counts[w] = nb
+            psi = oracle_mod.basis_state(circ.n_qubits, 0)
+            for t, m in plan_blocks(pkg, plan):
+                assert list(t) == sorted(t) and len(set(t)) == len(t) <= kmax
+                oracle_mod.apply_kq(psi, t, m)
+            assert np.linalg.norm(psi - want) < 1e-12
+        finally:
+            pkg.sim_plan_destroy(plan)
+    assert all(counts[w] <= counts[1] for w in counts)
+    assert counts[0] == counts[16] < counts[1]  # 0 = the default width, 16
+
+
+def test_planner_search_on_the_33_qubit_phases(pkg):
+    # the 33-qubit, 20-cycle workload after its 3-pair front, phased over the lattice's two ends:
+    # the default search plans fewer blocks than the greedy schedule; bad widths are refused
+    circ = si.workload_circuit("syc33_6x6m3_d20", seed=0)
+    n, g = circ.n_qubits, pkg.gates_array(circ)
+    _, nf = pkg.sim_split_choose(n, g, 3)
+    blocks = {}
+    for w in (1, 0):
+        ph = pkg.sim_phases_create(n, g[nf:], 3, [0, 1, 2], [n - 3, n - 2, n - 1], kmax=6, search=w)
+        blocks[w] = pkg.sim_phases_info(ph)
+        pkg.sim_phases_destroy(ph)
+    assert blocks[0][0] == blocks[1][0] == 3
+    assert blocks[0][1] < blocks[1][1]
+    for bad in (-1, 257):
+        with pytest.raises(pkg.SimError) as e:
+            pkg.sim_plan_create(n, g, kmax=6, search=bad)
+        assert e.value.code == pkg.SIM_E_INVAL
+
+
 def test_planner_custom_matrices(pkg, oracle_mod):
     n = 5
     rng = np.random.default_rng(2)
