@@ -6,8 +6,10 @@
 // "units" of at most two qubits.  Then blocks are formed one at a time from the units whose
 // predecessors on their qubits are all placed (so every qubit sees its gates in circuit order):
 // from the seed unit that lets it absorb the most units, the open block takes the ready unit
-// that adds the fewest new qubits while it fits in k_max qubits.  Block matrices are composed in
-// FP64 on the block's own qubits (ascending), later gates multiplying from the left.
+// that adds the fewest new qubits while it fits in k_max qubits.  A beam search over the seeds
+// (sim_plan_opts.search) replaces that schedule when it finds one of fewer blocks.  Block
+// matrices are composed in FP64 on the block's own qubits (ascending), later gates multiplying
+// from the left.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
