@@ -13,7 +13,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <map>
 #include <random>
 #include <vector>
 
@@ -74,6 +73,7 @@ struct Unit {
     int q[2];
     int nq;
     std::vector<int> gates;  // indices into the full gate list
+    uint64_t mask;           // bit q set for each of its qubits
 };
 
 struct Grouping {
@@ -110,7 +110,7 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             pending[g.q0].push_back(gi);
             continue;
         }
-        Unit u{{g.q0, g.q1}, 2, {}};
+        Unit u{{g.q0, g.q1}, 2, {}, (1ull << g.q0) | (1ull << g.q1)};
         for (int i = 0; i < 2; i++) {
             u.gates.insert(u.gates.end(), pending[Q[i]].begin(), pending[Q[i]].end());
             pending[Q[i]].clear();
@@ -125,7 +125,7 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             auto &gl = units[last2q[q]].gates;
             gl.insert(gl.end(), pending[q].begin(), pending[q].end());
         } else {
-            units.push_back(Unit{{q, -1}, 1, pending[q]});
+            units.push_back(Unit{{q, -1}, 1, pending[q], 1ull << q});
         }
     }
 
@@ -163,7 +163,9 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
     // qubits to `bq`.
     auto fill = [&](int seed, std::vector<int> &rd, std::vector<int> &ind, std::vector<int> &taken,
                     std::vector<int> &bq) {
-        int next = seed;
+        uint64_t bm = 0;  // the block's qubits as a mask (bq keeps their order of first use)
+        for (const int q : bq) bm |= 1ull << q;
+        int nbq = (int)bq.size(), next = seed;
         for (;;) {
             int pos = -1;
             if (next >= 0) {
@@ -171,10 +173,8 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             } else {
                 int best_add = kMaxK + 1;
                 for (int r = 0; r < (int)rd.size(); r++) {
-                    const Unit &u = units[rd[r]];
-                    int add = 0;
-                    for (int i = 0; i < u.nq; i++) add += std::find(bq.begin(), bq.end(), u.q[i]) == bq.end();
-                    if ((int)bq.size() + add > kmax) continue;
+                    const int add = __builtin_popcountll(units[rd[r]].mask & ~bm);
+                    if (nbq + add > kmax) continue;
                     if (add < best_add || (add == best_add && rd[r] < rd[pos])) {
                         pos = r;
                         best_add = add;
@@ -188,7 +188,11 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
             taken.push_back(ui);
             const Unit &u = units[ui];
             for (int i = 0; i < u.nq; i++)
-                if (std::find(bq.begin(), bq.end(), u.q[i]) == bq.end()) bq.push_back(u.q[i]);
+                if (!((bm >> u.q[i]) & 1)) {
+                    bq.push_back(u.q[i]);
+                    bm |= 1ull << u.q[i];
+                    nbq++;
+                }
             for (const int sx : succ[ui])
                 if (--ind[sx] == 0) rd.push_back(sx);
         }
@@ -221,47 +225,82 @@ int group_gates(int n_qubits, const sim_gate *gates, const std::vector<int> &idx
         }
     }
     // Beam search (width > 1) for a schedule of fewer blocks: after each block, keep the `width`
-    // partial schedules that have placed the most units (earlier ones on ties).  A partial
-    // schedule is identified by its ready units, which fix the placed ones (the units not
-    // placed are exactly those at or after a ready unit), so two that reach the same ready
-    // units are one.  The first schedule to place every unit in fewer blocks than the greedy
-    // one replaces it.
+    // partial schedules that have placed the most units (earlier ones on ties).  Two partial
+    // schedules that have placed the same units are one; they are told apart by a key, the XOR
+    // of a random 64-bit word per placed unit (Zobrist hashing).  Each child is scored without
+    // being kept (its parent, seed, count and key) and only the `width` chosen are rebuilt.  The
+    // first schedule to place every unit in fewer blocks than the greedy one replaces it.
     if (width > 1) {
+        std::vector<uint64_t> zob(nu);
+        uint64_t z = 0;
+        for (int ui = 0; ui < nu; ui++) {  // splitmix64 (Steele, Lea, Flood 2014)
+            z += 0x9E3779B97F4A7C15ull;
+            uint64_t x = z;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            zob[ui] = x ^ (x >> 31);
+        }
         struct Partial {
-            int placed;
+            int placed = 0;
+            uint64_t key = 0;
             std::vector<int> ready, ind, seeds;
         };
-        std::vector<Partial> cur, next;
-        cur.push_back(Partial{0, ready0, indeg, {}});
-        std::map<std::vector<int>, int> seen;
-        std::vector<int> key;
+        struct Child {
+            int placed;
+            uint64_t key;
+            int parent, seed;
+        };
+        std::vector<Partial> cur(width), next(width);
+        cur[0].ready = ready0;
+        cur[0].ind = indeg;
+        int ncur = 1;
+        std::vector<Child> kids;
+        std::vector<int> rd2, ind2;
         bool done = false;
-        for (int depth = 1; depth < (int)seeds.size() && !done && !cur.empty(); depth++) {
-            next.clear();
-            seen.clear();
-            for (size_t pi = 0; pi < cur.size() && !done; pi++) {
+        for (int depth = 1; depth < (int)seeds.size() && !done; depth++) {
+            kids.clear();
+            for (int pi = 0; pi < ncur && !done; pi++) {
                 const Partial &p = cur[pi];
                 for (const int seed : p.ready) {
-                    Partial c{p.placed, p.ready, p.ind, p.seeds};
+                    rd2 = p.ready;
+                    ind2 = p.ind;
                     taken.clear();
                     bq.clear();
-                    fill(seed, c.ready, c.ind, taken, bq);
-                    c.placed += (int)taken.size();
-                    c.seeds.push_back(seed);
-                    if (c.placed == nu) {
-                        seeds = std::move(c.seeds);
+                    fill(seed, rd2, ind2, taken, bq);
+                    const int placed = p.placed + (int)taken.size();
+                    if (placed == nu) {
+                        seeds = p.seeds;
+                        seeds.push_back(seed);
                         done = true;
                         break;
                     }
-                    key = c.ready;
-                    std::sort(key.begin(), key.end());
-                    if (seen.emplace(key, (int)next.size()).second) next.push_back(std::move(c));
+                    uint64_t key = p.key;
+                    for (const int ui : taken) key ^= zob[ui];
+                    kids.push_back(Child{placed, key, pi, seed});
                 }
             }
-            std::stable_sort(next.begin(), next.end(),
-                             [](const Partial &a, const Partial &b) { return a.placed > b.placed; });
-            if ((int)next.size() > width) next.resize(width);
+            if (done) break;
+            std::stable_sort(kids.begin(), kids.end(), [](const Child &x, const Child &y) { return x.placed > y.placed; });
+            int nnext = 0;
+            for (const Child &c : kids) {
+                if (nnext == width) break;
+                bool dup = false;
+                for (int j = 0; j < nnext && !dup; j++) dup = next[j].key == c.key;
+                if (dup) continue;
+                const Partial &p = cur[c.parent];
+                Partial &d = next[nnext++];
+                d.placed = c.placed;
+                d.key = c.key;
+                d.ready = p.ready;
+                d.ind = p.ind;
+                d.seeds = p.seeds;
+                d.seeds.push_back(c.seed);
+                taken.clear();
+                bq.clear();
+                fill(c.seed, d.ready, d.ind, taken, bq);
+            }
             cur.swap(next);
+            ncur = nnext;
         }
     }
     // the blocks of the chosen schedule
