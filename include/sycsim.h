@@ -618,8 +618,9 @@ typedef struct srv_opts {
 
 typedef struct srv_stats_t {
     uint64_t submitted, completed, rejected, in_flight;
-    double p50_ms, p99_ms, mean_ms; /* latency: submit -> completion */
-    double circuits_per_s;          /* completed / (last completion - first submit) */
+    double p50_ms, p99_ms, mean_ms; /* latency: srv_submit's call (its planning included) ->
+                                     * completion */
+    double circuits_per_s;          /* completed / (last completion - first srv_submit call) */
     uint64_t hbm_budget, hbm_used;
     uint64_t graph_replays;         /* requests served by replaying a repeated circuit's CUDA graph */
 } srv_stats_t;

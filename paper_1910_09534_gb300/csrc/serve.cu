@@ -1038,6 +1038,7 @@ int srv_submit(srv_t *s, int n_qubits, int n_gates, const sim_gate *gates, void 
     if (!s || !ticket) return srv_fail(s, SIM_E_INVAL, "srv_submit: NULL argument");
     *ticket = 0;
     auto r = std::make_shared<Req>();
+    r->t_submit = Clock::now();  // latency counts from the call: planning below is part of it
     r->n = n_qubits;
     r->packed = n_qubits <= s->o.small_n;
     r->precision = r->packed ? SIM_FP32 : s->o.precision;
@@ -1235,7 +1236,7 @@ static int enqueue_request(srv_t *s, const std::shared_ptr<Req> &r, uint64_t *ti
         if (s->stop) return srv_fail(s, SIM_E_BUSY, "srv_submit: server is stopping");
         r->ticket = s->next_ticket++;
         r->h_res = s->h_results + 2 * (r->ticket % kResultRing);
-        r->t_submit = Clock::now();
+        if (r->t_submit == Clock::time_point{}) r->t_submit = Clock::now();
         if (s->submitted == 0) s->t_first = r->t_submit;
         s->submitted++;
         s->reqs[r->ticket] = r;
