@@ -57,6 +57,52 @@ void left_multiply_t(double *U, int D, const double *G, int l0, int l1)
     }
 }
 
+// U <- G U as left_multiply_t, with U's real and imaginary parts in separate D x D row-major
+// planes (so the loop over columns vectorises).
+template <int GD>
+void left_multiply_planes(double *ure, double *uim, int D, const double *G, int l0, int l1)
+{
+    double gr[GD][GD], gi[GD][GD];
+    for (int r = 0; r < GD; r++)
+        for (int x = 0; x < GD; x++) {
+            gr[r][x] = G[2 * (r * GD + x)];
+            gi[r][x] = G[2 * (r * GD + x) + 1];
+        }
+    for (int base = 0; base < D; base++) {
+        if ((base >> l0) & 1) continue;
+        if (GD == 4 && ((base >> l1) & 1)) continue;
+        int rows[GD];
+        rows[0] = base;
+        rows[1] = base | (1 << l0);
+        if (GD == 4) {
+            rows[2] = base | (1 << l1);
+            rows[3] = base | (1 << l0) | (1 << l1);
+        }
+        double *pr[GD], *pi[GD];
+        for (int x = 0; x < GD; x++) {
+            pr[x] = ure + (size_t)rows[x] * D;
+            pi[x] = uim + (size_t)rows[x] * D;
+        }
+#pragma GCC ivdep
+        for (int c = 0; c < D; c++) {
+            double xr[GD], xi[GD];
+            for (int x = 0; x < GD; x++) {
+                xr[x] = pr[x][c];
+                xi[x] = pi[x][c];
+            }
+            for (int r = 0; r < GD; r++) {
+                double re = 0, im = 0;
+                for (int x = 0; x < GD; x++) {
+                    re += gr[r][x] * xr[x] - gi[r][x] * xi[x];
+                    im += gr[r][x] * xi[x] + gi[r][x] * xr[x];
+                }
+                pr[r][c] = re;
+                pi[r][c] = im;
+            }
+        }
+    }
+}
+
 // Beam width of the block search (sim_plan_opts.search; 0 = the default, 1 = the greedy
 // schedule alone).
 constexpr int kPlanSearchDefault = 16, kPlanSearchMax = 256;
@@ -414,13 +460,20 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
         }
     }
     // compose each block in FP64: each unit's gates first into one 2x2 or 4x4 matrix (local bit 0
-    // = the unit's first qubit), then that matrix into the block
+    // = the unit's first qubit), then that matrix into the block.  The block's matrix grows with
+    // its qubits: it starts as the 1x1 identity, and when a unit brings a qubit the block has not
+    // met yet, the matrix becomes M (x) I on a new top bit, so a unit is multiplied in on the
+    // qubits met so far (2-2.7x fewer products at k_max 5-6 than on all k from the start).  The
+    // local bits follow the order the qubits were met; the last step reorders rows and columns
+    // to ascending qubits.  Real and imaginary parts are kept in separate planes.
+    std::vector<double> mre, mim, tre, tim;
     for (size_t bi = 0; bi < p->blocks.size(); bi++) {
         PlanBlock &b = p->blocks[bi];
         std::sort(b.qubits.begin(), b.qubits.end());
         const int k = (int)b.qubits.size(), D = 1 << k;
-        b.mat.assign(2 * D * D, 0.0);
-        for (int i = 0; i < D; i++) b.mat[2 * (i * D + i)] = 1.0;
+        int met[kMaxK], n_met = 0, d = 1;
+        mre.assign(1, 1.0);
+        mim.assign(1, 0.0);
         for (int ui : block_units[bi]) {
             const Unit &u = units[ui];
             const int ud = u.nq == 2 ? 4 : 2;
@@ -428,22 +481,57 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
             for (int i = 0; i < ud; i++) Mu[2 * (i * ud + i)] = 1.0;
             for (int gi : u.gates) {
                 const sim_gate &g = gates[gi];
-                const int d = gate_matrix(g, G);
-                if (d == 4) {
+                const int gd = gate_matrix(g, G);
+                if (gd == 4) {
                     const bool same = g.q0 == u.q[0];  // the gate's bit 0 on the unit's bit 0?
                     left_multiply_t<4>(Mu, 4, G, same ? 0 : 1, same ? 1 : 0);
                 } else {
                     left_multiply_t<2>(Mu, ud, G, g.q0 == u.q[0] ? 0 : 1, -1);
                 }
             }
-            const int l0 = (int)(std::find(b.qubits.begin(), b.qubits.end(), u.q[0]) - b.qubits.begin());
-            if (u.nq == 2) {
-                const int l1 = (int)(std::find(b.qubits.begin(), b.qubits.end(), u.q[1]) - b.qubits.begin());
-                left_multiply_t<4>(b.mat.data(), D, Mu, l0, l1);
-            } else {
-                left_multiply_t<2>(b.mat.data(), D, Mu, l0, -1);
+            int lb[2] = {-1, -1};
+            for (int i = 0; i < u.nq; i++) {
+                lb[i] = (int)(std::find(met, met + n_met, u.q[i]) - met);
+                if (lb[i] < n_met) continue;
+                // a new qubit: M -> diag(M, M), the qubit on the new top bit
+                const int d2 = 2 * d;
+                tre.assign((size_t)d2 * d2, 0.0);
+                tim.assign((size_t)d2 * d2, 0.0);
+                for (int r = 0; r < d; r++)
+                    for (int c = 0; c < d; c++) {
+                        const double vr = mre[(size_t)r * d + c], vi = mim[(size_t)r * d + c];
+                        tre[(size_t)r * d2 + c] = vr;
+                        tim[(size_t)r * d2 + c] = vi;
+                        tre[(size_t)(d + r) * d2 + d + c] = vr;
+                        tim[(size_t)(d + r) * d2 + d + c] = vi;
+                    }
+                mre.swap(tre);
+                mim.swap(tim);
+                d = d2;
+                met[n_met++] = u.q[i];
             }
+            if (u.nq == 2)
+                left_multiply_planes<4>(mre.data(), mim.data(), d, Mu, lb[0], lb[1]);
+            else
+                left_multiply_planes<2>(mre.data(), mim.data(), d, Mu, lb[0], -1);
         }
+        // local bit i (the i-th qubit met) -> bit pos[i] of the ascending order
+        int pos[kMaxK];
+        for (int i = 0; i < n_met; i++)
+            pos[i] = (int)(std::find(b.qubits.begin(), b.qubits.end(), met[i]) - b.qubits.begin());
+        std::vector<int> to(D);
+        for (int x = 0; x < D; x++) {
+            int y = 0;
+            for (int i = 0; i < n_met; i++) y |= ((x >> i) & 1) << pos[i];
+            to[x] = y;
+        }
+        b.mat.assign(2 * (size_t)D * D, 0.0);
+        for (int r = 0; r < D; r++)
+            for (int c = 0; c < D; c++) {
+                const size_t o = 2 * ((size_t)to[r] * D + to[c]);
+                b.mat[o] = mre[(size_t)r * D + c];
+                b.mat[o + 1] = mim[(size_t)r * D + c];
+            }
     }
     *out = p;
     return SIM_OK;
