@@ -515,6 +515,10 @@ int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_
             else
                 left_multiply_planes<2>(mre.data(), mim.data(), d, Mu, lb[0], -1);
         }
+        if (d != D) {  // the units' qubits are the block's qubits by construction
+            delete p;
+            return fail(nullptr, SIM_E_INVAL, "sim_plan_create: block %zu met %d of its %d qubits", bi, n_met, k);
+        }
         // local bit i (the i-th qubit met) -> bit pos[i] of the ascending order
         int pos[kMaxK];
         for (int i = 0; i < n_met; i++)
