@@ -198,6 +198,43 @@ def test_planner_custom_matrices(pkg, oracle_mod):
     assert np.linalg.norm(got - psi) < 1e-12
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_planner_random_pairs_and_lone_qubits(pkg, oracle_mod, seed):
+    # arbitrary one- and two-qubit unitaries on random (not lattice) pairs of 7 qubits, two of
+    # which only ever see single-qubit gates (units of one qubit): at every width and search,
+    # the blocks -- composed on the qubits met so far, in the order met, then reordered --
+    # reproduce the gate-by-gate run
+    n, lone = 7, (2, 5)
+    rng = np.random.default_rng(40 + seed)
+    paired = [q for q in range(n) if q not in lone]
+    recs = np.zeros(60, dtype=pkg._native.GATE_DTYPE)
+    psi = oracle_mod.basis_state(n, 0)
+    for i in range(recs.size):
+        if rng.random() < 0.4:
+            q = int(rng.integers(n))
+            u = si.random_unitary(1, seed=1000 * seed + i)
+            recs[i]["kind"], recs[i]["q0"] = pkg.SIM_GATE_U1, q
+            recs[i]["u"][:8] = u.view(np.float64).ravel()
+            oracle_mod.apply_1q(psi, q, u)
+        else:
+            q0, q1 = (int(x) for x in rng.choice(paired, 2, replace=False))
+            u = si.random_unitary(2, seed=1000 * seed + i)
+            recs[i]["kind"], recs[i]["q0"], recs[i]["q1"] = pkg.SIM_GATE_U2, q0, q1
+            recs[i]["u"][:] = u.view(np.float64).ravel()
+            oracle_mod.apply_2q(psi, q0, q1, u)
+    for kmax in (2, 3, 4, 5, 6):
+        for search in (1, 3, 16):
+            plan = pkg.sim_plan_create(n, recs, kmax=kmax, search=search)
+            try:
+                got = oracle_mod.basis_state(n, 0)
+                for t, m in plan_blocks(pkg, plan):
+                    assert list(t) == sorted(t) and len(t) <= kmax
+                    oracle_mod.apply_kq(got, t, m)
+                assert np.linalg.norm(got - psi) < 1e-12, (kmax, search)
+            finally:
+                pkg.sim_plan_destroy(plan)
+
+
 def test_planner_rejects_bad_gates(pkg):
     recs = np.zeros(1, dtype=pkg._native.GATE_DTYPE)
     recs[0]["kind"], recs[0]["q0"], recs[0]["q1"] = si.FSIM, 2, 2
