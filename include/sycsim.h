@@ -287,6 +287,9 @@ typedef struct sim_plan_opts {
  * qubits; Appendix A "new cache" lines list such groups).  Partitions the gate
  * list into blocks that respect gate order on every qubit and composes each
  * block's 2^k x 2^k matrix in FP64 (later gates multiply from the left).
+ * Blocks are formed greedily, each from the seed unit that lets it take the most
+ * gates; with o->search > 1 (the default, 0, means 16) a beam search over those
+ * seeds replaces that schedule when it finds one of fewer blocks.
  * Host-side; the plan is immutable and may be applied to many handles. */
 int sim_plan_create(int n_qubits, int n_gates, const sim_gate *gates, const sim_plan_opts *o,
                     sim_plan_t **out);
